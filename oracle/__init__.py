@@ -1,0 +1,296 @@
+"""FP64 CPU oracle of the PackUV-GS render step (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``packuv_oracle.c`` (plain C,
+double precision, single-threaded) through ctypes; it shares no code with the
+CUDA library.  See the C file's header for the passage of the paper each
+function follows.
+
+Inputs are scene-like objects with the attributes ``atlas`` ([F][D][H][W]
+float32/float16), ``occ`` / ``dyn`` (bit-packed rows), ``sh_degree``,
+``views`` (objects with R, t, fx, fy, cx, cy, width, height, frame) and
+``n_live``.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "packuv_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle_packuv.so")
+_lock = threading.Lock()
+_lib = None
+
+VS = 20     # doubles per view
+REC = 12    # doubles per projected record
+G2D = 9     # doubles per per-view 2D gradient
+ZNEAR = 0.01
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+P = C.c_void_p
+I32, I64, U64, DBL = C.c_int32, C.c_int64, C.c_uint64, C.c_double
+
+
+def _declare(L):
+    sig = {
+        "or_pyramid_sizes": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P]),
+        "or_atlas_layout": (C.c_int, [C.c_int, C.c_int, P, P]),
+        "or_texel_to_uv": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P]),
+        "or_uv_to_texel": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int, P]),
+        "or_half_to_double": (DBL, [C.c_uint16]),
+        "or_count_live": (I64, [P, C.c_int, C.c_int]),
+        "or_gather": (I64, [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, P, I64, P, P, P]),
+        "or_quat_rot": (None, [P, P]),
+        "or_sh_basis": (None, [C.c_int, P, P, P]),
+        "or_project": (None, [P, I64, I64, C.c_int, C.c_int, P, C.c_int, DBL, P]),
+        "or_tiles_total": (I64, [C.c_int, P, P, C.c_int, P]),
+        "or_bin_sort": (I64, [P, P, P, P, C.c_int, I64, P, P, C.c_int, P, I64, P]),
+        "or_render": (U64, [P, C.c_int, I64, P, C.c_int, P, P, P, DBL, P, P, P, P]),
+        "or_render_bwd": (None, [P, C.c_int, I64, P, C.c_int, P, P, P, P, P]),
+        "or_scatter_grad": (None, [P, I64, I64, C.c_int, C.c_int, P, C.c_int, DBL, P, P, P]),
+        "or_render_pixels": (None, [P, C.c_int, I64, P, C.c_int, P, DBL, I64, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+# --------------------------------------------------------------------------
+# Layout
+# --------------------------------------------------------------------------
+
+def pyramid_sizes(M0, N0, K):
+    M = np.zeros(K, np.int32)
+    N = np.zeros(K, np.int32)
+    if lib().or_pyramid_sizes(M0, N0, K, _p(M), _p(N)):
+        raise ValueError("invalid pyramid")
+    return M, N
+
+
+def atlas_layout(S, K):
+    lv = np.zeros((K, 5), np.int32)
+    wh = np.zeros(2, np.int32)
+    if lib().or_atlas_layout(S, K, _p(lv), _p(wh)):
+        raise ValueError("invalid layout")
+    return [tuple(int(a) for a in r) for r in lv], (int(wh[0]), int(wh[1]))
+
+
+def texel_to_uv(levels, x, y):
+    lv = np.ascontiguousarray(np.asarray(levels, np.int32))
+    out = np.zeros(3, np.int32)
+    if lib().or_texel_to_uv(_p(lv), len(levels), x, y, _p(out)):
+        return None
+    return tuple(int(a) for a in out)
+
+
+def uv_to_texel(levels, k, u, v):
+    lv = np.ascontiguousarray(np.asarray(levels, np.int32))
+    out = np.zeros(2, np.int32)
+    if lib().or_uv_to_texel(_p(lv), len(levels), k, u, v, _p(out)):
+        return None
+    return int(out[0]), int(out[1])
+
+
+def half_to_double(h: int) -> float:
+    return lib().or_half_to_double(int(h))
+
+
+# --------------------------------------------------------------------------
+# Steps
+# --------------------------------------------------------------------------
+
+def views_array(views) -> np.ndarray:
+    a = np.zeros((len(views), VS), np.float64)
+    for i, v in enumerate(views):
+        a[i, 0:9] = np.asarray(v.R, np.float64).reshape(9)
+        a[i, 9:12] = np.asarray(v.t, np.float64)
+        a[i, 12:16] = (v.fx, v.fy, v.cx, v.cy)
+        a[i, 16:19] = (v.width, v.height, v.frame)
+    return a
+
+
+def count_live(occ, H, W) -> int:
+    occ = np.ascontiguousarray(occ, np.uint32)
+    return int(lib().or_count_live(_p(occ), H, W))
+
+
+def gather(scene):
+    atlas = np.ascontiguousarray(scene.atlas)
+    F, D, H, W = atlas.shape
+    dtype = 1 if atlas.dtype == np.float16 else 0
+    if dtype == 0:
+        atlas = np.ascontiguousarray(atlas, np.float32)
+    occ = np.ascontiguousarray(scene.occ, np.uint32)
+    dyn = None if scene.dyn is None else np.ascontiguousarray(scene.dyn, np.uint32)
+    N = count_live(occ, H, W)
+    soa = np.zeros((D, F * N), np.float64)
+    texel = np.zeros(N, np.uint32)
+    dynflag = np.zeros(N, np.uint8)
+    r = lib().or_gather(_p(atlas), dtype, F, D, H, W, _p(occ), _p(dyn), N, _p(soa), _p(texel), _p(dynflag))
+    assert r == N
+    return soa, texel, dynflag
+
+
+def quat_rot(q):
+    q = np.ascontiguousarray(q, np.float64)
+    R = np.zeros(9, np.float64)
+    lib().or_quat_rot(_p(q), _p(R))
+    return R.reshape(3, 3)
+
+
+def sh_basis(deg, d):
+    d = np.ascontiguousarray(d, np.float64)
+    Y = np.zeros(16, np.float64)
+    dY = np.zeros(48, np.float64)
+    lib().or_sh_basis(deg, _p(d), _p(Y), _p(dY))
+    nb = (deg + 1) ** 2
+    return Y[:nb], dY.reshape(16, 3)[:nb]
+
+
+def project(soa, N, sh_degree, views_arr, znear=ZNEAR):
+    soa = np.ascontiguousarray(soa, np.float64)
+    D, G = soa.shape
+    V = views_arr.shape[0]
+    rec = np.zeros((V, N, REC), np.float64)
+    lib().or_project(_p(soa), G, N, D, sh_degree, _p(np.ascontiguousarray(views_arr)), V, znear, _p(rec))
+    return rec
+
+
+def tiles_total(views_arr, tile):
+    vw = np.ascontiguousarray(views_arr[:, 16], np.int32)
+    vh = np.ascontiguousarray(views_arr[:, 17], np.int32)
+    toff = np.zeros(len(vw) + 1, np.int64)
+    t = lib().or_tiles_total(len(vw), _p(vw), _p(vh), tile, _p(toff))
+    return int(t), toff[:-1]
+
+
+def bin_sort32(mx, my, rad, z, views_arr, N, tile, cap=None):
+    """Integer stage on FP32 inputs (each a flat [V*N] float32 array)."""
+    mx, my, rad, z = (np.ascontiguousarray(a, np.float32).reshape(-1) for a in (mx, my, rad, z))
+    V = views_arr.shape[0]
+    vw = np.ascontiguousarray(views_arr[:, 16], np.int32)
+    vh = np.ascontiguousarray(views_arr[:, 17], np.int32)
+    ntiles, _ = tiles_total(views_arr, tile)
+    ranges = np.zeros((ntiles, 2), np.uint32)
+    n = lib().or_bin_sort(_p(mx), _p(my), _p(rad), _p(z), V, N, _p(vw), _p(vh), tile, None, 0, _p(ranges))
+    vals = np.zeros(max(n, 1), np.uint32)
+    n2 = lib().or_bin_sort(_p(mx), _p(my), _p(rad), _p(z), V, N, _p(vw), _p(vh), tile, _p(vals), n, _p(ranges))
+    assert n2 == n
+    return vals[:n].copy(), ranges
+
+
+def bin_sort(rec, views_arr, tile):
+    V, N, _ = rec.shape
+    r = rec.reshape(V * N, REC)
+    return bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], views_arr, N, tile)
+
+
+def render(rec, views_arr, tile, vals, ranges, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
+    V, N, _ = rec.shape
+    P = int(np.sum(views_arr[:, 16] * views_arr[:, 17]))
+    img = np.zeros(3 * P, np.float64)
+    T = np.zeros(P, np.float64)
+    last = np.zeros(P, np.uint32)
+    border = np.zeros(P, np.uint8)
+    bg = np.ascontiguousarray(bg, np.float64)
+    h = lib().or_render(_p(np.ascontiguousarray(rec)), V, N, _p(np.ascontiguousarray(views_arr)), tile,
+                        _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
+                        _p(bg), m_tol, _p(img), _p(T), _p(last), _p(border))
+    return dict(img=img, T=T, last=last, border=border, hash=int(h))
+
+
+def render_bwd(rec, views_arr, tile, vals, ranges, dimg, bg=(0.0, 0.0, 0.0)):
+    V, N, _ = rec.shape
+    g2 = np.zeros((V, N, G2D), np.float64)
+    bg = np.ascontiguousarray(bg, np.float64)
+    lib().or_render_bwd(_p(np.ascontiguousarray(rec)), V, N, _p(np.ascontiguousarray(views_arr)), tile,
+                        _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
+                        _p(bg), _p(np.ascontiguousarray(dimg, np.float64)), _p(g2))
+    return g2
+
+
+def scatter_grad(soa, N, sh_degree, views_arr, grad2d, dynflag=None, znear=ZNEAR):
+    soa = np.ascontiguousarray(soa, np.float64)
+    D, G = soa.shape
+    V = views_arr.shape[0]
+    out = np.zeros((D, G), np.float64)
+    df = None if dynflag is None else np.ascontiguousarray(dynflag, np.uint8)
+    lib().or_scatter_grad(_p(soa), G, N, D, sh_degree, _p(np.ascontiguousarray(views_arr)), V, znear,
+                          _p(np.ascontiguousarray(grad2d, np.float64)), _p(df), _p(out))
+    return out
+
+
+def render_pixels(rec, views_arr, tile, pix, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
+    V, N, _ = rec.shape
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
+    n = pix.shape[0]
+    rgb = np.zeros((n, 3), np.float64)
+    T = np.zeros(n, np.float64)
+    border = np.zeros(n, np.uint8)
+    lib().or_render_pixels(_p(np.ascontiguousarray(rec)), V, N, _p(np.ascontiguousarray(views_arr)), tile,
+                           _p(np.ascontiguousarray(bg, np.float64)), m_tol, n, _p(pix), _p(rgb), _p(T), _p(border))
+    return rgb, T, border
+
+
+# --------------------------------------------------------------------------
+# Whole step
+# --------------------------------------------------------------------------
+
+def forward(scene, tile=16, znear=ZNEAR, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
+    soa, texel, dynflag = gather(scene)
+    va = views_array(scene.views)
+    N = len(texel)
+    rec = project(soa, N, scene.sh_degree, va, znear)
+    vals, ranges = bin_sort(rec, va, tile)
+    out = render(rec, va, tile, vals, ranges, bg, m_tol)
+    out.update(soa=soa, texel=texel, dynflag=dynflag, views=va, rec=rec, vals=vals, ranges=ranges, N=N)
+    return out
+
+
+def backward(scene, fwd, dimg, tile=16, znear=ZNEAR, bg=(0.0, 0.0, 0.0)):
+    g2 = render_bwd(fwd["rec"], fwd["views"], tile, fwd["vals"], fwd["ranges"], dimg, bg)
+    gsoa = scatter_grad(fwd["soa"], fwd["N"], scene.sh_degree, fwd["views"], g2, fwd["dynflag"]
+                        if scene.dyn is not None else None, znear)
+    return dict(grad2d=g2, grad_soa=gsoa)
+
+
+def grad_to_atlas(scene, grad_soa, texel):
+    """Place [D][F*N] gradients at their texels: [F][D][H][W] (zeros elsewhere)."""
+    F, D, H, W = scene.atlas.shape
+    N = len(texel)
+    out = np.zeros((F, D, H * W), np.float64)
+    for f in range(F):
+        out[f][:, texel] = grad_soa[:, f * N:(f + 1) * N]
+    return out.reshape(F, D, H, W)
