@@ -1,0 +1,418 @@
+#!/usr/bin/env python3
+"""Benchmark of the PackUV-GS render step (forward + backward) on GB300.
+
+One step = one fitting iteration over every view of the workload: atlas
+gather, projection + SH, binning + sort, forward compositing, L1 loss
+gradient, backward compositing, texel-gradient scatter -- all views in one
+sequence of launches, captured once in a CUDA graph and replayed.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on bounded samples of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "fwd+bwd rendered MPix/s on 1 GB300, batched vs per-view, % of HBM roofline"
+UNIT = "MPix/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+# FP32 operations of one (pixel, splat) evaluation, counted from the method:
+# forward 17 (offset 2, quadratic form 5, exponent 2, alpha 2, transmittance
+# 2, blend 4); backward 45 (the forward's 10 to recompute alpha, transmittance
+# recovery 2, dL/dalpha 9, colour 6, opacity/conic/mean 14, warp sum share 4).
+OPS_FWD = 17
+OPS_BWD = 45
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of one step (the byte model of the method)
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(plan, texel_bytes, dups, n_dyn):
+    N, V, D, P = plan.N, plan.V, plan.D, plan.P
+    G = plan.G
+    return {
+        "a1_atlas_gather": G * D * texel_bytes + G * D * 4,
+        "a2_project_and_sh": G * D * 4 + plan.pairs * 48,
+        "a3_bin_and_sort": dups * (12 + 24),
+        "a4_rasterize_fwd": dups * 40 + P * 20,
+        "a5_rasterize_bwd": dups * 40 + P * 20 + plan.pairs * 36,
+        "a6_atlas_scatter_grad": G * D * 4 + plan.pairs * 36 + n_dyn * D * 4,
+    }
+
+
+def launches_per_step(plan):
+    npass = (max(1, math.ceil(math.log2(max(2, plan.n_tiles)))) + 7) // 8
+    # gather 2, project 1, bin_and_sort 21 + 3 per tile-sort pass, fwd 1, loss 1, bwd 1, scatter 1
+    return 2 + 1 + (21 + 3 * npass) + 4
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on bounded windows of the workload's views
+# ---------------------------------------------------------------------------
+
+def window_views(scene, n, size, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in rng.choice(len(scene.views), n, replace=False):
+        v = scene.views[int(i)]
+        w, h = min(size, v.width), min(size, v.height)
+        x0, y0 = (v.width - w) // 2, (v.height - h) // 2
+        out.append(synth.View(R=v.R, t=v.t, fx=v.fx, fy=v.fy, cx=v.cx - x0, cy=v.cy - y0, width=w, height=h,
+                              frame=v.frame))
+    return out
+
+
+def oracle_step(orc, scene, views, soa, texel, dynflag, target_seed=0):
+    """One oracle fwd + L1 + bwd over `views`; returns pixels rendered."""
+    va = orc.views_array(views)
+    N = len(texel)
+    rec = orc.project(soa, N, scene.sh_degree, va)
+    vals, ranges = orc.bin_sort(rec, va, 16)
+    r = orc.render(rec, va, 16, vals, ranges)
+    P = int(sum(v.width * v.height for v in views))
+    tgt = np.random.default_rng(target_seed).uniform(0, 1, 3 * P)
+    dimg = np.sign(r["img"] - tgt) / (3 * P)
+    g2 = orc.render_bwd(rec, va, 16, vals, ranges, dimg)
+    orc.scatter_grad(soa, N, scene.sh_degree, va, g2, dynflag if scene.dyn is not None else None)
+    return P
+
+
+def cpu_baseline(scene, budget_s=20.0, window=256):
+    import oracle as orc
+    soa, texel, dynflag = orc.gather(scene)
+    t0 = time.perf_counter()
+    pix, n = 0, 0
+    views = window_views(scene, min(8, len(scene.views)), window)
+    while n < len(views) and (time.perf_counter() - t0) < budget_s:
+        pix += oracle_step(orc, scene, [views[n]], soa, texel, dynflag, n)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": pix / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} view windows of {window}x{window} px from {scene.name}, all {scene.n_live} "
+                      f"Gaussians each, fwd + L1 + bwd in FP64, single thread",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the FP64 CPU oracle, on bounded samples of the same workload."""
+    if rank != 0:
+        return 0
+    import oracle as orc
+    scene = synth.config_scene(args.config)
+    soa, texel, dynflag = orc.gather(scene)
+    views = window_views(scene, len(scene.views), args.ref_window, seed=1)
+    times, pix = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        p = oracle_step(orc, scene, [views[i % len(views)]], soa, texel, dynflag, i)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            pix += p
+    total = sum(times)
+    value = pix / total / 1e6
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": scene.name, "sample": f"one {args.ref_window}x{args.ref_window} px window "
+                                                         f"of one view per step, all {scene.n_live} Gaussians"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.ref_window}x{args.ref_window} px window per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--ref-window", type=int, default=192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-view", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="short run for a profiler: no extras")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2602_23040_gb300 as pk
+
+    pk.build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    scene = synth.config_scene(args.config)
+    F, D, Hh, W = scene.atlas.shape
+    texel_bytes = scene.atlas.dtype.itemsize
+    dev = torch.device("cuda", local)
+    atlas = torch.from_numpy(scene.atlas).to(dev)
+    occ = torch.from_numpy(scene.occ.view(np.int32)).to(dev)
+    dyn = None if scene.dyn is None else torch.from_numpy(scene.dyn.view(np.int32)).to(dev)
+    target = torch.from_numpy(synth.random_target(scene)).to(dev)
+    grad = torch.zeros(F * D * Hh * W, dtype=torch.float32, device=dev)
+
+    # plan sized from a first eager step (re-planned once if the entries overflow)
+    r = pk.Renderer(pk.Plan.for_scene(scene), dev)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        r.ensure_capacity(atlas, occ, dyn)
+        r.l1_step(atlas, occ, dyn, target, grad)
+    plan = r.plan
+    st = r.status(stream)
+    assert st["flags"] == 0, st
+    dups, evals_fwd, evals_bwd = int(st["dups"]), int(st["evals_fwd"]), int(st["evals_bwd"])
+
+    # CUDA graph of the whole step
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        r.l1_step(atlas, occ, dyn, target, grad)
+    for _ in range(max(3, args.warmup)):
+        g.replay()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    mpix = plan.P * world / (ms * 1e-3) / 1e6
+
+    # per-call durations (eager, CUDA events on the launching stream)
+    stage_names = ["a1_atlas_gather", "a2_project_and_sh", "a3_bin_and_sort", "a4_rasterize_fwd", "l1_loss_grad",
+                   "a5_rasterize_bwd", "a6_atlas_scatter_grad"]
+    calls = [
+        lambda: pk.atlas_gather(plan, atlas, occ, dyn, r.soa, r.texel, r.dynflag, r.ws),
+        lambda: pk.project_and_sh(plan, r.soa, r.records, r.ws),
+        lambda: pk.bin_and_sort(plan, r.records, r.sorted_vals, r.ranges, r.ws),
+        lambda: pk.rasterize_fwd(plan, r.records, r.sorted_vals, r.ranges, r.image, r.T, r.n_contrib, r.ws),
+        lambda: pk.l1_loss_grad(plan, r.image, target, r.dimage, r.ws),
+        lambda: pk.rasterize_bwd(plan, r.records, r.sorted_vals, r.ranges, r.T, r.n_contrib, r.dimage, r.grad2d,
+                                 r.ws),
+        lambda: pk.atlas_scatter_grad(plan, r.soa, r.grad2d, r.dynflag if dyn is not None else None, r.texel,
+                                      grad, False, r.ws),
+    ]
+    ksteps = max(1, min(args.steps, 5))
+    stage_ms = {n: 0.0 for n in stage_names}
+    with torch.cuda.stream(stream):
+        for _ in range(ksteps):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)]
+            evs[0].record(stream)
+            for i, c in enumerate(calls):
+                c()
+                evs[i + 1].record(stream)
+            torch.cuda.synchronize(dev)
+            for i, n in enumerate(stage_names):
+                stage_ms[n] += evs[i].elapsed_time(evs[i + 1]) / ksteps
+
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+    n_dyn = plan.G if scene.dyn is None else int(r.dynflag[:plan.N].sum().item()) * F
+    bytes_alg = algorithmic_bytes(plan, texel_bytes, dups, n_dyn)
+    step_bytes = sum(bytes_alg.values())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"]))
+    alu_peak_tops = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    dom = max(("a1_atlas_gather", "a2_project_and_sh", "a3_bin_and_sort", "a4_rasterize_fwd",
+               "a5_rasterize_bwd", "a6_atlas_scatter_grad"), key=lambda n: stage_ms[n])
+    t_dom = stage_ms[dom] * 1e-3
+    if dom in ("a4_rasterize_fwd", "a5_rasterize_bwd"):
+        ops = (evals_fwd * OPS_FWD) if dom == "a4_rasterize_fwd" else (evals_bwd * OPS_BWD)
+        ach = ops / t_dom / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak_tops, "unit": "TOP/s (FP32)",
+                "frac": ach / alu_peak_tops, "traffic": None,
+                "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz",
+                "hbm_frac": bytes_alg[dom] / t_dom / 1e9 / hbm}
+    else:
+        ach = bytes_alg[dom] / t_dom / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None, "peak_source": f"hbm_gbs ({peak_kind})"}
+
+    out = {
+        "metric": METRIC, "value": mpix, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": scene.name, "gaussians": plan.G, "views": plan.V, "pixels": plan.P,
+                   "sh_degree": scene.sh_degree, "texels": "fp16" if texel_bytes == 2 else "fp32",
+                   "tile": 16, "graph": "whole step in one CUDA graph",
+                   "l2": "inputs larger than L2 (atlas %.0f MB, records %.0f MB)" % (
+                       scene.atlas.nbytes / 1e6, plan.pairs * 48 / 1e6),
+                   "parallelism": f"replica x{world}" if world > 1 else "single GPU"},
+        "gaussians_per_s": plan.G * plan.V * world / (ms * 1e-3),
+        "hbm_roofline_step": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                              "peak_gbs": hbm, "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm, "peak": peak_kind},
+        "roofline": roof,
+        "stages_ms": stage_ms,
+        "counts": {"dups": dups, "evals_fwd": evals_fwd, "evals_bwd": evals_bwd, "valid_pairs": int(st["valid_pairs"])},
+        "gpu_launches": launches_per_step(plan) * args.steps,
+        "clocks": clk,
+    }
+
+    if not args.profile and not args.no_e2e:
+        # end to end through the public API with host buffers
+        h_atlas = torch.from_numpy(scene.atlas).pin_memory()
+        h_target = torch.from_numpy(synth.random_target(scene)).pin_memory()
+        h_grad = torch.empty(grad.numel(), dtype=torch.float32).pin_memory()
+        ke = max(1, min(args.steps, 5))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            with torch.cuda.stream(stream):
+                atlas.copy_(h_atlas, non_blocking=True)
+                target.copy_(h_target, non_blocking=True)
+                g.replay()
+                h_grad.copy_(grad, non_blocking=True)
+            s = r.status(stream)          # device -> host read of the loss, synchronises the stream
+        dt = (time.perf_counter() - t0) / ke
+        out["e2e"] = {"value": plan.P / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
+                      "h2d_bytes_per_step": int(h_atlas.numel() * h_atlas.element_size() +
+                                                h_target.numel() * 4),
+                      "d2h_bytes_per_step": int(h_grad.numel() * 4 + 64), "loss": s["loss"]}
+
+    if not args.profile and not args.no_per_view and rank == 0:
+        loop = pk.PerViewLoop.for_scene(scene, dev, max_dups=int(dups / max(1, plan.V) * 4) + 65536)
+        with torch.cuda.stream(stream):
+            loop.step(atlas, occ, dyn, target, grad)
+        torch.cuda.synchronize(dev)
+        kp = max(1, min(args.steps, 3))
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a0.record(stream)
+            for _ in range(kp):
+                loop.step(atlas, occ, dyn, target, grad)
+            a1.record(stream)
+        torch.cuda.synchronize(dev)
+        pv_ms = a0.elapsed_time(a1) / kp
+        ok = all(pk.read_status(p, w)["flags"] == 0 for p, w in zip(loop.plans, loop.ws))
+        out["per_view_loop"] = {"value": plan.P / (pv_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pv_ms,
+                                "launch": "eager, one view per call sequence", "status_ok": ok,
+                                "batched_speedup": pv_ms / ms}
+        del loop
+
+    if not args.profile and not args.no_cpu_baseline and rank == 0:
+        out["cpu_baseline"] = cpu_baseline(scene)
+
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

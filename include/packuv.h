@@ -1,0 +1,265 @@
+/*
+ * packuv.h -- C ABI of the PackUV-GS render step on one GB300 (sm_103a).
+ *
+ * The library renders Gaussians stored as texels of packed multi-scale UV
+ * atlases (PackUV, arXiv 2602.23040, Sec. 4.1 "Pyramid UV Mapping" and "UV
+ * Atlas Layout"; Sec. 4.2 "Fitting UV Maps Directly") with the tile-based
+ * splatting rasteriser of 3DGS (Sec. 3), and returns gradients to the
+ * texels (Sec. 4.2 "Objective", "Gradient Freezing", "Low Precision
+ * Optimization").  One fitting iteration is the chain
+ *
+ *   pk_atlas_gather -> pk_project_and_sh -> pk_bin_and_sort ->
+ *   pk_rasterize_fwd -> [loss] -> pk_rasterize_bwd -> pk_atlas_scatter_grad
+ *
+ * over every view (camera x frame) of the plan in one sequence of launches.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All array arguments are raw DEVICE pointers owned by the caller; the
+ *    library never frees them and never allocates device memory after
+ *    pk_plan_create (which allocates none either), so every call can be
+ *    captured in a CUDA graph.  Scratch lives in the caller-owned
+ *    `workspace` of pk_sizes.workspace_bytes, initialised once by
+ *    pk_workspace_init.
+ *  - Every call only enqueues work on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream) and returns without synchronising.  Host-side
+ *    argument errors return a non-zero pk_status before anything is
+ *    enqueued.  Errors found on the device (capacity overflow, a mismatch of
+ *    the live-texel count, non-finite splats) are recorded in the status
+ *    block inside the workspace; read it with pk_read_status.  No kernel
+ *    traps, asserts or spins without bound.
+ *  - Pointers must be 16-byte aligned (256-byte for the workspace).
+ *  - Texel channels (D = 11 + 3 (L+1)^2): 0..2 position, 3..5 log-scale,
+ *    6..9 quaternion (w, x, y, z), 10 opacity logit, 11 + 3 j + c the SH
+ *    coefficient j = l^2 + l + m of colour c (real SH, Condon-Shortley
+ *    phase, degree L <= 3).
+ *  - Gaussian g of frame f is the g-th live texel of the occupancy mask in
+ *    row-major atlas order; its global index is f * N + g.
+ *  - A "pair" is (view v, Gaussian g of v's frame), index v * N + g.
+ *  - Images are planar per view, views concatenated: channel c of pixel
+ *    (x, y) of view v is at 3 * pix_off(v) + c * W_v * H_v + y * W_v + x,
+ *    with pix_off(v) = sum_{u<v} W_u H_u; per-pixel scalars at
+ *    pix_off(v) + y * W_v + x.
+ *  - Constants: opacity alpha = min(0.99, o exp(-q/2)); a splat is skipped
+ *    at a pixel if q > 9 (the 3-sigma footprint of Alg. 1 step 5) or alpha
+ *    < 1/255; compositing stops before the splat that would bring the
+ *    transmittance below 1e-4.
+ */
+#ifndef PACKUV_H
+#define PACKUV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PK_VERSION 1
+#define PK_MAX_LEVELS 16
+#define PK_MAX_VIEWS 4096
+#define PK_RECORD_FLOATS 12  /* projected record, 48 bytes */
+#define PK_GRAD2D_FLOATS 12  /* per-pair 2D gradient record, 48 bytes (9 used) */
+
+typedef struct CUstream_st *pk_stream_t; /* identical to cudaStream_t */
+
+typedef enum pk_status {
+  PK_OK = 0,
+  PK_ERR_ARG = 1,         /* null/misaligned pointer, size out of range */
+  PK_ERR_DESC = 2,        /* invalid atlas descriptor or view table */
+  PK_ERR_CAPACITY = 3,    /* a device capacity was exceeded (device status) */
+  PK_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (device status) */
+  PK_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+  PK_ERR_UNSUPPORTED = 6  /* option not supported by this build */
+} pk_status;
+
+typedef enum pk_texel_type { PK_TEXEL_F32 = 0, PK_TEXEL_F16 = 1 } pk_texel_type;
+
+/* One pyramid level inside the atlas: stored size and origin; a rotated
+ * level is stored turned 90 degrees counter-clockwise (Sec. 4.1). */
+typedef struct pk_level {
+  int32_t w, h, x0, y0, rotated;
+} pk_level;
+
+typedef struct pk_atlas_desc {
+  int32_t atlas_w, atlas_h;        /* W_A, H_A in texels */
+  int32_t num_levels;              /* 1 .. PK_MAX_LEVELS */
+  pk_level level[PK_MAX_LEVELS];
+  int32_t sh_degree;               /* L in 0..3 */
+  int32_t frames;                  /* F atlases per launch (Sec. 4.1: one atlas per frame) */
+  int32_t texel_type;              /* pk_texel_type */
+} pk_atlas_desc;
+
+/* Pinhole view: X_cam = R X + t, camera looks along +z, x right, y down
+ * (Supp. "Viewer"); pixel (i, j) has centre (i + 0.5, j + 0.5). */
+typedef struct pk_view {
+  float R[9];                      /* row-major world->camera rotation */
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  int32_t frame;                   /* atlas frame rendered by this view */
+} pk_view;
+
+typedef struct pk_options {
+  int32_t tile;                    /* tile side: 16 (8 and 32 reserved) */
+  float znear;                     /* cull z <= znear; default 0.01 */
+  float bg[3];                     /* background colour; default 0 */
+  uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
+} pk_options;
+
+typedef struct pk_plan pk_plan;
+
+typedef struct pk_sizes {
+  int64_t n_live;                  /* N: live texels = Gaussians per frame */
+  int64_t n_gauss;                 /* F * N */
+  int32_t channels;                /* D */
+  int32_t n_views;                 /* V */
+  int64_t n_pairs;                 /* V * N */
+  int64_t n_pixels;                /* P = sum_v W_v H_v */
+  int64_t n_tiles;                 /* sum_v ceil(W_v/T) ceil(H_v/T) */
+  uint64_t max_dups;               /* capacity of sorted_vals */
+  uint64_t workspace_bytes;
+} pk_sizes;
+
+/* Device status block (in the workspace).  flags is a bit set of
+ * PK_DEV_* bits; counters describe the last call that set them. */
+#define PK_DEV_CAPACITY 1u       /* bin_and_sort: entries > max_dups, emitted none */
+#define PK_DEV_LIVE_MISMATCH 2u  /* gather: occupancy holds != N live texels */
+#define PK_DEV_TIMEOUT 4u        /* a bounded device wait gave up */
+typedef struct pk_device_status {
+  uint32_t flags;
+  uint32_t live_seen;              /* live texels counted by the last gather (saturating) */
+  uint64_t dups;                   /* entries emitted by the last bin_and_sort */
+  uint64_t dups_needed;            /* entries the last bin_and_sort needed */
+  uint64_t valid_pairs;            /* pairs touching at least one tile */
+  uint64_t evals_fwd;              /* (pixel, splat) evaluations of the last forward */
+  uint64_t evals_bwd;              /* ... of the last backward */
+  double loss;                     /* last pk_l1_loss_grad value */
+} pk_device_status;
+
+/* ------------------------------------------------------------------------ */
+/* Plan and workspace                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Packed layout of K pyramid levels of an S x S base, per Sec. 4.1: the
+ * level sizes follow the "Pyramid UV Mapping" equation (odd k halves N,
+ * even k halves M); L0 sits at the right, L1 (rotated) and L2 on the left,
+ * deeper levels rightward of L2 alternating rotated/horizontal.  Fills
+ * desc->atlas_w/h, num_levels and level[]; other fields are untouched.
+ * Returns PK_ERR_ARG for S < 2, K outside 1..16 or a level of size 0. */
+pk_status pk_atlas_layout(int32_t S, int32_t K, pk_atlas_desc *desc);
+
+/* Validate the descriptor (levels inside the atlas, not overlapping), the
+ * views (positive sizes, frame < F, finite parameters) and n_live, and
+ * build the host-side plan.  Copies everything it needs.  Allocates no
+ * device memory.  On error *out is NULL. */
+pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *views, int32_t n_views,
+                         int64_t n_live, const pk_options *opts, pk_plan **out);
+pk_status pk_plan_sizes(const pk_plan *plan, pk_sizes *out);
+void pk_plan_destroy(pk_plan *plan);
+
+/* Upload the plan's view tables into the workspace and clear its status
+ * block.  Call once per workspace (and again after reusing the memory
+ * for another plan), before any other call and outside graph capture. */
+pk_status pk_workspace_init(const pk_plan *plan, void *workspace, pk_stream_t stream);
+
+/* Copy the device status block to *out (enqueues a copy on `stream` and
+ * synchronises that stream). */
+pk_status pk_read_status(const pk_plan *plan, const void *workspace, pk_stream_t stream,
+                         pk_device_status *out);
+
+/* ------------------------------------------------------------------------ */
+/* The render step                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* a1 -- Sec. 4.2 "Fitting UV Maps Directly" (U[u,v,k] = g_i) and "Low
+ * Precision Optimization" (the renderer reads the low-precision proxy).
+ * atlas:   [F][D][H_A][W_A] texels of desc.texel_type (FP16 decoded to FP32).
+ * occ:     [H_A][ceil(W_A/32)] uint32 occupancy bits (texel x in bit x & 31
+ *          of word x >> 5); the same mask for every frame.
+ * dyn:     same layout, dynamic-texel mask D_i; NULL = all dynamic.
+ * soa:     out [D][F*N] float32, channel-major.
+ * texel:   out [N] uint32, y * W_A + x of Gaussian g.
+ * dynflag: out [N] uint8, 1 = dynamic.
+ * If the mask holds a number of live texels other than N the device sets
+ * PK_DEV_LIVE_MISMATCH and writes only Gaussians with index < N. */
+pk_status pk_atlas_gather(const pk_plan *plan, const void *atlas, const uint32_t *occ,
+                          const uint32_t *dyn, float *soa, uint32_t *texel, uint8_t *dynflag,
+                          void *workspace, pk_stream_t stream);
+
+/* a2 -- Sec. 4.2 "Covariance-Aware Gaussian Masking" and Alg. 1 steps 1-4
+ * (Sigma3D = R diag(s^2) R^T, Sigma2D = J W Sigma3D W^T J^T + 0.3 I, det
+ * check, lambda_max, r = ceil(3 sqrt(lambda_max))), Supp. "Viewer" for the
+ * pinhole mean, Sec. 3 for opacity and SH colour.  Per pair writes the
+ * 12-float record {m_x, m_y, conic_a, conic_b, conic_c, opacity, z,
+ * radius, red, green, blue, 0}, conic = Sigma2D^-1 = [[a, b], [b, c]],
+ * s = exp(log-scale), opacity = sigmoid(logit), colour =
+ * max(0, sum_j k_j Y_j(normalize(mu - camera centre)) + 0.5).  A culled
+ * pair (z <= znear, det <= 1e-7, non-finite) has radius 0.
+ * soa: [D][F*N] float32 from pk_atlas_gather.  records: out [V*N][12]. */
+pk_status pk_project_and_sh(const pk_plan *plan, const float *soa, float *records,
+                            void *workspace, pk_stream_t stream);
+
+/* a3 -- Sec. 3 (tile-based rasteriser), Supp. "Viewer" (per-camera depth
+ * order).  For each pair with radius > 0 the tile rectangle is, in FP32 and
+ * this order without fused multiply-add: lo = max(ceil((m - 0.5) - r), 0),
+ * hi = min(floor((m - 0.5) + r), size - 1) per axis, empty if lo > hi;
+ * tiles lo/T .. hi/T.  Every (pair, tile) becomes one entry; entries are
+ * ordered by (global tile id, bits(z), pair index), which is a stable sort
+ * of the keys (tile << 32 | bits(z)) in emission order (view, Gaussian,
+ * tile row-major).  Bit-exact by contract.
+ * records:     [V*N][12] (reads m, z, radius only).
+ * sorted_vals: out [max_dups] uint32 pair index of each entry.
+ * tile_ranges: out [n_tiles][2] uint32 [start, end) into sorted_vals;
+ *              global tile id = tile_off(v) + ty * ceil(W_v/T) + tx.
+ * If the entries exceed max_dups the device sets PK_DEV_CAPACITY, records
+ * dups_needed and emits nothing (all ranges empty). */
+pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
+                          uint32_t *tile_ranges, void *workspace, pk_stream_t stream);
+
+/* a4 -- Supp. "Viewer": C = sum_i T_i alpha_i c_i, T_i = prod_{j<i}
+ * (1 - alpha_j), front to back in the order of pk_bin_and_sort, plus
+ * T_final * bg.  One persistent launch over the tiles of every view.
+ * image:     out [3 * P] float32 (planar per view).
+ * T_final:   out [P] float32 transmittance after the last blended splat.
+ * n_contrib: out [P] uint32, 1-based position within the tile's list of
+ *            the last blended entry (0 = none). */
+pk_status pk_rasterize_fwd(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
+                           const uint32_t *tile_ranges, float *image, float *T_final,
+                           uint32_t *n_contrib, void *workspace, pk_stream_t stream);
+
+/* a5 -- adjoint of pk_rasterize_fwd (Sec. 4.2 "Objective").  Walks each
+ * pixel's list backwards from n_contrib, recovering T_i = T_{i+1} /
+ * (1 - alpha_i) from T_final.  grad2d: out [V*N][12] float32, zeroed by the
+ * call then accumulated; fields 0..8 are dL/d(m_x, m_y, conic_a, conic_b,
+ * conic_c, opacity, red, green, blue), conic_b being the off-diagonal
+ * entry counted once.  dL_dimage has the layout of image. */
+pk_status pk_rasterize_bwd(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
+                           const uint32_t *tile_ranges, const float *T_final,
+                           const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                           void *workspace, pk_stream_t stream);
+
+/* a6 -- chain rule from grad2d through the projection and SH colour back to
+ * the texel attributes, summed over the views of each Gaussian's frame,
+ * then multiplied by D_i (Sec. 4.2 "Gradient Freezing"); the FP16 proxy is
+ * passed straight through (Sec. 4.2 "Low Precision Optimization").
+ * grad_atlas: [F][D][H_A][W_A] float32; the live texels are overwritten
+ * (accumulate = 0) or added to (accumulate = 1); other texels untouched.
+ * dynflag may be NULL (all dynamic). */
+pk_status pk_atlas_scatter_grad(const pk_plan *plan, const float *soa, const float *grad2d,
+                                const uint8_t *dynflag, const uint32_t *texel, float *grad_atlas,
+                                int32_t accumulate, void *workspace, pk_stream_t stream);
+
+/* Photometric L1 term of Sec. 4.2 "Objective": loss = mean |image - target|
+ * over 3 P values (stored in the status block), dL_dimage = sign(image -
+ * target) / (3 P) (0 where equal). */
+pk_status pk_l1_loss_grad(const pk_plan *plan, const float *image, const float *target,
+                          float *dL_dimage, void *workspace, pk_stream_t stream);
+
+const char *pk_status_string(pk_status s);
+int32_t pk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PACKUV_H */

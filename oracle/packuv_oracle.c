@@ -585,6 +585,7 @@ static int composite_pixel(const double *rec, const uint32_t *vals, int64_t s, i
   double T = 1.0;
   int n = 0;
   uint32_t prev_zb = 0;
+  double prev_z = 0.0, prev_m[2] = {0.0, 0.0};
   int have_prev = 0;
   rgb[0] = rgb[1] = rgb[2] = 0.0;
   *last = 0;
@@ -617,9 +618,18 @@ static int composite_pixel(const double *rec, const uint32_t *vals, int64_t s, i
     }
     if (((uint32_t)r[R_FLAGS]) & F_CULL_NEAR) *flags |= B_CULL;
     if (fabs(araw - ALPHA_MAX) <= 1e-4) *flags |= B_CLAMP;
+    /* an FP32 depth order can differ from this one between two depths within
+       a few FP32 ulps of each other -- exact FP64 ties included, since FP32
+       rounding can split them -- unless the two splats sit at the same
+       place (same depth and mean), which every precision computes alike */
     uint32_t zb = f32_bits((float)r[R_Z]);
-    if (have_prev && (zb - prev_zb) <= 8u) *flags |= B_DEPTH;
+    if (have_prev && (zb - prev_zb) <= 4u &&
+        !(r[R_Z] == prev_z && r[R_MX] == prev_m[0] && r[R_MY] == prev_m[1]))
+      *flags |= B_DEPTH;
     prev_zb = zb;
+    prev_z = r[R_Z];
+    prev_m[0] = r[R_MX];
+    prev_m[1] = r[R_MY];
     have_prev = 1;
     rgb[0] += T * alpha * r[R_RED];
     rgb[1] += T * alpha * r[R_GRN];

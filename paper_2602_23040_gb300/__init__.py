@@ -1,0 +1,30 @@
+"""PackUV-GS render step on GB300: C-ABI CUDA library + thin torch binding.
+
+The hot path (atlas gather, EWA projection and SH colour, tile binning and
+radix sort, compositing forward and backward, texel-gradient scatter) runs
+entirely in the hand-written sm_103a kernels of ``libpackuv.so``; this
+package only marshals torch tensors and streams into the C calls.
+"""
+
+from . import build  # noqa: F401
+from .api import (  # noqa: F401
+    Plan,
+    atlas_gather,
+    atlas_layout,
+    atlas_scatter_grad,
+    bin_and_sort,
+    l1_loss_grad,
+    make_workspace,
+    project_and_sh,
+    rasterize_bwd,
+    rasterize_fwd,
+    read_status,
+    workspace_init,
+)
+from .render import PerViewLoop, Renderer, render  # noqa: F401
+
+__all__ = [
+    "Plan", "Renderer", "PerViewLoop", "render", "atlas_layout", "atlas_gather", "project_and_sh",
+    "bin_and_sort", "rasterize_fwd", "rasterize_bwd", "atlas_scatter_grad", "l1_loss_grad",
+    "make_workspace", "workspace_init", "read_status",
+]

@@ -1,0 +1,252 @@
+"""Python binding of the C ABI (``include/packuv.h``), one function per call.
+
+Every function only checks and marshals its torch tensors (device, dtype,
+size, contiguity) and forwards raw pointers plus the current CUDA stream to
+the library; all arithmetic runs in the library's kernels.  uint32 buffers
+are carried in ``torch.int32`` tensors (same bits).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import torch
+
+from . import _native as N
+
+_I32 = torch.int32
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: Optional[torch.Tensor], name: str, dtype=None, numel: Optional[int] = None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise ValueError(f"{name} has dtype {t.dtype}, expected {dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# Plan
+# ---------------------------------------------------------------------------
+
+def atlas_layout(S: int, K: int):
+    """Pyramid levels of an S x S base packed into one atlas (Sec. 4.1)."""
+    lib = N.load()
+    d = N.AtlasDesc()
+    N.check("pk_atlas_layout", lib.pk_atlas_layout(S, K, C.byref(d)))
+    levels = [(d.level[k].w, d.level[k].h, d.level[k].x0, d.level[k].y0, d.level[k].rotated)
+              for k in range(d.num_levels)]
+    return levels, (d.atlas_w, d.atlas_h)
+
+
+def _views_array(views) -> "C.Array":
+    arr = (N.View * len(views))()
+    for i, v in enumerate(views):
+        R = [float(x) for x in getattr(v.R, "reshape", lambda *_: v.R)(-1)]
+        arr[i].R[:] = R
+        arr[i].t[:] = [float(x) for x in v.t]
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = float(v.fx), float(v.fy), float(v.cx), float(v.cy)
+        arr[i].width, arr[i].height, arr[i].frame = int(v.width), int(v.height), int(getattr(v, "frame", 0))
+    return arr
+
+
+class Plan:
+    """Host-side plan of one launch: atlas descriptor, views and options."""
+
+    def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
+                 sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 16,
+                 znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0):
+        lib = N.load()
+        self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
+                          texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
+                          bg=tuple(bg), max_dups=max_dups)
+        d = N.AtlasDesc()
+        d.atlas_w, d.atlas_h = int(atlas_wh[0]), int(atlas_wh[1])
+        d.num_levels = len(levels)
+        for k, (w, h, x0, y0, rot) in enumerate(levels):
+            d.level[k] = N.Level(w, h, x0, y0, rot)
+        d.sh_degree = int(sh_degree)
+        d.frames = int(frames)
+        d.texel_type = {"f32": 0, "f16": 1}[texel_type]
+        o = N.Options()
+        o.tile, o.znear, o.max_dups = int(tile), float(znear), int(max_dups)
+        o.bg[:] = [float(b) for b in bg]
+        self._views = _views_array(views)
+        h = C.c_void_p()
+        N.check("pk_plan_create", lib.pk_plan_create(C.byref(d), self._views, len(views), int(n_live),
+                                                     C.byref(o), C.byref(h)))
+        self.handle = h
+        self.desc = d
+        self.texel_type = texel_type
+        self.views = list(views)
+        s = N.Sizes()
+        N.check("pk_plan_sizes", lib.pk_plan_sizes(h, C.byref(s)))
+        self.sizes = s
+        self.view_pixels = [int(v.width) * int(v.height) for v in views]
+
+    @classmethod
+    def for_scene(cls, scene, views=None, **kw):
+        F, D, H, W = scene.atlas.shape
+        tt = "f16" if str(scene.atlas.dtype) == "float16" else "f32"
+        return cls(scene.levels, (W, H), scene.sh_degree, F, tt, views if views is not None else scene.views,
+                   scene.n_live, tile=scene.tile, **kw)
+
+    def with_capacity(self, max_dups: int) -> "Plan":
+        """Same plan with another capacity of (pair, tile) entries."""
+        a = dict(self._args)
+        a["max_dups"] = int(max_dups)
+        return Plan(**a)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.load().pk_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # sizes
+    @property
+    def N(self):
+        return self.sizes.n_live
+
+    @property
+    def G(self):
+        return self.sizes.n_gauss
+
+    @property
+    def D(self):
+        return self.sizes.channels
+
+    @property
+    def V(self):
+        return self.sizes.n_views
+
+    @property
+    def pairs(self):
+        return self.sizes.n_pairs
+
+    @property
+    def P(self):
+        return self.sizes.n_pixels
+
+    @property
+    def n_tiles(self):
+        return self.sizes.n_tiles
+
+    @property
+    def max_dups(self):
+        return self.sizes.max_dups
+
+
+def make_workspace(plan: Plan, device="cuda") -> torch.Tensor:
+    return torch.empty(int(plan.sizes.workspace_bytes), dtype=torch.uint8, device=device)
+
+
+def workspace_init(plan: Plan, ws: torch.Tensor, stream=None) -> None:
+    N.check("pk_workspace_init", N.load().pk_workspace_init(plan.handle, _ptr(ws, "workspace"), _stream(stream)))
+
+
+def read_status(plan: Plan, ws: torch.Tensor, stream=None, check: bool = False) -> dict:
+    s = N.DeviceStatus()
+    rc = N.load().pk_read_status(plan.handle, _ptr(ws, "workspace"), _stream(stream), C.byref(s))
+    if rc not in (0, 3, 4):
+        N.check("pk_read_status", rc)
+    out = {f: getattr(s, f) for f, _ in N.DeviceStatus._fields_}
+    out["rc"] = rc
+    if check:
+        N.check("device status", rc)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# The six calls of the render step (and the L1 loss helper)
+# ---------------------------------------------------------------------------
+
+def atlas_gather(plan: Plan, atlas, occ, dyn, soa, texel, dynflag, ws, stream=None) -> None:
+    F, D = plan.desc.frames, plan.D
+    W, H = plan.desc.atlas_w, plan.desc.atlas_h
+    words = H * ((W + 31) // 32)
+    adt = torch.float16 if plan.texel_type == "f16" else torch.float32
+    rc = N.load().pk_atlas_gather(
+        plan.handle, _ptr(atlas, "atlas", adt, F * D * H * W), _ptr(occ, "occ", _I32, words),
+        _ptr(dyn, "dyn", _I32, words, allow_none=True), _ptr(soa, "soa", torch.float32, D * plan.G),
+        _ptr(texel, "texel", _I32, plan.N), _ptr(dynflag, "dynflag", torch.uint8, plan.N),
+        _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_atlas_gather", rc)
+
+
+def project_and_sh(plan: Plan, soa, records, ws, stream=None) -> None:
+    rc = N.load().pk_project_and_sh(plan.handle, _ptr(soa, "soa", torch.float32, plan.D * plan.G),
+                                    _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+                                    _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_project_and_sh", rc)
+
+
+def bin_and_sort(plan: Plan, records, sorted_vals, tile_ranges, ws, stream=None) -> None:
+    rc = N.load().pk_bin_and_sort(plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+                                  _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups),
+                                  _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+                                  _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_bin_and_sort", rc)
+
+
+def rasterize_fwd(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws,
+                  stream=None) -> None:
+    rc = N.load().pk_rasterize_fwd(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(image, "image", torch.float32, 3 * plan.P), _ptr(T_final, "T_final", torch.float32, plan.P),
+        _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_rasterize_fwd", rc)
+
+
+def rasterize_bwd(plan: Plan, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws,
+                  stream=None) -> None:
+    rc = N.load().pk_rasterize_bwd(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(T_final, "T_final", torch.float32, plan.P), _ptr(n_contrib, "n_contrib", _I32, plan.P),
+        _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
+        _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs), _ptr(ws, "workspace"),
+        _stream(stream))
+    N.check("pk_rasterize_bwd", rc)
+
+
+def atlas_scatter_grad(plan: Plan, soa, grad2d, dynflag, texel, grad_atlas, accumulate: bool, ws,
+                       stream=None) -> None:
+    F, D = plan.desc.frames, plan.D
+    W, H = plan.desc.atlas_w, plan.desc.atlas_h
+    rc = N.load().pk_atlas_scatter_grad(
+        plan.handle, _ptr(soa, "soa", torch.float32, D * plan.G),
+        _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs),
+        _ptr(dynflag, "dynflag", torch.uint8, plan.N, allow_none=True), _ptr(texel, "texel", _I32, plan.N),
+        _ptr(grad_atlas, "grad_atlas", torch.float32, F * D * H * W), int(bool(accumulate)),
+        _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_atlas_scatter_grad", rc)
+
+
+def l1_loss_grad(plan: Plan, image, target, dL_dimage, ws, stream=None) -> None:
+    rc = N.load().pk_l1_loss_grad(plan.handle, _ptr(image, "image", torch.float32, 3 * plan.P),
+                                  _ptr(target, "target", torch.float32, 3 * plan.P),
+                                  _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
+                                  _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_l1_loss_grad", rc)

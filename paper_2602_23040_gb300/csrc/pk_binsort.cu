@@ -1,0 +1,514 @@
+// a3 -- duplicate-key tile binning and a stable device radix sort
+// (Sec. 3 tile-based rasteriser; Supp. "Viewer": per-camera depth order).
+//
+// Contract: entries ordered by (global tile id, bits(z), pair index).
+// Instead of sorting (tile << 32 | bits(z)) keys over all entries, which
+// costs about 7 radix passes over every (pair, tile) entry, the pairs are
+// first sorted by depth alone (4 passes over pairs, ~15x fewer than
+// entries), entries are emitted in that depth order, and a stable sort on
+// the tile id alone (ceil(log2 tiles) bits, 2-3 passes) finishes the job:
+// inside one tile every entry comes from the same view, so the stable
+// tile sort leaves them in (bits(z), pair) order, exactly the contract.
+//
+// Every kernel runs on a fixed grid and reads its element count from
+// device memory, so the whole step can be captured in a CUDA graph while
+// the counts change from iteration to iteration.
+#include <algorithm>
+
+#include "pk_common.cuh"
+
+using namespace pk;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;     // 2048
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kThreads * kSortItems;     // 4096
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Tile rectangle of a splat in FP32, in the contract's order, no FMA.
+__device__ __forceinline__ bool bin_rect(float mx, float my, float r, int W, int H, int T, int &tx0, int &ty0,
+                                         int &tx1, int &ty1) {
+  if (!(r > 0.f)) return false;
+  if (!isfinite(mx) || !isfinite(my)) return false;
+  const float ax = __fsub_rn(mx, 0.5f), ay = __fsub_rn(my, 0.5f);
+  const float lox = fmaxf(ceilf(__fsub_rn(ax, r)), 0.f);
+  const float hix = fminf(floorf(__fadd_rn(ax, r)), (float)(W - 1));
+  const float loy = fmaxf(ceilf(__fsub_rn(ay, r)), 0.f);
+  const float hiy = fminf(floorf(__fadd_rn(ay, r)), (float)(H - 1));
+  if (!(lox <= hix) || !(loy <= hiy)) return false;
+  tx0 = (int)lox / T;
+  ty0 = (int)loy / T;
+  tx1 = (int)hix / T;
+  ty1 = (int)hiy / T;
+  return true;
+}
+
+// Contiguous chunk [begin, end) of block b when n items are split over nb
+// blocks in whole tiles of `tile` items.
+__device__ __forceinline__ void chunk_of(uint64_t n, int nb, int b, int tile, uint64_t &begin, uint64_t &end) {
+  uint64_t per = (n + nb - 1) / nb;
+  per = (per + tile - 1) / tile * tile;
+  begin = per * b;
+  end = begin + per;
+  if (begin > n) begin = n;
+  if (end > n) end = n;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the prefix and
+// the block total.  s must hold kWarps + 1 elements.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T &total, T *s) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T incl = warp_incl_scan(v);
+  if (lane == 31) s[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    T w = lane < kWarps ? s[lane] : T(0);
+    T wi = warp_incl_scan(w);
+    if (lane < kWarps) s[lane] = wi - w;
+    if (lane == kWarps - 1) s[kWarps] = wi;
+  }
+  __syncthreads();
+  T r = s[warp] + incl - v;
+  total = s[kWarps];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Per-pair tile counts
+// ---------------------------------------------------------------------------
+
+__global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict__ rec, int64_t pairs, int64_t N,
+                                                         const DevView *__restrict__ views, int T,
+                                                         uint32_t *__restrict__ cnt) {
+  for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < pairs; p += (int64_t)gridDim.x * kThreads) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec) + 1);
+    const DevView &v = views[p / N];
+    int tx0, ty0, tx1, ty1;
+    uint32_t n = 0;
+    if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, tx0, ty0, tx1, ty1))
+      n = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    cnt[p] = n;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Chunked reduce-then-scan.  Item i of the scanned sequence is src(i).
+// ---------------------------------------------------------------------------
+
+struct SrcValid {      // 1 if pair i touches a tile
+  const uint32_t *cnt;
+  __device__ uint32_t operator()(uint64_t i) const { return cnt[i] > 0u ? 1u : 0u; }
+};
+struct SrcSorted {     // tile count of the i-th pair in depth order
+  const uint32_t *cnt, *pval;
+  __device__ uint32_t operator()(uint64_t i) const { return cnt[pval[i]]; }
+};
+
+__device__ __forceinline__ uint64_t load_n(const uint32_t *n_dev, uint64_t n_host) {
+  return n_dev ? (uint64_t)*n_dev : n_host;
+}
+
+template <typename Src>
+__global__ __launch_bounds__(kThreads) void k_scan_reduce(Src src, const uint32_t *n_dev, uint64_t n_host,
+                                                          uint64_t *__restrict__ bsum) {
+  __shared__ uint64_t s[kWarps + 1];
+  const uint64_t n = load_n(n_dev, n_host);
+  uint64_t b0, b1;
+  chunk_of(n, gridDim.x, blockIdx.x, kScanTile, b0, b1);
+  uint64_t acc = 0;
+  for (uint64_t i = b0 + threadIdx.x; i < b1; i += kThreads) acc += src(i);
+  uint64_t tot;
+  block_excl_scan<uint64_t>(acc, tot, s);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block sums (one block).  mode 0: compaction (total
+// = valid pairs); mode 1: emission offsets (total = entries, checked
+// against the capacity).
+__global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, int nb, int mode,
+                                                   uint64_t max_dups, DevCounters *ctr, pk_device_status *status) {
+  __shared__ uint64_t s[33];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t v = tid < nb ? bsum[tid] : 0;
+  uint64_t incl = warp_incl_scan(v);
+  if (lane == 31) s[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = s[lane];
+    uint64_t wi = warp_incl_scan(w);
+    s[lane] = wi - w;
+    if (lane == 31) s[32] = wi;
+  }
+  __syncthreads();
+  if (tid < nb) bsum[tid] = s[warp] + incl - v;
+  if (tid == 0) {
+    const uint64_t total = s[32];
+    ctr->scan_total = total;
+    if (mode == 0) {
+      ctr->n_valid = (uint32_t)total;
+      status->valid_pairs = total;
+    } else {
+      status->dups_needed = total;
+      if (total > max_dups) {
+        ctr->dups = 0;
+        status->dups = 0;
+        atomicOr(&status->flags, PK_DEV_CAPACITY);
+      } else {
+        ctr->dups = (uint32_t)total;
+        status->dups = total;
+      }
+    }
+  }
+}
+
+// Down-sweep of the compaction: writes (bits(z), pair) of every valid pair
+// in pair order.
+__global__ __launch_bounds__(kThreads) void k_compact_down(const uint32_t *__restrict__ cnt,
+                                                           const float *__restrict__ rec, uint64_t n,
+                                                           const uint64_t *__restrict__ bsum,
+                                                           uint32_t *__restrict__ zkey, uint32_t *__restrict__ pval) {
+  __shared__ uint32_t s[kWarps + 1];
+  uint64_t b0, b1;
+  chunk_of(n, gridDim.x, blockIdx.x, kScanTile, b0, b1);
+  uint32_t run = (uint32_t)bsum[blockIdx.x];
+  for (uint64_t base = b0; base < b1; base += kScanTile) {
+    const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t f[kScanItems], c = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      f[j] = (i0 + j < b1 && cnt[i0 + j] > 0u) ? 1u : 0u;
+      c += f[j];
+    }
+    uint32_t tot;
+    uint32_t pre = block_excl_scan<uint32_t>(c, tot, s) + run;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      if (f[j]) {
+        const uint64_t p = i0 + j;
+        zkey[pre] = __float_as_uint(__ldg(rec + p * kRec + 6));
+        pval[pre] = (uint32_t)p;
+        ++pre;
+      }
+    }
+    run += tot;
+  }
+}
+
+// Down-sweep of the emission-offset scan: offs[i] = entries before pair i.
+__global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const uint32_t *n_dev,
+                                                           const uint64_t *__restrict__ bsum,
+                                                           const DevCounters *ctr, uint32_t *__restrict__ offs) {
+  __shared__ uint32_t s[kWarps + 1];
+  if (ctr->dups == 0) return;   // overflow (or nothing): nothing will be emitted
+  const uint64_t n = *n_dev;
+  uint64_t b0, b1;
+  chunk_of(n, gridDim.x, blockIdx.x, kScanTile, b0, b1);
+  uint32_t run = (uint32_t)bsum[blockIdx.x];
+  for (uint64_t base = b0; base < b1; base += kScanTile) {
+    const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], c = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      v[j] = i0 + j < b1 ? src(i0 + j) : 0u;
+      c += v[j];
+    }
+    uint32_t tot;
+    uint32_t pre = block_excl_scan<uint32_t>(c, tot, s) + run;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+      if (i0 + j < b1) offs[i0 + j] = pre;
+      pre += v[j];
+    }
+    run += tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort, one pass = upsweep + scan + downsweep.
+// ---------------------------------------------------------------------------
+
+__global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__restrict__ keys,
+                                                            const uint32_t *n_dev, uint64_t n_host, int shift,
+                                                            uint32_t mask, uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_cnt[kRadix];
+  for (int d = threadIdx.x; d < kRadix; d += kThreads) s_cnt[d] = 0;
+  __syncthreads();
+  const uint64_t n = load_n(n_dev, n_host);
+  uint64_t b0, b1;
+  chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
+  for (uint64_t i = b0 + threadIdx.x; i < b1; i += kThreads) {
+    const uint32_t d = (__ldg(keys + i) >> shift) & mask;
+    const uint32_t peers = __match_any_sync(__activemask(), d);
+    if ((peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += kThreads) hist[(size_t)d * gridDim.x + blockIdx.x] = s_cnt[d];
+}
+
+// Exclusive scan of hist in [digit][block] order (one block of 1024).
+__global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist, int count) {
+  __shared__ uint32_t s[33];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (count + 1023) / 1024;
+  const int b = tid * per, e = min(count, b + per);
+  uint32_t acc = 0;
+  for (int i = b; i < e; ++i) acc += hist[i];
+  uint32_t incl = warp_incl_scan(acc);
+  if (lane == 31) s[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = s[lane];
+    uint32_t wi = warp_incl_scan(w);
+    s[lane] = wi - w;
+  }
+  __syncthreads();
+  uint32_t run = s[warp] + incl - acc;
+  for (int i = b; i < e; ++i) {
+    uint32_t h = hist[i];
+    hist[i] = run;
+    run += h;
+  }
+}
+
+__global__ __launch_bounds__(kThreads) void k_radix_downsweep(const uint32_t *__restrict__ kin,
+                                                              const uint32_t *__restrict__ vin,
+                                                              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                              const uint32_t *n_dev, uint64_t n_host, int shift,
+                                                              uint32_t mask, const uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_wcnt[kWarps][kRadix];
+  __shared__ uint32_t s_start[kRadix];
+  __shared__ uint32_t s_gbase[kRadix];
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_scan[kWarps + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t n = load_n(n_dev, n_host);
+  uint64_t b0, b1;
+  chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
+  for (int d = tid; d < kRadix; d += kThreads) s_gbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+  const uint32_t lt = lanemask_lt();
+  for (uint64_t base = b0; base < b1; base += kSortTile) {
+    const uint32_t valid = (uint32_t)min((uint64_t)kSortTile, b1 - base);
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const uint32_t li = (uint32_t)(warp * 32 * kSortItems + j * 32 + lane);
+      const bool in = li < valid;
+      key[j] = in ? __ldg(kin + base + li) : 0xffffffffu;
+      val[j] = in ? __ldg(vin + base + li) : 0u;
+      const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t before = __popc(peers & lt);
+      const uint32_t c = s_wcnt[warp][d];
+      rank[j] = c + before;
+      __syncwarp();
+      if (before == 0) s_wcnt[warp][d] = c + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // per digit: prefix over warps, then over digits
+    uint32_t dcount = 0;
+    {
+      const int d = tid;   // kThreads == kRadix
+      uint32_t sum = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = sum;
+        sum += c;
+      }
+      dcount = sum;
+      uint32_t tot;
+      s_start[d] = block_excl_scan<uint32_t>(sum, tot, s_scan);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+      const uint32_t li = (uint32_t)(warp * 32 * kSortItems + j * 32 + lane);
+      const uint32_t d = li < valid ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
+      const uint32_t r = s_start[d] + s_wcnt[warp][d] + rank[j];
+      s_keys[r] = key[j];
+      s_vals[r] = val[j];
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < valid; i += kThreads) {
+      const uint32_t k = s_keys[i];
+      const uint32_t d = (k >> shift) & mask;
+      const uint32_t o = s_gbase[d] + (i - s_start[d]);
+      kout[o] = k;
+      vout[o] = s_vals[i];
+    }
+    __syncthreads();
+    s_gbase[tid] += dcount;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Emission: one (tile, pair) entry per touched tile, warp-cooperative so
+// that the stores of a warp are contiguous.
+// ---------------------------------------------------------------------------
+
+__global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
+                                                   const uint32_t *__restrict__ offs, const DevCounters *ctr,
+                                                   const DevView *__restrict__ views, int64_t N, int T,
+                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+  if (ctr->dups == 0) return;
+  const uint64_t n = ctr->n_valid;
+  const int lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
+  for (uint64_t w = blockIdx.x * (uint64_t)kWarps + (threadIdx.x >> 5); w * 32 < n; w += nwarps) {
+    const uint64_t k = w * 32 + lane;
+    uint32_t cnt = 0, p = 0, tbase = 0, wt = 1, tx_n = 1, off0 = 0;
+    if (k < n) {
+      p = pval[k];
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec));
+      const float rr = __ldg(rec + (uint64_t)p * kRec + 7);
+      const DevView &v = views[p / N];
+      int tx0, ty0, tx1, ty1;
+      if (bin_rect(a.x, a.y, rr, v.width, v.height, T, tx0, ty0, tx1, ty1)) {
+        wt = (uint32_t)(tx1 - tx0 + 1);
+        cnt = wt * (uint32_t)(ty1 - ty0 + 1);
+        tx_n = (uint32_t)v.tiles_x;
+        tbase = (uint32_t)v.tile_off + (uint32_t)ty0 * tx_n + (uint32_t)tx0;
+      }
+    }
+    if (lane == 0) off0 = offs[w * 32];
+    off0 = __shfl_sync(0xffffffffu, off0, 0);
+    const uint32_t incl = warp_incl_scan(cnt);
+    const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
+    for (uint32_t e0 = 0; e0 < E; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const uint32_t ee = e < E ? e : E - 1;
+      // owner = number of lanes whose inclusive count is <= ee
+      int pos = 0;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t c = __shfl_sync(0xffffffffu, incl, pos + s - 1);
+        if (c <= ee) pos += s;
+      }
+      const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, pos);
+      const uint32_t o_cnt = __shfl_sync(0xffffffffu, cnt, pos);
+      const uint32_t o_p = __shfl_sync(0xffffffffu, p, pos);
+      const uint32_t o_tb = __shfl_sync(0xffffffffu, tbase, pos);
+      const uint32_t o_wt = __shfl_sync(0xffffffffu, wt, pos);
+      const uint32_t o_txn = __shfl_sync(0xffffffffu, tx_n, pos);
+      if (e < E) {
+        const uint32_t local = ee - (o_incl - o_cnt);
+        const uint32_t ty = local / o_wt, tx = local - ty * o_wt;
+        keys[off0 + e] = o_tb + ty * o_txn + tx;
+        vals[off0 + e] = o_p;
+      }
+    }
+  }
+}
+
+// Tile ranges from the sorted tile ids.
+__global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, const DevCounters *ctr,
+                                                     uint32_t *__restrict__ ranges) {
+  const uint32_t n = ctr->dups;
+  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+    const uint32_t t = keys[i];
+    if (i == 0 || keys[i - 1] != t) ranges[2 * (size_t)t] = i;
+    if (i + 1 == n || keys[i + 1] != t) ranges[2 * (size_t)t + 1] = i + 1;
+  }
+}
+
+pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                     const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist,
+                     cudaStream_t st) {
+  const uint32_t mask = (1u << bits) - 1u;
+  k_radix_upsweep<<<kSortBlocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist);
+  k_radix_scan<<<1, 1024, 0, st>>>(hist, kRadix * kSortBlocks);
+  k_radix_downsweep<<<kSortBlocks, kThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_host, shift, mask, hist);
+  return check_launch();
+}
+
+}  // namespace
+
+extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
+                                     uint32_t *tile_ranges, void *ws, pk_stream_t stream) {
+  if (!p || !records || !sorted_vals || !tile_ranges || !ws) return PK_ERR_ARG;
+  if (!aligned16(records)) return PK_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const WsLayout &L = p->ws;
+  const DevView *views = at<DevView>(ws, L.views);
+  DevCounters *ctr = at<DevCounters>(ws, L.counters);
+  pk_device_status *status = at<pk_device_status>(ws, L.status);
+  uint32_t *cnt = at<uint32_t>(ws, L.pair_cnt);
+  uint32_t *zk0 = at<uint32_t>(ws, L.zkey0), *zk1 = at<uint32_t>(ws, L.zkey1);
+  uint32_t *pv0 = at<uint32_t>(ws, L.pval0), *pv1 = at<uint32_t>(ws, L.pval1);
+  uint32_t *offs = at<uint32_t>(ws, L.offs);
+  uint64_t *bsum = at<uint64_t>(ws, L.blocksums);
+  uint32_t *hist = at<uint32_t>(ws, L.hist);
+  uint32_t *dk0 = at<uint32_t>(ws, L.dkey0), *dk1 = at<uint32_t>(ws, L.dkey1);
+  uint32_t *dv = at<uint32_t>(ws, L.dval);
+  const uint32_t *n_valid = &ctr->n_valid;
+  const uint64_t pairs = (uint64_t)p->pairs;
+
+  if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
+    return PK_ERR_CUDA;
+  if (pairs == 0) {
+    if (cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st) != cudaSuccess) return PK_ERR_CUDA;
+    return PK_OK;
+  }
+  int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
+  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, cnt);
+  // compaction of the pairs that touch a tile, keyed by depth bits
+  k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
+  k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, p->max_dups, ctr, status);
+  k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, records, pairs, bsum, zk0, pv0);
+  // depth sort of the pairs: 4 stable passes over the 32 bits of z
+  pk_status e;
+  for (int pass = 0; pass < 4; ++pass) {
+    const uint32_t *ki = (pass & 1) ? zk1 : zk0;
+    const uint32_t *vi = (pass & 1) ? pv1 : pv0;
+    uint32_t *ko = (pass & 1) ? zk0 : zk1;
+    uint32_t *vo = (pass & 1) ? pv0 : pv1;
+    if ((e = radix_pass(ki, vi, ko, vo, n_valid, 0, 8 * pass, 8, hist, st)) != PK_OK) return e;
+  }
+  // emission offsets in depth order, capacity check
+  SrcSorted ss{cnt, pv0};
+  k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
+  k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, p->max_dups, ctr, status);
+  k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, bsum, ctr, offs);
+  // emission and the stable tile sort; the last pass lands in sorted_vals
+  const int npass = (p->tile_bits + 7) / 8;
+  uint32_t *vbuf[2] = {(npass & 1) ? dv : sorted_vals, (npass & 1) ? sorted_vals : dv};
+  uint32_t *kbuf[2] = {dk0, dk1};
+  k_emit<<<152 * 8, kThreads, 0, st>>>(records, pv0, offs, ctr, views, p->N, p->T, kbuf[0], vbuf[0]);
+  const uint32_t *n_dups = &ctr->dups;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int bits = std::min(8, p->tile_bits - 8 * pass);
+    if ((e = radix_pass(kbuf[pass & 1], vbuf[pass & 1], kbuf[(pass + 1) & 1], vbuf[(pass + 1) & 1], n_dups, 0,
+                        8 * pass, bits, hist, st)) != PK_OK)
+      return e;
+  }
+  k_ranges<<<152 * 8, kThreads, 0, st>>>(kbuf[npass & 1], ctr, tile_ranges);
+  return check_launch();
+}

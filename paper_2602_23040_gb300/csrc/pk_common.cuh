@@ -1,0 +1,93 @@
+// Internal definitions shared by the kernels and the host side of the
+// library.  Not part of the public ABI (include/packuv.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/packuv.h"
+
+namespace pk {
+
+constexpr int kRec = PK_RECORD_FLOATS;   // floats per projected record
+constexpr int kG2d = PK_GRAD2D_FLOATS;   // floats per 2D gradient record
+
+// Compositing constants (see packuv.h): alpha clamp, skip threshold,
+// transmittance cutoff, footprint d^2 <= 9.
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kQMax = 9.0f;
+constexpr float kLowPass = 0.3f;
+constexpr float kDetMin = 1e-7f;
+// exp(-q/2) = exp2(q * kExpScale), kExpScale = -log2(e) / 2
+constexpr float kExpScale = -0.72134752044448170f;
+
+// Fixed grid sizes of the device-count-driven kernels (scan, radix sort).
+constexpr int kScanBlocks = 1024;
+constexpr int kSortBlocks = 1024;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+// Per-view constants on the device, 128 bytes.
+struct alignas(16) DevView {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float campos[3];    // -R^T t
+  int32_t width, height, frame;
+  int32_t tiles_x, tiles_y;
+  int32_t pad0;
+  int64_t pix_off;    // first pixel of this view in the concatenated images
+  int64_t tile_off;   // first global tile id of this view
+};
+static_assert(sizeof(DevView) % 16 == 0, "DevView layout");
+
+// Internal device scalars kept after the public status block.
+struct DevCounters {
+  uint32_t n_valid;        // pairs with >= 1 tile (after the compaction scan)
+  uint32_t dups;           // entries emitted (0 on overflow)
+  uint32_t tile_queue[4];  // persistent-kernel work counters
+  uint64_t scan_total;     // total of the last scan
+  double loss_acc;
+};
+
+// Byte offsets of every region inside the workspace.
+struct WsLayout {
+  size_t status, counters, views, toff, fview_off, fview_idx, woff;
+  size_t pair_cnt, zkey0, zkey1, pval0, pval1, offs;
+  size_t blocksums, hist;
+  size_t dkey0, dkey1, dval;
+  size_t total;
+};
+
+}  // namespace pk
+
+// Host-side plan (opaque to C callers).
+struct pk_plan {
+  pk_atlas_desc desc;
+  pk_options opts;
+  int32_t V, F, D, T, L;
+  int64_t N, G, pairs, P, n_tiles;
+  uint64_t max_dups;
+  int32_t tile_bits;       // bits needed for a global tile id
+  int32_t num_sms;
+  pk::WsLayout ws;
+  pk::DevView *h_views;    // host copies uploaded by pk_workspace_init
+  uint32_t *h_toff;        // [V+1] tile offsets (global tile id -> view)
+  int32_t *h_fview_off;    // [F+1]
+  int32_t *h_fview_idx;    // [V]
+};
+
+namespace pk {
+
+template <typename T>
+__host__ __device__ inline T *at(void *base, size_t off) {
+  return reinterpret_cast<T *>(reinterpret_cast<char *>(base) + off);
+}
+
+// Host-side launch helpers (implemented in pk_plan.cu).
+pk_status check_launch();
+bool aligned16(const void *p);
+
+}  // namespace pk

@@ -1,0 +1,172 @@
+// a1 -- atlas gather (Sec. 4.2 "Fitting UV Maps Directly"; FP16 proxy of
+// "Low Precision Optimization").  Live texels of the occupancy mask, in
+// row-major order, become the Gaussians 0..N-1 of every frame.
+//
+// Two kernels: a single-block scan of per-word popcounts (the mask is at
+// most a few hundred thousand words), then one thread per group of four
+// texels that reads each channel with one 16-byte (FP32) or 8-byte (FP16)
+// load and writes the live ones to the channel-major SoA.
+#include <cuda_fp16.h>
+
+#include "pk_common.cuh"
+
+using namespace pk;
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+
+// woff[i] = number of live texels in mask words [0, i); woff[nwords] = total.
+__global__ __launch_bounds__(kScanThreads) void k_word_scan(const uint32_t *__restrict__ occ, int64_t nwords,
+                                                            uint32_t *__restrict__ woff,
+                                                            pk_device_status *status, int64_t N) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nwords; base += kScanThreads) {
+    int64_t i = base + tid;
+    uint32_t c = i < nwords ? __popc(occ[i]) : 0u;
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = s_warp[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    uint32_t carry = s_carry;
+    uint32_t excl = carry + (warp ? s_warp[warp - 1] : 0u) + x - c;
+    if (i < nwords) woff[i] = excl;
+    __syncthreads();
+    if (tid == kScanThreads - 1) s_carry = excl + c;
+    __syncthreads();
+  }
+  if (tid == 0) {
+    woff[nwords] = s_carry;
+    status->live_seen = s_carry;
+    if ((int64_t)s_carry != N) atomicOr(&status->flags, PK_DEV_LIVE_MISMATCH);
+  }
+}
+
+template <typename Tex>
+struct Quad;
+template <>
+struct Quad<float> {
+  using V = float4;
+  __device__ static float get(const V &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+  __device__ static float one(const float *p) { return *p; }
+};
+template <>
+struct Quad<__half> {
+  using V = uint2;
+  __device__ static float get(const V &v, int i) {
+    uint32_t w = (i < 2) ? v.x : v.y;
+    unsigned short h = (i & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
+    return __half2float(__ushort_as_half(h));
+  }
+  __device__ static float one(const __half *p) { return __half2float(*p); }
+};
+
+// One thread per 4 consecutive texels of a row.
+template <typename Tex, bool kVec>
+__global__ __launch_bounds__(256) void k_gather(const Tex *__restrict__ atlas, const uint32_t *__restrict__ occ,
+                                                const uint32_t *__restrict__ dyn, const uint32_t *__restrict__ woff,
+                                                int W, int H, int F, int D, int64_t N,
+                                                float *__restrict__ soa, uint32_t *__restrict__ texel,
+                                                uint8_t *__restrict__ dynflag) {
+  const int Wq = (W + 3) / 4, Wp = (W + 31) / 32;
+  const int64_t nq = (int64_t)Wq * H;
+  const int64_t plane = (int64_t)W * H;
+  const int64_t G = (int64_t)F * N;
+  for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(qi / Wq), x0 = (int)(qi % Wq) * 4;
+    // live bits of the (up to) four texels and their Gaussian indices
+    int64_t gidx[4];
+    bool live[4];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int x = x0 + i;
+      live[i] = false;
+      gidx[i] = 0;
+      if (x < W) {
+        uint32_t word = occ[(int64_t)y * Wp + (x >> 5)];
+        uint32_t bit = 1u << (x & 31);
+        if (word & bit) {
+          int64_t g = woff[(int64_t)y * Wp + (x >> 5)] + __popc(word & (bit - 1u));
+          if (g < N) {
+            live[i] = true;
+            gidx[i] = g;
+            any = true;
+            texel[g] = (uint32_t)((int64_t)y * W + x);
+            dynflag[g] = dyn ? (uint8_t)((dyn[(int64_t)y * Wp + (x >> 5)] >> (x & 31)) & 1u) : (uint8_t)1;
+          }
+        }
+      }
+    }
+    if (!any) continue;
+    const int64_t pix = (int64_t)y * W + x0;
+    for (int f = 0; f < F; ++f) {
+#pragma unroll 4
+      for (int c = 0; c < D; ++c) {
+        const Tex *src = atlas + ((int64_t)f * D + c) * plane + pix;
+        float* dst = soa + (int64_t)c * G + (int64_t)f * N;
+        if (kVec) {
+          typename Quad<Tex>::V v = __ldg(reinterpret_cast<const typename Quad<Tex>::V *>(src));
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (live[i]) dst[gidx[i]] = Quad<Tex>::get(v, i);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (live[i]) dst[gidx[i]] = Quad<Tex>::one(src + i);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" pk_status pk_atlas_gather(const pk_plan *p, const void *atlas, const uint32_t *occ, const uint32_t *dyn,
+                                     float *soa, uint32_t *texel, uint8_t *dynflag, void *ws, pk_stream_t stream) {
+  if (!p || !atlas || !occ || !soa || !texel || !dynflag || !ws) return PK_ERR_ARG;
+  if (!aligned16(atlas) || !aligned16(soa)) return PK_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int W = p->desc.atlas_w, H = p->desc.atlas_h;
+  const int64_t nwords = (int64_t)((W + 31) / 32) * H;
+  uint32_t *woff = at<uint32_t>(ws, p->ws.woff);
+  pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
+  k_word_scan<<<1, kScanThreads, 0, st>>>(occ, nwords, woff, status, p->N);
+  const int64_t nq = (int64_t)((W + 3) / 4) * H;
+  int blocks = (int)((nq + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  const bool vec = (W % 4) == 0;
+  if (p->desc.texel_type == PK_TEXEL_F16) {
+    auto a = reinterpret_cast<const __half *>(atlas);
+    if (vec)
+      k_gather<__half, true><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+    else
+      k_gather<__half, false><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+  } else {
+    auto a = reinterpret_cast<const float *>(atlas);
+    if (vec)
+      k_gather<float, true><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+    else
+      k_gather<float, false><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+  }
+  return check_launch();
+}

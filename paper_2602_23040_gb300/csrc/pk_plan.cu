@@ -1,0 +1,297 @@
+// Host side of the C ABI: atlas layout, plan validation, workspace layout,
+// status read-back.  No kernel lives here.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "pk_common.cuh"
+
+using namespace pk;
+
+namespace pk {
+
+pk_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PK_OK : PK_ERR_CUDA;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace pk
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+extern "C" int32_t pk_version(void) { return PK_VERSION; }
+
+extern "C" const char *pk_status_string(pk_status s) {
+  switch (s) {
+    case PK_OK: return "ok";
+    case PK_ERR_ARG: return "invalid argument";
+    case PK_ERR_DESC: return "invalid atlas descriptor or view table";
+    case PK_ERR_CAPACITY: return "device capacity exceeded";
+    case PK_ERR_TIMEOUT: return "device wait timed out";
+    case PK_ERR_CUDA: return "CUDA runtime error";
+    case PK_ERR_UNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+// Sec. 4.1: level k of the pyramid has (M_k, N_k) = (M_{k-1}, N_{k-1}/2) for
+// odd k and (M_{k-1}/2, N_{k-1}) for even k; native width M_k (along u),
+// height N_k (along v).  Packing: L0 at the right, L1 turned CCW in the
+// left column, L2 under it, deeper levels in the strip under L0 from the
+// right edge of L2 on, odd ones turned.
+extern "C" pk_status pk_atlas_layout(int32_t S, int32_t K, pk_atlas_desc *d) {
+  if (!d || S < 2 || K < 1 || K > PK_MAX_LEVELS) return PK_ERR_ARG;
+  int32_t M[PK_MAX_LEVELS], N[PK_MAX_LEVELS];
+  M[0] = S;
+  N[0] = S;
+  for (int k = 1; k < K; ++k) {
+    M[k] = (k & 1) ? M[k - 1] : M[k - 1] / 2;
+    N[k] = (k & 1) ? N[k - 1] / 2 : N[k - 1];
+    if (M[k] < 1 || N[k] < 1) return PK_ERR_ARG;
+  }
+  int32_t W = 0, H = 0, strip_x = 0;
+  for (int k = 0; k < K; ++k) {
+    pk_level &l = d->level[k];
+    bool turned = (k & 1) != 0;
+    l.rotated = turned ? 1 : 0;
+    l.w = turned ? N[k] : M[k];
+    l.h = turned ? M[k] : N[k];
+    if (K == 1) {
+      l.x0 = 0;
+      l.y0 = 0;
+    } else if (k == 0) {
+      l.x0 = N[1];   // right of the left column (width of the turned L1)
+      l.y0 = 0;
+    } else if (k == 1) {
+      l.x0 = 0;
+      l.y0 = 0;
+    } else if (k == 2) {
+      l.x0 = 0;
+      l.y0 = M[1];
+      strip_x = l.w;
+    } else {
+      l.x0 = strip_x;
+      l.y0 = M[1];
+      strip_x += l.w;
+    }
+    if (l.x0 + l.w > W) W = l.x0 + l.w;
+    if (l.y0 + l.h > H) H = l.y0 + l.h;
+  }
+  for (int k = K; k < PK_MAX_LEVELS; ++k) d->level[k] = pk_level{0, 0, 0, 0, 0};
+  d->num_levels = K;
+  d->atlas_w = W;
+  d->atlas_h = H;
+  return PK_OK;
+}
+
+static bool finite_view(const pk_view &v) {
+  for (int i = 0; i < 9; ++i)
+    if (!isfinite(v.R[i])) return false;
+  for (int i = 0; i < 3; ++i)
+    if (!isfinite(v.t[i])) return false;
+  return isfinite(v.fx) && isfinite(v.fy) && isfinite(v.cx) && isfinite(v.cy) && v.fx > 0 && v.fy > 0;
+}
+
+extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *views, int32_t n_views,
+                                    int64_t n_live, const pk_options *opts, pk_plan **out) {
+  if (!out) return PK_ERR_ARG;
+  *out = nullptr;
+  if (!desc || !views || n_views < 1 || n_views > PK_MAX_VIEWS || n_live < 0) return PK_ERR_ARG;
+  const pk_atlas_desc &d = *desc;
+  if (d.atlas_w < 1 || d.atlas_h < 1 || d.atlas_w > 65536 || d.atlas_h > 65536) return PK_ERR_DESC;
+  if (d.num_levels < 1 || d.num_levels > PK_MAX_LEVELS) return PK_ERR_DESC;
+  if (d.sh_degree < 0 || d.sh_degree > 3 || d.frames < 1 || d.frames > 4096) return PK_ERR_DESC;
+  if (d.texel_type != PK_TEXEL_F32 && d.texel_type != PK_TEXEL_F16) return PK_ERR_DESC;
+  for (int k = 0; k < d.num_levels; ++k) {
+    const pk_level &a = d.level[k];
+    if (a.w < 1 || a.h < 1 || a.x0 < 0 || a.y0 < 0 || a.x0 + a.w > d.atlas_w || a.y0 + a.h > d.atlas_h)
+      return PK_ERR_DESC;
+    for (int j = 0; j < k; ++j) {
+      const pk_level &b = d.level[j];
+      bool apart = a.x0 >= b.x0 + b.w || b.x0 >= a.x0 + a.w || a.y0 >= b.y0 + b.h || b.y0 >= a.y0 + a.h;
+      if (!apart) return PK_ERR_DESC;
+    }
+  }
+  if (n_live > (int64_t)d.atlas_w * d.atlas_h) return PK_ERR_ARG;
+  pk_options o;
+  o.tile = 16;
+  o.znear = 0.01f;
+  o.bg[0] = o.bg[1] = o.bg[2] = 0.0f;
+  o.max_dups = 0;
+  if (opts) o = *opts;
+  if (o.tile != 16) return PK_ERR_UNSUPPORTED;
+  if (!(o.znear > 0.0f) || !isfinite(o.znear)) return PK_ERR_ARG;
+  for (int c = 0; c < 3; ++c)
+    if (!isfinite(o.bg[c])) return PK_ERR_ARG;
+  const int64_t N = n_live, F = d.frames, V = n_views;
+  if (F * N >= (int64_t(1) << 31) || V * N >= (int64_t(1) << 32) - 1) return PK_ERR_ARG;
+  int64_t P = 0, tiles = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const pk_view &w = views[v];
+    if (w.width < 1 || w.height < 1 || w.width > 32768 || w.height > 32768) return PK_ERR_DESC;
+    if (w.frame < 0 || w.frame >= d.frames || !finite_view(w)) return PK_ERR_DESC;
+    P += (int64_t)w.width * w.height;
+    tiles += (int64_t)((w.width + o.tile - 1) / o.tile) * ((w.height + o.tile - 1) / o.tile);
+  }
+  if (tiles >= (int64_t(1) << 31) || 3 * P >= (int64_t(1) << 40)) return PK_ERR_ARG;
+  uint64_t pairs = (uint64_t)(V * N);
+  uint64_t maxd = o.max_dups ? o.max_dups : 32 * pairs;
+  if (maxd < 1024) maxd = 1024;
+  if (maxd > 0xFFFFF000ull) maxd = 0xFFFFF000ull;
+  o.max_dups = maxd;
+
+  pk_plan *p = new (std::nothrow) pk_plan;
+  if (!p) return PK_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->desc = d;
+  p->opts = o;
+  p->V = n_views;
+  p->F = d.frames;
+  p->L = d.sh_degree;
+  p->D = 11 + 3 * (d.sh_degree + 1) * (d.sh_degree + 1);
+  p->T = o.tile;
+  p->N = N;
+  p->G = F * N;
+  p->pairs = (int64_t)pairs;
+  p->P = P;
+  p->n_tiles = tiles;
+  p->max_dups = maxd;
+  int bits = 1;
+  while ((int64_t(1) << bits) < tiles) ++bits;
+  p->tile_bits = bits;
+
+  p->h_views = new DevView[V];
+  p->h_toff = new uint32_t[V + 1];
+  p->h_fview_off = new int32_t[F + 1];
+  p->h_fview_idx = new int32_t[V];
+  int64_t po = 0, to = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const pk_view &w = views[v];
+    DevView &dv = p->h_views[v];
+    memset(&dv, 0, sizeof(dv));
+    memcpy(dv.R, w.R, sizeof(dv.R));
+    memcpy(dv.t, w.t, sizeof(dv.t));
+    dv.fx = w.fx;
+    dv.fy = w.fy;
+    dv.cx = w.cx;
+    dv.cy = w.cy;
+    for (int a = 0; a < 3; ++a)
+      dv.campos[a] = -(w.R[a] * w.t[0] + w.R[3 + a] * w.t[1] + w.R[6 + a] * w.t[2]);
+    dv.width = w.width;
+    dv.height = w.height;
+    dv.frame = w.frame;
+    dv.tiles_x = (w.width + o.tile - 1) / o.tile;
+    dv.tiles_y = (w.height + o.tile - 1) / o.tile;
+    dv.pix_off = po;
+    dv.tile_off = to;
+    p->h_toff[v] = (uint32_t)to;
+    po += (int64_t)w.width * w.height;
+    to += (int64_t)dv.tiles_x * dv.tiles_y;
+  }
+  p->h_toff[V] = (uint32_t)to;
+  // views grouped by frame (CSR), keeping view order inside a frame
+  int32_t k = 0;
+  for (int f = 0; f < d.frames; ++f) {
+    p->h_fview_off[f] = k;
+    for (int v = 0; v < n_views; ++v)
+      if (views[v].frame == f) p->h_fview_idx[k++] = v;
+  }
+  p->h_fview_off[F] = k;
+
+  // workspace layout
+  WsLayout &L = p->ws;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  const size_t Wp = (size_t)(d.atlas_w + 31) / 32;
+  L.status = take(sizeof(pk_device_status));
+  L.counters = take(sizeof(DevCounters));
+  L.views = take(sizeof(DevView) * V);
+  L.toff = take(sizeof(uint32_t) * (V + 1));
+  L.fview_off = take(sizeof(int32_t) * (F + 1));
+  L.fview_idx = take(sizeof(int32_t) * V);
+  L.woff = take(sizeof(uint32_t) * (Wp * d.atlas_h + 1));
+  L.pair_cnt = take(sizeof(uint32_t) * pairs);
+  L.zkey0 = take(sizeof(uint32_t) * pairs);
+  L.zkey1 = take(sizeof(uint32_t) * pairs);
+  L.pval0 = take(sizeof(uint32_t) * pairs);
+  L.pval1 = take(sizeof(uint32_t) * pairs);
+  L.offs = take(sizeof(uint32_t) * pairs);
+  L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
+  L.hist = take(sizeof(uint32_t) * kRadix * kSortBlocks);
+  L.dkey0 = take(sizeof(uint32_t) * maxd);
+  L.dkey1 = take(sizeof(uint32_t) * maxd);
+  L.dval = take(sizeof(uint32_t) * maxd);
+  L.total = off;
+  *out = p;
+  return PK_OK;
+}
+
+extern "C" pk_status pk_plan_sizes(const pk_plan *p, pk_sizes *s) {
+  if (!p || !s) return PK_ERR_ARG;
+  s->n_live = p->N;
+  s->n_gauss = p->G;
+  s->channels = p->D;
+  s->n_views = p->V;
+  s->n_pairs = p->pairs;
+  s->n_pixels = p->P;
+  s->n_tiles = p->n_tiles;
+  s->max_dups = p->max_dups;
+  s->workspace_bytes = p->ws.total;
+  return PK_OK;
+}
+
+extern "C" void pk_plan_destroy(pk_plan *p) {
+  if (!p) return;
+  delete[] p->h_views;
+  delete[] p->h_toff;
+  delete[] p->h_fview_off;
+  delete[] p->h_fview_idx;
+  delete p;
+}
+
+extern "C" pk_status pk_workspace_init(const pk_plan *p, void *ws, pk_stream_t stream) {
+  if (!p || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PK_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const WsLayout &L = p->ws;
+  if (cudaMemsetAsync(at<char>(ws, L.status), 0, L.views - L.status, st) != cudaSuccess) return PK_ERR_CUDA;
+  if (cudaMemcpyAsync(at<char>(ws, L.views), p->h_views, sizeof(DevView) * p->V, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return PK_ERR_CUDA;
+  if (cudaMemcpyAsync(at<char>(ws, L.toff), p->h_toff, sizeof(uint32_t) * (p->V + 1), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return PK_ERR_CUDA;
+  if (cudaMemcpyAsync(at<char>(ws, L.fview_off), p->h_fview_off, sizeof(int32_t) * (p->F + 1),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return PK_ERR_CUDA;
+  if (cudaMemcpyAsync(at<char>(ws, L.fview_idx), p->h_fview_idx, sizeof(int32_t) * p->V, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return PK_ERR_CUDA;
+  // pageable sources: make sure the copies are done before the plan may go away
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PK_ERR_CUDA;
+  return PK_OK;
+}
+
+extern "C" pk_status pk_read_status(const pk_plan *p, const void *ws, pk_stream_t stream, pk_device_status *out) {
+  if (!p || !ws || !out) return PK_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DevCounters c;
+  if (cudaMemcpyAsync(out, at<char>(const_cast<void *>(ws), p->ws.status), sizeof(*out), cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess)
+    return PK_ERR_CUDA;
+  if (cudaMemcpyAsync(&c, at<char>(const_cast<void *>(ws), p->ws.counters), sizeof(c), cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess)
+    return PK_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PK_ERR_CUDA;
+  out->loss = c.loss_acc / (3.0 * (double)p->P);
+  if (out->flags & PK_DEV_CAPACITY) return PK_ERR_CAPACITY;
+  if (out->flags & PK_DEV_TIMEOUT) return PK_ERR_TIMEOUT;
+  return PK_OK;
+}

@@ -1,0 +1,92 @@
+// Shared pieces of the forward (a4) and backward (a5) compositing kernels:
+// tile -> view lookup, batch staging of a tile's splats into shared memory,
+// and the per-pixel alpha evaluation.  The evaluation is written with
+// explicit round-to-nearest intrinsics so that both kernels take exactly
+// the same skip / clamp decisions for the same (pixel, splat).
+#pragma once
+
+#include "pk_common.cuh"
+
+namespace pk {
+
+constexpr int kTileSide = 16;
+constexpr int kRasterThreads = 256;   // one pixel per thread
+constexpr int kBatch = 256;           // splats staged per batch
+
+// Warp w covers the 8 x 4 pixel block (w % 2, w / 2) of the 16 x 16 tile.
+__device__ __forceinline__ void pixel_of(int tid, int &ox, int &oy) {
+  const int w = tid >> 5, l = tid & 31;
+  ox = (w & 1) * 8 + (l & 7);
+  oy = (w >> 1) * 4 + (l >> 3);
+}
+
+// View that owns global tile t (binary search over tile offsets).
+__device__ __forceinline__ int view_of_tile(const uint32_t *__restrict__ toff, int V, uint32_t t) {
+  int lo = 0, hi = V - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(toff + mid) <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct Staged {
+  float4 *a;     // m_x, m_y, conic_a, conic_b
+  float4 *b;     // conic_c, opacity, red, green
+  float4 *c;     // blue, pair index (bits), 0, 0
+  float4 *box;   // conservative pixel-centre box of the contributing ellipse
+};
+
+// Stage one splat.  The box bounds every pixel where q <= min(9, 2 ln(255 o))
+// (the only pixels where the splat can pass both skip tests), widened by a
+// relative 1e-3 and 0.01 px so FP32 rounding can never put a passing pixel
+// outside; the box only lets whole warps skip, the per-pixel tests still
+// decide.
+__device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint32_t pid, const Staged &s, int j) {
+  const float4 *r = reinterpret_cast<const float4 *>(rec + (size_t)pid * kRec);
+  const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
+  s.a[j] = r0;
+  s.b[j] = make_float4(r1.x, r1.y, r2.x, r2.y);
+  s.c[j] = make_float4(r2.z, __uint_as_float(pid), 0.f, 0.f);
+  const float ca = r0.z, cb = r0.w, cc = r1.x, o = r1.y;
+  const float qlim = fminf(kQMax, 2.f * logf(255.f * o));
+  const float detq = ca * cc - cb * cb;
+  float4 box;
+  if (!(qlim >= 0.f)) {
+    box = make_float4(1.f, -1.f, 1.f, -1.f);    // can never pass the alpha test
+  } else if (detq > 0.f && isfinite(detq)) {
+    const float hx = sqrtf(qlim * cc / detq) * 1.001f + 0.01f;
+    const float hy = sqrtf(qlim * ca / detq) * 1.001f + 0.01f;
+    box = make_float4(r0.x - hx, r0.x + hx, r0.y - hy, r0.y + hy);
+  } else {
+    box = make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
+  }
+  s.box[j] = box;
+}
+
+struct Hit {
+  float alpha, G, dx, dy;
+  bool clamped;
+};
+
+// alpha of a splat at pixel centre (px, py); false if skipped (q > 9 or
+// alpha < 1/255).  q = ca dx^2 + 2 cb dx dy + cc dy^2, alpha = min(0.99,
+// o exp(-q/2)).
+__device__ __forceinline__ bool splat_alpha(const float4 &a, float cc, float o, float px, float py, Hit &h) {
+  h.dx = __fsub_rn(px, a.x);
+  h.dy = __fsub_rn(py, a.y);
+  const float u = __fmaf_rn(__fmul_rn(2.f, a.w), h.dy, __fmul_rn(a.z, h.dx));
+  const float q = __fmaf_rn(u, h.dx, __fmul_rn(__fmul_rn(cc, h.dy), h.dy));
+  if (!(q <= kQMax)) return false;
+  h.G = exp2f(__fmul_rn(q, kExpScale));
+  const float araw = __fmul_rn(o, h.G);
+  h.clamped = araw > kAlphaMax;
+  h.alpha = h.clamped ? kAlphaMax : araw;
+  return h.alpha >= kAlphaMin;
+}
+
+__device__ __forceinline__ bool box_misses(const float4 &box, float x0, float x1, float y0, float y1) {
+  return box.x > x1 || box.y < x0 || box.z > y1 || box.w < y0;
+}
+
+}  // namespace pk

@@ -1,0 +1,127 @@
+// a4 -- front-to-back compositing (Supp. "Viewer": C = sum_i T_i a_i c_i,
+// T_i = prod_{j<i} (1 - a_j)) over the depth-sorted list of each tile.
+//
+// One persistent launch covers the tiles of every view: each CTA takes the
+// next tile from a device counter, stages the tile's splats batch by
+// batch into shared memory and composites one pixel per thread.  Warps
+// cover 8 x 4 pixel blocks and skip, as a whole, every splat whose
+// contributing ellipse misses their block.  The CTA leaves a tile as soon
+// as every pixel has stopped (transmittance cutoff) or the list ends.
+#include "pk_raster.cuh"
+
+using namespace pk;
+
+namespace {
+
+__global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
+    const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+    const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
+    float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
+    uint32_t *queue, unsigned long long *evals_out) {
+  __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch];
+  __shared__ uint32_t s_tile;
+  __shared__ int s_view;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const Staged st{s_a, s_b, s_c, s_box};
+  int ox, oy;
+  pixel_of(tid, ox, oy);
+  unsigned long long evals = 0;
+  for (;;) {
+    if (tid == 0) {
+      const uint32_t t = atomicAdd(queue, 1u);
+      s_tile = t;
+      s_view = t < n_tiles ? view_of_tile(toff, V, t) : -1;
+    }
+    __syncthreads();
+    const uint32_t t = s_tile;
+    if (t >= n_tiles) break;
+    const DevView &view = views[s_view];
+    const int W = view.width, H = view.height;
+    const uint32_t local = t - (uint32_t)view.tile_off;
+    const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
+    const int x = tx * kTileSide + ox, y = ty * kTileSide + oy;
+    const bool inside = x < W && y < H;
+    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    // pixel-centre bounds of this warp's 8 x 4 block
+    const float wx0 = (float)(tx * kTileSide + (ox & ~7)) + 0.5f, wx1 = wx0 + 7.f;
+    const float wy0 = (float)(ty * kTileSide + (oy & ~3)) + 0.5f, wy1 = wy0 + 3.f;
+    const uint32_t s = __ldg(ranges + 2 * (size_t)t), e = __ldg(ranges + 2 * (size_t)t + 1);
+    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    for (uint32_t base = s; base < e; base += kBatch) {
+      const int nb = (int)min((uint32_t)kBatch, e - base);
+      __syncthreads();
+      if (tid < nb) stage_splat(rec, __ldg(vals + base + tid), st, tid);
+      __syncthreads();
+      if (!__all_sync(0xffffffffu, done)) {
+        for (int j = 0; j < nb; ++j) {
+          if (box_misses(s_box[j], wx0, wx1, wy0, wy1)) continue;
+          if (!done) {
+            const float4 a = s_a[j], b = s_b[j];
+            Hit h;
+            ++evals;
+            if (splat_alpha(a, b.x, b.y, px, py, h)) {
+              const float Tn = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
+              if (Tn < kTMin) {
+                done = true;
+              } else {
+                const float w = __fmul_rn(h.alpha, T);
+                c0 = __fmaf_rn(w, b.z, c0);
+                c1 = __fmaf_rn(w, b.w, c1);
+                c2 = __fmaf_rn(w, s_c[j].x, c2);
+                T = Tn;
+                last = base - s + (uint32_t)j + 1u;
+              }
+            }
+          }
+          if (__all_sync(0xffffffffu, done)) break;
+        }
+      }
+      if (__syncthreads_count(!done) == 0) break;
+    }
+    if (inside) {
+      const size_t pix = (size_t)view.pix_off + (size_t)y * W + x;
+      const size_t plane = (size_t)W * H;
+      float *img = image + 3 * (size_t)view.pix_off + (size_t)y * W + x;
+      img[0] = __fmaf_rn(T, bg0, c0);
+      img[plane] = __fmaf_rn(T, bg1, c1);
+      img[2 * plane] = __fmaf_rn(T, bg2, c2);
+      Tout[pix] = T;
+      ncontrib[pix] = last;
+    }
+    __syncthreads();   // everyone has read s_tile / s_view before the next fetch
+  }
+  // one atomic per warp for the evaluation counter
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
+  if (lane == 0 && evals) atomicAdd(evals_out, evals);
+}
+
+}  // namespace
+
+extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+                                      void *ws, pk_stream_t stream) {
+  if (!p || !records || !sorted_vals || !tile_ranges || !image || !T_final || !n_contrib || !ws) return PK_ERR_ARG;
+  if (!aligned16(records)) return PK_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
+  pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
+  if (cudaMemsetAsync(&ctr->tile_queue[0], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
+  if (cudaMemsetAsync(&status->evals_fwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd, kRasterThreads, 0);
+  if (sms < 1) sms = 1;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > p->n_tiles) grid = p->n_tiles;
+  if (grid < 1) grid = 1;
+  k_raster_fwd<<<(int)grid, kRasterThreads, 0, st>>>(
+      records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
+      (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
+      &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd));
+  return check_launch();
+}

@@ -1,0 +1,188 @@
+"""Buffers for one render-step launch, the per-view baseline loop, and the
+differentiable ``render`` (a ``torch.autograd.Function`` over the C ABI).
+
+A ``Renderer`` owns the device buffers of every intermediate (SoA
+attributes, projected records, sorted lists, images, per-pixel state, 2D
+gradients) and runs the six calls on one stream; torch only provides the
+memory and the stream.  All views of its plan are rendered by one sequence
+of launches (one persistent launch per rasterisation pass), which can be
+captured in a CUDA graph after the first call.
+"""
+
+from __future__ import annotations
+
+from typing import List, Optional
+
+import torch
+
+from . import api
+from .api import Plan
+
+
+class Renderer:
+    def __init__(self, plan: Plan, device="cuda", ws: Optional[torch.Tensor] = None):
+        p = plan
+        self.plan = p
+        self.device = torch.device(device)
+        f32, i32 = torch.float32, torch.int32
+        self.ws = ws if ws is not None else api.make_workspace(p, self.device)
+        api.workspace_init(p, self.ws)
+        self._alloc()
+
+    def _alloc(self):
+        p = self.plan
+        f32, i32 = torch.float32, torch.int32
+        self.soa = torch.empty(p.D * p.G, dtype=f32, device=self.device)
+        self.texel = torch.empty(max(p.N, 1), dtype=i32, device=self.device)
+        self.dynflag = torch.empty(max(p.N, 1), dtype=torch.uint8, device=self.device)
+        self.records = torch.empty(12 * max(p.pairs, 1), dtype=f32, device=self.device)
+        self.sorted_vals = torch.empty(int(p.max_dups) + 64, dtype=i32, device=self.device)
+        self.ranges = torch.empty(2 * p.n_tiles, dtype=i32, device=self.device)
+        self.image = torch.empty(3 * p.P, dtype=f32, device=self.device)
+        self.T = torch.empty(p.P, dtype=f32, device=self.device)
+        self.n_contrib = torch.empty(p.P, dtype=i32, device=self.device)
+        self.grad2d = torch.empty(12 * max(p.pairs, 1), dtype=f32, device=self.device)
+        self.dimage = torch.empty(3 * p.P, dtype=f32, device=self.device)
+        self._has_dyn = False
+
+    # forward: a1 .. a4
+    def forward(self, atlas, occ, dyn=None, stream=None):
+        p = self.plan
+        self._has_dyn = dyn is not None
+        api.atlas_gather(p, atlas, occ, dyn, self.soa, self.texel, self.dynflag, self.ws, stream)
+        api.project_and_sh(p, self.soa, self.records, self.ws, stream)
+        api.bin_and_sort(p, self.records, self.sorted_vals, self.ranges, self.ws, stream)
+        api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, self.image, self.T, self.n_contrib,
+                          self.ws, stream)
+        return self.image
+
+    # backward: a5 .. a6
+    def backward(self, dL_dimage, grad_atlas, accumulate=False, stream=None):
+        p = self.plan
+        api.rasterize_bwd(p, self.records, self.sorted_vals, self.ranges, self.T, self.n_contrib, dL_dimage,
+                          self.grad2d, self.ws, stream)
+        api.atlas_scatter_grad(p, self.soa, self.grad2d, self.dynflag if self._has_dyn else None, self.texel,
+                               grad_atlas, accumulate, self.ws, stream)
+        return grad_atlas
+
+    def l1_step(self, atlas, occ, dyn, target, grad_atlas, stream=None):
+        """One fitting step: forward, L1 loss gradient, backward."""
+        self.forward(atlas, occ, dyn, stream)
+        api.l1_loss_grad(self.plan, self.image, target, self.dimage, self.ws, stream)
+        self.backward(self.dimage, grad_atlas, False, stream)
+
+    def status(self, stream=None) -> dict:
+        return api.read_status(self.plan, self.ws, stream)
+
+    def ensure_capacity(self, atlas, occ, dyn=None, stream=None, headroom: float = 1.15) -> dict:
+        """Run one forward; if the (pair, tile) entries overflowed the plan's
+        capacity, re-plan with room for them (plus headroom) and run again.
+        A host-synchronising call: use it before graph capture."""
+        self.forward(atlas, occ, dyn, stream)
+        st = self.status(stream)
+        if st["flags"] & 1:
+            need = int(st["dups_needed"] * headroom) + 4096
+            self.plan = self.plan.with_capacity(need)
+            self.ws = api.make_workspace(self.plan, self.device)
+            api.workspace_init(self.plan, self.ws)
+            self._alloc()
+            self.forward(atlas, occ, dyn, stream)
+            st = self.status(stream)
+        return st
+
+
+class PerViewLoop:
+    """Baseline of prior art: the same kernels run one view at a time.
+
+    Each view has its own single-view plan (and small workspace); the large
+    intermediate buffers are shared, image outputs are written into slices
+    of full-size buffers, and texel gradients accumulate over the views.
+    The atlas is gathered again for every view, as a per-view training loop
+    would.
+    """
+
+    @classmethod
+    def for_scene(cls, scene, device="cuda", **kw):
+        F, D, H, W = scene.atlas.shape
+        tt = "f16" if str(scene.atlas.dtype) == "float16" else "f32"
+        args = dict(levels=scene.levels, atlas_wh=(W, H), sh_degree=scene.sh_degree, frames=F,
+                    texel_type=tt, n_live=scene.n_live, tile=scene.tile, **kw)
+        return cls(args, scene.views, device)
+
+    def __init__(self, scene_like_plan_args: dict, views, device="cuda"):
+        self.plans: List[Plan] = [Plan(views=[v], **scene_like_plan_args) for v in views]
+        self.device = torch.device(device)
+        f32, i32 = torch.float32, torch.int32
+        p0 = self.plans[0]
+        self.ws = [api.make_workspace(p, self.device) for p in self.plans]
+        for p, w in zip(self.plans, self.ws):
+            api.workspace_init(p, w)
+        self.soa = torch.empty(p0.D * p0.G, dtype=f32, device=self.device)
+        self.texel = torch.empty(max(p0.N, 1), dtype=i32, device=self.device)
+        self.dynflag = torch.empty(max(p0.N, 1), dtype=torch.uint8, device=self.device)
+        self.records = torch.empty(12 * max(p0.pairs, 1), dtype=f32, device=self.device)
+        self.grad2d = torch.empty(12 * max(p0.pairs, 1), dtype=f32, device=self.device)
+        md = max(int(p.max_dups) for p in self.plans)
+        self.sorted_vals = torch.empty(md + 64, dtype=i32, device=self.device)
+        self.ranges = torch.empty(2 * max(p.n_tiles for p in self.plans), dtype=i32, device=self.device)
+        P = sum(p.P for p in self.plans)
+        self.image = torch.empty(3 * P, dtype=f32, device=self.device)
+        self.T = torch.empty(P, dtype=f32, device=self.device)
+        self.n_contrib = torch.empty(P, dtype=i32, device=self.device)
+        self.dimage = torch.empty(3 * P, dtype=f32, device=self.device)
+        self.offsets = []
+        o = 0
+        for p in self.plans:
+            self.offsets.append(o)
+            o += p.P
+
+    def _slices(self, i):
+        o, P = self.offsets[i], self.plans[i].P
+        return (self.image[3 * o:3 * (o + P)], self.T[o:o + P], self.n_contrib[o:o + P],
+                self.dimage[3 * o:3 * (o + P)])
+
+    def step(self, atlas, occ, dyn, target, grad_atlas, stream=None, loss=True):
+        for i, (p, ws) in enumerate(zip(self.plans, self.ws)):
+            img, T, nc, dimg = self._slices(i)
+            api.atlas_gather(p, atlas, occ, dyn, self.soa, self.texel, self.dynflag, ws, stream)
+            api.project_and_sh(p, self.soa, self.records, ws, stream)
+            api.bin_and_sort(p, self.records, self.sorted_vals, self.ranges, ws, stream)
+            api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, img, T, nc, ws, stream)
+            if loss:
+                o = self.offsets[i]
+                api.l1_loss_grad(p, img, target[3 * o:3 * (o + p.P)], dimg, ws, stream)
+            api.rasterize_bwd(p, self.records, self.sorted_vals, self.ranges, T, nc, dimg, self.grad2d, ws, stream)
+            api.atlas_scatter_grad(p, self.soa, self.grad2d, self.dynflag if dyn is not None else None, self.texel,
+                                   grad_atlas, i > 0, ws, stream)
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, master, renderer: Renderer, proxy, occ, dyn):
+        src = master if proxy is None else proxy
+        renderer.forward(src.detach().contiguous(), occ, dyn)
+        ctx.renderer = renderer
+        ctx.shape = master.shape
+        ctx.device = master.device
+        # the renderer keeps the per-pixel state for the backward; hand out a copy of the image
+        return renderer.image.clone()
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        r: Renderer = ctx.renderer
+        grad = torch.zeros(ctx.shape, dtype=torch.float32, device=ctx.device)
+        r.backward(grad_image.contiguous().float(), grad, accumulate=False)
+        return grad, None, None, None, None
+
+
+def render(master: torch.Tensor, renderer: Renderer, occ: torch.Tensor, dyn: Optional[torch.Tensor] = None,
+           proxy: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Differentiable render of every view of ``renderer.plan``.
+
+    ``master`` is the FP32 atlas ``[F][D][H][W]`` (the parameter).  If
+    ``proxy`` (the FP16 texels actually read) is given, the gradient passes
+    straight through it to ``master``.  Returns the concatenated planar
+    images ``[3 * P]``; the gradient is zero on texels that are not live or
+    are frozen by ``dyn``.
+    """
+    return _RenderFn.apply(master, renderer, proxy, occ, dyn)

@@ -122,13 +122,15 @@ def ring_views(n_per_height: Sequence[int], heights: Sequence[float], radius: fl
                sizes: Sequence[Tuple[int, int]], frame: int = 0) -> List[View]:
     """Cameras on rings around the origin, all looking at it.
 
-    ``sizes[i % len(sizes)]`` gives (width, height) of camera i.
+    ``sizes[i % len(sizes)]`` gives (width, height) of camera i.  The ring
+    phase is offset so that no camera axis is aligned with a world axis
+    (an aligned axis makes many depths tie exactly for quantised texels).
     """
     views = []
     i = 0
     for n, h in zip(n_per_height, heights):
         for k in range(n):
-            phi = 2.0 * math.pi * (k + 0.5 * (h != 0)) / n
+            phi = 2.0 * math.pi * (k + 0.5 * (h != 0) + 0.137) / n
             eye = (radius * math.cos(phi), h, radius * math.sin(phi))
             w, hh = sizes[i % len(sizes)]
             views.append(pinhole(eye, w, hh, frame=frame))

@@ -1,0 +1,378 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle."""
+
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_23040_gb300 import build
+    build.build()
+
+
+def _pk():
+    import paper_2602_23040_gb300 as pk
+    return pk
+
+
+def run_gpu(scene, dimg=None):
+    pk = _pk()
+    plan = pk.Plan.for_scene(scene)
+    r = pk.Renderer(plan)
+    atlas, occ, dyn = H.upload(scene)
+    st = r.ensure_capacity(atlas, occ, dyn)
+    assert st["flags"] == 0, st
+    plan = r.plan
+    grad = None
+    if dimg is not None:
+        F, D, Hh, W = scene.atlas.shape
+        grad = torch.zeros(F * D * Hh * W, dtype=torch.float32, device="cuda")
+        r.backward(torch.from_numpy(dimg.astype(np.float32)).cuda(), grad)
+    torch.cuda.synchronize()
+    return plan, r, grad
+
+
+def oracle_run(orc, scene, dimg=None):
+    o = orc.forward(scene)
+    o["view_pixels"] = [v.width * v.height for v in scene.views]
+    if dimg is not None:
+        b = orc.backward(scene, o, dimg.astype(np.float32).astype(np.float64))
+        o.update(b)
+        o["grad_atlas"] = orc.grad_to_atlas(scene, b["grad_soa"], o["texel"])
+    return o
+
+
+def gpu_grad_soa(scene, grad, texel):
+    F, D, Hh, W = scene.atlas.shape
+    g = grad.view(F, D, Hh * W).cpu().numpy().astype(np.float64)
+    return np.concatenate([g[f][:, texel] for f in range(F)], axis=1)
+
+
+# ---------------------------------------------------------------------------
+# a1 gather, a2 projection
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["f32", "f16", "frames_dyn"])
+def test_gather_bit_exact(orc, which):
+    sc = {"f32": lambda: H.scene_small_sh3(), "f16": lambda: H.scene_multilevel_f16(),
+          "frames_dyn": lambda: H.scene_small_sh3(frames=2, dyn=0.3)}[which]()
+    plan, r, _ = run_gpu(sc)
+    soa, texel, dyn = orc.gather(sc)
+    assert np.array_equal(r.soa.view(plan.D, plan.G).cpu().numpy().astype(np.float64), soa)
+    assert np.array_equal(H.u32(r.texel[:plan.N]), texel)
+    assert np.array_equal(r.dynflag[:plan.N].cpu().numpy(), dyn)
+    st = r.status()
+    assert st["flags"] == 0 and st["live_seen"] == plan.N
+
+
+def test_project_matches_oracle(orc):
+    sc = H.scene_small_sh3()
+    plan, r, _ = run_gpu(sc)
+    o = orc.forward(sc)
+    got = r.records.view(plan.V, plan.N, 12).cpu().numpy().astype(np.float64)
+    ref = o["rec"]
+    live = ref[..., 7] > 0
+    assert np.array_equal(got[..., 7] > 0, live)
+    g, e = got[live], ref[live]
+    assert np.abs(g[:, 0:2] - e[:, 0:2]).max() < 2e-3                               # mean, px
+    assert (np.abs(g[:, 2:5] - e[:, 2:5]) / np.abs(e[:, 2:5]).max(1, keepdims=True)).max() < 1e-4
+    assert np.abs(g[:, 5] - e[:, 5]).max() < 1e-6                                   # opacity
+    assert (np.abs(g[:, 6] - e[:, 6]) / e[:, 6]).max() < 1e-6                      # depth
+    assert np.abs(g[:, 8:11] - e[:, 8:11]).max() < 1e-5                             # colour
+    # radius = ceil(3 sqrt(lambda_max)) may flip only where 3 sqrt(lambda) is an integer to FP32 precision
+    assert np.mean(g[:, 7] != e[:, 7]) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# a3 binning and sort: bit-exact on identical FP32 inputs
+# ---------------------------------------------------------------------------
+
+def _synthetic_records(views, N, seed):
+    rng = np.random.default_rng(seed)
+    V = len(views)
+    rec = np.zeros((V, N, 12), np.float32)
+    for v, vw in enumerate(views):
+        rec[v, :, 0] = rng.uniform(-30, vw.width + 30, N)
+        rec[v, :, 1] = rng.uniform(-30, vw.height + 30, N)
+        # Sigma2D = L L^T + 0.3 I
+        L = rng.normal(0, 1, (N, 2, 2)) * np.exp(rng.normal(0.8, 0.8, (N, 1, 1)))
+        S = L @ L.transpose(0, 2, 1) + 0.3 * np.eye(2)
+        det = S[:, 0, 0] * S[:, 1, 1] - S[:, 0, 1] ** 2
+        rec[v, :, 2] = S[:, 1, 1] / det
+        rec[v, :, 3] = -S[:, 0, 1] / det
+        rec[v, :, 4] = S[:, 0, 0] / det
+        rec[v, :, 5] = rng.uniform(0.02, 1.0, N)
+        rec[v, :, 6] = rng.uniform(0.5, 8.0, N)
+        tr = S[:, 0, 0] + S[:, 1, 1]
+        lam = 0.5 * (tr + np.sqrt(np.maximum(0, tr * tr - 4 * det)))
+        rec[v, :, 7] = np.ceil(3 * np.sqrt(lam))
+        rec[v, :, 8:11] = rng.uniform(0, 1, (N, 3))
+    rec[:, ::13, 7] = 0                          # culled pairs
+    rec[:, 5::17, 6] = rec[:, 5, 6][:, None]     # exact depth ties
+    rec[:, 7::29, 7] = 4000                      # footprints larger than the view
+    return rec
+
+
+def _records_plan(views, N):
+    pk = _pk()
+    side = int(math.ceil(math.sqrt(N)))
+    return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N)
+
+
+def _records_setup(seed, N=700):
+    views = [synth.scenes.pinhole((0, 0, -3), 150, 100), synth.scenes.pinhole((0, 0, -3), 67, 131),
+             synth.scenes.pinhole((0, 0, -3), 16, 16)]
+    rec = _synthetic_records(views, N, seed)
+    return views, rec
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_bin_and_sort_bit_exact(orc, seed):
+    pk = _pk()
+    views, rec = _records_setup(seed)
+    V, N = rec.shape[:2]
+    plan = _records_plan(views, N)
+    ws = pk.make_workspace(plan)
+    pk.workspace_init(plan, ws)
+    drec = torch.from_numpy(rec.reshape(-1)).cuda()
+    vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    pk.bin_and_sort(plan, drec, vals, ranges, ws)
+    st = pk.read_status(plan, ws)
+    va = orc.views_array(views)
+    r = rec.reshape(V * N, 12)
+    ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, 16)
+    assert st["dups"] == len(ref_vals) and st["flags"] == 0
+    assert np.array_equal(H.u32(vals[:len(ref_vals)]), ref_vals)
+    assert np.array_equal(H.u32(ranges).reshape(-1, 2), ref_ranges)
+
+
+def test_bin_and_sort_capacity_overflow(orc):
+    pk = _pk()
+    views, rec = _records_setup(4)
+    V, N = rec.shape[:2]
+    side = int(math.ceil(math.sqrt(N)))
+    plan = pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, max_dups=1024)
+    ws = pk.make_workspace(plan)
+    pk.workspace_init(plan, ws)
+    vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
+    ranges = torch.full((2 * plan.n_tiles,), 7, dtype=torch.int32, device="cuda")
+    pk.bin_and_sort(plan, torch.from_numpy(rec.reshape(-1)).cuda(), vals, ranges, ws)
+    st = pk.read_status(plan, ws)
+    assert st["flags"] & 1 and st["rc"] == 3 and st["dups"] == 0 and st["dups_needed"] > 1024
+    assert int(ranges.abs().sum()) == 0
+
+
+# ---------------------------------------------------------------------------
+# a4 / a5 on identical FP32 records
+# ---------------------------------------------------------------------------
+
+def _records_forward(seed, dimg_seed=None):
+    pk = _pk()
+    views, rec = _records_setup(seed, N=500)
+    V, N = rec.shape[:2]
+    rec[..., 5] = np.minimum(rec[..., 5], 0.999)
+    plan = _records_plan(views, N)
+    ws = pk.make_workspace(plan)
+    pk.workspace_init(plan, ws)
+    drec = torch.from_numpy(rec.reshape(-1)).cuda()
+    vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    img = torch.empty(3 * plan.P, dtype=torch.float32, device="cuda")
+    T = torch.empty(plan.P, dtype=torch.float32, device="cuda")
+    nc = torch.empty(plan.P, dtype=torch.int32, device="cuda")
+    pk.bin_and_sort(plan, drec, vals, ranges, ws)
+    pk.rasterize_fwd(plan, drec, vals, ranges, img, T, nc, ws)
+    out = dict(plan=plan, ws=ws, rec=rec, drec=drec, vals=vals, ranges=ranges, img=img, T=T, nc=nc, views=views)
+    if dimg_seed is not None:
+        w = np.random.default_rng(dimg_seed).standard_normal(3 * plan.P).astype(np.float32)
+        g2 = torch.empty(12 * plan.pairs, dtype=torch.float32, device="cuda")
+        pk.rasterize_bwd(plan, drec, vals, ranges, T, nc, torch.from_numpy(w).cuda(), g2, ws)
+        out.update(w=w, g2=g2)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_rasterize_fwd_on_identical_records(orc, seed):
+    o = _records_forward(seed)
+    rec64 = o["rec"].astype(np.float64)
+    rec64[..., 11] = 0
+    va = orc.views_array(o["views"])
+    vals, ranges = orc.bin_sort(rec64, va, 16)
+    ref = orc.render(rec64, va, 16, vals, ranges, m_tol=1e-5)
+    ref["view_pixels"] = [v.width * v.height for v in o["views"]]
+    H.check_images(o["img"].cpu().numpy(), o["T"].cpu().numpy(), ref, tol=2e-5, max_border_frac=0.01)
+    ok = ref["border"] == 0
+    assert np.array_equal(H.u32(o["nc"])[ok], ref["last"][ok])
+    st = _pk().read_status(o["plan"], o["ws"])
+    assert st["evals_fwd"] > 0
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_rasterize_bwd_on_identical_records(orc, seed):
+    o = _records_forward(seed, dimg_seed=seed + 100)
+    rec64 = o["rec"].astype(np.float64)
+    rec64[..., 11] = 0
+    va = orc.views_array(o["views"])
+    vals, ranges = orc.bin_sort(rec64, va, 16)
+    ref = orc.render_bwd(rec64, va, 16, vals, ranges, o["w"].astype(np.float64))
+    got = o["g2"].view(-1, 12).cpu().numpy().astype(np.float64)[:, :9]
+    ref = ref.reshape(-1, 9)
+    for name, sl in {"mean": slice(0, 2), "conic": slice(2, 5), "opacity": slice(5, 6),
+                     "colour": slice(6, 9)}.items():
+        assert H.rel_err(got[:, sl], ref[:, sl]) < 1e-3, name
+
+
+# ---------------------------------------------------------------------------
+# Whole step against the oracle
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["sh3_small", "fp16_multilevel", "frames_dyn", "config1"])
+def test_end_to_end(orc, which):
+    sc = {"sh3_small": lambda: H.scene_small_sh3(), "fp16_multilevel": lambda: H.scene_multilevel_f16(),
+          "frames_dyn": lambda: H.scene_small_sh3(frames=2, dyn=0.3),
+          "config1": lambda: synth.config_scene(1)}[which]()
+    P = sc.pixels
+    w = np.random.default_rng(11).standard_normal(3 * P).astype(np.float32)
+    plan, r, grad = run_gpu(sc, dimg=w)
+    o = oracle_run(orc, sc, dimg=w)
+    H.check_images(r.image.cpu().numpy(), r.T.cpu().numpy(), o)
+    g = gpu_grad_soa(sc, grad, o["texel"])
+    H.check_grads(g, o["grad_soa"])
+    if sc.dyn is not None:
+        frozen = np.tile(o["dynflag"] == 0, sc.frames)
+        assert np.all(g[:, frozen] == 0)
+    # texels that are not live receive nothing
+    F, D, Hh, W = sc.atlas.shape
+    live = np.zeros(Hh * W, bool)
+    live[o["texel"]] = True
+    assert np.all(grad.view(F, D, Hh * W).cpu().numpy()[:, :, ~live] == 0)
+
+
+def test_config2_full_size(orc):
+    """1080p single view, 157,286 Gaussians with SH degree 3: images and gradients in full."""
+    sc = synth.config_scene(2)
+    w = np.random.default_rng(12).standard_normal(3 * sc.pixels).astype(np.float32)
+    plan, r, grad = run_gpu(sc, dimg=w)
+    o = oracle_run(orc, sc, dimg=w)
+    H.check_images(r.image.cpu().numpy(), r.T.cpu().numpy(), o)
+    H.check_grads(gpu_grad_soa(sc, grad, o["texel"]), o["grad_soa"])
+
+
+def test_config3_full_size_sampled_pixels(orc):
+    """The 52-view rig at full size, in the bench's launch configuration: sampled pixels."""
+    sc = synth.config_scene(3)
+    plan, r, _ = run_gpu(sc)
+    st = r.status()
+    assert st["flags"] == 0 and st["dups"] > 0
+    img = r.image.cpu().numpy()
+    T = r.T.cpu().numpy()
+    soa, texel, _ = orc.gather(sc)
+    rng = np.random.default_rng(13)
+    vsel = [0, 1, 25, 51]
+    va = orc.views_array([sc.views[v] for v in vsel])
+    rec = orc.project(soa, len(texel), sc.sh_degree, va)
+    pix = []
+    for i, v in enumerate(vsel):
+        vw = sc.views[v]
+        for _ in range(60):
+            pix.append((i, int(rng.integers(0, vw.width)), int(rng.integers(0, vw.height))))
+    rgb, Tr, border = orc.render_pixels(rec, va, 16, np.array(pix))
+    poff = np.cumsum([0] + [v.width * v.height for v in sc.views])
+    bad = 0
+    for k, (i, x, y) in enumerate(pix):
+        v = vsel[i]
+        vw = sc.views[v]
+        base = 3 * poff[v] + y * vw.width + x
+        got = np.array([img[base + c * vw.width * vw.height] for c in range(3)])
+        if border[k]:
+            continue
+        err = max(np.abs(got - rgb[k]).max(), abs(T[poff[v] + y * vw.width + x] - Tr[k]))
+        bad += err > H.IMG_TOL
+    assert bad == 0
+
+
+def test_batched_equals_per_view_loop(orc):
+    pk = _pk()
+    sc = H.scene_small_sh3()
+    P = sc.pixels
+    w = np.random.default_rng(14).standard_normal(3 * P).astype(np.float32)
+    plan, r, grad = run_gpu(sc, dimg=w)
+    loop = pk.PerViewLoop.for_scene(sc)
+    atlas, occ, dyn = H.upload(sc)
+    loop.dimage.copy_(torch.from_numpy(w))
+    F, D, Hh, W = sc.atlas.shape
+    g2 = torch.zeros(F * D * Hh * W, dtype=torch.float32, device="cuda")
+    loop.step(atlas, occ, dyn, None, g2, loss=False)
+    torch.cuda.synchronize()
+    assert torch.equal(loop.image, r.image) and torch.equal(loop.T, r.T)
+    assert torch.equal(loop.n_contrib, r.n_contrib)
+    assert H.rel_err(g2.cpu().numpy().astype(np.float64), grad.cpu().numpy().astype(np.float64)) < 1e-5
+
+
+def test_cuda_graph_replay_matches_eager():
+    pk = _pk()
+    sc = H.scene_small_sh3(seed=303)
+    plan = pk.Plan.for_scene(sc)
+    r = pk.Renderer(plan)
+    atlas, occ, dyn = H.upload(sc)
+    tgt = torch.from_numpy(synth.random_target(sc)).cuda()
+    F, D, Hh, W = sc.atlas.shape
+    grad = torch.zeros(F * D * Hh * W, dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        r.l1_step(atlas, occ, dyn, tgt, grad)
+    torch.cuda.synchronize()
+    img0, g0 = r.image.clone(), grad.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        r.l1_step(atlas, occ, dyn, tgt, grad)
+    r.image.zero_()
+    grad.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(r.image, img0)
+    assert H.rel_err(grad.cpu().numpy(), g0.cpu().numpy()) < 1e-5
+    st = r.status()
+    assert st["flags"] == 0 and st["loss"] > 0
+
+
+def test_live_count_mismatch_is_reported():
+    pk = _pk()
+    sc = H.scene_small_sh3()
+    F, D, Hh, W = sc.atlas.shape
+    plan = pk.Plan(sc.levels, (W, Hh), sc.sh_degree, F, "f32", sc.views, sc.n_live - 5)
+    r = pk.Renderer(plan)
+    atlas, occ, dyn = H.upload(sc)
+    r.forward(atlas, occ, dyn)
+    st = r.status()
+    assert st["flags"] & 2 and st["live_seen"] == sc.n_live
+
+
+def test_nothing_visible_gives_background():
+    pk = _pk()
+    sc = H.scene_small_sh3()
+    # camera at z = +50 looking along +z: every mean is behind it
+    views = [synth.View(R=np.eye(3), t=np.array([0.0, 0.0, -50.0]), fx=60.0, fy=60.0, cx=32.0, cy=20.0,
+                        width=64, height=40)]
+    F, D, Hh, W = sc.atlas.shape
+    plan = pk.Plan(sc.levels, (W, Hh), sc.sh_degree, F, "f32", views, sc.n_live, bg=(0.25, 0.5, 1.0))
+    r = pk.Renderer(plan)
+    atlas, occ, dyn = H.upload(sc)
+    r.forward(atlas, occ, dyn)
+    torch.cuda.synchronize()
+    img = r.image.view(3, -1).cpu().numpy()
+    assert np.all(img[0] == 0.25) and np.all(img[1] == 0.5) and np.all(img[2] == 1.0)
+    assert np.all(r.T.cpu().numpy() == 1.0) and r.status()["dups"] == 0
