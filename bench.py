@@ -385,9 +385,9 @@ def main():
                       "d2h_bytes_per_step": int(h_grad.numel() * 4 + 64), "loss": s["loss"]}
 
     if not args.profile and not args.no_per_view and rank == 0:
-        loop = pk.PerViewLoop.for_scene(scene, dev, max_dups=int(dups / max(1, plan.V) * 4) + 65536)
+        loop = pk.PerViewLoop.for_scene(scene, dev, max_dups=int(dups / max(1, plan.V) * 2) + 65536)
         with torch.cuda.stream(stream):
-            loop.step(atlas, occ, dyn, target, grad)
+            loop.ensure_capacity(atlas, occ, dyn, target, grad)
         torch.cuda.synchronize(dev)
         kp = max(1, min(args.steps, 3))
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

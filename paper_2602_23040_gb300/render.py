@@ -136,6 +136,26 @@ class PerViewLoop:
             self.offsets.append(o)
             o += p.P
 
+    def ensure_capacity(self, atlas, occ, dyn, target, grad_atlas, headroom: float = 1.15) -> bool:
+        """Run one step; re-plan every view whose entries overflowed, once.
+        Host-synchronising.  Returns True when every view fits."""
+        self.step(atlas, occ, dyn, target, grad_atlas, loss=target is not None)
+        grown = False
+        for i, (p, w) in enumerate(zip(self.plans, self.ws)):
+            st = api.read_status(p, w)
+            if st["flags"] & 1:
+                p2 = p.with_capacity(int(st["dups_needed"] * headroom) + 4096)
+                w2 = api.make_workspace(p2, self.device)
+                api.workspace_init(p2, w2)
+                self.plans[i], self.ws[i] = p2, w2
+                grown = True
+        if grown:
+            md = max(int(p.max_dups) for p in self.plans)
+            if self.sorted_vals.numel() < md + 64:
+                self.sorted_vals = torch.empty(md + 64, dtype=torch.int32, device=self.device)
+            self.step(atlas, occ, dyn, target, grad_atlas, loss=target is not None)
+        return all(api.read_status(p, w)["flags"] == 0 for p, w in zip(self.plans, self.ws))
+
     def _slices(self, i):
         o, P = self.offsets[i], self.plans[i].P
         return (self.image[3 * o:3 * (o + P)], self.T[o:o + P], self.n_contrib[o:o + P],
