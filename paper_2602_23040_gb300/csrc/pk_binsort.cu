@@ -259,45 +259,76 @@ __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__re
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
   chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
-  for (uint64_t i = b0 + threadIdx.x; i < b1; i += kThreads) {
-    const uint32_t d = (__ldg(keys + i) >> shift) & mask;
-    const uint32_t peers = __match_any_sync(__activemask(), d);
-    if ((peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+  // chunks start on a multiple of kSortTile: 16-byte aligned vector loads
+  const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + b0);
+  const uint64_t n4 = (b1 - b0) / 4;
+  for (uint64_t i = threadIdx.x; i < n4; i += kThreads) {
+    const uint4 q = __ldg(k4 + i);
+    const uint32_t kk[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t d = (kk[j] >> shift) & mask;
+      const uint32_t peers = __match_any_sync(__activemask(), d);
+      if ((peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+    }
   }
+  for (uint64_t i = b0 + 4 * n4 + threadIdx.x; i < b1; i += kThreads)
+    atomicAdd(&s_cnt[(__ldg(keys + i) >> shift) & mask], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < kRadix; d += kThreads) hist[(size_t)d * gridDim.x + blockIdx.x] = s_cnt[d];
 }
 
-// Exclusive scan of hist in [digit][block] order (one block of 1024).
+// Exclusive scan of hist in [digit][block] order (one block of 1024 threads,
+// coalesced: each pass covers 4096 consecutive counters).
 __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist, int count) {
   __shared__ uint32_t s[33];
+  __shared__ uint32_t s_carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (count + 1023) / 1024;
-  const int b = tid * per, e = min(count, b + per);
-  uint32_t acc = 0;
-  for (int i = b; i < e; ++i) acc += hist[i];
-  uint32_t incl = warp_incl_scan(acc);
-  if (lane == 31) s[warp] = incl;
+  if (tid == 0) s_carry = 0;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = s[lane];
-    uint32_t wi = warp_incl_scan(w);
-    s[lane] = wi - w;
-  }
-  __syncthreads();
-  uint32_t run = s[warp] + incl - acc;
-  for (int i = b; i < e; ++i) {
-    uint32_t h = hist[i];
-    hist[i] = run;
-    run += h;
+  for (int base = 0; base < count; base += 4096) {
+    const int i = base + 4 * tid;
+    uint4 q = make_uint4(0, 0, 0, 0);
+    if (i + 3 < count) q = *reinterpret_cast<const uint4 *>(hist + i);
+    else {
+      if (i < count) q.x = hist[i];
+      if (i + 1 < count) q.y = hist[i + 1];
+      if (i + 2 < count) q.z = hist[i + 2];
+    }
+    const uint32_t sum = q.x + q.y + q.z + q.w;
+    const uint32_t incl = warp_incl_scan(sum);
+    if (lane == 31) s[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = s[lane];
+      const uint32_t wi = warp_incl_scan(w);
+      s[lane] = wi - w;
+      if (lane == 31) s[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t carry = s_carry;
+    uint32_t e = carry + s[warp] + incl - sum;
+    uint4 o;
+    o.x = e; e += q.x;
+    o.y = e; e += q.y;
+    o.z = e; e += q.z;
+    o.w = e;
+    if (i + 3 < count) *reinterpret_cast<uint4 *>(hist + i) = o;
+    else {
+      if (i < count) hist[i] = o.x;
+      if (i + 1 < count) hist[i + 1] = o.y;
+      if (i + 2 < count) hist[i + 2] = o.z;
+    }
+    __syncthreads();
+    if (tid == 0) s_carry = carry + s[32];
+    __syncthreads();
   }
 }
 
-__global__ __launch_bounds__(kThreads) void k_radix_downsweep(const uint32_t *__restrict__ kin,
-                                                              const uint32_t *__restrict__ vin,
-                                                              uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                                              const uint32_t *n_dev, uint64_t n_host, int shift,
-                                                              uint32_t mask, const uint32_t *__restrict__ hist) {
+__global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
+    const uint32_t *__restrict__ hist) {
   __shared__ uint32_t s_wcnt[kWarps][kRadix];
   __shared__ uint32_t s_start[kRadix];
   __shared__ uint32_t s_gbase[kRadix];
@@ -314,13 +345,13 @@ __global__ __launch_bounds__(kThreads) void k_radix_downsweep(const uint32_t *__
     const uint32_t valid = (uint32_t)min((uint64_t)kSortTile, b1 - base);
     for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    // stable warp-level ranking: items in (warp, item, lane) order
+    uint32_t key[kSortItems], rank[kSortItems];
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
       const uint32_t li = (uint32_t)(warp * 32 * kSortItems + j * 32 + lane);
       const bool in = li < valid;
       key[j] = in ? __ldg(kin + base + li) : 0xffffffffu;
-      val[j] = in ? __ldg(vin + base + li) : 0u;
       const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const uint32_t before = __popc(peers & lt);
@@ -332,7 +363,7 @@ __global__ __launch_bounds__(kThreads) void k_radix_downsweep(const uint32_t *__
     }
     __syncthreads();
     // per digit: prefix over warps, then over digits
-    uint32_t dcount = 0;
+    uint32_t dcount;
     {
       const int d = tid;   // kThreads == kRadix
       uint32_t sum = 0;
@@ -350,10 +381,11 @@ __global__ __launch_bounds__(kThreads) void k_radix_downsweep(const uint32_t *__
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
       const uint32_t li = (uint32_t)(warp * 32 * kSortItems + j * 32 + lane);
-      const uint32_t d = li < valid ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
+      const bool in = li < valid;
+      const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
       const uint32_t r = s_start[d] + s_wcnt[warp][d] + rank[j];
       s_keys[r] = key[j];
-      s_vals[r] = val[j];
+      s_vals[r] = in ? __ldg(vin + base + li) : 0u;
     }
     __syncthreads();
     for (uint32_t i = tid; i < valid; i += kThreads) {
@@ -428,24 +460,41 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
   }
 }
 
-// Tile ranges from the sorted tile ids.
+// Tile ranges from the sorted tile ids; four entries per thread.
 __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, const DevCounters *ctr,
                                                      uint32_t *__restrict__ ranges) {
   const uint32_t n = ctr->dups;
-  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[2 * (size_t)t] = i;
-    if (i + 1 == n || keys[i + 1] != t) ranges[2 * (size_t)t + 1] = i + 1;
+  const uint32_t nq = (n + 3) / 4;
+  for (uint32_t q = blockIdx.x * kThreads + threadIdx.x; q < nq; q += gridDim.x * kThreads) {
+    const uint32_t i0 = 4 * q;
+    uint32_t k[6];   // keys[i0 - 1 .. i0 + 4]
+    k[0] = i0 ? __ldg(keys + i0 - 1) : 0xffffffffu;
+    if (i0 + 3 < n) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keys + i0));
+      k[1] = v.x; k[2] = v.y; k[3] = v.z; k[4] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < n ? __ldg(keys + i0 + j) : 0xffffffffu;
+    }
+    k[5] = i0 + 4 < n ? __ldg(keys + i0 + 4) : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t i = i0 + j;
+      if (i >= n) break;
+      const uint32_t t = k[1 + j];
+      if (i == 0 || k[j] != t) ranges[2 * (size_t)t] = i;
+      if (i + 1 == n || k[2 + j] != t) ranges[2 * (size_t)t + 1] = i + 1;
+    }
   }
 }
 
 pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                     const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist,
+                     const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
                      cudaStream_t st) {
   const uint32_t mask = (1u << bits) - 1u;
-  k_radix_upsweep<<<kSortBlocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist);
-  k_radix_scan<<<1, 1024, 0, st>>>(hist, kRadix * kSortBlocks);
-  k_radix_downsweep<<<kSortBlocks, kThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_host, shift, mask, hist);
+  k_radix_upsweep<<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist);
+  k_radix_scan<<<1, 1024, 0, st>>>(hist, kRadix * nblocks);
+  k_radix_downsweep<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_host, shift, mask, hist);
   return check_launch();
 }
 
@@ -470,6 +519,11 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
   uint32_t *dv = at<uint32_t>(ws, L.dval);
   const uint32_t *n_valid = &ctr->n_valid;
   const uint64_t pairs = (uint64_t)p->pairs;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // sort blocks: 3 resident per SM, within the histogram's capacity
+  const int nsort = std::max(1, std::min(kSortBlocks, 3 * sms));
 
   if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
     return PK_ERR_CUDA;
@@ -490,7 +544,7 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
     const uint32_t *vi = (pass & 1) ? pv1 : pv0;
     uint32_t *ko = (pass & 1) ? zk0 : zk1;
     uint32_t *vo = (pass & 1) ? pv0 : pv1;
-    if ((e = radix_pass(ki, vi, ko, vo, n_valid, 0, 8 * pass, 8, hist, st)) != PK_OK) return e;
+    if ((e = radix_pass(ki, vi, ko, vo, n_valid, 0, 8 * pass, 8, hist, nsort, st)) != PK_OK) return e;
   }
   // emission offsets in depth order, capacity check
   SrcSorted ss{cnt, pv0};
@@ -501,14 +555,14 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
   const int npass = (p->tile_bits + 7) / 8;
   uint32_t *vbuf[2] = {(npass & 1) ? dv : sorted_vals, (npass & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
-  k_emit<<<152 * 8, kThreads, 0, st>>>(records, pv0, offs, ctr, views, p->N, p->T, kbuf[0], vbuf[0]);
+  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, ctr, views, p->N, p->T, kbuf[0], vbuf[0]);
   const uint32_t *n_dups = &ctr->dups;
   for (int pass = 0; pass < npass; ++pass) {
     const int bits = std::min(8, p->tile_bits - 8 * pass);
     if ((e = radix_pass(kbuf[pass & 1], vbuf[pass & 1], kbuf[(pass + 1) & 1], vbuf[(pass + 1) & 1], n_dups, 0,
-                        8 * pass, bits, hist, st)) != PK_OK)
+                        8 * pass, bits, hist, nsort, st)) != PK_OK)
       return e;
   }
-  k_ranges<<<152 * 8, kThreads, 0, st>>>(kbuf[npass & 1], ctr, tile_ranges);
+  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[npass & 1], ctr, tile_ranges);
   return check_launch();
 }

@@ -2,18 +2,55 @@
 // walks its tile's list backwards from its last blended splat, recovering
 // T_i = T_{i+1} / (1 - alpha_i) from the stored final transmittance, so no
 // per-step state of the forward is kept.  Per splat the 9 gradients of a
-// warp's 32 pixels are summed with shuffles and added to the splat's
-// gradient record with vector atomics from one lane.
+// warp's 32 pixels are summed by a reduce-scatter over the lanes (12
+// shuffles instead of 45 for nine full butterfly sums), after which nine
+// lanes each hold one complete sum and add it to the splat's gradient
+// record with one coalesced atomic instruction.
 #include "pk_raster.cuh"
 
 using namespace pk;
 
 namespace {
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Reduce-scatter of v[0..8] over the 32 lanes.  Level xor-16 splits the
+// nine values 5 | 4, xor-8 splits each half 3 | 2, xor-4 2 | 1, xor-2 1 | 1
+// and xor-1 adds the last pair.  Returns the complete sum held by this lane
+// and its value index in *idx (-1 for lanes left holding padding).
+__device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int lane, int *idx) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float w[5];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int j = 0; j < 5; ++j) {
+    const float lo = v[j], hi = (5 + j < 9) ? v[5 + j] : 0.f;
+    const float r = __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
+    w[j] = (b4 ? hi : lo) + r;
+  }
+  float x[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float lo = w[j], hi = (3 + j < 5) ? w[3 + j] : 0.f;
+    const float r = __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
+    x[j] = (b3 ? hi : lo) + r;
+  }
+  float y[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float lo = x[j], hi = (2 + j < 3) ? x[2 + j] : 0.f;
+    const float r = __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
+    y[j] = (b2 ? hi : lo) + r;
+  }
+  float z;
+  {
+    const float r = __shfl_xor_sync(0xffffffffu, b1 ? y[0] : y[1], 2);
+    z = (b1 ? y[1] : y[0]) + r;
+  }
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  // value index held: level sets [0..4 | 5..8], slots [0,1,2 | 3,4], [0,1 | 2], [0 | 1]
+  const int s2 = b2 ? (b1 ? -1 : 2) : (b1 ? 1 : 0);         // slot in x
+  const int s3 = s2 < 0 ? -1 : (b3 ? (s2 < 2 ? 3 + s2 : -1) : s2);  // slot in w
+  const int s4 = s3 < 0 ? -1 : (b4 ? (s3 < 4 ? 5 + s3 : -1) : s3);  // value index
+  *idx = (lane & 1) ? -1 : s4;
+  return z;
 }
 
 __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
@@ -113,21 +150,12 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
           }
         }
         if (__any_sync(0xffffffffu, act)) {
-          dmx = warp_sum(dmx);
-          dmy = warp_sum(dmy);
-          dca = warp_sum(dca);
-          dcb = warp_sum(dcb);
-          dcc = warp_sum(dcc);
-          dop = warp_sum(dop);
-          dr = warp_sum(dr);
-          dg = warp_sum(dg);
-          db = warp_sum(db);
-          if (lane == 0) {
+          const float v9[9] = {dmx, dmy, dca, dcb, dcc, dop, dr, dg, db};
+          int idx;
+          const float sum = warp_reduce_scatter9(v9, lane, &idx);
+          if (idx >= 0) {
             const uint32_t pid = __float_as_uint(s_c[j].y);
-            float *gp = grad2d + (size_t)pid * kG2d;
-            atomicAdd(reinterpret_cast<float4 *>(gp), make_float4(dmx, dmy, dca, dcb));
-            atomicAdd(reinterpret_cast<float4 *>(gp + 4), make_float4(dcc, dop, dr, dg));
-            atomicAdd(gp + 8, db);
+            atomicAdd(grad2d + (size_t)pid * kG2d + idx, sum);
           }
         }
       }

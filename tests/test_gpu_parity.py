@@ -213,6 +213,9 @@ def test_rasterize_fwd_on_identical_records(orc, seed):
     vals, ranges = orc.bin_sort(rec64, va, 16)
     ref = orc.render(rec64, va, 16, vals, ranges, m_tol=1e-5)
     ref["view_pixels"] = [v.width * v.height for v in o["views"]]
+    # identical FP32 depths on both sides: the depth order is the same (the sort is bit-exact), so
+    # near-equal depths are not borderline here
+    ref["border"] = ref["border"] & ~np.uint8(8)
     H.check_images(o["img"].cpu().numpy(), o["T"].cpu().numpy(), ref, tol=2e-5, max_border_frac=0.01)
     ok = ref["border"] == 0
     assert np.array_equal(H.u32(o["nc"])[ok], ref["last"][ok])
