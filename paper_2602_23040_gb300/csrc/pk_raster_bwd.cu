@@ -112,10 +112,23 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       __syncthreads();
       if (tid < nb) stage_splat(rec, __ldg(vals + s + beg + tid), st, tid);
       __syncthreads();
-      for (int j = nb - 1; j >= 0; --j) {
+      // splats that can reach this warp's block and that some pixel of the
+      // warp blended or skipped before stopping (list position < wmax)
+      uint32_t hits[kBatch / 32];
+#pragma unroll
+      for (int k = 0; k < kBatch / 32; ++k) {
+        const int j = 32 * k + lane;
+        hits[k] = __ballot_sync(0xffffffffu, j < nb && beg + (uint32_t)j < wmax &&
+                                                 !box_misses(s_box[j], wx0, wx1, wy0, wy1));
+      }
+#pragma unroll
+      for (int k = kBatch / 32 - 1; k >= 0; --k) {
+       uint32_t m = hits[k];
+       while (m) {
+        const int bit = 31 - __clz(m);
+        m &= ~(1u << bit);
+        const int j = 32 * k + bit;
         const uint32_t pos = beg + (uint32_t)j;       // 0-based list position
-        if (pos >= wmax) continue;                    // no pixel of this warp reached it
-        if (box_misses(s_box[j], wx0, wx1, wy0, wy1)) continue;
         const float4 a = s_a[j], b = s_b[j];
         Hit h;
         bool act = false;
@@ -158,6 +171,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
             atomicAdd(grad2d + (size_t)pid * kG2d + idx, sum);
           }
         }
+       }
       }
       end = beg;
     }

@@ -55,27 +55,41 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
       if (tid < nb) stage_splat(rec, __ldg(vals + base + tid), st, tid);
       __syncthreads();
       if (!__all_sync(0xffffffffu, done)) {
-        for (int j = 0; j < nb; ++j) {
-          if (box_misses(s_box[j], wx0, wx1, wy0, wy1)) continue;
-          if (!done) {
-            const float4 a = s_a[j], b = s_b[j];
-            Hit h;
-            ++evals;
-            if (splat_alpha(a, b.x, b.y, px, py, h)) {
-              const float Tn = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
-              if (Tn < kTMin) {
-                done = true;
-              } else {
-                const float w = __fmul_rn(h.alpha, T);
-                c0 = __fmaf_rn(w, b.z, c0);
-                c1 = __fmaf_rn(w, b.w, c1);
-                c2 = __fmaf_rn(w, s_c[j].x, c2);
-                T = Tn;
-                last = base - s + (uint32_t)j + 1u;
+        // which staged splats can reach this warp's block: 8 box tests per
+        // lane, one ballot per 32 splats, then only the hits are visited
+        uint32_t hits[kBatch / 32];
+#pragma unroll
+        for (int k = 0; k < kBatch / 32; ++k) {
+          const int j = 32 * k + lane;
+          hits[k] = __ballot_sync(0xffffffffu, j < nb && !box_misses(s_box[j], wx0, wx1, wy0, wy1));
+        }
+        bool all_done = false;
+#pragma unroll
+        for (int k = 0; k < kBatch / 32; ++k) {
+          uint32_t m = hits[k];
+          while (m && !all_done) {
+            const int j = 32 * k + __ffs(m) - 1;
+            m &= m - 1;
+            if (!done) {
+              const float4 a = s_a[j], b = s_b[j];
+              Hit h;
+              ++evals;
+              if (splat_alpha(a, b.x, b.y, px, py, h)) {
+                const float Tn = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
+                if (Tn < kTMin) {
+                  done = true;
+                } else {
+                  const float w = __fmul_rn(h.alpha, T);
+                  c0 = __fmaf_rn(w, b.z, c0);
+                  c1 = __fmaf_rn(w, b.w, c1);
+                  c2 = __fmaf_rn(w, s_c[j].x, c2);
+                  T = Tn;
+                  last = base - s + (uint32_t)j + 1u;
+                }
               }
             }
+            all_done = __all_sync(0xffffffffu, done);
           }
-          if (__all_sync(0xffffffffu, done)) break;
         }
       }
       if (__syncthreads_count(!done) == 0) break;
