@@ -100,11 +100,17 @@ typedef struct pk_view {
   int32_t frame;                   /* atlas frame rendered by this view */
 } pk_view;
 
+/* Which tiles of a splat's r-square (r = ceil(3 sqrt(lambda_max))) receive
+ * it: every one (PK_BIN_RECT), or those its footprint q <= 9 reaches
+ * (PK_BIN_ELLIPSE, the default).  Images are the same in both modes. */
+typedef enum pk_bin_mode { PK_BIN_RECT = 0, PK_BIN_ELLIPSE = 1 } pk_bin_mode;
+
 typedef struct pk_options {
   int32_t tile;                    /* tile side: 16 (8 and 32 reserved) */
   float znear;                     /* cull z <= znear; default 0.01 */
   float bg[3];                     /* background colour; default 0 */
   uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
+  int32_t bin_mode;                /* pk_bin_mode; default PK_BIN_ELLIPSE */
 } pk_options;
 
 typedef struct pk_plan pk_plan;
@@ -201,14 +207,19 @@ pk_status pk_project_and_sh(const pk_plan *plan, const float *soa, float *record
                             void *workspace, pk_stream_t stream);
 
 /* a3 -- Sec. 3 (tile-based rasteriser), Supp. "Viewer" (per-camera depth
- * order).  For each pair with radius > 0 the tile rectangle is, in FP32 and
- * this order without fused multiply-add: lo = max(ceil((m - 0.5) - r), 0),
- * hi = min(floor((m - 0.5) + r), size - 1) per axis, empty if lo > hi;
- * tiles lo/T .. hi/T.  Every (pair, tile) becomes one entry; entries are
- * ordered by (global tile id, bits(z), pair index), which is a stable sort
- * of the keys (tile << 32 | bits(z)) in emission order (view, Gaussian,
- * tile row-major).  Bit-exact by contract.
- * records:     [V*N][12] (reads m, z, radius only).
+ * order).  For each pair with radius > 0 the candidate tiles are, in FP32
+ * and this order without fused multiply-add: lo = max(ceil((m - 0.5) - r),
+ * 0), hi = min(floor((m - 0.5) + r), size - 1) per axis, empty if lo > hi;
+ * tiles lo/T .. hi/T.  In PK_BIN_ELLIPSE mode a candidate tile receives the
+ * splat only if the minimum of q = d^T conic d over the rectangle of the
+ * tile's pixel centres is <= 9 (1 + 2^-12) (the 3-sigma footprint of Sec.
+ * 4.2 / Alg. 1 step 5), evaluated in FP32 as: inside -> yes, else the
+ * least q over the four edges with the 1-D minimiser -(b d)/c (resp. /a)
+ * clamped to the edge.  Every receiving (pair, tile) becomes one entry;
+ * entries are ordered by (global tile id, bits(z), pair index), which is a
+ * stable sort of the keys (tile << 32 | bits(z)) in emission order (view,
+ * Gaussian, tile row-major).  Bit-exact by contract.
+ * records:     [V*N][12] (reads m, conic, z, radius).
  * sorted_vals: out [max_dups] uint32 pair index of each entry.
  * tile_ranges: out [n_tiles][2] uint32 [start, end) into sorted_vals;
  *              global tile id = tile_off(v) + ty * ceil(W_v/T) + tx.

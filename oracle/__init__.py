@@ -71,7 +71,7 @@ def _declare(L):
         "or_sh_basis": (None, [C.c_int, P, P, P]),
         "or_project": (None, [P, I64, I64, C.c_int, C.c_int, P, C.c_int, DBL, P]),
         "or_tiles_total": (I64, [C.c_int, P, P, C.c_int, P]),
-        "or_bin_sort": (I64, [P, P, P, P, C.c_int, I64, P, P, C.c_int, P, I64, P]),
+        "or_bin_sort": (I64, [P, P, P, P, P, P, P, C.c_int, C.c_int, I64, P, P, C.c_int, P, I64, P]),
         "or_render": (U64, [P, C.c_int, I64, P, C.c_int, P, P, P, DBL, P, P, P, P]),
         "or_render_bwd": (None, [P, C.c_int, I64, P, C.c_int, P, P, P, P, P]),
         "or_scatter_grad": (None, [P, I64, I64, C.c_int, C.c_int, P, C.c_int, DBL, P, P, P]),
@@ -196,25 +196,33 @@ def tiles_total(views_arr, tile):
     return int(t), toff[:-1]
 
 
-def bin_sort32(mx, my, rad, z, views_arr, N, tile, cap=None):
+BIN_RECT, BIN_ELLIPSE = 0, 1
+
+
+def bin_sort32(mx, my, rad, z, views_arr, N, tile, ca=None, cb=None, cc=None, mode=BIN_ELLIPSE):
     """Integer stage on FP32 inputs (each a flat [V*N] float32 array)."""
     mx, my, rad, z = (np.ascontiguousarray(a, np.float32).reshape(-1) for a in (mx, my, rad, z))
+    if mode == BIN_ELLIPSE:
+        ca, cb, cc = (np.ascontiguousarray(a, np.float32).reshape(-1) for a in (ca, cb, cc))
+    else:
+        ca = cb = cc = None
     V = views_arr.shape[0]
     vw = np.ascontiguousarray(views_arr[:, 16], np.int32)
     vh = np.ascontiguousarray(views_arr[:, 17], np.int32)
     ntiles, _ = tiles_total(views_arr, tile)
     ranges = np.zeros((ntiles, 2), np.uint32)
-    n = lib().or_bin_sort(_p(mx), _p(my), _p(rad), _p(z), V, N, _p(vw), _p(vh), tile, None, 0, _p(ranges))
+    args = (_p(mx), _p(my), _p(rad), _p(z), _p(ca), _p(cb), _p(cc), mode, V, N, _p(vw), _p(vh), tile)
+    n = lib().or_bin_sort(*args, None, 0, _p(ranges))
     vals = np.zeros(max(n, 1), np.uint32)
-    n2 = lib().or_bin_sort(_p(mx), _p(my), _p(rad), _p(z), V, N, _p(vw), _p(vh), tile, _p(vals), n, _p(ranges))
+    n2 = lib().or_bin_sort(*args, _p(vals), n, _p(ranges))
     assert n2 == n
     return vals[:n].copy(), ranges
 
 
-def bin_sort(rec, views_arr, tile):
+def bin_sort(rec, views_arr, tile, mode=BIN_ELLIPSE):
     V, N, _ = rec.shape
     r = rec.reshape(V * N, REC)
-    return bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], views_arr, N, tile)
+    return bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], views_arr, N, tile, r[:, 2], r[:, 3], r[:, 4], mode)
 
 
 def render(rec, views_arr, tile, vals, ranges, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
@@ -268,12 +276,12 @@ def render_pixels(rec, views_arr, tile, pix, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
 # Whole step
 # --------------------------------------------------------------------------
 
-def forward(scene, tile=16, znear=ZNEAR, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
+def forward(scene, tile=16, znear=ZNEAR, bg=(0.0, 0.0, 0.0), m_tol=5e-4, mode=BIN_ELLIPSE):
     soa, texel, dynflag = gather(scene)
     va = views_array(scene.views)
     N = len(texel)
     rec = project(soa, N, scene.sh_degree, va, znear)
-    vals, ranges = bin_sort(rec, va, tile)
+    vals, ranges = bin_sort(rec, va, tile, mode)
     out = render(rec, va, tile, vals, ranges, bg, m_tol)
     out.update(soa=soa, texel=texel, dynflag=dynflag, views=va, rec=rec, vals=vals, ranges=ranges, N=N)
     return out

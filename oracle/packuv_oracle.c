@@ -23,7 +23,10 @@
  *                      pinhole projection X_c = R X + t; Sec. 3 (3DGS:
  *                      opacity, SH colour)
  *   or_bin_sort        Sec. 3 (tile-based rasterizer) and Supp. "Viewer"
- *                      (Gaussians depth-sorted per camera)
+ *                      (Gaussians depth-sorted per camera); a tile receives
+ *                      a splat if its 3-sigma footprint (Sec. 4.2, d^2 <= 9)
+ *                      reaches the tile (or, in the rectangle mode, if the
+ *                      tile meets the r = ceil(3 sqrt(lambda_max)) square)
  *   or_render          Supp. "Viewer" compositing C = sum T_i a_i c_i,
  *                      T_i = prod_{j<i} (1 - a_j); footprint d^2 <= 9 of
  *                      Sec. 4.2 / Alg. 1 step 5
@@ -472,6 +475,46 @@ static int bin_rect32(float mx, float my, float r, int W, int H, int T, int *t) 
   return 1;
 }
 
+/*
+ * Ellipse binning rule: does the footprint q = d^T conic d <= 9 (times
+ * 1 + 2^-12, so FP32 per-pixel tests can never accept a pixel outside it)
+ * reach the rectangle [x0, x1] x [y0, y1] of a tile's pixel centres?  The
+ * minimum of q over the rectangle is 0 if the mean is inside, else it lies
+ * on an edge: on x = const the minimiser is dy = -(b dx)/c clamped to the
+ * edge, likewise on y = const.  FP32, in exactly this order, no FMA.
+ */
+static int ellipse_hits_rect32(float mx, float my, float a, float b, float c, float x0, float x1, float y0,
+                               float y1) {
+  const float qmax = 9.0f * (1.0f + 1.0f / 4096.0f);
+  if (!(a > 0.0f) || !(c > 0.0f)) return 1;
+  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 1;
+  const float ra = 1.0f / a, rc = 1.0f / c, b2 = b + b;
+  const float lx = x0 - mx, hx = x1 - mx, ly = y0 - my, hy = y1 - my;
+  float best = INFINITY;
+  const float ex[2] = {lx, hx}, ey[2] = {ly, hy};
+  for (int i = 0; i < 2; ++i) {
+    float dx = ex[i];
+    float t = b * dx;
+    t = t * rc;
+    float dy = fminf(fmaxf(-t, ly), hy);
+    float q = (a * dx) * dx;
+    q = q + (b2 * dx) * dy;
+    q = q + (c * dy) * dy;
+    best = fminf(best, q);
+  }
+  for (int i = 0; i < 2; ++i) {
+    float dy = ey[i];
+    float t = b * dy;
+    t = t * ra;
+    float dx = fminf(fmaxf(-t, lx), hx);
+    float q = (a * dx) * dx;
+    q = q + (b2 * dx) * dy;
+    q = q + (c * dy) * dy;
+    best = fminf(best, q);
+  }
+  return best <= qmax;
+}
+
 typedef struct {
   uint64_t key, idx;
   uint32_t val;
@@ -499,16 +542,29 @@ int64_t or_tiles_total(int V, const int32_t *vw, const int32_t *vh, int T, int64
   return t;
 }
 
+/* Does tile (tx, ty) of a W x H view receive the splat?  mode 0: every
+   tile of the rectangle does; mode 1: only tiles the ellipse reaches. */
+static int tile_receives(int mode, const float *ca, const float *cb, const float *cc, int64_t p, float mx,
+                         float my, int tx, int ty, int W, int H, int T) {
+  if (mode == 0) return 1;
+  const float x0 = (float)(tx * T) + 0.5f, y0 = (float)(ty * T) + 0.5f;
+  const float x1 = (float)((tx + 1) * T < W ? (tx + 1) * T : W) - 0.5f;
+  const float y1 = (float)((ty + 1) * T < H ? (ty + 1) * T : H) - 0.5f;
+  return ellipse_hits_rect32(mx, my, ca[p], cb[p], cc[p], x0, x1, y0, y1);
+}
+
 /*
- * Emit one (key, value) per touched tile, in order view, Gaussian, tile
- * row-major; key = (global tile id << 32) | bits(z), value = v*N + g; sort
- * ascending by (key, emission index).  ranges[2t], ranges[2t+1] = [start,
- * end) of tile t.  Returns the number of entries, or -1 if above cap;
- * with vals == NULL only counts them.
+ * Emit one (key, value) per receiving tile of the splat's rectangle, in
+ * order view, Gaussian, tile row-major; key = (global tile id << 32) |
+ * bits(z), value = v*N + g; sort ascending by (key, emission index).
+ * ranges[2t], ranges[2t+1] = [start, end) of tile t.  mode 0 = every tile
+ * of the rectangle, 1 = tiles the 3-sigma ellipse reaches (ca, cb, cc are
+ * the conic entries; unused in mode 0).  Returns the number of entries, or
+ * -1 if above cap; with vals == NULL only counts them.
  */
-int64_t or_bin_sort(const float *mx, const float *my, const float *rad, const float *z,
-                    int V, int64_t N, const int32_t *vw, const int32_t *vh, int T,
-                    uint32_t *vals, int64_t cap, uint32_t *ranges) {
+int64_t or_bin_sort(const float *mx, const float *my, const float *rad, const float *z, const float *ca,
+                    const float *cb, const float *cc, int mode, int V, int64_t N, const int32_t *vw,
+                    const int32_t *vh, int T, uint32_t *vals, int64_t cap, uint32_t *ranges) {
   int64_t *toff = (int64_t *)malloc(sizeof(int64_t) * (V + 1));
   int64_t ntiles = or_tiles_total(V, vw, vh, T, toff);
   int64_t n = 0;
@@ -516,8 +572,10 @@ int64_t or_bin_sort(const float *mx, const float *my, const float *rad, const fl
     for (int64_t g = 0; g < N; ++g) {
       int64_t p = (int64_t)v * N + g;
       int t[4];
-      if (bin_rect32(mx[p], my[p], rad[p], vw[v], vh[v], T, t))
-        n += (int64_t)(t[2] - t[0] + 1) * (t[3] - t[1] + 1);
+      if (!bin_rect32(mx[p], my[p], rad[p], vw[v], vh[v], T, t)) continue;
+      for (int ty = t[1]; ty <= t[3]; ++ty)
+        for (int tx = t[0]; tx <= t[2]; ++tx)
+          n += tile_receives(mode, ca, cb, cc, p, mx[p], my[p], tx, ty, vw[v], vh[v], T);
     }
   memset(ranges, 0, sizeof(uint32_t) * 2 * ntiles);
   if (!vals || n > cap) { /* count only, or not enough room */
@@ -534,6 +592,7 @@ int64_t or_bin_sort(const float *mx, const float *my, const float *rad, const fl
       if (!bin_rect32(mx[p], my[p], rad[p], vw[v], vh[v], T, t)) continue;
       for (int ty = t[1]; ty <= t[3]; ++ty)
         for (int tx = t[0]; tx <= t[2]; ++tx) {
+          if (!tile_receives(mode, ca, cb, cc, p, mx[p], my[p], tx, ty, vw[v], vh[v], T)) continue;
           uint64_t tile = (uint64_t)(toff[v] + (int64_t)ty * tx_n + tx);
           e[k].key = (tile << 32) | f32_bits(z[p]);
           e[k].idx = (uint64_t)k;

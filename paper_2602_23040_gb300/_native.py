@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "invalid descriptor", 3: "cap
 DEV_CAPACITY = 1
 DEV_LIVE_MISMATCH = 2
 DEV_TIMEOUT = 4
+BIN_RECT, BIN_ELLIPSE = 0, 1
 
 
 class Level(C.Structure):
@@ -42,7 +43,8 @@ class View(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("tile", C.c_int32), ("znear", C.c_float), ("bg", C.c_float * 3), ("max_dups", C.c_uint64)]
+    _fields_ = [("tile", C.c_int32), ("znear", C.c_float), ("bg", C.c_float * 3), ("max_dups", C.c_uint64),
+                ("bin_mode", C.c_int32)]
 
 
 class Sizes(C.Structure):

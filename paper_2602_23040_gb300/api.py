@@ -70,11 +70,11 @@ class Plan:
 
     def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
                  sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 16,
-                 znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0):
+                 znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse"):
         lib = N.load()
         self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
                           texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
-                          bg=tuple(bg), max_dups=max_dups)
+                          bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode)
         d = N.AtlasDesc()
         d.atlas_w, d.atlas_h = int(atlas_wh[0]), int(atlas_wh[1])
         d.num_levels = len(levels)
@@ -86,6 +86,8 @@ class Plan:
         o = N.Options()
         o.tile, o.znear, o.max_dups = int(tile), float(znear), int(max_dups)
         o.bg[:] = [float(b) for b in bg]
+        o.bin_mode = {"rect": N.BIN_RECT, "ellipse": N.BIN_ELLIPSE}[bin_mode]
+        self.bin_mode = bin_mode
         self._views = _views_array(views)
         h = C.c_void_p()
         N.check("pk_plan_create", lib.pk_plan_create(C.byref(d), self._views, len(views), int(n_live),

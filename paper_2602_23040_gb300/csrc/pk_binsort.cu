@@ -25,8 +25,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kThreads * kScanItems;     // 2048
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kThreads * kSortItems;     // 4096
+constexpr int kSortItems = 12;
+constexpr int kSortTile = kThreads * kSortItems;     // 3072
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -50,6 +50,51 @@ __device__ __forceinline__ bool bin_rect(float mx, float my, float r, int W, int
   tx1 = (int)hix / T;
   ty1 = (int)hiy / T;
   return true;
+}
+
+// Ellipse rule: does q = d^T conic d <= 9 (1 + 2^-12) reach the rectangle
+// [x0, x1] x [y0, y1] of a tile's pixel centres?  Minimum of q over the
+// rectangle: 0 with the mean inside, else on an edge, where the 1-D
+// minimiser is clamped to the edge.  FP32 in exactly this order, no FMA.
+__device__ __forceinline__ bool ellipse_hits_rect(float mx, float my, float a, float b, float c, float x0, float x1,
+                                                  float y0, float y1) {
+  const float qmax = 9.0f * (1.0f + 1.0f / 4096.0f);
+  if (!(a > 0.f) || !(c > 0.f)) return true;
+  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
+  const float ra = __fdiv_rn(1.f, a), rc = __fdiv_rn(1.f, c), b2 = __fadd_rn(b, b);
+  const float lx = __fsub_rn(x0, mx), hx = __fsub_rn(x1, mx), ly = __fsub_rn(y0, my), hy = __fsub_rn(y1, my);
+  float best = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float dx = i ? hx : lx;
+    const float t = __fmul_rn(__fmul_rn(b, dx), rc);
+    const float dy = fminf(fmaxf(-t, ly), hy);
+    float q = __fmul_rn(__fmul_rn(a, dx), dx);
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(b2, dx), dy));
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(c, dy), dy));
+    best = fminf(best, q);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float dy = i ? hy : ly;
+    const float t = __fmul_rn(__fmul_rn(b, dy), ra);
+    const float dx = fminf(fmaxf(-t, lx), hx);
+    float q = __fmul_rn(__fmul_rn(a, dx), dx);
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(b2, dx), dy));
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(c, dy), dy));
+    best = fminf(best, q);
+  }
+  return best <= qmax;
+}
+
+// Does tile (tx, ty) of a W x H view receive the splat (rectangle mode: all
+// tiles of the r-square do)?
+__device__ __forceinline__ bool tile_receives(int mode, float mx, float my, float a, float b, float c, int tx, int ty,
+                                              int W, int H, int T) {
+  if (mode == PK_BIN_RECT) return true;
+  const float x0 = (float)(tx * T) + 0.5f, y0 = (float)(ty * T) + 0.5f;
+  const float x1 = (float)min((tx + 1) * T, W) - 0.5f, y1 = (float)min((ty + 1) * T, H) - 0.5f;
+  return ellipse_hits_rect(mx, my, a, b, c, x0, x1, y0, y1);
 }
 
 // Contiguous chunk [begin, end) of block b when n items are split over nb
@@ -100,7 +145,7 @@ __device__ __forceinline__ T block_excl_scan(T v, T &total, T *s) {
 // ---------------------------------------------------------------------------
 
 __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict__ rec, int64_t pairs, int64_t N,
-                                                         const DevView *__restrict__ views, int T,
+                                                         const DevView *__restrict__ views, int T, int mode,
                                                          uint32_t *__restrict__ cnt) {
   for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < pairs; p += (int64_t)gridDim.x * kThreads) {
     const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec));
@@ -108,8 +153,15 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
     const DevView &v = views[p / N];
     int tx0, ty0, tx1, ty1;
     uint32_t n = 0;
-    if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, tx0, ty0, tx1, ty1))
-      n = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, tx0, ty0, tx1, ty1)) {
+      if (mode == PK_BIN_RECT) {
+        n = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+      } else {
+        for (int ty = ty0; ty <= ty1; ++ty)
+          for (int tx = tx0; tx <= tx1; ++tx)
+            n += tile_receives(mode, a.x, a.y, a.z, a.w, b.x, tx, ty, v.width, v.height, T) ? 1u : 0u;
+      }
+    }
     cnt[p] = n;
   }
 }
@@ -259,17 +311,30 @@ __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__re
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
   chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
-  // chunks start on a multiple of kSortTile: 16-byte aligned vector loads
+  // chunks start on a multiple of kSortTile: 16-byte aligned vector loads,
+  // four of them in flight per thread; the loop bound is block-uniform so
+  // every lane takes part in the matches
   const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + b0);
   const uint64_t n4 = (b1 - b0) / 4;
-  for (uint64_t i = threadIdx.x; i < n4; i += kThreads) {
-    const uint4 q = __ldg(k4 + i);
-    const uint32_t kk[4] = {q.x, q.y, q.z, q.w};
+  const uint32_t lt = lanemask_lt();
+  for (uint64_t t0 = 0; t0 < n4; t0 += 4 * kThreads) {
+    uint4 q[4];
+    bool ok[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t d = (kk[j] >> shift) & mask;
-      const uint32_t peers = __match_any_sync(__activemask(), d);
-      if ((peers & lanemask_lt()) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t i = t0 + (uint64_t)u * kThreads + threadIdx.x;
+      ok[u] = i < n4;
+      q[u] = ok[u] ? __ldg(k4 + i) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t kk[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t d = ok[u] ? (kk[j] >> shift) & mask : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (ok[u] && (peers & lt) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
+      }
     }
   }
   for (uint64_t i = b0 + 4 * n4 + threadIdx.x; i < b1; i += kThreads)
@@ -408,32 +473,43 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
 
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
                                                    const uint32_t *__restrict__ offs, const DevCounters *ctr,
-                                                   const DevView *__restrict__ views, int64_t N, int T,
+                                                   const DevView *__restrict__ views, int64_t N, int T, int mode,
                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
   if (ctr->dups == 0) return;
   const uint64_t n = ctr->n_valid;
   const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
   for (uint64_t w = blockIdx.x * (uint64_t)kWarps + (threadIdx.x >> 5); w * 32 < n; w += nwarps) {
     const uint64_t k = w * 32 + lane;
-    uint32_t cnt = 0, p = 0, tbase = 0, wt = 1, tx_n = 1, off0 = 0;
+    // candidate tiles: the splat's r-square; the receiving ones are compacted
+    uint32_t ncand = 0, p = 0, wt = 1, tx0 = 0, ty0 = 0, tx_n = 1, toff = 0;
+    float mx = 0.f, my = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
+    int W = 1, H = 1;
     if (k < n) {
       p = pval[k];
       const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec));
-      const float rr = __ldg(rec + (uint64_t)p * kRec + 7);
+      const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec) + 1);
       const DevView &v = views[p / N];
-      int tx0, ty0, tx1, ty1;
-      if (bin_rect(a.x, a.y, rr, v.width, v.height, T, tx0, ty0, tx1, ty1)) {
-        wt = (uint32_t)(tx1 - tx0 + 1);
-        cnt = wt * (uint32_t)(ty1 - ty0 + 1);
+      int x0, y0, x1, y1;
+      if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
+        wt = (uint32_t)(x1 - x0 + 1);
+        ncand = wt * (uint32_t)(y1 - y0 + 1);
+        tx0 = (uint32_t)x0;
+        ty0 = (uint32_t)y0;
         tx_n = (uint32_t)v.tiles_x;
-        tbase = (uint32_t)v.tile_off + (uint32_t)ty0 * tx_n + (uint32_t)tx0;
+        toff = (uint32_t)v.tile_off;
+        W = v.width;
+        H = v.height;
+        mx = a.x; my = a.y; ca = a.z; cb = a.w; cc = b.x;
       }
     }
+    uint32_t off0 = 0;
     if (lane == 0) off0 = offs[w * 32];
     off0 = __shfl_sync(0xffffffffu, off0, 0);
-    const uint32_t incl = warp_incl_scan(cnt);
+    const uint32_t incl = warp_incl_scan(ncand);
     const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t written = 0;
     for (uint32_t e0 = 0; e0 < E; e0 += 32) {
       const uint32_t e = e0 + lane;
       const uint32_t ee = e < E ? e : E - 1;
@@ -445,17 +521,30 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
         if (c <= ee) pos += s;
       }
       const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, pos);
-      const uint32_t o_cnt = __shfl_sync(0xffffffffu, cnt, pos);
+      const uint32_t o_cnt = __shfl_sync(0xffffffffu, ncand, pos);
       const uint32_t o_p = __shfl_sync(0xffffffffu, p, pos);
-      const uint32_t o_tb = __shfl_sync(0xffffffffu, tbase, pos);
       const uint32_t o_wt = __shfl_sync(0xffffffffu, wt, pos);
+      const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, pos);
+      const uint32_t o_ty0 = __shfl_sync(0xffffffffu, ty0, pos);
       const uint32_t o_txn = __shfl_sync(0xffffffffu, tx_n, pos);
-      if (e < E) {
-        const uint32_t local = ee - (o_incl - o_cnt);
-        const uint32_t ty = local / o_wt, tx = local - ty * o_wt;
-        keys[off0 + e] = o_tb + ty * o_txn + tx;
-        vals[off0 + e] = o_p;
+      const uint32_t o_toff = __shfl_sync(0xffffffffu, toff, pos);
+      const uint32_t local = ee - (o_incl - o_cnt);
+      const uint32_t ty = o_ty0 + local / o_wt, tx = o_tx0 + local % o_wt;
+      bool take = e < E;
+      if (mode != PK_BIN_RECT) {
+        const float o_mx = __shfl_sync(0xffffffffu, mx, pos), o_my = __shfl_sync(0xffffffffu, my, pos);
+        const float o_ca = __shfl_sync(0xffffffffu, ca, pos), o_cb = __shfl_sync(0xffffffffu, cb, pos);
+        const float o_cc = __shfl_sync(0xffffffffu, cc, pos);
+        const int o_W = __shfl_sync(0xffffffffu, W, pos), o_H = __shfl_sync(0xffffffffu, H, pos);
+        take = take && tile_receives(mode, o_mx, o_my, o_ca, o_cb, o_cc, (int)tx, (int)ty, o_W, o_H, T);
       }
+      const uint32_t bal = __ballot_sync(0xffffffffu, take);
+      if (take) {
+        const uint32_t at = off0 + written + __popc(bal & lt);
+        keys[at] = o_toff + ty * o_txn + tx;
+        vals[at] = o_p;
+      }
+      written += __popc(bal);
     }
   }
 }
@@ -522,7 +611,7 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // sort blocks: 3 resident per SM, within the histogram's capacity
+  // sort blocks: 3 resident per SM (79 registers x 256 threads), within the histogram's capacity
   const int nsort = std::max(1, std::min(kSortBlocks, 3 * sms));
 
   if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
@@ -532,7 +621,7 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
     return PK_OK;
   }
   int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
-  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, cnt);
+  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt);
   // compaction of the pairs that touch a tile, keyed by depth bits
   k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, p->max_dups, ctr, status);
@@ -555,7 +644,8 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
   const int npass = (p->tile_bits + 7) / 8;
   uint32_t *vbuf[2] = {(npass & 1) ? dv : sorted_vals, (npass & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
-  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, ctr, views, p->N, p->T, kbuf[0], vbuf[0]);
+  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, ctr, views, p->N, p->T, p->opts.bin_mode,
+                                                      kbuf[0], vbuf[0]);
   const uint32_t *n_dups = &ctr->dups;
   for (int pass = 0; pass < npass; ++pass) {
     const int bits = std::min(8, p->tile_bits - 8 * pass);

@@ -122,7 +122,9 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   o.znear = 0.01f;
   o.bg[0] = o.bg[1] = o.bg[2] = 0.0f;
   o.max_dups = 0;
+  o.bin_mode = PK_BIN_ELLIPSE;
   if (opts) o = *opts;
+  if (o.bin_mode != PK_BIN_RECT && o.bin_mode != PK_BIN_ELLIPSE) return PK_ERR_ARG;
   if (o.tile != 16) return PK_ERR_UNSUPPORTED;
   if (!(o.znear > 0.0f) || !isfinite(o.znear)) return PK_ERR_ARG;
   for (int c = 0; c < 3; ++c)

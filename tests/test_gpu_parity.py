@@ -26,9 +26,9 @@ def _pk():
     return pk
 
 
-def run_gpu(scene, dimg=None):
+def run_gpu(scene, dimg=None, **plan_kw):
     pk = _pk()
-    plan = pk.Plan.for_scene(scene)
+    plan = pk.Plan.for_scene(scene, **plan_kw)
     r = pk.Renderer(plan)
     atlas, occ, dyn = H.upload(scene)
     st = r.ensure_capacity(atlas, occ, dyn)
@@ -124,10 +124,10 @@ def _synthetic_records(views, N, seed):
     return rec
 
 
-def _records_plan(views, N):
+def _records_plan(views, N, bin_mode="ellipse"):
     pk = _pk()
     side = int(math.ceil(math.sqrt(N)))
-    return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N)
+    return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, bin_mode=bin_mode)
 
 
 def _records_setup(seed, N=700):
@@ -137,12 +137,12 @@ def _records_setup(seed, N=700):
     return views, rec
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_bin_and_sort_bit_exact(orc, seed):
+@pytest.mark.parametrize("seed,mode", [(1, "ellipse"), (2, "ellipse"), (3, "rect"), (4, "rect")])
+def test_bin_and_sort_bit_exact(orc, seed, mode):
     pk = _pk()
     views, rec = _records_setup(seed)
     V, N = rec.shape[:2]
-    plan = _records_plan(views, N)
+    plan = _records_plan(views, N, mode)
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
@@ -152,7 +152,8 @@ def test_bin_and_sort_bit_exact(orc, seed):
     st = pk.read_status(plan, ws)
     va = orc.views_array(views)
     r = rec.reshape(V * N, 12)
-    ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, 16)
+    ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, 16, r[:, 2], r[:, 3], r[:, 4],
+                                          mode={"ellipse": orc.BIN_ELLIPSE, "rect": orc.BIN_RECT}[mode])
     assert st["dups"] == len(ref_vals) and st["flags"] == 0
     assert np.array_equal(H.u32(vals[:len(ref_vals)]), ref_vals)
     assert np.array_equal(H.u32(ranges).reshape(-1, 2), ref_ranges)
@@ -262,6 +263,16 @@ def test_end_to_end(orc, which):
     live = np.zeros(Hh * W, bool)
     live[o["texel"]] = True
     assert np.all(grad.view(F, D, Hh * W).cpu().numpy()[:, :, ~live] == 0)
+
+
+def test_rect_and_ellipse_binning_give_the_same_images(orc):
+    sc = H.scene_small_sh3(seed=404)
+    w = np.random.default_rng(15).standard_normal(3 * sc.pixels).astype(np.float32)
+    _, r1, g1 = run_gpu(sc, dimg=w, bin_mode="ellipse")
+    _, r0, g0 = run_gpu(sc, dimg=w, bin_mode="rect")
+    assert r1.status()["dups"] < r0.status()["dups"]
+    assert torch.equal(r1.image, r0.image) and torch.equal(r1.T, r0.T)
+    assert H.rel_err(g1.cpu().numpy().astype(np.float64), g0.cpu().numpy().astype(np.float64)) < 1e-5
 
 
 def test_config2_full_size(orc):

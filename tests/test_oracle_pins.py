@@ -356,9 +356,10 @@ def test_tiled_render_equals_bruteforce_and_tile_size(orc):
     assert np.array_equal(got, rgb)
     assert np.array_equal(f16["T"], T)
     for t in (8, 32, 1):
-        ft = orc.forward(sc, tile=t)
-        assert np.array_equal(ft["img"], f16["img"]), t
-        assert np.array_equal(ft["T"], f16["T"]), t
+        for mode in (orc.BIN_ELLIPSE, orc.BIN_RECT):
+            ft = orc.forward(sc, tile=t, mode=mode)
+            assert np.array_equal(ft["img"], f16["img"]), (t, mode)
+            assert np.array_equal(ft["T"], f16["T"]), (t, mode)
     assert (f16["T"] >= 1e-4).all() and (f16["T"] <= 1).all()
     assert f16["img"].min() >= 0
 
@@ -434,7 +435,7 @@ def test_bin_sort_bruteforce_membership_and_order(orc):
     rad = rng.integers(0, 12, V * N).astype(np.float32)
     z = rng.uniform(0.5, 5, V * N).astype(np.float32)
     z[::17] = z[3]                     # exact depth ties across splats
-    vals, ranges = orc.bin_sort32(mx, my, rad, z, va, N, T)
+    vals, ranges = orc.bin_sort32(mx, my, rad, z, va, N, T, mode=orc.BIN_RECT)
     ntiles, toff = orc.tiles_total(va, T)
     for v, vw in enumerate(views):
         tx_n, ty_n = -(-vw.width // T), -(-vw.height // T)
@@ -456,6 +457,52 @@ def test_bin_sort_bruteforce_membership_and_order(orc):
                 expect.sort(key=lambda p: (int(z[p].view(np.uint32)), p))
                 assert got == expect, (v, tx, ty)
     assert ranges[:, 1].max() == len(vals)
+
+
+def test_bin_sort_ellipse_rule_against_bounded_minimisation(orc):
+    """Ellipse binning: a tile receives a splat iff min over the tile's pixel-centre rectangle of
+    q = d^T conic d is <= 9 (1 + 2^-12).  The minimum is recomputed here with scipy's bounded
+    L-BFGS-B; decisions must agree except inside a 1e-4 band around the cut."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(10)
+    views = [synth.scenes.pinhole((0, 0, -3), 70, 45)]
+    va = orc.views_array(views)
+    N, T = 120, 16
+    mx = rng.uniform(-10, 80, N).astype(np.float32)
+    my = rng.uniform(-10, 55, N).astype(np.float32)
+    L = rng.normal(0, 1, (N, 2, 2)) * np.exp(rng.normal(1.0, 0.7, (N, 1, 1)))
+    S = L @ L.transpose(0, 2, 1) + 0.3 * np.eye(2)
+    Q = np.linalg.inv(S).astype(np.float32)
+    ca, cb, cc = Q[:, 0, 0], Q[:, 0, 1], Q[:, 1, 1]
+    lam = np.linalg.eigvalsh(S)[:, 1]
+    rad = np.ceil(3 * np.sqrt(lam)).astype(np.float32)
+    z = rng.uniform(0.5, 5, N).astype(np.float32)
+    vals, ranges = orc.bin_sort32(mx, my, rad, z, va, N, T, ca, cb, cc, mode=orc.BIN_ELLIPSE)
+    rvals, rranges = orc.bin_sort32(mx, my, rad, z, va, N, T, mode=orc.BIN_RECT)
+    assert len(vals) < len(rvals)
+    W, H = views[0].width, views[0].height
+    qcut = 9.0 * (1 + 2.0 ** -12)
+    checked = 0
+    for t in range(len(ranges)):
+        ty, tx = divmod(t, -(-W // T))
+        x0, x1 = tx * T + 0.5, min(W, tx * T + T) - 0.5
+        y0, y1 = ty * T + 0.5, min(H, ty * T + T) - 0.5
+        got = set(vals[ranges[t, 0]:ranges[t, 1]].tolist())
+        cand = set(rvals[rranges[t, 0]:rranges[t, 1]].tolist())
+        assert got <= cand
+        for p in cand:
+            A = np.array([[ca[p], cb[p]], [cb[p], cc[p]]], np.float64)
+            m = np.array([mx[p], my[p]], np.float64)
+            f = lambda x: float((x - m) @ A @ (x - m))
+            x_init = np.clip(m, [x0, y0], [x1, y1])
+            res = minimize(f, x_init, jac=lambda x: 2 * A @ (x - m), method="L-BFGS-B",
+                           bounds=[(x0, x1), (y0, y1)], options=dict(ftol=1e-15, gtol=1e-12))
+            qmin = min(res.fun, f(x_init))
+            if abs(qmin - qcut) < 1e-4 * qcut:
+                continue
+            assert (p in got) == (qmin <= qcut), (t, p, qmin)
+            checked += 1
+    assert checked > 200
 
 
 # ---------------------------------------------------------------------------
