@@ -52,49 +52,82 @@ __device__ __forceinline__ bool bin_rect(float mx, float my, float r, int W, int
   return true;
 }
 
+// A splat's footprint for the ellipse rule, with the per-splat reciprocals
+// hoisted (the same values a per-tile evaluation would produce).
+struct Foot {
+  float mx, my, a, b, c, ra, rc, b2;
+};
+
+__device__ __forceinline__ Foot make_foot(float mx, float my, float a, float b, float c) {
+  Foot f;
+  f.mx = mx;
+  f.my = my;
+  f.a = a;
+  f.b = b;
+  f.c = c;
+  f.ra = __fdiv_rn(1.f, a);
+  f.rc = __fdiv_rn(1.f, c);
+  f.b2 = __fadd_rn(b, b);
+  return f;
+}
+
 // Ellipse rule: does q = d^T conic d <= 9 (1 + 2^-12) reach the rectangle
 // [x0, x1] x [y0, y1] of a tile's pixel centres?  Minimum of q over the
 // rectangle: 0 with the mean inside, else on an edge, where the 1-D
 // minimiser is clamped to the edge.  FP32 in exactly this order, no FMA.
-__device__ __forceinline__ bool ellipse_hits_rect(float mx, float my, float a, float b, float c, float x0, float x1,
-                                                  float y0, float y1) {
+__device__ __forceinline__ bool ellipse_hits_rect(const Foot &f, float x0, float x1, float y0, float y1) {
   const float qmax = 9.0f * (1.0f + 1.0f / 4096.0f);
-  if (!(a > 0.f) || !(c > 0.f)) return true;
-  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
-  const float ra = __fdiv_rn(1.f, a), rc = __fdiv_rn(1.f, c), b2 = __fadd_rn(b, b);
-  const float lx = __fsub_rn(x0, mx), hx = __fsub_rn(x1, mx), ly = __fsub_rn(y0, my), hy = __fsub_rn(y1, my);
+  if (!(f.a > 0.f) || !(f.c > 0.f)) return true;
+  if (f.mx >= x0 && f.mx <= x1 && f.my >= y0 && f.my <= y1) return true;
+  const float lx = __fsub_rn(x0, f.mx), hx = __fsub_rn(x1, f.mx), ly = __fsub_rn(y0, f.my), hy = __fsub_rn(y1, f.my);
   float best = INFINITY;
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const float dx = i ? hx : lx;
-    const float t = __fmul_rn(__fmul_rn(b, dx), rc);
+    const float t = __fmul_rn(__fmul_rn(f.b, dx), f.rc);
     const float dy = fminf(fmaxf(-t, ly), hy);
-    float q = __fmul_rn(__fmul_rn(a, dx), dx);
-    q = __fadd_rn(q, __fmul_rn(__fmul_rn(b2, dx), dy));
-    q = __fadd_rn(q, __fmul_rn(__fmul_rn(c, dy), dy));
+    float q = __fmul_rn(__fmul_rn(f.a, dx), dx);
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(f.b2, dx), dy));
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(f.c, dy), dy));
     best = fminf(best, q);
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const float dy = i ? hy : ly;
-    const float t = __fmul_rn(__fmul_rn(b, dy), ra);
+    const float t = __fmul_rn(__fmul_rn(f.b, dy), f.ra);
     const float dx = fminf(fmaxf(-t, lx), hx);
-    float q = __fmul_rn(__fmul_rn(a, dx), dx);
-    q = __fadd_rn(q, __fmul_rn(__fmul_rn(b2, dx), dy));
-    q = __fadd_rn(q, __fmul_rn(__fmul_rn(c, dy), dy));
+    float q = __fmul_rn(__fmul_rn(f.a, dx), dx);
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(f.b2, dx), dy));
+    q = __fadd_rn(q, __fmul_rn(__fmul_rn(f.c, dy), dy));
     best = fminf(best, q);
   }
   return best <= qmax;
 }
 
-// Does tile (tx, ty) of a W x H view receive the splat (rectangle mode: all
-// tiles of the r-square do)?
-__device__ __forceinline__ bool tile_receives(int mode, float mx, float my, float a, float b, float c, int tx, int ty,
-                                              int W, int H, int T) {
-  if (mode == PK_BIN_RECT) return true;
+__device__ __forceinline__ bool tile_hit(const Foot &f, int tx, int ty, int W, int H, int T) {
   const float x0 = (float)(tx * T) + 0.5f, y0 = (float)(ty * T) + 0.5f;
   const float x1 = (float)min((tx + 1) * T, W) - 0.5f, y1 = (float)min((ty + 1) * T, H) - 0.5f;
-  return ellipse_hits_rect(mx, my, a, b, c, x0, x1, y0, y1);
+  return ellipse_hits_rect(f, x0, x1, y0, y1);
+}
+
+// Per-warp staging of 32 splats' candidate rectangles for the cooperative
+// walk over their candidate tiles (one candidate per lane per step).
+struct WarpSplat {
+  float4 g0;   // mx, my, a, b
+  float4 g1;   // c, ra, rc, b2
+  int4 r0;     // tx0, ty0, wt, W
+  int4 r1;     // H, tile base (tile_off + ty0 * tiles_x + tx0), tiles_x, ncand
+};
+
+// Owner of candidate e: number of lanes whose inclusive count is <= e.
+__device__ __forceinline__ int candidate_owner(uint32_t incl, uint32_t e) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s > 0; s >>= 1) {
+    const uint32_t c = __shfl_sync(0xffffffffu, incl, pos + s - 1);
+    if (c <= e) pos += s;
+  }
+  return pos;
 }
 
 // Contiguous chunk [begin, end) of block b when n items are split over nb
@@ -144,25 +177,82 @@ __device__ __forceinline__ T block_excl_scan(T v, T &total, T *s) {
 // Per-pair tile counts
 // ---------------------------------------------------------------------------
 
+// Receiving tiles per pair.  Rectangle mode: the size of the r-square.
+// Ellipse mode: a warp walks the candidate tiles of its 32 pairs together,
+// one candidate per lane, so long and short pairs share the work; each pair
+// also keeps a bit mask of its receiving candidates when it has <= 32 of
+// them, so the emission need not test them again.
 __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict__ rec, int64_t pairs, int64_t N,
                                                          const DevView *__restrict__ views, int T, int mode,
-                                                         uint32_t *__restrict__ cnt) {
-  for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < pairs; p += (int64_t)gridDim.x * kThreads) {
-    const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec));
-    const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec) + 1);
-    const DevView &v = views[p / N];
-    int tx0, ty0, tx1, ty1;
-    uint32_t n = 0;
-    if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, tx0, ty0, tx1, ty1)) {
-      if (mode == PK_BIN_RECT) {
-        n = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-      } else {
-        for (int ty = ty0; ty <= ty1; ++ty)
-          for (int tx = tx0; tx <= tx1; ++tx)
-            n += tile_receives(mode, a.x, a.y, a.z, a.w, b.x, tx, ty, v.width, v.height, T) ? 1u : 0u;
+                                                         uint32_t *__restrict__ cnt, uint32_t *__restrict__ rmask) {
+  __shared__ WarpSplat s_ws[kWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = lanemask_lt();
+  const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
+  for (uint64_t w = blockIdx.x * (uint64_t)kWarps + warp; w * 32 < (uint64_t)pairs; w += nwarps) {
+    const uint64_t p = w * 32 + lane;
+    uint32_t ncand = 0;
+    WarpSplat ws;
+    ws.g0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    ws.g1 = ws.g0;
+    ws.r0 = make_int4(0, 0, 1, 1);
+    ws.r1 = make_int4(1, 0, 1, 0);
+    if (p < (uint64_t)pairs) {
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec));
+      const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec) + 1);
+      const DevView &v = views[p / N];
+      int x0, y0, x1, y1;
+      if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
+        const int wt = x1 - x0 + 1;
+        ncand = (uint32_t)(wt * (y1 - y0 + 1));
+        const Foot f = make_foot(a.x, a.y, a.z, a.w, b.x);
+        ws.g0 = make_float4(f.mx, f.my, f.a, f.b);
+        ws.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
+        ws.r0 = make_int4(x0, y0, wt, v.width);
+        ws.r1 = make_int4(v.height, 0, 0, (int)ncand);
       }
     }
-    cnt[p] = n;
+    if (mode == PK_BIN_RECT) {
+      if (p < (uint64_t)pairs) cnt[p] = ncand;
+      continue;
+    }
+    s_ws[warp][lane] = ws;
+    __syncwarp();
+    const uint32_t incl = warp_incl_scan(ncand);
+    const uint32_t excl = incl - ncand;
+    const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t mine = 0, mask = 0;
+    for (uint32_t e0 = 0; e0 < E; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const uint32_t ee = e < E ? e : E - 1;
+      const int o = candidate_owner(incl, ee);
+      const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
+      const WarpSplat &os = s_ws[warp][o];
+      const int4 r0 = os.r0;
+      const uint32_t local = ee - o_excl;
+      const int ty = r0.y + (int)(local / (uint32_t)r0.z), tx = r0.x + (int)(local % (uint32_t)r0.z);
+      bool hit = false;
+      if (e < E) {
+        const float4 g0 = os.g0, g1 = os.g1;
+        const Foot f{g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        hit = tile_hit(f, tx, ty, r0.w, os.r1.x, T);
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      // this lane's own pair: its candidates in [excl, incl) meet this step's [e0, e0 + 32)
+      const uint32_t lo = max(excl, e0), hi = min(incl, e0 + 32);
+      if (lo < hi) {
+        const uint32_t span = hi - lo;
+        const uint32_t bits = (bal >> (lo - e0)) & (span >= 32 ? 0xffffffffu : ((1u << span) - 1u));
+        mine += __popc(bits);
+        if (ncand <= 32) mask |= bits << (lo - excl);
+      }
+    }
+    (void)lt;
+    if (p < (uint64_t)pairs) {
+      cnt[p] = mine;
+      rmask[p] = mask;
+    }
+    __syncwarp();
   }
 }
 
@@ -305,42 +395,43 @@ __global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const 
 __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                             const uint32_t *n_dev, uint64_t n_host, int shift,
                                                             uint32_t mask, uint32_t *__restrict__ hist) {
-  __shared__ uint32_t s_cnt[kRadix];
-  for (int d = threadIdx.x; d < kRadix; d += kThreads) s_cnt[d] = 0;
+  __shared__ uint32_t s_cnt[kWarps][kRadix];   // warp-private digit counts
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&s_cnt[0][0])[i] = 0;
   __syncthreads();
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
   chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
   // chunks start on a multiple of kSortTile: 16-byte aligned vector loads,
-  // four of them in flight per thread; the loop bound is block-uniform so
-  // every lane takes part in the matches
+  // four in flight per thread
   const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + b0);
   const uint64_t n4 = (b1 - b0) / 4;
-  const uint32_t lt = lanemask_lt();
+  uint32_t *cw = s_cnt[warp];
   for (uint64_t t0 = 0; t0 < n4; t0 += 4 * kThreads) {
     uint4 q[4];
-    bool ok[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const uint64_t i = t0 + (uint64_t)u * kThreads + threadIdx.x;
-      ok[u] = i < n4;
-      q[u] = ok[u] ? __ldg(k4 + i) : make_uint4(0, 0, 0, 0);
+      q[u] = i < n4 ? __ldg(k4 + i) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t kk[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t d = ok[u] ? (kk[j] >> shift) & mask : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        if (ok[u] && (peers & lt) == 0) atomicAdd(&s_cnt[d], (uint32_t)__popc(peers));
-      }
+      if (t0 + (uint64_t)u * kThreads + threadIdx.x >= n4) break;
+      atomicAdd(&cw[(q[u].x >> shift) & mask], 1u);
+      atomicAdd(&cw[(q[u].y >> shift) & mask], 1u);
+      atomicAdd(&cw[(q[u].z >> shift) & mask], 1u);
+      atomicAdd(&cw[(q[u].w >> shift) & mask], 1u);
     }
   }
   for (uint64_t i = b0 + 4 * n4 + threadIdx.x; i < b1; i += kThreads)
-    atomicAdd(&s_cnt[(__ldg(keys + i) >> shift) & mask], 1u);
+    atomicAdd(&cw[(__ldg(keys + i) >> shift) & mask], 1u);
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kThreads) hist[(size_t)d * gridDim.x + blockIdx.x] = s_cnt[d];
+  for (int d = threadIdx.x; d < kRadix; d += kThreads) {
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += s_cnt[w][d];
+    hist[(size_t)d * gridDim.x + blockIdx.x] = t;
+  }
 }
 
 // Exclusive scan of hist in [digit][block] order (one block of 1024 threads,
@@ -472,20 +563,24 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
 // ---------------------------------------------------------------------------
 
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
-                                                   const uint32_t *__restrict__ offs, const DevCounters *ctr,
-                                                   const DevView *__restrict__ views, int64_t N, int T, int mode,
-                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                                                   const uint32_t *__restrict__ offs, const uint32_t *__restrict__ rmask,
+                                                   const DevCounters *ctr, const DevView *__restrict__ views,
+                                                   int64_t N, int T, int mode, uint32_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ vals) {
+  __shared__ WarpSplat s_ws[kWarps][32];
   if (ctr->dups == 0) return;
   const uint64_t n = ctr->n_valid;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
-  for (uint64_t w = blockIdx.x * (uint64_t)kWarps + (threadIdx.x >> 5); w * 32 < n; w += nwarps) {
+  for (uint64_t w = blockIdx.x * (uint64_t)kWarps + warp; w * 32 < n; w += nwarps) {
     const uint64_t k = w * 32 + lane;
-    // candidate tiles: the splat's r-square; the receiving ones are compacted
-    uint32_t ncand = 0, p = 0, wt = 1, tx0 = 0, ty0 = 0, tx_n = 1, toff = 0;
-    float mx = 0.f, my = 0.f, ca = 0.f, cb = 0.f, cc = 0.f;
-    int W = 1, H = 1;
+    uint32_t ncand = 0, p = 0, msk = 0;
+    WarpSplat ws;
+    ws.g0 = make_float4(0.f, 0.f, 0.f, 0.f);
+    ws.g1 = ws.g0;
+    ws.r0 = make_int4(0, 0, 1, 1);
+    ws.r1 = make_int4(1, 0, 1, 0);
     if (k < n) {
       p = pval[k];
       const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec));
@@ -493,59 +588,56 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const DevView &v = views[p / N];
       int x0, y0, x1, y1;
       if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
-        wt = (uint32_t)(x1 - x0 + 1);
-        ncand = wt * (uint32_t)(y1 - y0 + 1);
-        tx0 = (uint32_t)x0;
-        ty0 = (uint32_t)y0;
-        tx_n = (uint32_t)v.tiles_x;
-        toff = (uint32_t)v.tile_off;
-        W = v.width;
-        H = v.height;
-        mx = a.x; my = a.y; ca = a.z; cb = a.w; cc = b.x;
+        const int wt = x1 - x0 + 1;
+        ncand = (uint32_t)(wt * (y1 - y0 + 1));
+        const Foot f = make_foot(a.x, a.y, a.z, a.w, b.x);
+        ws.g0 = make_float4(f.mx, f.my, f.a, f.b);
+        ws.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
+        ws.r0 = make_int4(x0, y0, wt, v.width);
+        ws.r1 = make_int4(v.height, (int)((uint32_t)v.tile_off + (uint32_t)y0 * v.tiles_x + (uint32_t)x0),
+                          v.tiles_x, (int)ncand);
+        if (mode != PK_BIN_RECT && ncand <= 32) msk = rmask[p];
       }
     }
+    s_ws[warp][lane] = ws;
+    __syncwarp();
     uint32_t off0 = 0;
     if (lane == 0) off0 = offs[w * 32];
     off0 = __shfl_sync(0xffffffffu, off0, 0);
     const uint32_t incl = warp_incl_scan(ncand);
+    const uint32_t excl = incl - ncand;
     const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
     uint32_t written = 0;
     for (uint32_t e0 = 0; e0 < E; e0 += 32) {
       const uint32_t e = e0 + lane;
       const uint32_t ee = e < E ? e : E - 1;
-      // owner = number of lanes whose inclusive count is <= ee
-      int pos = 0;
-#pragma unroll
-      for (int s = 16; s > 0; s >>= 1) {
-        const uint32_t c = __shfl_sync(0xffffffffu, incl, pos + s - 1);
-        if (c <= ee) pos += s;
-      }
-      const uint32_t o_incl = __shfl_sync(0xffffffffu, incl, pos);
-      const uint32_t o_cnt = __shfl_sync(0xffffffffu, ncand, pos);
-      const uint32_t o_p = __shfl_sync(0xffffffffu, p, pos);
-      const uint32_t o_wt = __shfl_sync(0xffffffffu, wt, pos);
-      const uint32_t o_tx0 = __shfl_sync(0xffffffffu, tx0, pos);
-      const uint32_t o_ty0 = __shfl_sync(0xffffffffu, ty0, pos);
-      const uint32_t o_txn = __shfl_sync(0xffffffffu, tx_n, pos);
-      const uint32_t o_toff = __shfl_sync(0xffffffffu, toff, pos);
-      const uint32_t local = ee - (o_incl - o_cnt);
-      const uint32_t ty = o_ty0 + local / o_wt, tx = o_tx0 + local % o_wt;
+      const int o = candidate_owner(incl, ee);
+      const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
+      const uint32_t o_p = __shfl_sync(0xffffffffu, p, o);
+      const uint32_t o_msk = __shfl_sync(0xffffffffu, msk, o);
+      const WarpSplat &os = s_ws[warp][o];
+      const int4 r0 = os.r0, r1 = os.r1;
+      const uint32_t local = ee - o_excl;
+      const uint32_t ly = local / (uint32_t)r0.z, lx = local % (uint32_t)r0.z;
       bool take = e < E;
-      if (mode != PK_BIN_RECT) {
-        const float o_mx = __shfl_sync(0xffffffffu, mx, pos), o_my = __shfl_sync(0xffffffffu, my, pos);
-        const float o_ca = __shfl_sync(0xffffffffu, ca, pos), o_cb = __shfl_sync(0xffffffffu, cb, pos);
-        const float o_cc = __shfl_sync(0xffffffffu, cc, pos);
-        const int o_W = __shfl_sync(0xffffffffu, W, pos), o_H = __shfl_sync(0xffffffffu, H, pos);
-        take = take && tile_receives(mode, o_mx, o_my, o_ca, o_cb, o_cc, (int)tx, (int)ty, o_W, o_H, T);
+      if (take && mode != PK_BIN_RECT) {
+        if (r1.w <= 32) {
+          take = (o_msk >> local) & 1u;
+        } else {
+          const float4 g0 = os.g0, g1 = os.g1;
+          const Foot f{g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+          take = tile_hit(f, r0.x + (int)lx, r0.y + (int)ly, r0.w, r1.x, T);
+        }
       }
       const uint32_t bal = __ballot_sync(0xffffffffu, take);
       if (take) {
         const uint32_t at = off0 + written + __popc(bal & lt);
-        keys[at] = o_toff + ty * o_txn + tx;
+        keys[at] = (uint32_t)r1.y + ly * (uint32_t)r1.z + lx;
         vals[at] = o_p;
       }
       written += __popc(bal);
     }
+    __syncwarp();
   }
 }
 
@@ -621,7 +713,8 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
     return PK_OK;
   }
   int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
-  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt);
+  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt,
+                                              at<uint32_t>(ws, L.rmask));
   // compaction of the pairs that touch a tile, keyed by depth bits
   k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, p->max_dups, ctr, status);
@@ -644,8 +737,8 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
   const int npass = (p->tile_bits + 7) / 8;
   uint32_t *vbuf[2] = {(npass & 1) ? dv : sorted_vals, (npass & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
-  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, ctr, views, p->N, p->T, p->opts.bin_mode,
-                                                      kbuf[0], vbuf[0]);
+  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, at<uint32_t>(ws, L.rmask), ctr, views, p->N,
+                                                      p->T, p->opts.bin_mode, kbuf[0], vbuf[0]);
   const uint32_t *n_dups = &ctr->dups;
   for (int pass = 0; pass < npass; ++pass) {
     const int bits = std::min(8, p->tile_bits - 8 * pass);

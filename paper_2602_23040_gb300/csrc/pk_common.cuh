@@ -55,7 +55,7 @@ struct DevCounters {
 // Byte offsets of every region inside the workspace.
 struct WsLayout {
   size_t status, counters, views, toff, fview_off, fview_idx, woff;
-  size_t pair_cnt, zkey0, zkey1, pval0, pval1, offs;
+  size_t pair_cnt, zkey0, zkey1, pval0, pval1, offs, rmask;
   size_t blocksums, hist;
   size_t dkey0, dkey1, dval;
   size_t total;
