@@ -479,21 +479,24 @@ static int bin_rect32(float mx, float my, float r, int W, int H, int T, int *t) 
  * Ellipse binning rule: does the footprint q = d^T conic d <= 9 (times
  * 1 + 2^-12, so FP32 per-pixel tests can never accept a pixel outside it)
  * reach the rectangle [x0, x1] x [y0, y1] of a tile's pixel centres?  The
- * minimum of q over the rectangle is 0 if the mean is inside, else it lies
- * on an edge: on x = const the minimiser is dy = -(b dx)/c clamped to the
- * edge, likewise on y = const.  FP32, in exactly this order, no FMA.
+ * minimum of the convex q over the rectangle is 0 if the mean is inside;
+ * else it lies on an edge that faces the mean (x = x0 if m_x < x0, x = x1
+ * if m_x > x1, likewise in y): a segment from any point of the rectangle
+ * towards the mean lowers q and leaves the rectangle through such an edge.
+ * On x = const the minimiser is dy = -(b dx)/c clamped to the edge,
+ * likewise on y = const.  FP32, in exactly this order, no FMA.
  */
 static int ellipse_hits_rect32(float mx, float my, float a, float b, float c, float x0, float x1, float y0,
                                float y1) {
   const float qmax = 9.0f * (1.0f + 1.0f / 4096.0f);
   if (!(a > 0.0f) || !(c > 0.0f)) return 1;
-  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return 1;
+  const int inx = mx >= x0 && mx <= x1, iny = my >= y0 && my <= y1;
+  if (inx && iny) return 1;
   const float ra = 1.0f / a, rc = 1.0f / c, b2 = b + b;
   const float lx = x0 - mx, hx = x1 - mx, ly = y0 - my, hy = y1 - my;
   float best = INFINITY;
-  const float ex[2] = {lx, hx}, ey[2] = {ly, hy};
-  for (int i = 0; i < 2; ++i) {
-    float dx = ex[i];
+  if (!inx) {
+    float dx = mx < x0 ? lx : hx;
     float t = b * dx;
     t = t * rc;
     float dy = fminf(fmaxf(-t, ly), hy);
@@ -502,8 +505,8 @@ static int ellipse_hits_rect32(float mx, float my, float a, float b, float c, fl
     q = q + (c * dy) * dy;
     best = fminf(best, q);
   }
-  for (int i = 0; i < 2; ++i) {
-    float dy = ey[i];
+  if (!iny) {
+    float dy = my < y0 ? ly : hy;
     float t = b * dy;
     t = t * ra;
     float dx = fminf(fmaxf(-t, lx), hx);

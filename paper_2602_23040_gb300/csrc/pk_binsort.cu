@@ -72,18 +72,19 @@ __device__ __forceinline__ Foot make_foot(float mx, float my, float a, float b, 
 }
 
 // Ellipse rule: does q = d^T conic d <= 9 (1 + 2^-12) reach the rectangle
-// [x0, x1] x [y0, y1] of a tile's pixel centres?  Minimum of q over the
-// rectangle: 0 with the mean inside, else on an edge, where the 1-D
-// minimiser is clamped to the edge.  FP32 in exactly this order, no FMA.
+// [x0, x1] x [y0, y1] of a tile's pixel centres?  Minimum of the convex q
+// over the rectangle: 0 with the mean inside, else on an edge facing the
+// mean, where the 1-D minimiser is clamped to the edge.  FP32 in exactly
+// this order, no FMA.
 __device__ __forceinline__ bool ellipse_hits_rect(const Foot &f, float x0, float x1, float y0, float y1) {
   const float qmax = 9.0f * (1.0f + 1.0f / 4096.0f);
   if (!(f.a > 0.f) || !(f.c > 0.f)) return true;
-  if (f.mx >= x0 && f.mx <= x1 && f.my >= y0 && f.my <= y1) return true;
+  const bool inx = f.mx >= x0 && f.mx <= x1, iny = f.my >= y0 && f.my <= y1;
+  if (inx && iny) return true;
   const float lx = __fsub_rn(x0, f.mx), hx = __fsub_rn(x1, f.mx), ly = __fsub_rn(y0, f.my), hy = __fsub_rn(y1, f.my);
   float best = INFINITY;
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float dx = i ? hx : lx;
+  if (!inx) {
+    const float dx = f.mx < x0 ? lx : hx;
     const float t = __fmul_rn(__fmul_rn(f.b, dx), f.rc);
     const float dy = fminf(fmaxf(-t, ly), hy);
     float q = __fmul_rn(__fmul_rn(f.a, dx), dx);
@@ -91,9 +92,8 @@ __device__ __forceinline__ bool ellipse_hits_rect(const Foot &f, float x0, float
     q = __fadd_rn(q, __fmul_rn(__fmul_rn(f.c, dy), dy));
     best = fminf(best, q);
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float dy = i ? hy : ly;
+  if (!iny) {
+    const float dy = f.my < y0 ? ly : hy;
     const float t = __fmul_rn(__fmul_rn(f.b, dy), f.ra);
     const float dx = fminf(fmaxf(-t, lx), hx);
     float q = __fmul_rn(__fmul_rn(f.a, dx), dx);
@@ -102,6 +102,21 @@ __device__ __forceinline__ bool ellipse_hits_rect(const Foot &f, float x0, float
     best = fminf(best, q);
   }
   return best <= qmax;
+}
+
+// local = q * w + r for a candidate index below 2^24: quotient from a float
+// reciprocal, then corrected by one step, so the result is exact.
+__device__ __forceinline__ void divmod_small(uint32_t local, uint32_t w, float rw, uint32_t &q, uint32_t &r) {
+  q = __float2uint_rz(__fmul_rn(__uint2float_rn(local), rw));
+  int rr = (int)local - (int)(q * w);
+  if (rr < 0) {
+    --q;
+    rr += (int)w;
+  } else if (rr >= (int)w) {
+    ++q;
+    rr -= (int)w;
+  }
+  r = (uint32_t)rr;
 }
 
 __device__ __forceinline__ bool tile_hit(const Foot &f, int tx, int ty, int W, int H, int T) {
@@ -230,7 +245,9 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
       const WarpSplat &os = s_ws[warp][o];
       const int4 r0 = os.r0;
       const uint32_t local = ee - o_excl;
-      const int ty = r0.y + (int)(local / (uint32_t)r0.z), tx = r0.x + (int)(local % (uint32_t)r0.z);
+      uint32_t lyq, lxr;
+      divmod_small(local, (uint32_t)r0.z, __frcp_rn((float)r0.z), lyq, lxr);
+      const int ty = r0.y + (int)lyq, tx = r0.x + (int)lxr;
       bool hit = false;
       if (e < E) {
         const float4 g0 = os.g0, g1 = os.g1;
@@ -492,6 +509,7 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t s_scan[kWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int bits = __popc(mask);
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
   chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
@@ -509,7 +527,16 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
       const bool in = li < valid;
       key[j] = in ? __ldg(kin + base + li) : 0xffffffffu;
       const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      // lanes holding the same digit (and the same validity): one ballot per digit bit
+      const uint32_t vb = __ballot_sync(0xffffffffu, in);
+      uint32_t peers = in ? vb : ~vb;
+#pragma unroll
+      for (int b = 0; b < kRadixBits; ++b) {
+        if (b < bits) {
+          const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+          peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+      }
       const uint32_t before = __popc(peers & lt);
       const uint32_t c = s_wcnt[warp][d];
       rank[j] = c + before;
@@ -618,7 +645,8 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const WarpSplat &os = s_ws[warp][o];
       const int4 r0 = os.r0, r1 = os.r1;
       const uint32_t local = ee - o_excl;
-      const uint32_t ly = local / (uint32_t)r0.z, lx = local % (uint32_t)r0.z;
+      uint32_t ly, lx;
+      divmod_small(local, (uint32_t)r0.z, __frcp_rn((float)r0.z), ly, lx);
       bool take = e < E;
       if (take && mode != PK_BIN_RECT) {
         if (r1.w <= 32) {

@@ -22,6 +22,7 @@ constexpr float kLowPass = 0.3f;
 constexpr float kDetMin = 1e-7f;
 // exp(-q/2) = exp2(q * kExpScale), kExpScale = -log2(e) / 2
 constexpr float kExpScale = -0.72134752044448170f;
+constexpr float kInvExpScale = -1.38629436111989061f;   // 1 / kExpScale = -2 ln 2
 
 // Fixed grid sizes of the device-count-driven kernels (scan, radix sort).
 constexpr int kScanBlocks = 1024;

@@ -31,25 +31,35 @@ __device__ __forceinline__ int view_of_tile(const uint32_t *__restrict__ toff, i
 }
 
 struct Staged {
-  float4 *a;     // m_x, m_y, conic_a, conic_b
-  float4 *b;     // conic_c, opacity, red, green
-  float4 *c;     // blue, pair index (bits), 0, 0
+  float4 *a;     // m_x, m_y, A = k conic_a, B = 2 k conic_b      (k = -log2(e) / 2)
+  float4 *b;     // C = k conic_c, opacity, red, green
+  float4 *c;     // blue, pair index (bits), pcut, 0
   float4 *box;   // conservative pixel-centre box of the contributing ellipse
 };
 
-// Stage one splat.  The box bounds every pixel where q <= min(9, 2 ln(255 o))
-// (the only pixels where the splat can pass both skip tests), widened by a
-// relative 1e-3 and 0.01 px so FP32 rounding can never put a passing pixel
-// outside; the box only lets whole warps skip, the per-pixel tests still
-// decide.
+// 2^x on the MUFU unit (one instruction; relative error below 2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Stage one splat.  The exponent of the Gaussian is evaluated directly as
+// power = k q = A dx^2 + B dx dy + C dy^2, so alpha = o 2^power; a pixel is
+// skipped unless power >= pcut = max(9 k, -log2(255 o)), i.e. unless both
+// q <= 9 and o e^{-q/2} >= 1/255 hold.  The box bounds every pixel where
+// q <= min(9, 2 ln(255 o)), widened by a relative 1e-3 and 0.01 px so that
+// rounding can never put a passing pixel outside; it only lets whole warps
+// skip, the per-pixel test still decides.
 __device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint32_t pid, const Staged &s, int j) {
   const float4 *r = reinterpret_cast<const float4 *>(rec + (size_t)pid * kRec);
   const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
-  s.a[j] = r0;
-  s.b[j] = make_float4(r1.x, r1.y, r2.x, r2.y);
-  s.c[j] = make_float4(r2.z, __uint_as_float(pid), 0.f, 0.f);
   const float ca = r0.z, cb = r0.w, cc = r1.x, o = r1.y;
-  const float qlim = fminf(kQMax, 2.f * logf(255.f * o));
+  s.a[j] = make_float4(r0.x, r0.y, __fmul_rn(kExpScale, ca), __fmul_rn(2.f * kExpScale, cb));
+  s.b[j] = make_float4(__fmul_rn(kExpScale, cc), o, r2.x, r2.y);
+  const float pcut = fmaxf(9.f * kExpScale, -__log2f(255.f * o));
+  s.c[j] = make_float4(r2.z, __uint_as_float(pid), pcut, 0.f);
+  const float qlim = fminf(kQMax, 2.f * __logf(255.f * o));
   const float detq = ca * cc - cb * cb;
   float4 box;
   if (!(qlim >= 0.f)) {
@@ -69,20 +79,21 @@ struct Hit {
   bool clamped;
 };
 
-// alpha of a splat at pixel centre (px, py); false if skipped (q > 9 or
-// alpha < 1/255).  q = ca dx^2 + 2 cb dx dy + cc dy^2, alpha = min(0.99,
-// o exp(-q/2)).
-__device__ __forceinline__ bool splat_alpha(const float4 &a, float cc, float o, float px, float py, Hit &h) {
+// alpha of a staged splat at pixel centre (px, py); false if skipped.
+// alpha = min(0.99, o 2^power).  Written with explicit round-to-nearest
+// operations so the forward and the backward decide identically.
+__device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, float pcut, float px, float py,
+                                            Hit &h) {
   h.dx = __fsub_rn(px, a.x);
   h.dy = __fsub_rn(py, a.y);
-  const float u = __fmaf_rn(__fmul_rn(2.f, a.w), h.dy, __fmul_rn(a.z, h.dx));
-  const float q = __fmaf_rn(u, h.dx, __fmul_rn(__fmul_rn(cc, h.dy), h.dy));
-  if (!(q <= kQMax)) return false;
-  h.G = exp2f(__fmul_rn(q, kExpScale));
-  const float araw = __fmul_rn(o, h.G);
+  const float u = __fmaf_rn(a.w, h.dy, __fmul_rn(a.z, h.dx));
+  const float power = __fmaf_rn(u, h.dx, __fmul_rn(__fmul_rn(b.x, h.dy), h.dy));
+  if (!(power >= pcut)) return false;
+  h.G = ex2_approx(power);
+  const float araw = __fmul_rn(b.y, h.G);
   h.clamped = araw > kAlphaMax;
   h.alpha = h.clamped ? kAlphaMax : araw;
-  return h.alpha >= kAlphaMin;
+  return true;
 }
 
 __device__ __forceinline__ bool box_misses(const float4 &box, float x0, float x1, float y0, float y1) {

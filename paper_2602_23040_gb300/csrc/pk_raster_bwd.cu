@@ -133,12 +133,13 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
         Hit h;
         bool act = false;
         float dmx = 0.f, dmy = 0.f, dca = 0.f, dcb = 0.f, dcc = 0.f, dop = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+        const float4 c4 = s_c[j];
         if (pos < nc) {
           ++evals;
-          act = splat_alpha(a, b.x, b.y, px, py, h);
+          act = splat_alpha(a, b, c4.z, px, py, h);
         }
         if (act) {
-          const float cb_ = s_c[j].x;
+          const float cb_ = c4.x;
           const float om = __fsub_rn(1.f, h.alpha);
           const float inv = 1.f / om;
           const float Ti = T * inv;
@@ -152,14 +153,17 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
           dg = wT * g1;
           db = wT * g2;
           if (!h.clamped) {
+            // alpha = o 2^power, power = k q: dL/dq = -alpha dL/dalpha / 2
             dop = da * h.G;
             const float dq = -0.5f * h.alpha * da;
             const float dx = h.dx, dy = h.dy;
             dca = dq * dx * dx;
             dcb = dq * 2.f * dx * dy;
             dcc = dq * dy * dy;
-            dmx = -2.f * dq * (a.z * dx + a.w * dy);
-            dmy = -2.f * dq * (a.w * dx + b.x * dy);
+            // dq/dm = -2 conic d = -(2 A dx + B dy, B dx + 2 C dy) / k
+            const float s2 = dq * kInvExpScale;
+            dmx = -s2 * (2.f * a.z * dx + a.w * dy);
+            dmy = -s2 * (a.w * dx + 2.f * b.x * dy);
           }
         }
         if (__any_sync(0xffffffffu, act)) {
@@ -167,7 +171,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
           int idx;
           const float sum = warp_reduce_scatter9(v9, lane, &idx);
           if (idx >= 0) {
-            const uint32_t pid = __float_as_uint(s_c[j].y);
+            const uint32_t pid = __float_as_uint(c4.y);
             atomicAdd(grad2d + (size_t)pid * kG2d + idx, sum);
           }
         }

@@ -71,10 +71,10 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
             const int j = 32 * k + __ffs(m) - 1;
             m &= m - 1;
             if (!done) {
-              const float4 a = s_a[j], b = s_b[j];
+              const float4 a = s_a[j], b = s_b[j], c = s_c[j];
               Hit h;
               ++evals;
-              if (splat_alpha(a, b.x, b.y, px, py, h)) {
+              if (splat_alpha(a, b, c.z, px, py, h)) {
                 const float Tn = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
                 if (Tn < kTMin) {
                   done = true;
@@ -82,7 +82,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
                   const float w = __fmul_rn(h.alpha, T);
                   c0 = __fmaf_rn(w, b.z, c0);
                   c1 = __fmaf_rn(w, b.w, c1);
-                  c2 = __fmaf_rn(w, s_c[j].x, c2);
+                  c2 = __fmaf_rn(w, c.x, c2);
                   T = Tn;
                   last = base - s + (uint32_t)j + 1u;
                 }
