@@ -509,7 +509,6 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t s_scan[kWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int bits = __popc(mask);
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
   chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
@@ -527,16 +526,7 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
       const bool in = li < valid;
       key[j] = in ? __ldg(kin + base + li) : 0xffffffffu;
       const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
-      // lanes holding the same digit (and the same validity): one ballot per digit bit
-      const uint32_t vb = __ballot_sync(0xffffffffu, in);
-      uint32_t peers = in ? vb : ~vb;
-#pragma unroll
-      for (int b = 0; b < kRadixBits; ++b) {
-        if (b < bits) {
-          const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-          peers &= ((d >> b) & 1u) ? bb : ~bb;
-        }
-      }
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const uint32_t before = __popc(peers & lt);
       const uint32_t c = s_wcnt[warp][d];
       rank[j] = c + before;

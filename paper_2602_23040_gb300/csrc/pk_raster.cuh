@@ -35,6 +35,7 @@ struct Staged {
   float4 *b;     // C = k conic_c, opacity, red, green
   float4 *c;     // blue, pair index (bits), pcut, 0
   float4 *box;   // conservative pixel-centre box of the contributing ellipse
+  float4 *q;     // conic_a, conic_b, conic_c, qlim = min(9, 2 ln(255 o)) for the block test
 };
 
 // 2^x on the MUFU unit (one instruction; relative error below 2^-22).
@@ -60,6 +61,7 @@ __device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint3
   const float pcut = fmaxf(9.f * kExpScale, -__log2f(255.f * o));
   s.c[j] = make_float4(r2.z, __uint_as_float(pid), pcut, 0.f);
   const float qlim = fminf(kQMax, 2.f * __logf(255.f * o));
+  s.q[j] = make_float4(ca, cb, cc, qlim);
   const float detq = ca * cc - cb * cb;
   float4 box;
   if (!(qlim >= 0.f)) {
@@ -98,6 +100,33 @@ __device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, fl
 
 __device__ __forceinline__ bool box_misses(const float4 &box, float x0, float x1, float y0, float y1) {
   return box.x > x1 || box.y < x0 || box.z > y1 || box.w < y0;
+}
+
+// Can the staged splat pass both skip tests anywhere in the pixel-centre
+// rectangle [x0, x1] x [y0, y1] of a warp's block?  First the box, then the
+// least q over the rectangle (0 with the mean inside, else on an edge facing
+// the mean, at the clamped 1-D minimiser) against qlim, with a relative
+// 1e-3 + 1e-3 margin so rounding can only keep a splat, never drop one.
+__device__ __forceinline__ bool block_may_hit(const float4 &box, const float4 &q, float mx, float my, float x0,
+                                              float x1, float y0, float y1) {
+  if (box_misses(box, x0, x1, y0, y1)) return false;
+  const float a = q.x, b = q.y, c = q.z;
+  if (!(a > 0.f) || !(c > 0.f)) return true;
+  const bool inx = mx >= x0 && mx <= x1, iny = my >= y0 && my <= y1;
+  if (inx && iny) return true;
+  const float lx = x0 - mx, hx = x1 - mx, ly = y0 - my, hy = y1 - my;
+  float best = INFINITY;
+  if (!inx) {
+    const float dx = mx < x0 ? lx : hx;
+    const float dy = fminf(fmaxf(-__fdividef(b * dx, c), ly), hy);
+    best = fminf(best, (a * dx + 2.f * b * dy) * dx + c * dy * dy);
+  }
+  if (!iny) {
+    const float dy = my < y0 ? ly : hy;
+    const float dx = fminf(fmaxf(-__fdividef(b * dy, a), lx), hx);
+    best = fminf(best, (a * dx + 2.f * b * dy) * dx + c * dy * dy);
+  }
+  return best <= q.w * 1.001f + 1e-3f;
 }
 
 }  // namespace pk

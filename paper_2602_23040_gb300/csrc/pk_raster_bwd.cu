@@ -58,12 +58,12 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
     const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out) {
-  __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch];
+  __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ uint32_t s_tile;
   __shared__ int s_view;
   __shared__ uint32_t s_wmax[kRasterThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const Staged st{s_a, s_b, s_c, s_box};
+  const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy;
   pixel_of(tid, ox, oy);
   unsigned long long evals = 0;
@@ -119,7 +119,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       for (int k = 0; k < kBatch / 32; ++k) {
         const int j = 32 * k + lane;
         hits[k] = __ballot_sync(0xffffffffu, j < nb && beg + (uint32_t)j < wmax &&
-                                                 !box_misses(s_box[j], wx0, wx1, wy0, wy1));
+                                                 block_may_hit(s_box[j], s_q[j], s_a[j].x, s_a[j].y, wx0, wx1, wy0, wy1));
       }
 #pragma unroll
       for (int k = kBatch / 32 - 1; k >= 0; --k) {

@@ -13,16 +13,16 @@ using namespace pk;
 
 namespace {
 
-__global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
+__global__ __launch_bounds__(kRasterThreads, 5) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
     uint32_t *queue, unsigned long long *evals_out) {
-  __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch];
+  __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ uint32_t s_tile;
   __shared__ int s_view;
   const int tid = threadIdx.x, lane = tid & 31;
-  const Staged st{s_a, s_b, s_c, s_box};
+  const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy;
   pixel_of(tid, ox, oy);
   unsigned long long evals = 0;
@@ -61,7 +61,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
 #pragma unroll
         for (int k = 0; k < kBatch / 32; ++k) {
           const int j = 32 * k + lane;
-          hits[k] = __ballot_sync(0xffffffffu, j < nb && !box_misses(s_box[j], wx0, wx1, wy0, wy1));
+          hits[k] = __ballot_sync(0xffffffffu, j < nb && block_may_hit(s_box[j], s_q[j], s_a[j].x, s_a[j].y,
+                                                                       wx0, wx1, wy0, wy1));
         }
         bool all_done = false;
 #pragma unroll
