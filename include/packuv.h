@@ -70,7 +70,8 @@ typedef enum pk_status {
   PK_ERR_CAPACITY = 3,    /* a device capacity was exceeded (device status) */
   PK_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (device status) */
   PK_ERR_CUDA = 5,        /* a CUDA runtime call failed */
-  PK_ERR_UNSUPPORTED = 6  /* option not supported by this build */
+  PK_ERR_UNSUPPORTED = 6, /* option not supported by this build */
+  PK_ERR_TOO_LARGE = 7    /* problem larger than pk_bin_and_sort_noalloc's fixed scratch */
 } pk_status;
 
 typedef enum pk_texel_type { PK_TEXEL_F32 = 0, PK_TEXEL_F16 = 1 } pk_texel_type;
@@ -227,6 +228,26 @@ pk_status pk_project_and_sh(const pk_plan *plan, const float *soa, float *record
  * dups_needed and emits nothing (all ranges empty). */
 pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
                           uint32_t *tile_ranges, void *workspace, pk_stream_t stream);
+
+/* pk_bin_and_sort without a workspace.  The paper has no counterpart: this
+ * is a convenience for callers that cannot give the library device memory
+ * -- e.g. a renderer driven from inside another framework's frame callback,
+ * where allocating would stall the frame or break that framework's
+ * recorded CUDA graph, or a small tool without a device allocator.  Same
+ * inputs, outputs and bit-exact result as pk_bin_and_sort; the scratch is a
+ * 64 MiB array inside the library (reserved on every GPU that loads it, for
+ * the life of the process), so the plan must satisfy 28 * V * N + 12 *
+ * max_dups + about 1.1 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
+ * nothing is enqueued.  n_entries: out, one device uint32 -- the entries
+ * written, or 0xFFFFFFFF if they exceeded max_dups (then nothing was
+ * emitted).  The first call on a device looks up the array's address; make
+ * it before any stream capture.  Every call shares the one array and leaves
+ * its contents behind: calls whose work can overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The call copies the plan's view table from host memory each time and
+ * never allocates. */
+pk_status pk_bin_and_sort_noalloc(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
+                                  uint32_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream);
 
 /* a4 -- Supp. "Viewer": C = sum_i T_i alpha_i c_i, T_i = prod_{j<i}
  * (1 - alpha_j), front to back in the order of pk_bin_and_sort, plus

@@ -13,6 +13,7 @@ from .api import (  # noqa: F401
     atlas_layout,
     atlas_scatter_grad,
     bin_and_sort,
+    bin_and_sort_noalloc,
     l1_loss_grad,
     make_workspace,
     project_and_sh,
@@ -25,6 +26,6 @@ from .render import PerViewLoop, Renderer, render  # noqa: F401
 
 __all__ = [
     "Plan", "Renderer", "PerViewLoop", "render", "atlas_layout", "atlas_gather", "project_and_sh",
-    "bin_and_sort", "rasterize_fwd", "rasterize_bwd", "atlas_scatter_grad", "l1_loss_grad",
+    "bin_and_sort", "bin_and_sort_noalloc", "rasterize_fwd", "rasterize_bwd", "atlas_scatter_grad", "l1_loss_grad",
     "make_workspace", "workspace_init", "read_status",
 ]

@@ -18,7 +18,8 @@ GRAD2D_FLOATS = 12
 
 PK_OK = 0
 STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "invalid descriptor", 3: "capacity exceeded",
-                4: "device wait timed out", 5: "CUDA error", 6: "unsupported"}
+                4: "device wait timed out", 5: "CUDA error", 6: "unsupported",
+                7: "larger than the allocation-free call's fixed scratch"}
 DEV_CAPACITY = 1
 DEV_LIVE_MISMATCH = 2
 DEV_TIMEOUT = 4
@@ -79,6 +80,7 @@ SIGNATURES = {
     "pk_rasterize_bwd": (ST, [P, P, P, P, P, P, P, P, P, P]),
     "pk_atlas_scatter_grad": (ST, [P, P, P, P, P, P, C.c_int32, P, P]),
     "pk_l1_loss_grad": (ST, [P, P, P, P, P, P]),
+    "pk_bin_and_sort_noalloc": (ST, [P, P, P, P, P, P]),
 }
 
 _lock = threading.Lock()

@@ -252,3 +252,19 @@ def l1_loss_grad(plan: Plan, image, target, dL_dimage, ws, stream=None) -> None:
                                   _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
                                   _ptr(ws, "workspace"), _stream(stream))
     N.check("pk_l1_loss_grad", rc)
+
+
+def bin_and_sort_noalloc(plan: Plan, records, sorted_vals, tile_ranges, n_entries, stream=None) -> None:
+    """``pk_bin_and_sort`` for callers that cannot provide a workspace (for
+    example code running inside another framework's frame loop, where device
+    allocation is not allowed).  The scratch is a fixed 64 MiB array inside
+    the library; ``n_entries`` (one int32 on the device) receives the entry
+    count, or -1 (0xFFFFFFFF) if the entries exceeded ``plan.max_dups``.
+    Calls that overlap on the GPU share that array and must not run
+    concurrently."""
+    rc = N.load().pk_bin_and_sort_noalloc(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups),
+        _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles), _ptr(n_entries, "n_entries", _I32, 1),
+        _stream(stream))
+    N.check("pk_bin_and_sort_noalloc", rc)

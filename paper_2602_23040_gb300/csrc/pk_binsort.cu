@@ -767,3 +767,142 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
   k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[npass & 1], ctr, tile_ranges);
   return check_launch();
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of pk_bin_and_sort.
+//
+// Some callers cannot hand the library a workspace: a host application that
+// drives the renderer from inside another framework's frame callback, where
+// device allocation is forbidden (it would stall the frame or break the
+// framework's pre-recorded CUDA graph), or a small tool with no device
+// allocator of its own.  This entry point keeps its scratch in one
+// file-scope device array instead, sized once for every process that loads
+// the library.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB, held by every GPU that loads the library
+constexpr int kMaxDevices = 64;
+__device__ __align__(256) unsigned char g_bin_scratch[kStaticScratchBytes];
+
+std::mutex g_bin_scratch_mu;
+void *g_bin_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_bin_scratch on the current device (looked up once per
+// device; the host-side symbol itself is only a stand-in and must never be
+// passed to a kernel).
+pk_status static_scratch(void **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PK_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_bin_scratch_mu);
+  if (!g_bin_scratch_addr[dev]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_bin_scratch) != cudaSuccess || !ptr) return PK_ERR_CUDA;
+    g_bin_scratch_addr[dev] = ptr;
+  }
+  *out = g_bin_scratch_addr[dev];
+  return PK_OK;
+}
+
+__global__ void k_report_entries(const DevCounters *ctr, const pk_device_status *status, uint32_t *n_entries) {
+  *n_entries = (status->flags & PK_DEV_CAPACITY) ? 0xffffffffu : ctr->dups;
+}
+
+}  // namespace
+
+extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *records, uint32_t *sorted_vals,
+                                             uint32_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream) {
+  if (!p || !records || !sorted_vals || !tile_ranges || !n_entries) return PK_ERR_ARG;
+  if (!aligned16(records)) return PK_ERR_ARG;
+  // layout of this plan's scratch inside the static array
+  const uint64_t pairs = (uint64_t)p->pairs, maxd = p->max_dups;
+  WsLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at_ = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return at_;
+  };
+  L.status = take(sizeof(pk_device_status));
+  L.counters = take(sizeof(DevCounters));
+  L.views = take(sizeof(DevView) * p->V);
+  L.pair_cnt = take(sizeof(uint32_t) * pairs);
+  L.zkey0 = take(sizeof(uint32_t) * pairs);
+  L.zkey1 = take(sizeof(uint32_t) * pairs);
+  L.pval0 = take(sizeof(uint32_t) * pairs);
+  L.pval1 = take(sizeof(uint32_t) * pairs);
+  L.offs = take(sizeof(uint32_t) * pairs);
+  L.rmask = take(sizeof(uint32_t) * pairs);
+  L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
+  L.hist = take(sizeof(uint32_t) * kRadix * kSortBlocks);
+  L.dkey0 = take(sizeof(uint32_t) * maxd);
+  L.dkey1 = take(sizeof(uint32_t) * maxd);
+  L.dval = take(sizeof(uint32_t) * maxd);
+  if (off > kStaticScratchBytes) return PK_ERR_TOO_LARGE;
+  void *ws = nullptr;
+  pk_status e = static_scratch(&ws);
+  if (e != PK_OK) return e;
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the array keeps the previous call's contents: reset the status and
+  // counters, refresh this plan's view table
+  if (cudaMemsetAsync(at<char>(ws, L.status), 0, L.views - L.status, st) != cudaSuccess) return PK_ERR_CUDA;
+  if (cudaMemcpyAsync(at<char>(ws, L.views), p->h_views, sizeof(DevView) * p->V, cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return PK_ERR_CUDA;
+  const DevView *views = at<DevView>(ws, L.views);
+  DevCounters *ctr = at<DevCounters>(ws, L.counters);
+  pk_device_status *status = at<pk_device_status>(ws, L.status);
+  uint32_t *cnt = at<uint32_t>(ws, L.pair_cnt);
+  uint32_t *zk0 = at<uint32_t>(ws, L.zkey0), *zk1 = at<uint32_t>(ws, L.zkey1);
+  uint32_t *pv0 = at<uint32_t>(ws, L.pval0), *pv1 = at<uint32_t>(ws, L.pval1);
+  uint32_t *offs = at<uint32_t>(ws, L.offs);
+  uint64_t *bsum = at<uint64_t>(ws, L.blocksums);
+  uint32_t *hist = at<uint32_t>(ws, L.hist);
+  uint32_t *dk0 = at<uint32_t>(ws, L.dkey0), *dk1 = at<uint32_t>(ws, L.dkey1);
+  uint32_t *dv = at<uint32_t>(ws, L.dval);
+  const uint32_t *n_valid = &ctr->n_valid;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nsort = std::max(1, std::min(kSortBlocks, 3 * sms));
+
+  if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
+    return PK_ERR_CUDA;
+  if (pairs > 0) {
+    const int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
+    k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt,
+                                                at<uint32_t>(ws, L.rmask));
+    k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, maxd, ctr, status);
+    k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, records, pairs, bsum, zk0, pv0);
+    for (int pass = 0; pass < 4; ++pass) {
+      const uint32_t *ki = (pass & 1) ? zk1 : zk0;
+      const uint32_t *vi = (pass & 1) ? pv1 : pv0;
+      uint32_t *ko = (pass & 1) ? zk0 : zk1;
+      uint32_t *vo = (pass & 1) ? pv0 : pv1;
+      if ((e = radix_pass(ki, vi, ko, vo, n_valid, 0, 8 * pass, 8, hist, nsort, st)) != PK_OK) return e;
+    }
+    SrcSorted ss{cnt, pv0};
+    k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, maxd, ctr, status);
+    k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, bsum, ctr, offs);
+    const int npass = (p->tile_bits + 7) / 8;
+    uint32_t *vbuf[2] = {(npass & 1) ? dv : sorted_vals, (npass & 1) ? sorted_vals : dv};
+    uint32_t *kbuf[2] = {dk0, dk1};
+    k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, at<uint32_t>(ws, L.rmask), ctr, views,
+                                                        p->N, p->T, p->opts.bin_mode, kbuf[0], vbuf[0]);
+    for (int pass = 0; pass < npass; ++pass) {
+      const int bits = std::min(8, p->tile_bits - 8 * pass);
+      if ((e = radix_pass(kbuf[pass & 1], vbuf[pass & 1], kbuf[(pass + 1) & 1], vbuf[(pass + 1) & 1], &ctr->dups,
+                          0, 8 * pass, bits, hist, nsort, st)) != PK_OK)
+        return e;
+    }
+    k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[npass & 1], ctr, tile_ranges);
+  }
+  k_report_entries<<<1, 1, 0, st>>>(ctr, status, n_entries);
+  return check_launch();
+}

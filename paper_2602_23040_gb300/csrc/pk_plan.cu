@@ -34,6 +34,7 @@ extern "C" const char *pk_status_string(pk_status s) {
     case PK_ERR_TIMEOUT: return "device wait timed out";
     case PK_ERR_CUDA: return "CUDA runtime error";
     case PK_ERR_UNSUPPORTED: return "unsupported option";
+    case PK_ERR_TOO_LARGE: return "problem larger than the fixed scratch of the allocation-free call";
   }
   return "unknown status";
 }
