@@ -233,6 +233,7 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
     }
     s_ws[warp][lane] = ws;
     __syncwarp();
+    const float rw = __frcp_rn((float)ws.r0.z);   // for the candidate -> (row, column) split
     const uint32_t incl = warp_incl_scan(ncand);
     const uint32_t excl = incl - ncand;
     const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
@@ -246,7 +247,7 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
       const int4 r0 = os.r0;
       const uint32_t local = ee - o_excl;
       uint32_t lyq, lxr;
-      divmod_small(local, (uint32_t)r0.z, __frcp_rn((float)r0.z), lyq, lxr);
+      divmod_small(local, (uint32_t)r0.z, __shfl_sync(0xffffffffu, rw, o), lyq, lxr);
       const int ty = r0.y + (int)lyq, tx = r0.x + (int)lxr;
       bool hit = false;
       if (e < E) {
@@ -618,6 +619,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
     }
     s_ws[warp][lane] = ws;
     __syncwarp();
+    const float rw = __frcp_rn((float)ws.r0.z);
     uint32_t off0 = 0;
     if (lane == 0) off0 = offs[w * 32];
     off0 = __shfl_sync(0xffffffffu, off0, 0);
@@ -636,7 +638,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const int4 r0 = os.r0, r1 = os.r1;
       const uint32_t local = ee - o_excl;
       uint32_t ly, lx;
-      divmod_small(local, (uint32_t)r0.z, __frcp_rn((float)r0.z), ly, lx);
+      divmod_small(local, (uint32_t)r0.z, __shfl_sync(0xffffffffu, rw, o), ly, lx);
       bool take = e < E;
       if (take && mode != PK_BIN_RECT) {
         if (r1.w <= 32) {

@@ -10,14 +10,15 @@
 namespace pk {
 
 constexpr int kTileSide = 16;
-constexpr int kRasterThreads = 256;   // one pixel per thread
-constexpr int kBatch = 256;           // splats staged per batch
+constexpr int kRasterThreads = 128;   // two pixels per thread
+constexpr int kBatch = 256;           // splats staged per batch (two per thread)
 
-// Warp w covers the 8 x 4 pixel block (w % 2, w / 2) of the 16 x 16 tile.
+// Warp w covers the 8 x 8 pixel block (w % 2, w / 2) of the 16 x 16 tile;
+// lane l holds pixels (l % 8, l / 8) and (l % 8, l / 8 + 4) of that block.
 __device__ __forceinline__ void pixel_of(int tid, int &ox, int &oy) {
   const int w = tid >> 5, l = tid & 31;
   ox = (w & 1) * 8 + (l & 7);
-  oy = (w >> 1) * 4 + (l >> 3);
+  oy = (w >> 1) * 8 + (l >> 3);
 }
 
 // View that owns global tile t (binary search over tile offsets).

@@ -1,8 +1,9 @@
 // a5 -- adjoint of the compositing (Sec. 4.2 "Objective").  Each pixel
 // walks its tile's list backwards from its last blended splat, recovering
 // T_i = T_{i+1} / (1 - alpha_i) from the stored final transmittance, so no
-// per-step state of the forward is kept.  Per splat the 9 gradients of a
-// warp's 32 pixels are summed by a reduce-scatter over the lanes (12
+// per-step state of the forward is kept.  Each thread holds two pixels; per
+// splat the 9 gradients of a warp's 64 pixels are summed by a reduce-scatter
+// over the lanes (12
 // shuffles instead of 45 for nine full butterfly sums), after which nine
 // lanes each hold one complete sum and add it to the splat's gradient
 // record with one coalesced atomic instruction.
@@ -53,6 +54,43 @@ __device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int l
   return z;
 }
 
+// One pixel's share of the adjoint of a blended splat.  T (transmittance
+// after the splat) becomes T before it; S (colour composited behind,
+// background included) takes the splat's own term; the nine gradients are
+// added to acc.  Returns false if the pixel skips the splat.
+__device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, const float4 &c4, float px, float py,
+                                              float g0, float g1, float g2, float &T, float &S0, float &S1,
+                                              float &S2, float (&acc)[9]) {
+  Hit h;
+  if (!splat_alpha(a, b, c4.z, px, py, h)) return false;
+  const float om = __fsub_rn(1.f, h.alpha);
+  const float inv = 1.f / om;
+  const float Ti = T * inv;
+  const float wT = h.alpha * Ti;
+  const float da = g0 * (Ti * b.z - S0 * inv) + g1 * (Ti * b.w - S1 * inv) + g2 * (Ti * c4.x - S2 * inv);
+  S0 = fmaf(wT, b.z, S0);
+  S1 = fmaf(wT, b.w, S1);
+  S2 = fmaf(wT, c4.x, S2);
+  T = Ti;
+  acc[6] = fmaf(wT, g0, acc[6]);
+  acc[7] = fmaf(wT, g1, acc[7]);
+  acc[8] = fmaf(wT, g2, acc[8]);
+  if (!h.clamped) {
+    // alpha = o 2^power, power = k q: dL/dq = -alpha dL/dalpha / 2
+    acc[5] = fmaf(da, h.G, acc[5]);
+    const float dq = -0.5f * h.alpha * da;
+    const float dx = h.dx, dy = h.dy;
+    acc[2] = fmaf(dq * dx, dx, acc[2]);
+    acc[3] = fmaf(dq * 2.f * dx, dy, acc[3]);
+    acc[4] = fmaf(dq * dy, dy, acc[4]);
+    // dq/dm = -2 conic d = -(2 A dx + B dy, B dx + 2 C dy) / k
+    const float s2 = dq * kInvExpScale;
+    acc[0] = fmaf(-s2, 2.f * a.z * dx + a.w * dy, acc[0]);
+    acc[1] = fmaf(-s2, a.w * dx + 2.f * b.x * dy, acc[1]);
+  }
+  return true;
+}
+
 __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
@@ -80,27 +118,37 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kTileSide + ox, y = ty * kTileSide + oy;
-    const bool inside = x < W && y < H;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy, y1 = y0 + 4;
+    const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
+    const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
     const float wx0 = (float)(tx * kTileSide + (ox & ~7)) + 0.5f, wx1 = wx0 + 7.f;
-    const float wy0 = (float)(ty * kTileSide + (oy & ~3)) + 0.5f, wy1 = wy0 + 3.f;
+    const float wy0 = (float)(ty * kTileSide + (oy & ~7)) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t);
-    float T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    uint32_t nc = 0;
-    if (inside) {
-      const size_t pix = (size_t)view.pix_off + (size_t)y * W + x;
-      const size_t plane = (size_t)W * H;
-      const float *gi = dimg + 3 * (size_t)view.pix_off + (size_t)y * W + x;
-      T = Tfin[pix];
-      nc = ncontrib[pix];
-      g0 = gi[0];
-      g1 = gi[plane];
-      g2 = gi[2 * plane];
+    const size_t plane = (size_t)W * H;
+    float T0 = 1.f, T1 = 1.f, g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f;
+    uint32_t nc0 = 0, nc1 = 0;
+    if (in0) {
+      const size_t pix = (size_t)view.pix_off + (size_t)y0 * W + x;
+      const float *gi = dimg + 3 * (size_t)view.pix_off + (size_t)y0 * W + x;
+      T0 = Tfin[pix];
+      nc0 = ncontrib[pix];
+      g00 = gi[0];
+      g01 = gi[plane];
+      g02 = gi[2 * plane];
+    }
+    if (in1) {
+      const size_t pix = (size_t)view.pix_off + (size_t)y1 * W + x;
+      const float *gi = dimg + 3 * (size_t)view.pix_off + (size_t)y1 * W + x;
+      T1 = Tfin[pix];
+      nc1 = ncontrib[pix];
+      g10 = gi[0];
+      g11 = gi[plane];
+      g12 = gi[2 * plane];
     }
     // colour composited behind the current splat, background included
-    float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nc);
+    float S00 = T0 * bg0, S01 = T0 * bg1, S02 = T0 * bg2;
+    float S10 = T1 * bg0, S11 = T1 * bg1, S12 = T1 * bg2;
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(nc0, nc1));
     if (lane == 0) s_wmax[warp] = wmax;
     __syncthreads();
     uint32_t tmax = 0;
@@ -111,6 +159,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       const int nb = (int)(end - beg);
       __syncthreads();
       if (tid < nb) stage_splat(rec, __ldg(vals + s + beg + tid), st, tid);
+      if (tid + kRasterThreads < nb)
+        stage_splat(rec, __ldg(vals + s + beg + tid + kRasterThreads), st, tid + kRasterThreads);
       __syncthreads();
       // splats that can reach this warp's block and that some pixel of the
       // warp blended or skipped before stopping (list position < wmax)
@@ -123,59 +173,29 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       }
 #pragma unroll
       for (int k = kBatch / 32 - 1; k >= 0; --k) {
-       uint32_t m = hits[k];
-       while (m) {
-        const int bit = 31 - __clz(m);
-        m &= ~(1u << bit);
-        const int j = 32 * k + bit;
-        const uint32_t pos = beg + (uint32_t)j;       // 0-based list position
-        const float4 a = s_a[j], b = s_b[j];
-        Hit h;
-        bool act = false;
-        float dmx = 0.f, dmy = 0.f, dca = 0.f, dcb = 0.f, dcc = 0.f, dop = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-        const float4 c4 = s_c[j];
-        if (pos < nc) {
-          ++evals;
-          act = splat_alpha(a, b, c4.z, px, py, h);
-        }
-        if (act) {
-          const float cb_ = c4.x;
-          const float om = __fsub_rn(1.f, h.alpha);
-          const float inv = 1.f / om;
-          const float Ti = T * inv;
-          const float wT = h.alpha * Ti;
-          const float da = g0 * (Ti * b.z - S0 * inv) + g1 * (Ti * b.w - S1 * inv) + g2 * (Ti * cb_ - S2 * inv);
-          S0 = fmaf(wT, b.z, S0);
-          S1 = fmaf(wT, b.w, S1);
-          S2 = fmaf(wT, cb_, S2);
-          T = Ti;
-          dr = wT * g0;
-          dg = wT * g1;
-          db = wT * g2;
-          if (!h.clamped) {
-            // alpha = o 2^power, power = k q: dL/dq = -alpha dL/dalpha / 2
-            dop = da * h.G;
-            const float dq = -0.5f * h.alpha * da;
-            const float dx = h.dx, dy = h.dy;
-            dca = dq * dx * dx;
-            dcb = dq * 2.f * dx * dy;
-            dcc = dq * dy * dy;
-            // dq/dm = -2 conic d = -(2 A dx + B dy, B dx + 2 C dy) / k
-            const float s2 = dq * kInvExpScale;
-            dmx = -s2 * (2.f * a.z * dx + a.w * dy);
-            dmy = -s2 * (a.w * dx + 2.f * b.x * dy);
+        uint32_t m = hits[k];
+        while (m) {
+          const int bit = 31 - __clz(m);
+          m &= ~(1u << bit);
+          const int j = 32 * k + bit;
+          const uint32_t pos = beg + (uint32_t)j;   // 0-based list position
+          const float4 a = s_a[j], b = s_b[j], c4 = s_c[j];
+          float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          bool act = false;
+          if (pos < nc0) {
+            ++evals;
+            act |= pixel_adjoint(a, b, c4, px, py0, g00, g01, g02, T0, S00, S01, S02, acc);
+          }
+          if (pos < nc1) {
+            ++evals;
+            act |= pixel_adjoint(a, b, c4, px, py1, g10, g11, g12, T1, S10, S11, S12, acc);
+          }
+          if (__any_sync(0xffffffffu, act)) {
+            int idx;
+            const float sum = warp_reduce_scatter9(acc, lane, &idx);
+            if (idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + idx, sum);
           }
         }
-        if (__any_sync(0xffffffffu, act)) {
-          const float v9[9] = {dmx, dmy, dca, dcb, dcc, dop, dr, dg, db};
-          int idx;
-          const float sum = warp_reduce_scatter9(v9, lane, &idx);
-          if (idx >= 0) {
-            const uint32_t pid = __float_as_uint(c4.y);
-            atomicAdd(grad2d + (size_t)pid * kG2d + idx, sum);
-          }
-        }
-       }
       }
       end = beg;
     }

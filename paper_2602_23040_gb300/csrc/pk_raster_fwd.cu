@@ -3,8 +3,8 @@
 //
 // One persistent launch covers the tiles of every view: each CTA takes the
 // next tile from a device counter, stages the tile's splats batch by
-// batch into shared memory and composites one pixel per thread.  Warps
-// cover 8 x 4 pixel blocks and skip, as a whole, every splat whose
+// batch into shared memory and composites two pixels per thread.  Warps
+// cover 8 x 8 pixel blocks and skip, as a whole, every splat whose
 // contributing ellipse misses their block.  The CTA leaves a tile as soon
 // as every pixel has stopped (transmittance cutoff) or the list ends.
 #include "pk_raster.cuh"
@@ -13,7 +13,7 @@ using namespace pk;
 
 namespace {
 
-__global__ __launch_bounds__(kRasterThreads, 5) void k_raster_fwd(
+__global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
@@ -39,24 +39,26 @@ __global__ __launch_bounds__(kRasterThreads, 5) void k_raster_fwd(
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kTileSide + ox, y = ty * kTileSide + oy;
-    const bool inside = x < W && y < H;
-    const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-    // pixel-centre bounds of this warp's 8 x 4 block
+    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy, y1 = y0 + 4;
+    const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
+    const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
+    // pixel-centre bounds of this warp's 8 x 8 block
     const float wx0 = (float)(tx * kTileSide + (ox & ~7)) + 0.5f, wx1 = wx0 + 7.f;
-    const float wy0 = (float)(ty * kTileSide + (oy & ~3)) + 0.5f, wy1 = wy0 + 3.f;
+    const float wy0 = (float)(ty * kTileSide + (oy & ~7)) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t), e = __ldg(ranges + 2 * (size_t)t + 1);
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
+    float T0 = 1.f, T1 = 1.f, c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
+    uint32_t last0 = 0, last1 = 0;
+    bool done0 = !in0, done1 = !in1;
     for (uint32_t base = s; base < e; base += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, e - base);
       __syncthreads();
       if (tid < nb) stage_splat(rec, __ldg(vals + base + tid), st, tid);
+      if (tid + kRasterThreads < nb)
+        stage_splat(rec, __ldg(vals + base + tid + kRasterThreads), st, tid + kRasterThreads);
       __syncthreads();
-      if (!__all_sync(0xffffffffu, done)) {
-        // which staged splats can reach this warp's block: 8 box tests per
-        // lane, one ballot per 32 splats, then only the hits are visited
+      if (!__all_sync(0xffffffffu, done0 && done1)) {
+        // which staged splats can reach this warp's block: 8 tests per lane,
+        // one ballot per 32 splats, then only the hits are visited
         uint32_t hits[kBatch / 32];
 #pragma unroll
         for (int k = 0; k < kBatch / 32; ++k) {
@@ -71,39 +73,65 @@ __global__ __launch_bounds__(kRasterThreads, 5) void k_raster_fwd(
           while (m && !all_done) {
             const int j = 32 * k + __ffs(m) - 1;
             m &= m - 1;
-            if (!done) {
-              const float4 a = s_a[j], b = s_b[j], c = s_c[j];
-              Hit h;
+            const float4 a = s_a[j], b = s_b[j], c = s_c[j];
+            const uint32_t pos1 = base - s + (uint32_t)j + 1u;
+            Hit h;
+            if (!done0) {
               ++evals;
-              if (splat_alpha(a, b, c.z, px, py, h)) {
-                const float Tn = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
+              if (splat_alpha(a, b, c.z, px, py0, h)) {
+                const float Tn = __fmul_rn(T0, __fsub_rn(1.f, h.alpha));
                 if (Tn < kTMin) {
-                  done = true;
+                  done0 = true;
                 } else {
-                  const float w = __fmul_rn(h.alpha, T);
-                  c0 = __fmaf_rn(w, b.z, c0);
-                  c1 = __fmaf_rn(w, b.w, c1);
-                  c2 = __fmaf_rn(w, c.x, c2);
-                  T = Tn;
-                  last = base - s + (uint32_t)j + 1u;
+                  const float w = __fmul_rn(h.alpha, T0);
+                  c00 = __fmaf_rn(w, b.z, c00);
+                  c01 = __fmaf_rn(w, b.w, c01);
+                  c02 = __fmaf_rn(w, c.x, c02);
+                  T0 = Tn;
+                  last0 = pos1;
                 }
               }
             }
-            all_done = __all_sync(0xffffffffu, done);
+            if (!done1) {
+              ++evals;
+              if (splat_alpha(a, b, c.z, px, py1, h)) {
+                const float Tn = __fmul_rn(T1, __fsub_rn(1.f, h.alpha));
+                if (Tn < kTMin) {
+                  done1 = true;
+                } else {
+                  const float w = __fmul_rn(h.alpha, T1);
+                  c10 = __fmaf_rn(w, b.z, c10);
+                  c11 = __fmaf_rn(w, b.w, c11);
+                  c12 = __fmaf_rn(w, c.x, c12);
+                  T1 = Tn;
+                  last1 = pos1;
+                }
+              }
+            }
+            all_done = __all_sync(0xffffffffu, done0 && done1);
           }
         }
       }
-      if (__syncthreads_count(!done) == 0) break;
+      if (__syncthreads_count(!(done0 && done1)) == 0) break;
     }
-    if (inside) {
-      const size_t pix = (size_t)view.pix_off + (size_t)y * W + x;
-      const size_t plane = (size_t)W * H;
-      float *img = image + 3 * (size_t)view.pix_off + (size_t)y * W + x;
-      img[0] = __fmaf_rn(T, bg0, c0);
-      img[plane] = __fmaf_rn(T, bg1, c1);
-      img[2 * plane] = __fmaf_rn(T, bg2, c2);
-      Tout[pix] = T;
-      ncontrib[pix] = last;
+    const size_t plane = (size_t)W * H;
+    if (in0) {
+      const size_t pix = (size_t)view.pix_off + (size_t)y0 * W + x;
+      float *img = image + 3 * (size_t)view.pix_off + (size_t)y0 * W + x;
+      img[0] = __fmaf_rn(T0, bg0, c00);
+      img[plane] = __fmaf_rn(T0, bg1, c01);
+      img[2 * plane] = __fmaf_rn(T0, bg2, c02);
+      Tout[pix] = T0;
+      ncontrib[pix] = last0;
+    }
+    if (in1) {
+      const size_t pix = (size_t)view.pix_off + (size_t)y1 * W + x;
+      float *img = image + 3 * (size_t)view.pix_off + (size_t)y1 * W + x;
+      img[0] = __fmaf_rn(T1, bg0, c10);
+      img[plane] = __fmaf_rn(T1, bg1, c11);
+      img[2 * plane] = __fmaf_rn(T1, bg2, c12);
+      Tout[pix] = T1;
+      ncontrib[pix] = last1;
     }
     __syncthreads();   // everyone has read s_tile / s_view before the next fetch
   }
