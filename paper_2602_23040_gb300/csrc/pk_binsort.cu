@@ -407,24 +407,39 @@ __global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const 
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort, one pass = upsweep + scan + downsweep.
+// Stable LSD radix sort, one pass = upsweep + scan + downsweep.  Digits are
+// up to 8 or up to 11 bits wide (RB); wide digits cut the passes over the
+// (pair, tile) entries at the price of more buckets per pass.
 // ---------------------------------------------------------------------------
 
+template <int RB>
+struct Radix {
+  static constexpr int kR = 1 << RB;                       // buckets
+  static constexpr int kItems = RB <= 8 ? 12 : 11;         // keys per thread and tile
+  static constexpr int kTile = kThreads * kItems;          // 3072 or 2816 (multiples of 4)
+  static constexpr int kCopies = RB <= 8 ? kWarps : 2;     // private histograms in the upsweep
+  static constexpr int kPerThread = kR / kThreads;         // buckets per thread in the digit scan
+  // dynamic shared memory of the downsweep
+  static constexpr size_t kSmem = 2 * sizeof(uint32_t) * kR + 2 * sizeof(uint32_t) * kTile +
+                                  sizeof(uint32_t) * (kWarps + 1) + sizeof(uint16_t) * kWarps * kR;
+};
+
+template <int RB>
 __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                             const uint32_t *n_dev, uint64_t n_host, int shift,
                                                             uint32_t mask, uint32_t *__restrict__ hist) {
-  __shared__ uint32_t s_cnt[kWarps][kRadix];   // warp-private digit counts
-  const int warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&s_cnt[0][0])[i] = 0;
+  using C = Radix<RB>;
+  __shared__ uint32_t s_cnt[C::kCopies][C::kR];   // private digit counts
+  for (int i = threadIdx.x; i < C::kCopies * C::kR; i += kThreads) (&s_cnt[0][0])[i] = 0;
   __syncthreads();
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
-  chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
-  // chunks start on a multiple of kSortTile: 16-byte aligned vector loads,
-  // four in flight per thread
+  chunk_of(n, gridDim.x, blockIdx.x, C::kTile, b0, b1);
+  // chunks start on a multiple of the tile (itself a multiple of 4 keys):
+  // 16-byte aligned vector loads, four in flight per thread
   const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + b0);
   const uint64_t n4 = (b1 - b0) / 4;
-  uint32_t *cw = s_cnt[warp];
+  uint32_t *cw = s_cnt[(threadIdx.x >> 5) % C::kCopies];
   for (uint64_t t0 = 0; t0 < n4; t0 += 4 * kThreads) {
     uint4 q[4];
 #pragma unroll
@@ -444,10 +459,10 @@ __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__re
   for (uint64_t i = b0 + 4 * n4 + threadIdx.x; i < b1; i += kThreads)
     atomicAdd(&cw[(__ldg(keys + i) >> shift) & mask], 1u);
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kThreads) {
+  for (int d = threadIdx.x; d < C::kR; d += kThreads) {
     uint32_t t = 0;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) t += s_cnt[w][d];
+    for (int w = 0; w < C::kCopies; ++w) t += s_cnt[w][d];
     hist[(size_t)d * gridDim.x + blockIdx.x] = t;
   }
 }
@@ -499,65 +514,77 @@ __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist
   }
 }
 
-__global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
+template <int RB>
+__global__ __launch_bounds__(kThreads, 2) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist) {
-  __shared__ uint32_t s_wcnt[kWarps][kRadix];
-  __shared__ uint32_t s_start[kRadix];
-  __shared__ uint32_t s_gbase[kRadix];
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t s_scan[kWarps + 1];
+  using C = Radix<RB>;
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  uint32_t *s_start = reinterpret_cast<uint32_t *>(s_raw);           // [kR]
+  uint32_t *s_gbase = s_start + C::kR;                                // [kR]
+  uint32_t *s_keys = s_gbase + C::kR;                                 // [kTile]
+  uint32_t *s_vals = s_keys + C::kTile;                               // [kTile]
+  uint32_t *s_scan = s_vals + C::kTile;                               // [kWarps + 1]
+  uint16_t *s_wcnt = reinterpret_cast<uint16_t *>(s_scan + kWarps + 1);   // [kWarps][kR]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
-  chunk_of(n, gridDim.x, blockIdx.x, kSortTile, b0, b1);
-  for (int d = tid; d < kRadix; d += kThreads) s_gbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+  chunk_of(n, gridDim.x, blockIdx.x, C::kTile, b0, b1);
+  for (int d = tid; d < C::kR; d += kThreads) s_gbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
   const uint32_t lt = lanemask_lt();
-  for (uint64_t base = b0; base < b1; base += kSortTile) {
-    const uint32_t valid = (uint32_t)min((uint64_t)kSortTile, b1 - base);
-    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&s_wcnt[0][0])[i] = 0;
+  uint16_t *wc = s_wcnt + warp * C::kR;
+  for (uint64_t base = b0; base < b1; base += C::kTile) {
+    const uint32_t valid = (uint32_t)min((uint64_t)C::kTile, b1 - base);
+    for (int i = tid; i < kWarps * C::kR / 2; i += kThreads) reinterpret_cast<uint32_t *>(s_wcnt)[i] = 0;
     __syncthreads();
     // stable warp-level ranking: items in (warp, item, lane) order
-    uint32_t key[kSortItems], rank[kSortItems];
+    uint32_t key[C::kItems], rank[C::kItems];
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      const uint32_t li = (uint32_t)(warp * 32 * kSortItems + j * 32 + lane);
+    for (int j = 0; j < C::kItems; ++j) {
+      const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);
       const bool in = li < valid;
       key[j] = in ? __ldg(kin + base + li) : 0xffffffffu;
-      const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
+      const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(C::kR - 1);
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const uint32_t before = __popc(peers & lt);
-      const uint32_t c = s_wcnt[warp][d];
+      const uint32_t c = wc[d];
       rank[j] = c + before;
       __syncwarp();
-      if (before == 0) s_wcnt[warp][d] = c + __popc(peers);
+      if (before == 0) wc[d] = (uint16_t)(c + __popc(peers));
       __syncwarp();
     }
     __syncthreads();
-    // per digit: prefix over warps, then over digits
-    uint32_t dcount;
-    {
-      const int d = tid;   // kThreads == kRadix
+    // per digit: prefix over warps (in place), then over digits
+    uint32_t dcount[C::kPerThread];
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int u = 0; u < C::kPerThread; ++u) {
+      const int d = tid * C::kPerThread + u;
       uint32_t sum = 0;
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_wcnt[w][d];
-        s_wcnt[w][d] = sum;
+        const uint32_t c = s_wcnt[w * C::kR + d];
+        s_wcnt[w * C::kR + d] = (uint16_t)sum;
         sum += c;
       }
-      dcount = sum;
-      uint32_t tot;
-      s_start[d] = block_excl_scan<uint32_t>(sum, tot, s_scan);
+      dcount[u] = sum;
+      tsum += sum;
+    }
+    uint32_t tot;
+    uint32_t run = block_excl_scan<uint32_t>(tsum, tot, s_scan);
+#pragma unroll
+    for (int u = 0; u < C::kPerThread; ++u) {
+      s_start[tid * C::kPerThread + u] = run;
+      run += dcount[u];
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-      const uint32_t li = (uint32_t)(warp * 32 * kSortItems + j * 32 + lane);
+    for (int j = 0; j < C::kItems; ++j) {
+      const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);
       const bool in = li < valid;
-      const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(kRadix - 1);
-      const uint32_t r = s_start[d] + s_wcnt[warp][d] + rank[j];
+      const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(C::kR - 1);
+      const uint32_t r = s_start[d] + wc[d] + rank[j];
       s_keys[r] = key[j];
       s_vals[r] = in ? __ldg(vin + base + li) : 0u;
     }
@@ -570,7 +597,8 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
       vout[o] = s_vals[i];
     }
     __syncthreads();
-    s_gbase[tid] += dcount;
+#pragma unroll
+    for (int u = 0; u < C::kPerThread; ++u) s_gbase[tid * C::kPerThread + u] += dcount[u];
     __syncthreads();
   }
 }
@@ -689,31 +717,53 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
   }
 }
 
-pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                     const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                     cudaStream_t st) {
+template <int RB>
+pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                        const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
+                        cudaStream_t st) {
+  using C = Radix<RB>;
+  if (cudaFuncSetAttribute(k_radix_downsweep<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem) !=
+      cudaSuccess)
+    return PK_ERR_CUDA;
   const uint32_t mask = (1u << bits) - 1u;
-  k_radix_upsweep<<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist);
-  k_radix_scan<<<1, 1024, 0, st>>>(hist, kRadix * nblocks);
-  k_radix_downsweep<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n_dev, n_host, shift, mask, hist);
+  k_radix_upsweep<RB><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist);
+  k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
+  k_radix_downsweep<RB><<<nblocks, kThreads, C::kSmem, st>>>(kin, vin, kout, vout, n_dev, n_host, shift, mask,
+                                                               hist);
   return check_launch();
 }
 
-}  // namespace
+// One stable pass over key bits [shift, shift + bits), bits <= 11.
+pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+                     const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
+                     cudaStream_t st) {
+  if (bits <= 8) return radix_pass_rb<8>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, st);
+  return radix_pass_rb<11>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, st);
+}
 
-extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
-                                     uint32_t *tile_ranges, void *ws, pk_stream_t stream) {
-  if (!p || !records || !sorted_vals || !tile_ranges || !ws) return PK_ERR_ARG;
-  if (!aligned16(records)) return PK_ERR_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const WsLayout &L = p->ws;
+// Digit widths for a key of `bits` bits: as few passes of <= 11 bits as
+// possible, split evenly.
+int radix_plan(int bits, int *widths) {
+  const int npass = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
+  for (int i = 0, left = bits; i < npass; ++i) {
+    widths[i] = (left + (npass - i) - 1) / (npass - i);
+    left -= widths[i];
+  }
+  return npass;
+}
+
+// The whole binning + sort on one workspace layout (shared by the two
+// entry points below).
+pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const float *records,
+                            uint32_t *sorted_vals, uint32_t *tile_ranges, uint64_t maxd, cudaStream_t st) {
   const DevView *views = at<DevView>(ws, L.views);
   DevCounters *ctr = at<DevCounters>(ws, L.counters);
   pk_device_status *status = at<pk_device_status>(ws, L.status);
   uint32_t *cnt = at<uint32_t>(ws, L.pair_cnt);
-  uint32_t *zk0 = at<uint32_t>(ws, L.zkey0), *zk1 = at<uint32_t>(ws, L.zkey1);
-  uint32_t *pv0 = at<uint32_t>(ws, L.pval0), *pv1 = at<uint32_t>(ws, L.pval1);
+  uint32_t *zk[2] = {at<uint32_t>(ws, L.zkey0), at<uint32_t>(ws, L.zkey1)};
+  uint32_t *pv[2] = {at<uint32_t>(ws, L.pval0), at<uint32_t>(ws, L.pval1)};
   uint32_t *offs = at<uint32_t>(ws, L.offs);
+  uint32_t *rmask = at<uint32_t>(ws, L.rmask);
   uint64_t *bsum = at<uint64_t>(ws, L.blocksums);
   uint32_t *hist = at<uint32_t>(ws, L.hist);
   uint32_t *dk0 = at<uint32_t>(ws, L.dkey0), *dk1 = at<uint32_t>(ws, L.dkey1);
@@ -723,8 +773,8 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // sort blocks: 3 resident per SM (79 registers x 256 threads), within the histogram's capacity
-  const int nsort = std::max(1, std::min(kSortBlocks, 3 * sms));
+  // sort blocks: 2 resident per SM, within the histogram's capacity
+  const int nsort = std::max(1, std::min(kSortBlocks, 2 * sms));
 
   if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
     return PK_ERR_CUDA;
@@ -732,42 +782,54 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
     if (cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st) != cudaSuccess) return PK_ERR_CUDA;
     return PK_OK;
   }
-  int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
-  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt,
-                                              at<uint32_t>(ws, L.rmask));
+  const int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
+  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt, rmask);
   // compaction of the pairs that touch a tile, keyed by depth bits
   k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
-  k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, p->max_dups, ctr, status);
-  k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, records, pairs, bsum, zk0, pv0);
-  // depth sort of the pairs: 4 stable passes over the 32 bits of z
+  k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, maxd, ctr, status);
+  k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, records, pairs, bsum, zk[0], pv[0]);
+  // depth sort of the pairs: stable passes over the 32 bits of z
   pk_status e;
-  for (int pass = 0; pass < 4; ++pass) {
-    const uint32_t *ki = (pass & 1) ? zk1 : zk0;
-    const uint32_t *vi = (pass & 1) ? pv1 : pv0;
-    uint32_t *ko = (pass & 1) ? zk0 : zk1;
-    uint32_t *vo = (pass & 1) ? pv0 : pv1;
-    if ((e = radix_pass(ki, vi, ko, vo, n_valid, 0, 8 * pass, 8, hist, nsort, st)) != PK_OK) return e;
+  int widths[8];
+  int np = radix_plan(32, widths), shift = 0;
+  for (int pass = 0; pass < np; ++pass) {
+    const int a = pass & 1, b = a ^ 1;
+    if ((e = radix_pass(zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist, nsort, st)) != PK_OK)
+      return e;
+    shift += widths[pass];
   }
+  const uint32_t *pval = pv[np & 1];
   // emission offsets in depth order, capacity check
-  SrcSorted ss{cnt, pv0};
+  SrcSorted ss{cnt, pval};
   k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
-  k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, p->max_dups, ctr, status);
+  k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, maxd, ctr, status);
   k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, bsum, ctr, offs);
   // emission and the stable tile sort; the last pass lands in sorted_vals
-  const int npass = (p->tile_bits + 7) / 8;
-  uint32_t *vbuf[2] = {(npass & 1) ? dv : sorted_vals, (npass & 1) ? sorted_vals : dv};
+  np = radix_plan(p->tile_bits, widths);
+  uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
-  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, at<uint32_t>(ws, L.rmask), ctr, views, p->N,
-                                                      p->T, p->opts.bin_mode, kbuf[0], vbuf[0]);
-  const uint32_t *n_dups = &ctr->dups;
-  for (int pass = 0; pass < npass; ++pass) {
-    const int bits = std::min(8, p->tile_bits - 8 * pass);
-    if ((e = radix_pass(kbuf[pass & 1], vbuf[pass & 1], kbuf[(pass + 1) & 1], vbuf[(pass + 1) & 1], n_dups, 0,
-                        8 * pass, bits, hist, nsort, st)) != PK_OK)
+  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, rmask, ctr, views, p->N, p->T,
+                                                      p->opts.bin_mode, kbuf[0], vbuf[0]);
+  shift = 0;
+  for (int pass = 0; pass < np; ++pass) {
+    const int a = pass & 1, b = a ^ 1;
+    if ((e = radix_pass(kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nsort, st)) !=
+        PK_OK)
       return e;
+    shift += widths[pass];
   }
-  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[npass & 1], ctr, tile_ranges);
+  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], ctr, tile_ranges);
   return check_launch();
+}
+
+}  // namespace
+
+extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
+                                     uint32_t *tile_ranges, void *ws, pk_stream_t stream) {
+  if (!p || !records || !sorted_vals || !tile_ranges || !ws) return PK_ERR_ARG;
+  if (!aligned16(records)) return PK_ERR_ARG;
+  return bin_and_sort_impl(p, p->ws, ws, records, sorted_vals, tile_ranges, p->max_dups,
+                           reinterpret_cast<cudaStream_t>(stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -839,7 +901,7 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   L.offs = take(sizeof(uint32_t) * pairs);
   L.rmask = take(sizeof(uint32_t) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
-  L.hist = take(sizeof(uint32_t) * kRadix * kSortBlocks);
+  L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);
   L.dval = take(sizeof(uint32_t) * maxd);
@@ -855,56 +917,9 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   if (cudaMemcpyAsync(at<char>(ws, L.views), p->h_views, sizeof(DevView) * p->V, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return PK_ERR_CUDA;
-  const DevView *views = at<DevView>(ws, L.views);
-  DevCounters *ctr = at<DevCounters>(ws, L.counters);
-  pk_device_status *status = at<pk_device_status>(ws, L.status);
-  uint32_t *cnt = at<uint32_t>(ws, L.pair_cnt);
-  uint32_t *zk0 = at<uint32_t>(ws, L.zkey0), *zk1 = at<uint32_t>(ws, L.zkey1);
-  uint32_t *pv0 = at<uint32_t>(ws, L.pval0), *pv1 = at<uint32_t>(ws, L.pval1);
-  uint32_t *offs = at<uint32_t>(ws, L.offs);
-  uint64_t *bsum = at<uint64_t>(ws, L.blocksums);
-  uint32_t *hist = at<uint32_t>(ws, L.hist);
-  uint32_t *dk0 = at<uint32_t>(ws, L.dkey0), *dk1 = at<uint32_t>(ws, L.dkey1);
-  uint32_t *dv = at<uint32_t>(ws, L.dval);
-  const uint32_t *n_valid = &ctr->n_valid;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nsort = std::max(1, std::min(kSortBlocks, 3 * sms));
-
-  if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
-    return PK_ERR_CUDA;
-  if (pairs > 0) {
-    const int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
-    k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt,
-                                                at<uint32_t>(ws, L.rmask));
-    k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
-    k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, maxd, ctr, status);
-    k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, records, pairs, bsum, zk0, pv0);
-    for (int pass = 0; pass < 4; ++pass) {
-      const uint32_t *ki = (pass & 1) ? zk1 : zk0;
-      const uint32_t *vi = (pass & 1) ? pv1 : pv0;
-      uint32_t *ko = (pass & 1) ? zk0 : zk1;
-      uint32_t *vo = (pass & 1) ? pv0 : pv1;
-      if ((e = radix_pass(ki, vi, ko, vo, n_valid, 0, 8 * pass, 8, hist, nsort, st)) != PK_OK) return e;
-    }
-    SrcSorted ss{cnt, pv0};
-    k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
-    k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, maxd, ctr, status);
-    k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, bsum, ctr, offs);
-    const int npass = (p->tile_bits + 7) / 8;
-    uint32_t *vbuf[2] = {(npass & 1) ? dv : sorted_vals, (npass & 1) ? sorted_vals : dv};
-    uint32_t *kbuf[2] = {dk0, dk1};
-    k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pv0, offs, at<uint32_t>(ws, L.rmask), ctr, views,
-                                                        p->N, p->T, p->opts.bin_mode, kbuf[0], vbuf[0]);
-    for (int pass = 0; pass < npass; ++pass) {
-      const int bits = std::min(8, p->tile_bits - 8 * pass);
-      if ((e = radix_pass(kbuf[pass & 1], vbuf[pass & 1], kbuf[(pass + 1) & 1], vbuf[(pass + 1) & 1], &ctr->dups,
-                          0, 8 * pass, bits, hist, nsort, st)) != PK_OK)
-        return e;
-    }
-    k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[npass & 1], ctr, tile_ranges);
-  }
+  if ((e = bin_and_sort_impl(p, L, ws, records, sorted_vals, tile_ranges, maxd, st)) != PK_OK) return e;
+  const DevCounters *ctr = at<DevCounters>(ws, L.counters);
+  const pk_device_status *status = at<pk_device_status>(ws, L.status);
   k_report_entries<<<1, 1, 0, st>>>(ctr, status, n_entries);
   return check_launch();
 }

@@ -229,7 +229,7 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   L.offs = take(sizeof(uint32_t) * pairs);
   L.rmask = take(sizeof(uint32_t) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
-  L.hist = take(sizeof(uint32_t) * kRadix * kSortBlocks);
+  L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);
   L.dval = take(sizeof(uint32_t) * maxd);
