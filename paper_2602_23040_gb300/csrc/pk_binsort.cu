@@ -407,9 +407,8 @@ __global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const 
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort, one pass = upsweep + scan + downsweep.  Digits are
-// up to 8 or up to 11 bits wide (RB); wide digits cut the passes over the
-// (pair, tile) entries at the price of more buckets per pass.
+// Stable LSD radix sort, one pass = upsweep + scan + downsweep, digits of
+// up to RB bits.
 // ---------------------------------------------------------------------------
 
 template <int RB>
@@ -515,7 +514,7 @@ __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist
 }
 
 template <int RB>
-__global__ __launch_bounds__(kThreads, 2) void k_radix_downsweep(
+__global__ __launch_bounds__(kThreads, RB <= 8 ? 3 : 2) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist) {
@@ -733,16 +732,17 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
   return check_launch();
 }
 
-// One stable pass over key bits [shift, shift + bits), bits <= 11.
+// One stable pass over key bits [shift, shift + bits), bits <= 8.  (Wider
+// digits, tried at 11 bits, cut the passes but each pass ran at two blocks
+// per SM with scattered short runs and came out slower overall.)
 pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
                      cudaStream_t st) {
-  if (bits <= 8) return radix_pass_rb<8>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, st);
-  return radix_pass_rb<11>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, st);
+  return radix_pass_rb<kMaxRadixBits>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, st);
 }
 
-// Digit widths for a key of `bits` bits: as few passes of <= 11 bits as
-// possible, split evenly.
+// Digit widths for a key of `bits` bits: as few passes of <= kMaxRadixBits
+// bits as possible, split evenly.
 int radix_plan(int bits, int *widths) {
   const int npass = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
   for (int i = 0, left = bits; i < npass; ++i) {
@@ -773,8 +773,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // sort blocks: 2 resident per SM, within the histogram's capacity
-  const int nsort = std::max(1, std::min(kSortBlocks, 2 * sms));
+  // sort blocks: 3 resident per SM, within the histogram's capacity
+  const int nsort = std::max(1, std::min(kSortBlocks, 3 * sms));
 
   if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
     return PK_ERR_CUDA;
