@@ -13,11 +13,28 @@ using namespace pk;
 
 namespace {
 
+// Index of the value a lane holds after warp_reduce_scatter9 (-1: padding).
+// Level sets [0..4 | 5..8], then slots [0,1,2 | 3,4], [0,1 | 2], [0 | 1].
+__device__ __forceinline__ int reduce_scatter9_index(int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  const int s2 = b2 ? (b1 ? -1 : 2) : (b1 ? 1 : 0);                  // slot in x
+  const int s3 = s2 < 0 ? -1 : (b3 ? (s2 < 2 ? 3 + s2 : -1) : s2);    // slot in w
+  const int s4 = s3 < 0 ? -1 : (b4 ? (s3 < 4 ? 5 + s3 : -1) : s3);    // value index
+  return (lane & 1) ? -1 : s4;
+}
+
+// 1 / x on the MUFU unit (one instruction).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Reduce-scatter of v[0..8] over the 32 lanes.  Level xor-16 splits the
 // nine values 5 | 4, xor-8 splits each half 3 | 2, xor-4 2 | 1, xor-2 1 | 1
-// and xor-1 adds the last pair.  Returns the complete sum held by this lane
-// and its value index in *idx (-1 for lanes left holding padding).
-__device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int lane, int *idx) {
+// and xor-1 adds the last pair.  Returns the complete sum of value
+// reduce_scatter9_index(lane) held by this lane.
+__device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int lane) {
   const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
   float w[5];
 #pragma unroll
@@ -46,11 +63,6 @@ __device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int l
     z = (b1 ? y[1] : y[0]) + r;
   }
   z += __shfl_xor_sync(0xffffffffu, z, 1);
-  // value index held: level sets [0..4 | 5..8], slots [0,1,2 | 3,4], [0,1 | 2], [0 | 1]
-  const int s2 = b2 ? (b1 ? -1 : 2) : (b1 ? 1 : 0);         // slot in x
-  const int s3 = s2 < 0 ? -1 : (b3 ? (s2 < 2 ? 3 + s2 : -1) : s2);  // slot in w
-  const int s4 = s3 < 0 ? -1 : (b4 ? (s3 < 4 ? 5 + s3 : -1) : s3);  // value index
-  *idx = (lane & 1) ? -1 : s4;
   return z;
 }
 
@@ -64,7 +76,7 @@ __device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, 
   Hit h;
   if (!splat_alpha(a, b, c4.z, px, py, h)) return false;
   const float om = __fsub_rn(1.f, h.alpha);
-  const float inv = 1.f / om;
+  const float inv = rcp_approx(om);
   const float Ti = T * inv;
   const float wT = h.alpha * Ti;
   const float da = g0 * (Ti * b.z - S0 * inv) + g1 * (Ti * b.w - S1 * inv) + g2 * (Ti * c4.x - S2 * inv);
@@ -104,6 +116,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
   const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy;
   pixel_of(tid, ox, oy);
+  const int my_idx = reduce_scatter9_index(lane);
   unsigned long long evals = 0;
   for (;;) {
     if (tid == 0) {
@@ -191,9 +204,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
             act |= pixel_adjoint(a, b, c4, px, py1, g10, g11, g12, T1, S10, S11, S12, acc);
           }
           if (__any_sync(0xffffffffu, act)) {
-            int idx;
-            const float sum = warp_reduce_scatter9(acc, lane, &idx);
-            if (idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + idx, sum);
+            const float sum = warp_reduce_scatter9(acc, lane);
+            if (my_idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + my_idx, sum);
           }
         }
       }
