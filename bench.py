@@ -123,6 +123,38 @@ def algorithmic_bytes(plan, texel_bytes, dups, n_dyn):
     }
 
 
+# Sources of each rooflined kernel: the DRAM traffic measured by ncu is
+# reported only while these still hash to the profiled version.
+KERNEL_SOURCES = {
+    "a4_rasterize_fwd": ("k_raster_fwd", ["pk_raster_fwd.cu", "pk_raster.cuh", "pk_common.cuh"]),
+    "a5_rasterize_bwd": ("k_raster_bwd", ["pk_raster_bwd.cu", "pk_raster.cuh", "pk_common.cuh"]),
+}
+
+
+def measured_traffic(stage, dups):
+    """Bytes per launch = ncu bytes per entry (small case) x this launch's entries, or None."""
+    import hashlib
+    if stage not in KERNEL_SOURCES:
+        return None, None
+    kernel, files = KERNEL_SOURCES[stage]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2602_23040_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "traffic_per_entry.md")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as fh:
+        for line in fh:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) == 3 and cells[0] == kernel:
+                if cells[1] != digest:
+                    return None, "kernel changed since its ncu capture"
+                return float(cells[2]) * dups, "ncu C3 4-view capture, bytes per entry x entries"
+    return None, None
+
+
 def launches_per_step(plan):
     npass = (max(1, math.ceil(math.log2(max(2, plan.n_tiles)))) + 7) // 8
     # gather 2, project 1, bin_and_sort 21 + 3 per tile-sort pass, fwd 1, loss 1, bwd 1, scatter 1
@@ -338,8 +370,9 @@ def main():
     if dom in ("a4_rasterize_fwd", "a5_rasterize_bwd"):
         ops = (evals_fwd * OPS_FWD) if dom == "a4_rasterize_fwd" else (evals_bwd * OPS_BWD)
         ach = ops / t_dom / 1e12
+        traffic, tsrc = measured_traffic(dom, dups)
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak_tops, "unit": "TOP/s (FP32)",
-                "frac": ach / alu_peak_tops, "traffic": None,
+                "frac": ach / alu_peak_tops, "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz",
                 "hbm_frac": bytes_alg[dom] / t_dom / 1e9 / hbm}
     else:
