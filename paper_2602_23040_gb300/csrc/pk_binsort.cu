@@ -418,9 +418,6 @@ struct Radix {
   static constexpr int kTile = kThreads * kItems;          // 3072 or 2816 (multiples of 4)
   static constexpr int kCopies = RB <= 8 ? kWarps : 2;     // private histograms in the upsweep
   static constexpr int kPerThread = kR / kThreads;         // buckets per thread in the digit scan
-  // dynamic shared memory of the downsweep
-  static constexpr size_t kSmem = 2 * sizeof(uint32_t) * kR + 2 * sizeof(uint32_t) * kTile +
-                                  sizeof(uint32_t) * (kWarps + 1) + sizeof(uint16_t) * kWarps * kR;
 };
 
 template <int RB>
@@ -513,37 +510,140 @@ __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist
   }
 }
 
+// --- TMA bulk copies into shared memory, completed on an mbarrier ---------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Announce `bytes` of transfers on `bar` (arrival of the issuing thread).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One-dimensional bulk copy global -> shared (16-byte aligned, size a
+// multiple of 16), completing its bytes on `bar`.
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Generic-proxy writes to shared memory before async-proxy (TMA) writes.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Bounded wait: gives up after ~2^22 polls (each poll may block briefly).
+constexpr uint32_t kWaitPolls = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Downsweep with the next tile's keys and values prefetched by TMA into the
+// other half of a double buffer while the current tile is ranked and
+// scattered; the ranking permutes the current tile in place.
 template <int RB>
-__global__ __launch_bounds__(kThreads, RB <= 8 ? 3 : 2) void k_radix_downsweep(
+struct Down {
+  static constexpr int kTile = Radix<RB>::kTile;
+  static constexpr size_t kBuf = 2 * sizeof(uint32_t) * kTile;    // keys + values of one tile
+  static constexpr size_t kSmem = 2 * kBuf + sizeof(uint16_t) * kWarps * Radix<RB>::kR +
+                                  2 * sizeof(uint32_t) * Radix<RB>::kR + sizeof(uint32_t) * (kWarps + 1) +
+                                  2 * sizeof(uint64_t) + 16;
+};
+
+template <int RB>
+__global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist) {
+    const uint32_t *__restrict__ hist, pk_device_status *status) {
   using C = Radix<RB>;
+  constexpr int kTile = C::kTile;
   extern __shared__ __align__(16) unsigned char s_raw[];
-  uint32_t *s_start = reinterpret_cast<uint32_t *>(s_raw);           // [kR]
-  uint32_t *s_gbase = s_start + C::kR;                                // [kR]
-  uint32_t *s_keys = s_gbase + C::kR;                                 // [kTile]
-  uint32_t *s_vals = s_keys + C::kTile;                               // [kTile]
-  uint32_t *s_scan = s_vals + C::kTile;                               // [kWarps + 1]
-  uint16_t *s_wcnt = reinterpret_cast<uint16_t *>(s_scan + kWarps + 1);   // [kWarps][kR]
+  uint32_t *buf[2] = {reinterpret_cast<uint32_t *>(s_raw), reinterpret_cast<uint32_t *>(s_raw + Down<RB>::kBuf)};
+  uint16_t *s_wcnt = reinterpret_cast<uint16_t *>(s_raw + 2 * Down<RB>::kBuf);       // [kWarps][kR]
+  uint32_t *s_start = reinterpret_cast<uint32_t *>(s_wcnt + kWarps * C::kR);         // [kR]
+  uint32_t *s_gbase = s_start + C::kR;                                              // [kR]
+  uint32_t *s_scan = s_gbase + C::kR;                                               // [kWarps + 1]
+  uint64_t *s_bar = reinterpret_cast<uint64_t *>(
+      (reinterpret_cast<uintptr_t>(s_scan + kWarps + 1) + 7) & ~uintptr_t(7));      // [2]
+  __shared__ int s_abort;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
-  chunk_of(n, gridDim.x, blockIdx.x, C::kTile, b0, b1);
+  chunk_of(n, gridDim.x, blockIdx.x, kTile, b0, b1);
   for (int d = tid; d < C::kR; d += kThreads) s_gbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+  const int ntile = (int)((b1 - b0 + kTile - 1) / kTile);
+  // the bulk-copied part of tile t: its first multiple of 4 keys
+  auto issue = [&](int t) {
+    const uint64_t base = b0 + (uint64_t)t * kTile;
+    const uint32_t valid = (uint32_t)min((uint64_t)kTile, b1 - base);
+    const uint32_t bytes = (valid & ~3u) * 4u;
+    uint32_t *dst = buf[t & 1];
+    mbar_expect_tx(&s_bar[t & 1], 2 * bytes);
+    if (bytes) {
+      tma_load_1d(dst, kin + base, bytes, &s_bar[t & 1]);
+      tma_load_1d(dst + kTile, vin + base, bytes, &s_bar[t & 1]);
+    }
+  };
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (ntile > 0) issue(0);
+  }
+  __syncthreads();
   const uint32_t lt = lanemask_lt();
   uint16_t *wc = s_wcnt + warp * C::kR;
-  for (uint64_t base = b0; base < b1; base += C::kTile) {
-    const uint32_t valid = (uint32_t)min((uint64_t)C::kTile, b1 - base);
+  uint32_t parity[2] = {0u, 0u};
+  for (int t = 0; t < ntile; ++t) {
+    const int cur = t & 1;
+    const uint64_t base = b0 + (uint64_t)t * kTile;
+    const uint32_t valid = (uint32_t)min((uint64_t)kTile, b1 - base);
+    uint32_t *bk = buf[cur], *bv = buf[cur] + kTile;
+    // the other buffer was last written (by this block's scatter) before the
+    // fence and barrier that ended the previous tile
+    if (tid == 0 && t + 1 < ntile) issue(t + 1);
+    const bool ok = mbar_wait_bounded(&s_bar[cur], parity[cur]);
+    // keys past the last multiple of 4 come by plain loads
+    const uint32_t tail0 = valid & ~3u;
+    if (tid < (int)(valid - tail0)) {
+      bk[tail0 + tid] = __ldg(kin + base + tail0 + tid);
+      bv[tail0 + tid] = __ldg(vin + base + tail0 + tid);
+    }
     for (int i = tid; i < kWarps * C::kR / 2; i += kThreads) reinterpret_cast<uint32_t *>(s_wcnt)[i] = 0;
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        s_abort = 1;
+        // copies in flight: tile t (not yet arrived) and tile t + 1 if issued
+        mbar_wait_bounded(&s_bar[cur], parity[cur]);
+        if (t + 1 < ntile) mbar_wait_bounded(&s_bar[cur ^ 1], parity[cur ^ 1]);
+      }
+      break;
+    }
+    parity[cur] ^= 1u;
     // stable warp-level ranking: items in (warp, item, lane) order
     uint32_t key[C::kItems], rank[C::kItems];
 #pragma unroll
     for (int j = 0; j < C::kItems; ++j) {
       const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);
       const bool in = li < valid;
-      key[j] = in ? __ldg(kin + base + li) : 0xffffffffu;
+      key[j] = in ? bk[li] : 0xffffffffu;
       const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(C::kR - 1);
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       const uint32_t before = __popc(peers & lt);
@@ -577,6 +677,13 @@ __global__ __launch_bounds__(kThreads, RB <= 8 ? 3 : 2) void k_radix_downsweep(
       s_start[tid * C::kPerThread + u] = run;
       run += dcount[u];
     }
+    // values of this thread's items, read before the in-place permutation
+    uint32_t val[C::kItems];
+#pragma unroll
+    for (int j = 0; j < C::kItems; ++j) {
+      const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);
+      val[j] = li < valid ? bv[li] : 0u;
+    }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < C::kItems; ++j) {
@@ -584,22 +691,24 @@ __global__ __launch_bounds__(kThreads, RB <= 8 ? 3 : 2) void k_radix_downsweep(
       const bool in = li < valid;
       const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(C::kR - 1);
       const uint32_t r = s_start[d] + wc[d] + rank[j];
-      s_keys[r] = key[j];
-      s_vals[r] = in ? __ldg(vin + base + li) : 0u;
+      bk[r] = key[j];
+      bv[r] = val[j];
     }
     __syncthreads();
     for (uint32_t i = tid; i < valid; i += kThreads) {
-      const uint32_t k = s_keys[i];
+      const uint32_t k = bk[i];
       const uint32_t d = (k >> shift) & mask;
       const uint32_t o = s_gbase[d] + (i - s_start[d]);
       kout[o] = k;
-      vout[o] = s_vals[i];
+      vout[o] = bv[i];
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < C::kPerThread; ++u) s_gbase[tid * C::kPerThread + u] += dcount[u];
+    fence_proxy_async();   // this buffer's generic writes before the next TMA into it
     __syncthreads();
   }
+  if (s_abort && tid == 0) atomicOr(&status->flags, PK_DEV_TIMEOUT);
 }
 
 // ---------------------------------------------------------------------------
@@ -719,16 +828,16 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
 template <int RB>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                        cudaStream_t st) {
+                        pk_device_status *status, cudaStream_t st) {
   using C = Radix<RB>;
-  if (cudaFuncSetAttribute(k_radix_downsweep<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(k_radix_downsweep<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Down<RB>::kSmem) != cudaSuccess)
     return PK_ERR_CUDA;
   const uint32_t mask = (1u << bits) - 1u;
   k_radix_upsweep<RB><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist);
   k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
-  k_radix_downsweep<RB><<<nblocks, kThreads, C::kSmem, st>>>(kin, vin, kout, vout, n_dev, n_host, shift, mask,
-                                                               hist);
+  k_radix_downsweep<RB><<<nblocks, kThreads, Down<RB>::kSmem, st>>>(kin, vin, kout, vout, n_dev, n_host, shift,
+                                                                      mask, hist, status);
   return check_launch();
 }
 
@@ -737,8 +846,8 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 // per SM with scattered short runs and came out slower overall.)
 pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                     cudaStream_t st) {
-  return radix_pass_rb<kMaxRadixBits>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, st);
+                     pk_device_status *status, cudaStream_t st) {
+  return radix_pass_rb<kMaxRadixBits>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, st);
 }
 
 // Digit widths for a key of `bits` bits: as few passes of <= kMaxRadixBits
@@ -794,7 +903,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int np = radix_plan(32, widths), shift = 0;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
-    if ((e = radix_pass(zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist, nsort, st)) != PK_OK)
+    if ((e = radix_pass(zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist, nsort, status, st)) !=
+        PK_OK)
       return e;
     shift += widths[pass];
   }
@@ -813,8 +923,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   shift = 0;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
-    if ((e = radix_pass(kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nsort, st)) !=
-        PK_OK)
+    if ((e = radix_pass(kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nsort, status,
+                        st)) != PK_OK)
       return e;
     shift += widths[pass];
   }
@@ -827,7 +937,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
 extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
                                      uint32_t *tile_ranges, void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !ws) return PK_ERR_ARG;
-  if (!aligned16(records)) return PK_ERR_ARG;
+  if (!aligned16(records) || !aligned16(sorted_vals) || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PK_ERR_ARG;
   return bin_and_sort_impl(p, p->ws, ws, records, sorted_vals, tile_ranges, p->max_dups,
                            reinterpret_cast<cudaStream_t>(stream));
 }
@@ -880,7 +990,7 @@ __global__ void k_report_entries(const DevCounters *ctr, const pk_device_status 
 extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *records, uint32_t *sorted_vals,
                                              uint32_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !n_entries) return PK_ERR_ARG;
-  if (!aligned16(records)) return PK_ERR_ARG;
+  if (!aligned16(records) || !aligned16(sorted_vals)) return PK_ERR_ARG;
   // layout of this plan's scratch inside the static array
   const uint64_t pairs = (uint64_t)p->pairs, maxd = p->max_dups;
   WsLayout L{};
