@@ -76,6 +76,9 @@ def _declare(L):
         "or_render_bwd": (None, [P, C.c_int, I64, P, C.c_int, P, P, P, P, P]),
         "or_scatter_grad": (None, [P, I64, I64, C.c_int, C.c_int, P, C.c_int, DBL, P, P, P]),
         "or_render_pixels": (None, [P, C.c_int, I64, P, C.c_int, P, DBL, I64, P, P, P, P]),
+        "or_motion_mask": (None, [P, C.c_int, C.c_int, C.c_float, C.c_int, P]),
+        "or_dynamic_mask32": (None, [P, C.c_int, I64, P, P, P, C.c_float, P]),
+        "or_dynamic_mask": (None, [P, C.c_int, I64, P, P, P, DBL, DBL, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -270,6 +273,63 @@ def render_pixels(rec, views_arr, tile, pix, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
     lib().or_render_pixels(_p(np.ascontiguousarray(rec)), V, N, _p(np.ascontiguousarray(views_arr)), tile,
                            _p(np.ascontiguousarray(bg, np.float64)), m_tol, n, _p(pix), _p(rgb), _p(T), _p(border))
     return rgb, T, border
+
+
+# --------------------------------------------------------------------------
+# Motion masks and the dynamic mask
+# --------------------------------------------------------------------------
+
+def motion_mask(flow, tau, r):
+    """One view: flow [2][H][W] float32 -> mask [H][W] uint8 (0/1)."""
+    flow = np.ascontiguousarray(flow, np.float32)
+    _, H, W = flow.shape
+    M = np.zeros((H, W), np.uint8)
+    lib().or_motion_mask(_p(flow), W, H, float(tau), int(r), _p(M))
+    return M
+
+
+def motion_masks(flow_flat, views_arr, tau, r):
+    """All views: flow concatenated as [V][2][H_v][W_v] -> masks concatenated [P] uint8."""
+    out, off = [], 0
+    for v in range(views_arr.shape[0]):
+        W, H = int(views_arr[v, 16]), int(views_arr[v, 17])
+        out.append(motion_mask(np.asarray(flow_flat[off:off + 2 * W * H]).reshape(2, H, W), tau, r).reshape(-1))
+        off += 2 * W * H
+    return np.concatenate(out)
+
+
+def dynamic_mask32(rec32, views_arr, masks, r_max=0.0):
+    """FP32 stage on float32 records [V*N][12] -> D [N] uint8."""
+    V = views_arr.shape[0]
+    rec32 = np.ascontiguousarray(rec32, np.float32).reshape(-1, REC)
+    N = rec32.shape[0] // V
+    vw = np.ascontiguousarray(views_arr[:, 16], np.int32)
+    vh = np.ascontiguousarray(views_arr[:, 17], np.int32)
+    D = np.zeros(N, np.uint8)
+    lib().or_dynamic_mask32(_p(rec32), V, N, _p(vw), _p(vh), _p(np.ascontiguousarray(masks, np.uint8)),
+                            float(r_max), _p(D))
+    return D
+
+
+def dynamic_mask(rec, views_arr, masks, r_max=0.0, m_tol=5e-4):
+    """FP64 on the oracle's records [V][N][12] -> (D [N], border [N]) uint8."""
+    V, N, _ = rec.shape
+    vw = np.ascontiguousarray(views_arr[:, 16], np.int32)
+    vh = np.ascontiguousarray(views_arr[:, 17], np.int32)
+    D = np.zeros(N, np.uint8)
+    border = np.zeros(N, np.uint8)
+    lib().or_dynamic_mask(_p(np.ascontiguousarray(rec)), V, N, _p(vw), _p(vh),
+                          _p(np.ascontiguousarray(masks, np.uint8)), float(r_max), m_tol, _p(D), _p(border))
+    return D, border
+
+
+def dynamic_mask_scene(scene, masks, r_max=0.0, znear=ZNEAR, m_tol=5e-4):
+    """Gather, project (FP64) and mask: D and border per live texel, in gather order."""
+    soa, texel, _ = gather(scene)
+    va = views_array(scene.views)
+    rec = project(soa, len(texel), scene.sh_degree, va, znear)
+    D, border = dynamic_mask(rec, va, masks, r_max, m_tol)
+    return D, border, texel, rec
 
 
 # --------------------------------------------------------------------------

@@ -34,6 +34,12 @@
  *   or_scatter_grad    "Objective": gradients of the photometric loss flow
  *                      to every attribute) and gradient freezing
  *                      grad_i <- D_i grad_i (Sec. 4.2 "Gradient Freezing")
+ *   or_motion_mask     Sec. 4.2 "Optical Flow and Binary Motion Masks"
+ *                      (flow magnitude above tau, then dilation)
+ *   or_dynamic_mask,   Sec. 4.2 "Covariance-Aware Gaussian Masking" and
+ *   or_dynamic_mask32  Alg. 1 step 5: a Gaussian is dynamic if a masked
+ *                      pixel of some view lies in its d^2 <= 9 ellipse,
+ *                      OR-ed over the views
  *
  * Where the paper is silent the readings are: 3DGS conventions for the
  * opacity sigmoid, the +0.5 SH offset and the clamp of colour at 0; alpha
@@ -972,4 +978,144 @@ void or_render_pixels(const double *rec, int V, int64_t N, const double *views, 
   }
   free(e);
   free(vals);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Motion masks and the covariance-aware dynamic mask                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Binary motion mask of one view (Sec. 4.2 "Optical Flow and Binary Motion
+ * Masks"): a pixel is moving when the magnitude of its flow vector exceeds
+ * tau; the mask is then dilated with radius r.  Readings: the magnitude and
+ * the comparison are taken in FP32, the flow's own precision, as
+ * sqrtf(fx * fx + fy * fy) > tau; the dilation's structuring element is the
+ * (2r+1) x (2r+1) square and pixels outside the image count as still.
+ * flow: [2][H][W] (x component plane, then y); M: out [H][W], 0 or 1.
+ */
+void or_motion_mask(const float *flow, int W, int H, float tau, int r, uint8_t *M) {
+  const int64_t plane = (int64_t)W * H;
+  uint8_t *raw = (uint8_t *)malloc(plane > 0 ? (size_t)plane : 1);
+  for (int64_t i = 0; i < plane; ++i) {
+    float fx = flow[i], fy = flow[plane + i];
+    float mag = sqrtf(fx * fx + fy * fy);
+    raw[i] = mag > tau;
+  }
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      int on = 0;
+      for (int dy = -r; dy <= r && !on; ++dy) {
+        int yy = y + dy;
+        if (yy < 0 || yy >= H) continue;
+        for (int dx = -r; dx <= r; ++dx) {
+          int xx = x + dx;
+          if (xx >= 0 && xx < W && raw[(int64_t)yy * W + xx]) {
+            on = 1;
+            break;
+          }
+        }
+      }
+      M[(int64_t)y * W + x] = (uint8_t)on;
+    }
+  free(raw);
+}
+
+/*
+ * Dynamic mask from FP32 projected records (Alg. 1 step 5 and the OR over
+ * cameras of Sec. 4.2 "Covariance-Aware Gaussian Masking").  rec: [V*N][12]
+ * float records {m_x, m_y, a, b, c, opacity, z, radius, ...} with conic
+ * [[a, b], [b, c]] and radius 0 for a culled pair; M: the views' motion
+ * masks concatenated, [sum_v H_v W_v] bytes.  D_g = 1 iff in some view v a
+ * pixel (x, y) of the square |centre - m|_inf <= r, r = min(r_max, radius)
+ * (r_max <= 0: no clamp), lies in the image, has M_v = 1 and
+ * d^2 = (p - m)^T conic (p - m) <= 9 at its centre p = (x + 0.5, y + 0.5).
+ * Square and d^2 in FP32, in exactly this order, no fused multiply-add:
+ *   x_lo = ceil((m_x - 0.5) - r), x_hi = floor((m_x - 0.5) + r) (same in y),
+ *   clamped to the image;
+ *   d^2 = ((a dx) dx + (c dy) dy) + ((2 b) dy) dx, dx = (x + 0.5) - m_x.
+ */
+void or_dynamic_mask32(const float *rec, int V, int64_t N, const int32_t *vw, const int32_t *vh,
+                       const uint8_t *M, float r_max, uint8_t *D) {
+  memset(D, 0, (size_t)(N > 0 ? N : 0));
+  int64_t poff = 0;
+  for (int v = 0; v < V; ++v) {
+    const int W = vw[v], H = vh[v];
+    const uint8_t *Mv = M + poff;
+    for (int64_t g = 0; g < N; ++g) {
+      if (D[g]) continue;
+      const float *r = rec + ((int64_t)v * N + g) * OR_REC;
+      float rad = r[R_RAD];
+      if (!(rad > 0.0f)) continue;
+      if (r_max > 0.0f && rad > r_max) rad = r_max;
+      float mx = r[R_MX], my = r[R_MY], a = r[R_CA], b = r[R_CB], c = r[R_CC];
+      if (!isfinite(mx) || !isfinite(my)) continue;
+      float ax = mx - 0.5f, ay = my - 0.5f;
+      float lox = fmaxf(ceilf(ax - rad), 0.0f), hix = fminf(floorf(ax + rad), (float)(W - 1));
+      float loy = fmaxf(ceilf(ay - rad), 0.0f), hiy = fminf(floorf(ay + rad), (float)(H - 1));
+      if (!(lox <= hix) || !(loy <= hiy)) continue;
+      const float b2 = 2.0f * b;
+      for (int y = (int)loy; y <= (int)hiy && !D[g]; ++y) {
+        float dy = ((float)y + 0.5f) - my;
+        float cyy = (c * dy) * dy;
+        float bdy = b2 * dy;
+        for (int x = (int)lox; x <= (int)hix; ++x) {
+          if (!Mv[(int64_t)y * W + x]) continue;
+          float dx = ((float)x + 0.5f) - mx;
+          float q = ((a * dx) * dx + cyy) + bdy * dx;
+          if (q <= 9.0f) {
+            D[g] = 1;
+            break;
+          }
+        }
+      }
+    }
+    poff += (int64_t)W * H;
+  }
+}
+
+/*
+ * The same mask in FP64 from the oracle's own records (or_project), taking
+ * Alg. 1 step 5 literally.  border[g] = 1 when a finite-precision
+ * evaluation could decide D_g differently: a pair near a culling cutoff, a
+ * masked pixel whose d^2 lies within the error bound of 9 (the bound of the
+ * compositing rule: a shift of the mean by m_tol pixels, plus relative
+ * 1e-5), or, with the clamp active, a masked pixel in the footprint whose
+ * centre lies within 1e-3 px of the clamped square's edge.
+ */
+void or_dynamic_mask(const double *rec, int V, int64_t N, const int32_t *vw, const int32_t *vh,
+                     const uint8_t *M, double r_max, double m_tol, uint8_t *D, uint8_t *border) {
+  memset(D, 0, (size_t)(N > 0 ? N : 0));
+  memset(border, 0, (size_t)(N > 0 ? N : 0));
+  int64_t poff = 0;
+  for (int v = 0; v < V; ++v) {
+    const int W = vw[v], H = vh[v];
+    const uint8_t *Mv = M + poff;
+    for (int64_t g = 0; g < N; ++g) {
+      const double *r = rec + ((int64_t)v * N + g) * OR_REC;
+      if (((uint32_t)r[R_FLAGS]) & F_CULL_NEAR) border[g] = 1;
+      double rad = r[R_RAD];
+      if (!(rad > 0.0)) continue;
+      int clamp = r_max > 0.0 && rad > r_max;
+      if (clamp) rad = r_max;
+      double mx = r[R_MX], my = r[R_MY], a = r[R_CA], b = r[R_CB], c = r[R_CC];
+      /* scan one pixel beyond the square when clamped, for the edge rule */
+      double grow = clamp ? 1.0 : 0.0;
+      double lox = fmax(ceil(mx - 0.5 - rad - grow), 0.0), hix = fmin(floor(mx - 0.5 + rad + grow), W - 1.0);
+      double loy = fmax(ceil(my - 0.5 - rad - grow), 0.0), hiy = fmin(floor(my - 0.5 + rad + grow), H - 1.0);
+      for (int y = (int)loy; y <= (int)hiy; ++y)
+        for (int x = (int)lox; x <= (int)hix; ++x) {
+          if (!Mv[(int64_t)y * W + x]) continue;
+          double dx = x + 0.5 - mx, dy = y + 0.5 - my;
+          double q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;
+          double gq = 2.0 * sqrt((a * dx + b * dy) * (a * dx + b * dy) + (b * dx + c * dy) * (b * dx + c * dy));
+          double dq = gq * m_tol + 1e-5 * fabs(q) + 1e-6;
+          int inside = fabs(dx) <= rad && fabs(dy) <= rad;
+          if (fabs(q - Q_MAX) <= dq) border[g] = 1;
+          if (clamp && q <= Q_MAX + dq && (fabs(fabs(dx) - rad) <= 1e-3 || fabs(fabs(dy) - rad) <= 1e-3))
+            border[g] = 1;
+          if (inside && q <= Q_MAX) D[g] = 1;
+        }
+    }
+    poff += (int64_t)W * H;
+  }
 }

@@ -15,6 +15,7 @@ from .scenes import (  # noqa: F401
     config_scene,
     look_at,
     random_target,
+    motion_flow,
     pack_bits,
     channel_count,
 )

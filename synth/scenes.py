@@ -285,6 +285,36 @@ def config_scene(k: int, n_views: Optional[int] = None, frame_start: int = 0) ->
     return sc
 
 
+def motion_flow(views: Sequence[View], seed: int = BASE_SEED + 77, blobs: int = 3, cover: float = 0.15,
+                amp: float = 4.0, noise: float = 0.3) -> np.ndarray:
+    """Synthetic optical-flow fields standing in for the per-camera flow maps.
+
+    Per view, ``blobs`` moving regions at random places in the image (each a
+    Gaussian bump of peak magnitude ``amp`` pixels along a random direction,
+    sized so that together they cover about ``cover`` of the image), plus
+    i.i.d. N(0, ``noise``^2) flow on every component.  Returned concatenated
+    in view order, each view planar ``[2][H][W]`` (x component, then y), as
+    one flat float32 array.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for v in views:
+        W, H = v.width, v.height
+        f = rng.normal(0.0, noise, size=(2, H, W)).astype(np.float32)
+        rho = math.sqrt(cover * W * H / (blobs * math.pi))
+        ys = np.arange(H, dtype=np.float32)[:, None] + 0.5
+        xs = np.arange(W, dtype=np.float32)[None, :] + 0.5
+        for _ in range(blobs):
+            cx, cy = rng.uniform(0.15, 0.85) * W, rng.uniform(0.15, 0.85) * H
+            ang = rng.uniform(0.0, 2.0 * math.pi)
+            sig = rho / 1.5
+            bump = (amp * np.exp(-((xs - cx) ** 2 + (ys - cy) ** 2) / (2.0 * sig * sig))).astype(np.float32)
+            f[0] += bump * np.float32(math.cos(ang))
+            f[1] += bump * np.float32(math.sin(ang))
+        out.append(f.reshape(-1))
+    return np.concatenate(out) if out else np.zeros(0, np.float32)
+
+
 def random_target(scene: Scene, seed: int = BASE_SEED + 99) -> np.ndarray:
     """U[0,1] target images, concatenated planar ``[V][3][H][W]`` as one flat float32 array."""
     rng = np.random.default_rng(seed)
