@@ -79,6 +79,9 @@ def _declare(L):
         "or_motion_mask": (None, [P, C.c_int, C.c_int, C.c_float, C.c_int, P]),
         "or_dynamic_mask32": (None, [P, C.c_int, I64, P, P, P, C.c_float, P]),
         "or_dynamic_mask": (None, [P, C.c_int, I64, P, P, P, DBL, DBL, P, P]),
+        "or_lpo_minmax": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]),
+        "or_lpo_encode": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
+        "or_lpo_decode": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -330,6 +333,40 @@ def dynamic_mask_scene(scene, masks, r_max=0.0, znear=ZNEAR, m_tol=5e-4):
     rec = project(soa, len(texel), scene.sh_degree, va, znear)
     D, border = dynamic_mask(rec, va, masks, r_max, m_tol)
     return D, border, texel, rec
+
+
+# --------------------------------------------------------------------------
+# Low-precision proxy
+# --------------------------------------------------------------------------
+
+def lpo_minmax(atlas, occ):
+    """atlas [F][D][H][W] float32 -> lohi [D][2] float32 over live texels."""
+    atlas = np.ascontiguousarray(atlas, np.float32)
+    F, D, H, W = atlas.shape
+    lohi = np.zeros((D, 2), np.float32)
+    lib().or_lpo_minmax(_p(atlas), F, D, H, W, _p(np.ascontiguousarray(occ, np.uint32)), _p(lohi))
+    return lohi
+
+
+def lpo_encode(atlas, occ, lohi):
+    """-> codes [F][D+3][H][W] uint8."""
+    atlas = np.ascontiguousarray(atlas, np.float32)
+    F, D, H, W = atlas.shape
+    codes = np.zeros((F, D + 3, H, W), np.uint8)
+    lib().or_lpo_encode(_p(atlas), F, D, H, W, _p(np.ascontiguousarray(occ, np.uint32)),
+                        _p(np.ascontiguousarray(lohi, np.float32)), _p(codes))
+    return codes
+
+
+def lpo_decode(codes, occ, lohi):
+    """codes [F][D+3][H][W] -> proxy atlas [F][D][H][W] float32."""
+    codes = np.ascontiguousarray(codes, np.uint8)
+    F, NP, H, W = codes.shape
+    D = NP - 3
+    proxy = np.zeros((F, D, H, W), np.float32)
+    lib().or_lpo_decode(_p(codes), F, D, H, W, _p(np.ascontiguousarray(occ, np.uint32)),
+                        _p(np.ascontiguousarray(lohi, np.float32)), _p(proxy))
+    return proxy
 
 
 # --------------------------------------------------------------------------

@@ -40,6 +40,11 @@
  *   or_dynamic_mask32  Alg. 1 step 5: a Gaussian is dynamic if a masked
  *                      pixel of some view lies in its d^2 <= 9 ellipse,
  *                      OR-ed over the views
+ *   or_lpo_minmax,     Sec. 4.2 "Low Precision Optimization" and Supp.
+ *   or_lpo_encode,     "Video Coding": per-channel min/max normalisation,
+ *   or_lpo_decode      uniform 16-bit (position, as two 8-bit planes) and
+ *                      8-bit (all other channels) quantisation, proxy
+ *                      lo + q Delta
  *
  * Where the paper is silent the readings are: 3DGS conventions for the
  * opacity sigmoid, the +0.5 SH offset and the clamp of colour at 0; alpha
@@ -1076,14 +1081,17 @@ void or_dynamic_mask32(const float *rec, int V, int64_t N, const int32_t *vw, co
 /*
  * The same mask in FP64 from the oracle's own records (or_project), taking
  * Alg. 1 step 5 literally.  border[g] = 1 when a finite-precision
- * evaluation could decide D_g differently: a pair near a culling cutoff, a
- * masked pixel whose d^2 lies within the error bound of 9 (the bound of the
- * compositing rule: a shift of the mean by m_tol pixels, plus relative
- * 1e-5), or, with the clamp active, a masked pixel in the footprint whose
- * centre lies within 1e-3 px of the clamped square's edge.
+ * evaluation could decide D_g differently: D_g is an OR, so that needs a
+ * shaky pixel -- a masked pixel whose d^2 lies within the error bound of 9
+ * (the bound of the compositing rule: a shift of the mean by m_tol pixels,
+ * plus relative 1e-5), a masked footprint pixel within 1e-3 px of the
+ * clamped square's edge, or any masked footprint pixel of a pair near a
+ * culling cutoff -- and no firm hit anywhere else (a masked pixel clear of
+ * all three, inside the footprint).
  */
 void or_dynamic_mask(const double *rec, int V, int64_t N, const int32_t *vw, const int32_t *vh,
                      const uint8_t *M, double r_max, double m_tol, uint8_t *D, uint8_t *border) {
+  uint8_t *firm = (uint8_t *)calloc((size_t)(N > 0 ? N : 1), 1);
   memset(D, 0, (size_t)(N > 0 ? N : 0));
   memset(border, 0, (size_t)(N > 0 ? N : 0));
   int64_t poff = 0;
@@ -1092,9 +1100,13 @@ void or_dynamic_mask(const double *rec, int V, int64_t N, const int32_t *vw, con
     const uint8_t *Mv = M + poff;
     for (int64_t g = 0; g < N; ++g) {
       const double *r = rec + ((int64_t)v * N + g) * OR_REC;
-      if (((uint32_t)r[R_FLAGS]) & F_CULL_NEAR) border[g] = 1;
+      const int near_cull = (((uint32_t)r[R_FLAGS]) & F_CULL_NEAR) != 0;
       double rad = r[R_RAD];
-      if (!(rad > 0.0)) continue;
+      if (!(rad > 0.0)) {
+        /* culled here, possibly valid in FP32: any masked pixel may count */
+        if (near_cull) border[g] = 1;
+        continue;
+      }
       int clamp = r_max > 0.0 && rad > r_max;
       if (clamp) rad = r_max;
       double mx = r[R_MX], my = r[R_MY], a = r[R_CA], b = r[R_CB], c = r[R_CC];
@@ -1110,12 +1122,122 @@ void or_dynamic_mask(const double *rec, int V, int64_t N, const int32_t *vw, con
           double gq = 2.0 * sqrt((a * dx + b * dy) * (a * dx + b * dy) + (b * dx + c * dy) * (b * dx + c * dy));
           double dq = gq * m_tol + 1e-5 * fabs(q) + 1e-6;
           int inside = fabs(dx) <= rad && fabs(dy) <= rad;
-          if (fabs(q - Q_MAX) <= dq) border[g] = 1;
+          int shaky = fabs(q - Q_MAX) <= dq;
           if (clamp && q <= Q_MAX + dq && (fabs(fabs(dx) - rad) <= 1e-3 || fabs(fabs(dy) - rad) <= 1e-3))
-            border[g] = 1;
-          if (inside && q <= Q_MAX) D[g] = 1;
+            shaky = 1;
+          if (near_cull && q <= Q_MAX + dq) shaky = 1;
+          if (shaky) border[g] = 1;
+          if (inside && q <= Q_MAX) {
+            D[g] = 1;
+            if (!shaky) firm[g] = 1;
+          }
         }
     }
     poff += (int64_t)W * H;
   }
+  for (int64_t g = 0; g < N; ++g)
+    if (firm[g]) border[g] = 0;
+  free(firm);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Low-precision proxy (LPO) and the 8-bit plane layout                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Sec. 4.2 "Low Precision Optimization" and Supp. "Video Coding": every
+ * attribute channel is normalised by its min/max over the live texels of
+ * all frames and quantised uniformly to K bits with scale
+ * Delta = (hi - lo) / (2^K - 1); K = 16 for the three position channels,
+ * each kept as two 8-bit planes (high byte, then low byte), and K = 8 for
+ * scale, rotation, opacity and colour.  The renderer reads the proxy
+ * lo + q Delta.  Readings: q = floor((x - lo) / Delta + 0.5) clamped to
+ * [0, 2^K - 1], and q = 0 when that is not a number (hi == lo, or x NaN);
+ * min/max skip NaN texels and are 0 when no texel is live; every step in
+ * FP32, IEEE-rounded, in exactly this order.  Plane p of a frame holds
+ * channel p / 2's high (p even) or low byte for p < 6, channel p - 3
+ * otherwise: D + 3 planes per frame, [F][D + 3][H][W] bytes, 0 at texels
+ * that are not live.
+ */
+static int lpo_bits(int c) { return c < 3 ? 16 : 8; }
+
+void or_lpo_minmax(const float *atlas, int F, int D, int H, int W, const uint32_t *occ, float *lohi) {
+  const int Wp = (W + 31) / 32;
+  for (int c = 0; c < D; ++c) {
+    int any = 0;
+    float lo = 0.0f, hi = 0.0f;
+    for (int f = 0; f < F; ++f)
+      for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+          if (!bit_at(occ, Wp, x, y)) continue;
+          float v = atlas[(((int64_t)f * D + c) * H + y) * W + x];
+          if (v != v) continue;
+          if (!any || v < lo) lo = v;
+          if (!any || v > hi) hi = v;
+          any = 1;
+        }
+    lohi[2 * c] = lo;
+    lohi[2 * c + 1] = hi;
+  }
+}
+
+static float lpo_delta(const float *lohi, int c) {
+  const float L = (float)((1u << lpo_bits(c)) - 1u);
+  return (lohi[2 * c + 1] - lohi[2 * c]) / L;
+}
+
+static uint32_t lpo_code(float x, float lo, float delta, int bits) {
+  const float L = (float)((1u << bits) - 1u);
+  float t = (x - lo) / delta;
+  float u = floorf(t + 0.5f);
+  if (!(u >= 0.0f)) return 0u;
+  if (u >= L) return (uint32_t)L;
+  return (uint32_t)u;
+}
+
+void or_lpo_encode(const float *atlas, int F, int D, int H, int W, const uint32_t *occ, const float *lohi,
+                   uint8_t *codes) {
+  const int Wp = (W + 31) / 32, NP = D + 3;
+  const int64_t plane = (int64_t)W * H;
+  memset(codes, 0, (size_t)((int64_t)F * NP * plane));
+  for (int f = 0; f < F; ++f)
+    for (int c = 0; c < D; ++c) {
+      const float lo = lohi[2 * c], delta = lpo_delta(lohi, c);
+      for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+          if (!bit_at(occ, Wp, x, y)) continue;
+          const int64_t px = (int64_t)y * W + x;
+          uint32_t q = lpo_code(atlas[((int64_t)f * D + c) * plane + px], lo, delta, lpo_bits(c));
+          if (c < 3) {
+            codes[((int64_t)f * NP + 2 * c) * plane + px] = (uint8_t)(q >> 8);
+            codes[((int64_t)f * NP + 2 * c + 1) * plane + px] = (uint8_t)(q & 255u);
+          } else {
+            codes[((int64_t)f * NP + c + 3) * plane + px] = (uint8_t)q;
+          }
+        }
+    }
+}
+
+/* Codes back to the proxy atlas [F][D][H][W] float32 (0 where not live). */
+void or_lpo_decode(const uint8_t *codes, int F, int D, int H, int W, const uint32_t *occ, const float *lohi,
+                   float *proxy) {
+  const int Wp = (W + 31) / 32, NP = D + 3;
+  const int64_t plane = (int64_t)W * H;
+  memset(proxy, 0, sizeof(float) * (size_t)((int64_t)F * D * plane));
+  for (int f = 0; f < F; ++f)
+    for (int c = 0; c < D; ++c) {
+      const float lo = lohi[2 * c], delta = lpo_delta(lohi, c);
+      for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+          if (!bit_at(occ, Wp, x, y)) continue;
+          const int64_t px = (int64_t)y * W + x;
+          uint32_t q;
+          if (c < 3)
+            q = ((uint32_t)codes[((int64_t)f * NP + 2 * c) * plane + px] << 8) |
+                codes[((int64_t)f * NP + 2 * c + 1) * plane + px];
+          else
+            q = codes[((int64_t)f * NP + c + 3) * plane + px];
+          proxy[((int64_t)f * D + c) * plane + px] = lo + (float)q * delta;
+        }
+    }
 }

@@ -16,6 +16,7 @@ from .scenes import (  # noqa: F401
     look_at,
     random_target,
     motion_flow,
+    actor_sphere,
     pack_bits,
     channel_count,
 )

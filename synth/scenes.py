@@ -285,32 +285,53 @@ def config_scene(k: int, n_views: Optional[int] = None, frame_start: int = 0) ->
     return sc
 
 
-def motion_flow(views: Sequence[View], seed: int = BASE_SEED + 77, blobs: int = 3, cover: float = 0.15,
-                amp: float = 4.0, noise: float = 0.3) -> np.ndarray:
+def actor_sphere(scene: Scene, frac: float = 0.3, seed: int = BASE_SEED + 76):
+    """A moving "actor": a sphere around a random centre in [-0.5, 0.5]^3
+    holding ``frac`` of the live Gaussians' frame-0 means."""
+    rng = np.random.default_rng(seed)
+    centre = rng.uniform(-0.5, 0.5, size=3)
+    ys, xs = np.nonzero(unpack_bits(scene.occ, scene.atlas.shape[3]))
+    mu = scene.atlas[0, 0:3][:, ys, xs].astype(np.float64).T
+    radius = float(np.quantile(np.linalg.norm(mu - centre, axis=1), frac)) if len(mu) else 0.1
+    return centre, radius
+
+
+def motion_flow(views: Sequence[View], centre, radius: float, seed: int = BASE_SEED + 77, amp: float = 4.0,
+                noise: float = 0.2) -> np.ndarray:
     """Synthetic optical-flow fields standing in for the per-camera flow maps.
 
-    Per view, ``blobs`` moving regions at random places in the image (each a
-    Gaussian bump of peak magnitude ``amp`` pixels along a random direction,
-    sized so that together they cover about ``cover`` of the image), plus
-    i.i.d. N(0, ``noise``^2) flow on every component.  Returned concatenated
-    in view order, each view planar ``[2][H][W]`` (x component, then y), as
-    one flat float32 array.
+    The moving region of each view is the silhouette of the actor sphere
+    (``centre``, ``radius``): pixels whose viewing ray passes within
+    ``radius`` of the centre.  There the flow has magnitude
+    ``amp * sqrt(1 - dist^2 / radius^2)`` along a random direction per view;
+    every component also carries i.i.d. N(0, ``noise``^2) flow.  Returned
+    concatenated in view order, each view planar ``[2][H][W]`` (x component,
+    then y), as one flat float32 array.
     """
     rng = np.random.default_rng(seed)
+    centre = np.asarray(centre, np.float64)
     out = []
     for v in views:
         W, H = v.width, v.height
         f = rng.normal(0.0, noise, size=(2, H, W)).astype(np.float32)
-        rho = math.sqrt(cover * W * H / (blobs * math.pi))
-        ys = np.arange(H, dtype=np.float32)[:, None] + 0.5
-        xs = np.arange(W, dtype=np.float32)[None, :] + 0.5
-        for _ in range(blobs):
-            cx, cy = rng.uniform(0.15, 0.85) * W, rng.uniform(0.15, 0.85) * H
-            ang = rng.uniform(0.0, 2.0 * math.pi)
-            sig = rho / 1.5
-            bump = (amp * np.exp(-((xs - cx) ** 2 + (ys - cy) ** 2) / (2.0 * sig * sig))).astype(np.float32)
-            f[0] += bump * np.float32(math.cos(ang))
-            f[1] += bump * np.float32(math.sin(ang))
+        R = np.asarray(v.R, np.float64)
+        eye = -R.T @ np.asarray(v.t, np.float64)
+        xs = (np.arange(W) + 0.5 - v.cx) / v.fx
+        ys = (np.arange(H) + 0.5 - v.cy) / v.fy
+        d = np.empty((H, W, 3))
+        d[..., 0] = xs[None, :]
+        d[..., 1] = ys[:, None]
+        d[..., 2] = 1.0
+        d = d @ R                                    # camera ray -> world
+        d /= np.linalg.norm(d, axis=-1, keepdims=True)
+        w = centre - eye
+        along = d @ w
+        dist2 = float(w @ w) - along * along
+        inside = (along > 0) & (dist2 < radius * radius)
+        mag = np.where(inside, amp * np.sqrt(np.clip(1.0 - dist2 / (radius * radius), 0.0, 1.0)), 0.0)
+        ang = rng.uniform(0.0, 2.0 * math.pi)
+        f[0] += (mag * math.cos(ang)).astype(np.float32)
+        f[1] += (mag * math.sin(ang)).astype(np.float32)
         out.append(f.reshape(-1))
     return np.concatenate(out) if out else np.zeros(0, np.float32)
 
