@@ -82,6 +82,8 @@ def _declare(L):
         "or_lpo_minmax": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P]),
         "or_lpo_encode": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
         "or_lpo_decode": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
+        "or_uv_cell": (C.c_uint32, [DBL, DBL, DBL, C.c_int, C.c_int, P]),
+        "or_uv_max_k": (None, [P, I64, I64, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -367,6 +369,33 @@ def lpo_decode(codes, occ, lohi):
     lib().or_lpo_decode(_p(codes), F, D, H, W, _p(np.ascontiguousarray(occ, np.uint32)),
                         _p(np.ascontiguousarray(lohi, np.float32)), _p(proxy))
     return proxy
+
+
+# --------------------------------------------------------------------------
+# UV cells and Max-K pruning
+# --------------------------------------------------------------------------
+
+INVALID = 0xFFFFFFFF
+
+
+def uv_cell(x, y, z, M, N):
+    """-> (cell id or INVALID, border flag)."""
+    b = C.c_int(0)
+    c = lib().or_uv_cell(float(x), float(y), float(z), int(M), int(N), C.byref(b))
+    return int(c), int(b.value)
+
+
+def uv_max_k(soa, M, N, K):
+    """soa [D][n] -> dict(cell, rank, keep, count [M*N], border) for the n columns."""
+    soa = np.ascontiguousarray(soa, np.float64)
+    D, n = soa.shape
+    cell = np.zeros(n, np.uint32)
+    rank = np.zeros(n, np.uint32)
+    keep = np.zeros(n, np.uint8)
+    border = np.zeros(n, np.uint8)
+    count = np.zeros(M * N, np.uint32)
+    lib().or_uv_max_k(_p(soa), n, n, M, N, K, _p(cell), _p(rank), _p(keep), _p(count), _p(border))
+    return dict(cell=cell, rank=rank, keep=keep, count=count, border=border)
 
 
 # --------------------------------------------------------------------------

@@ -45,6 +45,9 @@
  *   or_lpo_decode      uniform 16-bit (position, as two 8-bit planes) and
  *                      8-bit (all other channels) quantisation, proxy
  *                      lo + q Delta
+ *   or_uv_cell,        Sec. 3 "UV-based Point-to-Image Transformation"
+ *   or_uv_max_k        (eq. uvgs2) and Sec. 4.2 "UV-Based Pruning": valid
+ *                      UV projection, top-K Gaussians per cell by opacity
  *
  * Where the paper is silent the readings are: 3DGS conventions for the
  * opacity sigmoid, the +0.5 SH offset and the clamp of colour at 0; alpha
@@ -1240,4 +1243,89 @@ void or_lpo_decode(const uint8_t *codes, int F, int D, int H, int W, const uint3
           proxy[((int64_t)f * D + c) * plane + px] = lo + (float)q * delta;
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* UV cells (eq. uvgs2) and Max-K UV pruning                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * UV cell of a position (Sec. 3 "UV-based Point-to-Image Transformation",
+ * eq. uvgs2): rho = |mu|, theta = atan2(y, x), phi = acos(z / rho),
+ * u = floor((pi + theta) / (2 pi) M), v = floor(phi / pi N).  The cell is
+ * valid (Sec. 4.2 "Valid UV Projection Pruning") iff rho is positive and
+ * finite and 0 <= u < M, 0 <= v < N; its id is v M + u (u along the width
+ * M, the reading of eq. uvgs2).  *border = 1 when either scaled coordinate
+ * lies within 1e-9 (relative to the map size) of an integer, where another
+ * precision could pick the neighbouring cell.  Returns the id or
+ * 0xFFFFFFFF.
+ */
+uint32_t or_uv_cell(double x, double y, double z, int M, int N, int *border) {
+  double rho = sqrt(x * x + y * y + z * z);
+  *border = 0;
+  if (!(rho > 0.0) || !isfinite(rho)) return 0xFFFFFFFFu;
+  double theta = atan2(y, x), phi = acos(z / rho);
+  double su = (M_PI + theta) / (2.0 * M_PI) * M, sv = phi / M_PI * N;
+  if (fabs(su - nearbyint(su)) <= 1e-9 * M || fabs(sv - nearbyint(sv)) <= 1e-9 * N) *border = 1;
+  double u = floor(su), v = floor(sv);
+  if (!(u >= 0.0 && u < M && v >= 0.0 && v < N)) return 0xFFFFFFFFu;
+  return (uint32_t)v * (uint32_t)M + (uint32_t)u;
+}
+
+typedef struct {
+  uint32_t cell;
+  double logit;
+  int64_t idx;
+} uvk_t;
+
+static int cmp_uvk(const void *pa, const void *pb) {
+  const uvk_t *a = (const uvk_t *)pa, *b = (const uvk_t *)pb;
+  if (a->cell != b->cell) return a->cell < b->cell ? -1 : 1;
+  if (a->logit != b->logit) return a->logit > b->logit ? -1 : 1;   /* higher opacity first */
+  return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+/*
+ * Max-K UV pruning (Sec. 4.2 "Max-K UV Pruning", UVGS layers ordered by
+ * opacity): of the valid Gaussians of each cell, the K of highest opacity
+ * are kept; rank = 0-based position in that order (ties: lower index
+ * first).  Opacity o = sigmoid(logit) is increasing, so logits are
+ * compared; a NaN logit makes a Gaussian invalid.  soa: channel-major
+ * [D][stride], Gaussian i in column i (position channels 0..2, logit 10).
+ * Outputs per Gaussian: cell (0xFFFFFFFF if invalid), rank (0xFFFFFFFF if
+ * invalid), keep; count [M N] = valid Gaussians per cell; border as in
+ * or_uv_cell, spread to every Gaussian of a cell that holds one.
+ */
+void or_uv_max_k(const double *soa, int64_t n, int64_t stride, int M, int N, int K, uint32_t *cell,
+                 uint32_t *rank, uint8_t *keep, uint32_t *count, uint8_t *border) {
+  uvk_t *e = (uvk_t *)malloc(sizeof(uvk_t) * (size_t)(n > 0 ? n : 1));
+  uint8_t *cb = (uint8_t *)calloc((size_t)M * (size_t)N, 1);
+  memset(count, 0, sizeof(uint32_t) * (size_t)M * (size_t)N);
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int b = 0;
+    double lg = soa[10 * stride + i];
+    uint32_t c = or_uv_cell(soa[i], soa[stride + i], soa[2 * stride + i], M, N, &b);
+    if (lg != lg) c = 0xFFFFFFFFu;
+    cell[i] = c;
+    rank[i] = 0xFFFFFFFFu;
+    keep[i] = 0;
+    border[i] = (uint8_t)b;
+    if (c == 0xFFFFFFFFu) continue;
+    if (b) cb[c] = 1;
+    e[m].cell = c;
+    e[m].logit = lg;
+    e[m].idx = i;
+    ++m;
+  }
+  qsort(e, (size_t)m, sizeof(uvk_t), cmp_uvk);
+  for (int64_t j = 0; j < m; ++j) {
+    uint32_t r = count[e[j].cell]++;
+    rank[e[j].idx] = r;
+    keep[e[j].idx] = r < (uint32_t)K;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (cell[i] != 0xFFFFFFFFu && cb[cell[i]]) border[i] = 1;
+  free(e);
+  free(cb);
 }
