@@ -60,6 +60,7 @@ extern "C" {
 #define PK_MAX_VIEWS 4096
 #define PK_RECORD_FLOATS 12  /* projected record, 48 bytes */
 #define PK_GRAD2D_FLOATS 12  /* per-pair 2D gradient record, 48 bytes (9 used) */
+#define PK_MAX_CHANNELS 59   /* D at SH degree 3 */
 
 typedef struct CUstream_st *pk_stream_t; /* identical to cudaStream_t */
 
@@ -126,6 +127,7 @@ typedef struct pk_sizes {
   int64_t n_tiles;                 /* sum_v ceil(W_v/T) ceil(H_v/T) */
   uint64_t max_dups;               /* capacity of sorted_vals */
   uint64_t workspace_bytes;
+  int64_t mask_words;              /* sum_v H_v ceil(W_v/32): uint32 words of the motion masks */
 } pk_sizes;
 
 /* Device status block (in the workspace).  flags is a bit set of
@@ -237,7 +239,7 @@ pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *s
  * inputs, outputs and bit-exact result as pk_bin_and_sort; the scratch is a
  * 64 MiB array inside the library (reserved on every GPU that loads it, for
  * the life of the process), so the plan must satisfy 28 * V * N + 12 *
- * max_dups + about 0.6 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
+ * max_dups + 144 * V + about 0.55 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
  * nothing is enqueued.  n_entries: out, one device uint32 -- the entries
  * written, or 0xFFFFFFFF if they exceeded max_dups (then nothing was
  * emitted).  The first call on a device looks up the array's address; make
@@ -287,6 +289,116 @@ pk_status pk_atlas_scatter_grad(const pk_plan *plan, const float *soa, const flo
  * target) / (3 P) (0 where equal). */
 pk_status pk_l1_loss_grad(const pk_plan *plan, const float *image, const float *target,
                           float *dL_dimage, void *workspace, pk_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Motion masks and the dynamic mask D_i                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Binary motion masks (Sec. 4.2 "Optical Flow and Binary Motion Masks"):
+ * M_v(p) = 1 iff the flow vector at p has magnitude > tau, then M_v <-
+ * dilate(M_v; dilate_r).  The magnitude and its comparison are taken in
+ * FP32 as sqrt(fx * fx + fy * fy) > tau, IEEE-rounded, without fused
+ * multiply-adds; the dilation uses the (2r+1) x (2r+1) square and treats
+ * pixels outside the image as still.
+ * flow:      [2 * P] float32, per view planar [2][H_v][W_v] (x component
+ *            plane, then y), views concatenated: component k of pixel
+ *            (x, y) of view v at 2 * pix_off(v) + k * W_v * H_v + y * W_v + x.
+ * mask_bits: out [pk_sizes.mask_words] uint32; view v's rows start at word
+ *            sum_{u<v} H_u ceil(W_u/32), row y at + y * ceil(W_v/32), pixel
+ *            x in bit x & 31 of word x >> 5; bits past W_v are 0.
+ * tau:       any value but NaN; dilate_r in [0, 4096], else PK_ERR_ARG.
+ * Uses the workspace's mask scratch (one mask's worth of words). */
+pk_status pk_motion_mask(const pk_plan *plan, const float *flow, float tau, int32_t dilate_r,
+                         uint32_t *mask_bits, void *workspace, pk_stream_t stream);
+
+/* Dynamic mask (Sec. 4.2 "Covariance-Aware Gaussian Masking", Alg. 1 step
+ * 5, and D_i = OR over cameras): Gaussian g is dynamic iff, for some view
+ * v, a pixel of v's image with M_v = 1 lies in g's ellipse d^2 = (p -
+ * m)^T conic (p - m) <= 9, p being the pixel centre (x + 0.5, y + 0.5) and
+ * the candidates the square |p - m|_inf <= r, r = min(r_max, radius) of the
+ * pair's record (r_max <= 0: no clamp).  Square and d^2 are evaluated in
+ * FP32 in the order
+ *   x_lo = ceil((m_x - 0.5) - r), x_hi = floor((m_x - 0.5) + r) (same in
+ *   y), clamped to the image;
+ *   d^2 = ((a dx) dx + (c dy) dy) + ((2 b) dy) dx, dx = (x + 0.5) - m_x,
+ * without fused multiply-adds, so the result is a function of the records.
+ * records:   [V*N][12] from pk_project_and_sh (culled pairs have radius 0).
+ * texel:     [N] from pk_atlas_gather.
+ * mask_bits: [pk_sizes.mask_words] from pk_motion_mask (same layout).
+ * dyn:       in/out [H_A][ceil(W_A/32)] uint32 texel bits, the layout of
+ *            pk_atlas_gather's dyn input: bit of texel[g] set for every
+ *            dynamic g.  accumulate = 0 clears it first; 1 ORs into it.
+ * r_max must not be NaN.  Texels of non-live texels are left as they are.
+ * Uses the workspace's block-mask scratch (one bit per 32 x 32 pixels). */
+pk_status pk_dynamic_mask(const pk_plan *plan, const float *records, const uint32_t *texel,
+                          const uint32_t *mask_bits, float r_max, uint32_t *dyn, int32_t accumulate,
+                          void *workspace, pk_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Low-precision proxy (Sec. 4.2 "Low Precision Optimization", Supp. "Video  */
+/* Coding")                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Channel c of every texel is quantised uniformly to K_c bits over its
+ * range [lo_c, hi_c]: K_c = 16 for the position channels 0..2, 8 for all
+ * others; Delta_c = (hi_c - lo_c) / (2^K_c - 1); code
+ * q = floor((x - lo_c) / Delta_c + 0.5) clamped to [0, 2^K_c - 1], 0 when
+ * that is not a number (hi_c == lo_c, or x NaN); the renderer's proxy is
+ * lo_c + q Delta_c.  Every step in FP32, IEEE-rounded, in that order, no
+ * fused multiply-adds.  The 8-bit plane layout ("codes") is
+ * [F][D + 3][H_A][W_A] bytes: plane 2c / 2c + 1 holds the high / low byte
+ * of position channel c < 3, plane c + 3 the code of channel c >= 3;
+ * texels that are not live hold 0.  Gradients pass the quantiser straight
+ * through: pk_atlas_scatter_grad's texel gradients are those of the FP32
+ * masters. */
+#define PK_LPO_CODES 0    /* pk_atlas_gather_lpo reads 8-bit code planes */
+#define PK_LPO_MASTERS 1  /* ... or fake-quantises the FP32 master atlas */
+
+/* lohi: out [D][2] float32 {lo_c, hi_c}, min and max of channel c over the
+ * live texels of all F frames of the FP32 atlas [F][D][H_A][W_A]; NaN
+ * texels are skipped; 0, 0 for a channel without a live texel. */
+pk_status pk_lpo_minmax(const pk_plan *plan, const float *atlas, const uint32_t *occ, float *lohi,
+                        void *workspace, pk_stream_t stream);
+
+/* codes: out [F][D + 3][H_A][W_A] uint8 from the FP32 atlas and lohi. */
+pk_status pk_lpo_encode(const pk_plan *plan, const float *atlas, const uint32_t *occ, const float *lohi,
+                        uint8_t *codes, void *workspace, pk_stream_t stream);
+
+/* a1 on the proxy: as pk_atlas_gather (same occ, dyn, soa, texel, dynflag
+ * and status), the SoA receiving the proxy values lo_c + q Delta_c.  src
+ * is the codes (src_kind = PK_LPO_CODES) or the FP32 master atlas
+ * (PK_LPO_MASTERS: quantised on the fly, nothing stored).  The plan's
+ * texel_type is not used. */
+pk_status pk_atlas_gather_lpo(const pk_plan *plan, const void *src, int32_t src_kind, const float *lohi,
+                              const uint32_t *occ, const uint32_t *dyn, float *soa, uint32_t *texel,
+                              uint8_t *dynflag, void *workspace, pk_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* UV cells and Max-K UV pruning                                             */
+/* ------------------------------------------------------------------------ */
+
+/* UV cell of a Gaussian by eq. uvgs2 (Sec. 3 "UV-based Point-to-Image
+ * Transformation"): rho = |mu|, theta = atan2(y, x), phi = acos(z / rho),
+ * u = floor((pi + theta) / (2 pi) M), v = floor(phi / pi N), computed in
+ * FP64; cell id v M + u.  Valid UV projection (Sec. 4.2 "UV-Based
+ * Pruning"): rho positive and finite, 0 <= u < M, 0 <= v < N, and the
+ * opacity logit not NaN.  Max-K UV pruning: of the valid Gaussians of a
+ * cell, the K of highest opacity are kept (opacity = sigmoid(logit) is
+ * increasing, so logits are compared; ties go to the lower index).  The
+ * Gaussians need no plan: the call takes n candidates, e.g. the children
+ * of a densification step.
+ * soa:   [D][stride] float32, Gaussian i in column i (position channels
+ *        0..2, opacity logit channel 10), stride >= n.
+ * cell:  out [n] uint32 cell id, 0xFFFFFFFF if not valid.
+ * rank:  out [n] uint32 0-based position in its cell's order (0xFFFFFFFF
+ *        if not valid); keep: out [n] uint8, rank < K.
+ * count: out [M N] uint32 valid Gaussians per cell.
+ * scratch: pk_uv_max_k_scratch_bytes(n, M, N) bytes of device memory,
+ *        256-byte aligned.  M N and n must be below 2^32 - 1. */
+uint64_t pk_uv_max_k_scratch_bytes(int64_t n, int32_t M, int32_t N);
+pk_status pk_uv_max_k(const float *soa, int64_t n, int64_t stride, int32_t M, int32_t N, int32_t K,
+                      uint32_t *cell, uint32_t *rank, uint8_t *keep, uint32_t *count, void *scratch,
+                      pk_stream_t stream);
 
 const char *pk_status_string(pk_status s);
 int32_t pk_version(void);

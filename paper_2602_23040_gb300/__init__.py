@@ -10,16 +10,22 @@ from . import build  # noqa: F401
 from .api import (  # noqa: F401
     Plan,
     atlas_gather,
+    atlas_gather_lpo,
     atlas_layout,
     atlas_scatter_grad,
     bin_and_sort,
     bin_and_sort_noalloc,
+    dynamic_mask,
     l1_loss_grad,
+    lpo_encode,
+    lpo_minmax,
     make_workspace,
+    motion_mask,
     project_and_sh,
     rasterize_bwd,
     rasterize_fwd,
     read_status,
+    uv_max_k,
     workspace_init,
 )
 from .render import PerViewLoop, Renderer, render  # noqa: F401
@@ -27,5 +33,6 @@ from .render import PerViewLoop, Renderer, render  # noqa: F401
 __all__ = [
     "Plan", "Renderer", "PerViewLoop", "render", "atlas_layout", "atlas_gather", "project_and_sh",
     "bin_and_sort", "bin_and_sort_noalloc", "rasterize_fwd", "rasterize_bwd", "atlas_scatter_grad", "l1_loss_grad",
+    "motion_mask", "dynamic_mask", "lpo_minmax", "lpo_encode", "atlas_gather_lpo", "uv_max_k",
     "make_workspace", "workspace_init", "read_status",
 ]

@@ -51,7 +51,8 @@ class Options(C.Structure):
 class Sizes(C.Structure):
     _fields_ = [("n_live", C.c_int64), ("n_gauss", C.c_int64), ("channels", C.c_int32),
                 ("n_views", C.c_int32), ("n_pairs", C.c_int64), ("n_pixels", C.c_int64),
-                ("n_tiles", C.c_int64), ("max_dups", C.c_uint64), ("workspace_bytes", C.c_uint64)]
+                ("n_tiles", C.c_int64), ("max_dups", C.c_uint64), ("workspace_bytes", C.c_uint64),
+                ("mask_words", C.c_int64)]
 
 
 class DeviceStatus(C.Structure):
@@ -81,6 +82,13 @@ SIGNATURES = {
     "pk_atlas_scatter_grad": (ST, [P, P, P, P, P, P, C.c_int32, P, P]),
     "pk_l1_loss_grad": (ST, [P, P, P, P, P, P]),
     "pk_bin_and_sort_noalloc": (ST, [P, P, P, P, P, P]),
+    "pk_motion_mask": (ST, [P, P, C.c_float, C.c_int32, P, P, P]),
+    "pk_dynamic_mask": (ST, [P, P, P, P, C.c_float, P, C.c_int32, P, P]),
+    "pk_lpo_minmax": (ST, [P, P, P, P, P, P]),
+    "pk_lpo_encode": (ST, [P, P, P, P, P, P, P]),
+    "pk_atlas_gather_lpo": (ST, [P, P, C.c_int32, P, P, P, P, P, P, P, P]),
+    "pk_uv_max_k_scratch_bytes": (C.c_uint64, [C.c_int64, C.c_int32, C.c_int32]),
+    "pk_uv_max_k": (ST, [P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
 }
 
 _lock = threading.Lock()

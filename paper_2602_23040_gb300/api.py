@@ -158,6 +158,10 @@ class Plan:
     def max_dups(self):
         return self.sizes.max_dups
 
+    @property
+    def mask_words(self):
+        return self.sizes.mask_words
+
 
 def make_workspace(plan: Plan, device="cuda") -> torch.Tensor:
     return torch.empty(int(plan.sizes.workspace_bytes), dtype=torch.uint8, device=device)
@@ -268,3 +272,96 @@ def bin_and_sort_noalloc(plan: Plan, records, sorted_vals, tile_ranges, n_entrie
         _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles), _ptr(n_entries, "n_entries", _I32, 1),
         _stream(stream))
     N.check("pk_bin_and_sort_noalloc", rc)
+
+
+# ---------------------------------------------------------------------------
+# Motion masks and the dynamic mask D_i
+# ---------------------------------------------------------------------------
+
+def motion_mask(plan: Plan, flow, tau: float, dilate_r: int, mask_bits, ws, stream=None) -> None:
+    """Binary motion masks of every view: flow magnitude above ``tau``, then
+    a square dilation of radius ``dilate_r`` (``flow``: float32 ``[2 * P]``,
+    per view ``[2][H][W]``; ``mask_bits``: int32 ``[plan.mask_words]``)."""
+    rc = N.load().pk_motion_mask(plan.handle, _ptr(flow, "flow", torch.float32, 2 * plan.P), float(tau),
+                                 int(dilate_r), _ptr(mask_bits, "mask_bits", _I32, plan.mask_words),
+                                 _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_motion_mask", rc)
+
+
+def dynamic_mask(plan: Plan, records, texel, mask_bits, dyn, ws, r_max: float = 0.0, accumulate: bool = False,
+                 stream=None) -> None:
+    """Covariance-aware dynamic mask: sets the texel bit of every Gaussian
+    whose d^2 <= 9 ellipse covers a moving pixel in some view (``dyn``:
+    int32 ``[H_A][ceil(W_A/32)]``, the layout ``atlas_gather`` reads)."""
+    W, H = plan.desc.atlas_w, plan.desc.atlas_h
+    rc = N.load().pk_dynamic_mask(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(texel, "texel", _I32, plan.N), _ptr(mask_bits, "mask_bits", _I32, plan.mask_words), float(r_max),
+        _ptr(dyn, "dyn", _I32, H * ((W + 31) // 32)), 1 if accumulate else 0, _ptr(ws, "workspace"),
+        _stream(stream))
+    N.check("pk_dynamic_mask", rc)
+
+
+# ---------------------------------------------------------------------------
+# Low-precision proxy (16-bit position, 8-bit everything else)
+# ---------------------------------------------------------------------------
+
+LPO_CODES, LPO_MASTERS = 0, 1
+
+
+def lpo_minmax(plan: Plan, atlas, occ, lohi, ws, stream=None) -> None:
+    """Per-channel [lo, hi] over the live texels of every frame (``lohi``:
+    float32 ``[D][2]``) of the FP32 atlas."""
+    F, D, W, H = plan.desc.frames, plan.D, plan.desc.atlas_w, plan.desc.atlas_h
+    rc = N.load().pk_lpo_minmax(plan.handle, _ptr(atlas, "atlas", torch.float32, F * D * H * W),
+                                _ptr(occ, "occ", _I32, H * ((W + 31) // 32)), _ptr(lohi, "lohi", torch.float32, 2 * D),
+                                _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_lpo_minmax", rc)
+
+
+def lpo_encode(plan: Plan, atlas, occ, lohi, codes, ws, stream=None) -> None:
+    """8-bit code planes ``[F][D+3][H][W]`` (uint8) of the FP32 atlas."""
+    F, D, W, H = plan.desc.frames, plan.D, plan.desc.atlas_w, plan.desc.atlas_h
+    rc = N.load().pk_lpo_encode(plan.handle, _ptr(atlas, "atlas", torch.float32, F * D * H * W),
+                                _ptr(occ, "occ", _I32, H * ((W + 31) // 32)), _ptr(lohi, "lohi", torch.float32, 2 * D),
+                                _ptr(codes, "codes", torch.uint8, F * (D + 3) * H * W), _ptr(ws, "workspace"),
+                                _stream(stream))
+    N.check("pk_lpo_encode", rc)
+
+
+def atlas_gather_lpo(plan: Plan, src, src_kind: int, lohi, occ, dyn, soa, texel, dynflag, ws, stream=None) -> None:
+    """``atlas_gather`` on the low-precision proxy: ``src`` is the uint8 code
+    planes (``LPO_CODES``) or the FP32 master atlas (``LPO_MASTERS``)."""
+    F, D, W, H = plan.desc.frames, plan.D, plan.desc.atlas_w, plan.desc.atlas_h
+    words = H * ((W + 31) // 32)
+    if src_kind == LPO_CODES:
+        sp = _ptr(src, "codes", torch.uint8, F * (D + 3) * H * W)
+    else:
+        sp = _ptr(src, "atlas", torch.float32, F * D * H * W)
+    rc = N.load().pk_atlas_gather_lpo(
+        plan.handle, sp, int(src_kind), _ptr(lohi, "lohi", torch.float32, 2 * D), _ptr(occ, "occ", _I32, words),
+        _ptr(dyn, "dyn", _I32, words, allow_none=True), _ptr(soa, "soa", torch.float32, D * plan.G),
+        _ptr(texel, "texel", _I32, plan.N), _ptr(dynflag, "dynflag", torch.uint8, plan.N), _ptr(ws, "workspace"),
+        _stream(stream))
+    N.check("pk_atlas_gather_lpo", rc)
+
+
+# ---------------------------------------------------------------------------
+# UV cells and Max-K UV pruning
+# ---------------------------------------------------------------------------
+
+def uv_max_k(soa, n: int, map_w: int, map_h: int, K: int, cell, rank, keep, count, scratch=None, stream=None):
+    """Cells of eq. uvgs2 on a ``map_w`` (M, along u) x ``map_h`` (N, along v)
+    map and the top-K Gaussians per cell by opacity, for the first ``n``
+    columns of ``soa`` (float32 ``[D][stride]``).  Returns the scratch
+    tensor (allocated if not given; reuse it)."""
+    need = int(N.load().pk_uv_max_k_scratch_bytes(n, map_w, map_h))
+    if scratch is None or scratch.numel() < need:
+        scratch = torch.empty(max(need, 256), dtype=torch.uint8, device=soa.device)
+    stride = soa.shape[1] if soa.dim() == 2 else n
+    rc = N.load().pk_uv_max_k(_ptr(soa, "soa", torch.float32), int(n), int(stride), int(map_w), int(map_h), int(K),
+                              _ptr(cell, "cell", _I32, n), _ptr(rank, "rank", _I32, n),
+                              _ptr(keep, "keep", torch.uint8, n), _ptr(count, "count", _I32, map_w * map_h),
+                              _ptr(scratch, "scratch"), _stream(stream))
+    N.check("pk_uv_max_k", rc)
+    return scratch

@@ -29,7 +29,7 @@ constexpr int kScanBlocks = 1024;
 constexpr int kSortBlocks = 512;      // most radix blocks of one pass (histogram capacity)
 constexpr int kMaxRadixBits = 8;      // widest radix digit
 
-// Per-view constants on the device, 128 bytes.
+// Per-view constants on the device, 144 bytes.
 struct alignas(16) DevView {
   float R[9];
   float t[3];
@@ -40,6 +40,8 @@ struct alignas(16) DevView {
   int32_t pad0;
   int64_t pix_off;    // first pixel of this view in the concatenated images
   int64_t tile_off;   // first global tile id of this view
+  int64_t mask_off;   // first word of this view's motion-mask rows
+  int64_t coarse_off; // first word of this view's 32 x 32-pixel block mask
 };
 static_assert(sizeof(DevView) % 16 == 0, "DevView layout");
 
@@ -58,6 +60,8 @@ struct WsLayout {
   size_t pair_cnt, zkey0, zkey1, pval0, pval1, offs, rmask;
   size_t blocksums, hist;
   size_t dkey0, dkey1, dval;
+  size_t mask_tmp;         // one motion mask's worth of words (dilation scratch)
+  size_t mask_coarse;      // per view, one bit per 32 x 32-pixel block: any moving pixel
   size_t total;
 };
 
@@ -68,7 +72,7 @@ struct pk_plan {
   pk_atlas_desc desc;
   pk_options opts;
   int32_t V, F, D, T, L;
-  int64_t N, G, pairs, P, n_tiles;
+  int64_t N, G, pairs, P, n_tiles, mask_words, coarse_words;
   uint64_t max_dups;
   int32_t tile_bits;       // bits needed for a global tile id
   int32_t num_sms;

@@ -79,6 +79,37 @@ struct Quad<__half> {
   __device__ static float one(const __half *p) { return __half2float(*p); }
 };
 
+// Live bits and Gaussian indices of the (up to) four texels x0 .. x0 + 3
+// of row y; writes their texel ids and dynamic flags.  False if none is live.
+__device__ __forceinline__ bool quad_live(const uint32_t *__restrict__ occ, const uint32_t *__restrict__ dyn,
+                                          const uint32_t *__restrict__ woff, int W, int y, int x0, int64_t N,
+                                          uint32_t *__restrict__ texel, uint8_t *__restrict__ dynflag,
+                                          bool live[4], int64_t gidx[4]) {
+  const int Wp = (W + 31) / 32;
+  bool any = false;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int x = x0 + i;
+    live[i] = false;
+    gidx[i] = 0;
+    if (x < W) {
+      uint32_t word = occ[(int64_t)y * Wp + (x >> 5)];
+      uint32_t bit = 1u << (x & 31);
+      if (word & bit) {
+        int64_t g = woff[(int64_t)y * Wp + (x >> 5)] + __popc(word & (bit - 1u));
+        if (g < N) {
+          live[i] = true;
+          gidx[i] = g;
+          any = true;
+          texel[g] = (uint32_t)((int64_t)y * W + x);
+          dynflag[g] = dyn ? (uint8_t)((dyn[(int64_t)y * Wp + (x >> 5)] >> (x & 31)) & 1u) : (uint8_t)1;
+        }
+      }
+    }
+  }
+  return any;
+}
+
 // One thread per 4 consecutive texels of a row.
 template <typename Tex, bool kVec>
 __global__ __launch_bounds__(256) void k_gather(const Tex *__restrict__ atlas, const uint32_t *__restrict__ occ,
@@ -86,37 +117,15 @@ __global__ __launch_bounds__(256) void k_gather(const Tex *__restrict__ atlas, c
                                                 int W, int H, int F, int D, int64_t N,
                                                 float *__restrict__ soa, uint32_t *__restrict__ texel,
                                                 uint8_t *__restrict__ dynflag) {
-  const int Wq = (W + 3) / 4, Wp = (W + 31) / 32;
+  const int Wq = (W + 3) / 4;
   const int64_t nq = (int64_t)Wq * H;
   const int64_t plane = (int64_t)W * H;
   const int64_t G = (int64_t)F * N;
   for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += (int64_t)gridDim.x * blockDim.x) {
     const int y = (int)(qi / Wq), x0 = (int)(qi % Wq) * 4;
-    // live bits of the (up to) four texels and their Gaussian indices
     int64_t gidx[4];
     bool live[4];
-    bool any = false;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      int x = x0 + i;
-      live[i] = false;
-      gidx[i] = 0;
-      if (x < W) {
-        uint32_t word = occ[(int64_t)y * Wp + (x >> 5)];
-        uint32_t bit = 1u << (x & 31);
-        if (word & bit) {
-          int64_t g = woff[(int64_t)y * Wp + (x >> 5)] + __popc(word & (bit - 1u));
-          if (g < N) {
-            live[i] = true;
-            gidx[i] = g;
-            any = true;
-            texel[g] = (uint32_t)((int64_t)y * W + x);
-            dynflag[g] = dyn ? (uint8_t)((dyn[(int64_t)y * Wp + (x >> 5)] >> (x & 31)) & 1u) : (uint8_t)1;
-          }
-        }
-      }
-    }
-    if (!any) continue;
+    if (!quad_live(occ, dyn, woff, W, y, x0, N, texel, dynflag, live, gidx)) continue;
     const int64_t pix = (int64_t)y * W + x0;
     for (int f = 0; f < F; ++f) {
 #pragma unroll 4
@@ -138,7 +147,95 @@ __global__ __launch_bounds__(256) void k_gather(const Tex *__restrict__ atlas, c
   }
 }
 
+// Low-precision proxy (Sec. 4.2 "Low Precision Optimization"): channel c
+// quantised to 16 (position) or 8 bits over [lo_c, hi_c], read either as
+// codes ([F][D + 3][H][W] bytes, position as high and low byte planes) or
+// by fake-quantising the FP32 masters on the fly.  FP32 steps in the order
+// packuv.h states, without fused multiply-adds.
+__device__ __forceinline__ float lpo_proxy(uint32_t q, float lo, float delta) {
+  return __fadd_rn(lo, __fmul_rn((float)q, delta));
+}
+
+__device__ __forceinline__ uint32_t lpo_code(float x, float lo, float delta, float L) {
+  const float u = floorf(__fadd_rn(__fdiv_rn(__fsub_rn(x, lo), delta), 0.5f));
+  if (!(u >= 0.0f)) return 0u;
+  if (u >= L) return (uint32_t)L;
+  return (uint32_t)u;
+}
+
+template <bool kCodes>
+__global__ __launch_bounds__(256) void k_gather_lpo(const void *__restrict__ src, const float *__restrict__ lohi,
+                                                    const uint32_t *__restrict__ occ,
+                                                    const uint32_t *__restrict__ dyn,
+                                                    const uint32_t *__restrict__ woff, int W, int H, int F, int D,
+                                                    int64_t N, float *__restrict__ soa,
+                                                    uint32_t *__restrict__ texel, uint8_t *__restrict__ dynflag) {
+  __shared__ float s_lo[PK_MAX_CHANNELS], s_delta[PK_MAX_CHANNELS];
+  for (int c = threadIdx.x; c < D; c += blockDim.x) {
+    const float L = c < 3 ? 65535.0f : 255.0f;
+    s_lo[c] = lohi[2 * c];
+    s_delta[c] = __fdiv_rn(__fsub_rn(lohi[2 * c + 1], lohi[2 * c]), L);
+  }
+  __syncthreads();
+  const int Wq = (W + 3) / 4;
+  const int64_t nq = (int64_t)Wq * H;
+  const int64_t plane = (int64_t)W * H;
+  const int64_t G = (int64_t)F * N;
+  for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += (int64_t)gridDim.x * blockDim.x) {
+    const int y = (int)(qi / Wq), x0 = (int)(qi % Wq) * 4;
+    int64_t gidx[4];
+    bool live[4];
+    if (!quad_live(occ, dyn, woff, W, y, x0, N, texel, dynflag, live, gidx)) continue;
+    const int64_t pix = (int64_t)y * W + x0;
+    for (int f = 0; f < F; ++f) {
+      for (int c = 0; c < D; ++c) {
+        const float lo = s_lo[c], delta = s_delta[c];
+        float *dst = soa + (int64_t)c * G + (int64_t)f * N;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (!live[i]) continue;
+          uint32_t q;
+          if (kCodes) {
+            const uint8_t *cb = reinterpret_cast<const uint8_t *>(src) + (int64_t)f * (D + 3) * plane + pix + i;
+            q = c < 3 ? ((uint32_t)__ldg(cb + (2 * c) * plane) << 8) | __ldg(cb + (2 * c + 1) * plane)
+                      : (uint32_t)__ldg(cb + (c + 3) * plane);
+          } else {
+            const float x = __ldg(reinterpret_cast<const float *>(src) + ((int64_t)f * D + c) * plane + pix + i);
+            q = lpo_code(x, lo, delta, c < 3 ? 65535.0f : 255.0f);
+          }
+          dst[gidx[i]] = lpo_proxy(q, lo, delta);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace
+
+extern "C" pk_status pk_atlas_gather_lpo(const pk_plan *p, const void *src, int32_t src_kind, const float *lohi,
+                                         const uint32_t *occ, const uint32_t *dyn, float *soa, uint32_t *texel,
+                                         uint8_t *dynflag, void *ws, pk_stream_t stream) {
+  if (!p || !src || !lohi || !occ || !soa || !texel || !dynflag || !ws) return PK_ERR_ARG;
+  if (src_kind != PK_LPO_CODES && src_kind != PK_LPO_MASTERS) return PK_ERR_ARG;
+  if (!aligned16(soa)) return PK_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int W = p->desc.atlas_w, H = p->desc.atlas_h;
+  const int64_t nwords = (int64_t)((W + 31) / 32) * H;
+  uint32_t *woff = at<uint32_t>(ws, p->ws.woff);
+  pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
+  k_word_scan<<<1, kScanThreads, 0, st>>>(occ, nwords, woff, status, p->N);
+  const int64_t nq = (int64_t)((W + 3) / 4) * H;
+  int blocks = (int)((nq + 255) / 256);
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  if (src_kind == PK_LPO_CODES)
+    k_gather_lpo<true><<<blocks, 256, 0, st>>>(src, lohi, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel,
+                                               dynflag);
+  else
+    k_gather_lpo<false><<<blocks, 256, 0, st>>>(src, lohi, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel,
+                                                dynflag);
+  return check_launch();
+}
 
 extern "C" pk_status pk_atlas_gather(const pk_plan *p, const void *atlas, const uint32_t *occ, const uint32_t *dyn,
                                      float *soa, uint32_t *texel, uint8_t *dynflag, void *ws, pk_stream_t stream) {

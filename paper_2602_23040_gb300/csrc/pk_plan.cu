@@ -171,7 +171,7 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   p->h_toff = new uint32_t[V + 1];
   p->h_fview_off = new int32_t[F + 1];
   p->h_fview_idx = new int32_t[V];
-  int64_t po = 0, to = 0;
+  int64_t po = 0, to = 0, mo = 0, co = 0;
   for (int v = 0; v < n_views; ++v) {
     const pk_view &w = views[v];
     DevView &dv = p->h_views[v];
@@ -191,10 +191,17 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
     dv.tiles_y = (w.height + o.tile - 1) / o.tile;
     dv.pix_off = po;
     dv.tile_off = to;
+    dv.mask_off = mo;
+    dv.coarse_off = co;
     p->h_toff[v] = (uint32_t)to;
     po += (int64_t)w.width * w.height;
     to += (int64_t)dv.tiles_x * dv.tiles_y;
+    const int64_t wpr = (w.width + 31) / 32;
+    mo += (int64_t)w.height * wpr;
+    co += (int64_t)((w.height + 31) / 32) * ((wpr + 31) / 32);
   }
+  p->mask_words = mo;
+  p->coarse_words = co;
   p->h_toff[V] = (uint32_t)to;
   // views grouped by frame (CSR), keeping view order inside a frame
   int32_t k = 0;
@@ -233,6 +240,8 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);
   L.dval = take(sizeof(uint32_t) * maxd);
+  L.mask_tmp = take(sizeof(uint32_t) * (size_t)p->mask_words);
+  L.mask_coarse = take(sizeof(uint32_t) * (size_t)p->coarse_words);
   L.total = off;
   *out = p;
   return PK_OK;
@@ -249,6 +258,7 @@ extern "C" pk_status pk_plan_sizes(const pk_plan *p, pk_sizes *s) {
   s->n_tiles = p->n_tiles;
   s->max_dups = p->max_dups;
   s->workspace_bytes = p->ws.total;
+  s->mask_words = p->mask_words;
   return PK_OK;
 }
 

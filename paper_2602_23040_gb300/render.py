@@ -27,6 +27,10 @@ class Renderer:
         f32, i32 = torch.float32, torch.int32
         self.ws = ws if ws is not None else api.make_workspace(p, self.device)
         api.workspace_init(p, self.ws)
+        # Per-channel [lo, hi] of the low-precision proxy: when set, forward()
+        # reads the FP32 masters through the LPO quantiser (16-bit position,
+        # 8-bit other channels) and the gradients pass it straight through.
+        self.lohi: Optional[torch.Tensor] = None
         self._alloc()
 
     def _alloc(self):
@@ -49,7 +53,11 @@ class Renderer:
     def forward(self, atlas, occ, dyn=None, stream=None):
         p = self.plan
         self._has_dyn = dyn is not None
-        api.atlas_gather(p, atlas, occ, dyn, self.soa, self.texel, self.dynflag, self.ws, stream)
+        if self.lohi is not None:
+            api.atlas_gather_lpo(p, atlas, api.LPO_MASTERS, self.lohi, occ, dyn, self.soa, self.texel, self.dynflag,
+                                 self.ws, stream)
+        else:
+            api.atlas_gather(p, atlas, occ, dyn, self.soa, self.texel, self.dynflag, self.ws, stream)
         api.project_and_sh(p, self.soa, self.records, self.ws, stream)
         api.bin_and_sort(p, self.records, self.sorted_vals, self.ranges, self.ws, stream)
         api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, self.image, self.T, self.n_contrib,
