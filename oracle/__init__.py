@@ -84,6 +84,7 @@ def _declare(L):
         "or_lpo_decode": (None, [P, C.c_int, C.c_int, C.c_int, C.c_int, P, P, P]),
         "or_uv_cell": (C.c_uint32, [DBL, DBL, DBL, C.c_int, C.c_int, P]),
         "or_uv_max_k": (None, [P, I64, I64, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
+        "or_photo_loss": (DBL, [P, P, C.c_int, P, P, DBL, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -396,6 +397,27 @@ def uv_max_k(soa, M, N, K):
     count = np.zeros(M * N, np.uint32)
     lib().or_uv_max_k(_p(soa), n, n, M, N, K, _p(cell), _p(rank), _p(keep), _p(count), _p(border))
     return dict(cell=cell, rank=rank, keep=keep, count=count, border=border)
+
+
+# --------------------------------------------------------------------------
+# Photometric objective
+# --------------------------------------------------------------------------
+
+SSIM_LAMBDA = 0.2
+
+
+def photo_loss(img, tgt, views_arr, lam=SSIM_LAMBDA, grad=True, ssim_map=False):
+    """-> dict(loss, ssim, grad [3P] or None, map [3P] or None)."""
+    img = np.ascontiguousarray(img, np.float64)
+    tgt = np.ascontiguousarray(tgt, np.float64)
+    V = views_arr.shape[0]
+    vw = np.ascontiguousarray(views_arr[:, 16], np.int32)
+    vh = np.ascontiguousarray(views_arr[:, 17], np.int32)
+    g = np.zeros_like(img) if grad else None
+    m = np.zeros_like(img) if ssim_map else None
+    s = C.c_double(0.0)
+    L = lib().or_photo_loss(_p(img), _p(tgt), V, _p(vw), _p(vh), float(lam), _p(g), _p(m), C.byref(s))
+    return dict(loss=float(L), ssim=float(s.value), grad=g, map=m)
 
 
 # --------------------------------------------------------------------------

@@ -48,6 +48,8 @@
  *   or_uv_cell,        Sec. 3 "UV-based Point-to-Image Transformation"
  *   or_uv_max_k        (eq. uvgs2) and Sec. 4.2 "UV-Based Pruning": valid
  *                      UV projection, top-K Gaussians per cell by opacity
+ *   or_photo_loss      Sec. 4.2 "Objective": (1 - lambda) L1 +
+ *                      lambda (1 - SSIM) and its gradient
  *
  * Where the paper is silent the readings are: 3DGS conventions for the
  * opacity sigmoid, the +0.5 SH offset and the clamp of colour at 0; alpha
@@ -1328,4 +1330,113 @@ void or_uv_max_k(const double *soa, int64_t n, int64_t stride, int M, int N, int
     if (cell[i] != 0xFFFFFFFFu && cb[cell[i]]) border[i] = 1;
   free(e);
   free(cb);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Photometric objective: L1 + D-SSIM                                        */
+/* ------------------------------------------------------------------------ */
+
+#define SSIM_R 5          /* 11 x 11 window */
+static const double SSIM_SIGMA = 1.5, SSIM_C1 = 0.0001, SSIM_C2 = 0.0009;
+
+/* 1-D Gaussian weights of standard deviation 1.5 over -5..5, summing to 1;
+ * the 2-D window is their outer product. */
+static void ssim_weights(double w[2 * SSIM_R + 1]) {
+  double s = 0.0;
+  for (int k = -SSIM_R; k <= SSIM_R; ++k) s += (w[k + SSIM_R] = exp(-(double)(k * k) / (2.0 * SSIM_SIGMA * SSIM_SIGMA)));
+  for (int k = 0; k <= 2 * SSIM_R; ++k) w[k] /= s;
+}
+
+/*
+ * Photometric objective of Sec. 4.2 "Objective":
+ *   L = (1 - lambda) ||I^ - I||_1 + lambda (1 - SSIM(I^, I)).
+ * Readings (the paper gives neither constants nor normalisation): the L1
+ * term is the mean of |I^ - I| over the 3 P values; SSIM is the mean over
+ * the 3 P values of the per-channel SSIM map of Wang et al. with the 11 x 11
+ * Gaussian window (standard deviation 1.5, weights summing to 1), pixels
+ * outside the image counting as 0 in every window sum, C1 = 0.01^2 and
+ * C2 = 0.03^2 (the 3DGS convention); lambda = 0.2 by default.  Per pixel
+ * with window sums m1 = G*X, m2 = G*Y, e11 = G*(X X), e22 = G*(Y Y),
+ * e12 = G*(X Y):
+ *   s = (2 m1 m2 + C1)(2 (e12 - m1 m2) + C2) /
+ *       ((m1^2 + m2^2 + C1)((e11 - m1^2) + (e22 - m2^2) + C2)).
+ * img, tgt: [3P] planar per view as the images of the render step.
+ * grad: out dL/dimg [3P] (or NULL) -- the L1 part is sign(X - Y) / (3P),
+ * 0 where equal; the SSIM part is the adjoint of every window sum.
+ * ssim_map: out [3P] (or NULL).  Returns L; *ssim = mean SSIM.
+ */
+double or_photo_loss(const double *img, const double *tgt, int V, const int32_t *vw, const int32_t *vh,
+                     double lambda, double *grad, double *ssim_map, double *ssim) {
+  double w[2 * SSIM_R + 1];
+  ssim_weights(w);
+  int64_t P = 0;
+  for (int v = 0; v < V; ++v) P += (int64_t)vw[v] * vh[v];
+  const double n = 3.0 * (double)P;
+  double l1 = 0.0, ssum = 0.0;
+  int64_t off = 0;
+  for (int v = 0; v < V; ++v) {
+    const int W = vw[v], H = vh[v];
+    const int64_t plane = (int64_t)W * H;
+    double *ds1 = (double *)malloc(sizeof(double) * (size_t)plane);
+    double *ds11 = (double *)malloc(sizeof(double) * (size_t)plane);
+    double *ds12 = (double *)malloc(sizeof(double) * (size_t)plane);
+    for (int c = 0; c < 3; ++c) {
+      const double *X = img + 3 * off + c * plane, *Y = tgt + 3 * off + c * plane;
+      for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+          double m1 = 0, m2 = 0, e11 = 0, e22 = 0, e12 = 0;
+          for (int i = -SSIM_R; i <= SSIM_R; ++i)
+            for (int j = -SSIM_R; j <= SSIM_R; ++j) {
+              int yy = y + i, xx = x + j;
+              if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+              double g = w[i + SSIM_R] * w[j + SSIM_R], a = X[(int64_t)yy * W + xx], b = Y[(int64_t)yy * W + xx];
+              m1 += g * a;
+              m2 += g * b;
+              e11 += g * a * a;
+              e22 += g * b * b;
+              e12 += g * a * b;
+            }
+          double A1 = 2.0 * m1 * m2 + SSIM_C1, A2 = 2.0 * (e12 - m1 * m2) + SSIM_C2;
+          double B1 = m1 * m1 + m2 * m2 + SSIM_C1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + SSIM_C2;
+          double s = (A1 * A2) / (B1 * B2);
+          const int64_t p = (int64_t)y * W + x;
+          ssum += s;
+          if (ssim_map) ssim_map[3 * off + c * plane + p] = s;
+          /* partial derivatives of s with respect to m1, e11, e12 */
+          ds1[p] = s * (2.0 * m2 / A1 - 2.0 * m2 / A2 - 2.0 * m1 / B1 + 2.0 * m1 / B2);
+          ds11[p] = -s / B2;
+          ds12[p] = 2.0 * s / A2;
+          double d = X[p] - Y[p];
+          l1 += fabs(d);
+        }
+      if (grad) {
+        for (int y = 0; y < H; ++y)
+          for (int x = 0; x < W; ++x) {
+            const int64_t p = (int64_t)y * W + x;
+            /* d(sum_q s(q)) / dX(p): every window sum at q that contains p */
+            double t1 = 0, t11 = 0, t12 = 0;
+            for (int i = -SSIM_R; i <= SSIM_R; ++i)
+              for (int j = -SSIM_R; j <= SSIM_R; ++j) {
+                int yy = y + i, xx = x + j;
+                if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+                double g = w[i + SSIM_R] * w[j + SSIM_R];
+                int64_t q = (int64_t)yy * W + xx;
+                t1 += g * ds1[q];
+                t11 += g * ds11[q];
+                t12 += g * ds12[q];
+              }
+            double dS = t1 + 2.0 * X[p] * t11 + Y[p] * t12;
+            double d = X[p] - Y[p];
+            double sg = d > 0 ? 1.0 : (d < 0 ? -1.0 : 0.0);
+            grad[3 * off + c * plane + p] = (1.0 - lambda) * sg / n - lambda * dS / n;
+          }
+      }
+    }
+    free(ds1);
+    free(ds11);
+    free(ds12);
+    off += plane;
+  }
+  *ssim = ssum / n;
+  return (1.0 - lambda) * l1 / n + lambda * (1.0 - ssum / n);
 }
