@@ -143,7 +143,8 @@ typedef struct pk_device_status {
   uint64_t valid_pairs;            /* pairs touching at least one tile */
   uint64_t evals_fwd;              /* (pixel, splat) evaluations of the last forward */
   uint64_t evals_bwd;              /* ... of the last backward */
-  double loss;                     /* last pk_l1_loss_grad value */
+  double loss;                     /* last pk_l1_loss_grad / pk_photo_loss_grad value */
+  double ssim;                     /* mean SSIM of the last pk_photo_loss_grad (0 after L1) */
 } pk_device_status;
 
 /* ------------------------------------------------------------------------ */
@@ -399,6 +400,18 @@ uint64_t pk_uv_max_k_scratch_bytes(int64_t n, int32_t M, int32_t N);
 pk_status pk_uv_max_k(const float *soa, int64_t n, int64_t stride, int32_t M, int32_t N, int32_t K,
                       uint32_t *cell, uint32_t *rank, uint8_t *keep, uint32_t *count, void *scratch,
                       pk_stream_t stream);
+
+/* Photometric objective of Sec. 4.2 "Objective":
+ *   loss = (1 - lambda) mean|image - target| + lambda (1 - SSIM),
+ * SSIM being the mean over the 3 P values of the per-channel SSIM map with
+ * the 11 x 11 Gaussian window (standard deviation 1.5, weights summing to
+ * 1; pixels outside the image count as 0 in every window sum), C1 = 0.01^2,
+ * C2 = 0.03^2.  dL_dimage: out, the exact gradient of that loss (FP32
+ * arithmetic): sign(image - target) (1 - lambda) / (3 P) plus the adjoint
+ * of the window sums.  loss and ssim are stored in the status block.
+ * lambda in [0, 1], else PK_ERR_ARG; lambda = 0.2 is the usual choice. */
+pk_status pk_photo_loss_grad(const pk_plan *plan, const float *image, const float *target, float lambda,
+                             float *dL_dimage, void *workspace, pk_stream_t stream);
 
 const char *pk_status_string(pk_status s);
 int32_t pk_version(void);

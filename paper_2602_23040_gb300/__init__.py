@@ -21,6 +21,7 @@ from .api import (  # noqa: F401
     lpo_minmax,
     make_workspace,
     motion_mask,
+    photo_loss_grad,
     project_and_sh,
     rasterize_bwd,
     rasterize_fwd,
@@ -33,6 +34,6 @@ from .render import PerViewLoop, Renderer, render  # noqa: F401
 __all__ = [
     "Plan", "Renderer", "PerViewLoop", "render", "atlas_layout", "atlas_gather", "project_and_sh",
     "bin_and_sort", "bin_and_sort_noalloc", "rasterize_fwd", "rasterize_bwd", "atlas_scatter_grad", "l1_loss_grad",
-    "motion_mask", "dynamic_mask", "lpo_minmax", "lpo_encode", "atlas_gather_lpo", "uv_max_k",
+    "photo_loss_grad", "motion_mask", "dynamic_mask", "lpo_minmax", "lpo_encode", "atlas_gather_lpo", "uv_max_k",
     "make_workspace", "workspace_init", "read_status",
 ]

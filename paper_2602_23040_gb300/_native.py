@@ -58,7 +58,7 @@ class Sizes(C.Structure):
 class DeviceStatus(C.Structure):
     _fields_ = [("flags", C.c_uint32), ("live_seen", C.c_uint32), ("dups", C.c_uint64),
                 ("dups_needed", C.c_uint64), ("valid_pairs", C.c_uint64), ("evals_fwd", C.c_uint64),
-                ("evals_bwd", C.c_uint64), ("loss", C.c_double)]
+                ("evals_bwd", C.c_uint64), ("loss", C.c_double), ("ssim", C.c_double)]
 
 
 P = C.c_void_p
@@ -89,6 +89,7 @@ SIGNATURES = {
     "pk_atlas_gather_lpo": (ST, [P, P, C.c_int32, P, P, P, P, P, P, P, P]),
     "pk_uv_max_k_scratch_bytes": (C.c_uint64, [C.c_int64, C.c_int32, C.c_int32]),
     "pk_uv_max_k": (ST, [P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
+    "pk_photo_loss_grad": (ST, [P, P, P, C.c_float, P, P, P]),
 }
 
 _lock = threading.Lock()

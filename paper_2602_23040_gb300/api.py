@@ -258,6 +258,16 @@ def l1_loss_grad(plan: Plan, image, target, dL_dimage, ws, stream=None) -> None:
     N.check("pk_l1_loss_grad", rc)
 
 
+def photo_loss_grad(plan: Plan, image, target, dL_dimage, ws, lam: float = 0.2, stream=None) -> None:
+    """(1 - lam) L1 + lam (1 - SSIM) and its gradient (loss and mean SSIM
+    land in the status block)."""
+    rc = N.load().pk_photo_loss_grad(plan.handle, _ptr(image, "image", torch.float32, 3 * plan.P),
+                                     _ptr(target, "target", torch.float32, 3 * plan.P), float(lam),
+                                     _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
+                                     _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_photo_loss_grad", rc)
+
+
 def bin_and_sort_noalloc(plan: Plan, records, sorted_vals, tile_ranges, n_entries, stream=None) -> None:
     """``pk_bin_and_sort`` for callers that cannot provide a workspace (for
     example code running inside another framework's frame loop, where device

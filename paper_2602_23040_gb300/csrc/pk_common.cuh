@@ -51,7 +51,10 @@ struct DevCounters {
   uint32_t dups;           // entries emitted (0 on overflow)
   uint32_t tile_queue[4];  // persistent-kernel work counters
   uint64_t scan_total;     // total of the last scan
-  double loss_acc;
+  double loss_acc;         // sum of |image - target| of the last loss call
+  double ssim_acc;         // sum of the SSIM map of the last photometric loss call
+  float ssim_lambda;       // its lambda (0 after pk_l1_loss_grad)
+  uint32_t pad;
 };
 
 // Byte offsets of every region inside the workspace.

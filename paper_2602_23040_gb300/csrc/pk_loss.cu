@@ -34,7 +34,8 @@ extern "C" pk_status pk_l1_loss_grad(const pk_plan *p, const float *image, const
   if (!p || !image || !target || !dL_dimage || !ws) return PK_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
-  if (cudaMemsetAsync(&ctr->loss_acc, 0, sizeof(double), st) != cudaSuccess) return PK_ERR_CUDA;
+  // loss_acc, ssim_acc and ssim_lambda (0: the loss is L1 alone)
+  if (cudaMemsetAsync(&ctr->loss_acc, 0, 2 * sizeof(double) + sizeof(float), st) != cudaSuccess) return PK_ERR_CUDA;
   const int64_t n = 3 * p->P;
   if (n == 0) return PK_OK;
   int64_t blocks = (n + 255) / 256;

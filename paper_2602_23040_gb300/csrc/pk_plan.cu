@@ -304,7 +304,9 @@ extern "C" pk_status pk_read_status(const pk_plan *p, const void *ws, pk_stream_
                       st) != cudaSuccess)
     return PK_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PK_ERR_CUDA;
-  out->loss = c.loss_acc / (3.0 * (double)p->P);
+  const double n = 3.0 * (double)p->P, lam = c.ssim_lambda;
+  out->ssim = c.ssim_acc / n;
+  out->loss = (1.0 - lam) * c.loss_acc / n + (lam > 0.0 ? lam * (1.0 - out->ssim) : 0.0);
   if (out->flags & PK_DEV_CAPACITY) return PK_ERR_CAPACITY;
   if (out->flags & PK_DEV_TIMEOUT) return PK_ERR_TIMEOUT;
   return PK_OK;

@@ -79,6 +79,13 @@ class Renderer:
         api.l1_loss_grad(self.plan, self.image, target, self.dimage, self.ws, stream)
         self.backward(self.dimage, grad_atlas, False, stream)
 
+    def photo_step(self, atlas, occ, dyn, target, grad_atlas, lam: float = 0.2, stream=None):
+        """One fitting step with the paper's photometric objective
+        (1 - lam) L1 + lam (1 - SSIM)."""
+        self.forward(atlas, occ, dyn, stream)
+        api.photo_loss_grad(self.plan, self.image, target, self.dimage, self.ws, lam, stream)
+        self.backward(self.dimage, grad_atlas, False, stream)
+
     def status(self, stream=None) -> dict:
         return api.read_status(self.plan, self.ws, stream)
 
