@@ -244,6 +244,85 @@ def run_reference(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def next_rows(plan, r, scene, atlas, occ, target, stream, dev, hbm):
+    """The rows after the render step, timed at the same workload: motion
+    masks and the dynamic mask (Alg. 1), the LPO proxy, Max-K UV pruning and
+    the L1 + D-SSIM objective.  Each: median of 5 eager calls (CUDA events on
+    the launching stream, L2 flushed between calls) and its HBM roofline."""
+    import torch
+    import paper_2602_23040_gb300 as pk
+    F, D, Hh, W = scene.atlas.shape
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, reps=5):
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                fn()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    def row(ms, nbytes, unit_count, unit):
+        return {"ms": ms, "algorithmic_bytes": int(nbytes), "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
+                "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm, "rate": unit_count / (ms * 1e-3), "rate_unit": unit}
+
+    out = {}
+    # motion masks and the dynamic mask
+    flow = torch.from_numpy(synth.motion_flow(scene.views, *synth.actor_sphere(scene, 0.05), seed=77)).to(dev)
+    bits = torch.empty(max(plan.mask_words, 1), dtype=torch.int32, device=dev)
+    dynb = torch.empty(Hh * ((W + 31) // 32), dtype=torch.int32, device=dev)
+    ms = timed(lambda: pk.motion_mask(plan, flow, 1.0, 2, bits, r.ws))
+    out["motion_mask"] = row(ms, 8 * plan.P + 4 * plan.mask_words, plan.P, "pixels/s")
+    out["motion_mask"]["dilate_r"] = 2
+    pk.motion_mask(plan, flow, 1.0, 2, bits, r.ws)
+    ms = timed(lambda: pk.dynamic_mask(plan, r.records, r.texel, bits, dynb, r.ws))
+    out["dynamic_mask"] = row(ms, 24 * plan.pairs + 4 * plan.mask_words, plan.pairs, "pairs/s")
+    t = r.texel[:plan.N].long()
+    wp = (W + 31) // 32
+    dbit = (dynb.long()[(t // W) * wp + (t % W) // 32] >> (t % 32)) & 1
+    out["dynamic_mask"]["dynamic_fraction"] = float(dbit.float().mean().item())
+    del flow
+    # LPO proxy
+    if scene.atlas.dtype == np.float32:
+        lohi = torch.empty(2 * D, dtype=torch.float32, device=dev)
+        codes = torch.empty(F * (D + 3) * Hh * W, dtype=torch.uint8, device=dev)
+        texels = F * D * Hh * W
+        ms = timed(lambda: pk.lpo_minmax(plan, atlas, occ, lohi, r.ws))
+        out["lpo_minmax"] = row(ms, 4 * texels, plan.G, "gaussians/s")
+        ms = timed(lambda: pk.lpo_encode(plan, atlas, occ, lohi, codes, r.ws))
+        out["lpo_encode"] = row(ms, 4 * texels + F * (D + 3) * Hh * W, plan.G, "gaussians/s")
+        ms = timed(lambda: pk.atlas_gather_lpo(plan, codes, pk.api.LPO_CODES, lohi, occ, None, r.soa, r.texel,
+                                               r.dynflag, r.ws))
+        out["gather_lpo_codes"] = row(ms, plan.G * ((D + 3) + 4 * D), plan.G, "gaussians/s")
+        ms = timed(lambda: pk.atlas_gather_lpo(plan, atlas, pk.api.LPO_MASTERS, lohi, occ, None, r.soa, r.texel,
+                                               r.dynflag, r.ws))
+        out["gather_lpo_fakequant"] = row(ms, plan.G * 8 * D, plan.G, "gaussians/s")
+        pk.atlas_gather(plan, atlas, occ, None, r.soa, r.texel, r.dynflag, r.ws)
+        del codes
+    # Max-K UV pruning of the live set on the base map
+    n = plan.N
+    soa2 = r.soa.view(plan.D, plan.G)
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    rank = torch.empty_like(cell)
+    keep = torch.empty(n, dtype=torch.uint8, device=dev)
+    count = torch.empty(W * Hh, dtype=torch.int32, device=dev)
+    scratch = pk.uv_max_k(soa2, n, W, Hh, 4, cell, rank, keep, count)
+    ms = timed(lambda: pk.uv_max_k(soa2, n, W, Hh, 4, cell, rank, keep, count, scratch))
+    out["uv_max_k"] = row(ms, n * (4 * 4 + 4 + 4 + 1 + 8) + W * Hh * 4 * 4, n, "gaussians/s")
+    out["uv_max_k"]["map"] = f"{W}x{Hh}, K=4"
+    # L1 + D-SSIM objective
+    ms = timed(lambda: pk.photo_loss_grad(plan, r.image, target, r.dimage, r.ws, 0.2))
+    out["photo_loss_l1_dssim"] = row(ms, 12 * 3 * plan.P, 3 * plan.P, "values/s")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,6 +336,7 @@ def main():
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler: no extras")
+    ap.add_argument("--no-rows", action="store_true", help="skip the rows after the render step")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -440,6 +520,9 @@ def main():
                                 "launch": "eager, one view per call sequence", "status_ok": ok,
                                 "batched_speedup": pv_ms / ms}
         del loop
+
+    if not args.profile and not args.no_rows and rank == 0:
+        out["next_rows"] = next_rows(plan, r, scene, atlas, occ, target, stream, dev, hbm)
 
     if not args.profile and not args.no_cpu_baseline and rank == 0:
         out["cpu_baseline"] = cpu_baseline(scene)

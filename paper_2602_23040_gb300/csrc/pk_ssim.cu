@@ -5,11 +5,14 @@
 // the 52 x 52 input window of image and target (halo 2 x 5) in shared
 // memory, forms the five window sums (X, Y, XX, YY, XY) on the 42 x 42
 // region (halo 5) by a horizontal then a vertical 11-tap pass, turns them
-// into the SSIM value and its partial derivatives in place, and sums those
-// back onto the 32 x 32 tile with the same separable window (the adjoint of
-// the window sums).  Image and target are read once per tile (plus halo)
-// and the gradient written once; the arithmetic (about 400 FP32 operations
-// per value) bounds the kernel.
+// into the SSIM value and its partial derivatives, and sums those back onto
+// the 32 x 32 tile with the same separable window (the adjoint of the
+// window sums).  Every pass is register-tiled: a thread produces 6 or 8
+// consecutive outputs of one row or column from one sliding read of the
+// inputs, so shared-memory reads are about 1/4 of the multiply-adds.
+// Image and target are read once per tile (plus halo) and the gradient
+// written once; the arithmetic (about 400 FP32 operations per value)
+// bounds the kernel.
 #include "pk_common.cuh"
 
 using namespace pk;
@@ -27,10 +30,18 @@ constexpr float kC1 = 0.0001f, kC2 = 0.0009f;
 // the host in double precision and rounded once.
 __constant__ float c_w[2 * kR + 1];
 
+// Row strides padded to odd lengths so that threads walking down a column
+// hit distinct banks.
+constexpr int kIP = kI + 1, kMP = kM + 1, kTP = kT + 1;
+constexpr int kGB = 6;   // stage B: window-sum columns per item (42 = 7 x 6)
+constexpr int kGC = 6;   // stage C: window-sum rows per item (42 = 7 x 6)
+constexpr int kGD = 8;   // stage D: tile columns per item (32 = 4 x 8)
+constexpr int kGE = 8;   // stage E: tile rows per item (32 = 4 x 8)
+
 struct SsimSmem {
-  float x[kI][kI], y[kI][kI];         // inputs, 0 outside the image
-  float h[5][kI][kM];                 // horizontal sums; later [3][kM][kT] backward sums
-  float m[5][kM][kM];                 // window sums; later the three partial maps
+  float x[kI][kIP], y[kI][kIP];       // inputs, 0 outside the image
+  float h[5][kI][kMP];                // horizontal sums; later [3][kM][kTP] backward sums
+  float d[3][kM][kMP];                // partial derivatives of the SSIM map
 };
 
 __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restrict__ img,
@@ -50,109 +61,179 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
   const int64_t plane = (int64_t)W * H;
   const float *X = img + 3 * view.pix_off + c * plane, *Y = tgt + 3 * view.pix_off + c * plane;
   const int tid = threadIdx.x;
+  float w[2 * kR + 1];
+#pragma unroll
+  for (int j = 0; j <= 2 * kR; ++j) w[j] = c_w[j];
 
-  // inputs over [ty0 - 10, ty0 + 42) x [tx0 - 10, tx0 + 42)
-  for (int i = tid; i < kI * kI; i += kSsimThreads) {
-    const int r = i / kI, q = i - r * kI;
-    const int yy = ty0 - 2 * kR + r, xx = tx0 - 2 * kR + q;
-    const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
-    S.x[r][q] = in ? __ldg(X + (int64_t)yy * W + xx) : 0.0f;
-    S.y[r][q] = in ? __ldg(Y + (int64_t)yy * W + xx) : 0.0f;
-  }
-  __syncthreads();
-  // horizontal window sums: every input row, the 42 window-sum columns
-  for (int i = tid; i < kI * kM; i += kSsimThreads) {
-    const int r = i / kM, q = i - r * kM;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+  // A: inputs over [ty0 - 10, ty0 + 42) x [tx0 - 10, tx0 + 42), every load
+  // of a thread issued before the first store
+  {
+    constexpr int kLoads = (kI * kI + kSsimThreads - 1) / kSsimThreads;
+    float xv[kLoads], yv[kLoads];
 #pragma unroll
-    for (int j = 0; j <= 2 * kR; ++j) {
-      const float w = c_w[j], xv = S.x[r][q + j], yv = S.y[r][q + j];
-      a0 = fmaf(w, xv, a0);
-      a1 = fmaf(w, yv, a1);
-      a2 = fmaf(w, xv * xv, a2);
-      a3 = fmaf(w, yv * yv, a3);
-      a4 = fmaf(w, xv * yv, a4);
+    for (int k = 0; k < kLoads; ++k) {
+      const int i = tid + k * kSsimThreads;
+      const int r = i / kI, q = i - r * kI;
+      const int yy = ty0 - 2 * kR + r, xx = tx0 - 2 * kR + q;
+      const bool in = i < kI * kI && yy >= 0 && yy < H && xx >= 0 && xx < W;
+      xv[k] = in ? __ldg(X + (int64_t)yy * W + xx) : 0.0f;
+      yv[k] = in ? __ldg(Y + (int64_t)yy * W + xx) : 0.0f;
     }
-    S.h[0][r][q] = a0;
-    S.h[1][r][q] = a1;
-    S.h[2][r][q] = a2;
-    S.h[3][r][q] = a3;
-    S.h[4][r][q] = a4;
+#pragma unroll
+    for (int k = 0; k < kLoads; ++k) {
+      const int i = tid + k * kSsimThreads;
+      if (i < kI * kI) {
+        const int r = i / kI, q = i - r * kI;
+        S.x[r][q] = xv[k];
+        S.y[r][q] = yv[k];
+      }
+    }
   }
   __syncthreads();
-  // vertical window sums, then the SSIM value and its partial derivatives
-  // with respect to m1 = G*X, e11 = G*XX, e12 = G*XY (0 outside the image)
+  // B: horizontal window sums of X, Y, XX, YY, XY: each item one input row
+  // and kGB consecutive window-sum columns (threads walk down the rows)
+  for (int it = tid; it < kI * (kM / kGB); it += kSsimThreads) {
+    const int g = it / kI, r = it - g * kI, q0 = g * kGB;
+    float a[5][kGB];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int o = 0; o < kGB; ++o) a[k][o] = 0.f;
+#pragma unroll
+    for (int t = 0; t < kGB + 2 * kR; ++t) {
+      const float xv = S.x[r][q0 + t], yv = S.y[r][q0 + t];
+      const float xx2 = xv * xv, yy2 = yv * yv, xy = xv * yv;
+#pragma unroll
+      for (int o = 0; o < kGB; ++o) {
+        const int j = t - o;
+        if (j < 0 || j > 2 * kR) continue;
+        a[0][o] = fmaf(w[j], xv, a[0][o]);
+        a[1][o] = fmaf(w[j], yv, a[1][o]);
+        a[2][o] = fmaf(w[j], xx2, a[2][o]);
+        a[3][o] = fmaf(w[j], yy2, a[3][o]);
+        a[4][o] = fmaf(w[j], xy, a[4][o]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int o = 0; o < kGB; ++o) S.h[k][r][q0 + o] = a[k][o];
+  }
+  __syncthreads();
+  // C: vertical window sums on kGC consecutive rows of one column, then the
+  // SSIM value and its partial derivatives with respect to m1 = G*X,
+  // e11 = G*XX, e12 = G*XY (0 outside the image)
   float ssim_sum = 0.f;
-  for (int i = tid; i < kM * kM; i += kSsimThreads) {
-    const int r = i / kM, q = i - r * kM;
-    float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+  for (int it = tid; it < kM * (kM / kGC); it += kSsimThreads) {
+    const int g = it / kM, q = it - g * kM, r0 = g * kGC;
+    float a[5][kGC];
 #pragma unroll
-    for (int j = 0; j <= 2 * kR; ++j) {
-      const float w = c_w[j];
-      m1 = fmaf(w, S.h[0][r + j][q], m1);
-      m2 = fmaf(w, S.h[1][r + j][q], m2);
-      e11 = fmaf(w, S.h[2][r + j][q], e11);
-      e22 = fmaf(w, S.h[3][r + j][q], e22);
-      e12 = fmaf(w, S.h[4][r + j][q], e12);
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+      for (int o = 0; o < kGC; ++o) a[k][o] = 0.f;
+#pragma unroll
+    for (int t = 0; t < kGC + 2 * kR; ++t) {
+      float hv[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) hv[k] = S.h[k][r0 + t][q];
+#pragma unroll
+      for (int o = 0; o < kGC; ++o) {
+        const int j = t - o;
+        if (j < 0 || j > 2 * kR) continue;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) a[k][o] = fmaf(w[j], hv[k], a[k][o]);
+      }
     }
-    const int yy = ty0 - kR + r, xx = tx0 - kR + q;
-    float d1 = 0.f, d11 = 0.f, d12 = 0.f;
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-      const float A1 = 2.f * m1 * m2 + kC1, A2 = 2.f * (e12 - m1 * m2) + kC2;
-      const float B1 = m1 * m1 + m2 * m2 + kC1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + kC2;
-      // approximate reciprocals (2 ulp): far inside the FP32 tolerance of the loss
-      const float iA1 = __fdividef(1.f, A1), iA2 = __fdividef(1.f, A2), iB1 = __fdividef(1.f, B1),
-                  iB2 = __fdividef(1.f, B2);
-      const float s = A1 * A2 * iB1 * iB2;
-      d1 = 2.f * s * (m2 * (iA1 - iA2) + m1 * (iB2 - iB1));
-      d11 = -s * iB2;
-      d12 = 2.f * s * iA2;
-      if (r >= kR && r < kR + kT && q >= kR && q < kR + kT) ssim_sum += s;
+    const int xx = tx0 - kR + q;
+#pragma unroll
+    for (int o = 0; o < kGC; ++o) {
+      const int r = r0 + o, yy = ty0 - kR + r;
+      float d1 = 0.f, d11 = 0.f, d12 = 0.f;
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+        const float m1 = a[0][o], m2 = a[1][o], e11 = a[2][o], e22 = a[3][o], e12 = a[4][o];
+        const float A1 = 2.f * m1 * m2 + kC1, A2 = 2.f * (e12 - m1 * m2) + kC2;
+        const float B1 = m1 * m1 + m2 * m2 + kC1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + kC2;
+        // approximate reciprocals (2 ulp): far inside the FP32 tolerance of the loss
+        const float iA1 = __fdividef(1.f, A1), iA2 = __fdividef(1.f, A2), iB1 = __fdividef(1.f, B1),
+                    iB2 = __fdividef(1.f, B2);
+        const float s = A1 * A2 * iB1 * iB2;
+        d1 = 2.f * s * (m2 * (iA1 - iA2) + m1 * (iB2 - iB1));
+        d11 = -s * iB2;
+        d12 = 2.f * s * iA2;
+        if (r >= kR && r < kR + kT && q >= kR && q < kR + kT) ssim_sum += s;
+      }
+      S.d[0][r][q] = d1;
+      S.d[1][r][q] = d11;
+      S.d[2][r][q] = d12;
     }
-    S.m[0][r][q] = d1;
-    S.m[1][r][q] = d11;
-    S.m[2][r][q] = d12;
   }
   __syncthreads();
-  // backward horizontal sums of the three maps: rows of the 42 region,
-  // the 32 tile columns (into the h buffer, as [3][kM][kT])
-  float(*hb)[kM][kT] = reinterpret_cast<float(*)[kM][kT]>(&S.h[0][0][0]);
-  for (int i = tid; i < kM * kT; i += kSsimThreads) {
-    const int r = i / kT, q = i - r * kT;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  // D: backward horizontal sums of the three maps: one row of the 42 region,
+  // kGD consecutive tile columns (into the h buffer, as [3][kM][kTP])
+  float(*hb)[kM][kTP] = reinterpret_cast<float(*)[kM][kTP]>(&S.h[0][0][0]);
+  for (int it = tid; it < kM * (kT / kGD); it += kSsimThreads) {
+    const int g = it / kM, r = it - g * kM, q0 = g * kGD;
+    float a[3][kGD];
 #pragma unroll
-    for (int j = 0; j <= 2 * kR; ++j) {
-      const float w = c_w[j];
-      a0 = fmaf(w, S.m[0][r][q + j], a0);
-      a1 = fmaf(w, S.m[1][r][q + j], a1);
-      a2 = fmaf(w, S.m[2][r][q + j], a2);
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int o = 0; o < kGD; ++o) a[k][o] = 0.f;
+#pragma unroll
+    for (int t = 0; t < kGD + 2 * kR; ++t) {
+      float dv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dv[k] = S.d[k][r][q0 + t];
+#pragma unroll
+      for (int o = 0; o < kGD; ++o) {
+        const int j = t - o;
+        if (j < 0 || j > 2 * kR) continue;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k][o] = fmaf(w[j], dv[k], a[k][o]);
+      }
     }
-    hb[0][r][q] = a0;
-    hb[1][r][q] = a1;
-    hb[2][r][q] = a2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int o = 0; o < kGD; ++o) hb[k][r][q0 + o] = a[k][o];
   }
   __syncthreads();
-  // vertical sums onto the tile, combined with X, Y and the L1 term
+  // E: vertical sums onto kGE rows of one tile column, combined with X, Y
+  // and the L1 term
   float l1_sum = 0.f;
   const float gl1 = (1.f - lambda) * inv_n, gs = lambda * inv_n;
-  for (int i = tid; i < kT * kT; i += kSsimThreads) {
-    const int r = i / kT, q = i - r * kT;
-    const int yy = ty0 + r, xx = tx0 + q;
-    if (yy >= H || xx >= W) continue;
-    float t1 = 0.f, t11 = 0.f, t12 = 0.f;
+  for (int it = tid; it < kT * (kT / kGE); it += kSsimThreads) {
+    const int g = it / kT, q = it - g * kT, r0 = g * kGE;
+    const int xx = tx0 + q;
+    if (xx >= W) continue;
+    float a[3][kGE];
 #pragma unroll
-    for (int j = 0; j <= 2 * kR; ++j) {
-      const float w = c_w[j];
-      t1 = fmaf(w, hb[0][r + j][q], t1);
-      t11 = fmaf(w, hb[1][r + j][q], t11);
-      t12 = fmaf(w, hb[2][r + j][q], t12);
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int o = 0; o < kGE; ++o) a[k][o] = 0.f;
+#pragma unroll
+    for (int t = 0; t < kGE + 2 * kR; ++t) {
+      float bv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) bv[k] = hb[k][r0 + t][q];
+#pragma unroll
+      for (int o = 0; o < kGE; ++o) {
+        const int j = t - o;
+        if (j < 0 || j > 2 * kR) continue;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[k][o] = fmaf(w[j], bv[k], a[k][o]);
+      }
     }
-    const float xv = S.x[r + 2 * kR][q + 2 * kR], yv = S.y[r + 2 * kR][q + 2 * kR];
-    const float dS = t1 + 2.f * xv * t11 + yv * t12;
-    const float d = xv - yv;
-    l1_sum += fabsf(d);
-    const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-    grad[3 * view.pix_off + c * plane + (int64_t)yy * W + xx] = gl1 * sg - gs * dS;
+#pragma unroll
+    for (int o = 0; o < kGE; ++o) {
+      const int r = r0 + o, yy = ty0 + r;
+      if (yy >= H) break;
+      const float xv = S.x[r + 2 * kR][q + 2 * kR], yv = S.y[r + 2 * kR][q + 2 * kR];
+      const float dS = a[0][o] + 2.f * xv * a[1][o] + yv * a[2][o];
+      const float dd = xv - yv;
+      l1_sum += fabsf(dd);
+      const float sg = dd > 0.f ? 1.f : (dd < 0.f ? -1.f : 0.f);
+      grad[3 * view.pix_off + c * plane + (int64_t)yy * W + xx] = gl1 * sg - gs * dS;
+    }
   }
   // block sums of L1 and SSIM, one double atomic each
 #pragma unroll
@@ -167,9 +248,9 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
   __syncthreads();
   if (tid == 0) {
     double a = 0.0, b = 0.0;
-    for (int w = 0; w < kSsimThreads / 32; ++w) {
-      a += s_red[0][w];
-      b += s_red[1][w];
+    for (int k = 0; k < kSsimThreads / 32; ++k) {
+      a += s_red[0][k];
+      b += s_red[1][k];
     }
     atomicAdd(l1_acc, a);
     atomicAdd(ssim_acc, b);
