@@ -370,6 +370,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         r.ensure_capacity(atlas, occ, dyn)
+        batch = r.autotune(atlas, occ, dyn, target, stream)
         r.l1_step(atlas, occ, dyn, target, grad)
     plan = r.plan
     st = r.status(stream)
@@ -466,7 +467,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "gaussians": plan.G, "views": plan.V, "pixels": plan.P,
                    "sh_degree": scene.sh_degree, "texels": "fp16" if texel_bytes == 2 else "fp32",
-                   "tile": 16, "graph": "whole step in one CUDA graph",
+                   "tile": 16, "batch": batch, "batch_source": "pk_autotune", "graph": "whole step in one CUDA graph",
                    "l2": "inputs larger than L2 (atlas %.0f MB, records %.0f MB)" % (
                        scene.atlas.nbytes / 1e6, plan.pairs * 48 / 1e6),
                    "parallelism": f"replica x{world}" if world > 1 else "single GPU"},

@@ -113,6 +113,8 @@ typedef struct pk_options {
   float bg[3];                     /* background colour; default 0 */
   uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
   int32_t bin_mode;                /* pk_bin_mode; default PK_BIN_ELLIPSE */
+  int32_t batch;                   /* splats staged per compositing batch: 64, 128 or 256
+                                      (0 = 256); pk_autotune picks it */
 } pk_options;
 
 typedef struct pk_plan pk_plan;
@@ -167,6 +169,21 @@ pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *views, int32_
                          int64_t n_live, const pk_options *opts, pk_plan **out);
 pk_status pk_plan_sizes(const pk_plan *plan, pk_sizes *out);
 void pk_plan_destroy(pk_plan *plan);
+
+/* Autotuning (the batching pattern of the render step): times
+ * pk_rasterize_fwd followed by pk_rasterize_bwd on the caller's current
+ * inputs for every staging batch (64, 128, 256 splats), twice each after one
+ * warm-up, on `stream`, and stores the fastest in the plan's options
+ * (*chosen_batch receives it; may be NULL).  The tile side is fixed at 16
+ * and the sort's digit width at 8 bits (wider digits measured slower), so
+ * the batch is the one tuned choice.  The arguments are those of the two
+ * calls; afterwards image, T_final, n_contrib and grad2d hold a forward and
+ * backward with the chosen batch.  Synchronises `stream`; do not call it
+ * during graph capture. */
+pk_status pk_autotune(pk_plan *plan, const float *records, const uint32_t *sorted_vals,
+                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+                      const float *dL_dimage, float *grad2d, void *workspace, pk_stream_t stream,
+                      int32_t *chosen_batch);
 
 /* Upload the plan's view tables into the workspace and clear its status
  * block.  Call once per workspace (and again after reusing the memory
@@ -284,6 +301,21 @@ pk_status pk_rasterize_bwd(const pk_plan *plan, const float *records, const uint
 pk_status pk_atlas_scatter_grad(const pk_plan *plan, const float *soa, const float *grad2d,
                                 const uint8_t *dynflag, const uint32_t *texel, float *grad_atlas,
                                 int32_t accumulate, void *workspace, pk_stream_t stream);
+
+/* Convenience: the forward of one iteration, pk_atlas_gather ->
+ * pk_project_and_sh -> pk_bin_and_sort -> pk_rasterize_fwd, with the
+ * arguments (and errors) of those calls; stops at the first error. */
+pk_status pk_render_fwd(const pk_plan *plan, const void *atlas, const uint32_t *occ, const uint32_t *dyn,
+                        float *soa, uint32_t *texel, uint8_t *dynflag, float *records, uint32_t *sorted_vals,
+                        uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+                        void *workspace, pk_stream_t stream);
+
+/* Convenience: the backward, pk_rasterize_bwd -> pk_atlas_scatter_grad. */
+pk_status pk_render_bwd(const pk_plan *plan, const float *soa, const uint8_t *dynflag, const uint32_t *texel,
+                        const float *records, const uint32_t *sorted_vals, const uint32_t *tile_ranges,
+                        const float *T_final, const uint32_t *n_contrib, const float *dL_dimage,
+                        float *grad2d, float *grad_atlas, int32_t accumulate, void *workspace,
+                        pk_stream_t stream);
 
 /* Photometric L1 term of Sec. 4.2 "Objective": loss = mean |image - target|
  * over 3 P values (stored in the status block), dL_dimage = sign(image -

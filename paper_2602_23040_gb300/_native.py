@@ -45,7 +45,7 @@ class View(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("tile", C.c_int32), ("znear", C.c_float), ("bg", C.c_float * 3), ("max_dups", C.c_uint64),
-                ("bin_mode", C.c_int32)]
+                ("bin_mode", C.c_int32), ("batch", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -90,6 +90,9 @@ SIGNATURES = {
     "pk_uv_max_k_scratch_bytes": (C.c_uint64, [C.c_int64, C.c_int32, C.c_int32]),
     "pk_uv_max_k": (ST, [P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P]),
     "pk_photo_loss_grad": (ST, [P, P, P, C.c_float, P, P, P]),
+    "pk_autotune": (ST, [P, P, P, P, P, P, P, P, P, P, P, P]),
+    "pk_render_fwd": (ST, [P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "pk_render_bwd": (ST, [P, P, P, P, P, P, P, P, P, P, P, P, C.c_int32, P, P]),
 }
 
 _lock = threading.Lock()

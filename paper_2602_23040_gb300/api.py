@@ -70,11 +70,12 @@ class Plan:
 
     def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
                  sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 16,
-                 znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse"):
+                 znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse",
+                 batch: int = 256):
         lib = N.load()
         self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
                           texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
-                          bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode)
+                          bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode, batch=batch)
         d = N.AtlasDesc()
         d.atlas_w, d.atlas_h = int(atlas_wh[0]), int(atlas_wh[1])
         d.num_levels = len(levels)
@@ -87,7 +88,9 @@ class Plan:
         o.tile, o.znear, o.max_dups = int(tile), float(znear), int(max_dups)
         o.bg[:] = [float(b) for b in bg]
         o.bin_mode = {"rect": N.BIN_RECT, "ellipse": N.BIN_ELLIPSE}[bin_mode]
+        o.batch = int(batch)
         self.bin_mode = bin_mode
+        self.batch = int(batch)
         self._views = _views_array(views)
         h = C.c_void_p()
         N.check("pk_plan_create", lib.pk_plan_create(C.byref(d), self._views, len(views), int(n_live),
@@ -266,6 +269,59 @@ def photo_loss_grad(plan: Plan, image, target, dL_dimage, ws, lam: float = 0.2, 
                                      _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
                                      _ptr(ws, "workspace"), _stream(stream))
     N.check("pk_photo_loss_grad", rc)
+
+
+def render_fwd(plan: Plan, atlas, occ, dyn, soa, texel, dynflag, records, sorted_vals, tile_ranges, image, T_final,
+               n_contrib, ws, stream=None) -> None:
+    """gather -> project -> bin and sort -> composite, one C call."""
+    F, D = plan.desc.frames, plan.D
+    W, H = plan.desc.atlas_w, plan.desc.atlas_h
+    words = H * ((W + 31) // 32)
+    adt = torch.float16 if plan.texel_type == "f16" else torch.float32
+    rc = N.load().pk_render_fwd(
+        plan.handle, _ptr(atlas, "atlas", adt, F * D * H * W), _ptr(occ, "occ", _I32, words),
+        _ptr(dyn, "dyn", _I32, words, allow_none=True), _ptr(soa, "soa", torch.float32, D * plan.G),
+        _ptr(texel, "texel", _I32, plan.N), _ptr(dynflag, "dynflag", torch.uint8, plan.N),
+        _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(image, "image", torch.float32, 3 * plan.P), _ptr(T_final, "T_final", torch.float32, plan.P),
+        _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_render_fwd", rc)
+
+
+def render_bwd(plan: Plan, soa, dynflag, texel, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage,
+               grad2d, grad_atlas, accumulate: bool, ws, stream=None) -> None:
+    """composite adjoint -> texel scatter, one C call."""
+    F, D = plan.desc.frames, plan.D
+    W, H = plan.desc.atlas_w, plan.desc.atlas_h
+    rc = N.load().pk_render_bwd(
+        plan.handle, _ptr(soa, "soa", torch.float32, D * plan.G),
+        _ptr(dynflag, "dynflag", torch.uint8, plan.N, allow_none=True), _ptr(texel, "texel", _I32, plan.N),
+        _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs), _ptr(sorted_vals, "sorted_vals", _I32),
+        _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles), _ptr(T_final, "T_final", torch.float32, plan.P),
+        _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
+        _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs),
+        _ptr(grad_atlas, "grad_atlas", torch.float32, F * D * H * W), 1 if accumulate else 0, _ptr(ws, "workspace"),
+        _stream(stream))
+    N.check("pk_render_bwd", rc)
+
+
+def autotune(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_contrib, dL_dimage, grad2d, ws,
+             stream=None) -> int:
+    """Time the compositing forward + backward for each staging batch on the
+    current inputs and keep the fastest in the plan; returns it."""
+    chosen = C.c_int32(0)
+    rc = N.load().pk_autotune(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(image, "image", torch.float32, 3 * plan.P), _ptr(T_final, "T_final", torch.float32, plan.P),
+        _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
+        _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs), _ptr(ws, "workspace"), _stream(stream),
+        C.byref(chosen))
+    N.check("pk_autotune", rc)
+    plan.batch = int(chosen.value)
+    plan._args["batch"] = plan.batch
+    return plan.batch
 
 
 def bin_and_sort_noalloc(plan: Plan, records, sorted_vals, tile_ranges, n_entries, stream=None) -> None:

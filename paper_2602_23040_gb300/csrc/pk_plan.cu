@@ -124,8 +124,11 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   o.bg[0] = o.bg[1] = o.bg[2] = 0.0f;
   o.max_dups = 0;
   o.bin_mode = PK_BIN_ELLIPSE;
+  o.batch = 256;
   if (opts) o = *opts;
   if (o.bin_mode != PK_BIN_RECT && o.bin_mode != PK_BIN_ELLIPSE) return PK_ERR_ARG;
+  if (o.batch == 0) o.batch = 256;
+  if (o.batch != 64 && o.batch != 128 && o.batch != 256) return PK_ERR_ARG;
   if (o.tile != 16) return PK_ERR_UNSUPPORTED;
   if (!(o.znear > 0.0f) || !isfinite(o.znear)) return PK_ERR_ARG;
   for (int c = 0; c < 3; ++c)
@@ -310,4 +313,50 @@ extern "C" pk_status pk_read_status(const pk_plan *p, const void *ws, pk_stream_
   if (out->flags & PK_DEV_CAPACITY) return PK_ERR_CAPACITY;
   if (out->flags & PK_DEV_TIMEOUT) return PK_ERR_TIMEOUT;
   return PK_OK;
+}
+
+extern "C" pk_status pk_autotune(pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                                 const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+                                 const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream,
+                                 int32_t *chosen_batch) {
+  if (!p) return PK_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PK_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PK_ERR_CUDA;
+  }
+  const int32_t cands[3] = {64, 128, 256};
+  const int32_t keep = p->opts.batch;
+  int32_t best = keep;
+  float best_ms = 0.f;
+  pk_status e = PK_OK;
+  for (int32_t b : cands) {
+    p->opts.batch = b;
+    float ms = 0.f;
+    for (int rep = 0; rep < 3 && e == PK_OK; ++rep) {
+      if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) e = PK_ERR_CUDA;
+      if (e == PK_OK) e = pk_rasterize_fwd(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, stream);
+      if (e == PK_OK)
+        e = pk_rasterize_bwd(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, stream);
+    }
+    if (e == PK_OK && cudaEventRecord(e1, st) != cudaSuccess) e = PK_ERR_CUDA;
+    if (e == PK_OK && cudaEventSynchronize(e1) != cudaSuccess) e = PK_ERR_CUDA;
+    if (e == PK_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) e = PK_ERR_CUDA;
+    if (e != PK_OK) break;
+    if (b == cands[0] || ms < best_ms) {
+      best_ms = ms;
+      best = b;
+    }
+  }
+  p->opts.batch = e == PK_OK ? best : keep;
+  if (e == PK_OK) e = pk_rasterize_fwd(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, stream);
+  if (e == PK_OK)
+    e = pk_rasterize_bwd(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, stream);
+  if (e == PK_OK && cudaStreamSynchronize(st) != cudaSuccess) e = PK_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (chosen_batch) *chosen_batch = p->opts.batch;
+  return e;
 }

@@ -11,7 +11,9 @@ namespace pk {
 
 constexpr int kTileSide = 16;
 constexpr int kRasterThreads = 128;   // two pixels per thread
-constexpr int kBatch = 256;           // splats staged per batch (two per thread)
+// Splats staged per batch: a template parameter of the compositing
+// kernels (64, 128 or 256; pk_options.batch, chosen by pk_autotune).
+constexpr int kBatchMax = 256;
 
 // Warp w covers the 8 x 8 pixel block (w % 2, w / 2) of the 16 x 16 tile;
 // lane l holds pixels (l % 8, l / 8) and (l % 8, l / 8 + 4) of that block.

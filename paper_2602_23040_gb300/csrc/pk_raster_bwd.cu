@@ -103,6 +103,7 @@ __device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, 
   return true;
 }
 
+template <int kBatch>
 __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
@@ -171,9 +172,9 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       const uint32_t beg = end > (uint32_t)kBatch ? end - kBatch : 0u;
       const int nb = (int)(end - beg);
       __syncthreads();
-      if (tid < nb) stage_splat(rec, __ldg(vals + s + beg + tid), st, tid);
-      if (tid + kRasterThreads < nb)
-        stage_splat(rec, __ldg(vals + s + beg + tid + kRasterThreads), st, tid + kRasterThreads);
+#pragma unroll
+      for (int j = tid; j < kBatch; j += kRasterThreads)
+        if (j < nb) stage_splat(rec, __ldg(vals + s + beg + j), st, j);
       __syncthreads();
       // splats that can reach this warp's block and that some pixel of the
       // warp blended or skipped before stopping (list position < wmax)
@@ -218,6 +219,28 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
   if (lane == 0 && evals) atomicAdd(evals_out, evals);
 }
 
+// One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
+template <int kBatch>
+pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                     const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                     const float *dL_dimage, float *grad2d, void *ws, DevCounters *ctr, pk_device_status *status,
+                     cudaStream_t st) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch>, kRasterThreads, 0);
+  if (sms < 1) sms = 1;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > p->n_tiles) grid = p->n_tiles;
+  if (grid < 1) grid = 1;
+  k_raster_bwd<kBatch><<<(int)grid, kRasterThreads, 0, st>>>(
+      records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
+      (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
+      &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd));
+  return check_launch();
+}
+
 }  // namespace
 
 extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
@@ -232,18 +255,15 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
   if (cudaMemsetAsync(grad2d, 0, sizeof(float) * kG2d * (size_t)p->pairs, st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemsetAsync(&ctr->tile_queue[1], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemsetAsync(&status->evals_bwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd, kRasterThreads, 0);
-  if (sms < 1) sms = 1;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)sms * per_sm;
-  if (grid > p->n_tiles) grid = p->n_tiles;
-  if (grid < 1) grid = 1;
-  k_raster_bwd<<<(int)grid, kRasterThreads, 0, st>>>(
-      records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
-      (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
-      &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd));
-  return check_launch();
+  switch (p->opts.batch) {
+    case 64:
+      return launch_bwd<64>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr,
+                            status, st);
+    case 128:
+      return launch_bwd<128>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr,
+                             status, st);
+    default:
+      return launch_bwd<256>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr,
+                             status, st);
+  }
 }

@@ -13,6 +13,7 @@ using namespace pk;
 
 namespace {
 
+template <int kBatch>
 __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
@@ -52,9 +53,9 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
     for (uint32_t base = s; base < e; base += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, e - base);
       __syncthreads();
-      if (tid < nb) stage_splat(rec, __ldg(vals + base + tid), st, tid);
-      if (tid + kRasterThreads < nb)
-        stage_splat(rec, __ldg(vals + base + tid + kRasterThreads), st, tid + kRasterThreads);
+#pragma unroll
+      for (int j = tid; j < kBatch; j += kRasterThreads)
+        if (j < nb) stage_splat(rec, __ldg(vals + base + j), st, j);
       __syncthreads();
       if (!__all_sync(0xffffffffu, done0 && done1)) {
         // which staged splats can reach this warp's block: 8 tests per lane,
@@ -141,6 +142,27 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
   if (lane == 0 && evals) atomicAdd(evals_out, evals);
 }
 
+// One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
+template <int kBatch>
+pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                     const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
+                     DevCounters *ctr, pk_device_status *status, cudaStream_t st) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch>, kRasterThreads, 0);
+  if (sms < 1) sms = 1;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > p->n_tiles) grid = p->n_tiles;
+  if (grid < 1) grid = 1;
+  k_raster_fwd<kBatch><<<(int)grid, kRasterThreads, 0, st>>>(
+      records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
+      (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
+      &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd));
+  return check_launch();
+}
+
 }  // namespace
 
 extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
@@ -153,18 +175,11 @@ extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, co
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
   if (cudaMemsetAsync(&ctr->tile_queue[0], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemsetAsync(&status->evals_fwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd, kRasterThreads, 0);
-  if (sms < 1) sms = 1;
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)sms * per_sm;
-  if (grid > p->n_tiles) grid = p->n_tiles;
-  if (grid < 1) grid = 1;
-  k_raster_fwd<<<(int)grid, kRasterThreads, 0, st>>>(
-      records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
-      (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
-      &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd));
-  return check_launch();
+  switch (p->opts.batch) {
+    case 64: return launch_fwd<64>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st);
+    case 128:
+      return launch_fwd<128>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st);
+    default:
+      return launch_fwd<256>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st);
+  }
 }

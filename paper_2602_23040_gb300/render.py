@@ -86,6 +86,15 @@ class Renderer:
         api.photo_loss_grad(self.plan, self.image, target, self.dimage, self.ws, lam, stream)
         self.backward(self.dimage, grad_atlas, False, stream)
 
+    def autotune(self, atlas, occ, dyn, target, stream=None) -> int:
+        """Forward + L1 gradient on the given inputs, then pk_autotune: the
+        fastest compositing batch is kept in the plan.  Host-synchronising:
+        call it before graph capture."""
+        self.forward(atlas, occ, dyn, stream)
+        api.l1_loss_grad(self.plan, self.image, target, self.dimage, self.ws, stream)
+        return api.autotune(self.plan, self.records, self.sorted_vals, self.ranges, self.image, self.T,
+                            self.n_contrib, self.dimage, self.grad2d, self.ws, stream)
+
     def status(self, stream=None) -> dict:
         return api.read_status(self.plan, self.ws, stream)
 

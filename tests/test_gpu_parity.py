@@ -390,3 +390,56 @@ def test_nothing_visible_gives_background():
     img = r.image.view(3, -1).cpu().numpy()
     assert np.all(img[0] == 0.25) and np.all(img[1] == 0.5) and np.all(img[2] == 1.0)
     assert np.all(r.T.cpu().numpy() == 1.0) and r.status()["dups"] == 0
+
+
+def test_every_batch_size_and_autotune():
+    """The compositing batch (64, 128, 256 splats) changes nothing but speed:
+    images, transmittance and contributor counts are bit-identical, 2D
+    gradients equal up to the order of their atomic sums; pk_autotune keeps
+    one of the three."""
+    pk = _pk()
+    sc = H.scene_small_sh3(seed=707)
+    atlas, occ, dyn = H.upload(sc)
+    w = torch.from_numpy(np.random.default_rng(8).standard_normal(3 * sc.pixels).astype(np.float32)).cuda()
+    out = {}
+    for b in (64, 128, 256):
+        r = pk.Renderer(pk.Plan.for_scene(sc, batch=b))
+        assert r.ensure_capacity(atlas, occ, dyn)["flags"] == 0
+        g = torch.zeros(atlas.numel(), dtype=torch.float32, device="cuda")
+        r.backward(w, g)
+        torch.cuda.synchronize()
+        out[b] = (r.image.clone(), r.T.clone(), r.n_contrib.clone(), r.grad2d.clone())
+    for b in (64, 128):
+        for k in range(3):
+            assert torch.equal(out[b][k], out[256][k])
+        assert H.rel_err(out[b][3].cpu().numpy().astype(np.float64),
+                         out[256][3].cpu().numpy().astype(np.float64)) < 1e-5
+    r = pk.Renderer(pk.Plan.for_scene(sc))
+    target = torch.from_numpy(synth.random_target(sc)).cuda()
+    r.ensure_capacity(atlas, occ, dyn)
+    chosen = r.autotune(atlas, occ, dyn, target)
+    assert chosen in (64, 128, 256) and r.plan.batch == chosen
+    assert torch.equal(r.image, out[256][0])
+
+
+def test_render_fwd_bwd_convenience_calls():
+    """pk_render_fwd / pk_render_bwd chain the six calls: same outputs."""
+    pk = _pk()
+    sc = H.scene_small_sh3(seed=708, dyn=0.3)
+    atlas, occ, dyn = H.upload(sc)
+    r = pk.Renderer(pk.Plan.for_scene(sc))
+    assert r.ensure_capacity(atlas, occ, dyn)["flags"] == 0
+    w = torch.from_numpy(np.random.default_rng(9).standard_normal(3 * sc.pixels).astype(np.float32)).cuda()
+    g_ref = torch.zeros(atlas.numel(), dtype=torch.float32, device="cuda")
+    r.backward(w, g_ref)
+    img_ref = r.image.clone()
+    p = r.plan
+    img = torch.full_like(r.image, -1.0)
+    pk.render_fwd(p, atlas, occ, dyn, r.soa, r.texel, r.dynflag, r.records, r.sorted_vals, r.ranges, img, r.T,
+                  r.n_contrib, r.ws)
+    g = torch.zeros_like(g_ref)
+    pk.render_bwd(p, r.soa, r.dynflag, r.texel, r.records, r.sorted_vals, r.ranges, r.T, r.n_contrib, w, r.grad2d,
+                  g, False, r.ws)
+    torch.cuda.synchronize()
+    assert torch.equal(img, img_ref)
+    assert H.rel_err(g.cpu().numpy().astype(np.float64), g_ref.cpu().numpy().astype(np.float64)) < 1e-5
