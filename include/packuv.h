@@ -107,6 +107,12 @@ typedef struct pk_view {
  * (PK_BIN_ELLIPSE, the default).  Images are the same in both modes. */
 typedef enum pk_bin_mode { PK_BIN_RECT = 0, PK_BIN_ELLIPSE = 1 } pk_bin_mode;
 
+/* How the compositing kernels stage a batch of a tile's splats into shared
+ * memory: every thread loads its splats' records (PK_STAGE_LOADS), or the
+ * next batch's records are fetched by bulk copies on the TMA unit while the
+ * current batch is composited (PK_STAGE_BULK).  Same results either way. */
+typedef enum pk_stage_mode { PK_STAGE_LOADS = 0, PK_STAGE_BULK = 1 } pk_stage_mode;
+
 typedef struct pk_options {
   int32_t tile;                    /* tile side: 16 (8 and 32 reserved) */
   float znear;                     /* cull z <= znear; default 0.01 */
@@ -115,6 +121,8 @@ typedef struct pk_options {
   int32_t bin_mode;                /* pk_bin_mode; default PK_BIN_ELLIPSE */
   int32_t batch;                   /* splats staged per compositing batch: 64, 128 or 256
                                       (0 = 256); pk_autotune picks it */
+  int32_t stage_fwd;               /* pk_stage_mode of pk_rasterize_fwd; default PK_STAGE_LOADS */
+  int32_t stage_bwd;               /* pk_stage_mode of pk_rasterize_bwd; default PK_STAGE_LOADS */
 } pk_options;
 
 typedef struct pk_plan pk_plan;
@@ -168,18 +176,21 @@ pk_status pk_atlas_layout(int32_t S, int32_t K, pk_atlas_desc *desc);
 pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *views, int32_t n_views,
                          int64_t n_live, const pk_options *opts, pk_plan **out);
 pk_status pk_plan_sizes(const pk_plan *plan, pk_sizes *out);
+/* The plan's current options (after defaults and pk_autotune). */
+pk_status pk_plan_options(const pk_plan *plan, pk_options *out);
 void pk_plan_destroy(pk_plan *plan);
 
-/* Autotuning (the batching pattern of the render step): times
- * pk_rasterize_fwd followed by pk_rasterize_bwd on the caller's current
- * inputs for every staging batch (64, 128, 256 splats), twice each after one
- * warm-up, on `stream`, and stores the fastest in the plan's options
- * (*chosen_batch receives it; may be NULL).  The tile side is fixed at 16
- * and the sort's digit width at 8 bits (wider digits measured slower), so
- * the batch is the one tuned choice.  The arguments are those of the two
- * calls; afterwards image, T_final, n_contrib and grad2d hold a forward and
- * backward with the chosen batch.  Synchronises `stream`; do not call it
- * during graph capture. */
+/* Autotuning (the batching pattern of the render step): times, on the
+ * caller's current inputs and on `stream`, pk_rasterize_fwd followed by
+ * pk_rasterize_bwd for every staging batch (64, 128, 256 splats) and keeps
+ * the fastest, then times each kernel with both staging modes and keeps the
+ * faster one per kernel (two timed runs after one warm-up each).  The
+ * choices are stored in the plan's options; *chosen_batch receives the
+ * batch (may be NULL).  The tile side is fixed at 16 and the sort's digit
+ * width at 8 bits (10- and 11-bit digits measured slower).  The arguments
+ * are those of the two calls; afterwards image, T_final, n_contrib and
+ * grad2d hold a forward and backward with the chosen options.
+ * Synchronises `stream`; do not call it during graph capture. */
 pk_status pk_autotune(pk_plan *plan, const float *records, const uint32_t *sorted_vals,
                       const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
                       const float *dL_dimage, float *grad2d, void *workspace, pk_stream_t stream,

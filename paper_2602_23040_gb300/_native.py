@@ -45,7 +45,7 @@ class View(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("tile", C.c_int32), ("znear", C.c_float), ("bg", C.c_float * 3), ("max_dups", C.c_uint64),
-                ("bin_mode", C.c_int32), ("batch", C.c_int32)]
+                ("bin_mode", C.c_int32), ("batch", C.c_int32), ("stage_fwd", C.c_int32), ("stage_bwd", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -71,6 +71,7 @@ SIGNATURES = {
     "pk_plan_create": (ST, [C.POINTER(AtlasDesc), C.POINTER(View), C.c_int32, C.c_int64,
                             C.POINTER(Options), C.POINTER(P)]),
     "pk_plan_sizes": (ST, [P, C.POINTER(Sizes)]),
+    "pk_plan_options": (ST, [P, C.POINTER(Options)]),
     "pk_plan_destroy": (None, [P]),
     "pk_workspace_init": (ST, [P, P, P]),
     "pk_read_status": (ST, [P, P, P, C.POINTER(DeviceStatus)]),

@@ -65,17 +65,21 @@ def _views_array(views) -> "C.Array":
     return arr
 
 
+STAGE_MODES = {"loads": 0, "bulk": 1}
+
+
 class Plan:
     """Host-side plan of one launch: atlas descriptor, views and options."""
 
     def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
                  sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 16,
                  znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse",
-                 batch: int = 256):
+                 batch: int = 256, stage_fwd: str = "loads", stage_bwd: str = "loads"):
         lib = N.load()
         self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
                           texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
-                          bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode, batch=batch)
+                          bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode, batch=batch, stage_fwd=stage_fwd,
+                          stage_bwd=stage_bwd)
         d = N.AtlasDesc()
         d.atlas_w, d.atlas_h = int(atlas_wh[0]), int(atlas_wh[1])
         d.num_levels = len(levels)
@@ -89,8 +93,11 @@ class Plan:
         o.bg[:] = [float(b) for b in bg]
         o.bin_mode = {"rect": N.BIN_RECT, "ellipse": N.BIN_ELLIPSE}[bin_mode]
         o.batch = int(batch)
+        o.stage_fwd = STAGE_MODES[stage_fwd]
+        o.stage_bwd = STAGE_MODES[stage_bwd]
         self.bin_mode = bin_mode
         self.batch = int(batch)
+        self.stage_fwd, self.stage_bwd = stage_fwd, stage_bwd
         self._views = _views_array(views)
         h = C.c_void_p()
         N.check("pk_plan_create", lib.pk_plan_create(C.byref(d), self._views, len(views), int(n_live),
@@ -319,8 +326,11 @@ def autotune(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_co
         _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs), _ptr(ws, "workspace"), _stream(stream),
         C.byref(chosen))
     N.check("pk_autotune", rc)
-    plan.batch = int(chosen.value)
-    plan._args["batch"] = plan.batch
+    o = N.Options()
+    N.check("pk_plan_options", N.load().pk_plan_options(plan.handle, C.byref(o)))
+    names = {v: k for k, v in STAGE_MODES.items()}
+    plan.batch, plan.stage_fwd, plan.stage_bwd = int(o.batch), names[o.stage_fwd], names[o.stage_bwd]
+    plan._args.update(batch=plan.batch, stage_fwd=plan.stage_fwd, stage_bwd=plan.stage_bwd)
     return plan.batch
 
 

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "pk_common.cuh"
+#include "pk_tma.cuh"
 
 using namespace pk;
 
@@ -25,8 +26,6 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kThreads * kScanItems;     // 2048
-constexpr int kSortItems = 12;
-constexpr int kSortTile = kThreads * kSortItems;     // 3072
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -508,50 +507,6 @@ __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist
     if (tid == 0) s_carry = carry + s[32];
     __syncthreads();
   }
-}
-
-// --- TMA bulk copies into shared memory, completed on an mbarrier ---------
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-// Announce `bytes` of transfers on `bar` (arrival of the issuing thread).
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-// One-dimensional bulk copy global -> shared (16-byte aligned, size a
-// multiple of 16), completing its bytes on `bar`.
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Generic-proxy writes to shared memory before async-proxy (TMA) writes.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// Bounded wait: gives up after ~2^22 polls (each poll may block briefly).
-constexpr uint32_t kWaitPolls = 1u << 22;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitPolls; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
 }
 
 // Downsweep with the next tile's keys and values prefetched by TMA into the

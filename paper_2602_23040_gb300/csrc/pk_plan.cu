@@ -125,10 +125,15 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   o.max_dups = 0;
   o.bin_mode = PK_BIN_ELLIPSE;
   o.batch = 256;
+  o.stage_fwd = PK_STAGE_LOADS;
+  o.stage_bwd = PK_STAGE_LOADS;
   if (opts) o = *opts;
   if (o.bin_mode != PK_BIN_RECT && o.bin_mode != PK_BIN_ELLIPSE) return PK_ERR_ARG;
   if (o.batch == 0) o.batch = 256;
   if (o.batch != 64 && o.batch != 128 && o.batch != 256) return PK_ERR_ARG;
+  if ((o.stage_fwd != PK_STAGE_LOADS && o.stage_fwd != PK_STAGE_BULK) ||
+      (o.stage_bwd != PK_STAGE_LOADS && o.stage_bwd != PK_STAGE_BULK))
+    return PK_ERR_ARG;
   if (o.tile != 16) return PK_ERR_UNSUPPORTED;
   if (!(o.znear > 0.0f) || !isfinite(o.znear)) return PK_ERR_ARG;
   for (int c = 0; c < 3; ++c)
@@ -265,6 +270,12 @@ extern "C" pk_status pk_plan_sizes(const pk_plan *p, pk_sizes *s) {
   return PK_OK;
 }
 
+extern "C" pk_status pk_plan_options(const pk_plan *p, pk_options *out) {
+  if (!p || !out) return PK_ERR_ARG;
+  *out = p->opts;
+  return PK_OK;
+}
+
 extern "C" void pk_plan_destroy(pk_plan *p) {
   if (!p) return;
   delete[] p->h_views;
@@ -315,6 +326,24 @@ extern "C" pk_status pk_read_status(const pk_plan *p, const void *ws, pk_stream_
   return PK_OK;
 }
 
+namespace {
+
+// Milliseconds of `reps` runs of fn after one warm-up, on stream st.
+template <typename Fn>
+pk_status time_runs(Fn fn, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps, float *ms) {
+  pk_status e = fn();
+  if (e != PK_OK) return e;
+  if (cudaEventRecord(e0, st) != cudaSuccess) return PK_ERR_CUDA;
+  for (int r = 0; r < reps && e == PK_OK; ++r) e = fn();
+  if (e != PK_OK) return e;
+  if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+      cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+    return PK_ERR_CUDA;
+  return PK_OK;
+}
+
+}  // namespace
+
 extern "C" pk_status pk_autotune(pk_plan *p, const float *records, const uint32_t *sorted_vals,
                                  const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
                                  const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream,
@@ -327,33 +356,47 @@ extern "C" pk_status pk_autotune(pk_plan *p, const float *records, const uint32_
     cudaEventDestroy(e0);
     return PK_ERR_CUDA;
   }
-  const int32_t cands[3] = {64, 128, 256};
-  const int32_t keep = p->opts.batch;
-  int32_t best = keep;
-  float best_ms = 0.f;
+  const pk_options keep = p->opts;
+  auto fwd = [&]() { return pk_rasterize_fwd(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, stream); };
+  auto bwd = [&]() {
+    return pk_rasterize_bwd(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, stream);
+  };
+  auto both = [&]() {
+    pk_status e = fwd();
+    return e == PK_OK ? bwd() : e;
+  };
   pk_status e = PK_OK;
-  for (int32_t b : cands) {
-    p->opts.batch = b;
+  // the batch, with plain loads
+  const int32_t cands[3] = {64, 128, 256};
+  int32_t best = keep.batch;
+  float best_ms = 0.f;
+  p->opts.stage_fwd = p->opts.stage_bwd = PK_STAGE_LOADS;
+  for (int i = 0; i < 3 && e == PK_OK; ++i) {
+    p->opts.batch = cands[i];
     float ms = 0.f;
-    for (int rep = 0; rep < 3 && e == PK_OK; ++rep) {
-      if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) e = PK_ERR_CUDA;
-      if (e == PK_OK) e = pk_rasterize_fwd(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, stream);
-      if (e == PK_OK)
-        e = pk_rasterize_bwd(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, stream);
-    }
-    if (e == PK_OK && cudaEventRecord(e1, st) != cudaSuccess) e = PK_ERR_CUDA;
-    if (e == PK_OK && cudaEventSynchronize(e1) != cudaSuccess) e = PK_ERR_CUDA;
-    if (e == PK_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) e = PK_ERR_CUDA;
-    if (e != PK_OK) break;
-    if (b == cands[0] || ms < best_ms) {
+    e = time_runs(both, st, e0, e1, 2, &ms);
+    if (e == PK_OK && (i == 0 || ms < best_ms)) {
       best_ms = ms;
-      best = b;
+      best = cands[i];
     }
   }
-  p->opts.batch = e == PK_OK ? best : keep;
-  if (e == PK_OK) e = pk_rasterize_fwd(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, stream);
-  if (e == PK_OK)
-    e = pk_rasterize_bwd(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, stream);
+  if (e == PK_OK) p->opts.batch = best;
+  // the staging mode of each kernel
+  for (int k = 0; k < 2 && e == PK_OK; ++k) {
+    int32_t *mode = k == 0 ? &p->opts.stage_fwd : &p->opts.stage_bwd;
+    float ms_loads = 0.f, ms_bulk = 0.f;
+    *mode = PK_STAGE_LOADS;
+    e = k == 0 ? time_runs(fwd, st, e0, e1, 2, &ms_loads) : time_runs(bwd, st, e0, e1, 2, &ms_loads);
+    if (e != PK_OK) break;
+    *mode = PK_STAGE_BULK;
+    e = k == 0 ? time_runs(fwd, st, e0, e1, 2, &ms_bulk) : time_runs(bwd, st, e0, e1, 2, &ms_bulk);
+    if (e == PK_OK) *mode = ms_bulk < ms_loads ? PK_STAGE_BULK : PK_STAGE_LOADS;
+  }
+  if (e != PK_OK) {
+    p->opts = keep;
+  } else {
+    e = both();
+  }
   if (e == PK_OK && cudaStreamSynchronize(st) != cudaSuccess) e = PK_ERR_CUDA;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

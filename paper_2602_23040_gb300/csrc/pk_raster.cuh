@@ -55,9 +55,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // q <= min(9, 2 ln(255 o)), widened by a relative 1e-3 and 0.01 px so that
 // rounding can never put a passing pixel outside; it only lets whole warps
 // skip, the per-pixel test still decides.
-__device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint32_t pid, const Staged &s, int j) {
-  const float4 *r = reinterpret_cast<const float4 *>(rec + (size_t)pid * kRec);
-  const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
+__device__ __forceinline__ void stage_from(const float4 r0, const float4 r1, const float4 r2, uint32_t pid,
+                                           const Staged &s, int j) {
   const float ca = r0.z, cb = r0.w, cc = r1.x, o = r1.y;
   s.a[j] = make_float4(r0.x, r0.y, __fmul_rn(kExpScale, ca), __fmul_rn(2.f * kExpScale, cb));
   s.b[j] = make_float4(__fmul_rn(kExpScale, cc), o, r2.x, r2.y);
@@ -77,6 +76,11 @@ __device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint3
     box = make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
   }
   s.box[j] = box;
+}
+
+__device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint32_t pid, const Staged &s, int j) {
+  const float4 *r = reinterpret_cast<const float4 *>(rec + (size_t)pid * kRec);
+  stage_from(__ldg(r), __ldg(r + 1), __ldg(r + 2), pid, s, j);
 }
 
 struct Hit {

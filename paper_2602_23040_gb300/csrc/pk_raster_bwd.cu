@@ -8,6 +8,7 @@
 // lanes each hold one complete sum and add it to the splat's gradient
 // record with one coalesced atomic instruction.
 #include "pk_raster.cuh"
+#include "pk_tma.cuh"
 
 using namespace pk;
 
@@ -103,13 +104,20 @@ __device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, 
   return true;
 }
 
-template <int kBatch>
+// kTma: the records of the next (earlier) batch are fetched into shared
+// memory by bulk copies (one 48-byte copy per splat, completed on an
+// mbarrier) while the current batch is processed.
+template <int kBatch, bool kTma>
 __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
-    const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out) {
+    const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out,
+    pk_device_status *status) {
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
+  __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
+  __shared__ uint32_t s_pid[kTma ? kBatch : 1];
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tile;
   __shared__ int s_view;
   __shared__ uint32_t s_wmax[kRasterThreads / 32];
@@ -119,6 +127,24 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
   pixel_of(tid, ox, oy);
   const int my_idx = reduce_scatter9_index(lane);
   unsigned long long evals = 0;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  if (kTma) {
+    if (tid == 0) {
+      mbar_init(&s_bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
+  // bulk copies of the records of list entries [b, b + nb) into s_raw
+  // (expect_tx is set by thread 0 before the block barrier that precedes this)
+  auto fetch = [&](uint32_t b, int nb) {
+    for (int j = tid; j < nb; j += kRasterThreads) {
+      const uint32_t pid = __ldg(vals + b + j);
+      s_pid[j] = pid;
+      tma_load_1d(&s_raw[3 * j], rec + (size_t)pid * kRec, 3 * sizeof(float4), &s_bar);
+    }
+  };
   for (;;) {
     if (tid == 0) {
       const uint32_t t = atomicAdd(queue, 1u);
@@ -168,14 +194,40 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     uint32_t tmax = 0;
 #pragma unroll
     for (int w = 0; w < kRasterThreads / 32; ++w) tmax = max(tmax, s_wmax[w]);
+    if (kTma && tmax > 0) {
+      const uint32_t b0 = tmax > (uint32_t)kBatch ? tmax - kBatch : 0u;
+      if (tid == 0) mbar_expect_tx(&s_bar, (tmax - b0) * 3u * (uint32_t)sizeof(float4));
+      __syncthreads();
+      fetch(s + b0, (int)(tmax - b0));
+    }
     for (uint32_t end = tmax; end > 0;) {
       const uint32_t beg = end > (uint32_t)kBatch ? end - kBatch : 0u;
       const int nb = (int)(end - beg);
-      __syncthreads();
+      if (kTma) {
+        if (!mbar_wait_bounded(&s_bar, phase)) {
+          timed_out = true;
+          mbar_wait_bounded(&s_bar, phase);   // let this batch's copies land before leaving
+        }
+        phase ^= 1u;
+        __syncthreads();   // every warp is done with the previous batch's staged values
 #pragma unroll
-      for (int j = tid; j < kBatch; j += kRasterThreads)
-        if (j < nb) stage_splat(rec, __ldg(vals + s + beg + j), st, j);
-      __syncthreads();
+        for (int j = tid; j < kBatch; j += kRasterThreads)
+          if (j < nb) stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
+        fence_proxy_async();   // these reads of s_raw before the next bulk writes into it
+        const uint32_t nbeg = beg > (uint32_t)kBatch ? beg - kBatch : 0u;
+        if (tid == 0 && beg > 0) mbar_expect_tx(&s_bar, (beg - nbeg) * 3u * (uint32_t)sizeof(float4));
+        if (__syncthreads_or(timed_out)) {
+          timed_out = true;
+          break;
+        }
+        if (beg > 0) fetch(s + nbeg, (int)(beg - nbeg));
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int j = tid; j < kBatch; j += kRasterThreads)
+          if (j < nb) stage_splat(rec, __ldg(vals + s + beg + j), st, j);
+        __syncthreads();
+      }
       // splats that can reach this warp's block and that some pixel of the
       // warp blended or skipped before stopping (list position < wmax)
       uint32_t hits[kBatch / 32];
@@ -212,6 +264,10 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       }
       end = beg;
     }
+    if (kTma && timed_out) {
+      if (tid == 0) atomicOr(&status->flags, PK_DEV_TIMEOUT);
+      break;
+    }
     __syncthreads();
   }
 #pragma unroll
@@ -220,7 +276,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
-template <int kBatch>
+template <int kBatch, bool kBwdTma>
 pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
                      const float *dL_dimage, float *grad2d, void *ws, DevCounters *ctr, pk_device_status *status,
@@ -228,16 +284,16 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch>, kRasterThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma>, kRasterThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > p->n_tiles) grid = p->n_tiles;
   if (grid < 1) grid = 1;
-  k_raster_bwd<kBatch><<<(int)grid, kRasterThreads, 0, st>>>(
+  k_raster_bwd<kBatch, kBwdTma><<<(int)grid, kRasterThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
-      &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd));
+      &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd), status);
   return check_launch();
 }
 
@@ -255,15 +311,20 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
   if (cudaMemsetAsync(grad2d, 0, sizeof(float) * kG2d * (size_t)p->pairs, st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemsetAsync(&ctr->tile_queue[1], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemsetAsync(&status->evals_bwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
+#define PK_BWD(B, M)                                                                                         \
+  return launch_bwd<B, M>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr, \
+                          status, st)
+  const bool tma = p->opts.stage_bwd == PK_STAGE_BULK;
   switch (p->opts.batch) {
     case 64:
-      return launch_bwd<64>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr,
-                            status, st);
+      if (tma) PK_BWD(64, true);
+      PK_BWD(64, false);
     case 128:
-      return launch_bwd<128>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr,
-                             status, st);
+      if (tma) PK_BWD(128, true);
+      PK_BWD(128, false);
     default:
-      return launch_bwd<256>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr,
-                             status, st);
+      if (tma) PK_BWD(256, true);
+      PK_BWD(256, false);
   }
+#undef PK_BWD
 }

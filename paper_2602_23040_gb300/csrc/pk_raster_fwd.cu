@@ -8,18 +8,26 @@
 // contributing ellipse misses their block.  The CTA leaves a tile as soon
 // as every pixel has stopped (transmittance cutoff) or the list ends.
 #include "pk_raster.cuh"
+#include "pk_tma.cuh"
 
 using namespace pk;
 
 namespace {
 
-template <int kBatch>
+// kTma: the records of the next batch are fetched into shared memory by
+// bulk copies (one 48-byte copy per splat, completed on an mbarrier) while
+// the current batch is composited; the derived per-splat values are then
+// computed from shared memory.
+template <int kBatch, bool kTma>
 __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
-    uint32_t *queue, unsigned long long *evals_out) {
+    uint32_t *queue, unsigned long long *evals_out, pk_device_status *status) {
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
+  __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
+  __shared__ uint32_t s_pid[kTma ? kBatch : 1];
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tile;
   __shared__ int s_view;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -27,6 +35,24 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
   int ox, oy;
   pixel_of(tid, ox, oy);
   unsigned long long evals = 0;
+  uint32_t phase = 0;
+  bool timed_out = false;
+  if (kTma) {
+    if (tid == 0) {
+      mbar_init(&s_bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
+  // bulk copies of the records of list entries [b, b + nb) into s_raw
+  // (expect_tx is set by thread 0 before the block barrier that precedes this)
+  auto fetch = [&](uint32_t b, int nb) {
+    for (int j = tid; j < nb; j += kRasterThreads) {
+      const uint32_t pid = __ldg(vals + b + j);
+      s_pid[j] = pid;
+      tma_load_1d(&s_raw[3 * j], rec + (size_t)pid * kRec, 3 * sizeof(float4), &s_bar);
+    }
+  };
   for (;;) {
     if (tid == 0) {
       const uint32_t t = atomicAdd(queue, 1u);
@@ -50,13 +76,44 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
     float T0 = 1.f, T1 = 1.f, c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
     uint32_t last0 = 0, last1 = 0;
     bool done0 = !in0, done1 = !in1;
+    bool pending = false;   // a fetch is in flight (uniform over the block)
+    if (kTma && s < e) {
+      if (tid == 0) mbar_expect_tx(&s_bar, (uint32_t)min((uint32_t)kBatch, e - s) * 3u * sizeof(float4));
+      __syncthreads();
+      fetch(s, (int)min((uint32_t)kBatch, e - s));
+      pending = true;
+    }
     for (uint32_t base = s; base < e; base += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, e - base);
-      __syncthreads();
+      if (kTma) {
+        if (!mbar_wait_bounded(&s_bar, phase)) {
+          timed_out = true;
+          mbar_wait_bounded(&s_bar, phase);   // let this batch's copies land before leaving
+        }
+        phase ^= 1u;
+        pending = false;
 #pragma unroll
-      for (int j = tid; j < kBatch; j += kRasterThreads)
-        if (j < nb) stage_splat(rec, __ldg(vals + base + j), st, j);
-      __syncthreads();
+        for (int j = tid; j < kBatch; j += kRasterThreads)
+          if (j < nb) stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
+        fence_proxy_async();   // these reads of s_raw before the next bulk writes into it
+        const uint32_t nxt = base + kBatch;
+        const int nbn = nxt < e ? (int)min((uint32_t)kBatch, e - nxt) : 0;
+        if (tid == 0 && nbn > 0) mbar_expect_tx(&s_bar, (uint32_t)nbn * 3u * sizeof(float4));
+        if (__syncthreads_or(timed_out)) {
+          timed_out = true;
+          break;
+        }
+        if (nbn > 0) {
+          fetch(nxt, nbn);
+          pending = true;
+        }
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int j = tid; j < kBatch; j += kRasterThreads)
+          if (j < nb) stage_splat(rec, __ldg(vals + base + j), st, j);
+        __syncthreads();
+      }
       if (!__all_sync(0xffffffffu, done0 && done1)) {
         // which staged splats can reach this warp's block: 8 tests per lane,
         // one ballot per 32 splats, then only the hits are visited
@@ -115,6 +172,20 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
       }
       if (__syncthreads_count(!(done0 && done1)) == 0) break;
     }
+    if (kTma) {
+      // a tile that stopped early may still have its next batch in flight
+      if (pending) {
+        if (!mbar_wait_bounded(&s_bar, phase)) {
+          timed_out = true;
+          mbar_wait_bounded(&s_bar, phase);
+        }
+        phase ^= 1u;
+      }
+      if (__syncthreads_or(timed_out)) {
+        if (tid == 0) atomicOr(&status->flags, PK_DEV_TIMEOUT);
+        break;
+      }
+    }
     const size_t plane = (size_t)W * H;
     if (in0) {
       const size_t pix = (size_t)view.pix_off + (size_t)y0 * W + x;
@@ -143,23 +214,23 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
-template <int kBatch>
+template <int kBatch, bool kFwdTma>
 pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
                      DevCounters *ctr, pk_device_status *status, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch>, kRasterThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma>, kRasterThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > p->n_tiles) grid = p->n_tiles;
   if (grid < 1) grid = 1;
-  k_raster_fwd<kBatch><<<(int)grid, kRasterThreads, 0, st>>>(
+  k_raster_fwd<kBatch, kFwdTma><<<(int)grid, kRasterThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
-      &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd));
+      &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status);
   return check_launch();
 }
 
@@ -175,11 +246,19 @@ extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, co
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
   if (cudaMemsetAsync(&ctr->tile_queue[0], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemsetAsync(&status->evals_fwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
+#define PK_FWD(B, M) \
+  return launch_fwd<B, M>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st)
+  const bool tma = p->opts.stage_fwd == PK_STAGE_BULK;
   switch (p->opts.batch) {
-    case 64: return launch_fwd<64>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st);
+    case 64:
+      if (tma) PK_FWD(64, true);
+      PK_FWD(64, false);
     case 128:
-      return launch_fwd<128>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st);
+      if (tma) PK_FWD(128, true);
+      PK_FWD(128, false);
     default:
-      return launch_fwd<256>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st);
+      if (tma) PK_FWD(256, true);
+      PK_FWD(256, false);
   }
+#undef PK_FWD
 }

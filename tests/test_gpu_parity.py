@@ -393,33 +393,34 @@ def test_nothing_visible_gives_background():
 
 
 def test_every_batch_size_and_autotune():
-    """The compositing batch (64, 128, 256 splats) changes nothing but speed:
-    images, transmittance and contributor counts are bit-identical, 2D
-    gradients equal up to the order of their atomic sums; pk_autotune keeps
-    one of the three."""
+    """The compositing batch (64, 128, 256 splats) and the staging mode (loads
+    or bulk copies) change nothing but speed: images, transmittance and
+    contributor counts are bit-identical, 2D gradients equal up to the order
+    of their atomic sums; pk_autotune keeps one of the choices."""
     pk = _pk()
     sc = H.scene_small_sh3(seed=707)
     atlas, occ, dyn = H.upload(sc)
     w = torch.from_numpy(np.random.default_rng(8).standard_normal(3 * sc.pixels).astype(np.float32)).cuda()
     out = {}
-    for b in (64, 128, 256):
-        r = pk.Renderer(pk.Plan.for_scene(sc, batch=b))
+    for case in ((64, "loads", "bulk"), (128, "bulk", "loads"), (256, "loads", "loads"), (256, "bulk", "bulk")):
+        b, mf, mb = case
+        r = pk.Renderer(pk.Plan.for_scene(sc, batch=b, stage_fwd=mf, stage_bwd=mb))
         assert r.ensure_capacity(atlas, occ, dyn)["flags"] == 0
         g = torch.zeros(atlas.numel(), dtype=torch.float32, device="cuda")
         r.backward(w, g)
         torch.cuda.synchronize()
-        out[b] = (r.image.clone(), r.T.clone(), r.n_contrib.clone(), r.grad2d.clone())
-    for b in (64, 128):
+        out[case] = (r.image.clone(), r.T.clone(), r.n_contrib.clone(), r.grad2d.clone())
+    ref = out[(256, "loads", "loads")]
+    for case, got in out.items():
         for k in range(3):
-            assert torch.equal(out[b][k], out[256][k])
-        assert H.rel_err(out[b][3].cpu().numpy().astype(np.float64),
-                         out[256][3].cpu().numpy().astype(np.float64)) < 1e-5
+            assert torch.equal(got[k], ref[k]), case
+        assert H.rel_err(got[3].cpu().numpy().astype(np.float64), ref[3].cpu().numpy().astype(np.float64)) < 1e-5
     r = pk.Renderer(pk.Plan.for_scene(sc))
     target = torch.from_numpy(synth.random_target(sc)).cuda()
     r.ensure_capacity(atlas, occ, dyn)
     chosen = r.autotune(atlas, occ, dyn, target)
     assert chosen in (64, 128, 256) and r.plan.batch == chosen
-    assert torch.equal(r.image, out[256][0])
+    assert torch.equal(r.image, ref[0])
 
 
 def test_render_fwd_bwd_convenience_calls():
