@@ -126,8 +126,8 @@ def algorithmic_bytes(plan, texel_bytes, dups, n_dyn):
 # Sources of each rooflined kernel: the DRAM traffic measured by ncu is
 # reported only while these still hash to the profiled version.
 KERNEL_SOURCES = {
-    "a4_rasterize_fwd": ("k_raster_fwd", ["pk_raster_fwd.cu", "pk_raster.cuh", "pk_common.cuh"]),
-    "a5_rasterize_bwd": ("k_raster_bwd", ["pk_raster_bwd.cu", "pk_raster.cuh", "pk_common.cuh"]),
+    "a4_rasterize_fwd": ("k_raster_fwd", ["pk_raster_fwd.cu", "pk_raster.cuh", "pk_common.cuh", "pk_tma.cuh"]),
+    "a5_rasterize_bwd": ("k_raster_bwd", ["pk_raster_bwd.cu", "pk_raster.cuh", "pk_common.cuh", "pk_tma.cuh"]),
 }
 
 
