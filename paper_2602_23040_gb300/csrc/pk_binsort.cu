@@ -124,6 +124,11 @@ __device__ __forceinline__ bool tile_hit(const Foot &f, int tx, int ty, int W, i
   return ellipse_hits_rect(f, x0, x1, y0, y1);
 }
 
+// A pair with at most this many candidate tiles keeps a bit mask of its
+// receiving candidates from the count pass, so the emission need not test
+// them again.
+constexpr uint32_t kMaskBits = 64;
+
 // Per-warp staging of 32 splats' candidate rectangles for the cooperative
 // walk over their candidate tiles (one candidate per lane per step).
 struct WarpSplat {
@@ -194,11 +199,11 @@ __device__ __forceinline__ T block_excl_scan(T v, T &total, T *s) {
 // Receiving tiles per pair.  Rectangle mode: the size of the r-square.
 // Ellipse mode: a warp walks the candidate tiles of its 32 pairs together,
 // one candidate per lane, so long and short pairs share the work; each pair
-// also keeps a bit mask of its receiving candidates when it has <= 32 of
+// also keeps a bit mask of its receiving candidates when it has <= 64 of
 // them, so the emission need not test them again.
 __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict__ rec, int64_t pairs, int64_t N,
                                                          const DevView *__restrict__ views, int T, int mode,
-                                                         uint32_t *__restrict__ cnt, uint32_t *__restrict__ rmask) {
+                                                         uint32_t *__restrict__ cnt, uint64_t *__restrict__ rmask) {
   __shared__ WarpSplat s_ws[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
@@ -236,7 +241,8 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
     const uint32_t incl = warp_incl_scan(ncand);
     const uint32_t excl = incl - ncand;
     const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
-    uint32_t mine = 0, mask = 0;
+    uint32_t mine = 0;
+    uint64_t mask = 0;
     for (uint32_t e0 = 0; e0 < E; e0 += 32) {
       const uint32_t e = e0 + lane;
       const uint32_t ee = e < E ? e : E - 1;
@@ -261,7 +267,7 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
         const uint32_t span = hi - lo;
         const uint32_t bits = (bal >> (lo - e0)) & (span >= 32 ? 0xffffffffu : ((1u << span) - 1u));
         mine += __popc(bits);
-        if (ncand <= 32) mask |= bits << (lo - excl);
+        if (ncand <= kMaskBits) mask |= (uint64_t)bits << (lo - excl);
       }
     }
     (void)lt;
@@ -672,7 +678,7 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
 // ---------------------------------------------------------------------------
 
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
-                                                   const uint32_t *__restrict__ offs, const uint32_t *__restrict__ rmask,
+                                                   const uint32_t *__restrict__ offs, const uint64_t *__restrict__ rmask,
                                                    const DevCounters *ctr, const DevView *__restrict__ views,
                                                    int64_t N, int T, int mode, uint32_t *__restrict__ keys,
                                                    uint32_t *__restrict__ vals) {
@@ -684,7 +690,8 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
   for (uint64_t w = blockIdx.x * (uint64_t)kWarps + warp; w * 32 < n; w += nwarps) {
     const uint64_t k = w * 32 + lane;
-    uint32_t ncand = 0, p = 0, msk = 0;
+    uint32_t ncand = 0, p = 0;
+    uint64_t msk = 0;
     WarpSplat ws;
     ws.g0 = make_float4(0.f, 0.f, 0.f, 0.f);
     ws.g1 = ws.g0;
@@ -705,7 +712,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
         ws.r0 = make_int4(x0, y0, wt, v.width);
         ws.r1 = make_int4(v.height, (int)((uint32_t)v.tile_off + (uint32_t)y0 * v.tiles_x + (uint32_t)x0),
                           v.tiles_x, (int)ncand);
-        if (mode != PK_BIN_RECT && ncand <= 32) msk = rmask[p];
+        if (mode != PK_BIN_RECT && ncand <= kMaskBits) msk = rmask[p];
       }
     }
     s_ws[warp][lane] = ws;
@@ -724,7 +731,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const int o = candidate_owner(incl, ee);
       const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
       const uint32_t o_p = __shfl_sync(0xffffffffu, p, o);
-      const uint32_t o_msk = __shfl_sync(0xffffffffu, msk, o);
+      const uint64_t o_msk = __shfl_sync(0xffffffffu, msk, o);
       const WarpSplat &os = s_ws[warp][o];
       const int4 r0 = os.r0, r1 = os.r1;
       const uint32_t local = ee - o_excl;
@@ -732,7 +739,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       divmod_small(local, (uint32_t)r0.z, __shfl_sync(0xffffffffu, rw, o), ly, lx);
       bool take = e < E;
       if (take && mode != PK_BIN_RECT) {
-        if (r1.w <= 32) {
+        if (r1.w <= kMaskBits) {
           take = (o_msk >> local) & 1u;
         } else {
           const float4 g0 = os.g0, g1 = os.g1;
@@ -827,7 +834,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   uint32_t *zk[2] = {at<uint32_t>(ws, L.zkey0), at<uint32_t>(ws, L.zkey1)};
   uint32_t *pv[2] = {at<uint32_t>(ws, L.pval0), at<uint32_t>(ws, L.pval1)};
   uint32_t *offs = at<uint32_t>(ws, L.offs);
-  uint32_t *rmask = at<uint32_t>(ws, L.rmask);
+  uint64_t *rmask = at<uint64_t>(ws, L.rmask);
   uint64_t *bsum = at<uint64_t>(ws, L.blocksums);
   uint32_t *hist = at<uint32_t>(ws, L.hist);
   uint32_t *dk0 = at<uint32_t>(ws, L.dkey0), *dk1 = at<uint32_t>(ws, L.dkey1);
@@ -964,7 +971,7 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   L.pval0 = take(sizeof(uint32_t) * pairs);
   L.pval1 = take(sizeof(uint32_t) * pairs);
   L.offs = take(sizeof(uint32_t) * pairs);
-  L.rmask = take(sizeof(uint32_t) * pairs);
+  L.rmask = take(sizeof(uint64_t) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
   L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
