@@ -118,6 +118,26 @@ __device__ __forceinline__ void divmod_small(uint32_t local, uint32_t w, float r
   r = (uint32_t)rr;
 }
 
+// Ellipse mode: the candidate tiles need only cover the footprint's
+// bounding box |dx| <= 3 sqrt(Sigma_xx), |dy| <= 3 sqrt(Sigma_yy) (Sigma =
+// conic^-1) rather than the whole r-square.  The box is widened by 1 % and
+// one pixel, far beyond FP32 rounding, so every tile the exact test accepts
+// stays a candidate and the entries are unchanged; it only skips tiles
+// that the test would reject.
+__device__ __forceinline__ void shrink_to_footprint(float mx, float my, float a, float b, float c, int T, int &tx0,
+                                                    int &ty0, int &tx1, int &ty1) {
+  const float det = a * c - b * b;
+  if (!(a > 0.f) || !(c > 0.f) || !(det > 0.f) || !isfinite(det)) return;
+  const float ex = 3.f * sqrtf(c / det) * 1.01f + 1.f, ey = 3.f * sqrtf(a / det) * 1.01f + 1.f;
+  // tile tx holds pixel centres [tx T + 0.5, tx T + T - 0.5]
+  const float fx0 = floorf((mx - ex - 0.5f) / (float)T), fx1 = floorf((mx + ex - 0.5f) / (float)T);
+  const float fy0 = floorf((my - ey - 0.5f) / (float)T), fy1 = floorf((my + ey - 0.5f) / (float)T);
+  if (fx0 > (float)tx0) tx0 = (int)fminf(fx0, (float)tx1);
+  if (fx1 < (float)tx1) tx1 = (int)fmaxf(fx1, (float)tx0);
+  if (fy0 > (float)ty0) ty0 = (int)fminf(fy0, (float)ty1);
+  if (fy1 < (float)ty1) ty1 = (int)fmaxf(fy1, (float)ty0);
+}
+
 __device__ __forceinline__ bool tile_hit(const Foot &f, int tx, int ty, int W, int H, int T) {
   const float x0 = (float)(tx * T) + 0.5f, y0 = (float)(ty * T) + 0.5f;
   const float x1 = (float)min((tx + 1) * T, W) - 0.5f, y1 = (float)min((ty + 1) * T, H) - 0.5f;
@@ -222,6 +242,7 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
       const DevView &v = views[p / N];
       int x0, y0, x1, y1;
       if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
+        if (mode != PK_BIN_RECT) shrink_to_footprint(a.x, a.y, a.z, a.w, b.x, T, x0, y0, x1, y1);
         const int wt = x1 - x0 + 1;
         ncand = (uint32_t)(wt * (y1 - y0 + 1));
         const Foot f = make_foot(a.x, a.y, a.z, a.w, b.x);
@@ -704,6 +725,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const DevView &v = views[p / N];
       int x0, y0, x1, y1;
       if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
+        if (mode != PK_BIN_RECT) shrink_to_footprint(a.x, a.y, a.z, a.w, b.x, T, x0, y0, x1, y1);
         const int wt = x1 - x0 + 1;
         ncand = (uint32_t)(wt * (y1 - y0 + 1));
         const Foot f = make_foot(a.x, a.y, a.z, a.w, b.x);
