@@ -91,11 +91,13 @@ struct Hit {
 // alpha of a staged splat at pixel centre (px, py); false if skipped.
 // alpha = min(0.99, o 2^power).  Written with explicit round-to-nearest
 // operations so the forward and the backward decide identically.
-__device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, float pcut, float px, float py,
-                                            Hit &h) {
-  h.dx = __fsub_rn(px, a.x);
+// dx = px - m_x and zx = A dx are shared by the two pixels of a thread
+// (same column), so the caller computes them once per splat.
+__device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, float pcut, float dx, float zx,
+                                            float py, Hit &h) {
+  h.dx = dx;
   h.dy = __fsub_rn(py, a.y);
-  const float u = __fmaf_rn(a.w, h.dy, __fmul_rn(a.z, h.dx));
+  const float u = __fmaf_rn(a.w, h.dy, zx);
   const float power = __fmaf_rn(u, h.dx, __fmul_rn(__fmul_rn(b.x, h.dy), h.dy));
   if (!(power >= pcut)) return false;
   h.G = ex2_approx(power);

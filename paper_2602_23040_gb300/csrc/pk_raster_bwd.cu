@@ -71,11 +71,11 @@ __device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int l
 // after the splat) becomes T before it; S (colour composited behind,
 // background included) takes the splat's own term; the nine gradients are
 // added to acc.  Returns false if the pixel skips the splat.
-__device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, const float4 &c4, float px, float py,
-                                              float g0, float g1, float g2, float &T, float &S0, float &S1,
+__device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, const float4 &c4, float dx, float zx,
+                                              float py, float g0, float g1, float g2, float &T, float &S0, float &S1,
                                               float &S2, float (&acc)[9]) {
   Hit h;
-  if (!splat_alpha(a, b, c4.z, px, py, h)) return false;
+  if (!splat_alpha(a, b, c4.z, dx, zx, py, h)) return false;
   const float om = __fsub_rn(1.f, h.alpha);
   const float inv = rcp_approx(om);
   const float Ti = T * inv;
@@ -126,7 +126,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
   int ox, oy;
   pixel_of(tid, ox, oy);
   const int my_idx = reduce_scatter9_index(lane);
-  unsigned long long evals = 0;
+  uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
   bool timed_out = false;
   if (kTma) {
@@ -246,15 +246,16 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
           const int j = 32 * k + bit;
           const uint32_t pos = beg + (uint32_t)j;   // 0-based list position
           const float4 a = s_a[j], b = s_b[j], c4 = s_c[j];
+          const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
           float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           bool act = false;
           if (pos < nc0) {
             ++evals;
-            act |= pixel_adjoint(a, b, c4, px, py0, g00, g01, g02, T0, S00, S01, S02, acc);
+            act |= pixel_adjoint(a, b, c4, dx, zx, py0, g00, g01, g02, T0, S00, S01, S02, acc);
           }
           if (pos < nc1) {
             ++evals;
-            act |= pixel_adjoint(a, b, c4, px, py1, g10, g11, g12, T1, S10, S11, S12, acc);
+            act |= pixel_adjoint(a, b, c4, dx, zx, py1, g10, g11, g12, T1, S10, S11, S12, acc);
           }
           if (__any_sync(0xffffffffu, act)) {
             const float sum = warp_reduce_scatter9(acc, lane);
@@ -271,8 +272,9 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     __syncthreads();
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-  if (lane == 0 && evals) atomicAdd(evals_out, evals);
+  unsigned long long ev = evals;
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+  if (lane == 0 && ev) atomicAdd(evals_out, ev);
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.

@@ -34,7 +34,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
   const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy;
   pixel_of(tid, ox, oy);
-  unsigned long long evals = 0;
+  uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
   bool timed_out = false;
   if (kTma) {
@@ -132,11 +132,12 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
             const int j = 32 * k + __ffs(m) - 1;
             m &= m - 1;
             const float4 a = s_a[j], b = s_b[j], c = s_c[j];
+            const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
             const uint32_t pos1 = base - s + (uint32_t)j + 1u;
             Hit h;
             if (!done0) {
               ++evals;
-              if (splat_alpha(a, b, c.z, px, py0, h)) {
+              if (splat_alpha(a, b, c.z, dx, zx, py0, h)) {
                 const float Tn = __fmul_rn(T0, __fsub_rn(1.f, h.alpha));
                 if (Tn < kTMin) {
                   done0 = true;
@@ -152,7 +153,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
             }
             if (!done1) {
               ++evals;
-              if (splat_alpha(a, b, c.z, px, py1, h)) {
+              if (splat_alpha(a, b, c.z, dx, zx, py1, h)) {
                 const float Tn = __fmul_rn(T1, __fsub_rn(1.f, h.alpha));
                 if (Tn < kTMin) {
                   done1 = true;
@@ -209,8 +210,9 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
   }
   // one atomic per warp for the evaluation counter
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-  if (lane == 0 && evals) atomicAdd(evals_out, evals);
+  unsigned long long ev = evals;
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+  if (lane == 0 && ev) atomicAdd(evals_out, ev);
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
