@@ -184,7 +184,8 @@ void pk_plan_destroy(pk_plan *plan);
  * caller's current inputs and on `stream`, pk_rasterize_fwd followed by
  * pk_rasterize_bwd for every staging batch (64, 128, 256 splats) and keeps
  * the fastest, then times each kernel with both staging modes and keeps the
- * faster one per kernel (two timed runs after one warm-up each).  The
+ * faster one per kernel (two timed runs after one warm-up each; a choice
+ * other than the default 256 / plain loads must be more than 2 % faster).  The
  * choices are stored in the plan's options; *chosen_batch receives the
  * batch (may be NULL).  The tile side is fixed at 16 and the sort's digit
  * width at 8 bits (10- and 11-bit digits measured slower).  The arguments
