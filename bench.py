@@ -208,6 +208,33 @@ def cpu_baseline(scene, budget_s=20.0, window=256):
             "seconds": dt}
 
 
+def _oracle_worker(args):
+    """One process of the all-core oracle baseline: its own copy of the
+    scene, its own view windows; returns (pixels, compute seconds)."""
+    config, n_views, window, seed = args
+    import oracle as orc
+    scene = synth.config_scene(config, n_views=n_views or None)
+    soa, texel, dynflag = orc.gather(scene)
+    views = window_views(scene, 1, window, seed=seed)
+    t0 = time.perf_counter()
+    pix = oracle_step(orc, scene, views, soa, texel, dynflag, seed)
+    return pix, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(config, n_views, window=256):
+    """The same oracle, one process per host core (spawned), each rendering
+    one window: pixels of all processes over the slowest process's time."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(config, n_views, window, 100 + i) for i in range(cores)])
+    pix = sum(r[0] for r in res)
+    slow = max(r[1] for r in res)
+    return {"value": pix / slow / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x one {window}x{window} px view window, fwd + L1 + bwd in FP64",
+            "seconds": slow}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the FP64 CPU oracle, on bounded samples of the same workload."""
     if rank != 0:
@@ -567,6 +594,7 @@ def main():
 
     if not args.profile and not args.no_cpu_baseline and rank == 0:
         out["cpu_baseline"] = cpu_baseline(scene)
+        out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args.config, args.views)
 
     if rank == 0:
         print(json.dumps(out), flush=True)

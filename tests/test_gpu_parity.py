@@ -444,3 +444,32 @@ def test_render_fwd_bwd_convenience_calls():
     torch.cuda.synchronize()
     assert torch.equal(img, img_ref)
     assert H.rel_err(g.cpu().numpy().astype(np.float64), g_ref.cpu().numpy().astype(np.float64)) < 1e-5
+
+
+@pytest.mark.parametrize("mode", ["ellipse", "rect"])
+def test_binning_from_fp64_projection_differs_only_at_borderline_pairs(orc, mode):
+    """The sort is bit-exact as a function of the records; fed the oracle's
+    own FP64 projection (rounded to FP32) instead of the GPU's, only pairs
+    whose tile set sits on a threshold may differ: count them (a tiny
+    fraction) and check that their summed entry counts nearly agree."""
+    pk = _pk()
+    sc = H.scene_small_sh3(seed=811)
+    r = pk.Renderer(pk.Plan.for_scene(sc, bin_mode=mode))
+    atlas, occ, dyn = H.upload(sc)
+    assert r.ensure_capacity(atlas, occ, dyn)["flags"] == 0
+    V, N = len(sc.views), r.plan.N
+    gpu_rec = r.records.cpu().numpy().reshape(V * N, 12)
+    o = orc.forward(sc, mode={"ellipse": orc.BIN_ELLIPSE, "rect": orc.BIN_RECT}[mode])
+    ora_rec = o["rec"].reshape(V * N, 12).astype(np.float32)
+    va = orc.views_array(sc.views)
+    m = {"ellipse": orc.BIN_ELLIPSE, "rect": orc.BIN_RECT}[mode]
+
+    def per_pair(rr):
+        vals, _ = orc.bin_sort32(rr[:, 0], rr[:, 1], rr[:, 7], rr[:, 6], va, N, 16, rr[:, 2], rr[:, 3], rr[:, 4], mode=m)
+        return np.bincount(vals, minlength=V * N)
+
+    a, b = per_pair(gpu_rec), per_pair(ora_rec)
+    differ = int(np.count_nonzero(a != b))
+    print(f"{mode}: {differ} of {V * N} pairs have another tile count from the FP64 projection")
+    assert differ <= max(3, 0.002 * V * N)
+    assert abs(int(a.sum()) - int(b.sum())) <= 2 * max(1, differ)
