@@ -269,15 +269,15 @@ pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *s
  * inputs, outputs and bit-exact result as pk_bin_and_sort; the scratch is a
  * 64 MiB array inside the library (reserved on every GPU that loads it, for
  * the life of the process), so the plan must satisfy 32 * V * N + 12 *
- * max_dups + 144 * V + about 0.55 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
+ * max_dups + 152 * V + about 0.55 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
  * nothing is enqueued.  n_entries: out, one device uint32 -- the entries
  * written, or 0xFFFFFFFF if they exceeded max_dups (then nothing was
  * emitted).  The first call on a device looks up the array's address; make
  * it before any stream capture.  Every call shares the one array and leaves
  * its contents behind: calls whose work can overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
- * The call copies the plan's view table from host memory each time and
- * never allocates. */
+ * The call copies the plan's view and tile tables from host memory each
+ * time and never allocates. */
 pk_status pk_bin_and_sort_noalloc(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
                                   uint32_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream);
 

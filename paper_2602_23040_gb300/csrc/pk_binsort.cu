@@ -437,6 +437,35 @@ __global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const 
 // up to RB bits.
 // ---------------------------------------------------------------------------
 
+// Where a radix block works.  Global mode (tab == nullptr): the whole
+// array [0, n) split over the grid, histogram counter of digit d at
+// d * gridDim.x + blockIdx.x.  Segmented mode: block b belongs to segment
+// tab[b].x (a view's entries [seg[v], seg[v + 1])), as part tab[b].y of
+// tab[b].z parts, counters at tab[b].w + d * tab[b].z + tab[b].y, so the
+// one scan of the histogram keeps every segment in place and sorts within
+// it.
+struct SegSpec {
+  const int4 *tab;
+  const uint32_t *seg;
+};
+
+__device__ __forceinline__ void radix_chunk(const SegSpec &sp, uint64_t n, int tile, uint64_t &b0, uint64_t &b1,
+                                            uint32_t &hbase, uint32_t &hstride) {
+  if (!sp.tab) {
+    chunk_of(n, gridDim.x, blockIdx.x, tile, b0, b1);
+    hbase = blockIdx.x;
+    hstride = gridDim.x;
+    return;
+  }
+  const int4 t = sp.tab[blockIdx.x];
+  const uint64_t s0 = sp.seg[t.x], s1 = sp.seg[t.x + 1];
+  chunk_of(s1 - s0, t.z, t.y, tile, b0, b1);
+  b0 += s0;
+  b1 += s0;
+  hbase = (uint32_t)(t.w + t.y);
+  hstride = (uint32_t)t.z;
+}
+
 template <int RB>
 struct Radix {
   static constexpr int kR = 1 << RB;                       // buckets
@@ -449,19 +478,22 @@ struct Radix {
 template <int RB>
 __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                             const uint32_t *n_dev, uint64_t n_host, int shift,
-                                                            uint32_t mask, uint32_t *__restrict__ hist) {
+                                                            uint32_t mask, uint32_t *__restrict__ hist, SegSpec sp) {
   using C = Radix<RB>;
   __shared__ uint32_t s_cnt[C::kCopies][C::kR];   // private digit counts
   for (int i = threadIdx.x; i < C::kCopies * C::kR; i += kThreads) (&s_cnt[0][0])[i] = 0;
   __syncthreads();
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
-  chunk_of(n, gridDim.x, blockIdx.x, C::kTile, b0, b1);
-  // chunks start on a multiple of the tile (itself a multiple of 4 keys):
-  // 16-byte aligned vector loads, four in flight per thread
-  const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + b0);
-  const uint64_t n4 = (b1 - b0) / 4;
+  uint32_t hbase, hstride;
+  radix_chunk(sp, n, C::kTile, b0, b1, hbase, hstride);
   uint32_t *cw = s_cnt[(threadIdx.x >> 5) % C::kCopies];
+  // up to 3 keys before the first 16-byte boundary (segments start anywhere)
+  const uint64_t a0 = min(b1, (b0 + 3) & ~uint64_t(3));
+  if (threadIdx.x < a0 - b0) atomicAdd(&cw[(__ldg(keys + b0 + threadIdx.x) >> shift) & mask], 1u);
+  // 16-byte vector loads, four in flight per thread
+  const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + a0);
+  const uint64_t n4 = (b1 - a0) / 4;
   for (uint64_t t0 = 0; t0 < n4; t0 += 4 * kThreads) {
     uint4 q[4];
 #pragma unroll
@@ -478,14 +510,14 @@ __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__re
       atomicAdd(&cw[(q[u].w >> shift) & mask], 1u);
     }
   }
-  for (uint64_t i = b0 + 4 * n4 + threadIdx.x; i < b1; i += kThreads)
+  for (uint64_t i = a0 + 4 * n4 + threadIdx.x; i < b1; i += kThreads)
     atomicAdd(&cw[(__ldg(keys + i) >> shift) & mask], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < C::kR; d += kThreads) {
     uint32_t t = 0;
 #pragma unroll
     for (int w = 0; w < C::kCopies; ++w) t += s_cnt[w][d];
-    hist[(size_t)d * gridDim.x + blockIdx.x] = t;
+    hist[hbase + (size_t)d * hstride] = t;
   }
 }
 
@@ -542,7 +574,8 @@ __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist
 template <int RB>
 struct Down {
   static constexpr int kTile = Radix<RB>::kTile;
-  static constexpr size_t kBuf = 2 * sizeof(uint32_t) * kTile;    // keys + values of one tile
+  static constexpr int kSpan = kTile + 4;                         // a tile plus up to 3 keys of misalignment
+  static constexpr size_t kBuf = 2 * sizeof(uint32_t) * kSpan;    // keys + values of one tile
   static constexpr size_t kSmem = 2 * kBuf + sizeof(uint16_t) * kWarps * Radix<RB>::kR +
                                   2 * sizeof(uint32_t) * Radix<RB>::kR + sizeof(uint32_t) * (kWarps + 1) +
                                   2 * sizeof(uint64_t) + 16;
@@ -552,9 +585,10 @@ template <int RB>
 __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist, pk_device_status *status) {
+    const uint32_t *__restrict__ hist, pk_device_status *status, SegSpec sp) {
   using C = Radix<RB>;
   constexpr int kTile = C::kTile;
+  constexpr int kSpan = Down<RB>::kSpan;
   extern __shared__ __align__(16) unsigned char s_raw[];
   uint32_t *buf[2] = {reinterpret_cast<uint32_t *>(s_raw), reinterpret_cast<uint32_t *>(s_raw + Down<RB>::kBuf)};
   uint16_t *s_wcnt = reinterpret_cast<uint16_t *>(s_raw + 2 * Down<RB>::kBuf);       // [kWarps][kR]
@@ -567,19 +601,23 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t n = load_n(n_dev, n_host);
   uint64_t b0, b1;
-  chunk_of(n, gridDim.x, blockIdx.x, kTile, b0, b1);
-  for (int d = tid; d < C::kR; d += kThreads) s_gbase[d] = hist[(size_t)d * gridDim.x + blockIdx.x];
+  uint32_t hbase, hstride;
+  radix_chunk(sp, n, kTile, b0, b1, hbase, hstride);
+  for (int d = tid; d < C::kR; d += kThreads) s_gbase[d] = hist[hbase + (size_t)d * hstride];
   const int ntile = (int)((b1 - b0 + kTile - 1) / kTile);
-  // the bulk-copied part of tile t: its first multiple of 4 keys
+  // Every tile of this chunk starts mis = b0 mod 4 keys past a 16-byte
+  // boundary: the bulk copy starts at that boundary and takes whole
+  // 16-byte groups; tile key li lands at buf[mis + li].
+  const uint32_t mis = (uint32_t)(b0 & 3);
   auto issue = [&](int t) {
     const uint64_t base = b0 + (uint64_t)t * kTile;
     const uint32_t valid = (uint32_t)min((uint64_t)kTile, b1 - base);
-    const uint32_t bytes = (valid & ~3u) * 4u;
+    const uint32_t bytes = ((mis + valid) & ~3u) * 4u;
     uint32_t *dst = buf[t & 1];
     mbar_expect_tx(&s_bar[t & 1], 2 * bytes);
     if (bytes) {
-      tma_load_1d(dst, kin + base, bytes, &s_bar[t & 1]);
-      tma_load_1d(dst + kTile, vin + base, bytes, &s_bar[t & 1]);
+      tma_load_1d(dst, kin + (base - mis), bytes, &s_bar[t & 1]);
+      tma_load_1d(dst + kSpan, vin + (base - mis), bytes, &s_bar[t & 1]);
     }
   };
   if (tid == 0) {
@@ -597,13 +635,13 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
     const int cur = t & 1;
     const uint64_t base = b0 + (uint64_t)t * kTile;
     const uint32_t valid = (uint32_t)min((uint64_t)kTile, b1 - base);
-    uint32_t *bk = buf[cur], *bv = buf[cur] + kTile;
+    uint32_t *bk = buf[cur] + mis, *bv = buf[cur] + kSpan + mis;
     // the other buffer was last written (by this block's scatter) before the
     // fence and barrier that ended the previous tile
     if (tid == 0 && t + 1 < ntile) issue(t + 1);
     const bool ok = mbar_wait_bounded(&s_bar[cur], parity[cur]);
-    // keys past the last multiple of 4 come by plain loads
-    const uint32_t tail0 = valid & ~3u;
+    // keys past the last whole 16-byte group come by plain loads
+    const uint32_t tail0 = ((mis + valid) & ~3u) - mis;
     if (tid < (int)(valid - tail0)) {
       bk[tail0 + tid] = __ldg(kin + base + tail0 + tid);
       bv[tail0 + tid] = __ldg(vin + base + tail0 + tid);
@@ -701,8 +739,8 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
                                                    const uint32_t *__restrict__ offs, const uint64_t *__restrict__ rmask,
                                                    const DevCounters *ctr, const DevView *__restrict__ views,
-                                                   int64_t N, int T, int mode, uint32_t *__restrict__ keys,
-                                                   uint32_t *__restrict__ vals) {
+                                                   int64_t N, int T, int mode, bool local_keys,
+                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
   __shared__ WarpSplat s_ws[kWarps][32];
   if (ctr->dups == 0) return;
   const uint64_t n = ctr->n_valid;
@@ -732,7 +770,8 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
         ws.g0 = make_float4(f.mx, f.my, f.a, f.b);
         ws.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
         ws.r0 = make_int4(x0, y0, wt, v.width);
-        ws.r1 = make_int4(v.height, (int)((uint32_t)v.tile_off + (uint32_t)y0 * v.tiles_x + (uint32_t)x0),
+        ws.r1 = make_int4(v.height, (int)((local_keys ? 0u : (uint32_t)v.tile_off) + (uint32_t)y0 * v.tiles_x +
+                                          (uint32_t)x0),
                           v.tiles_x, (int)ncand);
         if (mode != PK_BIN_RECT && ncand <= kMaskBits) msk = rmask[p];
       }
@@ -782,13 +821,17 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
 }
 
 // Tile ranges from the sorted tile ids; four entries per thread.
-__global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, const DevCounters *ctr,
+// Per-tile [start, end) of the sorted entries.  Keys are global tile ids,
+// or (seg != nullptr) per-view local ids: then the entry's view is found in
+// the segment starts seg[0..V) and its tile_off added.
+__global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *seg,
+                                                     const uint32_t *__restrict__ toff, int V, const DevCounters *ctr,
                                                      uint32_t *__restrict__ ranges) {
   const uint32_t n = ctr->dups;
   const uint32_t nq = (n + 3) / 4;
   for (uint32_t q = blockIdx.x * kThreads + threadIdx.x; q < nq; q += gridDim.x * kThreads) {
     const uint32_t i0 = 4 * q;
-    uint32_t k[6];   // keys[i0 - 1 .. i0 + 4]
+    uint32_t k[6];   // tile ids of entries i0 - 1 .. i0 + 4
     k[0] = i0 ? __ldg(keys + i0 - 1) : 0xffffffffu;
     if (i0 + 3 < n) {
       const uint4 v = __ldg(reinterpret_cast<const uint4 *>(keys + i0));
@@ -798,6 +841,22 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
       for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < n ? __ldg(keys + i0 + j) : 0xffffffffu;
     }
     k[5] = i0 + 4 < n ? __ldg(keys + i0 + 4) : 0xffffffffu;
+    if (seg) {
+      // view of entry i0 - 1 (or i0), then step forward across segment starts
+      const uint32_t first = i0 ? i0 - 1 : 0;
+      int lo = 0, hi = V - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(seg + mid) <= first) lo = mid; else hi = mid - 1;
+      }
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        const int64_t i = (int64_t)i0 - 1 + j;
+        if (i < 0 || i >= (int64_t)n) continue;
+        while (lo + 1 < V && __ldg(seg + lo + 1) <= (uint32_t)i) ++lo;
+        k[j] += __ldg(toff + lo);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint32_t i = i0 + j;
@@ -809,19 +868,48 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
   }
 }
 
+// View of each compacted pair in the current order (keys of the pass that
+// groups the depth-sorted pairs by view).
+__global__ __launch_bounds__(kThreads) void k_view_keys(const uint32_t *__restrict__ pval, const uint32_t *n_dev,
+                                                        uint32_t N, uint32_t *__restrict__ vkey) {
+  const uint32_t n = *n_dev;
+  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) vkey[i] = pval[i] / N;
+}
+
+// Entry offset of every view's first entry, pairs being in (view, depth)
+// order: seg[v] = offs of the first pair of view >= v (the total where no
+// such pair is left); seg[V] = the total.
+__global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__restrict__ pval,
+                                                            const uint32_t *__restrict__ offs,
+                                                            const DevCounters *ctr, uint32_t N, int V,
+                                                            uint32_t *__restrict__ seg) {
+  const uint32_t n = ctr->n_valid, total = ctr->dups;
+  if (n == 0 || total == 0) {
+    for (int v = blockIdx.x * kThreads + threadIdx.x; v <= V; v += gridDim.x * kThreads) seg[v] = 0;
+    return;
+  }
+  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+    const int v = (int)(pval[i] / N);
+    const int prev = i ? (int)(pval[i - 1] / N) : -1;
+    for (int u = prev + 1; u <= v; ++u) seg[u] = offs[i];
+    if (i + 1 == n)
+      for (int u = v + 1; u <= V; ++u) seg[u] = total;
+  }
+}
+
 template <int RB>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                        pk_device_status *status, cudaStream_t st) {
+                        pk_device_status *status, SegSpec sp, cudaStream_t st) {
   using C = Radix<RB>;
   if (cudaFuncSetAttribute(k_radix_downsweep<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Down<RB>::kSmem) != cudaSuccess)
     return PK_ERR_CUDA;
   const uint32_t mask = (1u << bits) - 1u;
-  k_radix_upsweep<RB><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist);
+  k_radix_upsweep<RB><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist, sp);
   k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
   k_radix_downsweep<RB><<<nblocks, kThreads, Down<RB>::kSmem, st>>>(kin, vin, kout, vout, n_dev, n_host, shift,
-                                                                      mask, hist, status);
+                                                                      mask, hist, status, sp);
   return check_launch();
 }
 
@@ -830,9 +918,41 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 // per SM with scattered short runs and came out slower overall.)
 pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                     pk_device_status *status, cudaStream_t st) {
-  return radix_pass_rb<kMaxRadixBits>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, st);
+                     pk_device_status *status, cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}) {
+  return radix_pass_rb<kMaxRadixBits>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, sp,
+                                      st);
 }
+
+}  // namespace
+
+// Blocks of the segmented tile sort: per view a share of `nsort` blocks
+// proportional to its tiles (at least one), each {view, part, parts,
+// first histogram counter}.  Returns the number of blocks, or 0 when the
+// views do not fit the histogram (then the tile sort runs unsegmented).
+int pk::sort_blocks() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // 3 resident per SM, within the histogram's capacity
+  return std::max(1, std::min(kSortBlocks, 3 * sms));
+}
+
+int pk::seg_table(const pk_plan *p, int nsort, int4 *tab) {
+  if (p->V < 2) return 0;
+  int64_t tiles = 0;
+  for (int v = 0; v < p->V; ++v) tiles += (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y;
+  int nb = 0;
+  for (int v = 0; v < p->V; ++v) {
+    const int64_t t = (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y;
+    const int parts = std::max<int>(1, (int)((int64_t)nsort * t / std::max<int64_t>(1, tiles)));
+    if (nb + parts > kSortBlocks) return 0;
+    for (int j = 0; j < parts; ++j) tab[nb + j] = make_int4(v, j, parts, (1 << kMaxRadixBits) * nb);
+    nb += parts;
+  }
+  return nb;
+}
+
+namespace {
 
 // Digit widths for a key of `bits` bits: as few passes of <= kMaxRadixBits
 // bits as possible, split evenly.
@@ -866,8 +986,12 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // sort blocks: 3 resident per SM, within the histogram's capacity
-  const int nsort = std::max(1, std::min(kSortBlocks, 3 * sms));
+  const int nsort = sort_blocks();
+  // segmented tile sort: pairs grouped by view, per-view local tile ids
+  int4 tab_host[kSortBlocks];
+  const int nseg = seg_table(p, nsort, tab_host);
+  const int4 *tab = at<int4>(ws, L.sblk);
+  uint32_t *vseg = at<uint32_t>(ws, L.vseg);
 
   if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
     return PK_ERR_CUDA;
@@ -892,27 +1016,55 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
       return e;
     shift += widths[pass];
   }
-  const uint32_t *pval = pv[np & 1];
-  // emission offsets in depth order, capacity check
+  int cur = np & 1;
+  if (nseg > 0) {
+    // stable pass on the view: pairs in (view, depth) order
+    int vbits = 1;
+    while ((1 << vbits) < p->V) ++vbits;
+    k_view_keys<<<std::max(1, sms) * 8, kThreads, 0, st>>>(pv[cur], n_valid, (uint32_t)p->N, zk[cur]);
+    for (int shift_v = 0; shift_v < vbits; shift_v += kMaxRadixBits) {
+      const int bits = std::min(kMaxRadixBits, vbits - shift_v);
+      if ((e = radix_pass(zk[cur], pv[cur], zk[cur ^ 1], pv[cur ^ 1], n_valid, 0, shift_v, bits, hist, nsort, status,
+                          st)) != PK_OK)
+        return e;
+      cur ^= 1;
+    }
+  }
+  const uint32_t *pval = pv[cur];
+  // emission offsets in (view,) depth order, capacity check
   SrcSorted ss{cnt, pval};
   k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, maxd, ctr, status);
   k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, bsum, ctr, offs);
   // emission and the stable tile sort; the last pass lands in sorted_vals
-  np = radix_plan(p->tile_bits, widths);
+  int key_bits = p->tile_bits;
+  SegSpec sp{nullptr, nullptr};
+  int nblocks = nsort;
+  if (nseg > 0) {
+    int64_t most = 1;
+    for (int v = 0; v < p->V; ++v)
+      most = std::max<int64_t>(most, (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y);
+    key_bits = 1;
+    while ((int64_t(1) << key_bits) < most) ++key_bits;
+    k_view_segments<<<std::max(1, sms) * 8, kThreads, 0, st>>>(pval, offs, ctr, (uint32_t)p->N, p->V, vseg);
+    sp = SegSpec{tab, vseg};
+    nblocks = nseg;
+  }
+  np = radix_plan(key_bits, widths);
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
   k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, rmask, ctr, views, p->N, p->T,
-                                                      p->opts.bin_mode, kbuf[0], vbuf[0]);
+                                                      p->opts.bin_mode, nseg > 0, kbuf[0], vbuf[0]);
   shift = 0;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
-    if ((e = radix_pass(kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nsort, status,
-                        st)) != PK_OK)
+    if ((e = radix_pass(kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
+                        status, st, sp)) != PK_OK)
       return e;
     shift += widths[pass];
   }
-  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], ctr, tile_ranges);
+  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], nseg > 0 ? vseg : nullptr,
+                                                        at<uint32_t>(ws, L.toff), p->V, ctr, tile_ranges);
   return check_launch();
 }
 
@@ -987,6 +1139,9 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   L.status = take(sizeof(pk_device_status));
   L.counters = take(sizeof(DevCounters));
   L.views = take(sizeof(DevView) * p->V);
+  L.toff = take(sizeof(uint32_t) * (p->V + 1));
+  L.sblk = take(sizeof(int4) * kSortBlocks);
+  L.vseg = take(sizeof(uint32_t) * (p->V + 1));
   L.pair_cnt = take(sizeof(uint32_t) * pairs);
   L.zkey0 = take(sizeof(uint32_t) * pairs);
   L.zkey1 = take(sizeof(uint32_t) * pairs);
@@ -1010,6 +1165,13 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   if (cudaMemsetAsync(at<char>(ws, L.status), 0, L.views - L.status, st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemcpyAsync(at<char>(ws, L.views), p->h_views, sizeof(DevView) * p->V, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
+    return PK_ERR_CUDA;
+  if (cudaMemcpyAsync(at<char>(ws, L.toff), p->h_toff, sizeof(uint32_t) * (p->V + 1), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return PK_ERR_CUDA;
+  int4 *tab = const_cast<pk_plan *>(p)->h_segtab;   // plan-owned: outlives the copy
+  if (seg_table(p, sort_blocks(), tab) > 0 &&
+      cudaMemcpyAsync(at<char>(ws, L.sblk), tab, sizeof(p->h_segtab), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return PK_ERR_CUDA;
   if ((e = bin_and_sort_impl(p, L, ws, records, sorted_vals, tile_ranges, maxd, st)) != PK_OK) return e;
   const DevCounters *ctr = at<DevCounters>(ws, L.counters);
