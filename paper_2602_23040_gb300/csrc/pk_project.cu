@@ -11,23 +11,29 @@ using namespace pk;
 
 namespace {
 
+constexpr int kProjThreads = 256;
+
+// The SH coefficients of a thread's Gaussian live in shared memory, column
+// tid of s_k[3 NB][kProjThreads] (each thread reads only its own column, so
+// no barrier is needed); in registers they would cap the occupancy.
 template <int L>
-__global__ __launch_bounds__(256) void k_project(const float *__restrict__ soa, int64_t G, int64_t N,
-                                                 const DevView *__restrict__ views,
-                                                 const int32_t *__restrict__ fview_off,
-                                                 const int32_t *__restrict__ fview_idx, float znear,
-                                                 float *__restrict__ rec) {
+__global__ __launch_bounds__(kProjThreads) void k_project(const float *__restrict__ soa, int64_t G, int64_t N,
+                                                          const DevView *__restrict__ views,
+                                                          const int32_t *__restrict__ fview_off,
+                                                          const int32_t *__restrict__ fview_idx, float znear,
+                                                          float *__restrict__ rec) {
   constexpr int NB = (L + 1) * (L + 1);
+  extern __shared__ float s_k[];   // [3 NB][kProjThreads]
   for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < G; gi += (int64_t)gridDim.x * blockDim.x) {
     const int64_t f = gi / N, g = gi - f * N;
     auto attr = [&](int c) { return __ldg(soa + (int64_t)c * G + gi); };
     Act a;
     activate(attr, a);
-    float k[NB][3];
+    auto k = [&](int j, int c) -> float & { return s_k[(3 * j + c) * kProjThreads + threadIdx.x]; };
 #pragma unroll
     for (int j = 0; j < NB; ++j)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) k[j][c] = attr(11 + 3 * j + c);
+      for (int c = 0; c < 3; ++c) k(j, c) = attr(11 + 3 * j + c);
     const int vb = __ldg(fview_off + f), ve = __ldg(fview_off + f + 1);
     for (int vi = vb; vi < ve; ++vi) {
       const int v = __ldg(fview_idx + vi);
@@ -45,7 +51,7 @@ __global__ __launch_bounds__(256) void k_project(const float *__restrict__ soa, 
         for (int c = 0; c < 3; ++c) {
           float acc = 0.5f;
 #pragma unroll
-          for (int j = 0; j < NB; ++j) acc = fmaf(k[j][c], Y[j], acc);
+          for (int j = 0; j < NB; ++j) acc = fmaf(k(j, c), Y[j], acc);
           rgb[c] = fmaxf(acc, 0.f);
         }
         ok = isfinite(rgb[0]) && isfinite(rgb[1]) && isfinite(rgb[2]) && isfinite(a.o);
@@ -73,14 +79,15 @@ extern "C" pk_status pk_project_and_sh(const pk_plan *p, const float *soa, float
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const DevView *views = at<DevView>(ws, p->ws.views);
   const int32_t *fo = at<int32_t>(ws, p->ws.fview_off), *fi = at<int32_t>(ws, p->ws.fview_idx);
-  int64_t blocks = (p->G + 255) / 256;
+  int64_t blocks = (p->G + kProjThreads - 1) / kProjThreads;
   if (blocks > 152 * 32) blocks = 152 * 32;
   const float zn = p->opts.znear;
+  const size_t smem = sizeof(float) * 3 * (p->L + 1) * (p->L + 1) * kProjThreads;
   switch (p->L) {
-    case 0: k_project<0><<<(int)blocks, 256, 0, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
-    case 1: k_project<1><<<(int)blocks, 256, 0, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
-    case 2: k_project<2><<<(int)blocks, 256, 0, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
-    default: k_project<3><<<(int)blocks, 256, 0, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
+    case 0: k_project<0><<<(int)blocks, kProjThreads, smem, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
+    case 1: k_project<1><<<(int)blocks, kProjThreads, smem, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
+    case 2: k_project<2><<<(int)blocks, kProjThreads, smem, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
+    default: k_project<3><<<(int)blocks, kProjThreads, smem, st>>>(soa, p->G, p->N, views, fo, fi, zn, records); break;
   }
   return check_launch();
 }

@@ -13,8 +13,10 @@ using namespace pk;
 
 namespace {
 
+constexpr int kScatterThreads = 128;
+
 template <int L>
-__global__ __launch_bounds__(128) void k_scatter(const float *__restrict__ soa, int64_t G, int64_t N,
+__global__ __launch_bounds__(kScatterThreads) void k_scatter(const float *__restrict__ soa, int64_t G, int64_t N,
                                                  const DevView *__restrict__ views,
                                                  const int32_t *__restrict__ fview_off,
                                                  const int32_t *__restrict__ fview_idx, float znear,
@@ -23,6 +25,7 @@ __global__ __launch_bounds__(128) void k_scatter(const float *__restrict__ soa, 
                                                  const uint32_t *__restrict__ texel, int64_t plane, int D,
                                                  float *__restrict__ out, int accumulate) {
   constexpr int NB = (L + 1) * (L + 1);
+  extern __shared__ float s_k[];   // [2 * 3 NB][kScatterThreads]: coefficients, then their gradients
   for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < G; gi += (int64_t)gridDim.x * blockDim.x) {
     const int64_t f = gi / N, g = gi - f * N;
     float *dst = out + (int64_t)f * D * plane + __ldg(texel + g);
@@ -34,13 +37,16 @@ __global__ __launch_bounds__(128) void k_scatter(const float *__restrict__ soa, 
     auto attr = [&](int c) { return __ldg(soa + (int64_t)c * G + gi); };
     Act a;
     activate(attr, a);
-    float k[NB][3], dk[NB][3];
+    // SH coefficients and their gradient sums in shared memory, column tid
+    // of s_k / s_dk (each thread touches only its own column)
+    auto k = [&](int j, int c) -> float & { return s_k[(3 * j + c) * kScatterThreads + threadIdx.x]; };
+    auto dk = [&](int j, int c) -> float & { return s_k[(3 * (NB + j) + c) * kScatterThreads + threadIdx.x]; };
 #pragma unroll
     for (int j = 0; j < NB; ++j)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        k[j][c] = attr(11 + 3 * j + c);
-        dk[j][c] = 0.f;
+        k(j, c) = attr(11 + 3 * j + c);
+        dk(j, c) = 0.f;
       }
     float dmu[3] = {0.f, 0.f, 0.f};
     float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3D entries xx xy xz yy yz zz
@@ -69,12 +75,12 @@ __global__ __launch_bounds__(128) void k_scatter(const float *__restrict__ soa, 
         for (int c = 0; c < 3; ++c) {
           float pre = 0.5f;
 #pragma unroll
-          for (int j = 0; j < NB; ++j) pre = fmaf(k[j][c], Y[j], pre);
+          for (int j = 0; j < NB; ++j) pre = fmaf(k(j, c), Y[j], pre);
           const float gc = pre >= 0.f ? grgb[c] : 0.f;
 #pragma unroll
           for (int j = 0; j < NB; ++j) {
-            dk[j][c] = fmaf(gc, Y[j], dk[j][c]);
-            const float w = gc * k[j][c];
+            dk(j, c) = fmaf(gc, Y[j], dk(j, c));
+            const float w = gc * k(j, c);
             ddir[0] = fmaf(w, dY[j][0], ddir[0]);
             ddir[1] = fmaf(w, dY[j][1], ddir[1]);
             ddir[2] = fmaf(w, dY[j][2], ddir[2]);
@@ -178,7 +184,7 @@ __global__ __launch_bounds__(128) void k_scatter(const float *__restrict__ soa, 
 #pragma unroll
     for (int j = 0; j < NB; ++j)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) put(11 + 3 * j + c, dk[j][c]);
+      for (int c = 0; c < 3; ++c) put(11 + 3 * j + c, dk(j, c));
   }
 }
 
@@ -194,13 +200,14 @@ extern "C" pk_status pk_atlas_scatter_grad(const pk_plan *p, const float *soa, c
   const DevView *views = at<DevView>(ws, p->ws.views);
   const int32_t *fo = at<int32_t>(ws, p->ws.fview_off), *fi = at<int32_t>(ws, p->ws.fview_idx);
   const int64_t plane = (int64_t)p->desc.atlas_w * p->desc.atlas_h;
-  int64_t blocks = (p->G + 127) / 128;
+  int64_t blocks = (p->G + kScatterThreads - 1) / kScatterThreads;
   if (blocks > 152 * 64) blocks = 152 * 64;
   const float zn = p->opts.znear;
   const int acc = accumulate ? 1 : 0;
-#define PK_SCATTER(LL)                                                                                      \
-  k_scatter<LL><<<(int)blocks, 128, 0, st>>>(soa, p->G, p->N, views, fo, fi, zn, grad2d, dynflag, texel, \
-                                             plane, p->D, grad_atlas, acc)
+  const size_t smem = sizeof(float) * 6 * (p->L + 1) * (p->L + 1) * kScatterThreads;
+#define PK_SCATTER(LL)                                                                                     \
+  k_scatter<LL><<<(int)blocks, kScatterThreads, smem, st>>>(soa, p->G, p->N, views, fo, fi, zn, grad2d,   \
+                                                            dynflag, texel, plane, p->D, grad_atlas, acc)
   switch (p->L) {
     case 0: PK_SCATTER(0); break;
     case 1: PK_SCATTER(1); break;
