@@ -144,6 +144,9 @@ __device__ __forceinline__ bool tile_hit(const Foot &f, int tx, int ty, int W, i
   return ellipse_hits_rect(f, x0, x1, y0, y1);
 }
 
+// Two 16-bit tile coordinates (or extents) in one word.
+__device__ __forceinline__ uint32_t pack_rect(int a, int b) { return (uint32_t)a | ((uint32_t)b << 16); }
+
 // A pair with at most this many candidate tiles keeps a bit mask of its
 // receiving candidates from the count pass, so the emission need not test
 // them again.
@@ -223,7 +226,7 @@ __device__ __forceinline__ T block_excl_scan(T v, T &total, T *s) {
 // them, so the emission need not test them again.
 __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict__ rec, int64_t pairs, int64_t N,
                                                          const DevView *__restrict__ views, int T, int mode,
-                                                         uint32_t *__restrict__ cnt, uint64_t *__restrict__ rmask) {
+                                                         uint32_t *__restrict__ cnt, uint4 *__restrict__ pinfo) {
   __shared__ WarpSplat s_ws[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
@@ -253,7 +256,10 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
       }
     }
     if (mode == PK_BIN_RECT) {
-      if (p < (uint64_t)pairs) cnt[p] = ncand;
+      if (p < (uint64_t)pairs) {
+        cnt[p] = ncand;
+        pinfo[p] = make_uint4(0u, 0u, pack_rect(ws.r0.x, ws.r0.y), pack_rect(ws.r0.z, ncand ? (int)ncand / ws.r0.z : 0));
+      }
       continue;
     }
     s_ws[warp][lane] = ws;
@@ -294,7 +300,8 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
     (void)lt;
     if (p < (uint64_t)pairs) {
       cnt[p] = mine;
-      rmask[p] = mask;
+      pinfo[p] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), pack_rect(ws.r0.x, ws.r0.y),
+                            pack_rect(ws.r0.z, ncand ? (int)ncand / ws.r0.z : 0));
     }
     __syncwarp();
   }
@@ -737,7 +744,7 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
 // ---------------------------------------------------------------------------
 
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
-                                                   const uint32_t *__restrict__ offs, const uint64_t *__restrict__ rmask,
+                                                   const uint32_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
                                                    const DevCounters *ctr, const DevView *__restrict__ views,
                                                    int64_t N, int T, int mode, bool local_keys,
                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
@@ -757,23 +764,28 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
     ws.r0 = make_int4(0, 0, 1, 1);
     ws.r1 = make_int4(1, 0, 1, 0);
     if (k < n) {
+      // the count pass left the candidate rectangle and, for up to 64
+      // candidates, the mask of the receiving ones: the record is read
+      // again only for a larger footprint
       p = pval[k];
-      const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec));
-      const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec) + 1);
-      const DevView &v = views[p / N];
-      int x0, y0, x1, y1;
-      if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
-        if (mode != PK_BIN_RECT) shrink_to_footprint(a.x, a.y, a.z, a.w, b.x, T, x0, y0, x1, y1);
-        const int wt = x1 - x0 + 1;
-        ncand = (uint32_t)(wt * (y1 - y0 + 1));
-        const Foot f = make_foot(a.x, a.y, a.z, a.w, b.x);
-        ws.g0 = make_float4(f.mx, f.my, f.a, f.b);
-        ws.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
+      const uint4 info = __ldg(pinfo + p);
+      const int x0 = (int)(info.z & 0xffffu), y0 = (int)(info.z >> 16);
+      const int wt = (int)(info.w & 0xffffu), ht = (int)(info.w >> 16);
+      ncand = (uint32_t)(wt * ht);
+      if (ncand) {
+        const DevView &v = views[p / N];
+        if (mode != PK_BIN_RECT && ncand > kMaskBits) {
+          const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec));
+          const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec) + 1);
+          const Foot f = make_foot(a.x, a.y, a.z, a.w, b.x);
+          ws.g0 = make_float4(f.mx, f.my, f.a, f.b);
+          ws.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
+        }
         ws.r0 = make_int4(x0, y0, wt, v.width);
         ws.r1 = make_int4(v.height, (int)((local_keys ? 0u : (uint32_t)v.tile_off) + (uint32_t)y0 * v.tiles_x +
                                           (uint32_t)x0),
                           v.tiles_x, (int)ncand);
-        if (mode != PK_BIN_RECT && ncand <= kMaskBits) msk = rmask[p];
+        msk = ((uint64_t)info.y << 32) | info.x;
       }
     }
     s_ws[warp][lane] = ws;
@@ -976,7 +988,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   uint32_t *zk[2] = {at<uint32_t>(ws, L.zkey0), at<uint32_t>(ws, L.zkey1)};
   uint32_t *pv[2] = {at<uint32_t>(ws, L.pval0), at<uint32_t>(ws, L.pval1)};
   uint32_t *offs = at<uint32_t>(ws, L.offs);
-  uint64_t *rmask = at<uint64_t>(ws, L.rmask);
+  uint4 *pinfo = at<uint4>(ws, L.rmask);
   uint64_t *bsum = at<uint64_t>(ws, L.blocksums);
   uint32_t *hist = at<uint32_t>(ws, L.hist);
   uint32_t *dk0 = at<uint32_t>(ws, L.dkey0), *dk1 = at<uint32_t>(ws, L.dkey1);
@@ -1000,7 +1012,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     return PK_OK;
   }
   const int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
-  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt, rmask);
+  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt, pinfo);
   // compaction of the pairs that touch a tile, keyed by depth bits
   k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, maxd, ctr, status);
@@ -1053,7 +1065,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   np = radix_plan(key_bits, widths);
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
-  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, rmask, ctr, views, p->N, p->T,
+  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->T,
                                                       p->opts.bin_mode, nseg > 0, kbuf[0], vbuf[0]);
   shift = 0;
   for (int pass = 0; pass < np; ++pass) {
@@ -1148,7 +1160,7 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   L.pval0 = take(sizeof(uint32_t) * pairs);
   L.pval1 = take(sizeof(uint32_t) * pairs);
   L.offs = take(sizeof(uint32_t) * pairs);
-  L.rmask = take(sizeof(uint64_t) * pairs);
+  L.rmask = take(sizeof(uint4) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
   L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);

@@ -60,7 +60,7 @@ struct DevCounters {
 // Byte offsets of every region inside the workspace.
 struct WsLayout {
   size_t status, counters, views, toff, fview_off, fview_idx, woff;
-  size_t pair_cnt, zkey0, zkey1, pval0, pval1, offs, rmask;
+  size_t pair_cnt, zkey0, zkey1, pval0, pval1, offs, rmask;   // rmask: per pair {mask (2 words), rectangle (2)}
   size_t blocksums, hist;
   size_t dkey0, dkey1, dval;
   size_t sblk, vseg;       // segmented tile sort: block table [kSortBlocks] int4, view entry starts [V + 1]

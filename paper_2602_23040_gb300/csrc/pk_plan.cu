@@ -242,7 +242,7 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   L.pval0 = take(sizeof(uint32_t) * pairs);
   L.pval1 = take(sizeof(uint32_t) * pairs);
   L.offs = take(sizeof(uint32_t) * pairs);
-  L.rmask = take(sizeof(uint64_t) * pairs);
+  L.rmask = take(sizeof(uint4) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
   L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
