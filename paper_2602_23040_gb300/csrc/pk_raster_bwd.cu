@@ -69,11 +69,14 @@ __device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int l
 
 // One pixel's share of the adjoint of a blended splat.  T (transmittance
 // after the splat) becomes T before it; S (colour composited behind,
-// background included) takes the splat's own term; the nine gradients are
-// added to acc.  Returns false if the pixel skips the splat.
+// background included) takes the splat's own term; the colour and opacity
+// gradients are added to acc[5..8].  The conic and mean gradients are
+// linear in dq = dL/dq, so the pixel only adds dq, dq dy and dq dy^2 to
+// q1, qy, qyy (dx is the same for both pixels of a thread) and the caller
+// forms acc[0..4] once per splat.  Returns false if the pixel skips the splat.
 __device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, const float4 &c4, float dx, float zx,
                                               float py, float g0, float g1, float g2, float &T, float &S0, float &S1,
-                                              float &S2, float (&acc)[9]) {
+                                              float &S2, float (&acc)[9], float &q1, float &qy, float &qyy) {
   Hit h;
   if (!splat_alpha(a, b, c4.z, dx, zx, py, h)) return false;
   const float om = __fsub_rn(1.f, h.alpha);
@@ -92,16 +95,25 @@ __device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, 
     // alpha = o 2^power, power = k q: dL/dq = -alpha dL/dalpha / 2
     acc[5] = fmaf(da, h.G, acc[5]);
     const float dq = -0.5f * h.alpha * da;
-    const float dx = h.dx, dy = h.dy;
-    acc[2] = fmaf(dq * dx, dx, acc[2]);
-    acc[3] = fmaf(dq * 2.f * dx, dy, acc[3]);
-    acc[4] = fmaf(dq * dy, dy, acc[4]);
-    // dq/dm = -2 conic d = -(2 A dx + B dy, B dx + 2 C dy) / k
-    const float s2 = dq * kInvExpScale;
-    acc[0] = fmaf(-s2, 2.f * a.z * dx + a.w * dy, acc[0]);
-    acc[1] = fmaf(-s2, a.w * dx + 2.f * b.x * dy, acc[1]);
+    const float t = dq * h.dy;
+    q1 += dq;
+    qy += t;
+    qyy = fmaf(t, h.dy, qyy);
   }
   return true;
+}
+
+// Conic and mean gradients of a splat from the pixel sums q1 = sum dq,
+// qy = sum dq dy, qyy = sum dq dy^2 (common dx): d/dconic = dq (dx^2,
+// 2 dx dy, dy^2), dq/dm = -2 conic d = -(2 A dx + B dy, B dx + 2 C dy) / k.
+__device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &b, float dx, float q1, float qy,
+                                                 float qyy, float (&acc)[9]) {
+  const float dq1 = dx * q1;
+  acc[2] = dx * dq1;
+  acc[3] = 2.f * dx * qy;
+  acc[4] = qyy;
+  acc[0] = -kInvExpScale * (2.f * a.z * dq1 + a.w * qy);
+  acc[1] = -kInvExpScale * (a.w * dq1 + 2.f * b.x * qy);
 }
 
 // kTma: the records of the next (earlier) batch are fetched into shared
@@ -248,16 +260,18 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
           const float4 a = s_a[j], b = s_b[j], c4 = s_c[j];
           const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
           float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          float q1 = 0.f, qy = 0.f, qyy = 0.f;
           bool act = false;
           if (pos < nc0) {
             ++evals;
-            act |= pixel_adjoint(a, b, c4, dx, zx, py0, g00, g01, g02, T0, S00, S01, S02, acc);
+            act |= pixel_adjoint(a, b, c4, dx, zx, py0, g00, g01, g02, T0, S00, S01, S02, acc, q1, qy, qyy);
           }
           if (pos < nc1) {
             ++evals;
-            act |= pixel_adjoint(a, b, c4, dx, zx, py1, g10, g11, g12, T1, S10, S11, S12, acc);
+            act |= pixel_adjoint(a, b, c4, dx, zx, py1, g10, g11, g12, T1, S10, S11, S12, acc, q1, qy, qyy);
           }
           if (__any_sync(0xffffffffu, act)) {
+            conic_mean_grads(a, b, dx, q1, qy, qyy, acc);
             const float sum = warp_reduce_scatter9(acc, lane);
             if (my_idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + my_idx, sum);
           }
