@@ -68,25 +68,26 @@ __device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int l
 }
 
 // One pixel's share of the adjoint of a blended splat.  T (transmittance
-// after the splat) becomes T before it; S (colour composited behind,
-// background included) takes the splat's own term; the colour and opacity
+// after the splat) becomes T before it; GS = dL/dC . S, S being the colour
+// composited behind (background included), takes the splat's own term
+// (only that dot product enters dL/dalpha); the colour and opacity
 // gradients are added to acc[5..8].  The conic and mean gradients are
 // linear in dq = dL/dq, so the pixel only adds dq, dq dy and dq dy^2 to
 // q1, qy, qyy (dx is the same for both pixels of a thread) and the caller
 // forms acc[0..4] once per splat.  Returns false if the pixel skips the splat.
 __device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, const float4 &c4, float dx, float zx,
-                                              float py, float g0, float g1, float g2, float &T, float &S0, float &S1,
-                                              float &S2, float (&acc)[9], float &q1, float &qy, float &qyy) {
+                                              float py, float g0, float g1, float g2, float &T, float &GS,
+                                              float (&acc)[9], float &q1, float &qy, float &qyy) {
   Hit h;
   if (!splat_alpha(a, b, c4.z, dx, zx, py, h)) return false;
   const float om = __fsub_rn(1.f, h.alpha);
   const float inv = rcp_approx(om);
   const float Ti = T * inv;
   const float wT = h.alpha * Ti;
-  const float da = g0 * (Ti * b.z - S0 * inv) + g1 * (Ti * b.w - S1 * inv) + g2 * (Ti * c4.x - S2 * inv);
-  S0 = fmaf(wT, b.z, S0);
-  S1 = fmaf(wT, b.w, S1);
-  S2 = fmaf(wT, c4.x, S2);
+  // dL/dalpha = sum_c g_c (T_i rgb_c - S_c / (1 - alpha)) = (T g.rgb - g.S) / (1 - alpha)
+  const float gr = fmaf(g2, c4.x, fmaf(g1, b.w, g0 * b.z));
+  const float da = (T * gr - GS) * inv;
+  GS = fmaf(wT, gr, GS);
   T = Ti;
   acc[6] = fmaf(wT, g0, acc[6]);
   acc[7] = fmaf(wT, g1, acc[7]);
@@ -197,9 +198,9 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       g11 = gi[plane];
       g12 = gi[2 * plane];
     }
-    // colour composited behind the current splat, background included
-    float S00 = T0 * bg0, S01 = T0 * bg1, S02 = T0 * bg2;
-    float S10 = T1 * bg0, S11 = T1 * bg1, S12 = T1 * bg2;
+    // dL/dC . (colour composited behind the current splat, background included)
+    float GS0 = T0 * fmaf(g02, bg2, fmaf(g01, bg1, g00 * bg0));
+    float GS1 = T1 * fmaf(g12, bg2, fmaf(g11, bg1, g10 * bg0));
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(nc0, nc1));
     if (lane == 0) s_wmax[warp] = wmax;
     __syncthreads();
@@ -264,11 +265,11 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
           bool act = false;
           if (pos < nc0) {
             ++evals;
-            act |= pixel_adjoint(a, b, c4, dx, zx, py0, g00, g01, g02, T0, S00, S01, S02, acc, q1, qy, qyy);
+            act |= pixel_adjoint(a, b, c4, dx, zx, py0, g00, g01, g02, T0, GS0, acc, q1, qy, qyy);
           }
           if (pos < nc1) {
             ++evals;
-            act |= pixel_adjoint(a, b, c4, dx, zx, py1, g10, g11, g12, T1, S10, S11, S12, acc, q1, qy, qyy);
+            act |= pixel_adjoint(a, b, c4, dx, zx, py1, g10, g11, g12, T1, GS1, acc, q1, qy, qyy);
           }
           if (__any_sync(0xffffffffu, act)) {
             conic_mean_grads(a, b, dx, q1, qy, qyy, acc);
