@@ -746,7 +746,7 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
                                                    const uint32_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
                                                    const DevCounters *ctr, const DevView *__restrict__ views,
-                                                   int64_t N, int T, int mode, bool local_keys,
+                                                   int64_t N, int T, int mode, int local_bits,
                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
   __shared__ WarpSplat s_ws[kWarps][32];
   if (ctr->dups == 0) return;
@@ -782,9 +782,10 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
           ws.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
         }
         ws.r0 = make_int4(x0, y0, wt, v.width);
-        ws.r1 = make_int4(v.height, (int)((local_keys ? 0u : (uint32_t)v.tile_off) + (uint32_t)y0 * v.tiles_x +
-                                          (uint32_t)x0),
-                          v.tiles_x, (int)ncand);
+        // key: the global tile id, or (segmented sort) the view above the
+        // local tile id, whose low local_bits bits alone are sorted
+        const uint32_t kbase = local_bits ? ((uint32_t)(p / N) << local_bits) : (uint32_t)v.tile_off;
+        ws.r1 = make_int4(v.height, (int)(kbase + (uint32_t)y0 * v.tiles_x + (uint32_t)x0), v.tiles_x, (int)ncand);
         msk = ((uint64_t)info.y << 32) | info.x;
       }
     }
@@ -834,13 +835,14 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
 
 // Tile ranges from the sorted tile ids; four entries per thread.
 // Per-tile [start, end) of the sorted entries.  Keys are global tile ids,
-// or (seg != nullptr) per-view local ids: then the entry's view is found in
-// the segment starts seg[0..V) and its tile_off added.
-__global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *seg,
-                                                     const uint32_t *__restrict__ toff, int V, const DevCounters *ctr,
+// or (local_bits > 0) the view above a per-view local tile id: then the
+// view's tile_off is added to the local id.
+__global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, int local_bits,
+                                                     const uint32_t *__restrict__ toff, const DevCounters *ctr,
                                                      uint32_t *__restrict__ ranges) {
   const uint32_t n = ctr->dups;
   const uint32_t nq = (n + 3) / 4;
+  const uint32_t lmask = (1u << local_bits) - 1u;
   for (uint32_t q = blockIdx.x * kThreads + threadIdx.x; q < nq; q += gridDim.x * kThreads) {
     const uint32_t i0 = 4 * q;
     uint32_t k[6];   // tile ids of entries i0 - 1 .. i0 + 4
@@ -853,21 +855,10 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
       for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < n ? __ldg(keys + i0 + j) : 0xffffffffu;
     }
     k[5] = i0 + 4 < n ? __ldg(keys + i0 + 4) : 0xffffffffu;
-    if (seg) {
-      // view of entry i0 - 1 (or i0), then step forward across segment starts
-      const uint32_t first = i0 ? i0 - 1 : 0;
-      int lo = 0, hi = V - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(seg + mid) <= first) lo = mid; else hi = mid - 1;
-      }
+    if (local_bits) {
 #pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        const int64_t i = (int64_t)i0 - 1 + j;
-        if (i < 0 || i >= (int64_t)n) continue;
-        while (lo + 1 < V && __ldg(seg + lo + 1) <= (uint32_t)i) ++lo;
-        k[j] += __ldg(toff + lo);
-      }
+      for (int j = 0; j < 6; ++j)
+        if (k[j] != 0xffffffffu) k[j] = __ldg(toff + (k[j] >> local_bits)) + (k[j] & lmask);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1066,7 +1057,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
   k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->T,
-                                                      p->opts.bin_mode, nseg > 0, kbuf[0], vbuf[0]);
+                                                      p->opts.bin_mode, nseg > 0 ? key_bits : 0, kbuf[0], vbuf[0]);
   shift = 0;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
@@ -1075,8 +1066,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
       return e;
     shift += widths[pass];
   }
-  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], nseg > 0 ? vseg : nullptr,
-                                                        at<uint32_t>(ws, L.toff), p->V, ctr, tile_ranges);
+  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], nseg > 0 ? key_bits : 0,
+                                                        at<uint32_t>(ws, L.toff), ctr, tile_ranges);
   return check_launch();
 }
 
