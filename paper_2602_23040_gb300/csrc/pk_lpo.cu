@@ -22,10 +22,6 @@ __device__ __forceinline__ float unordered(uint32_t k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-__device__ __forceinline__ bool live_at(const uint32_t *__restrict__ occ, int Wp, int x, int y) {
-  return (__ldg(occ + (int64_t)y * Wp + (x >> 5)) >> (x & 31)) & 1u;
-}
-
 __global__ void k_minmax_init(uint32_t *keys, int D) {
   const int i = threadIdx.x;
   if (i < 2 * D) keys[i] = (i & 1) ? 0u : 0xffffffffu;
@@ -38,6 +34,7 @@ __global__ __launch_bounds__(kLpoThreads) void k_minmax(const float *__restrict_
                                                         int64_t planes, uint32_t *keys) {
   const int Wq = (W + 3) >> 2, Wp = (W + 31) >> 5;
   const int64_t nq = (int64_t)Wq * H, plane = (int64_t)W * H;
+  const bool vec = (W & 3) == 0;   // 16-byte aligned rows of four texels
   for (int64_t fc = blockIdx.y; fc < planes; fc += gridDim.y) {
     const int c = (int)(fc % D);
     const float *src = atlas + fc * plane;
@@ -45,12 +42,21 @@ __global__ __launch_bounds__(kLpoThreads) void k_minmax(const float *__restrict_
     for (int64_t qi = (int64_t)blockIdx.x * kLpoThreads + threadIdx.x; qi < nq;
          qi += (int64_t)gridDim.x * kLpoThreads) {
       const int y = (int)(qi / Wq), x0 = (int)(qi - (int64_t)y * Wq) * 4;
+      // the four texels share one occupancy word (x0 is a multiple of 4)
+      const uint32_t word = __ldg(occ + (int64_t)y * Wp + (x0 >> 5)) >> (x0 & 31);
+      if (!(word & 15u)) continue;
+      float v4[4];
+      if (vec) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(src + (int64_t)y * W + x0));
+        v4[0] = q.x; v4[1] = q.y; v4[2] = q.z; v4[3] = q.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v4[i] = x0 + i < W ? __ldg(src + (int64_t)y * W + x0 + i) : 0.f;
+      }
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int x = x0 + i;
-        if (x >= W || !live_at(occ, Wp, x, y)) continue;
-        const float v = __ldg(src + (int64_t)y * W + x);
-        if (v != v) continue;
+        const float v = v4[i];
+        if (x0 + i >= W || !((word >> i) & 1u) || v != v) continue;
         const uint32_t k = ordered(v);
         lo = min(lo, k);
         hi = max(hi, k);
@@ -102,12 +108,23 @@ __device__ __forceinline__ void encode_plane(const float *__restrict__ atlas, co
        qi += (int64_t)gridDim.x * kLpoThreads) {
     const int y = (int)(qi / Wq), x0 = (int)(qi - (int64_t)y * Wq) * 4;
     const int64_t at0 = (int64_t)y * W + x0;
+    const uint32_t word = __ldg(occ + (int64_t)y * Wp + (x0 >> 5)) >> (x0 & 31);
+    float v4[4] = {0.f, 0.f, 0.f, 0.f};
+    if (word & 15u) {
+      if (vec) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(src + at0));
+        v4[0] = q.x; v4[1] = q.y; v4[2] = q.z; v4[3] = q.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v4[i] = x0 + i < W ? __ldg(src + at0 + i) : 0.f;
+      }
+    }
     uint32_t b0 = 0, b1 = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int x = x0 + i;
-      if (x >= W || !live_at(occ, Wp, x, y)) continue;
-      const uint32_t q = lpo_code(__ldg(src + at0 + i), lo, delta, L);
+      if (x >= W || !((word >> i) & 1u)) continue;
+      const uint32_t q = lpo_code(v4[i], lo, delta, L);
       if (c < 3) {
         b0 |= (q >> 8) << (8 * i);
         b1 |= (q & 255u) << (8 * i);
