@@ -14,7 +14,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -156,9 +155,8 @@ def measured_traffic(stage, dups):
 
 
 def launches_per_step(plan):
-    npass = (max(1, math.ceil(math.log2(max(2, plan.n_tiles)))) + 7) // 8
-    # gather 2, project 1, bin_and_sort 21 + 3 per tile-sort pass, fwd 1, loss 1, bwd 1, scatter 1
-    return 2 + 1 + (21 + 3 * npass) + 4
+    # gather 2, project 1, bin_and_sort (as the library counts it), fwd 1, loss 1, bwd 1, scatter 1
+    return 2 + 1 + int(plan.sizes.bin_kernels) + 4
 
 
 # ---------------------------------------------------------------------------

@@ -138,6 +138,7 @@ typedef struct pk_sizes {
   uint64_t max_dups;               /* capacity of sorted_vals */
   uint64_t workspace_bytes;
   int64_t mask_words;              /* sum_v H_v ceil(W_v/32): uint32 words of the motion masks */
+  int32_t bin_kernels;             /* kernels one pk_bin_and_sort call launches on this device */
 } pk_sizes;
 
 /* Device status block (in the workspace).  flags is a bit set of

@@ -52,7 +52,8 @@ class Sizes(C.Structure):
     _fields_ = [("n_live", C.c_int64), ("n_gauss", C.c_int64), ("channels", C.c_int32),
                 ("n_views", C.c_int32), ("n_pairs", C.c_int64), ("n_pixels", C.c_int64),
                 ("n_tiles", C.c_int64), ("max_dups", C.c_uint64), ("workspace_bytes", C.c_uint64),
-                ("mask_words", C.c_int64)]
+                ("mask_words", C.c_int64),
+                ("bin_kernels", C.c_int32)]
 
 
 class DeviceStatus(C.Structure):

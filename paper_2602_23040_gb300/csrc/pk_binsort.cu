@@ -968,6 +968,22 @@ int radix_plan(int bits, int *widths) {
   return npass;
 }
 
+// Bits of the largest per-view tile id (the digits of the segmented sort).
+int local_tile_bits(const pk_plan *p) {
+  int64_t most = 1;
+  for (int v = 0; v < p->V; ++v)
+    most = std::max<int64_t>(most, (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y);
+  int bits = 1;
+  while ((int64_t(1) << bits) < most) ++bits;
+  return bits;
+}
+
+int view_bits(const pk_plan *p) {
+  int vbits = 1;
+  while ((1 << vbits) < p->V) ++vbits;
+  return vbits;
+}
+
 // The whole binning + sort on one workspace layout (shared by the two
 // entry points below).
 pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const float *records,
@@ -1022,8 +1038,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int cur = np & 1;
   if (nseg > 0) {
     // stable pass on the view: pairs in (view, depth) order
-    int vbits = 1;
-    while ((1 << vbits) < p->V) ++vbits;
+    const int vbits = view_bits(p);
     k_view_keys<<<std::max(1, sms) * 8, kThreads, 0, st>>>(pv[cur], n_valid, (uint32_t)p->N, zk[cur]);
     for (int shift_v = 0; shift_v < vbits; shift_v += kMaxRadixBits) {
       const int bits = std::min(kMaxRadixBits, vbits - shift_v);
@@ -1044,11 +1059,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   SegSpec sp{nullptr, nullptr};
   int nblocks = nsort;
   if (nseg > 0) {
-    int64_t most = 1;
-    for (int v = 0; v < p->V; ++v)
-      most = std::max<int64_t>(most, (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y);
-    key_bits = 1;
-    while ((int64_t(1) << key_bits) < most) ++key_bits;
+    key_bits = local_tile_bits(p);
     k_view_segments<<<std::max(1, sms) * 8, kThreads, 0, st>>>(pval, offs, ctr, (uint32_t)p->N, p->V, vseg);
     sp = SegSpec{tab, vseg};
     nblocks = nseg;
@@ -1072,6 +1083,25 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
 }
 
 }  // namespace
+
+// Mirrors the launches of bin_and_sort_impl: count, scan (2), compaction,
+// the depth passes, [view keys + view passes], offsets (3), [view
+// segments], emission, the tile passes, ranges; 3 kernels per radix pass.
+int pk::bin_kernel_count(const pk_plan *p) {
+  if (!p || p->pairs == 0) return 0;
+  int4 tab[kSortBlocks];
+  const bool seg = seg_table(p, sort_blocks(), tab) > 0;
+  int widths[8];
+  int passes = radix_plan(32, widths);
+  int kernels = 4 + 3 + 1 + 1;
+  if (seg) {
+    const int vbits = view_bits(p);
+    kernels += 1 + 1;
+    passes += (vbits + kMaxRadixBits - 1) / kMaxRadixBits;
+  }
+  passes += radix_plan(seg ? local_tile_bits(p) : p->tile_bits, widths);
+  return kernels + 3 * passes;
+}
 
 extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
                                      uint32_t *tile_ranges, void *ws, pk_stream_t stream) {

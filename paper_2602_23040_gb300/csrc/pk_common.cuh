@@ -102,5 +102,7 @@ bool aligned16(const void *p);
 // segmented (per-view) tile sort (pk_binsort.cu); 0 = run it unsegmented.
 int sort_blocks();
 int seg_table(const pk_plan *p, int nsort, int4 *tab);
+// Kernels one pk_bin_and_sort call launches for this plan on this device.
+int bin_kernel_count(const pk_plan *p);
 
 }  // namespace pk

@@ -269,6 +269,7 @@ extern "C" pk_status pk_plan_sizes(const pk_plan *p, pk_sizes *s) {
   s->max_dups = p->max_dups;
   s->workspace_bytes = p->ws.total;
   s->mask_words = p->mask_words;
+  s->bin_kernels = bin_kernel_count(p);
   return PK_OK;
 }
 
