@@ -249,10 +249,13 @@ pk_status pk_project_and_sh(const pk_plan *plan, const float *soa, float *record
  * tile's pixel centres is <= 9 (1 + 2^-12) (the 3-sigma footprint of Sec.
  * 4.2 / Alg. 1 step 5), evaluated in FP32 as: inside -> yes, else the
  * least q over the four edges with the 1-D minimiser -(b d)/c (resp. /a)
- * clamped to the edge.  Every receiving (pair, tile) becomes one entry;
- * entries are ordered by (global tile id, bits(z), pair index), which is a
- * stable sort of the keys (tile << 32 | bits(z)) in emission order (view,
- * Gaussian, tile row-major).  Bit-exact by contract.
+ * clamped to the edge.  Every receiving (pair, tile) becomes one entry.
+ * A tile's entries are contiguous and ordered by (bits(z), pair index),
+ * i.e. as a stable sort of the keys (tile << 32 | bits(z)) in emission
+ * order (view, Gaussian, tile row-major) leaves them; each tile's list is
+ * bit-exact by contract.  The tiles' lists follow one another in an order
+ * of the library's choosing (not necessarily by tile id): read a tile's
+ * list through tile_ranges.
  * records:     [V*N][12] (reads m, conic, z, radius).
  * sorted_vals: out [max_dups] uint32 pair index of each entry.
  * tile_ranges: out [n_tiles][2] uint32 [start, end) into sorted_vals;

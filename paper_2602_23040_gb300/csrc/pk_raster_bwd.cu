@@ -24,13 +24,6 @@ __device__ __forceinline__ int reduce_scatter9_index(int lane) {
   return (lane & 1) ? -1 : s4;
 }
 
-// 1 / x on the MUFU unit (one instruction).
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // Reduce-scatter of v[0..8] over the 32 lanes.  Level xor-16 splits the
 // nine values 5 | 4, xor-8 splits each half 3 | 2, xor-4 2 | 1, xor-2 1 | 1
 // and xor-1 adds the last pair.  Returns the complete sum of value
@@ -286,8 +279,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     }
     __syncthreads();
   }
-#pragma unroll
   unsigned long long ev = evals;
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
   if (lane == 0 && ev) atomicAdd(evals_out, ev);
 }

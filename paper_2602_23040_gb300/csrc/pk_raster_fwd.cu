@@ -209,8 +209,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
     __syncthreads();   // everyone has read s_tile / s_view before the next fetch
   }
   // one atomic per warp for the evaluation counter
-#pragma unroll
   unsigned long long ev = evals;
+#pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
   if (lane == 0 && ev) atomicAdd(evals_out, ev);
 }

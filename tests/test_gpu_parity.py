@@ -155,8 +155,28 @@ def test_bin_and_sort_bit_exact(orc, seed, mode):
     ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, 16, r[:, 2], r[:, 3], r[:, 4],
                                           mode={"ellipse": orc.BIN_ELLIPSE, "rect": orc.BIN_RECT}[mode])
     assert st["dups"] == len(ref_vals) and st["flags"] == 0
-    assert np.array_equal(H.u32(vals[:len(ref_vals)]), ref_vals)
-    assert np.array_equal(H.u32(ranges).reshape(-1, 2), ref_ranges)
+    assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.u32(ranges).reshape(-1, 2), ref_vals, ref_ranges)
+
+
+def assert_same_tile_lists(vals, ranges, ref_vals, ref_ranges):
+    """Every tile's list equal to the oracle's, bit for bit (the contract);
+    the lists tile sorted_vals (disjoint, covering), in any order of tiles."""
+    assert ranges.shape == ref_ranges.shape
+    n = len(ref_vals)
+    lens = ranges[:, 1].astype(np.int64) - ranges[:, 0]
+    assert np.array_equal(lens, ref_ranges[:, 1].astype(np.int64) - ref_ranges[:, 0])
+    live = np.flatnonzero(lens > 0)
+    if n == 0:
+        assert len(live) == 0
+        return
+    starts = ranges[live, 0].astype(np.int64)
+    order = np.argsort(starts)
+    ends = starts[order] + lens[live][order]
+    assert starts[order][0] == 0 and ends[-1] == n and np.array_equal(starts[order][1:], ends[:-1])
+    for t in live:
+        a, b = ranges[t]
+        c, d = ref_ranges[t]
+        assert np.array_equal(vals[a:b], ref_vals[c:d]), t
 
 
 def test_bin_and_sort_capacity_overflow(orc):
