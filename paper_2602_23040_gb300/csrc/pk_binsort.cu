@@ -581,9 +581,7 @@ __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist
 template <int RB>
 struct Down {
   static constexpr int kTile = Radix<RB>::kTile;
-  // a tile, up to 3 keys of misalignment, and one pad word per 32 keys for
-  // the in-place permutation (slot r is stored at r + r / 32)
-  static constexpr int kSpan = kTile + kTile / 32 + 4;
+  static constexpr int kSpan = kTile + 4;                         // a tile plus up to 3 keys of misalignment
   static constexpr size_t kBuf = 2 * sizeof(uint32_t) * kSpan;    // keys + values of one tile
   static constexpr size_t kSmem = 2 * kBuf + sizeof(uint16_t) * kWarps * Radix<RB>::kR +
                                   2 * sizeof(uint32_t) * Radix<RB>::kR + sizeof(uint32_t) * (kWarps + 1) +
@@ -719,19 +717,17 @@ __global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
       const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);
       const bool in = li < valid;
       const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(C::kR - 1);
-      // padded slot: runs of neighbouring digits (a splat's row of tiles)
-      // land a bucket length apart, which would otherwise share banks
       const uint32_t r = s_start[d] + wc[d] + rank[j];
-      bk[r + (r >> 5)] = key[j];
-      bv[r + (r >> 5)] = val[j];
+      bk[r] = key[j];
+      bv[r] = val[j];
     }
     __syncthreads();
     for (uint32_t i = tid; i < valid; i += kThreads) {
-      const uint32_t k = bk[i + (i >> 5)];
+      const uint32_t k = bk[i];
       const uint32_t d = (k >> shift) & mask;
       const uint32_t o = s_gbase[d] + (i - s_start[d]);
       kout[o] = k;
-      vout[o] = bv[i + (i >> 5)];
+      vout[o] = bv[i];
     }
     __syncthreads();
 #pragma unroll
@@ -1075,10 +1071,10 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
                                                       p->opts.bin_mode, nseg > 0 ? key_bits : 0, kbuf[0], vbuf[0]);
   // Digits from the top down: each tile's entries still end up contiguous
   // and in emission order, and the first pass, whose input holds each
-  // splat's tiles side by side, ranks on tile-row bands that few splats of
-  // a warp's 32 entries differ in (the pass is bound by the shared-memory
-  // traffic of its distinct digits).  The tiles follow one another by
-  // (low digit, high digit) instead of by id.
+  // splat's tiles side by side, ranks on tile-row bands that the 32 entries
+  // of a warp rarely differ in (ranking slows with the distinct digits of
+  // a warp).  The tiles follow one another by (low digit, high digit)
+  // instead of by id.
   shift = key_bits;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
