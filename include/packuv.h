@@ -273,7 +273,7 @@ pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *s
  * inputs, outputs and bit-exact result as pk_bin_and_sort; the scratch is a
  * 64 MiB array inside the library (reserved on every GPU that loads it, for
  * the life of the process), so the plan must satisfy 40 * V * N + 12 *
- * max_dups + 152 * V + about 0.55 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
+ * max_dups + 152 * V + about 0.8 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
  * nothing is enqueued.  n_entries: out, one device uint32 -- the entries
  * written, or 0xFFFFFFFF if they exceeded max_dups (then nothing was
  * emitted).  The first call on a device looks up the array's address; make

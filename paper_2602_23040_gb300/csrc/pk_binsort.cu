@@ -476,8 +476,8 @@ __device__ __forceinline__ void radix_chunk(const SegSpec &sp, uint64_t n, int t
 template <int RB>
 struct Radix {
   static constexpr int kR = 1 << RB;                       // buckets
-  static constexpr int kItems = RB <= 8 ? 12 : 11;         // keys per thread and tile
-  static constexpr int kTile = kThreads * kItems;          // 3072 or 2816 (multiples of 4)
+  static constexpr int kItems = RB <= 8 ? 8 : 11;          // keys per thread and tile
+  static constexpr int kTile = kThreads * kItems;          // 2048 or 2816 (multiples of 4)
   static constexpr int kCopies = RB <= 8 ? kWarps : 2;     // private histograms in the upsweep
   static constexpr int kPerThread = kR / kThreads;         // buckets per thread in the digit scan
 };
@@ -589,7 +589,7 @@ struct Down {
 };
 
 template <int RB>
-__global__ __launch_bounds__(kThreads, 3) void k_radix_downsweep(
+__global__ __launch_bounds__(kThreads, 4) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, pk_device_status *status, SegSpec sp) {
@@ -936,8 +936,9 @@ int pk::sort_blocks() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // 3 resident per SM, within the histogram's capacity
-  return std::max(1, std::min(kSortBlocks, 3 * sms));
+  // 4 resident per SM (64 registers, 39 KB of shared memory each), leaving
+  // the histogram room for the segmented table's one extra block per view
+  return std::max(1, std::min(kSortBlocks - 128, 4 * sms));
 }
 
 int pk::seg_table(const pk_plan *p, int nsort, int4 *tab) {

@@ -26,7 +26,7 @@ constexpr float kInvExpScale = -1.38629436111989061f;   // 1 / kExpScale = -2 ln
 
 // Fixed grid sizes of the device-count-driven kernels (scan, radix sort).
 constexpr int kScanBlocks = 1024;
-constexpr int kSortBlocks = 512;      // most radix blocks of one pass (histogram capacity)
+constexpr int kSortBlocks = 768;      // most radix blocks of one pass (histogram capacity)
 constexpr int kMaxRadixBits = 8;      // widest radix digit
 
 // Per-view constants on the device, 144 bytes.
