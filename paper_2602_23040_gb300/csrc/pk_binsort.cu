@@ -473,20 +473,26 @@ __device__ __forceinline__ void radix_chunk(const SegSpec &sp, uint64_t n, int t
   hstride = (uint32_t)t.z;
 }
 
-template <int RB>
+// RB-bit digits, IT keys per thread and tile.  More keys per thread give
+// longer runs per bucket in the scatter; fewer give more resident blocks.
+// The pair passes (33 M keys at C3, random low digits) take 12 at 3 blocks
+// per SM, the entry passes (410 M keys) 8 at 4 blocks per SM.
+template <int RB, int IT>
 struct Radix {
   static constexpr int kR = 1 << RB;                       // buckets
-  static constexpr int kItems = RB <= 8 ? 8 : 11;          // keys per thread and tile
-  static constexpr int kTile = kThreads * kItems;          // 2048 or 2816 (multiples of 4)
+  static constexpr int kItems = IT;                        // keys per thread and tile
+  static constexpr int kTile = kThreads * kItems;          // a multiple of 4
   static constexpr int kCopies = RB <= 8 ? kWarps : 2;     // private histograms in the upsweep
   static constexpr int kPerThread = kR / kThreads;         // buckets per thread in the digit scan
+  static constexpr int kMinBlocks = IT >= 12 ? 3 : (IT >= 8 ? 4 : 5);   // resident per SM (downsweep)
 };
+constexpr int kPairItems = 12, kEntryItems = 8;
 
-template <int RB>
+template <int RB, int IT>
 __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__restrict__ keys,
                                                             const uint32_t *n_dev, uint64_t n_host, int shift,
                                                             uint32_t mask, uint32_t *__restrict__ hist, SegSpec sp) {
-  using C = Radix<RB>;
+  using C = Radix<RB, IT>;
   __shared__ uint32_t s_cnt[C::kCopies][C::kR];   // private digit counts
   for (int i = threadIdx.x; i < C::kCopies * C::kR; i += kThreads) (&s_cnt[0][0])[i] = 0;
   __syncthreads();
@@ -578,27 +584,27 @@ __global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist
 // Downsweep with the next tile's keys and values prefetched by TMA into the
 // other half of a double buffer while the current tile is ranked and
 // scattered; the ranking permutes the current tile in place.
-template <int RB>
+template <int RB, int IT>
 struct Down {
-  static constexpr int kTile = Radix<RB>::kTile;
+  static constexpr int kTile = Radix<RB, IT>::kTile;
   static constexpr int kSpan = kTile + 4;                         // a tile plus up to 3 keys of misalignment
   static constexpr size_t kBuf = 2 * sizeof(uint32_t) * kSpan;    // keys + values of one tile
-  static constexpr size_t kSmem = 2 * kBuf + sizeof(uint16_t) * kWarps * Radix<RB>::kR +
-                                  2 * sizeof(uint32_t) * Radix<RB>::kR + sizeof(uint32_t) * (kWarps + 1) +
+  static constexpr size_t kSmem = 2 * kBuf + sizeof(uint16_t) * kWarps * Radix<RB, IT>::kR +
+                                  2 * sizeof(uint32_t) * Radix<RB, IT>::kR + sizeof(uint32_t) * (kWarps + 1) +
                                   2 * sizeof(uint64_t) + 16;
 };
 
-template <int RB>
-__global__ __launch_bounds__(kThreads, 4) void k_radix_downsweep(
+template <int RB, int IT>
+__global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, pk_device_status *status, SegSpec sp) {
-  using C = Radix<RB>;
+  using C = Radix<RB, IT>;
   constexpr int kTile = C::kTile;
-  constexpr int kSpan = Down<RB>::kSpan;
+  constexpr int kSpan = Down<RB, IT>::kSpan;
   extern __shared__ __align__(16) unsigned char s_raw[];
-  uint32_t *buf[2] = {reinterpret_cast<uint32_t *>(s_raw), reinterpret_cast<uint32_t *>(s_raw + Down<RB>::kBuf)};
-  uint16_t *s_wcnt = reinterpret_cast<uint16_t *>(s_raw + 2 * Down<RB>::kBuf);       // [kWarps][kR]
+  uint32_t *buf[2] = {reinterpret_cast<uint32_t *>(s_raw), reinterpret_cast<uint32_t *>(s_raw + Down<RB, IT>::kBuf)};
+  uint16_t *s_wcnt = reinterpret_cast<uint16_t *>(s_raw + 2 * Down<RB, IT>::kBuf);       // [kWarps][kR]
   uint32_t *s_start = reinterpret_cast<uint32_t *>(s_wcnt + kWarps * C::kR);         // [kR]
   uint32_t *s_gbase = s_start + C::kR;                                              // [kR]
   uint32_t *s_scan = s_gbase + C::kR;                                               // [kWarps + 1]
@@ -900,30 +906,47 @@ __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__re
   }
 }
 
-template <int RB>
+template <int RB, int IT>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
                         pk_device_status *status, SegSpec sp, cudaStream_t st) {
-  using C = Radix<RB>;
-  if (cudaFuncSetAttribute(k_radix_downsweep<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)Down<RB>::kSmem) != cudaSuccess)
+  using C = Radix<RB, IT>;
+  if (cudaFuncSetAttribute(k_radix_downsweep<RB, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Down<RB, IT>::kSmem) != cudaSuccess)
     return PK_ERR_CUDA;
   const uint32_t mask = (1u << bits) - 1u;
-  k_radix_upsweep<RB><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist, sp);
+  k_radix_upsweep<RB, IT><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist, sp);
   k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
-  k_radix_downsweep<RB><<<nblocks, kThreads, Down<RB>::kSmem, st>>>(kin, vin, kout, vout, n_dev, n_host, shift,
-                                                                      mask, hist, status, sp);
+  k_radix_downsweep<RB, IT><<<nblocks, kThreads, Down<RB, IT>::kSmem, st>>>(kin, vin, kout, vout, n_dev, n_host,
+                                                                              shift, mask, hist, status, sp);
   return check_launch();
 }
 
-// One stable pass over key bits [shift, shift + bits), bits <= 8.  (Wider
-// digits, tried at 11 bits, cut the passes but each pass ran at two blocks
-// per SM with scattered short runs and came out slower overall.)
-pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+// One stable pass over key bits [shift, shift + bits), bits <= 8, over the
+// depth-sorted pairs (pair_blocks() blocks) or over the entries
+// (sort_blocks() blocks, or the segmented table's).  (Wider digits, tried
+// at 11 bits, cut the passes but each pass ran at two blocks per SM with
+// scattered short runs and came out slower overall.)
+pk_status radix_pass(bool entries, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
                      pk_device_status *status, cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}) {
-  return radix_pass_rb<kMaxRadixBits>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, sp,
-                                      st);
+  if (entries)
+    return radix_pass_rb<kMaxRadixBits, kEntryItems>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks,
+                                                      status, sp, st);
+  return radix_pass_rb<kMaxRadixBits, kPairItems>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks,
+                                                   status, sp, st);
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms);
+}
+
+// Blocks of the pair passes: resident ones, within the histogram.
+int pair_blocks() {
+  return std::max(1, std::min(kSortBlocks, Radix<kMaxRadixBits, kPairItems>::kMinBlocks * sm_count()));
 }
 
 }  // namespace
@@ -933,12 +956,9 @@ pk_status radix_pass(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, u
 // first histogram counter}.  Returns the number of blocks, or 0 when the
 // views do not fit the histogram (then the tile sort runs unsegmented).
 int pk::sort_blocks() {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // 4 resident per SM (64 registers, 39 KB of shared memory each), leaving
-  // the histogram room for the segmented table's one extra block per view
-  return std::max(1, std::min(kSortBlocks - 128, 4 * sms));
+  // the entry passes' resident blocks, leaving the histogram room for the
+  // segmented table's one extra block per view
+  return std::max(1, std::min(kSortBlocks - 128, Radix<kMaxRadixBits, kEntryItems>::kMinBlocks * sm_count()));
 }
 
 int pk::seg_table(const pk_plan *p, int nsort, int4 *tab) {
@@ -1006,7 +1026,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nsort = sort_blocks();
+  const int nsort = sort_blocks(), npair = pair_blocks();
   // segmented tile sort: pairs grouped by view, per-view local tile ids
   int4 tab_host[kSortBlocks];
   const int nseg = seg_table(p, nsort, tab_host);
@@ -1031,8 +1051,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int np = radix_plan(32, widths), shift = 0;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
-    if ((e = radix_pass(zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist, nsort, status, st)) !=
-        PK_OK)
+    if ((e = radix_pass(false, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist, npair, status,
+                        st)) != PK_OK)
       return e;
     shift += widths[pass];
   }
@@ -1043,8 +1063,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     k_view_keys<<<std::max(1, sms) * 8, kThreads, 0, st>>>(pv[cur], n_valid, (uint32_t)p->N, zk[cur]);
     for (int shift_v = 0; shift_v < vbits; shift_v += kMaxRadixBits) {
       const int bits = std::min(kMaxRadixBits, vbits - shift_v);
-      if ((e = radix_pass(zk[cur], pv[cur], zk[cur ^ 1], pv[cur ^ 1], n_valid, 0, shift_v, bits, hist, nsort, status,
-                          st)) != PK_OK)
+      if ((e = radix_pass(false, zk[cur], pv[cur], zk[cur ^ 1], pv[cur ^ 1], n_valid, 0, shift_v, bits, hist, npair,
+                          status, st)) != PK_OK)
         return e;
       cur ^= 1;
     }
@@ -1080,7 +1100,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
     shift -= widths[pass];
-    if ((e = radix_pass(kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
+    if ((e = radix_pass(true, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
                         status, st, sp)) != PK_OK)
       return e;
   }
