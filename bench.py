@@ -502,7 +502,9 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "gaussians": plan.G, "views": plan.V, "pixels": plan.P,
                    "sh_degree": scene.sh_degree, "texels": "fp16" if texel_bytes == 2 else "fp32",
-                   "tile": 16, "batch": batch, "staging": {"fwd": plan.stage_fwd, "bwd": plan.stage_bwd},
+                   "tile": 16, "batch": {"fwd": plan.batch, "bwd": plan.batch_bwd},
+                   "staging": {"fwd": plan.stage_fwd, "bwd": plan.stage_bwd},
+                   "pixels_per_thread": {"fwd": 2, "bwd": 4},
                    "tuned_by": "defaults (profiler run)" if args.profile else "pk_autotune", "graph": "whole step in one CUDA graph",
                    "l2": "inputs larger than L2 (atlas %.0f MB, records %.0f MB)" % (
                        scene.atlas.nbytes / 1e6, plan.pairs * 48 / 1e6),

@@ -119,10 +119,11 @@ typedef struct pk_options {
   float bg[3];                     /* background colour; default 0 */
   uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
   int32_t bin_mode;                /* pk_bin_mode; default PK_BIN_ELLIPSE */
-  int32_t batch;                   /* splats staged per compositing batch: 64, 128 or 256
-                                      (0 = 256); pk_autotune picks it */
+  int32_t batch;                   /* splats staged per batch by pk_rasterize_fwd: 64, 128 or
+                                      256 (0 = 256); pk_autotune picks it */
   int32_t stage_fwd;               /* pk_stage_mode of pk_rasterize_fwd; default PK_STAGE_LOADS */
   int32_t stage_bwd;               /* pk_stage_mode of pk_rasterize_bwd; default PK_STAGE_LOADS */
+  int32_t batch_bwd;               /* the same for pk_rasterize_bwd (0 = 256) */
 } pk_options;
 
 typedef struct pk_plan pk_plan;
@@ -182,13 +183,13 @@ pk_status pk_plan_options(const pk_plan *plan, pk_options *out);
 void pk_plan_destroy(pk_plan *plan);
 
 /* Autotuning (the batching pattern of the render step): times, on the
- * caller's current inputs and on `stream`, pk_rasterize_fwd followed by
+ * caller's current inputs and on `stream`, pk_rasterize_fwd and then
  * pk_rasterize_bwd for every staging batch (64, 128, 256 splats) and keeps
- * the fastest, then times each kernel with both staging modes and keeps the
- * faster one per kernel (two timed runs after one warm-up each; a choice
- * other than the default 256 / plain loads must be more than 2 % faster).  The
- * choices are stored in the plan's options; *chosen_batch receives the
- * batch (may be NULL).  The tile side is fixed at 16 and the sort's digit
+ * the fastest of each, then times each kernel with both staging modes and
+ * keeps the faster one per kernel (two timed runs after one warm-up each; a
+ * choice other than the default 256 / plain loads must be more than 2 %
+ * faster).  The choices are stored in the plan's options; *chosen_batch
+ * receives the forward's batch (may be NULL).  The tile side is fixed at 16 and the sort's digit
  * width at 8 bits (10- and 11-bit digits measured slower).  The arguments
  * are those of the two calls; afterwards image, T_final, n_contrib and
  * grad2d hold a forward and backward with the chosen options.

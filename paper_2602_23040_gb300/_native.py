@@ -45,7 +45,8 @@ class View(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("tile", C.c_int32), ("znear", C.c_float), ("bg", C.c_float * 3), ("max_dups", C.c_uint64),
-                ("bin_mode", C.c_int32), ("batch", C.c_int32), ("stage_fwd", C.c_int32), ("stage_bwd", C.c_int32)]
+                ("bin_mode", C.c_int32), ("batch", C.c_int32), ("stage_fwd", C.c_int32), ("stage_bwd", C.c_int32),
+                ("batch_bwd", C.c_int32)]
 
 
 class Sizes(C.Structure):

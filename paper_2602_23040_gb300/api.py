@@ -74,12 +74,14 @@ class Plan:
     def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
                  sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 16,
                  znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse",
-                 batch: int = 256, stage_fwd: str = "loads", stage_bwd: str = "loads"):
+                 batch: int = 256, stage_fwd: str = "loads", stage_bwd: str = "loads", batch_bwd: int = None):
         lib = N.load()
         self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
                           texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
                           bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode, batch=batch, stage_fwd=stage_fwd,
-                          stage_bwd=stage_bwd)
+                          stage_bwd=stage_bwd, batch_bwd=batch_bwd)
+        if batch_bwd is None:
+            batch_bwd = batch
         d = N.AtlasDesc()
         d.atlas_w, d.atlas_h = int(atlas_wh[0]), int(atlas_wh[1])
         d.num_levels = len(levels)
@@ -95,8 +97,10 @@ class Plan:
         o.batch = int(batch)
         o.stage_fwd = STAGE_MODES[stage_fwd]
         o.stage_bwd = STAGE_MODES[stage_bwd]
+        o.batch_bwd = int(batch_bwd)
         self.bin_mode = bin_mode
         self.batch = int(batch)
+        self.batch_bwd = int(batch_bwd)
         self.stage_fwd, self.stage_bwd = stage_fwd, stage_bwd
         self._views = _views_array(views)
         h = C.c_void_p()
@@ -315,8 +319,9 @@ def render_bwd(plan: Plan, soa, dynflag, texel, records, sorted_vals, tile_range
 
 def autotune(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_contrib, dL_dimage, grad2d, ws,
              stream=None) -> int:
-    """Time the compositing forward + backward for each staging batch on the
-    current inputs and keep the fastest in the plan; returns it."""
+    """Time the compositing forward and backward for each staging batch on
+    the current inputs and keep the fastest of each in the plan; returns the
+    forward's."""
     chosen = C.c_int32(0)
     rc = N.load().pk_autotune(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
@@ -330,7 +335,9 @@ def autotune(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_co
     N.check("pk_plan_options", N.load().pk_plan_options(plan.handle, C.byref(o)))
     names = {v: k for k, v in STAGE_MODES.items()}
     plan.batch, plan.stage_fwd, plan.stage_bwd = int(o.batch), names[o.stage_fwd], names[o.stage_bwd]
-    plan._args.update(batch=plan.batch, stage_fwd=plan.stage_fwd, stage_bwd=plan.stage_bwd)
+    plan.batch_bwd = int(o.batch_bwd)
+    plan._args.update(batch=plan.batch, stage_fwd=plan.stage_fwd, stage_bwd=plan.stage_bwd,
+                      batch_bwd=plan.batch_bwd)
     return plan.batch
 
 

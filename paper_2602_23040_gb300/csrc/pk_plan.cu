@@ -127,10 +127,13 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   o.batch = 256;
   o.stage_fwd = PK_STAGE_LOADS;
   o.stage_bwd = PK_STAGE_LOADS;
+  o.batch_bwd = 256;
   if (opts) o = *opts;
   if (o.bin_mode != PK_BIN_RECT && o.bin_mode != PK_BIN_ELLIPSE) return PK_ERR_ARG;
   if (o.batch == 0) o.batch = 256;
-  if (o.batch != 64 && o.batch != 128 && o.batch != 256) return PK_ERR_ARG;
+  if (o.batch_bwd == 0) o.batch_bwd = 256;
+  for (const int32_t b : {o.batch, o.batch_bwd})
+    if (b != 64 && b != 128 && b != 256) return PK_ERR_ARG;
   if ((o.stage_fwd != PK_STAGE_LOADS && o.stage_fwd != PK_STAGE_BULK) ||
       (o.stage_bwd != PK_STAGE_LOADS && o.stage_bwd != PK_STAGE_BULK))
     return PK_ERR_ARG;
@@ -374,23 +377,30 @@ extern "C" pk_status pk_autotune(pk_plan *p, const float *records, const uint32_
     return e == PK_OK ? bwd() : e;
   };
   pk_status e = PK_OK;
-  // the batch, with plain loads; another choice than the default (256,
-  // loads) must win by more than 2 %, so timing noise does not flip it
+  // each kernel's batch, with plain loads (the backward reads the
+  // forward's outputs, which no batch changes); another choice than the
+  // default (256, loads) must win by more than 2 %, so timing noise does not
+  // flip it
   const float kMargin = 0.98f;
   const int32_t cands[3] = {256, 128, 64};
-  int32_t best = 256;
-  float best_ms = 0.f;
   p->opts.stage_fwd = p->opts.stage_bwd = PK_STAGE_LOADS;
-  for (int i = 0; i < 3 && e == PK_OK; ++i) {
-    p->opts.batch = cands[i];
-    float ms = 0.f;
-    e = time_runs(both, st, e0, e1, 2, &ms);
-    if (e == PK_OK && (i == 0 || ms < kMargin * best_ms)) {
-      best_ms = ms;
-      best = cands[i];
+  p->opts.batch = p->opts.batch_bwd = 256;
+  e = fwd();
+  for (int k = 0; k < 2 && e == PK_OK; ++k) {
+    int32_t *batch = k == 0 ? &p->opts.batch : &p->opts.batch_bwd;
+    int32_t best = 256;
+    float best_ms = 0.f;
+    for (int i = 0; i < 3 && e == PK_OK; ++i) {
+      *batch = cands[i];
+      float ms = 0.f;
+      e = k == 0 ? time_runs(fwd, st, e0, e1, 2, &ms) : time_runs(bwd, st, e0, e1, 2, &ms);
+      if (e == PK_OK && (i == 0 || ms < kMargin * best_ms)) {
+        best_ms = ms;
+        best = cands[i];
+      }
     }
+    *batch = best;
   }
-  if (e == PK_OK) p->opts.batch = best;
   // the staging mode of each kernel
   for (int k = 0; k < 2 && e == PK_OK; ++k) {
     int32_t *mode = k == 0 ? &p->opts.stage_fwd : &p->opts.stage_bwd;

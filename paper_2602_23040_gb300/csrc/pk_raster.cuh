@@ -10,17 +10,44 @@
 namespace pk {
 
 constexpr int kTileSide = 16;
-constexpr int kRasterThreads = 128;   // two pixels per thread
 // Splats staged per batch: a template parameter of the compositing
 // kernels (64, 128 or 256; pk_options.batch, chosen by pk_autotune).
 constexpr int kBatchMax = 256;
 
-// Warp w covers the 8 x 8 pixel block (w % 2, w / 2) of the 16 x 16 tile;
-// lane l holds pixels (l % 8, l / 8) and (l % 8, l / 8 + 4) of that block.
-__device__ __forceinline__ void pixel_of(int tid, int &ox, int &oy) {
+// One CTA per 16 x 16 tile with kPx pixels per thread (2 or 4).  A warp
+// covers a kBW x 8 block (8 x 8 for 2 pixels, 16 x 8 for 4) and skips as a
+// whole every splat that misses its block; a lane holds one column of it,
+// kPx pixels kRowStep rows apart.  More pixels per lane spread the per-splat
+// work of a warp (shared-memory loads, the block test, the gradient
+// reduction) over more pixels, at the price of a coarser block test.
+template <int kPx>
+struct Geo {
+  static constexpr int kThreads = kTileSide * kTileSide / kPx;   // 128 or 64
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kBW = kPx == 2 ? 8 : 16;
+  static constexpr int kRowStep = 32 / kBW;                       // 4 or 2
+};
+
+// Pixels per thread: the forward keeps 2 (its per-splat work is small, and
+// 8 x 8 blocks skip more), the backward 4 (its per-splat reduction of nine
+// gradients is spread over twice the pixels); measured at the 52-view rig.
+constexpr int kFwdPx = 2, kBwdPx = 4;
+
+// Lane's column ox and first row oy in the tile; (bx, by) = its warp block's corner.
+template <int kPx>
+__device__ __forceinline__ void pixel_of(int tid, int &ox, int &oy, int &bx, int &by) {
   const int w = tid >> 5, l = tid & 31;
-  ox = (w & 1) * 8 + (l & 7);
-  oy = (w >> 1) * 8 + (l >> 3);
+  if (kPx == 2) {
+    bx = (w & 1) * 8;
+    by = (w >> 1) * 8;
+    ox = bx + (l & 7);
+    oy = by + (l >> 3);
+  } else {
+    bx = 0;
+    by = w * 8;
+    ox = l & 15;
+    oy = by + (l >> 4);
+  }
 }
 
 // View that owns global tile t (binary search over tile offsets).

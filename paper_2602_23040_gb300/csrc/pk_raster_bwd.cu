@@ -112,25 +112,26 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 
 // kTma: the records of the next (earlier) batch are fetched into shared
 // memory by bulk copies (one 48-byte copy per splat, completed on an
-// mbarrier) while the current batch is processed.
-template <int kBatch, bool kTma>
-__global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
+// mbarrier) while the current batch is processed.  kPx: pixels per thread.
+template <int kBatch, bool kTma, int kPx>
+__global__ __launch_bounds__(Geo<kPx>::kThreads) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
     const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out,
     pk_device_status *status) {
+  using G = Geo<kPx>;
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
   __shared__ uint32_t s_pid[kTma ? kBatch : 1];
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ uint32_t s_tile;
   __shared__ int s_view;
-  __shared__ uint32_t s_wmax[kRasterThreads / 32];
+  __shared__ uint32_t s_wmax[G::kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Staged st{s_a, s_b, s_c, s_box, s_q};
-  int ox, oy;
-  pixel_of(tid, ox, oy);
+  int ox, oy, bx, by;
+  pixel_of<kPx>(tid, ox, oy, bx, by);
   const int my_idx = reduce_scatter9_index(lane);
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
@@ -145,7 +146,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
   // bulk copies of the records of list entries [b, b + nb) into s_raw
   // (expect_tx is set by thread 0 before the block barrier that precedes this)
   auto fetch = [&](uint32_t b, int nb) {
-    for (int j = tid; j < nb; j += kRasterThreads) {
+    for (int j = tid; j < nb; j += G::kThreads) {
       const uint32_t pid = __ldg(vals + b + j);
       s_pid[j] = pid;
       tma_load_1d(&s_raw[3 * j], rec + (size_t)pid * kRec, 3 * sizeof(float4), &s_bar);
@@ -164,42 +165,40 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy, y1 = y0 + 4;
-    const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
-    const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
-    const float wx0 = (float)(tx * kTileSide + (ox & ~7)) + 0.5f, wx1 = wx0 + 7.f;
-    const float wy0 = (float)(ty * kTileSide + (oy & ~7)) + 0.5f, wy1 = wy0 + 7.f;
+    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy;
+    const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
+    const float wx0 = (float)(tx * kTileSide + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
+    const float wy0 = (float)(ty * kTileSide + by) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t);
     const size_t plane = (size_t)W * H;
-    float T0 = 1.f, T1 = 1.f, g00 = 0.f, g01 = 0.f, g02 = 0.f, g10 = 0.f, g11 = 0.f, g12 = 0.f;
-    uint32_t nc0 = 0, nc1 = 0;
-    if (in0) {
-      const size_t pix = (size_t)view.pix_off + (size_t)y0 * W + x;
-      const float *gi = dimg + 3 * (size_t)view.pix_off + (size_t)y0 * W + x;
-      T0 = Tfin[pix];
-      nc0 = ncontrib[pix];
-      g00 = gi[0];
-      g01 = gi[plane];
-      g02 = gi[2 * plane];
+    float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx];
+    uint32_t nc[kPx];
+    uint32_t ncmax = 0;
+#pragma unroll
+    for (int q = 0; q < kPx; ++q) {
+      const int y = y0 + q * G::kRowStep;
+      T[q] = 1.f;
+      g0[q] = g1[q] = g2[q] = 0.f;
+      nc[q] = 0;
+      if (x < W && y < H) {
+        const size_t pix = (size_t)view.pix_off + (size_t)y * W + x;
+        const float *gi = dimg + 3 * (size_t)view.pix_off + (size_t)y * W + x;
+        T[q] = Tfin[pix];
+        nc[q] = ncontrib[pix];
+        g0[q] = gi[0];
+        g1[q] = gi[plane];
+        g2[q] = gi[2 * plane];
+      }
+      // dL/dC . (colour composited behind the current splat, background included)
+      GS[q] = T[q] * fmaf(g2[q], bg2, fmaf(g1[q], bg1, g0[q] * bg0));
+      ncmax = max(ncmax, nc[q]);
     }
-    if (in1) {
-      const size_t pix = (size_t)view.pix_off + (size_t)y1 * W + x;
-      const float *gi = dimg + 3 * (size_t)view.pix_off + (size_t)y1 * W + x;
-      T1 = Tfin[pix];
-      nc1 = ncontrib[pix];
-      g10 = gi[0];
-      g11 = gi[plane];
-      g12 = gi[2 * plane];
-    }
-    // dL/dC . (colour composited behind the current splat, background included)
-    float GS0 = T0 * fmaf(g02, bg2, fmaf(g01, bg1, g00 * bg0));
-    float GS1 = T1 * fmaf(g12, bg2, fmaf(g11, bg1, g10 * bg0));
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, max(nc0, nc1));
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, ncmax);
     if (lane == 0) s_wmax[warp] = wmax;
     __syncthreads();
     uint32_t tmax = 0;
 #pragma unroll
-    for (int w = 0; w < kRasterThreads / 32; ++w) tmax = max(tmax, s_wmax[w]);
+    for (int w = 0; w < G::kWarps; ++w) tmax = max(tmax, s_wmax[w]);
     if (kTma && tmax > 0) {
       const uint32_t b0 = tmax > (uint32_t)kBatch ? tmax - kBatch : 0u;
       if (tid == 0) mbar_expect_tx(&s_bar, (tmax - b0) * 3u * (uint32_t)sizeof(float4));
@@ -217,7 +216,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
         phase ^= 1u;
         __syncthreads();   // every warp is done with the previous batch's staged values
 #pragma unroll
-        for (int j = tid; j < kBatch; j += kRasterThreads)
+        for (int j = tid; j < kBatch; j += G::kThreads)
           if (j < nb) stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
         fence_proxy_async();   // these reads of s_raw before the next bulk writes into it
         const uint32_t nbeg = beg > (uint32_t)kBatch ? beg - kBatch : 0u;
@@ -230,7 +229,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
       } else {
         __syncthreads();
 #pragma unroll
-        for (int j = tid; j < kBatch; j += kRasterThreads)
+        for (int j = tid; j < kBatch; j += G::kThreads)
           if (j < nb) stage_splat(rec, __ldg(vals + s + beg + j), st, j);
         __syncthreads();
       }
@@ -256,13 +255,13 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_bwd(
           float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           float q1 = 0.f, qy = 0.f, qyy = 0.f;
           bool act = false;
-          if (pos < nc0) {
-            ++evals;
-            act |= pixel_adjoint(a, b, c4, dx, zx, py0, g00, g01, g02, T0, GS0, acc, q1, qy, qyy);
-          }
-          if (pos < nc1) {
-            ++evals;
-            act |= pixel_adjoint(a, b, c4, dx, zx, py1, g10, g11, g12, T1, GS1, acc, q1, qy, qyy);
+#pragma unroll
+          for (int q = 0; q < kPx; ++q) {
+            if (pos < nc[q]) {
+              ++evals;
+              act |= pixel_adjoint(a, b, c4, dx, zx, py0 + (float)(q * G::kRowStep), g0[q], g1[q], g2[q], T[q],
+                                   GS[q], acc, q1, qy, qyy);
+            }
           }
           if (__any_sync(0xffffffffu, act)) {
             conic_mean_grads(a, b, dx, q1, qy, qyy, acc);
@@ -294,13 +293,14 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma>, kRasterThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma, kBwdPx>,
+                                                Geo<kBwdPx>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > p->n_tiles) grid = p->n_tiles;
   if (grid < 1) grid = 1;
-  k_raster_bwd<kBatch, kBwdTma><<<(int)grid, kRasterThreads, 0, st>>>(
+  k_raster_bwd<kBatch, kBwdTma, kBwdPx><<<(int)grid, Geo<kBwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
       &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd), status);
@@ -325,7 +325,7 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
   return launch_bwd<B, M>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr, \
                           status, st)
   const bool tma = p->opts.stage_bwd == PK_STAGE_BULK;
-  switch (p->opts.batch) {
+  switch (p->opts.batch_bwd) {
     case 64:
       if (tma) PK_BWD(64, true);
       PK_BWD(64, false);

@@ -17,13 +17,14 @@ namespace {
 // kTma: the records of the next batch are fetched into shared memory by
 // bulk copies (one 48-byte copy per splat, completed on an mbarrier) while
 // the current batch is composited; the derived per-splat values are then
-// computed from shared memory.
-template <int kBatch, bool kTma>
-__global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
+// computed from shared memory.  kPx: pixels per thread (Geo).
+template <int kBatch, bool kTma, int kPx>
+__global__ __launch_bounds__(Geo<kPx>::kThreads) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
     uint32_t *queue, unsigned long long *evals_out, pk_device_status *status) {
+  using G = Geo<kPx>;
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
   __shared__ uint32_t s_pid[kTma ? kBatch : 1];
@@ -32,8 +33,8 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
   __shared__ int s_view;
   const int tid = threadIdx.x, lane = tid & 31;
   const Staged st{s_a, s_b, s_c, s_box, s_q};
-  int ox, oy;
-  pixel_of(tid, ox, oy);
+  int ox, oy, bx, by;
+  pixel_of<kPx>(tid, ox, oy, bx, by);
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
   bool timed_out = false;
@@ -47,7 +48,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
   // bulk copies of the records of list entries [b, b + nb) into s_raw
   // (expect_tx is set by thread 0 before the block barrier that precedes this)
   auto fetch = [&](uint32_t b, int nb) {
-    for (int j = tid; j < nb; j += kRasterThreads) {
+    for (int j = tid; j < nb; j += G::kThreads) {
       const uint32_t pid = __ldg(vals + b + j);
       s_pid[j] = pid;
       tma_load_1d(&s_raw[3 * j], rec + (size_t)pid * kRec, 3 * sizeof(float4), &s_bar);
@@ -66,16 +67,22 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy, y1 = y0 + 4;
-    const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
-    const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
-    // pixel-centre bounds of this warp's 8 x 8 block
-    const float wx0 = (float)(tx * kTileSide + (ox & ~7)) + 0.5f, wx1 = wx0 + 7.f;
-    const float wy0 = (float)(ty * kTileSide + (oy & ~7)) + 0.5f, wy1 = wy0 + 7.f;
+    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy;
+    const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
+    // pixel-centre bounds of this warp's block
+    const float wx0 = (float)(tx * kTileSide + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
+    const float wy0 = (float)(ty * kTileSide + by) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t), e = __ldg(ranges + 2 * (size_t)t + 1);
-    float T0 = 1.f, T1 = 1.f, c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c12 = 0.f;
-    uint32_t last0 = 0, last1 = 0;
-    bool done0 = !in0, done1 = !in1;
+    float T[kPx], c0[kPx], c1[kPx], c2[kPx];
+    uint32_t last[kPx];
+    uint32_t live = 0;   // bit k: pixel k is inside the view and still compositing
+#pragma unroll
+    for (int k = 0; k < kPx; ++k) {
+      T[k] = 1.f;
+      c0[k] = c1[k] = c2[k] = 0.f;
+      last[k] = 0;
+      if (x < W && y0 + k * G::kRowStep < H) live |= 1u << k;
+    }
     bool pending = false;   // a fetch is in flight (uniform over the block)
     if (kTma && s < e) {
       if (tid == 0) mbar_expect_tx(&s_bar, (uint32_t)min((uint32_t)kBatch, e - s) * 3u * sizeof(float4));
@@ -93,7 +100,7 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
         phase ^= 1u;
         pending = false;
 #pragma unroll
-        for (int j = tid; j < kBatch; j += kRasterThreads)
+        for (int j = tid; j < kBatch; j += G::kThreads)
           if (j < nb) stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
         fence_proxy_async();   // these reads of s_raw before the next bulk writes into it
         const uint32_t nxt = base + kBatch;
@@ -110,13 +117,13 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
       } else {
         __syncthreads();
 #pragma unroll
-        for (int j = tid; j < kBatch; j += kRasterThreads)
+        for (int j = tid; j < kBatch; j += G::kThreads)
           if (j < nb) stage_splat(rec, __ldg(vals + base + j), st, j);
         __syncthreads();
       }
-      if (!__all_sync(0xffffffffu, done0 && done1)) {
-        // which staged splats can reach this warp's block: 8 tests per lane,
-        // one ballot per 32 splats, then only the hits are visited
+      if (__any_sync(0xffffffffu, live != 0)) {
+        // which staged splats can reach this warp's block: one ballot per
+        // 32 splats, then only the hits are visited
         uint32_t hits[kBatch / 32];
 #pragma unroll
         for (int k = 0; k < kBatch / 32; ++k) {
@@ -124,54 +131,40 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
           hits[k] = __ballot_sync(0xffffffffu, j < nb && block_may_hit(s_box[j], s_q[j], s_a[j].x, s_a[j].y,
                                                                        wx0, wx1, wy0, wy1));
         }
-        bool all_done = false;
+        bool any_live = true;
 #pragma unroll
         for (int k = 0; k < kBatch / 32; ++k) {
           uint32_t m = hits[k];
-          while (m && !all_done) {
+          while (m && any_live) {
             const int j = 32 * k + __ffs(m) - 1;
             m &= m - 1;
             const float4 a = s_a[j], b = s_b[j], c = s_c[j];
             const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
             const uint32_t pos1 = base - s + (uint32_t)j + 1u;
-            Hit h;
-            if (!done0) {
+#pragma unroll
+            for (int q = 0; q < kPx; ++q) {
+              if (!((live >> q) & 1u)) continue;
               ++evals;
-              if (splat_alpha(a, b, c.z, dx, zx, py0, h)) {
-                const float Tn = __fmul_rn(T0, __fsub_rn(1.f, h.alpha));
+              Hit h;
+              if (splat_alpha(a, b, c.z, dx, zx, py0 + (float)(q * G::kRowStep), h)) {
+                const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, h.alpha));
                 if (Tn < kTMin) {
-                  done0 = true;
+                  live &= ~(1u << q);
                 } else {
-                  const float w = __fmul_rn(h.alpha, T0);
-                  c00 = __fmaf_rn(w, b.z, c00);
-                  c01 = __fmaf_rn(w, b.w, c01);
-                  c02 = __fmaf_rn(w, c.x, c02);
-                  T0 = Tn;
-                  last0 = pos1;
+                  const float w = __fmul_rn(h.alpha, T[q]);
+                  c0[q] = __fmaf_rn(w, b.z, c0[q]);
+                  c1[q] = __fmaf_rn(w, b.w, c1[q]);
+                  c2[q] = __fmaf_rn(w, c.x, c2[q]);
+                  T[q] = Tn;
+                  last[q] = pos1;
                 }
               }
             }
-            if (!done1) {
-              ++evals;
-              if (splat_alpha(a, b, c.z, dx, zx, py1, h)) {
-                const float Tn = __fmul_rn(T1, __fsub_rn(1.f, h.alpha));
-                if (Tn < kTMin) {
-                  done1 = true;
-                } else {
-                  const float w = __fmul_rn(h.alpha, T1);
-                  c10 = __fmaf_rn(w, b.z, c10);
-                  c11 = __fmaf_rn(w, b.w, c11);
-                  c12 = __fmaf_rn(w, c.x, c12);
-                  T1 = Tn;
-                  last1 = pos1;
-                }
-              }
-            }
-            all_done = __all_sync(0xffffffffu, done0 && done1);
+            any_live = __any_sync(0xffffffffu, live != 0);
           }
         }
       }
-      if (__syncthreads_count(!(done0 && done1)) == 0) break;
+      if (__syncthreads_count(live != 0) == 0) break;
     }
     if (kTma) {
       // a tile that stopped early may still have its next batch in flight
@@ -188,23 +181,18 @@ __global__ __launch_bounds__(kRasterThreads) void k_raster_fwd(
       }
     }
     const size_t plane = (size_t)W * H;
-    if (in0) {
-      const size_t pix = (size_t)view.pix_off + (size_t)y0 * W + x;
-      float *img = image + 3 * (size_t)view.pix_off + (size_t)y0 * W + x;
-      img[0] = __fmaf_rn(T0, bg0, c00);
-      img[plane] = __fmaf_rn(T0, bg1, c01);
-      img[2 * plane] = __fmaf_rn(T0, bg2, c02);
-      Tout[pix] = T0;
-      ncontrib[pix] = last0;
-    }
-    if (in1) {
-      const size_t pix = (size_t)view.pix_off + (size_t)y1 * W + x;
-      float *img = image + 3 * (size_t)view.pix_off + (size_t)y1 * W + x;
-      img[0] = __fmaf_rn(T1, bg0, c10);
-      img[plane] = __fmaf_rn(T1, bg1, c11);
-      img[2 * plane] = __fmaf_rn(T1, bg2, c12);
-      Tout[pix] = T1;
-      ncontrib[pix] = last1;
+#pragma unroll
+    for (int q = 0; q < kPx; ++q) {
+      const int y = y0 + q * G::kRowStep;
+      if (x < W && y < H) {
+        const size_t pix = (size_t)view.pix_off + (size_t)y * W + x;
+        float *img = image + 3 * (size_t)view.pix_off + (size_t)y * W + x;
+        img[0] = __fmaf_rn(T[q], bg0, c0[q]);
+        img[plane] = __fmaf_rn(T[q], bg1, c1[q]);
+        img[2 * plane] = __fmaf_rn(T[q], bg2, c2[q]);
+        Tout[pix] = T[q];
+        ncontrib[pix] = last[q];
+      }
     }
     __syncthreads();   // everyone has read s_tile / s_view before the next fetch
   }
@@ -223,13 +211,14 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma>, kRasterThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma, kFwdPx>,
+                                                Geo<kFwdPx>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > p->n_tiles) grid = p->n_tiles;
   if (grid < 1) grid = 1;
-  k_raster_fwd<kBatch, kFwdTma><<<(int)grid, kRasterThreads, 0, st>>>(
+  k_raster_fwd<kBatch, kFwdTma, kFwdPx><<<(int)grid, Geo<kFwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
       &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status);
