@@ -877,22 +877,17 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
   }
 }
 
-// View of each compacted pair in the current order (keys of the pass that
-// groups the depth-sorted pairs by view).
-__global__ __launch_bounds__(kThreads) void k_view_keys(const uint32_t *__restrict__ pval, const uint32_t *n_dev,
-                                                        uint32_t N, uint32_t *__restrict__ vkey) {
-  const uint32_t n = *n_dev;
-  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) vkey[i] = pval[i] / N;
-}
-
-// Entry offset of every view's first entry, pairs being in (view, depth)
-// order: seg[v] = offs of the first pair of view >= v (the total where no
-// such pair is left); seg[V] = the total.
+// Where every view's items start, the pairs being grouped by view (pair
+// pid belongs to view pid / N).  kEntries: seg[v] = offs of the first pair
+// of a view >= v (the total number of entries where no such pair is left),
+// else seg[v] = the index of that pair (n where none is left); seg[V] =
+// the total.
+template <bool kEntries>
 __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__restrict__ pval,
                                                             const uint32_t *__restrict__ offs,
                                                             const DevCounters *ctr, uint32_t N, int V,
                                                             uint32_t *__restrict__ seg) {
-  const uint32_t n = ctr->n_valid, total = ctr->dups;
+  const uint32_t n = ctr->n_valid, total = kEntries ? ctr->dups : n;
   if (n == 0 || total == 0) {
     for (int v = blockIdx.x * kThreads + threadIdx.x; v <= V; v += gridDim.x * kThreads) seg[v] = 0;
     return;
@@ -900,7 +895,7 @@ __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__re
   for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
     const int v = (int)(pval[i] / N);
     const int prev = i ? (int)(pval[i - 1] / N) : -1;
-    for (int u = prev + 1; u <= v; ++u) seg[u] = offs[i];
+    for (int u = prev + 1; u <= v; ++u) seg[u] = kEntries ? offs[i] : i;
     if (i + 1 == n)
       for (int u = v + 1; u <= V; ++u) seg[u] = total;
   }
@@ -951,29 +946,49 @@ int pair_blocks() {
 
 }  // namespace
 
-// Blocks of the segmented tile sort: per view a share of `nsort` blocks
-// proportional to its tiles (at least one), each {view, part, parts,
-// first histogram counter}.  Returns the number of blocks, or 0 when the
-// views do not fit the histogram (then the tile sort runs unsegmented).
+// Blocks of the entry passes on this device.
 int pk::sort_blocks() {
   // the entry passes' resident blocks, leaving the histogram room for the
   // segmented table's one extra block per view
   return std::max(1, std::min(kSortBlocks - 128, Radix<kMaxRadixBits, kEntryItems>::kMinBlocks * sm_count()));
 }
 
-int pk::seg_table(const pk_plan *p, int nsort, int4 *tab) {
-  if (p->V < 2) return 0;
-  int64_t tiles = 0;
-  for (int v = 0; v < p->V; ++v) tiles += (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y;
+namespace {
+
+// Block table of a segmented sort: per view a share of `nblocks`
+// proportional to weight(v) (at least one), each {view, part, parts, first
+// histogram counter}.  Returns the number of blocks, or 0 when the views do
+// not fit the histogram.
+template <typename Weight>
+int share_blocks(int V, int nblocks, const Weight &weight, int4 *tab) {
+  int64_t total = 0;
+  for (int v = 0; v < V; ++v) total += weight(v);
   int nb = 0;
-  for (int v = 0; v < p->V; ++v) {
-    const int64_t t = (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y;
-    const int parts = std::max<int>(1, (int)((int64_t)nsort * t / std::max<int64_t>(1, tiles)));
+  for (int v = 0; v < V; ++v) {
+    const int parts = std::max<int>(1, (int)((int64_t)nblocks * weight(v) / std::max<int64_t>(1, total)));
     if (nb + parts > kSortBlocks) return 0;
     for (int j = 0; j < parts; ++j) tab[nb + j] = make_int4(v, j, parts, (1 << kMaxRadixBits) * nb);
     nb += parts;
   }
   return nb;
+}
+
+}  // namespace
+
+// The tile passes' table (shares by tiles) and the depth passes' (equal
+// shares: every view has N pairs at most); false when the plan sorts
+// unsegmented (one view, or too many views for the histogram).
+bool pk::seg_tables(const pk_plan *p, int4 *tab, int *ntile, int *npair) {
+  *ntile = *npair = 0;
+  if (p->V < 2) return false;
+  const int nt = share_blocks(p->V, sort_blocks(),
+                              [&](int v) { return (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y; },
+                              tab);
+  const int np = share_blocks(p->V, pair_blocks(), [](int) { return int64_t(1); }, tab + kSortBlocks);
+  if (nt == 0 || np == 0) return false;
+  *ntile = nt;
+  *npair = np;
+  return true;
 }
 
 namespace {
@@ -999,12 +1014,6 @@ int local_tile_bits(const pk_plan *p) {
   return bits;
 }
 
-int view_bits(const pk_plan *p) {
-  int vbits = 1;
-  while ((1 << vbits) < p->V) ++vbits;
-  return vbits;
-}
-
 // The whole binning + sort on one workspace layout (shared by the two
 // entry points below).
 pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const float *records,
@@ -1026,12 +1035,13 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nsort = sort_blocks(), npair = pair_blocks();
-  // segmented tile sort: pairs grouped by view, per-view local tile ids
-  int4 tab_host[kSortBlocks];
-  const int nseg = seg_table(p, nsort, tab_host);
+  // segmented sorts (V >= 2): the depth passes sort each view's pairs in
+  // place, the tile passes each view's entries on per-view local tile ids
+  int4 tab_host[2 * kSortBlocks];
+  int nseg = 0, npseg = 0;
+  const bool seg = seg_tables(p, tab_host, &nseg, &npseg);
   const int4 *tab = at<int4>(ws, L.sblk);
-  uint32_t *vseg = at<uint32_t>(ws, L.vseg);
+  uint32_t *vseg = at<uint32_t>(ws, L.vseg), *pseg = vseg + (p->V + 1);
 
   if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
     return PK_ERR_CUDA;
@@ -1045,31 +1055,26 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, maxd, ctr, status);
   k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, records, pairs, bsum, zk[0], pv[0]);
-  // depth sort of the pairs: stable passes over the 32 bits of z
+  // depth sort of the pairs: stable passes over the 32 bits of z; the
+  // compaction kept the (view, Gaussian) order, so sorting inside each
+  // view's segment leaves the pairs in (view, depth) order
+  SegSpec psp{nullptr, nullptr};
+  if (seg) {
+    k_view_segments<false><<<std::max(1, sms) * 8, kThreads, 0, st>>>(pv[0], nullptr, ctr, (uint32_t)p->N, p->V,
+                                                                      pseg);
+    psp = SegSpec{tab + kSortBlocks, pseg};
+  }
   pk_status e;
   int widths[8];
   int np = radix_plan(32, widths), shift = 0;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
-    if ((e = radix_pass(false, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist, npair, status,
-                        st)) != PK_OK)
+    if ((e = radix_pass(false, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist,
+                        seg ? npseg : pair_blocks(), status, st, psp)) != PK_OK)
       return e;
     shift += widths[pass];
   }
-  int cur = np & 1;
-  if (nseg > 0) {
-    // stable pass on the view: pairs in (view, depth) order
-    const int vbits = view_bits(p);
-    k_view_keys<<<std::max(1, sms) * 8, kThreads, 0, st>>>(pv[cur], n_valid, (uint32_t)p->N, zk[cur]);
-    for (int shift_v = 0; shift_v < vbits; shift_v += kMaxRadixBits) {
-      const int bits = std::min(kMaxRadixBits, vbits - shift_v);
-      if ((e = radix_pass(false, zk[cur], pv[cur], zk[cur ^ 1], pv[cur ^ 1], n_valid, 0, shift_v, bits, hist, npair,
-                          status, st)) != PK_OK)
-        return e;
-      cur ^= 1;
-    }
-  }
-  const uint32_t *pval = pv[cur];
+  const uint32_t *pval = pv[np & 1];
   // emission offsets in (view,) depth order, capacity check
   SrcSorted ss{cnt, pval};
   k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
@@ -1078,10 +1083,10 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   // emission and the stable tile sort; the last pass lands in sorted_vals
   int key_bits = p->tile_bits;
   SegSpec sp{nullptr, nullptr};
-  int nblocks = nsort;
-  if (nseg > 0) {
+  int nblocks = sort_blocks();
+  if (seg) {
     key_bits = local_tile_bits(p);
-    k_view_segments<<<std::max(1, sms) * 8, kThreads, 0, st>>>(pval, offs, ctr, (uint32_t)p->N, p->V, vseg);
+    k_view_segments<true><<<std::max(1, sms) * 8, kThreads, 0, st>>>(pval, offs, ctr, (uint32_t)p->N, p->V, vseg);
     sp = SegSpec{tab, vseg};
     nblocks = nseg;
   }
@@ -1089,7 +1094,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
   k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->T,
-                                                      p->opts.bin_mode, nseg > 0 ? key_bits : 0, kbuf[0], vbuf[0]);
+                                                      p->opts.bin_mode, seg ? key_bits : 0, kbuf[0], vbuf[0]);
   // Digits from the top down: each tile's entries still end up contiguous
   // and in emission order, and the first pass, whose input holds each
   // splat's tiles side by side, ranks on tile-row bands that the 32 entries
@@ -1104,7 +1109,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
                         status, st, sp)) != PK_OK)
       return e;
   }
-  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], nseg > 0 ? key_bits : 0,
+  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], seg ? key_bits : 0,
                                                         at<uint32_t>(ws, L.toff), ctr, tile_ranges);
   return check_launch();
 }
@@ -1116,16 +1121,13 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
 // segments], emission, the tile passes, ranges; 3 kernels per radix pass.
 int pk::bin_kernel_count(const pk_plan *p) {
   if (!p || p->pairs == 0) return 0;
-  int4 tab[kSortBlocks];
-  const bool seg = seg_table(p, sort_blocks(), tab) > 0;
+  int4 tab[2 * kSortBlocks];
+  int nt = 0, np = 0;
+  const bool seg = seg_tables(p, tab, &nt, &np);
   int widths[8];
   int passes = radix_plan(32, widths);
   int kernels = 4 + 3 + 1 + 1;
-  if (seg) {
-    const int vbits = view_bits(p);
-    kernels += 1 + 1;
-    passes += (vbits + kMaxRadixBits - 1) / kMaxRadixBits;
-  }
+  if (seg) kernels += 2;   // the pairs' and the entries' view segments
   passes += radix_plan(seg ? local_tile_bits(p) : p->tile_bits, widths);
   return kernels + 3 * passes;
 }
@@ -1200,8 +1202,8 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   L.counters = take(sizeof(DevCounters));
   L.views = take(sizeof(DevView) * p->V);
   L.toff = take(sizeof(uint32_t) * (p->V + 1));
-  L.sblk = take(sizeof(int4) * kSortBlocks);
-  L.vseg = take(sizeof(uint32_t) * (p->V + 1));
+  L.sblk = take(sizeof(int4) * 2 * kSortBlocks);
+  L.vseg = take(sizeof(uint32_t) * 2 * (p->V + 1));
   L.pair_cnt = take(sizeof(uint32_t) * pairs);
   L.zkey0 = take(sizeof(uint32_t) * pairs);
   L.zkey1 = take(sizeof(uint32_t) * pairs);
@@ -1230,7 +1232,8 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
       cudaSuccess)
     return PK_ERR_CUDA;
   int4 *tab = const_cast<pk_plan *>(p)->h_segtab;   // plan-owned: outlives the copy
-  if (seg_table(p, sort_blocks(), tab) > 0 &&
+  int nt = 0, np = 0;
+  if (seg_tables(p, tab, &nt, &np) &&
       cudaMemcpyAsync(at<char>(ws, L.sblk), tab, sizeof(p->h_segtab), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return PK_ERR_CUDA;
   if ((e = bin_and_sort_impl(p, L, ws, records, sorted_vals, tile_ranges, maxd, st)) != PK_OK) return e;

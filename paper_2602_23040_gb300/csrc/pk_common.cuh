@@ -63,7 +63,8 @@ struct WsLayout {
   size_t pair_cnt, zkey0, zkey1, pval0, pval1, offs, rmask;   // rmask: per pair {mask (2 words), rectangle (2)}
   size_t blocksums, hist;
   size_t dkey0, dkey1, dval;
-  size_t sblk, vseg;       // segmented tile sort: block table [kSortBlocks] int4, view entry starts [V + 1]
+  size_t sblk, vseg;       // segmented sorts: block tables [2][kSortBlocks] int4 (tile passes, depth
+                           // passes), view starts [2][V + 1] (entries, pairs)
   size_t mask_tmp;         // one motion mask's worth of words (dilation scratch)
   size_t mask_coarse;      // per view, one bit per 32 x 32-pixel block: any moving pixel
   size_t total;
@@ -85,7 +86,7 @@ struct pk_plan {
   uint32_t *h_toff;        // [V+1] tile offsets (global tile id -> view)
   int32_t *h_fview_off;    // [F+1]
   int32_t *h_fview_idx;    // [V]
-  int4 h_segtab[pk::kSortBlocks];   // block table of the segmented tile sort (copied to the device)
+  int4 h_segtab[2 * pk::kSortBlocks];   // block tables of the segmented sorts (copied to the device)
 };
 
 namespace pk {
@@ -98,10 +99,12 @@ __host__ __device__ inline T *at(void *base, size_t off) {
 // Host-side launch helpers (implemented in pk_plan.cu).
 pk_status check_launch();
 bool aligned16(const void *p);
-// Radix blocks per pass on the current device, and the block table of the
-// segmented (per-view) tile sort (pk_binsort.cu); 0 = run it unsegmented.
+// Radix blocks of the entry passes on the current device, and the block
+// tables of the segmented (per-view) sorts: tab[0, kSortBlocks) for the
+// tile passes, tab[kSortBlocks, 2 kSortBlocks) for the depth passes
+// (pk_binsort.cu); false = the plan sorts unsegmented.
 int sort_blocks();
-int seg_table(const pk_plan *p, int nsort, int4 *tab);
+bool seg_tables(const pk_plan *p, int4 *tab, int *ntile, int *npair);
 // Kernels one pk_bin_and_sort call launches for this plan on this device.
 int bin_kernel_count(const pk_plan *p);
 

@@ -251,8 +251,8 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);
   L.dval = take(sizeof(uint32_t) * maxd);
-  L.sblk = take(sizeof(int4) * kSortBlocks);
-  L.vseg = take(sizeof(uint32_t) * (V + 1));
+  L.sblk = take(sizeof(int4) * 2 * kSortBlocks);
+  L.vseg = take(sizeof(uint32_t) * 2 * (V + 1));
   L.mask_tmp = take(sizeof(uint32_t) * (size_t)p->mask_words);
   L.mask_coarse = take(sizeof(uint32_t) * (size_t)p->coarse_words);
   L.total = off;
@@ -308,9 +308,10 @@ extern "C" pk_status pk_workspace_init(const pk_plan *p, void *ws, pk_stream_t s
   if (cudaMemcpyAsync(at<char>(ws, L.fview_idx), p->h_fview_idx, sizeof(int32_t) * p->V, cudaMemcpyHostToDevice,
                       st) != cudaSuccess)
     return PK_ERR_CUDA;
-  // block table of the segmented tile sort (for this device's SM count)
+  // block tables of the segmented sorts (for this device's SM count)
   int4 *tab = const_cast<pk_plan *>(p)->h_segtab;
-  if (seg_table(p, sort_blocks(), tab) > 0 &&
+  int nt = 0, np = 0;
+  if (seg_tables(p, tab, &nt, &np) &&
       cudaMemcpyAsync(at<char>(ws, L.sblk), tab, sizeof(p->h_segtab), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return PK_ERR_CUDA;
   // pageable sources: make sure the copies are done before the plan may go away

@@ -58,46 +58,58 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float *Y) {
   }
 }
 
-// Gradient of each polynomial above with respect to (x, y, z).
+// sum_j K_j grad Y_j(x, y, z) for the polynomials above (their gradient
+// with respect to (x, y, z), contracted with the weights K without forming
+// the 3 x (L+1)^2 gradient table).
 template <int L>
-__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float (*dY)[3]) {
-  dY[0][0] = dY[0][1] = dY[0][2] = 0.f;
+__device__ __forceinline__ void sh_grad_dot(float x, float y, float z, const float *K, float *g) {
+  float gx = 0.f, gy = 0.f, gz = 0.f;
   if (L >= 1) {
-    dY[1][0] = 0.f;   dY[1][1] = -kC1;  dY[1][2] = 0.f;
-    dY[2][0] = 0.f;   dY[2][1] = 0.f;   dY[2][2] = kC1;
-    dY[3][0] = -kC1;  dY[3][1] = 0.f;   dY[3][2] = 0.f;
+    gx = -kC1 * K[3];
+    gy = -kC1 * K[1];
+    gz = kC1 * K[2];
   }
   if (L >= 2) {
-    const float xx = x * x, yy = y * y, zz = z * z;
-    dY[4][0] = kC2a * y;          dY[4][1] = kC2a * x;          dY[4][2] = 0.f;
-    dY[5][0] = 0.f;               dY[5][1] = -kC2a * z;         dY[5][2] = -kC2a * y;
-    dY[6][0] = -2.f * kC2c * x;   dY[6][1] = -2.f * kC2c * y;   dY[6][2] = 4.f * kC2c * z;
-    dY[7][0] = -kC2a * z;         dY[7][1] = 0.f;               dY[7][2] = -kC2a * x;
-    dY[8][0] = 2.f * kC2e * x;    dY[8][1] = -2.f * kC2e * y;   dY[8][2] = 0.f;
+    const float a4 = kC2a * K[4], a5 = kC2a * K[5], a7 = kC2a * K[7];
+    const float c6 = 2.f * kC2c * K[6], e8 = 2.f * kC2e * K[8];
+    gx += a4 * y - a7 * z - c6 * x + e8 * x;
+    gy += a4 * x - a5 * z - c6 * y - e8 * y;
+    gz += -a5 * y + 2.f * c6 * z - a7 * x;
     if (L >= 3) {
-      dY[9][0] = -6.f * kC3a * x * y;
-      dY[9][1] = -3.f * kC3a * (xx - yy);
-      dY[9][2] = 0.f;
-      dY[10][0] = kC3b * y * z;
-      dY[10][1] = kC3b * x * z;
-      dY[10][2] = kC3b * x * y;
-      dY[11][0] = 2.f * kC3c * x * y;
-      dY[11][1] = -kC3c * (4.f * zz - xx - 3.f * yy);
-      dY[11][2] = -8.f * kC3c * y * z;
-      dY[12][0] = -6.f * kC3d * x * z;
-      dY[12][1] = -6.f * kC3d * y * z;
-      dY[12][2] = kC3d * (6.f * zz - 3.f * xx - 3.f * yy);
-      dY[13][0] = -kC3c * (4.f * zz - 3.f * xx - yy);
-      dY[13][1] = 2.f * kC3c * x * y;
-      dY[13][2] = -8.f * kC3c * x * z;
-      dY[14][0] = 2.f * kC3f * x * z;
-      dY[14][1] = -2.f * kC3f * y * z;
-      dY[14][2] = kC3f * (xx - yy);
-      dY[15][0] = -3.f * kC3a * (xx - yy);
-      dY[15][1] = 6.f * kC3a * x * y;
-      dY[15][2] = 0.f;
+      const float xx = x * x, yy = y * y, zz = z * z;
+      const float k9 = kC3a * K[9], k10 = kC3b * K[10], k11 = kC3c * K[11], k12 = kC3d * K[12];
+      const float k13 = kC3c * K[13], k14 = kC3f * K[14], k15 = kC3a * K[15];
+      // Y9 = -a y (3x^2 - y^2): (-6a x y, -3a (x^2 - y^2), 0)
+      gx += -6.f * k9 * x * y;
+      gy += -3.f * k9 * (xx - yy);
+      // Y10 = b x y z
+      gx += k10 * y * z;
+      gy += k10 * x * z;
+      gz += k10 * x * y;
+      // Y11 = -c y (4z^2 - x^2 - y^2): (2c x y, -c (4z^2 - x^2 - 3y^2), -8c y z)
+      gx += 2.f * k11 * x * y;
+      gy += -k11 * (4.f * zz - xx - 3.f * yy);
+      gz += -8.f * k11 * y * z;
+      // Y12 = d z (2z^2 - 3x^2 - 3y^2): (-6d x z, -6d y z, d (6z^2 - 3x^2 - 3y^2))
+      gx += -6.f * k12 * x * z;
+      gy += -6.f * k12 * y * z;
+      gz += k12 * (6.f * zz - 3.f * xx - 3.f * yy);
+      // Y13 = -c x (4z^2 - x^2 - y^2): (-c (4z^2 - 3x^2 - y^2), 2c x y, -8c x z)
+      gx += -k13 * (4.f * zz - 3.f * xx - yy);
+      gy += 2.f * k13 * x * y;
+      gz += -8.f * k13 * x * z;
+      // Y14 = f z (x^2 - y^2): (2f x z, -2f y z, f (x^2 - y^2))
+      gx += 2.f * k14 * x * z;
+      gy += -2.f * k14 * y * z;
+      gz += k14 * (xx - yy);
+      // Y15 = -a x (x^2 - 3y^2): (-3a (x^2 - y^2), 6a x y, 0)
+      gx += -3.f * k15 * (xx - yy);
+      gy += 6.f * k15 * x * y;
     }
   }
+  g[0] = gx;
+  g[1] = gy;
+  g[2] = gz;
 }
 
 // View-independent activation of one Gaussian.

@@ -14,9 +14,11 @@ using namespace pk;
 namespace {
 
 constexpr int kScatterThreads = 128;
+// 4 resident blocks per SM (at most 128 registers, a few spilled): latency
+// of the per-view gradient loads, not arithmetic, bounds this kernel.
 
 template <int L>
-__global__ __launch_bounds__(kScatterThreads) void k_scatter(const float *__restrict__ soa, int64_t G, int64_t N,
+__global__ __launch_bounds__(kScatterThreads, 4) void k_scatter(const float *__restrict__ soa, int64_t G, int64_t N,
                                                  const DevView *__restrict__ views,
                                                  const int32_t *__restrict__ fview_off,
                                                  const int32_t *__restrict__ fview_idx, float znear,
@@ -66,26 +68,32 @@ __global__ __launch_bounds__(kScatterThreads) void k_scatter(const float *__rest
       {
         float d[3], len;
         view_dir(a, view, d, len);
-        float Y[NB], dY[NB][3];
+        float Y[NB];
         sh_basis<L>(d[0], d[1], d[2], Y);
-        sh_basis_grad<L>(d[0], d[1], d[2], dY);
         const float grgb[3] = {g1.z, g1.w, g2.x};
-        float ddir[3] = {0.f, 0.f, 0.f};
+        float gcs[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           float pre = 0.5f;
 #pragma unroll
           for (int j = 0; j < NB; ++j) pre = fmaf(k(j, c), Y[j], pre);
-          const float gc = pre >= 0.f ? grgb[c] : 0.f;
-#pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            dk(j, c) = fmaf(gc, Y[j], dk(j, c));
-            const float w = gc * k(j, c);
-            ddir[0] = fmaf(w, dY[j][0], ddir[0]);
-            ddir[1] = fmaf(w, dY[j][1], ddir[1]);
-            ddir[2] = fmaf(w, dY[j][2], ddir[2]);
-          }
+          gcs[c] = pre >= 0.f ? grgb[c] : 0.f;
         }
+        // d rgb_c / d dir = sum_j k_jc grad Y_j: contract the channels first
+        float K[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+          float kj = 0.f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float kc = k(j, c);
+            dk(j, c) = fmaf(gcs[c], Y[j], dk(j, c));
+            kj = fmaf(gcs[c], kc, kj);
+          }
+          K[j] = kj;
+        }
+        float ddir[3];
+        sh_grad_dot<L>(d[0], d[1], d[2], K, ddir);
         const float dd = ddir[0] * d[0] + ddir[1] * d[1] + ddir[2] * d[2];
         const float il = 1.f / len;
 #pragma unroll
