@@ -113,8 +113,10 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // kTma: the records of the next (earlier) batch are fetched into shared
 // memory by bulk copies (one 48-byte copy per splat, completed on an
 // mbarrier) while the current batch is processed.  kPx: pixels per thread.
+// At 4 pixels per thread the kernel is held to 64 registers (no spills):
+// 16 resident CTAs per SM instead of 10 hide more of its latency.
 template <int kBatch, bool kTma, int kPx>
-__global__ __launch_bounds__(Geo<kPx>::kThreads) void k_raster_bwd(
+__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,

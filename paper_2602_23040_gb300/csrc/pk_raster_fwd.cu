@@ -18,8 +18,10 @@ namespace {
 // bulk copies (one 48-byte copy per splat, completed on an mbarrier) while
 // the current batch is composited; the derived per-splat values are then
 // computed from shared memory.  kPx: pixels per thread (Geo).
+// At 2 pixels per thread the kernel is held to 48 registers (a few spilled)
+// for 10 resident CTAs per SM instead of 9.
 template <int kBatch, bool kTma, int kPx>
-__global__ __launch_bounds__(Geo<kPx>::kThreads) void k_raster_fwd(
+__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
