@@ -226,7 +226,8 @@ __device__ __forceinline__ T block_excl_scan(T v, T &total, T *s) {
 // them, so the emission need not test them again.
 __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict__ rec, int64_t pairs, int64_t N,
                                                          const DevView *__restrict__ views, int T, int mode,
-                                                         uint32_t *__restrict__ cnt, uint4 *__restrict__ pinfo) {
+                                                         uint32_t *__restrict__ cnt, uint4 *__restrict__ pinfo,
+                                                         uint32_t *__restrict__ zbits) {
   __shared__ WarpSplat s_ws[kWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
@@ -242,6 +243,7 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
     if (p < (uint64_t)pairs) {
       const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec));
       const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec) + 1);
+      zbits[p] = __float_as_uint(b.z);   // the depth key, for the compaction
       const DevView &v = views[p / N];
       int x0, y0, x1, y1;
       if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
@@ -380,7 +382,7 @@ __global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, 
 // Down-sweep of the compaction: writes (bits(z), pair) of every valid pair
 // in pair order.
 __global__ __launch_bounds__(kThreads) void k_compact_down(const uint32_t *__restrict__ cnt,
-                                                           const float *__restrict__ rec, uint64_t n,
+                                                           const uint32_t *__restrict__ zbits, uint64_t n,
                                                            const uint64_t *__restrict__ bsum,
                                                            uint32_t *__restrict__ zkey, uint32_t *__restrict__ pval) {
   __shared__ uint32_t s[kWarps + 1];
@@ -401,7 +403,7 @@ __global__ __launch_bounds__(kThreads) void k_compact_down(const uint32_t *__res
     for (int j = 0; j < kScanItems; ++j) {
       if (f[j]) {
         const uint64_t p = i0 + j;
-        zkey[pre] = __float_as_uint(__ldg(rec + p * kRec + 6));
+        zkey[pre] = __ldg(zbits + p);
         pval[pre] = (uint32_t)p;
         ++pre;
       }
@@ -1050,11 +1052,12 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     return PK_OK;
   }
   const int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
-  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt, pinfo);
+  k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt, pinfo,
+                                              zk[1]);
   // compaction of the pairs that touch a tile, keyed by depth bits
   k_scan_reduce<SrcValid><<<kScanBlocks, kThreads, 0, st>>>(SrcValid{cnt}, nullptr, pairs, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 0, maxd, ctr, status);
-  k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, records, pairs, bsum, zk[0], pv[0]);
+  k_compact_down<<<kScanBlocks, kThreads, 0, st>>>(cnt, zk[1], pairs, bsum, zk[0], pv[0]);
   // depth sort of the pairs: stable passes over the 32 bits of z; the
   // compaction kept the (view, Gaussian) order, so sorting inside each
   // view's segment leaves the pairs in (view, depth) order
