@@ -120,10 +120,10 @@ typedef struct pk_options {
   uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
   int32_t bin_mode;                /* pk_bin_mode; default PK_BIN_ELLIPSE */
   int32_t batch;                   /* splats staged per batch by pk_rasterize_fwd: 64, 128 or
-                                      256 (0 = 256); pk_autotune picks it */
+                                      256 (0 = 128); pk_autotune picks it */
   int32_t stage_fwd;               /* pk_stage_mode of pk_rasterize_fwd; default PK_STAGE_LOADS */
   int32_t stage_bwd;               /* pk_stage_mode of pk_rasterize_bwd; default PK_STAGE_LOADS */
-  int32_t batch_bwd;               /* the same for pk_rasterize_bwd (0 = 256) */
+  int32_t batch_bwd;               /* the same for pk_rasterize_bwd (0 = 128) */
 } pk_options;
 
 typedef struct pk_plan pk_plan;
@@ -187,7 +187,7 @@ void pk_plan_destroy(pk_plan *plan);
  * pk_rasterize_bwd for every staging batch (64, 128, 256 splats) and keeps
  * the fastest of each, then times each kernel with both staging modes and
  * keeps the faster one per kernel (two timed runs after one warm-up each; a
- * choice other than the default 256 / plain loads must be more than 2 %
+ * choice other than the default 128 / plain loads must be more than 2 %
  * faster).  The choices are stored in the plan's options; *chosen_batch
  * receives the forward's batch (may be NULL).  The tile side is fixed at 16 and the sort's digit
  * width at 8 bits (10- and 11-bit digits measured slower).  The arguments
@@ -339,6 +339,16 @@ pk_status pk_render_bwd(const pk_plan *plan, const float *soa, const uint8_t *dy
  * target) / (3 P) (0 where equal). */
 pk_status pk_l1_loss_grad(const pk_plan *plan, const float *image, const float *target,
                           float *dL_dimage, void *workspace, pk_stream_t stream);
+
+/* pk_rasterize_fwd with pk_l1_loss_grad fused into its epilogue: the same
+ * image, T_final and n_contrib, the same dL_dimage bit for bit, the loss
+ * in the status block (summed in another order: equal to pk_l1_loss_grad's
+ * up to rounding).  Saves writing the image out and reading it back.
+ * target: [3 * P] float32, planar per view like the image. */
+pk_status pk_rasterize_fwd_l1(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
+                              const uint32_t *tile_ranges, const float *target, float *image,
+                              float *T_final, uint32_t *n_contrib, float *dL_dimage, void *workspace,
+                              pk_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Motion masks and the dynamic mask D_i                                     */

@@ -74,7 +74,7 @@ class Plan:
     def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
                  sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 16,
                  znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse",
-                 batch: int = 256, stage_fwd: str = "loads", stage_bwd: str = "loads", batch_bwd: int = None):
+                 batch: int = 128, stage_fwd: str = "loads", stage_bwd: str = "loads", batch_bwd: int = None):
         lib = N.load()
         self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
                           texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
@@ -270,6 +270,18 @@ def l1_loss_grad(plan: Plan, image, target, dL_dimage, ws, stream=None) -> None:
                                   _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
                                   _ptr(ws, "workspace"), _stream(stream))
     N.check("pk_l1_loss_grad", rc)
+
+
+def rasterize_fwd_l1(plan: Plan, records, sorted_vals, tile_ranges, target, image, T_final, n_contrib, dL_dimage,
+                     ws, stream=None) -> None:
+    """rasterize_fwd with the L1 loss gradient fused into its epilogue."""
+    rc = N.load().pk_rasterize_fwd_l1(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(target, "target", torch.float32, 3 * plan.P), _ptr(image, "image", torch.float32, 3 * plan.P),
+        _ptr(T_final, "T_final", torch.float32, plan.P), _ptr(n_contrib, "n_contrib", _I32, plan.P),
+        _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P), _ptr(ws, "workspace"), _stream(stream))
+    N.check("pk_rasterize_fwd_l1", rc)
 
 
 def photo_loss_grad(plan: Plan, image, target, dL_dimage, ws, lam: float = 0.2, stream=None) -> None:

@@ -124,14 +124,14 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   o.bg[0] = o.bg[1] = o.bg[2] = 0.0f;
   o.max_dups = 0;
   o.bin_mode = PK_BIN_ELLIPSE;
-  o.batch = 256;
+  o.batch = 128;
   o.stage_fwd = PK_STAGE_LOADS;
   o.stage_bwd = PK_STAGE_LOADS;
-  o.batch_bwd = 256;
+  o.batch_bwd = 128;
   if (opts) o = *opts;
   if (o.bin_mode != PK_BIN_RECT && o.bin_mode != PK_BIN_ELLIPSE) return PK_ERR_ARG;
-  if (o.batch == 0) o.batch = 256;
-  if (o.batch_bwd == 0) o.batch_bwd = 256;
+  if (o.batch == 0) o.batch = 128;
+  if (o.batch_bwd == 0) o.batch_bwd = 128;
   for (const int32_t b : {o.batch, o.batch_bwd})
     if (b != 64 && b != 128 && b != 256) return PK_ERR_ARG;
   if ((o.stage_fwd != PK_STAGE_LOADS && o.stage_fwd != PK_STAGE_BULK) ||
@@ -380,16 +380,16 @@ extern "C" pk_status pk_autotune(pk_plan *p, const float *records, const uint32_
   pk_status e = PK_OK;
   // each kernel's batch, with plain loads (the backward reads the
   // forward's outputs, which no batch changes); another choice than the
-  // default (256, loads) must win by more than 2 %, so timing noise does not
+  // default (128, loads) must win by more than 2 %, so timing noise does not
   // flip it
   const float kMargin = 0.98f;
-  const int32_t cands[3] = {256, 128, 64};
+  const int32_t cands[3] = {128, 256, 64};
   p->opts.stage_fwd = p->opts.stage_bwd = PK_STAGE_LOADS;
-  p->opts.batch = p->opts.batch_bwd = 256;
+  p->opts.batch = p->opts.batch_bwd = 128;
   e = fwd();
   for (int k = 0; k < 2 && e == PK_OK; ++k) {
     int32_t *batch = k == 0 ? &p->opts.batch : &p->opts.batch_bwd;
-    int32_t best = 256;
+    int32_t best = 128;
     float best_ms = 0.f;
     for (int i = 0; i < 3 && e == PK_OK; ++i) {
       *batch = cands[i];

@@ -20,12 +20,16 @@ namespace {
 // computed from shared memory.  kPx: pixels per thread (Geo).
 // At 2 pixels per thread the kernel is held to 48 registers (a few spilled)
 // for 10 resident CTAs per SM instead of 9.
+// With a target (not null) the epilogue also takes the L1 term of the
+// objective: dL/dimage = sign(image - target) * scale and the sum of
+// |image - target| (FP32 per thread, FP64 across warps) into loss_acc.
 template <int kBatch, bool kTma, int kPx>
 __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
-    uint32_t *queue, unsigned long long *evals_out, pk_device_status *status) {
+    uint32_t *queue, unsigned long long *evals_out, pk_device_status *status, const float *__restrict__ target,
+    float *__restrict__ dimg, float scale, double *loss_acc) {
   using G = Geo<kPx>;
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
@@ -40,6 +44,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
   bool timed_out = false;
+  float lsum = 0.f;     // sum of |image - target| over this thread's pixels
   if (kTma) {
     if (tid == 0) {
       mbar_init(&s_bar, 1);
@@ -188,28 +193,46 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
       const int y = y0 + q * G::kRowStep;
       if (x < W && y < H) {
         const size_t pix = (size_t)view.pix_off + (size_t)y * W + x;
-        float *img = image + 3 * (size_t)view.pix_off + (size_t)y * W + x;
-        img[0] = __fmaf_rn(T[q], bg0, c0[q]);
-        img[plane] = __fmaf_rn(T[q], bg1, c1[q]);
-        img[2 * plane] = __fmaf_rn(T[q], bg2, c2[q]);
+        const size_t at0 = 3 * (size_t)view.pix_off + (size_t)y * W + x;
+        const float v0 = __fmaf_rn(T[q], bg0, c0[q]), v1 = __fmaf_rn(T[q], bg1, c1[q]);
+        const float v2 = __fmaf_rn(T[q], bg2, c2[q]);
+        image[at0] = v0;
+        image[at0 + plane] = v1;
+        image[at0 + 2 * plane] = v2;
         Tout[pix] = T[q];
         ncontrib[pix] = last[q];
+        if (target) {
+          const float vs[3] = {v0, v1, v2};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float d = vs[c] - __ldcs(target + at0 + c * plane);
+            lsum += fabsf(d);
+            __stcs(dimg + at0 + c * plane, d > 0.f ? scale : (d < 0.f ? -scale : 0.f));
+          }
+        }
       }
     }
     __syncthreads();   // everyone has read s_tile / s_view before the next fetch
   }
-  // one atomic per warp for the evaluation counter
+  // one atomic per warp for the evaluation counter (and the loss)
   unsigned long long ev = evals;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
   if (lane == 0 && ev) atomicAdd(evals_out, ev);
+  if (target) {
+    double dl = (double)lsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+    if (lane == 0 && dl != 0.0) atomicAdd(loss_acc, dl);
+  }
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
 template <int kBatch, bool kFwdTma>
 pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
-                     DevCounters *ctr, pk_device_status *status, cudaStream_t st) {
+                     DevCounters *ctr, pk_device_status *status, const float *target, float *dimg,
+                     cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -223,24 +246,24 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
   k_raster_fwd<kBatch, kFwdTma, kFwdPx><<<(int)grid, Geo<kFwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
-      &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status);
+      &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status, target, dimg,
+      (float)(1.0 / (3.0 * (double)std::max<int64_t>(1, p->P))), &ctr->loss_acc);
   return check_launch();
 }
 
-}  // namespace
-
-extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
-                                      void *ws, pk_stream_t stream) {
-  if (!p || !records || !sorted_vals || !tile_ranges || !image || !T_final || !n_contrib || !ws) return PK_ERR_ARG;
-  if (!aligned16(records)) return PK_ERR_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                        const uint32_t *tile_ranges, const float *target, float *image, float *T_final,
+                        uint32_t *n_contrib, float *dimg, void *ws, cudaStream_t st) {
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
   if (cudaMemsetAsync(&ctr->tile_queue[0], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
   if (cudaMemsetAsync(&status->evals_fwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
-#define PK_FWD(B, M) \
-  return launch_fwd<B, M>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, st)
+  // loss_acc, ssim_acc and ssim_lambda (0: the loss is L1 alone)
+  if (target && cudaMemsetAsync(&ctr->loss_acc, 0, 2 * sizeof(double) + sizeof(float), st) != cudaSuccess)
+    return PK_ERR_CUDA;
+#define PK_FWD(B, M)                                                                                          \
+  return launch_fwd<B, M>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, \
+                          target, dimg, st)
   const bool tma = p->opts.stage_fwd == PK_STAGE_BULK;
   switch (p->opts.batch) {
     case 64:
@@ -254,4 +277,27 @@ extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, co
       PK_FWD(256, false);
   }
 #undef PK_FWD
+}
+
+}  // namespace
+
+extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+                                      void *ws, pk_stream_t stream) {
+  if (!p || !records || !sorted_vals || !tile_ranges || !image || !T_final || !n_contrib || !ws) return PK_ERR_ARG;
+  if (!aligned16(records)) return PK_ERR_ARG;
+  return rasterize_fwd(p, records, sorted_vals, tile_ranges, nullptr, image, T_final, n_contrib, nullptr, ws,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" pk_status pk_rasterize_fwd_l1(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                                         const uint32_t *tile_ranges, const float *target, float *image,
+                                         float *T_final, uint32_t *n_contrib, float *dL_dimage, void *ws,
+                                         pk_stream_t stream) {
+  if (!p || !records || !sorted_vals || !tile_ranges || !target || !image || !T_final || !n_contrib ||
+      !dL_dimage || !ws)
+    return PK_ERR_ARG;
+  if (!aligned16(records)) return PK_ERR_ARG;
+  return rasterize_fwd(p, records, sorted_vals, tile_ranges, target, image, T_final, n_contrib, dL_dimage, ws,
+                       reinterpret_cast<cudaStream_t>(stream));
 }

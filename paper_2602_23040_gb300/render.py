@@ -49,8 +49,8 @@ class Renderer:
         self.dimage = torch.empty(3 * p.P, dtype=f32, device=self.device)
         self._has_dyn = False
 
-    # forward: a1 .. a4
-    def forward(self, atlas, occ, dyn=None, stream=None):
+    # forward: a1 .. a4 (target: the L1 loss gradient fused into a4)
+    def forward(self, atlas, occ, dyn=None, stream=None, target=None):
         p = self.plan
         self._has_dyn = dyn is not None
         if self.lohi is not None:
@@ -60,8 +60,12 @@ class Renderer:
             api.atlas_gather(p, atlas, occ, dyn, self.soa, self.texel, self.dynflag, self.ws, stream)
         api.project_and_sh(p, self.soa, self.records, self.ws, stream)
         api.bin_and_sort(p, self.records, self.sorted_vals, self.ranges, self.ws, stream)
-        api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, self.image, self.T, self.n_contrib,
-                          self.ws, stream)
+        if target is None:
+            api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, self.image, self.T, self.n_contrib,
+                              self.ws, stream)
+        else:
+            api.rasterize_fwd_l1(p, self.records, self.sorted_vals, self.ranges, target, self.image, self.T,
+                                 self.n_contrib, self.dimage, self.ws, stream)
         return self.image
 
     # backward: a5 .. a6
@@ -74,9 +78,8 @@ class Renderer:
         return grad_atlas
 
     def l1_step(self, atlas, occ, dyn, target, grad_atlas, stream=None):
-        """One fitting step: forward, L1 loss gradient, backward."""
-        self.forward(atlas, occ, dyn, stream)
-        api.l1_loss_grad(self.plan, self.image, target, self.dimage, self.ws, stream)
+        """One fitting step: forward with the L1 loss gradient, backward."""
+        self.forward(atlas, occ, dyn, stream, target=target)
         self.backward(self.dimage, grad_atlas, False, stream)
 
     def photo_step(self, atlas, occ, dyn, target, grad_atlas, lam: float = 0.2, stream=None):
@@ -191,10 +194,12 @@ class PerViewLoop:
             api.atlas_gather(p, atlas, occ, dyn, self.soa, self.texel, self.dynflag, ws, stream)
             api.project_and_sh(p, self.soa, self.records, ws, stream)
             api.bin_and_sort(p, self.records, self.sorted_vals, self.ranges, ws, stream)
-            api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, img, T, nc, ws, stream)
             if loss:
                 o = self.offsets[i]
-                api.l1_loss_grad(p, img, target[3 * o:3 * (o + p.P)], dimg, ws, stream)
+                api.rasterize_fwd_l1(p, self.records, self.sorted_vals, self.ranges, target[3 * o:3 * (o + p.P)],
+                                     img, T, nc, dimg, ws, stream)
+            else:
+                api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, img, T, nc, ws, stream)
             api.rasterize_bwd(p, self.records, self.sorted_vals, self.ranges, T, nc, dimg, self.grad2d, ws, stream)
             api.atlas_scatter_grad(p, self.soa, self.grad2d, self.dynflag if dyn is not None else None, self.texel,
                                    grad_atlas, i > 0, ws, stream)

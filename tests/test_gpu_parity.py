@@ -226,6 +226,34 @@ def _records_forward(seed, dimg_seed=None):
 
 
 @pytest.mark.parametrize("seed", [5, 6])
+def test_rasterize_fwd_l1_matches_separate_calls(orc, seed):
+    """The fused forward + L1: image, T, n_contrib and dL/dimage bit for bit
+    equal to pk_rasterize_fwd then pk_l1_loss_grad, the loss equal up to
+    summation order, and both equal to the L1 of the oracle's definition."""
+    pk = _pk()
+    o = _records_forward(seed)
+    plan, ws = o["plan"], o["ws"]
+    target = torch.from_numpy(np.random.default_rng(seed + 40).random(3 * plan.P).astype(np.float32)).cuda()
+    # a few exact ties (zero gradient)
+    target[::97] = o["img"][::97]
+    g_ref = torch.empty_like(o["img"])
+    pk.l1_loss_grad(plan, o["img"], target, g_ref, ws)
+    loss_ref = pk.read_status(plan, ws)["loss"]
+    img, T = torch.full_like(o["img"], -1.0), torch.full_like(o["T"], -1.0)
+    nc, g = torch.full_like(o["nc"], -1), torch.full_like(o["img"], 7.0)
+    pk.rasterize_fwd_l1(plan, o["drec"], o["vals"], o["ranges"], target, img, T, nc, g, ws)
+    st = pk.read_status(plan, ws)
+    assert st["flags"] == 0
+    assert torch.equal(img.view(torch.int32), o["img"].view(torch.int32))
+    assert torch.equal(T.view(torch.int32), o["T"].view(torch.int32))
+    assert torch.equal(nc, o["nc"])
+    assert torch.equal(g.view(torch.int32), g_ref.view(torch.int32))
+    want = np.abs(o["img"].cpu().numpy().astype(np.float64) - target.cpu().numpy().astype(np.float64)).mean()
+    assert abs(st["loss"] - loss_ref) <= 1e-6 * abs(want)
+    assert abs(st["loss"] - want) <= 1e-6 * abs(want)
+
+
+@pytest.mark.parametrize("seed", [5, 6])
 def test_rasterize_fwd_on_identical_records(orc, seed):
     o = _records_forward(seed)
     rec64 = o["rec"].astype(np.float64)
