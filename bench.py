@@ -116,7 +116,7 @@ def algorithmic_bytes(plan, texel_bytes, dups, n_dyn):
         "a1_atlas_gather": G * D * texel_bytes + G * D * 4,
         "a2_project_and_sh": G * D * 4 + plan.pairs * 48,
         "a3_bin_and_sort": dups * (12 + 24),
-        "a4_rasterize_fwd": dups * 40 + P * 20,
+        "a4_rasterize_fwd_l1": dups * 40 + P * 20 + P * 24,   # + target read, dL/dimage write
         "a5_rasterize_bwd": dups * 40 + P * 20 + plan.pairs * 36,
         "a6_atlas_scatter_grad": G * D * 4 + plan.pairs * 36 + n_dyn * D * 4,
     }
@@ -125,7 +125,7 @@ def algorithmic_bytes(plan, texel_bytes, dups, n_dyn):
 # Sources of each rooflined kernel: the DRAM traffic measured by ncu is
 # reported only while these still hash to the profiled version.
 KERNEL_SOURCES = {
-    "a4_rasterize_fwd": ("k_raster_fwd", ["pk_raster_fwd.cu", "pk_raster.cuh", "pk_common.cuh", "pk_tma.cuh"]),
+    "a4_rasterize_fwd_l1": ("k_raster_fwd", ["pk_raster_fwd.cu", "pk_raster.cuh", "pk_common.cuh", "pk_tma.cuh"]),
     "a5_rasterize_bwd": ("k_raster_bwd", ["pk_raster_bwd.cu", "pk_raster.cuh", "pk_common.cuh", "pk_tma.cuh"]),
 }
 
@@ -155,8 +155,9 @@ def measured_traffic(stage, dups):
 
 
 def launches_per_step(plan):
-    # gather 2, project 1, bin_and_sort (as the library counts it), fwd 1, loss 1, bwd 1, scatter 1
-    return 2 + 1 + int(plan.sizes.bin_kernels) + 4
+    # gather 2, project 1, bin_and_sort (as the library counts it), fwd with the loss 2 (zeroing +
+    # compositing), bwd 2 (zeroing + adjoint), scatter 1
+    return 2 + 1 + int(plan.sizes.bin_kernels) + 5
 
 
 # ---------------------------------------------------------------------------
@@ -363,6 +364,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--views", type=int, default=0, help="use only the first N cameras (profiling cases)")
+    ap.add_argument("--tile", type=int, default=16, choices=[16, 32], help="tile side of the binning")
     ap.add_argument("--ref-window", type=int, default=192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-view", action="store_true")
@@ -399,7 +401,7 @@ def main():
     grad = torch.zeros(F * D * Hh * W, dtype=torch.float32, device=dev)
 
     # plan sized from a first eager step (re-planned once if the entries overflow)
-    r = pk.Renderer(pk.Plan.for_scene(scene), dev)
+    r = pk.Renderer(pk.Plan.for_scene(scene, tile=args.tile), dev)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         r.ensure_capacity(atlas, occ, dyn)
@@ -445,14 +447,14 @@ def main():
     mpix = plan.P * world / (ms * 1e-3) / 1e6
 
     # per-call durations (eager, CUDA events on the launching stream)
-    stage_names = ["a1_atlas_gather", "a2_project_and_sh", "a3_bin_and_sort", "a4_rasterize_fwd", "l1_loss_grad",
+    stage_names = ["a1_atlas_gather", "a2_project_and_sh", "a3_bin_and_sort", "a4_rasterize_fwd_l1",
                    "a5_rasterize_bwd", "a6_atlas_scatter_grad"]
     calls = [
         lambda: pk.atlas_gather(plan, atlas, occ, dyn, r.soa, r.texel, r.dynflag, r.ws),
         lambda: pk.project_and_sh(plan, r.soa, r.records, r.ws),
         lambda: pk.bin_and_sort(plan, r.records, r.sorted_vals, r.ranges, r.ws),
-        lambda: pk.rasterize_fwd(plan, r.records, r.sorted_vals, r.ranges, r.image, r.T, r.n_contrib, r.ws),
-        lambda: pk.l1_loss_grad(plan, r.image, target, r.dimage, r.ws),
+        lambda: pk.rasterize_fwd_l1(plan, r.records, r.sorted_vals, r.ranges, target, r.image, r.T, r.n_contrib,
+                                    r.dimage, r.ws),
         lambda: pk.rasterize_bwd(plan, r.records, r.sorted_vals, r.ranges, r.T, r.n_contrib, r.dimage, r.grad2d,
                                  r.ws),
         lambda: pk.atlas_scatter_grad(plan, r.soa, r.grad2d, r.dynflag if dyn is not None else None, r.texel,
@@ -480,11 +482,11 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"]))
     alu_peak_tops = sms * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
     # dominant single kernel (bin_and_sort is a chain of ~30 kernels and is reported in stages_ms)
-    dom = max(("a2_project_and_sh", "a4_rasterize_fwd", "a5_rasterize_bwd", "a6_atlas_scatter_grad"),
+    dom = max(("a2_project_and_sh", "a4_rasterize_fwd_l1", "a5_rasterize_bwd", "a6_atlas_scatter_grad"),
               key=lambda n: stage_ms[n])
     t_dom = stage_ms[dom] * 1e-3
-    if dom in ("a4_rasterize_fwd", "a5_rasterize_bwd"):
-        ops = (evals_fwd * OPS_FWD) if dom == "a4_rasterize_fwd" else (evals_bwd * OPS_BWD)
+    if dom in ("a4_rasterize_fwd_l1", "a5_rasterize_bwd"):
+        ops = (evals_fwd * OPS_FWD) if dom == "a4_rasterize_fwd_l1" else (evals_bwd * OPS_BWD)
         ach = ops / t_dom / 1e12
         traffic, tsrc = measured_traffic(dom, dups)
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak_tops, "unit": "TOP/s (FP32)",
@@ -502,7 +504,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "gaussians": plan.G, "views": plan.V, "pixels": plan.P,
                    "sh_degree": scene.sh_degree, "texels": "fp16" if texel_bytes == 2 else "fp32",
-                   "tile": 16, "batch": {"fwd": plan.batch, "bwd": plan.batch_bwd},
+                   "tile": args.tile, "batch": {"fwd": plan.batch, "bwd": plan.batch_bwd},
                    "staging": {"fwd": plan.stage_fwd, "bwd": plan.stage_bwd},
                    "pixels_per_thread": {"fwd": 2, "bwd": 4},
                    "tuned_by": "defaults (profiler run)" if args.profile else "pk_autotune", "graph": "whole step in one CUDA graph",
@@ -537,40 +539,53 @@ def main():
         copy_stream = torch.cuda.Stream(dev)
         ev_in = [torch.cuda.Event(), torch.cuda.Event()]
         ev_done = [torch.cuda.Event(), torch.cuda.Event()]
-        ke = max(3, min(args.steps, 10))
+        ke = max(3, min(args.steps, 20))
+        # device time of each step's graph and of each upload, for the breakdown
+        g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ke)]
+        u_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ke)]
 
-        def upload(slot):
+        def upload(slot, k):
             with torch.cuda.stream(copy_stream):
                 copy_stream.wait_event(ev_done[slot])
+                u_ev[k][0].record(copy_stream)
                 bufs[slot][0].copy_(h_atlas, non_blocking=True)
                 bufs[slot][1].copy_(h_target, non_blocking=True)
+                u_ev[k][1].record(copy_stream)
                 ev_in[slot].record(copy_stream)
 
         torch.cuda.synchronize(dev)
         for e_ in ev_done:
             e_.record(stream)
         t0 = time.perf_counter()
-        upload(0)
+        upload(0, 0)
         for k in range(ke):
             slot = k % 2
             with torch.cuda.stream(stream):
                 stream.wait_event(ev_in[slot])
+                g_ev[k][0].record(stream)
                 graphs[slot].replay()
+                g_ev[k][1].record(stream)
                 ev_done[slot].record(stream)
             if k + 1 < ke:
-                upload(1 - slot)
+                upload(1 - slot, k + 1)
             s = r.status(stream)          # device -> host read of this step's loss (waits for the step)
         torch.cuda.synchronize(dev)
         dt = (time.perf_counter() - t0) / ke
+        graph_ms = statistics.median(a.elapsed_time(b) for a, b in g_ev)
+        upload_ms = statistics.median(a.elapsed_time(b) for a, b in u_ev)
+        # when the next step's upload starts, from the start of this step's graph
+        upload_lag_ms = statistics.median(g_ev[k][0].elapsed_time(u_ev[k + 1][0]) for k in range(ke - 1))
         out["e2e"] = {"value": plan.P / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
                       "h2d_bytes_per_step": int(h_atlas.numel() * h_atlas.element_size() + h_target.numel() * 4),
                       "d2h_bytes_per_step": int(ctypes_sizeof_status()), "loss": s["loss"],
                       "pipeline": "inputs double-buffered; next step's copies overlap this step's compute",
-                      "steps": ke}
+                      "graph_ms_per_step": graph_ms, "upload_ms_per_step": upload_ms,
+                      "upload_start_after_graph_start_ms": upload_lag_ms, "steps": ke}
         del bufs, g2
 
     if not args.profile and not args.no_per_view and rank == 0:
-        loop = pk.PerViewLoop.for_scene(scene, dev, max_dups=int(dups / max(1, plan.V) * 2) + 65536)
+        loop = pk.PerViewLoop.for_scene(scene, dev, tile=args.tile,
+                                        max_dups=int(dups / max(1, plan.V) * 2) + 65536)
         with torch.cuda.stream(stream):
             loop.ensure_capacity(atlas, occ, dyn, target, grad)
         torch.cuda.synchronize(dev)

@@ -114,7 +114,7 @@ typedef enum pk_bin_mode { PK_BIN_RECT = 0, PK_BIN_ELLIPSE = 1 } pk_bin_mode;
 typedef enum pk_stage_mode { PK_STAGE_LOADS = 0, PK_STAGE_BULK = 1 } pk_stage_mode;
 
 typedef struct pk_options {
-  int32_t tile;                    /* tile side: 16 (8 and 32 reserved) */
+  int32_t tile;                    /* tile side: 16 (0 = 16) or 32; images do not depend on it */
   float znear;                     /* cull z <= znear; default 0.01 */
   float bg[3];                     /* background colour; default 0 */
   uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
@@ -189,8 +189,9 @@ void pk_plan_destroy(pk_plan *plan);
  * keeps the faster one per kernel (two timed runs after one warm-up each; a
  * choice other than the default 128 / plain loads must be more than 2 %
  * faster).  The choices are stored in the plan's options; *chosen_batch
- * receives the forward's batch (may be NULL).  The tile side is fixed at 16 and the sort's digit
- * width at 8 bits (10- and 11-bit digits measured slower).  The arguments
+ * receives the forward's batch (may be NULL).  The tile side (a plan option:
+ * it changes the binning) and the sort's digit width (8 bits; 10- and 11-bit
+ * digits measured slower) are not tuned here.  The arguments
  * are those of the two calls; afterwards image, T_final, n_contrib and
  * grad2d hold a forward and backward with the chosen options.
  * Synchronises `stream`; do not call it during graph capture. */

@@ -119,8 +119,9 @@ class Plan:
     def for_scene(cls, scene, views=None, **kw):
         F, D, H, W = scene.atlas.shape
         tt = "f16" if str(scene.atlas.dtype) == "float16" else "f32"
+        tile = kw.pop("tile", scene.tile)
         return cls(scene.levels, (W, H), scene.sh_degree, F, tt, views if views is not None else scene.views,
-                   scene.n_live, tile=scene.tile, **kw)
+                   scene.n_live, tile=tile, **kw)
 
     def with_capacity(self, max_dups: int) -> "Plan":
         """Same plan with another capacity of (pair, tile) entries."""

@@ -880,26 +880,28 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
 }
 
 // Where every view's items start, the pairs being grouped by view (pair
-// pid belongs to view pid / N).  kEntries: seg[v] = offs of the first pair
-// of a view >= v (the total number of entries where no such pair is left),
-// else seg[v] = the index of that pair (n where none is left); seg[V] =
-// the total.
+// pid belongs to view pid / N): one thread per view finds the first pair
+// with pid >= v N by binary search.  kEntries: seg[v] = offs of that pair
+// (the total number of entries where no such pair is left), else seg[v] =
+// its index (n where none is left); seg[V] = the total.
 template <bool kEntries>
 __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__restrict__ pval,
                                                             const uint32_t *__restrict__ offs,
                                                             const DevCounters *ctr, uint32_t N, int V,
                                                             uint32_t *__restrict__ seg) {
   const uint32_t n = ctr->n_valid, total = kEntries ? ctr->dups : n;
-  if (n == 0 || total == 0) {
-    for (int v = blockIdx.x * kThreads + threadIdx.x; v <= V; v += gridDim.x * kThreads) seg[v] = 0;
-    return;
-  }
-  for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-    const int v = (int)(pval[i] / N);
-    const int prev = i ? (int)(pval[i - 1] / N) : -1;
-    for (int u = prev + 1; u <= v; ++u) seg[u] = kEntries ? offs[i] : i;
-    if (i + 1 == n)
-      for (int u = v + 1; u <= V; ++u) seg[u] = total;
+  for (int v = blockIdx.x * kThreads + threadIdx.x; v <= V; v += gridDim.x * kThreads) {
+    if (n == 0 || total == 0) {
+      seg[v] = 0;
+      continue;
+    }
+    const uint64_t first = (uint64_t)v * N;
+    uint32_t lo = 0, hi = n;   // first index with pval >= first
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo) / 2;
+      if ((uint64_t)pval[mid] < first) lo = mid + 1; else hi = mid;
+    }
+    seg[v] = lo == n ? total : (kEntries ? offs[lo] : lo);
   }
 }
 
@@ -1045,12 +1047,10 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   const int4 *tab = at<int4>(ws, L.sblk);
   uint32_t *vseg = at<uint32_t>(ws, L.vseg), *pseg = vseg + (p->V + 1);
 
-  if (cudaMemsetAsync(tile_ranges, 0, sizeof(uint32_t) * 2 * (size_t)p->n_tiles, st) != cudaSuccess)
-    return PK_ERR_CUDA;
-  if (pairs == 0) {
-    if (cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st) != cudaSuccess) return PK_ERR_CUDA;
-    return PK_OK;
-  }
+  pk_status ze = zero_async({{tile_ranges, sizeof(uint32_t) * 2 * (size_t)p->n_tiles},
+                             {ctr, pairs == 0 ? sizeof(DevCounters) : 0}},
+                            st);
+  if (ze != PK_OK || pairs == 0) return ze;
   const int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
   k_pair_count<<<cblocks, kThreads, 0, st>>>(records, p->pairs, p->N, views, p->T, p->opts.bin_mode, cnt, pinfo,
                                               zk[1]);
@@ -1063,8 +1063,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   // view's segment leaves the pairs in (view, depth) order
   SegSpec psp{nullptr, nullptr};
   if (seg) {
-    k_view_segments<false><<<std::max(1, sms) * 8, kThreads, 0, st>>>(pv[0], nullptr, ctr, (uint32_t)p->N, p->V,
-                                                                      pseg);
+    k_view_segments<false><<<(p->V + kThreads) / kThreads, kThreads, 0, st>>>(pv[0], nullptr, ctr, (uint32_t)p->N,
+                                                                            p->V, pseg);
     psp = SegSpec{tab + kSortBlocks, pseg};
   }
   pk_status e;
@@ -1089,7 +1089,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int nblocks = sort_blocks();
   if (seg) {
     key_bits = local_tile_bits(p);
-    k_view_segments<true><<<std::max(1, sms) * 8, kThreads, 0, st>>>(pval, offs, ctr, (uint32_t)p->N, p->V, vseg);
+    k_view_segments<true><<<(p->V + kThreads) / kThreads, kThreads, 0, st>>>(pval, offs, ctr, (uint32_t)p->N, p->V,
+                                                                          vseg);
     sp = SegSpec{tab, vseg};
     nblocks = nseg;
   }
@@ -1119,17 +1120,18 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
 
 }  // namespace
 
-// Mirrors the launches of bin_and_sort_impl: count, scan (2), compaction,
-// the depth passes, [view keys + view passes], offsets (3), [view
+// Mirrors the launches of bin_and_sort_impl: zeroing, count, scan (2),
+// compaction, [pair segments], the depth passes, offsets (3), [entry
 // segments], emission, the tile passes, ranges; 3 kernels per radix pass.
 int pk::bin_kernel_count(const pk_plan *p) {
-  if (!p || p->pairs == 0) return 0;
+  if (!p) return 0;
+  if (p->pairs == 0) return 1;
   int4 tab[2 * kSortBlocks];
   int nt = 0, np = 0;
   const bool seg = seg_tables(p, tab, &nt, &np);
   int widths[8];
   int passes = radix_plan(32, widths);
-  int kernels = 4 + 3 + 1 + 1;
+  int kernels = 1 + 4 + 3 + 1 + 1;
   if (seg) kernels += 2;   // the pairs' and the entries' view segments
   passes += radix_plan(seg ? local_tile_bits(p) : p->tile_bits, widths);
   return kernels + 3 * passes;

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <initializer_list>
+#include <utility>
+
 #include "../../include/packuv.h"
 
 namespace pk {
@@ -99,6 +103,9 @@ __host__ __device__ inline T *at(void *base, size_t off) {
 // Host-side launch helpers (implemented in pk_plan.cu).
 pk_status check_launch();
 bool aligned16(const void *p);
+// Zero up to four (pointer, bytes) ranges with one kernel (4-byte aligned
+// pointers, sizes multiples of 4 bytes).
+pk_status zero_async(std::initializer_list<std::pair<void *, size_t>> spans, cudaStream_t st);
 // Radix blocks of the entry passes on the current device, and the block
 // tables of the segmented (per-view) sorts: tab[0, kSortBlocks) for the
 // tile passes, tab[kSortBlocks, 2 kSortBlocks) for the depth passes

@@ -1,5 +1,5 @@
 // Host side of the C ABI: atlas layout, plan validation, workspace layout,
-// status read-back.  No kernel lives here.
+// status read-back, and the one zeroing kernel the other calls share.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -18,6 +18,53 @@ pk_status check_launch() {
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+namespace {
+
+struct ZeroSpans {
+  uint32_t *p[4];
+  uint64_t n[4];   // 32-bit words
+  int k;
+};
+
+// Zeroes up to four word ranges: 16-byte stores over each range's aligned
+// body, single words at its ends.
+__global__ __launch_bounds__(256) void k_zero(ZeroSpans z) {
+  const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+  for (int s = 0; s < z.k; ++s) {
+    uint32_t *p = z.p[s];
+    const uint64_t n = z.n[s];
+    const uint64_t head = std::min<uint64_t>(n, ((16u - (reinterpret_cast<uintptr_t>(p) & 15u)) & 15u) / 4u);
+    const uint64_t n4 = (n - head) / 4;
+    if (tid < head) p[tid] = 0u;
+    uint4 *q = reinterpret_cast<uint4 *>(p + head);
+    for (uint64_t i = tid; i < n4; i += nt) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    const uint64_t tail = head + 4 * n4;
+    if (tid < n - tail) p[tail + tid] = 0u;
+  }
+}
+
+}  // namespace
+
+// One kernel instead of cudaMemsetAsync: inside a CUDA graph a memset node
+// may be run by a copy engine, where it queues behind (and is delayed by)
+// unrelated host <-> device copies of other streams.
+pk_status zero_async(std::initializer_list<std::pair<void *, size_t>> spans, cudaStream_t st) {
+  ZeroSpans z{};
+  uint64_t most = 0;
+  for (const auto &sp : spans) {
+    if (z.k == 4 || (reinterpret_cast<uintptr_t>(sp.first) & 3u) || (sp.second & 3u)) return PK_ERR_ARG;
+    if (sp.second == 0) continue;
+    z.p[z.k] = static_cast<uint32_t *>(sp.first);
+    z.n[z.k] = sp.second / 4;
+    most = std::max<uint64_t>(most, z.n[z.k]);
+    ++z.k;
+  }
+  if (z.k == 0) return PK_OK;
+  const uint64_t blocks = std::min<uint64_t>(std::max<uint64_t>(1, (most / 4 + 255) / 256), 152 * 8);
+  k_zero<<<(unsigned)blocks, 256, 0, st>>>(z);
+  return check_launch();
+}
 
 }  // namespace pk
 
@@ -137,7 +184,8 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   if ((o.stage_fwd != PK_STAGE_LOADS && o.stage_fwd != PK_STAGE_BULK) ||
       (o.stage_bwd != PK_STAGE_LOADS && o.stage_bwd != PK_STAGE_BULK))
     return PK_ERR_ARG;
-  if (o.tile != 16) return PK_ERR_UNSUPPORTED;
+  if (o.tile == 0) o.tile = 16;
+  if (o.tile != 16 && o.tile != 32) return PK_ERR_UNSUPPORTED;
   if (!(o.znear > 0.0f) || !isfinite(o.znear)) return PK_ERR_ARG;
   for (int c = 0; c < 3; ++c)
     if (!isfinite(o.bg[c])) return PK_ERR_ARG;

@@ -9,23 +9,27 @@
 
 namespace pk {
 
-constexpr int kTileSide = 16;
+constexpr int kTileSide = 16;   // the default tile side (pk_options.tile: 16 or 32)
 // Splats staged per batch: a template parameter of the compositing
 // kernels (64, 128 or 256; pk_options.batch, chosen by pk_autotune).
 constexpr int kBatchMax = 256;
 
-// One CTA per 16 x 16 tile with kPx pixels per thread (2 or 4).  A warp
-// covers a kBW x 8 block (8 x 8 for 2 pixels, 16 x 8 for 4) and skips as a
-// whole every splat that misses its block; a lane holds one column of it,
-// kPx pixels kRowStep rows apart.  More pixels per lane spread the per-splat
-// work of a warp (shared-memory loads, the block test, the gradient
-// reduction) over more pixels, at the price of a coarser block test.
-template <int kPx>
+// One CTA per kT x kT tile (16 or 32) with kPx pixels per thread (2 or 4).
+// A warp covers a kBW x 8 block (8 x 8 for 2 pixels, 16 x 8 for 4), the
+// blocks in row-major order over the tile, and skips as a whole every
+// splat that misses its block; a lane holds one column of it, kPx pixels
+// kRowStep rows apart.  More pixels per lane spread the per-splat work of
+// a warp (shared-memory loads, the block test, the gradient reduction)
+// over more pixels, at the price of a coarser block test; a larger tile
+// shares each staged splat among more warps and has fewer entries to sort.
+template <int kPx, int kT = kTileSide>
 struct Geo {
-  static constexpr int kThreads = kTileSide * kTileSide / kPx;   // 128 or 64
+  static_assert((kPx == 2 || kPx == 4) && (kT == 16 || kT == 32), "2 or 4 pixels, 16 or 32 px tiles");
+  static constexpr int kThreads = kT * kT / kPx;
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kBW = kPx == 2 ? 8 : 16;
   static constexpr int kRowStep = 32 / kBW;                       // 4 or 2
+  static constexpr int kBlocksX = kT / kBW;                       // warp blocks per tile row
 };
 
 // Pixels per thread: the forward keeps 2 (its per-splat work is small, and
@@ -34,20 +38,14 @@ struct Geo {
 constexpr int kFwdPx = 2, kBwdPx = 4;
 
 // Lane's column ox and first row oy in the tile; (bx, by) = its warp block's corner.
-template <int kPx>
+template <int kPx, int kT>
 __device__ __forceinline__ void pixel_of(int tid, int &ox, int &oy, int &bx, int &by) {
+  using G = Geo<kPx, kT>;
   const int w = tid >> 5, l = tid & 31;
-  if (kPx == 2) {
-    bx = (w & 1) * 8;
-    by = (w >> 1) * 8;
-    ox = bx + (l & 7);
-    oy = by + (l >> 3);
-  } else {
-    bx = 0;
-    by = w * 8;
-    ox = l & 15;
-    oy = by + (l >> 4);
-  }
+  bx = (w % G::kBlocksX) * G::kBW;
+  by = (w / G::kBlocksX) * 8;
+  ox = bx + (l % G::kBW);
+  oy = by + l / G::kBW;
 }
 
 // View that owns global tile t (binary search over tile offsets).

@@ -114,15 +114,16 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // memory by bulk copies (one 48-byte copy per splat, completed on an
 // mbarrier) while the current batch is processed.  kPx: pixels per thread.
 // At 4 pixels per thread the kernel is held to 64 registers (no spills):
-// 16 resident CTAs per SM instead of 10 hide more of its latency.
-template <int kBatch, bool kTma, int kPx>
-__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_raster_bwd(
+// 16 resident CTAs per SM instead of 10 hide more of its latency (4 of 256
+// threads with 32 px tiles).
+template <int kBatch, bool kTma, int kPx, int kT>
+__global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 4 ? (kT == 16 ? 16 : 4) : 1)) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
     const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out,
     pk_device_status *status) {
-  using G = Geo<kPx>;
+  using G = Geo<kPx, kT>;
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
   __shared__ uint32_t s_pid[kTma ? kBatch : 1];
@@ -133,7 +134,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_ras
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy, bx, by;
-  pixel_of<kPx>(tid, ox, oy, bx, by);
+  pixel_of<kPx, kT>(tid, ox, oy, bx, by);
   const int my_idx = reduce_scatter9_index(lane);
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
@@ -167,10 +168,10 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_ras
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy;
+    const int x = tx * kT + ox, y0 = ty * kT + oy;
     const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
-    const float wx0 = (float)(tx * kTileSide + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
-    const float wy0 = (float)(ty * kTileSide + by) + 0.5f, wy1 = wy0 + 7.f;
+    const float wx0 = (float)(tx * kT + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
+    const float wy0 = (float)(ty * kT + by) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t);
     const size_t plane = (size_t)W * H;
     float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx];
@@ -287,7 +288,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_ras
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
-template <int kBatch, bool kBwdTma>
+template <int kBatch, bool kBwdTma, int kT>
 pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
                      const float *dL_dimage, float *grad2d, void *ws, DevCounters *ctr, pk_device_status *status,
@@ -295,14 +296,14 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma, kBwdPx>,
-                                                Geo<kBwdPx>::kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT>,
+                                                Geo<kBwdPx, kT>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > p->n_tiles) grid = p->n_tiles;
   if (grid < 1) grid = 1;
-  k_raster_bwd<kBatch, kBwdTma, kBwdPx><<<(int)grid, Geo<kBwdPx>::kThreads, 0, st>>>(
+  k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT><<<(int)grid, Geo<kBwdPx, kT>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
       &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd), status);
@@ -320,12 +321,16 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
-  if (cudaMemsetAsync(grad2d, 0, sizeof(float) * kG2d * (size_t)p->pairs, st) != cudaSuccess) return PK_ERR_CUDA;
-  if (cudaMemsetAsync(&ctr->tile_queue[1], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
-  if (cudaMemsetAsync(&status->evals_bwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
-#define PK_BWD(B, M)                                                                                         \
-  return launch_bwd<B, M>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, ctr, \
-                          status, st)
+  pk_status ze = zero_async({{grad2d, sizeof(float) * kG2d * (size_t)p->pairs},
+                             {&ctr->tile_queue[1], sizeof(uint32_t)},
+                             {&status->evals_bwd, sizeof(uint64_t)}},
+                            st);
+  if (ze != PK_OK) return ze;
+#define PK_BWD(B, M)                                                                                          \
+  return p->T == 32 ? launch_bwd<B, M, 32>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, \
+                                           grad2d, ws, ctr, status, st)                                         \
+                    : launch_bwd<B, M, 16>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, \
+                                           grad2d, ws, ctr, status, st)
   const bool tma = p->opts.stage_bwd == PK_STAGE_BULK;
   switch (p->opts.batch_bwd) {
     case 64:

@@ -18,19 +18,20 @@ namespace {
 // bulk copies (one 48-byte copy per splat, completed on an mbarrier) while
 // the current batch is composited; the derived per-splat values are then
 // computed from shared memory.  kPx: pixels per thread (Geo).
-// At 2 pixels per thread the kernel is held to 48 registers (a few spilled)
-// for 10 resident CTAs per SM instead of 9.
+// At 2 pixels per thread and 16 px tiles the kernel is held to 48
+// registers (a few spilled) for 10 resident CTAs per SM instead of 9; with
+// 32 px tiles (512 threads) to 64 for 2 CTAs.
 // With a target (not null) the epilogue also takes the L1 term of the
 // objective: dL/dimage = sign(image - target) * scale and the sum of
 // |image - target| (FP32 per thread, FP64 across warps) into loss_acc.
-template <int kBatch, bool kTma, int kPx>
-__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_raster_fwd(
+template <int kBatch, bool kTma, int kPx, int kT>
+__global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 2 ? (kT == 16 ? 10 : 2) : 1)) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
     uint32_t *queue, unsigned long long *evals_out, pk_device_status *status, const float *__restrict__ target,
     float *__restrict__ dimg, float scale, double *loss_acc) {
-  using G = Geo<kPx>;
+  using G = Geo<kPx, kT>;
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
   __shared__ uint32_t s_pid[kTma ? kBatch : 1];
@@ -40,7 +41,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
   const int tid = threadIdx.x, lane = tid & 31;
   const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy, bx, by;
-  pixel_of<kPx>(tid, ox, oy, bx, by);
+  pixel_of<kPx, kT>(tid, ox, oy, bx, by);
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
   bool timed_out = false;
@@ -74,11 +75,11 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kTileSide + ox, y0 = ty * kTileSide + oy;
+    const int x = tx * kT + ox, y0 = ty * kT + oy;
     const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
     // pixel-centre bounds of this warp's block
-    const float wx0 = (float)(tx * kTileSide + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
-    const float wy0 = (float)(ty * kTileSide + by) + 0.5f, wy1 = wy0 + 7.f;
+    const float wx0 = (float)(tx * kT + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
+    const float wy0 = (float)(ty * kT + by) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t), e = __ldg(ranges + 2 * (size_t)t + 1);
     float T[kPx], c0[kPx], c1[kPx], c2[kPx];
     uint32_t last[kPx];
@@ -228,7 +229,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
-template <int kBatch, bool kFwdTma>
+template <int kBatch, bool kFwdTma, int kT>
 pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
                      DevCounters *ctr, pk_device_status *status, const float *target, float *dimg,
@@ -236,14 +237,14 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma, kFwdPx>,
-                                                Geo<kFwdPx>::kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT>,
+                                                Geo<kFwdPx, kT>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > p->n_tiles) grid = p->n_tiles;
   if (grid < 1) grid = 1;
-  k_raster_fwd<kBatch, kFwdTma, kFwdPx><<<(int)grid, Geo<kFwdPx>::kThreads, 0, st>>>(
+  k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT><<<(int)grid, Geo<kFwdPx, kT>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
       &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status, target, dimg,
@@ -256,14 +257,18 @@ pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *
                         uint32_t *n_contrib, float *dimg, void *ws, cudaStream_t st) {
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
-  if (cudaMemsetAsync(&ctr->tile_queue[0], 0, sizeof(uint32_t), st) != cudaSuccess) return PK_ERR_CUDA;
-  if (cudaMemsetAsync(&status->evals_fwd, 0, sizeof(uint64_t), st) != cudaSuccess) return PK_ERR_CUDA;
-  // loss_acc, ssim_acc and ssim_lambda (0: the loss is L1 alone)
-  if (target && cudaMemsetAsync(&ctr->loss_acc, 0, 2 * sizeof(double) + sizeof(float), st) != cudaSuccess)
-    return PK_ERR_CUDA;
-#define PK_FWD(B, M)                                                                                          \
-  return launch_fwd<B, M>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, ctr, status, \
-                          target, dimg, st)
+  // the tile queue, the evaluation counter and, with a target, loss_acc,
+  // ssim_acc and ssim_lambda (0: the loss is L1 alone)
+  pk_status ze = zero_async({{&ctr->tile_queue[0], sizeof(uint32_t)},
+                             {&status->evals_fwd, sizeof(uint64_t)},
+                             {&ctr->loss_acc, target ? 2 * sizeof(double) + sizeof(float) : 0}},
+                            st);
+  if (ze != PK_OK) return ze;
+#define PK_FWD(B, M)                                                                                           \
+  return p->T == 32 ? launch_fwd<B, M, 32>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, \
+                                           ctr, status, target, dimg, st)                                        \
+                    : launch_fwd<B, M, 16>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, \
+                                           ctr, status, target, dimg, st)
   const bool tma = p->opts.stage_fwd == PK_STAGE_BULK;
   switch (p->opts.batch) {
     case 64:

@@ -132,8 +132,9 @@ class PerViewLoop:
     def for_scene(cls, scene, device="cuda", **kw):
         F, D, H, W = scene.atlas.shape
         tt = "f16" if str(scene.atlas.dtype) == "float16" else "f32"
+        kw.setdefault("tile", scene.tile)
         args = dict(levels=scene.levels, atlas_wh=(W, H), sh_degree=scene.sh_degree, frames=F,
-                    texel_type=tt, n_live=scene.n_live, tile=scene.tile, **kw)
+                    texel_type=tt, n_live=scene.n_live, **kw)
         return cls(args, scene.views, device)
 
     def __init__(self, scene_like_plan_args: dict, views, device="cuda"):

@@ -124,10 +124,10 @@ def _synthetic_records(views, N, seed):
     return rec
 
 
-def _records_plan(views, N, bin_mode="ellipse"):
+def _records_plan(views, N, bin_mode="ellipse", tile=16):
     pk = _pk()
     side = int(math.ceil(math.sqrt(N)))
-    return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, bin_mode=bin_mode)
+    return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, bin_mode=bin_mode, tile=tile)
 
 
 def _records_setup(seed, N=700):
@@ -137,12 +137,13 @@ def _records_setup(seed, N=700):
     return views, rec
 
 
-@pytest.mark.parametrize("seed,mode", [(1, "ellipse"), (2, "ellipse"), (3, "rect"), (4, "rect")])
-def test_bin_and_sort_bit_exact(orc, seed, mode):
+@pytest.mark.parametrize("seed,mode,tile", [(1, "ellipse", 16), (2, "ellipse", 16), (3, "rect", 16), (4, "rect", 16),
+                                            (1, "ellipse", 32), (3, "rect", 32)])
+def test_bin_and_sort_bit_exact(orc, seed, mode, tile):
     pk = _pk()
     views, rec = _records_setup(seed)
     V, N = rec.shape[:2]
-    plan = _records_plan(views, N, mode)
+    plan = _records_plan(views, N, mode, tile)
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
@@ -152,8 +153,8 @@ def test_bin_and_sort_bit_exact(orc, seed, mode):
     st = pk.read_status(plan, ws)
     va = orc.views_array(views)
     r = rec.reshape(V * N, 12)
-    ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, 16, r[:, 2], r[:, 3], r[:, 4],
-                                          mode={"ellipse": orc.BIN_ELLIPSE, "rect": orc.BIN_RECT}[mode])
+    ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, tile, r[:, 2], r[:, 3],
+                                          r[:, 4], mode={"ellipse": orc.BIN_ELLIPSE, "rect": orc.BIN_RECT}[mode])
     assert st["dups"] == len(ref_vals) and st["flags"] == 0
     assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.u32(ranges).reshape(-1, 2), ref_vals, ref_ranges)
 
@@ -199,12 +200,12 @@ def test_bin_and_sort_capacity_overflow(orc):
 # a4 / a5 on identical FP32 records
 # ---------------------------------------------------------------------------
 
-def _records_forward(seed, dimg_seed=None):
+def _records_forward(seed, dimg_seed=None, tile=16):
     pk = _pk()
     views, rec = _records_setup(seed, N=500)
     V, N = rec.shape[:2]
     rec[..., 5] = np.minimum(rec[..., 5], 0.999)
-    plan = _records_plan(views, N)
+    plan = _records_plan(views, N, tile=tile)
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
@@ -223,6 +224,21 @@ def _records_forward(seed, dimg_seed=None):
         out.update(w=w, g2=g2)
     torch.cuda.synchronize()
     return out
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_tile_side_leaves_images_unchanged(seed):
+    """32 px tiles bin and composite the same splats per pixel in the same
+    order (the extra splats of a larger tile fail the alpha test): images
+    and transmittance bit for bit equal to 16 px tiles, the backward's
+    gradients equal up to the order of their atomic sums."""
+    a = _records_forward(seed, dimg_seed=seed + 3)
+    b = _records_forward(seed, dimg_seed=seed + 3, tile=32)
+    assert b["plan"].n_tiles < a["plan"].n_tiles
+    assert torch.equal(a["img"].view(torch.int32), b["img"].view(torch.int32))
+    assert torch.equal(a["T"].view(torch.int32), b["T"].view(torch.int32))
+    ga, gb = a["g2"].cpu().numpy().astype(np.float64), b["g2"].cpu().numpy().astype(np.float64)
+    assert np.abs(ga - gb).max() <= 1e-5 * max(1e-12, np.abs(ga).max())
 
 
 @pytest.mark.parametrize("seed", [5, 6])
@@ -253,14 +269,14 @@ def test_rasterize_fwd_l1_matches_separate_calls(orc, seed):
     assert abs(st["loss"] - want) <= 1e-6 * abs(want)
 
 
-@pytest.mark.parametrize("seed", [5, 6])
-def test_rasterize_fwd_on_identical_records(orc, seed):
-    o = _records_forward(seed)
+@pytest.mark.parametrize("seed,tile", [(5, 16), (6, 16), (5, 32)])
+def test_rasterize_fwd_on_identical_records(orc, seed, tile):
+    o = _records_forward(seed, tile=tile)
     rec64 = o["rec"].astype(np.float64)
     rec64[..., 11] = 0
     va = orc.views_array(o["views"])
-    vals, ranges = orc.bin_sort(rec64, va, 16)
-    ref = orc.render(rec64, va, 16, vals, ranges, m_tol=1e-5)
+    vals, ranges = orc.bin_sort(rec64, va, tile)
+    ref = orc.render(rec64, va, tile, vals, ranges, m_tol=1e-5)
     ref["view_pixels"] = [v.width * v.height for v in o["views"]]
     # identical FP32 depths on both sides: the depth order is the same (the sort is bit-exact), so
     # near-equal depths are not borderline here
@@ -272,14 +288,14 @@ def test_rasterize_fwd_on_identical_records(orc, seed):
     assert st["evals_fwd"] > 0
 
 
-@pytest.mark.parametrize("seed", [7, 8])
-def test_rasterize_bwd_on_identical_records(orc, seed):
-    o = _records_forward(seed, dimg_seed=seed + 100)
+@pytest.mark.parametrize("seed,tile", [(7, 16), (8, 16), (7, 32)])
+def test_rasterize_bwd_on_identical_records(orc, seed, tile):
+    o = _records_forward(seed, dimg_seed=seed + 100, tile=tile)
     rec64 = o["rec"].astype(np.float64)
     rec64[..., 11] = 0
     va = orc.views_array(o["views"])
-    vals, ranges = orc.bin_sort(rec64, va, 16)
-    ref = orc.render_bwd(rec64, va, 16, vals, ranges, o["w"].astype(np.float64))
+    vals, ranges = orc.bin_sort(rec64, va, tile)
+    ref = orc.render_bwd(rec64, va, tile, vals, ranges, o["w"].astype(np.float64))
     got = o["g2"].view(-1, 12).cpu().numpy().astype(np.float64)[:, :9]
     ref = ref.reshape(-1, 9)
     for name, sl in {"mean": slice(0, 2), "conic": slice(2, 5), "opacity": slice(5, 6),

@@ -592,3 +592,34 @@ def test_render_bwd_matches_differences_in_record_space(orc):
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
         n_ok += 1
     assert n_ok >= 30
+
+
+def test_images_do_not_depend_on_tile_side(orc):
+    """A larger tile only adds splats whose footprint misses the pixel (they
+    fail the alpha test), so the oracle's images and transmittance for 16
+    and 32 px tiles are identical, while the lists differ."""
+    rng = np.random.default_rng(21)
+    V, N = 2, 150
+    va = np.zeros((V, 20))
+    for v, (w, h) in enumerate([(70, 45), (33, 50)]):
+        va[v, 16], va[v, 17] = w, h
+    rec = np.zeros((V, N, 12))
+    for v in range(V):
+        w, h = va[v, 16], va[v, 17]
+        rec[v, :, 0] = rng.uniform(-5, w + 5, N)
+        rec[v, :, 1] = rng.uniform(-5, h + 5, N)
+        L = rng.normal(0, 1, (N, 2, 2)) * np.exp(rng.normal(0.8, 0.7, (N, 1, 1)))
+        S = L @ L.transpose(0, 2, 1) + 0.3 * np.eye(2)
+        Q = np.linalg.inv(S)
+        rec[v, :, 2], rec[v, :, 3], rec[v, :, 4] = Q[:, 0, 0], Q[:, 0, 1], Q[:, 1, 1]
+        rec[v, :, 5] = rng.uniform(0.05, 0.99, N)
+        rec[v, :, 6] = rng.uniform(1, 5, N)
+        rec[v, :, 7] = np.ceil(3 * np.sqrt(np.linalg.eigvalsh(S)[:, 1]))
+        rec[v, :, 8:11] = rng.uniform(0, 1, (N, 3))
+    out = {}
+    for tile in (16, 32):
+        vals, ranges = orc.bin_sort(rec, va, tile)
+        out[tile] = (len(vals), orc.render(rec, va, tile, vals, ranges))
+    assert out[16][0] != out[32][0]
+    assert np.array_equal(out[16][1]["img"], out[32][1]["img"])
+    assert np.array_equal(out[16][1]["T"], out[32][1]["T"])
