@@ -364,7 +364,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--views", type=int, default=0, help="use only the first N cameras (profiling cases)")
-    ap.add_argument("--tile", type=int, default=16, choices=[16, 32], help="tile side of the binning")
+    ap.add_argument("--tile", type=int, default=32, choices=[16, 32], help="tile side of the binning")
     ap.add_argument("--ref-window", type=int, default=192)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-view", action="store_true")
@@ -553,23 +553,36 @@ def main():
                 u_ev[k][1].record(copy_stream)
                 ev_in[slot].record(copy_stream)
 
+        # warm-up: the second graph's first replay uploads it to the device
+        with torch.cuda.stream(stream):
+            for gr in graphs:
+                gr.replay()
         torch.cuda.synchronize(dev)
         for e_ in ev_done:
             e_.record(stream)
         t0 = time.perf_counter()
         upload(0, 0)
+        host = {"replay": [], "upload": [], "status": []}
         for k in range(ke):
             slot = k % 2
+            h0 = time.perf_counter()
             with torch.cuda.stream(stream):
                 stream.wait_event(ev_in[slot])
                 g_ev[k][0].record(stream)
                 graphs[slot].replay()
                 g_ev[k][1].record(stream)
                 ev_done[slot].record(stream)
+            h1 = time.perf_counter()
             if k + 1 < ke:
                 upload(1 - slot, k + 1)
+            h2 = time.perf_counter()
             s = r.status(stream)          # device -> host read of this step's loss (waits for the step)
+            h3 = time.perf_counter()
+            host["replay"].append((h1 - h0) * 1e3)
+            host["upload"].append((h2 - h1) * 1e3)
+            host["status"].append((h3 - h2) * 1e3)
         torch.cuda.synchronize(dev)
+        gap_ms = statistics.median(g_ev[k][1].elapsed_time(g_ev[k + 1][0]) for k in range(ke - 1))
         dt = (time.perf_counter() - t0) / ke
         graph_ms = statistics.median(a.elapsed_time(b) for a, b in g_ev)
         upload_ms = statistics.median(a.elapsed_time(b) for a, b in u_ev)
@@ -580,7 +593,8 @@ def main():
                       "d2h_bytes_per_step": int(ctypes_sizeof_status()), "loss": s["loss"],
                       "pipeline": "inputs double-buffered; next step's copies overlap this step's compute",
                       "graph_ms_per_step": graph_ms, "upload_ms_per_step": upload_ms,
-                      "upload_start_after_graph_start_ms": upload_lag_ms, "steps": ke}
+                      "upload_start_after_graph_start_ms": upload_lag_ms, "device_gap_between_graphs_ms": gap_ms,
+                      "host_ms": {n: statistics.median(v) for n, v in host.items()}, "steps": ke}
         del bufs, g2
 
     if not args.profile and not args.no_per_view and rank == 0:

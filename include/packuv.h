@@ -114,7 +114,8 @@ typedef enum pk_bin_mode { PK_BIN_RECT = 0, PK_BIN_ELLIPSE = 1 } pk_bin_mode;
 typedef enum pk_stage_mode { PK_STAGE_LOADS = 0, PK_STAGE_BULK = 1 } pk_stage_mode;
 
 typedef struct pk_options {
-  int32_t tile;                    /* tile side: 16 (0 = 16) or 32; images do not depend on it */
+  int32_t tile;                    /* side of the binning tiles: 32 (0 = 32) or 16; images do not
+                                      depend on it, 32 halves the entries to sort at C3 */
   float znear;                     /* cull z <= znear; default 0.01 */
   float bg[3];                     /* background colour; default 0 */
   uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
@@ -292,8 +293,11 @@ pk_status pk_bin_and_sort_noalloc(const pk_plan *plan, const float *records, uin
  * T_final * bg.  One persistent launch over the tiles of every view.
  * image:     out [3 * P] float32 (planar per view).
  * T_final:   out [P] float32 transmittance after the last blended splat.
- * n_contrib: out [P] uint32, 1-based position within the tile's list of
- *            the last blended entry (0 = none). */
+ * n_contrib: out [P] uint32, 1-based position within the list of the
+ *            pixel's binning tile (pk_options.tile) of the last blended
+ *            entry (0 = none).
+ * Each CTA composites a 16 x 16 block: a 32 px tile's list is walked by the
+ * four CTAs of its quadrants. */
 pk_status pk_rasterize_fwd(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
                            const uint32_t *tile_ranges, float *image, float *T_final,
                            uint32_t *n_contrib, void *workspace, pk_stream_t stream);

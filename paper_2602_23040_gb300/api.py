@@ -72,7 +72,7 @@ class Plan:
     """Host-side plan of one launch: atlas descriptor, views and options."""
 
     def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
-                 sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 16,
+                 sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 32,
                  znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse",
                  batch: int = 128, stage_fwd: str = "loads", stage_bwd: str = "loads", batch_bwd: int = None):
         lib = N.load()

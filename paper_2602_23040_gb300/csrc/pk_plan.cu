@@ -166,7 +166,7 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   }
   if (n_live > (int64_t)d.atlas_w * d.atlas_h) return PK_ERR_ARG;
   pk_options o;
-  o.tile = 16;
+  o.tile = 32;
   o.znear = 0.01f;
   o.bg[0] = o.bg[1] = o.bg[2] = 0.0f;
   o.max_dups = 0;
@@ -184,7 +184,7 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   if ((o.stage_fwd != PK_STAGE_LOADS && o.stage_fwd != PK_STAGE_BULK) ||
       (o.stage_bwd != PK_STAGE_LOADS && o.stage_bwd != PK_STAGE_BULK))
     return PK_ERR_ARG;
-  if (o.tile == 0) o.tile = 16;
+  if (o.tile == 0) o.tile = 32;
   if (o.tile != 16 && o.tile != 32) return PK_ERR_UNSUPPORTED;
   if (!(o.znear > 0.0f) || !isfinite(o.znear)) return PK_ERR_ARG;
   for (int c = 0; c < 3; ++c)

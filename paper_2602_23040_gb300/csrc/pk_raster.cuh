@@ -9,27 +9,26 @@
 
 namespace pk {
 
-constexpr int kTileSide = 16;   // the default tile side (pk_options.tile: 16 or 32)
+constexpr int kTileSide = 16;   // side of the pixel block of one compositing CTA
 // Splats staged per batch: a template parameter of the compositing
 // kernels (64, 128 or 256; pk_options.batch, chosen by pk_autotune).
 constexpr int kBatchMax = 256;
 
-// One CTA per kT x kT tile (16 or 32) with kPx pixels per thread (2 or 4).
-// A warp covers a kBW x 8 block (8 x 8 for 2 pixels, 16 x 8 for 4), the
-// blocks in row-major order over the tile, and skips as a whole every
-// splat that misses its block; a lane holds one column of it, kPx pixels
-// kRowStep rows apart.  More pixels per lane spread the per-splat work of
-// a warp (shared-memory loads, the block test, the gradient reduction)
-// over more pixels, at the price of a coarser block test; a larger tile
-// shares each staged splat among more warps and has fewer entries to sort.
-template <int kPx, int kT = kTileSide>
+// One CTA per 16 x 16 pixel block with kPx pixels per thread (2 or 4).  A
+// warp covers a kBW x 8 block (8 x 8 for 2 pixels, 16 x 8 for 4) and skips
+// as a whole every splat that misses its block; a lane holds one column of
+// it, kPx pixels kRowStep rows apart.  More pixels per lane spread the
+// per-splat work of a warp (shared-memory loads, the block test, the
+// gradient reduction) over more pixels, at the price of a coarser block
+// test.
+template <int kPx>
 struct Geo {
-  static_assert((kPx == 2 || kPx == 4) && (kT == 16 || kT == 32), "2 or 4 pixels, 16 or 32 px tiles");
-  static constexpr int kThreads = kT * kT / kPx;
+  static_assert(kPx == 2 || kPx == 4, "2 or 4 pixels per thread");
+  static constexpr int kThreads = kTileSide * kTileSide / kPx;   // 128 or 64
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kBW = kPx == 2 ? 8 : 16;
   static constexpr int kRowStep = 32 / kBW;                       // 4 or 2
-  static constexpr int kBlocksX = kT / kBW;                       // warp blocks per tile row
+  static constexpr int kBlocksX = kTileSide / kBW;                // warp blocks per row
 };
 
 // Pixels per thread: the forward keeps 2 (its per-splat work is small, and
@@ -38,9 +37,9 @@ struct Geo {
 constexpr int kFwdPx = 2, kBwdPx = 4;
 
 // Lane's column ox and first row oy in the tile; (bx, by) = its warp block's corner.
-template <int kPx, int kT>
+template <int kPx>
 __device__ __forceinline__ void pixel_of(int tid, int &ox, int &oy, int &bx, int &by) {
-  using G = Geo<kPx, kT>;
+  using G = Geo<kPx>;
   const int w = tid >> 5, l = tid & 31;
   bx = (w % G::kBlocksX) * G::kBW;
   by = (w / G::kBlocksX) * 8;

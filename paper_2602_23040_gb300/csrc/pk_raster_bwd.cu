@@ -114,16 +114,18 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // memory by bulk copies (one 48-byte copy per splat, completed on an
 // mbarrier) while the current batch is processed.  kPx: pixels per thread.
 // At 4 pixels per thread the kernel is held to 64 registers (no spills):
-// 16 resident CTAs per SM instead of 10 hide more of its latency (4 of 256
-// threads with 32 px tiles).
+// 16 resident CTAs per SM instead of 10 hide more of its latency.
+// kT: side of the tiles the lists were binned for; each CTA takes a 16 x 16
+// quadrant of one, as in the forward.
 template <int kBatch, bool kTma, int kPx, int kT>
-__global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 4 ? (kT == 16 ? 16 : 4) : 1)) void k_raster_bwd(
+__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-    const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
+    const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
     const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out,
     pk_device_status *status) {
-  using G = Geo<kPx, kT>;
+  using G = Geo<kPx>;
+  constexpr uint32_t kQuads = (kT / kTileSide) * (kT / kTileSide);   // CTAs per list tile
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
   __shared__ uint32_t s_pid[kTma ? kBatch : 1];
@@ -134,7 +136,7 @@ __global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 4 ? (kT == 16 ? 16 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy, bx, by;
-  pixel_of<kPx, kT>(tid, ox, oy, bx, by);
+  pixel_of<kPx>(tid, ox, oy, bx, by);
   const int my_idx = reduce_scatter9_index(lane);
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
@@ -156,22 +158,30 @@ __global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 4 ? (kT == 16 ? 16 
     }
   };
   for (;;) {
+    // work item: (list tile t, 16 x 16 quadrant q of it)
     if (tid == 0) {
-      const uint32_t t = atomicAdd(queue, 1u);
-      s_tile = t;
-      s_view = t < n_tiles ? view_of_tile(toff, V, t) : -1;
+      const uint32_t w = atomicAdd(queue, 1u);
+      s_tile = w;
+      s_view = w < n_items ? view_of_tile(toff, V, w / kQuads) : -1;
     }
     __syncthreads();
-    const uint32_t t = s_tile;
-    if (t >= n_tiles) break;
+    const uint32_t w = s_tile;
+    if (w >= n_items) break;
+    const uint32_t t = w / kQuads, q = w - t * kQuads;
     const DevView &view = views[s_view];
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kT + ox, y0 = ty * kT + oy;
+    const int X0 = tx * kT + (int)(q % (kT / kTileSide)) * kTileSide;
+    const int Y0 = ty * kT + (int)(q / (kT / kTileSide)) * kTileSide;
+    if (X0 >= W || Y0 >= H) {   // a quadrant past the view's edge
+      __syncthreads();
+      continue;
+    }
+    const int x = X0 + ox, y0 = Y0 + oy;
     const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
-    const float wx0 = (float)(tx * kT + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
-    const float wy0 = (float)(ty * kT + by) + 0.5f, wy1 = wy0 + 7.f;
+    const float wx0 = (float)(X0 + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
+    const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t);
     const size_t plane = (size_t)W * H;
     float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx];
@@ -297,15 +307,16 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT>,
-                                                Geo<kBwdPx, kT>::kThreads, 0);
+                                                Geo<kBwdPx>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
+  const int64_t items = p->n_tiles * (kT / kTileSide) * (kT / kTileSide);
   int64_t grid = (int64_t)sms * per_sm;
-  if (grid > p->n_tiles) grid = p->n_tiles;
+  if (grid > items) grid = items;
   if (grid < 1) grid = 1;
-  k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT><<<(int)grid, Geo<kBwdPx, kT>::kThreads, 0, st>>>(
+  k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT><<<(int)grid, Geo<kBwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
-      (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
+      (uint32_t)items, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
       &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd), status);
   return check_launch();
 }

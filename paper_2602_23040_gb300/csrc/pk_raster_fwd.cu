@@ -18,20 +18,24 @@ namespace {
 // bulk copies (one 48-byte copy per splat, completed on an mbarrier) while
 // the current batch is composited; the derived per-splat values are then
 // computed from shared memory.  kPx: pixels per thread (Geo).
-// At 2 pixels per thread and 16 px tiles the kernel is held to 48
-// registers (a few spilled) for 10 resident CTAs per SM instead of 9; with
-// 32 px tiles (512 threads) to 64 for 2 CTAs.
+// At 2 pixels per thread the kernel is held to 48 registers (a few
+// spilled) for 10 resident CTAs per SM instead of 9.
+// kT: side of the tiles the lists were binned for (16 or 32); each CTA
+// composites a 16 x 16 quadrant of one, walking the whole list of its tile
+// (its warps' block tests skip what misses them), so a pixel still stops
+// as soon as its own 16 x 16 block is done.
 // With a target (not null) the epilogue also takes the L1 term of the
 // objective: dL/dimage = sign(image - target) * scale and the sum of
 // |image - target| (FP32 per thread, FP64 across warps) into loss_acc.
 template <int kBatch, bool kTma, int kPx, int kT>
-__global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 2 ? (kT == 16 ? 10 : 2) : 1)) void k_raster_fwd(
+__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
-    const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_tiles, float bg0,
+    const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
     uint32_t *queue, unsigned long long *evals_out, pk_device_status *status, const float *__restrict__ target,
     float *__restrict__ dimg, float scale, double *loss_acc) {
-  using G = Geo<kPx, kT>;
+  using G = Geo<kPx>;
+  constexpr uint32_t kQuads = (kT / kTileSide) * (kT / kTileSide);   // CTAs per list tile
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
   __shared__ __align__(16) float4 s_raw[kTma ? 3 * kBatch : 1];
   __shared__ uint32_t s_pid[kTma ? kBatch : 1];
@@ -41,7 +45,7 @@ __global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 2 ? (kT == 16 ? 10 
   const int tid = threadIdx.x, lane = tid & 31;
   const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy, bx, by;
-  pixel_of<kPx, kT>(tid, ox, oy, bx, by);
+  pixel_of<kPx>(tid, ox, oy, bx, by);
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
   bool timed_out = false;
@@ -63,23 +67,31 @@ __global__ __launch_bounds__(Geo<kPx, kT>::kThreads, (kPx == 2 ? (kT == 16 ? 10 
     }
   };
   for (;;) {
+    // work item: (list tile t, 16 x 16 quadrant q of it)
     if (tid == 0) {
-      const uint32_t t = atomicAdd(queue, 1u);
-      s_tile = t;
-      s_view = t < n_tiles ? view_of_tile(toff, V, t) : -1;
+      const uint32_t w = atomicAdd(queue, 1u);
+      s_tile = w;
+      s_view = w < n_items ? view_of_tile(toff, V, w / kQuads) : -1;
     }
     __syncthreads();
-    const uint32_t t = s_tile;
-    if (t >= n_tiles) break;
+    const uint32_t w = s_tile;
+    if (w >= n_items) break;
+    const uint32_t t = w / kQuads, q = w - t * kQuads;
     const DevView &view = views[s_view];
     const int W = view.width, H = view.height;
     const uint32_t local = t - (uint32_t)view.tile_off;
     const int ty = (int)(local / (uint32_t)view.tiles_x), tx = (int)(local - (uint32_t)ty * view.tiles_x);
-    const int x = tx * kT + ox, y0 = ty * kT + oy;
+    const int X0 = tx * kT + (int)(q % (kT / kTileSide)) * kTileSide;
+    const int Y0 = ty * kT + (int)(q / (kT / kTileSide)) * kTileSide;
+    if (X0 >= W || Y0 >= H) {   // a quadrant past the view's edge
+      __syncthreads();
+      continue;
+    }
+    const int x = X0 + ox, y0 = Y0 + oy;
     const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
     // pixel-centre bounds of this warp's block
-    const float wx0 = (float)(tx * kT + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
-    const float wy0 = (float)(ty * kT + by) + 0.5f, wy1 = wy0 + 7.f;
+    const float wx0 = (float)(X0 + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
+    const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t), e = __ldg(ranges + 2 * (size_t)t + 1);
     float T[kPx], c0[kPx], c1[kPx], c2[kPx];
     uint32_t last[kPx];
@@ -238,15 +250,16 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT>,
-                                                Geo<kFwdPx, kT>::kThreads, 0);
+                                                Geo<kFwdPx>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
+  const int64_t items = p->n_tiles * (kT / kTileSide) * (kT / kTileSide);
   int64_t grid = (int64_t)sms * per_sm;
-  if (grid > p->n_tiles) grid = p->n_tiles;
+  if (grid > items) grid = items;
   if (grid < 1) grid = 1;
-  k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT><<<(int)grid, Geo<kFwdPx, kT>::kThreads, 0, st>>>(
+  k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT><<<(int)grid, Geo<kFwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
-      (uint32_t)p->n_tiles, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
+      (uint32_t)items, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
       &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status, target, dimg,
       (float)(1.0 / (3.0 * (double)std::max<int64_t>(1, p->P))), &ctr->loss_acc);
   return check_launch();

@@ -62,7 +62,7 @@ class Scene:
     sh_degree: int
     views: List[View]
     n_live: int                        # live texels per frame
-    tile: int = 16
+    tile: int = 32                     # tile side of the binning (16 or 32; images do not depend on it)
 
     @property
     def frames(self) -> int:
@@ -183,7 +183,7 @@ def make_scene(levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple
                occupancy, views: List[View], sh_degree: int = 3, frames: int = 1,
                texel_dtype=np.float32, means: str = "clusters", seed: int = BASE_SEED,
                dynamic_frac: float = 0.0, flow_amp: float = 0.05, frame_start: int = 0,
-               name: str = "custom", tile: int = 16,
+               name: str = "custom", tile: int = 32,
                log_scale: Tuple[float, float] = (-4.0, 0.5), mean_box: float = 1.0) -> Scene:
     """Generate one scene.
 

@@ -68,9 +68,12 @@ def test_plan_sizes_and_workspace(lib):
     p = api.Plan(**_plan_args())
     s = p.sizes
     assert (s.n_live, s.n_gauss, s.channels, s.n_views, s.n_pairs) == (500, 500, 59, 1, 500)
-    assert s.n_pixels == 64 * 48 and s.n_tiles == 4 * 3
+    assert s.n_pixels == 64 * 48 and s.n_tiles == 2 * 2           # 32 px tiles by default
     assert s.max_dups == max(1024, 32 * 500) and s.workspace_bytes > 0
     p.close()
+    p16 = api.Plan(**_plan_args(tile=16))
+    assert p16.sizes.n_tiles == 4 * 3
+    p16.close()
 
 
 @pytest.mark.parametrize("over,code", [
