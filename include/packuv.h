@@ -148,6 +148,7 @@ typedef struct pk_sizes {
 #define PK_DEV_CAPACITY 1u       /* bin_and_sort: entries > max_dups, emitted none */
 #define PK_DEV_LIVE_MISMATCH 2u  /* gather: occupancy holds != N live texels */
 #define PK_DEV_TIMEOUT 4u        /* a bounded device wait gave up */
+#define PK_DEV_BOUNDS 8u         /* a data-dependent index failed its check; the access was skipped */
 typedef struct pk_device_status {
   uint32_t flags;
   uint32_t live_seen;              /* live texels counted by the last gather (saturating) */

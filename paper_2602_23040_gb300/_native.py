@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "invalid descriptor", 3: "cap
 DEV_CAPACITY = 1
 DEV_LIVE_MISMATCH = 2
 DEV_TIMEOUT = 4
+DEV_BOUNDS = 8
 BIN_RECT, BIN_ELLIPSE = 0, 1
 
 

@@ -734,6 +734,10 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
       const uint32_t k = bk[i];
       const uint32_t d = (k >> shift) & mask;
       const uint32_t o = s_gbase[d] + (i - s_start[d]);
+      if (o >= n) {   // a histogram out of step with the keys: never write past the items
+        atomicOr(&status->flags, PK_DEV_BOUNDS);
+        continue;
+      }
       kout[o] = k;
       vout[o] = bv[i];
     }
@@ -755,9 +759,11 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
                                                    const uint32_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
                                                    const DevCounters *ctr, const DevView *__restrict__ views,
                                                    int64_t N, int T, int mode, int local_bits,
-                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                                                   pk_device_status *status) {
   __shared__ WarpSplat s_ws[kWarps][32];
-  if (ctr->dups == 0) return;
+  const uint32_t dups = ctr->dups;
+  if (dups == 0) return;
   const uint64_t n = ctr->n_valid;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
@@ -832,8 +838,12 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const uint32_t bal = __ballot_sync(0xffffffffu, take);
       if (take) {
         const uint32_t at = off0 + written + __popc(bal & lt);
-        keys[at] = (uint32_t)r1.y + ly * (uint32_t)r1.z + lx;
-        vals[at] = o_p;
+        if (at < dups) {
+          keys[at] = (uint32_t)r1.y + ly * (uint32_t)r1.z + lx;
+          vals[at] = o_p;
+        } else {   // more receiving tiles than counted: never write past the entries
+          atomicOr(&status->flags, PK_DEV_BOUNDS);
+        }
       }
       written += __popc(bal);
     }
@@ -847,7 +857,8 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
 // view's tile_off is added to the local id.
 __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, int local_bits,
                                                      const uint32_t *__restrict__ toff, const DevCounters *ctr,
-                                                     uint32_t *__restrict__ ranges) {
+                                                     uint32_t *__restrict__ ranges, int V, uint32_t n_tiles,
+                                                     pk_device_status *status) {
   const uint32_t n = ctr->dups;
   const uint32_t nq = (n + 3) / 4;
   const uint32_t lmask = (1u << local_bits) - 1u;
@@ -863,10 +874,21 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
       for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < n ? __ldg(keys + i0 + j) : 0xffffffffu;
     }
     k[5] = i0 + 4 < n ? __ldg(keys + i0 + 4) : 0xffffffffu;
+    bool bad = false;
     if (local_bits) {
 #pragma unroll
       for (int j = 0; j < 6; ++j)
-        if (k[j] != 0xffffffffu) k[j] = __ldg(toff + (k[j] >> local_bits)) + (k[j] & lmask);
+        if (k[j] != 0xffffffffu) {
+          const uint32_t v = k[j] >> local_bits;
+          bad |= v >= (uint32_t)V;
+          k[j] = v < (uint32_t)V ? __ldg(toff + v) + (k[j] & lmask) : 0xffffffffu;
+        }
+    }
+#pragma unroll
+    for (int j = 1; j < 5; ++j) bad |= i0 + j - 1 < n && k[j] >= n_tiles;
+    if (bad) {   // a key that names no tile: record it, write nothing
+      atomicOr(&status->flags, PK_DEV_BOUNDS);
+      continue;
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1098,7 +1120,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
   k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->T,
-                                                      p->opts.bin_mode, seg ? key_bits : 0, kbuf[0], vbuf[0]);
+                                                      p->opts.bin_mode, seg ? key_bits : 0, kbuf[0], vbuf[0],
+                                                      status);
   // Digits from the top down: each tile's entries still end up contiguous
   // and in emission order, and the first pass, whose input holds each
   // splat's tiles side by side, ranks on tile-row bands that the 32 entries
@@ -1114,7 +1137,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
       return e;
   }
   k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], seg ? key_bits : 0,
-                                                        at<uint32_t>(ws, L.toff), ctr, tile_ranges);
+                                                        at<uint32_t>(ws, L.toff), ctr, tile_ranges, p->V,
+                                                        (uint32_t)p->n_tiles, status);
   return check_launch();
 }
 
