@@ -553,10 +553,15 @@ def main():
                 u_ev[k][1].record(copy_stream)
                 ev_in[slot].record(copy_stream)
 
-        # warm-up: the second graph's first replay uploads it to the device
-        with torch.cuda.stream(stream):
-            for gr in graphs:
-                gr.replay()
+        # warm-up: two untimed steps of the same pattern (each graph's first
+        # replay uploads it to the device; the first copies touch the pinned pages)
+        for k in range(2):
+            upload(k % 2, 0)
+            with torch.cuda.stream(stream):
+                stream.wait_event(ev_in[k % 2])
+                graphs[k % 2].replay()
+                ev_done[k % 2].record(stream)
+            r.status(stream)
         torch.cuda.synchronize(dev)
         for e_ in ev_done:
             e_.record(stream)
