@@ -174,7 +174,8 @@ typedef struct pk_device_status {
 pk_status pk_atlas_layout(int32_t S, int32_t K, pk_atlas_desc *desc);
 
 /* Validate the descriptor (levels inside the atlas, not overlapping), the
- * views (positive sizes, frame < F, finite parameters) and n_live, and
+ * views (positive sizes, frame < F, finite parameters) and n_live (the
+ * pairs V * n_live must stay below 2^32: pair indices are 32-bit), and
  * build the host-side plan.  Copies everything it needs.  Allocates no
  * device memory.  On error *out is NULL. */
 pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *views, int32_t n_views,

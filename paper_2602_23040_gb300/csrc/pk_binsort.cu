@@ -130,8 +130,9 @@ __device__ __forceinline__ void shrink_to_footprint(float mx, float my, float a,
   if (!(a > 0.f) || !(c > 0.f) || !(det > 0.f) || !isfinite(det)) return;
   const float ex = 3.f * sqrtf(c / det) * 1.01f + 1.f, ey = 3.f * sqrtf(a / det) * 1.01f + 1.f;
   // tile tx holds pixel centres [tx T + 0.5, tx T + T - 0.5]
-  const float fx0 = floorf((mx - ex - 0.5f) / (float)T), fx1 = floorf((mx + ex - 0.5f) / (float)T);
-  const float fy0 = floorf((my - ey - 0.5f) / (float)T), fy1 = floorf((my + ey - 0.5f) / (float)T);
+  const float rT = 1.f / (float)T;   // T is a power of two: x * rT == x / T exactly
+  const float fx0 = floorf((mx - ex - 0.5f) * rT), fx1 = floorf((mx + ex - 0.5f) * rT);
+  const float fy0 = floorf((my - ey - 0.5f) * rT), fy1 = floorf((my + ey - 0.5f) * rT);
   if (fx0 > (float)tx0) tx0 = (int)fminf(fx0, (float)tx1);
   if (fx1 < (float)tx1) tx1 = (int)fmaxf(fx1, (float)tx0);
   if (fy0 > (float)ty0) ty0 = (int)fminf(fy0, (float)ty1);
@@ -244,7 +245,7 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
       const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec));
       const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + p * kRec) + 1);
       zbits[p] = __float_as_uint(b.z);   // the depth key, for the compaction
-      const DevView &v = views[p / N];
+      const DevView &v = views[(uint32_t)p / (uint32_t)N];   // pairs < 2^32 (checked by the plan)
       int x0, y0, x1, y1;
       if (bin_rect(a.x, a.y, b.w, v.width, v.height, T, x0, y0, x1, y1)) {
         if (mode != PK_BIN_RECT) shrink_to_footprint(a.x, a.y, a.z, a.w, b.x, T, x0, y0, x1, y1);
@@ -787,7 +788,8 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const int wt = (int)(info.w & 0xffffu), ht = (int)(info.w >> 16);
       ncand = (uint32_t)(wt * ht);
       if (ncand) {
-        const DevView &v = views[p / N];
+        const uint32_t vi = p / (uint32_t)N;
+        const DevView &v = views[vi];
         if (mode != PK_BIN_RECT && ncand > kMaskBits) {
           const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec));
           const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec) + 1);
@@ -798,7 +800,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
         ws.r0 = make_int4(x0, y0, wt, v.width);
         // key: the global tile id, or (segmented sort) the view above the
         // local tile id, whose low local_bits bits alone are sorted
-        const uint32_t kbase = local_bits ? ((uint32_t)(p / N) << local_bits) : (uint32_t)v.tile_off;
+        const uint32_t kbase = local_bits ? (vi << local_bits) : (uint32_t)v.tile_off;
         ws.r1 = make_int4(v.height, (int)(kbase + (uint32_t)y0 * v.tiles_x + (uint32_t)x0), v.tiles_x, (int)ncand);
         msk = ((uint64_t)info.y << 32) | info.x;
       }

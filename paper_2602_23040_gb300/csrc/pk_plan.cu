@@ -201,6 +201,7 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   }
   if (tiles >= (int64_t(1) << 31) || 3 * P >= (int64_t(1) << 40)) return PK_ERR_ARG;
   uint64_t pairs = (uint64_t)(V * N);
+  if (pairs > 0xFFFFFFFFull) return PK_ERR_ARG;   // pair indices are 32-bit
   uint64_t maxd = o.max_dups ? o.max_dups : 32 * pairs;
   if (maxd < 1024) maxd = 1024;
   if (maxd > 0xFFFFF000ull) maxd = 0xFFFFF000ull;
