@@ -341,14 +341,21 @@ __global__ __launch_bounds__(kThreads) void k_scan_reduce(Src src, const uint32_
   if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the block sums (one block).  mode 0: compaction (total
+// Exclusive scan of the block sums (one block of 1024 threads, up to 4096
+// sums: kScanBlocks).  mode 0: compaction (total
 // = valid pairs); mode 1: emission offsets (total = entries, checked
 // against the capacity).
 __global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, int nb, int mode,
                                                    uint64_t max_dups, DevCounters *ctr, pk_device_status *status) {
   __shared__ uint64_t s[33];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  uint64_t v = tid < nb ? bsum[tid] : 0;
+  // four consecutive block sums per thread (nb <= 4096)
+  uint64_t q[4], v = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    q[j] = 4 * tid + j < nb ? bsum[4 * tid + j] : 0;
+    v += q[j];
+  }
   uint64_t incl = warp_incl_scan(v);
   if (lane == 31) s[warp] = incl;
   __syncthreads();
@@ -359,7 +366,12 @@ __global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, 
     if (lane == 31) s[32] = wi;
   }
   __syncthreads();
-  if (tid < nb) bsum[tid] = s[warp] + incl - v;
+  uint64_t run = s[warp] + incl - v;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (4 * tid + j < nb) bsum[4 * tid + j] = run;
+    run += q[j];
+  }
   if (tid == 0) {
     const uint64_t total = s[32];
     ctr->scan_total = total;

@@ -29,7 +29,7 @@ constexpr float kExpScale = -0.72134752044448170f;
 constexpr float kInvExpScale = -1.38629436111989061f;   // 1 / kExpScale = -2 ln 2
 
 // Fixed grid sizes of the device-count-driven kernels (scan, radix sort).
-constexpr int kScanBlocks = 1024;
+constexpr int kScanBlocks = 4096;
 constexpr int kSortBlocks = 768;      // most radix blocks of one pass (histogram capacity)
 constexpr int kMaxRadixBits = 8;      // widest radix digit
 
