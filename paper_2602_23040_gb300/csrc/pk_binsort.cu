@@ -668,8 +668,12 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     // fence and barrier that ended the previous tile
     if (tid == 0 && t + 1 < ntile) issue(t + 1);
     const bool ok = mbar_wait_bounded(&s_bar[cur], parity[cur]);
-    // keys past the last whole 16-byte group come by plain loads
-    const uint32_t tail0 = ((mis + valid) & ~3u) - mis;
+    // keys past the last whole 16-byte group come by plain loads; a tile
+    // that ends before the first group boundary (mis + valid < 4: nothing
+    // was copied) loads all its keys that way.  The start stays unsigned
+    // and in [0, valid]: (whole - mis) alone would wrap below zero there.
+    const uint32_t whole = (mis + valid) & ~3u;
+    const uint32_t tail0 = whole ? whole - mis : 0u;
     if (tid < (int)(valid - tail0)) {
       bk[tail0 + tid] = __ldg(kin + base + tail0 + tid);
       bv[tail0 + tid] = __ldg(vin + base + tail0 + tid);

@@ -196,6 +196,64 @@ def test_bin_and_sort_capacity_overflow(orc):
     assert int(ranges.abs().sum()) == 0
 
 
+# valid pairs per view: the views' segments start at every residue mod 4 and
+# several hold only 1-3 items, so a segment's only radix tile can start 1-3
+# keys past a 16-byte boundary and end before the next one
+RAGGED_COUNTS = [1, 2, 1, 1, 3, 2, 1, 2, 2, 1, 3, 3, 1, 2, 0, 1, 2, 3, 1]
+
+
+def _ragged_records(tile, seed, spread):
+    """Records with exactly RAGGED_COUNTS[v] valid pairs in view v, each a
+    small footprint that reaches one tile, or (spread) one to four tiles
+    when its mean sits on a tile edge or corner; the other pairs are culled."""
+    rng = np.random.default_rng(seed)
+    W = H_ = 64
+    views = [synth.scenes.pinhole((0, 0, -3), W, H_) for _ in RAGGED_COUNTS]
+    N = 8
+    rec = np.zeros((len(views), N, 12), np.float32)
+    nt = W // tile
+    for v, c in enumerate(RAGGED_COUNTS):
+        for i in rng.choice(N, c, replace=False):
+            tx, ty = rng.integers(0, nt, 2)
+            ox = oy = tile / 2
+            if spread:
+                ox = float(rng.choice([tile / 2, 0.0])) if tx else tile / 2
+                oy = float(rng.choice([tile / 2, 0.0])) if ty else tile / 2
+            rec[v, i, 0:2] = (tx * tile + ox, ty * tile + oy)
+            rec[v, i, 2:5] = (4.0, 0.0, 4.0)          # conic: sigma^2 = 1/4, footprint radius 1.5 px
+            rec[v, i, 5] = 0.5
+            rec[v, i, 6] = rng.uniform(0.5, 8.0)
+            rec[v, i, 7] = 2.0
+            rec[v, i, 8:11] = rng.uniform(0, 1, 3)
+    return views, rec
+
+
+@pytest.mark.parametrize("tile,spread", [(16, False), (16, True), (32, False), (32, True)])
+def test_bin_and_sort_ragged_view_segments(orc, tile, spread):
+    """Per-view segments of 0-3 items at every start residue (both the depth
+    passes and the tile passes run segmented by view here)."""
+    pk = _pk()
+    views, rec = _ragged_records(tile, 11 + tile + spread, spread)
+    V, N = rec.shape[:2]
+    plan = _records_plan(views, N, "ellipse", tile)
+    ws = pk.make_workspace(plan)
+    pk.workspace_init(plan, ws)
+    drec = torch.from_numpy(rec.reshape(-1)).cuda()
+    vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    pk.bin_and_sort(plan, drec, vals, ranges, ws)
+    st = pk.read_status(plan, ws)
+    va = orc.views_array(views)
+    r = rec.reshape(V * N, 12)
+    ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, tile, r[:, 2], r[:, 3],
+                                          r[:, 4], mode=orc.BIN_ELLIPSE)
+    assert st["valid_pairs"] == sum(RAGGED_COUNTS)
+    if not spread:
+        assert len(ref_vals) == sum(RAGGED_COUNTS)
+    assert st["dups"] == len(ref_vals) and st["flags"] == 0
+    assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.u32(ranges).reshape(-1, 2), ref_vals, ref_ranges)
+
+
 # ---------------------------------------------------------------------------
 # a4 / a5 on identical FP32 records
 # ---------------------------------------------------------------------------
