@@ -568,6 +568,7 @@ def main():
         t0 = time.perf_counter()
         upload(0, 0)
         host = {"replay": [], "upload": [], "status": []}
+        step_ms = []
         for k in range(ke):
             slot = k % 2
             h0 = time.perf_counter()
@@ -586,6 +587,7 @@ def main():
             host["replay"].append((h1 - h0) * 1e3)
             host["upload"].append((h2 - h1) * 1e3)
             host["status"].append((h3 - h2) * 1e3)
+            step_ms.append((h3 - h0) * 1e3)
         torch.cuda.synchronize(dev)
         gap_ms = statistics.median(g_ev[k][1].elapsed_time(g_ev[k + 1][0]) for k in range(ke - 1))
         dt = (time.perf_counter() - t0) / ke
@@ -599,7 +601,10 @@ def main():
                       "pipeline": "inputs double-buffered; next step's copies overlap this step's compute",
                       "graph_ms_per_step": graph_ms, "upload_ms_per_step": upload_ms,
                       "upload_start_after_graph_start_ms": upload_lag_ms, "device_gap_between_graphs_ms": gap_ms,
-                      "host_ms": {n: statistics.median(v) for n, v in host.items()}, "steps": ke}
+                      "host_ms": {n: statistics.median(v) for n, v in host.items()},
+                      "host_step_ms": {"median": statistics.median(step_ms), "max": max(step_ms),
+                                       "first_upload": u_ev[0][0].elapsed_time(u_ev[0][1])},
+                      "steps": ke}
         del bufs, g2
 
     if not args.profile and not args.no_per_view and rank == 0:
