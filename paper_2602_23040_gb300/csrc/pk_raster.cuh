@@ -121,6 +121,56 @@ __device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint3
   stage_from(__ldg(r), __ldg(r + 1), __ldg(r + 2), pid, s, j);
 }
 
+// Two FP32 values in one 64-bit register for the packed FP32 instructions
+// of this GPU generation (add / sub / mul / fma .rn.f32x2): one issue does
+// both round-to-nearest operations, each with exactly the scalar result.
+// The backward runs two pixels of a thread (same column, rows apart)
+// through them side by side.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+  f32x2 v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
+  return v;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 dup2(float v) { return pack2(v, v); }
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// The exponent power = k q = A dx^2 + B dx dy + C dy^2 of a staged splat at
+// two pixel centres of one column (common dx and zx = A dx, rows py, dy =
+// py - m_y), two lanes at a time: u = B dy + zx, power = u dx + (C dy) dy,
+// each step rounded to nearest in this order, exactly the steps of
+// splat_alpha below (the forward's scalar form), so the two kernels take
+// identical skip and clamp decisions.  A pixel skips the splat unless
+// power >= pcut; then alpha = min(0.99, o 2^power).
+__device__ __forceinline__ f32x2 splat_power2(const float4 &a, const float4 &b, float dx, float zx, f32x2 py,
+                                              f32x2 &dy) {
+  dy = sub2(py, dup2(a.y));
+  const f32x2 u = fma2(dup2(a.w), dy, dup2(zx));
+  return fma2(u, dup2(dx), mul2(mul2(dup2(b.x), dy), dy));
+}
+
 struct Hit {
   float alpha, G, dx, dy;
   bool clamped;

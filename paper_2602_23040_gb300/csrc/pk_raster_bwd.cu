@@ -1,10 +1,10 @@
 // a5 -- adjoint of the compositing (Sec. 4.2 "Objective").  Each pixel
 // walks its tile's list backwards from its last blended splat, recovering
 // T_i = T_{i+1} / (1 - alpha_i) from the stored final transmittance, so no
-// per-step state of the forward is kept.  Each thread holds two pixels; per
-// splat the 9 gradients of a warp's 64 pixels are summed by a reduce-scatter
-// over the lanes (12
-// shuffles instead of 45 for nine full butterfly sums), after which nine
+// per-step state of the forward is kept.  Each thread holds four pixels
+// (two packed pairs); per splat the 9 gradients of a warp's 128 pixels are
+// summed by a reduce-scatter over the lanes (12 shuffles instead of 45 for
+// nine full butterfly sums), after which nine
 // lanes each hold one complete sum and add it to the splat's gradient
 // record with one coalesced atomic instruction.
 #include "pk_raster.cuh"
@@ -60,41 +60,73 @@ __device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int l
   return z;
 }
 
-// One pixel's share of the adjoint of a blended splat.  T (transmittance
-// after the splat) becomes T before it; GS = dL/dC . S, S being the colour
-// composited behind (background included), takes the splat's own term
-// (only that dot product enters dL/dalpha); the colour and opacity
-// gradients are added to acc[5..8].  The conic and mean gradients are
-// linear in dq = dL/dq, so the pixel only adds dq, dq dy and dq dy^2 to
-// q1, qy, qyy (dx is the same for both pixels of a thread) and the caller
-// forms acc[0..4] once per splat.  Returns false if the pixel skips the splat.
-__device__ __forceinline__ bool pixel_adjoint(const float4 &a, const float4 &b, const float4 &c4, float dx, float zx,
-                                              float py, float g0, float g1, float g2, float &T, float &GS,
-                                              float (&acc)[9], float &q1, float &qy, float &qyy) {
-  Hit h;
-  if (!splat_alpha(a, b, c4.z, dx, zx, py, h)) return false;
-  const float om = __fsub_rn(1.f, h.alpha);
-  const float inv = rcp_approx(om);
-  const float Ti = T * inv;
-  const float wT = h.alpha * Ti;
-  // dL/dalpha = sum_c g_c (T_i rgb_c - S_c / (1 - alpha)) = (T g.rgb - g.S) / (1 - alpha)
-  const float gr = fmaf(g2, c4.x, fmaf(g1, b.w, g0 * b.z));
-  const float da = (T * gr - GS) * inv;
-  GS = fmaf(wT, gr, GS);
-  T = Ti;
-  acc[6] = fmaf(wT, g0, acc[6]);
-  acc[7] = fmaf(wT, g1, acc[7]);
-  acc[8] = fmaf(wT, g2, acc[8]);
-  if (!h.clamped) {
-    // alpha = o 2^power, power = k q: dL/dq = -alpha dL/dalpha / 2
-    acc[5] = fmaf(da, h.G, acc[5]);
-    const float dq = -0.5f * h.alpha * da;
-    const float t = dq * h.dy;
-    q1 += dq;
-    qy += t;
-    qyy = fmaf(t, h.dy, qyy);
-  }
+// Per-splat sums of a thread's pixels, kept as two packed lanes (the two
+// pixels of a pair) and added lane to lane once per splat.
+struct AdjSums {
+  f32x2 a5, a6, a7, a8, q1, qy, qyy;
+};
+
+// Two pixels' shares of the adjoint of a blended splat, pixels h and h + 1
+// of a thread side by side in the packed FP32 lanes (e0 / e1: the pixel
+// blended or skipped this splat in the forward).  Per pixel, T
+// (transmittance after the splat) becomes T before it; GS = dL/dC . S, S
+// being the colour composited behind (background included), takes the
+// splat's own term (only that dot product enters dL/dalpha); the colour and
+// opacity gradients go to the sums a5..a8.  The conic and mean gradients
+// are linear in dq = dL/dq, so a pixel only adds dq, dq dy and dq dy^2 to
+// q1, qy, qyy (dx is common to a thread's pixels) and the caller forms them
+// once per splat.  A lane that skips the splat takes alpha 0, which leaves
+// its T and GS unchanged and adds 0 to every sum.  Returns false if both
+// pixels skip.
+__device__ __forceinline__ bool pixel_adjoint2(const float4 &a, const float4 &b, const float4 &c4, float dx, float zx,
+                                               f32x2 py, bool e0, bool e1, f32x2 g0, f32x2 g1, f32x2 g2, float &T0,
+                                               float &T1, float &GS0, float &GS1, AdjSums &s) {
+  f32x2 dy;
+  float p0, p1;
+  unpack2(splat_power2(a, b, dx, zx, py, dy), p0, p1);
+  const bool ok0 = e0 && p0 >= c4.z, ok1 = e1 && p1 >= c4.z;
+  if (!(ok0 || ok1)) return false;
+  const float G0 = ex2_approx(p0), G1 = ex2_approx(p1);
+  float r0, r1;
+  unpack2(mul2(dup2(b.y), pack2(G0, G1)), r0, r1);
+  const bool cl0 = r0 > kAlphaMax, cl1 = r1 > kAlphaMax;
+  const float al0 = ok0 ? (cl0 ? kAlphaMax : r0) : 0.f;
+  const float al1 = ok1 ? (cl1 ? kAlphaMax : r1) : 0.f;
+  const f32x2 al = pack2(al0, al1);
+  float om0, om1;
+  unpack2(sub2(dup2(1.f), al), om0, om1);
+  const f32x2 inv = pack2(rcp_approx(om0), rcp_approx(om1));
+  const f32x2 Tv = pack2(T0, T1);
+  float ti0, ti1;
+  const f32x2 Ti = mul2(Tv, inv);
+  unpack2(Ti, ti0, ti1);
+  const f32x2 wT = mul2(al, Ti);
+  // dL/dalpha = (T g.rgb - g.S) / (1 - alpha)
+  const f32x2 gr = fma2(g2, dup2(c4.x), fma2(g1, dup2(b.w), mul2(g0, dup2(b.z))));
+  const f32x2 GSv = pack2(GS0, GS1);
+  float da0, da1;
+  unpack2(mul2(sub2(mul2(Tv, gr), GSv), inv), da0, da1);
+  unpack2(fma2(wT, gr, GSv), GS0, GS1);
+  if (ok0) T0 = ti0;
+  if (ok1) T1 = ti1;
+  s.a6 = fma2(wT, g0, s.a6);
+  s.a7 = fma2(wT, g1, s.a7);
+  s.a8 = fma2(wT, g2, s.a8);
+  // alpha = o 2^power, power = k q: dL/dq = -alpha dL/dalpha / 2 (unclamped pixels only)
+  const f32x2 dav = pack2(ok0 && !cl0 ? da0 : 0.f, ok1 && !cl1 ? da1 : 0.f);
+  s.a5 = fma2(dav, pack2(G0, G1), s.a5);
+  const f32x2 dq = mul2(mul2(dup2(-0.5f), al), dav);
+  const f32x2 t = mul2(dq, dy);
+  s.q1 = add2(s.q1, dq);
+  s.qy = add2(s.qy, t);
+  s.qyy = fma2(t, dy, s.qyy);
   return true;
+}
+
+__device__ __forceinline__ float lane_sum(f32x2 v) {
+  float lo, hi;
+  unpack2(v, lo, hi);
+  return lo + hi;
 }
 
 // Conic and mean gradients of a splat from the pixel sums q1 = sum dq,
@@ -113,12 +145,14 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // kTma: the records of the next (earlier) batch are fetched into shared
 // memory by bulk copies (one 48-byte copy per splat, completed on an
 // mbarrier) while the current batch is processed.  kPx: pixels per thread.
-// At 4 pixels per thread the kernel is held to 64 registers (no spills):
-// 16 resident CTAs per SM instead of 10 hide more of its latency.
+// At 4 pixels per thread the kernel is held to 72 registers (8 bytes
+// spilled) for 14 resident CTAs per SM: with the packed pixel pairs, 64
+// registers spill in the splat loop (9.07 ms at the 52-view rig) and 80
+// leave 12 CTAs (9.31 ms) against 8.78 ms.
 // kT: side of the tiles the lists were binned for; each CTA takes a 16 x 16
 // quadrant of one, as in the forward.
 template <int kBatch, bool kTma, int kPx, int kT>
-__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_raster_bwd(
+__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
@@ -184,12 +218,13 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_ras
     const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + 7.f;
     const uint32_t s = __ldg(ranges + 2 * (size_t)t);
     const size_t plane = (size_t)W * H;
-    float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx];
+    float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx], pyq[kPx];
     uint32_t nc[kPx];
     uint32_t ncmax = 0;
 #pragma unroll
     for (int q = 0; q < kPx; ++q) {
       const int y = y0 + q * G::kRowStep;
+      pyq[q] = py0 + (float)(q * G::kRowStep);
       T[q] = 1.f;
       g0[q] = g1[q] = g2[q] = 0.f;
       nc[q] = 0;
@@ -265,19 +300,25 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_ras
           const uint32_t pos = beg + (uint32_t)j;   // 0-based list position
           const float4 a = s_a[j], b = s_b[j], c4 = s_c[j];
           const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
-          float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          float q1 = 0.f, qy = 0.f, qyy = 0.f;
+          const f32x2 z2 = dup2(0.f);
+          AdjSums sums{z2, z2, z2, z2, z2, z2, z2};
           bool act = false;
 #pragma unroll
-          for (int q = 0; q < kPx; ++q) {
-            if (pos < nc[q]) {
-              ++evals;
-              act |= pixel_adjoint(a, b, c4, dx, zx, py0 + (float)(q * G::kRowStep), g0[q], g1[q], g2[q], T[q],
-                                   GS[q], acc, q1, qy, qyy);
-            }
+          for (int h = 0; h < kPx; h += 2) {
+            const bool e0 = pos < nc[h], e1 = pos < nc[h + 1];
+            if (!(e0 || e1)) continue;
+            evals += (uint32_t)e0 + (uint32_t)e1;
+            act |= pixel_adjoint2(a, b, c4, dx, zx, pack2(pyq[h], pyq[h + 1]), e0, e1, pack2(g0[h], g0[h + 1]),
+                                  pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]), T[h], T[h + 1], GS[h],
+                                  GS[h + 1], sums);
           }
           if (__any_sync(0xffffffffu, act)) {
-            conic_mean_grads(a, b, dx, q1, qy, qyy, acc);
+            float acc[9];
+            acc[5] = lane_sum(sums.a5);
+            acc[6] = lane_sum(sums.a6);
+            acc[7] = lane_sum(sums.a7);
+            acc[8] = lane_sum(sums.a8);
+            conic_mean_grads(a, b, dx, lane_sum(sums.q1), lane_sum(sums.qy), lane_sum(sums.qyy), acc);
             const float sum = warp_reduce_scatter9(acc, lane);
             if (my_idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + my_idx, sum);
           }
