@@ -603,7 +603,9 @@ def main():
                       "upload_start_after_graph_start_ms": upload_lag_ms, "device_gap_between_graphs_ms": gap_ms,
                       "host_ms": {n: statistics.median(v) for n, v in host.items()},
                       "host_step_ms": {"median": statistics.median(step_ms), "max": max(step_ms),
-                                       "first_upload": u_ev[0][0].elapsed_time(u_ev[0][1])},
+                                       "first_upload": u_ev[0][0].elapsed_time(u_ev[0][1]),
+                                       "each": [round(x, 3) for x in step_ms],
+                                       "graph_each": [round(a.elapsed_time(b), 3) for a, b in g_ev]},
                       "steps": ke}
         del bufs, g2
 
