@@ -407,23 +407,25 @@ def test_config2_full_size(orc):
     H.check_grads(gpu_grad_soa(sc, grad, o["texel"]), o["grad_soa"])
 
 
-def test_config3_full_size_sampled_pixels(orc):
-    """The 52-view rig at full size, in the bench's launch configuration: sampled pixels."""
-    sc = synth.config_scene(3)
+def _check_sampled_pixels(orc, sc, vsel, seed, per_view=60):
+    """Full-size run in the bench's launch configuration; the oracle renders
+    sampled pixels of the views vsel one by one (FP64, from its own gather
+    and projection) and they must match the GPU's image and transmittance."""
     plan, r, _ = run_gpu(sc)
     st = r.status()
     assert st["flags"] == 0 and st["dups"] > 0
     img = r.image.cpu().numpy()
     T = r.T.cpu().numpy()
+    del r
+    torch.cuda.empty_cache()
     soa, texel, _ = orc.gather(sc)
-    rng = np.random.default_rng(13)
-    vsel = [0, 1, 25, 51]
+    rng = np.random.default_rng(seed)
     va = orc.views_array([sc.views[v] for v in vsel])
     rec = orc.project(soa, len(texel), sc.sh_degree, va)
     pix = []
     for i, v in enumerate(vsel):
         vw = sc.views[v]
-        for _ in range(60):
+        for _ in range(per_view):
             pix.append((i, int(rng.integers(0, vw.width)), int(rng.integers(0, vw.height))))
     rgb, Tr, border = orc.render_pixels(rec, va, 16, np.array(pix))
     poff = np.cumsum([0] + [v.width * v.height for v in sc.views])
@@ -438,6 +440,22 @@ def test_config3_full_size_sampled_pixels(orc):
         err = max(np.abs(got - rgb[k]).max(), abs(T[poff[v] + y * vw.width + x] - Tr[k]))
         bad += err > H.IMG_TOL
     assert bad == 0
+
+
+def test_config3_full_size_sampled_pixels(orc):
+    """The 52-view rig at full size, in the bench's launch configuration: sampled pixels."""
+    _check_sampled_pixels(orc, synth.config_scene(3), [0, 1, 25, 51], 13)
+
+
+def test_config5_full_size_sampled_pixels(orc):
+    """The largest workload, 4 frames x 52 views with dynamic texels (208
+    views, 690 M list entries, 2.5 M Gaussians), at full size: sampled pixels
+    of views in every frame."""
+    sc = synth.config_scene(5)
+    assert len(sc.views) == 208 and sc.frames == 4
+    vsel = [0, 53, 118, 207]
+    assert sorted({sc.views[v].frame for v in vsel}) == [0, 1, 2, 3]
+    _check_sampled_pixels(orc, sc, vsel, 15, per_view=40)
 
 
 def test_batched_equals_per_view_loop(orc):
