@@ -13,6 +13,7 @@ oracle on bounded samples of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -565,6 +566,11 @@ def main():
         torch.cuda.synchronize(dev)
         for e_ in ev_done:
             e_.record(stream)
+        # a host loop that feeds the GPU: the interpreter's cyclic garbage
+        # collector is held off while it runs (its passes are host pauses
+        # unrelated to the library)
+        gc.collect()
+        gc.disable()
         t0 = time.perf_counter()
         upload(0, 0)
         host = {"replay": [], "upload": [], "status": []}
@@ -589,8 +595,9 @@ def main():
             host["status"].append((h3 - h2) * 1e3)
             step_ms.append((h3 - h0) * 1e3)
         torch.cuda.synchronize(dev)
-        gap_ms = statistics.median(g_ev[k][1].elapsed_time(g_ev[k + 1][0]) for k in range(ke - 1))
         dt = (time.perf_counter() - t0) / ke
+        gc.enable()
+        gap_ms = statistics.median(g_ev[k][1].elapsed_time(g_ev[k + 1][0]) for k in range(ke - 1))
         graph_ms = statistics.median(a.elapsed_time(b) for a, b in g_ev)
         upload_ms = statistics.median(a.elapsed_time(b) for a, b in u_ev)
         # when the next step's upload starts, from the start of this step's graph
@@ -605,6 +612,7 @@ def main():
                       "host_step_ms": {"median": statistics.median(step_ms), "max": max(step_ms),
                                        "first_upload": u_ev[0][0].elapsed_time(u_ev[0][1]),
                                        "each": [round(x, 3) for x in step_ms],
+                                       "phases_each": {n: [round(x, 3) for x in v] for n, v in host.items()},
                                        "graph_each": [round(a.elapsed_time(b), 3) for a, b in g_ev]},
                       "steps": ke}
         del bufs, g2
