@@ -209,7 +209,9 @@ pk_status pk_autotune(pk_plan *plan, const float *records, const uint32_t *sorte
 pk_status pk_workspace_init(const pk_plan *plan, void *workspace, pk_stream_t stream);
 
 /* Copy the device status block to *out (enqueues a copy on `stream` and
- * synchronises that stream). */
+ * synchronises that stream).  The copy goes through a small pinned host
+ * buffer that the plan allocates on first use and frees in
+ * pk_plan_destroy, so one plan's status is read by one thread at a time. */
 pk_status pk_read_status(const pk_plan *plan, const void *workspace, pk_stream_t stream,
                          pk_device_status *out);
 

@@ -337,6 +337,7 @@ extern "C" void pk_plan_destroy(pk_plan *p) {
   delete[] p->h_toff;
   delete[] p->h_fview_off;
   delete[] p->h_fview_idx;
+  if (p->h_status) cudaFreeHost(p->h_status);
   delete p;
 }
 
@@ -371,14 +372,26 @@ extern "C" pk_status pk_workspace_init(const pk_plan *p, void *ws, pk_stream_t s
 extern "C" pk_status pk_read_status(const pk_plan *p, const void *ws, pk_stream_t stream, pk_device_status *out) {
   if (!p || !ws || !out) return PK_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  DevCounters c;
-  if (cudaMemcpyAsync(out, at<char>(const_cast<void *>(ws), p->ws.status), sizeof(*out), cudaMemcpyDeviceToHost,
+  // both blocks land in a small pinned buffer of the plan (allocated on
+  // first use), so the copies are plain asynchronous ones instead of going
+  // through the driver's staging of pageable memory
+  constexpr size_t kCtrOff = (sizeof(pk_device_status) + 15) & ~size_t(15);
+  pk_plan *pm = const_cast<pk_plan *>(p);
+  if (!pm->h_status && cudaMallocHost(&pm->h_status, kCtrOff + sizeof(DevCounters)) != cudaSuccess) {
+    pm->h_status = nullptr;
+    return PK_ERR_CUDA;
+  }
+  char *hb = static_cast<char *>(pm->h_status);
+  if (cudaMemcpyAsync(hb, at<char>(const_cast<void *>(ws), p->ws.status), sizeof(*out), cudaMemcpyDeviceToHost,
                       st) != cudaSuccess)
     return PK_ERR_CUDA;
-  if (cudaMemcpyAsync(&c, at<char>(const_cast<void *>(ws), p->ws.counters), sizeof(c), cudaMemcpyDeviceToHost,
-                      st) != cudaSuccess)
+  if (cudaMemcpyAsync(hb + kCtrOff, at<char>(const_cast<void *>(ws), p->ws.counters), sizeof(DevCounters),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return PK_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PK_ERR_CUDA;
+  DevCounters c;
+  memcpy(out, hb, sizeof(*out));
+  memcpy(&c, hb + kCtrOff, sizeof(c));
   const double n = 3.0 * (double)p->P, lam = c.ssim_lambda;
   out->ssim = c.ssim_acc / n;
   out->loss = (1.0 - lam) * c.loss_acc / n + (lam > 0.0 ? lam * (1.0 - out->ssim) : 0.0);
