@@ -55,6 +55,34 @@ def load_peaks():
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 
+def _cpulist(text):
+    cpus = set()
+    for part in text.strip().split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def gpu_local_affinity(dev_index):
+    """Restrict this process to the CPUs local to the GPU (from sysfs);
+    returns (previous affinity or None, a short description)."""
+    import torch
+    try:
+        pr = torch.cuda.get_device_properties(dev_index)
+        bus = "%04x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        local = _cpulist(open("/sys/bus/pci/devices/%s/local_cpulist" % bus).read()) & os.sched_getaffinity(0)
+        if not local:
+            return None, "unchanged (no local CPUs listed for %s)" % bus
+        before = os.sched_getaffinity(0)
+        os.sched_setaffinity(0, local)
+        return before, "%d CPUs local to %s" % (len(local), bus)
+    except Exception as ex:  # no sysfs entry or property: leave the affinity alone
+        return None, "unchanged (%s)" % type(ex).__name__
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -528,6 +556,9 @@ def main():
         # memory and reads its loss back.  The inputs are double-buffered:
         # the next step's host->device copies run on a second stream while
         # this step computes (a second graph reads the second buffer pair).
+        # the host side runs on the CPUs local to this GPU, so the pinned
+        # input buffers are placed (first touch) in the memory nearest to it
+        cpus_before, host_cpus = gpu_local_affinity(local)
         h_atlas = torch.from_numpy(scene.atlas).pin_memory()
         h_target = torch.from_numpy(synth.random_target(scene)).pin_memory()
         bufs = [(atlas, target), (torch.empty_like(atlas), torch.empty_like(target))]
@@ -614,8 +645,10 @@ def main():
                                        "each": [round(x, 3) for x in step_ms],
                                        "phases_each": {n: [round(x, 3) for x in v] for n, v in host.items()},
                                        "graph_each": [round(a.elapsed_time(b), 3) for a, b in g_ev]},
-                      "steps": ke}
-        del bufs, g2
+                      "steps": ke, "host_cpus": host_cpus}
+        if cpus_before is not None:
+            os.sched_setaffinity(0, cpus_before)
+        del bufs, g2, h_atlas, h_target
 
     if not args.profile and not args.no_per_view and rank == 0:
         loop = pk.PerViewLoop.for_scene(scene, dev, tile=args.tile,
