@@ -125,6 +125,11 @@ typedef struct pk_options {
   int32_t stage_fwd;               /* pk_stage_mode of pk_rasterize_fwd; default PK_STAGE_LOADS */
   int32_t stage_bwd;               /* pk_stage_mode of pk_rasterize_bwd; default PK_STAGE_LOADS */
   int32_t batch_bwd;               /* the same for pk_rasterize_bwd (0 = 128) */
+  int32_t first_wait_polls;        /* polls of the first bounded wait on each bulk-copied batch
+                                      (radix sort, and the compositing kernels in PK_STAGE_BULK):
+                                      0 = the default (about 2^22); -1 = give up without polling,
+                                      a hook for testing the timeout path.  Waits that drain
+                                      copies already issued always keep the default. */
 } pk_options;
 
 typedef struct pk_plan pk_plan;
@@ -149,6 +154,9 @@ typedef struct pk_sizes {
 #define PK_DEV_LIVE_MISMATCH 2u  /* gather: occupancy holds != N live texels */
 #define PK_DEV_TIMEOUT 4u        /* a bounded device wait gave up */
 #define PK_DEV_BOUNDS 8u         /* a data-dependent index failed its check; the access was skipped */
+/* After PK_DEV_TIMEOUT or PK_DEV_BOUNDS inside pk_bin_and_sort the call
+ * emits nothing: every tile range is empty, so no later call reads a
+ * partly sorted list.  Flags stay set until pk_workspace_init. */
 typedef struct pk_device_status {
   uint32_t flags;
   uint32_t live_seen;              /* live texels counted by the last gather (saturating) */
@@ -159,6 +167,10 @@ typedef struct pk_device_status {
   uint64_t evals_bwd;              /* ... of the last backward */
   double loss;                     /* last pk_l1_loss_grad / pk_photo_loss_grad value */
   double ssim;                     /* mean SSIM of the last pk_photo_loss_grad (0 after L1) */
+  uint64_t nonfinite;              /* Gaussians (over all frames) with a non-finite texel value,
+                                      counted by the last pk_atlas_gather; pk_project_and_sh culls
+                                      every pair of such a Gaussian and pk_atlas_scatter_grad
+                                      gives it a zero gradient */
 } pk_device_status;
 
 /* ------------------------------------------------------------------------ */
@@ -242,7 +254,8 @@ pk_status pk_atlas_gather(const pk_plan *plan, const void *atlas, const uint32_t
  * radius, red, green, blue, 0}, conic = Sigma2D^-1 = [[a, b], [b, c]],
  * s = exp(log-scale), opacity = sigmoid(logit), colour =
  * max(0, sum_j k_j Y_j(normalize(mu - camera centre)) + 0.5).  A culled
- * pair (z <= znear, det <= 1e-7, non-finite) has radius 0.
+ * pair (z <= znear, det <= 1e-7, a non-finite texel value of the Gaussian
+ * -- any of its D channels -- or a non-finite result) has radius 0.
  * soa: [D][F*N] float32 from pk_atlas_gather.  records: out [V*N][12]. */
 pk_status pk_project_and_sh(const pk_plan *plan, const float *soa, float *records,
                             void *workspace, pk_stream_t stream);
@@ -275,20 +288,24 @@ pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *s
 /* pk_bin_and_sort without a workspace.  The paper has no counterpart: this
  * is a convenience for callers that cannot give the library device memory
  * -- e.g. a renderer driven from inside another framework's frame callback,
- * where allocating would stall the frame or break that framework's
- * recorded CUDA graph, or a small tool without a device allocator.  Same
+ * where that framework owns every device allocation and allocating would
+ * stall the frame, or a small tool without a device allocator.  Same
  * inputs, outputs and bit-exact result as pk_bin_and_sort; the scratch is a
  * 64 MiB array inside the library (reserved on every GPU that loads it, for
  * the life of the process), so the plan must satisfy 40 * V * N + 12 *
- * max_dups + 152 * V + about 0.8 MB <= 64 MiB, else PK_ERR_TOO_LARGE is returned and
- * nothing is enqueued.  n_entries: out, one device uint32 -- the entries
- * written, or 0xFFFFFFFF if they exceeded max_dups (then nothing was
- * emitted).  The first call on a device looks up the array's address; make
- * it before any stream capture.  Every call shares the one array and leaves
- * its contents behind: calls whose work can overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
- * The call copies the plan's view and tile tables from host memory each
- * time and never allocates. */
+ * max_dups + 152 * V + about 0.8 MB <= 64 MiB, else PK_ERR_TOO_LARGE is
+ * returned and nothing is enqueued.  n_entries: out, one device uint32 --
+ * the entries written; 0xFFFFFFFF if they exceeded max_dups (then nothing
+ * was emitted); 0xFFFFFFFE if a bounded device wait gave up or an index
+ * check failed inside the call (PK_DEV_TIMEOUT / PK_DEV_BOUNDS: nothing was
+ * emitted either, every tile range is empty).  The first call on a device
+ * looks up the array's address; make it before any stream capture.  Every
+ * call shares the one array and leaves its contents behind (each call
+ * clears its status and counters and uploads its own plan's tables before
+ * use): calls whose work can overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The call copies the
+ * plan's view and tile tables from host memory each time and never
+ * allocates. */
 pk_status pk_bin_and_sort_noalloc(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
                                   uint32_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream);
 

@@ -72,10 +72,11 @@ def _declare(L):
         "or_project": (None, [P, I64, I64, C.c_int, C.c_int, P, C.c_int, DBL, P]),
         "or_tiles_total": (I64, [C.c_int, P, P, C.c_int, P]),
         "or_bin_sort": (I64, [P, P, P, P, P, P, P, C.c_int, C.c_int, I64, P, P, C.c_int, P, I64, P]),
-        "or_render": (U64, [P, C.c_int, I64, P, C.c_int, P, P, P, DBL, P, P, P, P]),
+        "or_render": (U64, [P, C.c_int, I64, P, C.c_int, P, P, P, DBL, DBL, P, P, P, P, P]),
         "or_render_bwd": (None, [P, C.c_int, I64, P, C.c_int, P, P, P, P, P]),
         "or_scatter_grad": (None, [P, I64, I64, C.c_int, C.c_int, P, C.c_int, DBL, P, P, P]),
-        "or_render_pixels": (None, [P, C.c_int, I64, P, C.c_int, P, DBL, I64, P, P, P, P]),
+        "or_mean_error_bounds": (None, [P, C.c_int, I64, P, P, P]),
+        "or_render_pixels": (None, [P, C.c_int, I64, P, C.c_int, P, DBL, DBL, I64, P, P, P, P, P]),
         "or_motion_mask": (None, [P, C.c_int, C.c_int, C.c_float, C.c_int, P]),
         "or_dynamic_mask32": (None, [P, C.c_int, I64, P, P, P, C.c_float, P]),
         "or_dynamic_mask": (None, [P, C.c_int, I64, P, P, P, DBL, DBL, P, P]),
@@ -141,11 +142,14 @@ def half_to_double(h: int) -> float:
 # --------------------------------------------------------------------------
 
 def views_array(views) -> np.ndarray:
+    """Camera table; R, t, fx, fy, cx, cy rounded to FP32 first, the values
+    the library's pk_view carries, so both sides render the same cameras."""
     a = np.zeros((len(views), VS), np.float64)
+    f32 = lambda x: np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
     for i, v in enumerate(views):
-        a[i, 0:9] = np.asarray(v.R, np.float64).reshape(9)
-        a[i, 9:12] = np.asarray(v.t, np.float64)
-        a[i, 12:16] = (v.fx, v.fy, v.cx, v.cy)
+        a[i, 0:9] = f32(v.R).reshape(9)
+        a[i, 9:12] = f32(v.t)
+        a[i, 12:16] = f32([v.fx, v.fy, v.cx, v.cy])
         a[i, 16:19] = (v.width, v.height, v.frame)
     return a
 
@@ -234,18 +238,32 @@ def bin_sort(rec, views_arr, tile, mode=BIN_ELLIPSE):
     return bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], views_arr, N, tile, r[:, 2], r[:, 3], r[:, 4], mode)
 
 
-def render(rec, views_arr, tile, vals, ranges, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
+# Borderline rule (see composite_pixel in packuv_oracle.c).  M_DERIVE: the
+# mean's FP32 error bound is derived per record (records of the oracle's own
+# FP64 projection, compared with a GPU that projected in FP32); a value >= 0
+# is a fixed mean tolerance in pixels, 0 for identical FP32 records.
+# Q_REL: relative rounding of the quadratic form (FP32, a few roundings per
+# term; 2^-19 = 32 unit roundoffs), against |a| dx^2 + 2 |b dx dy| + |c| dy^2.
+M_DERIVE = -1.0
+Q_REL = 2.0 ** -19
+B_Q, B_ALPHA, B_STOP, B_DEPTH, B_CULL, B_CLAMP = 1, 2, 4, 8, 16, 32
+IMAGE_BORDER = B_Q | B_ALPHA | B_STOP | B_DEPTH | B_CULL   # B_CLAMP matters to gradients only
+
+
+def render(rec, views_arr, tile, vals, ranges, bg=(0.0, 0.0, 0.0), m_tol=M_DERIVE, q_rel=Q_REL):
+    """-> dict(img, T, last, border, bound [P][2] (colour, T flip bounds), hash)."""
     V, N, _ = rec.shape
     P = int(np.sum(views_arr[:, 16] * views_arr[:, 17]))
     img = np.zeros(3 * P, np.float64)
     T = np.zeros(P, np.float64)
     last = np.zeros(P, np.uint32)
     border = np.zeros(P, np.uint8)
+    bound = np.zeros((P, 2), np.float64)
     bg = np.ascontiguousarray(bg, np.float64)
     h = lib().or_render(_p(np.ascontiguousarray(rec)), V, N, _p(np.ascontiguousarray(views_arr)), tile,
                         _p(np.ascontiguousarray(vals, np.uint32)), _p(np.ascontiguousarray(ranges, np.uint32)),
-                        _p(bg), m_tol, _p(img), _p(T), _p(last), _p(border))
-    return dict(img=img, T=T, last=last, border=border, hash=int(h))
+                        _p(bg), float(m_tol), float(q_rel), _p(img), _p(T), _p(last), _p(border), _p(bound))
+    return dict(img=img, T=T, last=last, border=border, bound=bound, hash=int(h))
 
 
 def render_bwd(rec, views_arr, tile, vals, ranges, dimg, bg=(0.0, 0.0, 0.0)):
@@ -269,16 +287,29 @@ def scatter_grad(soa, N, sh_degree, views_arr, grad2d, dynflag=None, znear=ZNEAR
     return out
 
 
-def render_pixels(rec, views_arr, tile, pix, bg=(0.0, 0.0, 0.0), m_tol=5e-4):
+def mean_error_bounds(rec, views_arr):
+    """Per record: bound on the FP32 error of the projected mean (px) and depth."""
+    V, N, _ = rec.shape
+    mt = np.zeros(V * N, np.float64)
+    zt = np.zeros(V * N, np.float64)
+    lib().or_mean_error_bounds(_p(np.ascontiguousarray(rec)), V, N, _p(np.ascontiguousarray(views_arr)), _p(mt),
+                               _p(zt))
+    return mt.reshape(V, N), zt.reshape(V, N)
+
+
+def render_pixels(rec, views_arr, tile, pix, bg=(0.0, 0.0, 0.0), m_tol=M_DERIVE, q_rel=Q_REL):
+    """pix [n][3] = (view, x, y) -> (rgb [n][3], T [n], border [n], bound [n][2])."""
     V, N, _ = rec.shape
     pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 3)
     n = pix.shape[0]
     rgb = np.zeros((n, 3), np.float64)
     T = np.zeros(n, np.float64)
     border = np.zeros(n, np.uint8)
+    bound = np.zeros((n, 2), np.float64)
     lib().or_render_pixels(_p(np.ascontiguousarray(rec)), V, N, _p(np.ascontiguousarray(views_arr)), tile,
-                           _p(np.ascontiguousarray(bg, np.float64)), m_tol, n, _p(pix), _p(rgb), _p(T), _p(border))
-    return rgb, T, border
+                           _p(np.ascontiguousarray(bg, np.float64)), float(m_tol), float(q_rel), n, _p(pix),
+                           _p(rgb), _p(T), _p(border), _p(bound))
+    return rgb, T, border, bound
 
 
 # --------------------------------------------------------------------------
@@ -424,7 +455,7 @@ def photo_loss(img, tgt, views_arr, lam=SSIM_LAMBDA, grad=True, ssim_map=False):
 # Whole step
 # --------------------------------------------------------------------------
 
-def forward(scene, tile=16, znear=ZNEAR, bg=(0.0, 0.0, 0.0), m_tol=5e-4, mode=BIN_ELLIPSE):
+def forward(scene, tile=16, znear=ZNEAR, bg=(0.0, 0.0, 0.0), m_tol=M_DERIVE, mode=BIN_ELLIPSE):
     soa, texel, dynflag = gather(scene)
     va = views_array(scene.views)
     N = len(texel)

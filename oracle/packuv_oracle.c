@@ -374,6 +374,11 @@ static int near_rel(double a, double cut, double rel) {
 static void project_one(const double *attr, int64_t stride, int sh_deg, const double *cv,
                         double znear, proj_t *P) {
   memset(P, 0, sizeof(*P));
+  /* a Gaussian with a non-finite texel value (any of its D channels) is
+     culled in every view (reading of the contract's "non-finite" cull) */
+  const int D = 11 + 3 * (sh_deg + 1) * (sh_deg + 1);
+  for (int ch = 0; ch < D; ++ch)
+    if (!isfinite(attr[ch * stride])) return;
   const double *Rc = cv, *tc = cv + 9;
   double fx = cv[12], fy = cv[13], cx = cv[14], cy = cv[15];
   for (int i = 0; i < 3; ++i) P->mu[i] = attr[i * stride];
@@ -652,62 +657,141 @@ typedef struct {
 } contrib_t;
 
 /*
+ * Tolerances of the borderline rule.  A decision of the compositing (q vs 9,
+ * alpha vs 1/255, T' vs 1e-4, the depth order of two contributors, a cull)
+ * is borderline when an FP32 evaluation of the same step could take the
+ * other side:
+ *   - q is off by at most dq = |grad_m q| m_tol + (q_rel + cond_rel cond)
+ *     (|a| dx^2 + 2 |b dx dy| + |c| dy^2), m_tol bounding the error of the
+ *     projected mean (per record in mtol[], else m_fixed), q_rel the
+ *     rounding of the quadratic form, cond = (|a c| + b^2) / (a c - b^2)
+ *     the condition of the conic (its error grows with it);
+ *   - ln alpha is off by dq / 2 + 1e-5 (alpha's own rounding);
+ *   - T' relative 1e-4, and any decision after a flip whose change of T
+ *     could move the stop;
+ *   - two contributors' depths closer than ztol[] of both plus one FP32 ulp
+ *     (else 4 FP32 ulps).
+ * mtol / ztol are NULL when both sides composite identical FP32 records.
+ */
+typedef struct {
+  const double *mtol, *ztol;
+  double m_fixed, q_rel, cond_rel, bg_max;
+} tol_t;
+
+static const double U32 = 5.9604644775390625e-08;   /* 2^-24, FP32 unit roundoff */
+
+/*
  * Front-to-back compositing of one pixel over list positions [s, e).
  * Records contributors in c (if non-NULL, capacity e - s); returns their
  * count and sets *Tout, rgb, *last (1-based list position of the last
  * blended entry, 0 if none), *flags (borderline bits), *hash.
+ * bnd (if non-NULL) receives the pixel's flip bound: bnd[0] bounds the
+ * change of any colour channel, bnd[1] that of T_final, if every
+ * borderline decision went the other way.  A flipped splat k changes the
+ * colour by T_k a_k (c_k - B / (1 - a_k)), B the colour behind, so by at
+ * most T_k a_k cmax (cmax: the largest colour of the tile's list or the
+ * background); a swap of two adjacent contributors by T a_1 a_2 cmax; a
+ * flipped stop by T cmax.  A flip changes T behind it by a factor (1 -
+ * a_k)^(+-1), and a stop that such a change could move is a flip too.
  */
 static int composite_pixel(const double *rec, const uint32_t *vals, int64_t s, int64_t e,
-                           double px, double py, double m_tol, double *rgb, double *Tout,
-                           int64_t *last, uint32_t *flags, uint64_t *hash, contrib_t *c) {
+                           double px, double py, const tol_t *tol, double *rgb, double *Tout,
+                           int64_t *last, uint32_t *flags, uint64_t *hash, contrib_t *c,
+                           double *bnd) {
   double T = 1.0;
   int n = 0;
   uint32_t prev_zb = 0;
-  double prev_z = 0.0, prev_m[2] = {0.0, 0.0};
+  double prev_z = 0.0, prev_m[2] = {0.0, 0.0}, prev_T = 0.0, prev_a = 0.0, prev_zt = 0.0;
   int have_prev = 0;
+  double cmax = tol->bg_max, bI = 0.0, bT = 0.0;
+  double rho = 1.0;   /* T of the other side lies within [T rho^-1, T rho] */
+  if (bnd)
+    for (int64_t k = s; k < e; ++k) {
+      const double *r = rec + (int64_t)vals[k] * OR_REC;
+      for (int ch = 0; ch < 3; ++ch)
+        if (r[R_RED + ch] > cmax) cmax = r[R_RED + ch];
+    }
   rgb[0] = rgb[1] = rgb[2] = 0.0;
   *last = 0;
   for (int64_t k = s; k < e; ++k) {
     const double *r = rec + (int64_t)vals[k] * OR_REC;
     double dx = px - r[R_MX], dy = py - r[R_MY];
     double q = r[R_CA] * dx * dx + 2.0 * r[R_CB] * dx * dy + r[R_CC] * dy * dy;
-    /* error bound of q from an m_tol shift of the mean: |grad_m q| m_tol */
+    /* error bound of q: an m_tol shift of the mean (|grad_m q| m_tol) plus
+       the rounding of the form and of the conic */
     double gq = 2.0 * sqrt((r[R_CA] * dx + r[R_CB] * dy) * (r[R_CA] * dx + r[R_CB] * dy) +
                            (r[R_CB] * dx + r[R_CC] * dy) * (r[R_CB] * dx + r[R_CC] * dy));
-    double dq = gq * m_tol + 1e-5 * fabs(q) + 1e-6;
-    if (fabs(q - Q_MAX) <= dq) *flags |= B_Q;
+    double sabs = fabs(r[R_CA]) * dx * dx + 2.0 * fabs(r[R_CB] * dx * dy) + fabs(r[R_CC]) * dy * dy;
+    double detc = r[R_CA] * r[R_CC] - r[R_CB] * r[R_CB];
+    double cond = detc > 0 ? (fabs(r[R_CA] * r[R_CC]) + r[R_CB] * r[R_CB]) / detc : 1e30;
+    double mt = tol->mtol ? tol->mtol[vals[k]] : tol->m_fixed;
+    double dq = gq * mt + (tol->q_rel + tol->cond_rel * cond) * sabs;
+    int nearq = fabs(q - Q_MAX) <= dq;
+    double araw = r[R_OP] * exp(-0.5 * q);
+    int neara = araw > 0 && fabs(log(araw) - log(ALPHA_MIN)) <= 0.5 * dq + 1e-5;
+    if (nearq) *flags |= B_Q;
+    if (neara) *flags |= B_ALPHA;
+    /* the other side may blend a splat skipped here, or skip one blended
+       here: possible when each test either passes or is borderline */
+    if ((nearq || neara) && (q <= Q_MAX || nearq) && (araw >= ALPHA_MIN || neara)) {
+      double af = araw > ALPHA_MAX ? ALPHA_MAX : (araw < ALPHA_MIN ? ALPHA_MIN : araw);
+      bI += T * rho * af * cmax;
+      bT += T * rho * af;
+      rho /= (1.0 - af);
+    }
     if (q > Q_MAX) {
       *hash = fnv(*hash, ((uint64_t)k << 2) | 0);
       continue;
     }
     double Gv = exp(-0.5 * q);
-    double araw = r[R_OP] * Gv;
     double alpha = araw > ALPHA_MAX ? ALPHA_MAX : araw;
-    if (araw > 0 && fabs(log(araw) - log(ALPHA_MIN)) <= 0.5 * dq + 1e-5) *flags |= B_ALPHA;
     if (alpha < ALPHA_MIN) {
       *hash = fnv(*hash, ((uint64_t)k << 2) | 1);
       continue;
     }
     double Tn = T * (1.0 - alpha);
-    if (near_rel(Tn, T_MIN, 1e-4)) *flags |= B_STOP;
+    /* an FP32 depth order can differ from this one between two depths
+       closer than their FP32 errors -- exact FP64 ties included, since FP32
+       rounding can split them -- unless the two splats sit at the same
+       place (same depth and mean), which every precision computes alike.
+       Tested before the stop: swapping the pair can move the stop into it
+       (this splat first could already end the pixel, or ends it here). */
+    uint32_t zb = f32_bits((float)r[R_Z]);
+    double zt = tol->ztol ? tol->ztol[vals[k]] : 0.0;
+    int zclose = tol->ztol ? fabs(r[R_Z] - prev_z) <= zt + prev_zt + 2.0 * U32 * fabs(r[R_Z])
+                           : (zb - prev_zb) <= 4u;
+    if (have_prev && zclose && !(r[R_Z] == prev_z && r[R_MX] == prev_m[0] && r[R_MY] == prev_m[1])) {
+      *flags |= B_DEPTH;
+      double lim = T_MIN * (1.0 + 1e-4) * rho;
+      int stop_moves = Tn < lim || prev_T * (1.0 - alpha) < lim;
+      bI += prev_T * rho * (stop_moves ? 1.0 : prev_a * alpha) * cmax;
+      if (stop_moves) bT += prev_T * rho;
+    }
+    /* a stop the other side could take differently: near the cutoff, or
+       within the spread of T that earlier flips allow */
+    if (near_rel(Tn, T_MIN, 1e-4) || (Tn * rho >= T_MIN && Tn / rho < T_MIN)) {
+      *flags |= B_STOP;
+      bI += T * rho * cmax;
+      bT += T * rho;
+    }
     if (Tn < T_MIN) {
       *hash = fnv(*hash, ((uint64_t)k << 2) | 3);
       break;
     }
-    if (((uint32_t)r[R_FLAGS]) & F_CULL_NEAR) *flags |= B_CULL;
+    if (((uint32_t)r[R_FLAGS]) & F_CULL_NEAR) {
+      *flags |= B_CULL;
+      bI += T * rho * alpha * cmax;
+      bT += T * rho * alpha;
+      rho /= (1.0 - alpha);
+    }
     if (fabs(araw - ALPHA_MAX) <= 1e-4) *flags |= B_CLAMP;
-    /* an FP32 depth order can differ from this one between two depths within
-       a few FP32 ulps of each other -- exact FP64 ties included, since FP32
-       rounding can split them -- unless the two splats sit at the same
-       place (same depth and mean), which every precision computes alike */
-    uint32_t zb = f32_bits((float)r[R_Z]);
-    if (have_prev && (zb - prev_zb) <= 4u &&
-        !(r[R_Z] == prev_z && r[R_MX] == prev_m[0] && r[R_MY] == prev_m[1]))
-      *flags |= B_DEPTH;
     prev_zb = zb;
     prev_z = r[R_Z];
+    prev_zt = zt;
     prev_m[0] = r[R_MX];
     prev_m[1] = r[R_MY];
+    prev_T = T;
+    prev_a = alpha;
     have_prev = 1;
     rgb[0] += T * alpha * r[R_RED];
     rgb[1] += T * alpha * r[R_GRN];
@@ -722,7 +806,72 @@ static int composite_pixel(const double *rec, const uint32_t *vals, int64_t s, i
     *hash = fnv(*hash, ((uint64_t)k << 2) | 2);
   }
   *Tout = T;
+  if (bnd) {
+    bnd[0] = bI;
+    bnd[1] = bT;
+  }
   return n;
+}
+
+/*
+ * Bounds on the FP32 error of each record's projected mean and depth, as
+ * the library computes them from FP32 texels and an FP32 camera: X = R mu +
+ * t (four roundings over terms of size at most sqrt(3) |mu| + |t_i|), then
+ * m = fx X_x / X_z + cx (three roundings and the final add), to first
+ * order: dm = fx (dX_x + |x/z| dX_z) / z + 3u fx |x/z| + u |m|, and alike
+ * in y; dz = dX_z.  |mu| = |X - t| since R is a rotation.  Culled records
+ * get 0.
+ */
+static void mean_error_bounds(const double *rec, int V, int64_t N, const double *views, double *mtol,
+                              double *ztol) {
+  for (int v = 0; v < V; ++v) {
+    const double *cv = views + (int64_t)v * OR_VS;
+    const double *tc = cv + 9;
+    double fx = cv[12], fy = cv[13], cx = cv[14], cy = cv[15];
+    for (int64_t g = 0; g < N; ++g) {
+      int64_t p = (int64_t)v * N + g;
+      const double *r = rec + p * OR_REC;
+      mtol[p] = ztol[p] = 0.0;
+      if (!(r[R_RAD] > 0)) continue;
+      double z = r[R_Z], xz = (r[R_MX] - cx) / fx, yz = (r[R_MY] - cy) / fy;
+      double X[3] = {xz * z, yz * z, z};
+      double mu = sqrt((X[0] - tc[0]) * (X[0] - tc[0]) + (X[1] - tc[1]) * (X[1] - tc[1]) +
+                       (X[2] - tc[2]) * (X[2] - tc[2]));
+      double dX[3];
+      for (int a = 0; a < 3; ++a) dX[a] = 4.0 * U32 * (sqrt(3.0) * mu + fabs(tc[a]));
+      double dmx = fx * (dX[0] + fabs(xz) * dX[2]) / z + 3.0 * U32 * fx * fabs(xz) + U32 * fabs(r[R_MX]);
+      double dmy = fy * (dX[1] + fabs(yz) * dX[2]) / z + 3.0 * U32 * fy * fabs(yz) + U32 * fabs(r[R_MY]);
+      mtol[p] = dmx > dmy ? dmx : dmy;
+      ztol[p] = dX[2];
+    }
+  }
+}
+
+void or_mean_error_bounds(const double *rec, int V, int64_t N, const double *views, double *mtol,
+                          double *ztol) {
+  mean_error_bounds(rec, V, N, views, mtol, ztol);
+}
+
+/* The rule's tolerances: m_tol < 0 derives the per-record bounds above
+   (records of the oracle's own FP64 projection), m_tol >= 0 is a fixed
+   mean tolerance in pixels (0: identical FP32 records on both sides). */
+static void make_tol(tol_t *tol, const double *rec, int V, int64_t N, const double *views, double m_tol,
+                     double q_rel, const double *bg, double **mt, double **zt) {
+  memset(tol, 0, sizeof(*tol));
+  *mt = *zt = NULL;
+  tol->q_rel = q_rel;
+  for (int c = 0; c < 3; ++c)
+    if (bg && bg[c] > tol->bg_max) tol->bg_max = bg[c];
+  if (m_tol < 0) {
+    *mt = (double *)malloc(sizeof(double) * (size_t)(V * N > 0 ? V * N : 1));
+    *zt = (double *)malloc(sizeof(double) * (size_t)(V * N > 0 ? V * N : 1));
+    mean_error_bounds(rec, V, N, views, *mt, *zt);
+    tol->mtol = *mt;
+    tol->ztol = *zt;
+    tol->cond_rel = 8.0 * U32;
+  } else {
+    tol->m_fixed = m_tol;
+  }
 }
 
 static void view_offsets(const double *views, int V, int T, int64_t *poff, int64_t *toff) {
@@ -746,8 +895,11 @@ static void view_offsets(const double *views, int V, int T, int64_t *poff, int64
  */
 uint64_t or_render(const double *rec, int V, int64_t N, const double *views, int T,
                    const uint32_t *vals, const uint32_t *ranges, const double *bg, double m_tol,
-                   double *img, double *Tfin, uint32_t *last, uint8_t *border) {
-  (void)N;
+                   double q_rel, double *img, double *Tfin, uint32_t *last, uint8_t *border,
+                   double *bnd) {
+  tol_t tol;
+  double *mt, *zt;
+  make_tol(&tol, rec, V, N, views, m_tol, q_rel, bg, &mt, &zt);
   int64_t *poff = (int64_t *)malloc(sizeof(int64_t) * (V + 1));
   int64_t *toff = (int64_t *)malloc(sizeof(int64_t) * (V + 1));
   view_offsets(views, V, T, poff, toff);
@@ -763,8 +915,9 @@ uint64_t or_render(const double *rec, int V, int64_t N, const double *views, int
         int64_t lst;
         uint32_t fl = 0;
         hash = fnv(hash, (uint64_t)(poff[v] + (int64_t)y * W + x));
-        composite_pixel(rec, vals, s, e, x + 0.5, y + 0.5, m_tol, rgb, &Tv, &lst, &fl, &hash, NULL);
         int64_t pix = poff[v] + (int64_t)y * W + x;
+        composite_pixel(rec, vals, s, e, x + 0.5, y + 0.5, &tol, rgb, &Tv, &lst, &fl, &hash, NULL,
+                        bnd ? bnd + 2 * pix : NULL);
         for (int c = 0; c < 3; ++c)
           img[3 * poff[v] + (int64_t)c * W * H + (int64_t)y * W + x] = rgb[c] + Tv * bg[c];
         Tfin[pix] = Tv;
@@ -774,6 +927,8 @@ uint64_t or_render(const double *rec, int V, int64_t N, const double *views, int
   }
   free(poff);
   free(toff);
+  free(mt);
+  free(zt);
   return hash;
 }
 
@@ -794,6 +949,8 @@ void or_render_bwd(const double *rec, int V, int64_t N, const double *views, int
   for (int64_t t = 0; t < toff[V]; ++t)
     if ((int64_t)ranges[2 * t + 1] - ranges[2 * t] > maxlist) maxlist = ranges[2 * t + 1] - ranges[2 * t];
   contrib_t *cb = (contrib_t *)malloc(sizeof(contrib_t) * maxlist);
+  tol_t tol0;
+  memset(&tol0, 0, sizeof(tol0));
   for (int v = 0; v < V; ++v) {
     int W = (int)views[(int64_t)v * OR_VS + 16], H = (int)views[(int64_t)v * OR_VS + 17];
     int tx_n = (W + T - 1) / T;
@@ -805,7 +962,7 @@ void or_render_bwd(const double *rec, int V, int64_t N, const double *views, int
         int64_t lst;
         uint32_t fl = 0;
         uint64_t h = 0;
-        int n = composite_pixel(rec, vals, s, e, x + 0.5, y + 0.5, 0.0, rgb, &Tf, &lst, &fl, &h, cb);
+        int n = composite_pixel(rec, vals, s, e, x + 0.5, y + 0.5, &tol0, rgb, &Tf, &lst, &fl, &h, cb, NULL);
         double gC[3];
         for (int c = 0; c < 3; ++c) gC[c] = dimg[3 * poff[v] + (int64_t)c * W * H + (int64_t)y * W + x];
         /* S = colour composited behind contributor i (incl. background) */
@@ -955,9 +1112,11 @@ void or_scatter_grad(const double *soa, int64_t G, int64_t N, int D, int sh_deg,
  * does.  pix[3*i..] = (view, x, y).  rgb[3*i..] and Tout[i] are written.
  */
 void or_render_pixels(const double *rec, int V, int64_t N, const double *views, int T,
-                      const double *bg, double m_tol, int64_t npix, const int32_t *pix,
-                      double *rgb_out, double *Tout, uint8_t *border) {
-  (void)V;
+                      const double *bg, double m_tol, double q_rel, int64_t npix, const int32_t *pix,
+                      double *rgb_out, double *Tout, uint8_t *border, double *bnd) {
+  tol_t tol;
+  double *mt, *zt;
+  make_tol(&tol, rec, V, N, views, m_tol, q_rel, bg, &mt, &zt);
   entry_t *e = (entry_t *)malloc(sizeof(entry_t) * (N > 0 ? N : 1));
   uint32_t *vals = (uint32_t *)malloc(sizeof(uint32_t) * (N > 0 ? N : 1));
   for (int64_t i = 0; i < npix; ++i) {
@@ -981,13 +1140,16 @@ void or_render_pixels(const double *rec, int V, int64_t N, const double *views, 
     int64_t lst;
     uint32_t fl = 0;
     uint64_t h = 0;
-    composite_pixel(rec, vals, 0, n, x + 0.5, y + 0.5, m_tol, rgb, &Tv, &lst, &fl, &h, NULL);
+    composite_pixel(rec, vals, 0, n, x + 0.5, y + 0.5, &tol, rgb, &Tv, &lst, &fl, &h, NULL,
+                    bnd ? bnd + 2 * i : NULL);
     for (int c = 0; c < 3; ++c) rgb_out[3 * i + c] = rgb[c] + Tv * bg[c];
     Tout[i] = Tv;
     border[i] = (uint8_t)fl;
   }
   free(e);
   free(vals);
+  free(mt);
+  free(zt);
 }
 
 /* ------------------------------------------------------------------------ */

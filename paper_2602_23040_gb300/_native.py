@@ -47,7 +47,7 @@ class View(C.Structure):
 class Options(C.Structure):
     _fields_ = [("tile", C.c_int32), ("znear", C.c_float), ("bg", C.c_float * 3), ("max_dups", C.c_uint64),
                 ("bin_mode", C.c_int32), ("batch", C.c_int32), ("stage_fwd", C.c_int32), ("stage_bwd", C.c_int32),
-                ("batch_bwd", C.c_int32)]
+                ("batch_bwd", C.c_int32), ("first_wait_polls", C.c_int32)]
 
 
 class Sizes(C.Structure):
@@ -61,7 +61,7 @@ class Sizes(C.Structure):
 class DeviceStatus(C.Structure):
     _fields_ = [("flags", C.c_uint32), ("live_seen", C.c_uint32), ("dups", C.c_uint64),
                 ("dups_needed", C.c_uint64), ("valid_pairs", C.c_uint64), ("evals_fwd", C.c_uint64),
-                ("evals_bwd", C.c_uint64), ("loss", C.c_double), ("ssim", C.c_double)]
+                ("evals_bwd", C.c_uint64), ("loss", C.c_double), ("ssim", C.c_double), ("nonfinite", C.c_uint64)]
 
 
 P = C.c_void_p

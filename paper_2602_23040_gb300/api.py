@@ -74,12 +74,13 @@ class Plan:
     def __init__(self, levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple[int, int],
                  sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 32,
                  znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse",
-                 batch: int = 128, stage_fwd: str = "loads", stage_bwd: str = "loads", batch_bwd: int = None):
+                 batch: int = 128, stage_fwd: str = "loads", stage_bwd: str = "loads", batch_bwd: int = None,
+                 first_wait_polls: int = 0):
         lib = N.load()
         self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
                           texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
                           bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode, batch=batch, stage_fwd=stage_fwd,
-                          stage_bwd=stage_bwd, batch_bwd=batch_bwd)
+                          stage_bwd=stage_bwd, batch_bwd=batch_bwd, first_wait_polls=first_wait_polls)
         if batch_bwd is None:
             batch_bwd = batch
         d = N.AtlasDesc()
@@ -98,6 +99,7 @@ class Plan:
         o.stage_fwd = STAGE_MODES[stage_fwd]
         o.stage_bwd = STAGE_MODES[stage_bwd]
         o.batch_bwd = int(batch_bwd)
+        o.first_wait_polls = int(first_wait_polls)
         self.bin_mode = bin_mode
         self.batch = int(batch)
         self.batch_bwd = int(batch_bwd)
@@ -359,9 +361,10 @@ def bin_and_sort_noalloc(plan: Plan, records, sorted_vals, tile_ranges, n_entrie
     example code running inside another framework's frame loop, where device
     allocation is not allowed).  The scratch is a fixed 64 MiB array inside
     the library; ``n_entries`` (one int32 on the device) receives the entry
-    count, or -1 (0xFFFFFFFF) if the entries exceeded ``plan.max_dups``.
-    Calls that overlap on the GPU share that array and must not run
-    concurrently."""
+    count, -1 (0xFFFFFFFF) if the entries exceeded ``plan.max_dups``, or -2
+    (0xFFFFFFFE) if a bounded device wait gave up or an index check failed
+    (nothing emitted).  Calls that overlap on the GPU share that array and
+    must not run concurrently."""
     rc = N.load().pk_bin_and_sort_noalloc(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
         _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups),

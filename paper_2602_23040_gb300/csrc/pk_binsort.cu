@@ -320,7 +320,11 @@ struct SrcValid {      // 1 if pair i touches a tile
 };
 struct SrcSorted {     // tile count of the i-th pair in depth order
   const uint32_t *cnt, *pval;
-  __device__ uint32_t operator()(uint64_t i) const { return cnt[pval[i]]; }
+  uint64_t pairs;      // a pair index past the pairs (a depth pass that gave up) counts 0
+  __device__ uint32_t operator()(uint64_t i) const {
+    const uint32_t p = pval[i];
+    return p < pairs ? cnt[p] : 0u;
+  }
 };
 
 __device__ __forceinline__ uint64_t load_n(const uint32_t *n_dev, uint64_t n_host) {
@@ -380,7 +384,10 @@ __global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, 
       status->valid_pairs = total;
     } else {
       status->dups_needed = total;
-      if (total > max_dups) {
+      if (ctr->sort_abort) {   // a depth pass gave up: emit nothing
+        ctr->dups = 0;
+        status->dups = 0;
+      } else if (total > max_dups) {
         ctr->dups = 0;
         status->dups = 0;
         atomicOr(&status->flags, PK_DEV_CAPACITY);
@@ -613,7 +620,8 @@ template <int RB, int IT>
 __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist, pk_device_status *status, SegSpec sp) {
+    const uint32_t *__restrict__ hist, pk_device_status *status, SegSpec sp, uint32_t *abort_flag,
+    uint32_t first_polls) {
   using C = Radix<RB, IT>;
   constexpr int kTile = C::kTile;
   constexpr int kSpan = Down<RB, IT>::kSpan;
@@ -667,7 +675,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     // the other buffer was last written (by this block's scatter) before the
     // fence and barrier that ended the previous tile
     if (tid == 0 && t + 1 < ntile) issue(t + 1);
-    const bool ok = mbar_wait_bounded(&s_bar[cur], parity[cur]);
+    const bool ok = mbar_wait_bounded(&s_bar[cur], parity[cur], first_polls);
     // keys past the last whole 16-byte group come by plain loads; a tile
     // that ends before the first group boundary (mis + valid < 4: nothing
     // was copied) loads all its keys that way.  The start stays unsigned
@@ -753,6 +761,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
       const uint32_t o = s_gbase[d] + (i - s_start[d]);
       if (o >= n) {   // a histogram out of step with the keys: never write past the items
         atomicOr(&status->flags, PK_DEV_BOUNDS);
+        *abort_flag = 1u;
         continue;
       }
       kout[o] = k;
@@ -764,7 +773,10 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     fence_proxy_async();   // this buffer's generic writes before the next TMA into it
     __syncthreads();
   }
-  if (s_abort && tid == 0) atomicOr(&status->flags, PK_DEV_TIMEOUT);
+  if (s_abort && tid == 0) {
+    atomicOr(&status->flags, PK_DEV_TIMEOUT);
+    *abort_flag = 1u;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -774,8 +786,8 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
 
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
                                                    const uint32_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
-                                                   const DevCounters *ctr, const DevView *__restrict__ views,
-                                                   int64_t N, int T, int mode, int local_bits,
+                                                   DevCounters *ctr, const DevView *__restrict__ views,
+                                                   int64_t N, int64_t pairs, int T, int mode, int local_bits,
                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                                    pk_device_status *status) {
   __shared__ WarpSplat s_ws[kWarps][32];
@@ -799,6 +811,11 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       // candidates, the mask of the receiving ones: the record is read
       // again only for a larger footprint
       p = pval[k];
+      if ((uint64_t)p >= (uint64_t)pairs) {   // never index past the pairs
+        atomicOr(&status->flags, PK_DEV_BOUNDS);
+        ctr->sort_abort = 1u;
+        p = 0;
+      }
       const uint4 info = __ldg(pinfo + p);
       const int x0 = (int)(info.z & 0xffffu), y0 = (int)(info.z >> 16);
       const int wt = (int)(info.w & 0xffffu), ht = (int)(info.w >> 16);
@@ -861,6 +878,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
           vals[at] = o_p;
         } else {   // more receiving tiles than counted: never write past the entries
           atomicOr(&status->flags, PK_DEV_BOUNDS);
+          ctr->sort_abort = 1u;
         }
       }
       written += __popc(bal);
@@ -877,7 +895,7 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
                                                      const uint32_t *__restrict__ toff, const DevCounters *ctr,
                                                      uint32_t *__restrict__ ranges, int V, uint32_t n_tiles,
                                                      pk_device_status *status) {
-  const uint32_t n = ctr->dups;
+  const uint32_t n = ctr->sort_abort ? 0u : ctr->dups;   // a pass gave up: every range stays empty
   const uint32_t nq = (n + 3) / 4;
   const uint32_t lmask = (1u << local_bits) - 1u;
   for (uint32_t q = blockIdx.x * kThreads + threadIdx.x; q < nq; q += gridDim.x * kThreads) {
@@ -948,7 +966,8 @@ __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__re
 template <int RB, int IT>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                        pk_device_status *status, SegSpec sp, cudaStream_t st) {
+                        pk_device_status *status, SegSpec sp, uint32_t *abort_flag, uint32_t first_polls,
+                        cudaStream_t st) {
   using C = Radix<RB, IT>;
   if (cudaFuncSetAttribute(k_radix_downsweep<RB, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Down<RB, IT>::kSmem) != cudaSuccess)
@@ -956,8 +975,8 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
   const uint32_t mask = (1u << bits) - 1u;
   k_radix_upsweep<RB, IT><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist, sp);
   k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
-  k_radix_downsweep<RB, IT><<<nblocks, kThreads, Down<RB, IT>::kSmem, st>>>(kin, vin, kout, vout, n_dev, n_host,
-                                                                              shift, mask, hist, status, sp);
+  k_radix_downsweep<RB, IT><<<nblocks, kThreads, Down<RB, IT>::kSmem, st>>>(
+      kin, vin, kout, vout, n_dev, n_host, shift, mask, hist, status, sp, abort_flag, first_polls);
   return check_launch();
 }
 
@@ -968,12 +987,13 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 // scattered short runs and came out slower overall.)
 pk_status radix_pass(bool entries, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                     pk_device_status *status, cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}) {
+                     pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls, cudaStream_t st,
+                     SegSpec sp = SegSpec{nullptr, nullptr}) {
   if (entries)
     return radix_pass_rb<kMaxRadixBits, kEntryItems>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks,
-                                                      status, sp, st);
+                                                      status, sp, abort_flag, first_polls, st);
   return radix_pass_rb<kMaxRadixBits, kPairItems>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks,
-                                                   status, sp, st);
+                                                   status, sp, abort_flag, first_polls, st);
 }
 
 int sm_count() {
@@ -1088,7 +1108,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   uint32_t *vseg = at<uint32_t>(ws, L.vseg), *pseg = vseg + (p->V + 1);
 
   pk_status ze = zero_async({{tile_ranges, sizeof(uint32_t) * 2 * (size_t)p->n_tiles},
-                             {ctr, pairs == 0 ? sizeof(DevCounters) : 0}},
+                             {ctr, pairs == 0 ? sizeof(DevCounters) : 0},
+                             {&ctr->sort_abort, pairs == 0 ? 0 : sizeof(uint32_t)}},
                             st);
   if (ze != PK_OK || pairs == 0) return ze;
   const int cblocks = (int)std::min<uint64_t>((pairs + kThreads - 1) / kThreads, 152 * 16);
@@ -1113,13 +1134,13 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
     if ((e = radix_pass(false, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist,
-                        seg ? npseg : pair_blocks(), status, st, psp)) != PK_OK)
+                        seg ? npseg : pair_blocks(), status, &ctr->sort_abort, p->first_polls, st, psp)) != PK_OK)
       return e;
     shift += widths[pass];
   }
   const uint32_t *pval = pv[np & 1];
   // emission offsets in (view,) depth order, capacity check
-  SrcSorted ss{cnt, pval};
+  SrcSorted ss{cnt, pval, pairs};
   k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, maxd, ctr, status);
   k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, bsum, ctr, offs);
@@ -1137,7 +1158,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   np = radix_plan(key_bits, widths);
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
-  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->T,
+  k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->pairs, p->T,
                                                       p->opts.bin_mode, seg ? key_bits : 0, kbuf[0], vbuf[0],
                                                       status);
   // Digits from the top down: each tile's entries still end up contiguous
@@ -1151,7 +1172,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     const int a = pass & 1, b = a ^ 1;
     shift -= widths[pass];
     if ((e = radix_pass(true, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
-                        status, st, sp)) != PK_OK)
+                        status, &ctr->sort_abort, p->first_polls, st, sp)) != PK_OK)
       return e;
   }
   k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], seg ? key_bits : 0,
@@ -1192,11 +1213,10 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
 //
 // Some callers cannot hand the library a workspace: a host application that
 // drives the renderer from inside another framework's frame callback, where
-// device allocation is forbidden (it would stall the frame or break the
-// framework's pre-recorded CUDA graph), or a small tool with no device
-// allocator of its own.  This entry point keeps its scratch in one
-// file-scope device array instead, sized once for every process that loads
-// the library.
+// that framework owns every device allocation and allocating would stall
+// the frame, or a small tool with no device allocator of its own.  This
+// entry point keeps its scratch in one file-scope device array instead,
+// sized once for every process that loads the library.
 // ---------------------------------------------------------------------------
 
 #include <mutex>
@@ -1226,8 +1246,14 @@ pk_status static_scratch(void **out) {
   return PK_OK;
 }
 
+// The call's outcome in one word: the entries, or a sentinel -- the status
+// block lives in the static array, where the caller's pk_read_status cannot
+// reach it.
 __global__ void k_report_entries(const DevCounters *ctr, const pk_device_status *status, uint32_t *n_entries) {
-  *n_entries = (status->flags & PK_DEV_CAPACITY) ? 0xffffffffu : ctr->dups;
+  const uint32_t f = status->flags;
+  *n_entries = (f & PK_DEV_CAPACITY) ? 0xffffffffu
+                                     : ((f & (PK_DEV_TIMEOUT | PK_DEV_BOUNDS)) || ctr->sort_abort) ? 0xfffffffeu
+                                                                                                    : ctr->dups;
 }
 
 }  // namespace
@@ -1271,7 +1297,7 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // the array keeps the previous call's contents: reset the status and
   // counters, refresh this plan's view table
-  if (cudaMemsetAsync(at<char>(ws, L.status), 0, L.views - L.status, st) != cudaSuccess) return PK_ERR_CUDA;
+  if ((e = zero_async({{at<char>(ws, L.status), L.views - L.status}}, st)) != PK_OK) return e;
   if (cudaMemcpyAsync(at<char>(ws, L.views), p->h_views, sizeof(DevView) * p->V, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return PK_ERR_CUDA;

@@ -58,7 +58,8 @@ struct DevCounters {
   double loss_acc;         // sum of |image - target| of the last loss call
   double ssim_acc;         // sum of the SSIM map of the last photometric loss call
   float ssim_lambda;       // its lambda (0 after pk_l1_loss_grad)
-  uint32_t pad;
+  uint32_t sort_abort;     // this bin_and_sort call gave up (a wait timed out or an index check
+                           // failed): it emits nothing; cleared at the start of each call
 };
 
 // Byte offsets of every region inside the workspace.
@@ -85,6 +86,7 @@ struct pk_plan {
   uint64_t max_dups;
   int32_t tile_bits;       // bits needed for a global tile id
   int32_t num_sms;
+  uint32_t first_polls;    // polls of the first bounded wait on a bulk-copied batch
   pk::WsLayout ws;
   pk::DevView *h_views;    // host copies uploaded by pk_workspace_init
   uint32_t *h_toff;        // [V+1] tile offsets (global tile id -> view)

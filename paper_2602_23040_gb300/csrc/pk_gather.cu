@@ -56,6 +56,7 @@ __global__ __launch_bounds__(kScanThreads) void k_word_scan(const uint32_t *__re
   if (tid == 0) {
     woff[nwords] = s_carry;
     status->live_seen = s_carry;
+    status->nonfinite = 0;   // counted by the gather kernel that follows
     if ((int64_t)s_carry != N) atomicOr(&status->flags, PK_DEV_LIVE_MISMATCH);
   }
 }
@@ -116,8 +117,9 @@ __global__ __launch_bounds__(256) void k_gather(const Tex *__restrict__ atlas, c
                                                 const uint32_t *__restrict__ dyn, const uint32_t *__restrict__ woff,
                                                 int W, int H, int F, int D, int64_t N,
                                                 float *__restrict__ soa, uint32_t *__restrict__ texel,
-                                                uint8_t *__restrict__ dynflag) {
+                                                uint8_t *__restrict__ dynflag, pk_device_status *status) {
   const int Wq = (W + 3) / 4;
+  uint32_t nbad = 0;   // (frame, Gaussian) pairs of this thread with a non-finite texel value
   const int64_t nq = (int64_t)Wq * H;
   const int64_t plane = (int64_t)W * H;
   const int64_t G = (int64_t)F * N;
@@ -128,6 +130,7 @@ __global__ __launch_bounds__(256) void k_gather(const Tex *__restrict__ atlas, c
     if (!quad_live(occ, dyn, woff, W, y, x0, N, texel, dynflag, live, gidx)) continue;
     const int64_t pix = (int64_t)y * W + x0;
     for (int f = 0; f < F; ++f) {
+      uint32_t bad = 0;   // bit i: texel i has a non-finite value in some channel of frame f
 #pragma unroll 4
       for (int c = 0; c < D; ++c) {
         const Tex *src = atlas + ((int64_t)f * D + c) * plane + pix;
@@ -136,15 +139,27 @@ __global__ __launch_bounds__(256) void k_gather(const Tex *__restrict__ atlas, c
           typename Quad<Tex>::V v = __ldg(reinterpret_cast<const typename Quad<Tex>::V *>(src));
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (live[i]) dst[gidx[i]] = Quad<Tex>::get(v, i);
+            if (live[i]) {
+              const float x = Quad<Tex>::get(v, i);
+              dst[gidx[i]] = x;
+              bad |= (uint32_t)!isfinite(x) << i;
+            }
         } else {
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (live[i]) dst[gidx[i]] = Quad<Tex>::one(src + i);
+            if (live[i]) {
+              const float x = Quad<Tex>::one(src + i);
+              dst[gidx[i]] = x;
+              bad |= (uint32_t)!isfinite(x) << i;
+            }
         }
       }
+      nbad += __popc(bad);
     }
   }
+  // one atomic per warp
+  const uint32_t wbad = __reduce_add_sync(0xffffffffu, nbad);
+  if ((threadIdx.x & 31) == 0 && wbad) atomicAdd(reinterpret_cast<unsigned long long *>(&status->nonfinite), wbad);
 }
 
 // Low-precision proxy (Sec. 4.2 "Low Precision Optimization"): channel c
@@ -255,15 +270,18 @@ extern "C" pk_status pk_atlas_gather(const pk_plan *p, const void *atlas, const 
   if (p->desc.texel_type == PK_TEXEL_F16) {
     auto a = reinterpret_cast<const __half *>(atlas);
     if (vec)
-      k_gather<__half, true><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+      k_gather<__half, true><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag, status);
     else
-      k_gather<__half, false><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+      k_gather<__half, false><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag,
+                                                      status);
   } else {
     auto a = reinterpret_cast<const float *>(atlas);
     if (vec)
-      k_gather<float, true><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+      k_gather<float, true><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag,
+                                                    status);
     else
-      k_gather<float, false><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag);
+      k_gather<float, false><<<blocks, 256, 0, st>>>(a, occ, dyn, woff, W, H, p->F, p->D, p->N, soa, texel, dynflag,
+                                                     status);
   }
   return check_launch();
 }

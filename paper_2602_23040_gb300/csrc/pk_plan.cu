@@ -7,6 +7,7 @@
 #include <new>
 
 #include "pk_common.cuh"
+#include "pk_tma.cuh"
 
 using namespace pk;
 
@@ -175,7 +176,9 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   o.stage_fwd = PK_STAGE_LOADS;
   o.stage_bwd = PK_STAGE_LOADS;
   o.batch_bwd = 128;
+  o.first_wait_polls = 0;
   if (opts) o = *opts;
+  if (o.first_wait_polls < -1) return PK_ERR_ARG;
   if (o.bin_mode != PK_BIN_RECT && o.bin_mode != PK_BIN_ELLIPSE) return PK_ERR_ARG;
   if (o.batch == 0) o.batch = 128;
   if (o.batch_bwd == 0) o.batch_bwd = 128;
@@ -223,6 +226,7 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   p->P = P;
   p->n_tiles = tiles;
   p->max_dups = maxd;
+  p->first_polls = o.first_wait_polls == 0 ? kWaitPolls : (o.first_wait_polls < 0 ? 0u : (uint32_t)o.first_wait_polls);
   int bits = 1;
   while ((int64_t(1) << bits) < tiles) ++bits;
   p->tile_bits = bits;

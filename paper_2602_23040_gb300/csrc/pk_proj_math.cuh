@@ -121,6 +121,7 @@ struct Act {
   float R[9];      // rotation of qn, row-major
   float S[6];      // Sigma3D: xx, xy, xz, yy, yz, zz
   float o;         // sigmoid(logit)
+  bool finite;     // channels 0..10 (position, log-scale, quaternion, opacity logit) all finite
 };
 
 // attr(c) reads channel c of this Gaussian.
@@ -129,10 +130,13 @@ __device__ __forceinline__ void activate(const Get &attr, Act &a) {
   a.mu[0] = attr(0);
   a.mu[1] = attr(1);
   a.mu[2] = attr(2);
-  a.s[0] = expf(attr(3));
-  a.s[1] = expf(attr(4));
-  a.s[2] = expf(attr(5));
+  const float l0 = attr(3), l1 = attr(4), l2 = attr(5), logit = attr(10);
+  a.s[0] = expf(l0);
+  a.s[1] = expf(l1);
+  a.s[2] = expf(l2);
   float qw = attr(6), qx = attr(7), qy = attr(8), qz = attr(9);
+  a.finite = isfinite(a.mu[0]) && isfinite(a.mu[1]) && isfinite(a.mu[2]) && isfinite(l0) && isfinite(l1) &&
+             isfinite(l2) && isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(logit);
   float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
   a.qinv = rsqrtf(n2);
   qw *= a.qinv; qx *= a.qinv; qy *= a.qinv; qz *= a.qinv;
@@ -149,7 +153,7 @@ __device__ __forceinline__ void activate(const Get &attr, Act &a) {
   a.S[3] = R[3] * R[3] * s0 + R[4] * R[4] * s1 + R[5] * R[5] * s2;
   a.S[4] = R[3] * R[6] * s0 + R[4] * R[7] * s1 + R[5] * R[8] * s2;
   a.S[5] = R[6] * R[6] * s0 + R[7] * R[7] * s1 + R[8] * R[8] * s2;
-  a.o = 1.f / (1.f + expf(-attr(10)));
+  a.o = 1.f / (1.f + expf(-logit));
 }
 
 // Per-view projection of one activated Gaussian.

@@ -30,17 +30,22 @@ __global__ __launch_bounds__(kProjThreads) void k_project(const float *__restric
     Act a;
     activate(attr, a);
     auto k = [&](int j, int c) -> float & { return s_k[(3 * j + c) * kProjThreads + threadIdx.x]; };
+    bool finite = a.finite;   // a Gaussian with a non-finite texel value is culled in every view
 #pragma unroll
     for (int j = 0; j < NB; ++j)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) k(j, c) = attr(11 + 3 * j + c);
+      for (int c = 0; c < 3; ++c) {
+        const float kv = attr(11 + 3 * j + c);
+        k(j, c) = kv;
+        finite = finite && isfinite(kv);
+      }
     const int vb = __ldg(fview_off + f), ve = __ldg(fview_off + f + 1);
     for (int vi = vb; vi < ve; ++vi) {
       const int v = __ldg(fview_idx + vi);
       const DevView &view = views[v];
       float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
       Proj p;
-      bool ok = project(a, view, znear, p);
+      bool ok = finite && project(a, view, znear, p);
       if (ok) {
         float d[3], len;
         view_dir(a, view, d, len);

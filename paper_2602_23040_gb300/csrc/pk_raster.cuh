@@ -116,7 +116,24 @@ __device__ __forceinline__ void stage_from(const float4 r0, const float4 r1, con
   s.box[j] = box;
 }
 
-__device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint32_t pid, const Staged &s, int j) {
+// A list entry that names no pair of the plan (a list that pk_bin_and_sort
+// did not write for this plan): staged as a splat that reaches no pixel.
+constexpr uint32_t kNoPair = 0xffffffffu;   // never a pair index (pairs < 2^32 - 1)
+__device__ __forceinline__ void stage_none(const Staged &s, int j) {
+  s.a[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  s.b[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  s.c[j] = make_float4(0.f, __uint_as_float(kNoPair), INFINITY, 0.f);
+  s.q[j] = make_float4(0.f, 0.f, 0.f, -1.f);
+  s.box[j] = make_float4(1.f, -1.f, 1.f, -1.f);   // misses every block
+}
+
+__device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint32_t pid, uint32_t npairs,
+                                            const Staged &s, int j, pk_device_status *status) {
+  if (pid >= npairs) {
+    stage_none(s, j);
+    atomicOr(&status->flags, PK_DEV_BOUNDS);
+    return;
+  }
   const float4 *r = reinterpret_cast<const float4 *>(rec + (size_t)pid * kRec);
   stage_from(__ldg(r), __ldg(r + 1), __ldg(r + 2), pid, s, j);
 }

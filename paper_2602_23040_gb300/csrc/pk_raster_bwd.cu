@@ -157,7 +157,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
     const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out,
-    pk_device_status *status) {
+    pk_device_status *status, uint32_t first_polls, uint32_t npairs) {
   using G = Geo<kPx>;
   constexpr uint32_t kQuads = (kT / kTileSide) * (kT / kTileSide);   // CTAs per list tile
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
@@ -187,8 +187,9 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
   auto fetch = [&](uint32_t b, int nb) {
     for (int j = tid; j < nb; j += G::kThreads) {
       const uint32_t pid = __ldg(vals + b + j);
-      s_pid[j] = pid;
-      tma_load_1d(&s_raw[3 * j], rec + (size_t)pid * kRec, 3 * sizeof(float4), &s_bar);
+      const bool named = pid < npairs;   // else record 0 is fetched in its place and not used
+      s_pid[j] = named ? pid : kNoPair;
+      tma_load_1d(&s_raw[3 * j], rec + (size_t)(named ? pid : 0u) * kRec, 3 * sizeof(float4), &s_bar);
     }
   };
   for (;;) {
@@ -216,7 +217,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
     const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
     const float wx0 = (float)(X0 + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
     const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + 7.f;
-    const uint32_t s = __ldg(ranges + 2 * (size_t)t);
+    const uint32_t s = __ldg(ranges + 2 * (size_t)t), len = __ldg(ranges + 2 * (size_t)t + 1) - s;
     const size_t plane = (size_t)W * H;
     float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx], pyq[kPx];
     uint32_t nc[kPx];
@@ -232,7 +233,9 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
         const size_t pix = (size_t)view.pix_off + (size_t)y * W + x;
         const float *gi = dimg + 3 * (size_t)view.pix_off + (size_t)y * W + x;
         T[q] = Tfin[pix];
-        nc[q] = ncontrib[pix];
+        // a count past the tile's list (n_contrib not written by the forward
+        // of these lists) reads no entry beyond it
+        nc[q] = min(ncontrib[pix], len);
         g0[q] = gi[0];
         g1[q] = gi[plane];
         g2[q] = gi[2 * plane];
@@ -257,7 +260,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
       const uint32_t beg = end > (uint32_t)kBatch ? end - kBatch : 0u;
       const int nb = (int)(end - beg);
       if (kTma) {
-        if (!mbar_wait_bounded(&s_bar, phase)) {
+        if (!mbar_wait_bounded(&s_bar, phase, first_polls)) {
           timed_out = true;
           mbar_wait_bounded(&s_bar, phase);   // let this batch's copies land before leaving
         }
@@ -265,7 +268,14 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
         __syncthreads();   // every warp is done with the previous batch's staged values
 #pragma unroll
         for (int j = tid; j < kBatch; j += G::kThreads)
-          if (j < nb) stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
+          if (j < nb) {
+            if (s_pid[j] == kNoPair) {
+              stage_none(st, j);
+              atomicOr(&status->flags, PK_DEV_BOUNDS);
+            } else {
+              stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
+            }
+          }
         fence_proxy_async();   // these reads of s_raw before the next bulk writes into it
         const uint32_t nbeg = beg > (uint32_t)kBatch ? beg - kBatch : 0u;
         if (tid == 0 && beg > 0) mbar_expect_tx(&s_bar, (beg - nbeg) * 3u * (uint32_t)sizeof(float4));
@@ -278,7 +288,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
         __syncthreads();
 #pragma unroll
         for (int j = tid; j < kBatch; j += G::kThreads)
-          if (j < nb) stage_splat(rec, __ldg(vals + s + beg + j), st, j);
+          if (j < nb) stage_splat(rec, __ldg(vals + s + beg + j), npairs, st, j, status);
         __syncthreads();
       }
       // splats that can reach this warp's block and that some pixel of the
@@ -303,11 +313,14 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
           const f32x2 z2 = dup2(0.f);
           AdjSums sums{z2, z2, z2, z2, z2, z2, z2};
           bool act = false;
+          uint32_t on = 0;   // bit h: pixel h blended or skipped this splat in the forward
+#pragma unroll
+          for (int h = 0; h < kPx; ++h) on |= (uint32_t)(pos < nc[h]) << h;
+          evals += __popc(on);
 #pragma unroll
           for (int h = 0; h < kPx; h += 2) {
-            const bool e0 = pos < nc[h], e1 = pos < nc[h + 1];
+            const bool e0 = (on >> h) & 1u, e1 = (on >> (h + 1)) & 1u;
             if (!(e0 || e1)) continue;
-            evals += (uint32_t)e0 + (uint32_t)e1;
             act |= pixel_adjoint2(a, b, c4, dx, zx, pack2(pyq[h], pyq[h + 1]), e0, e1, pack2(g0[h], g0[h + 1]),
                                   pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]), T[h], T[h + 1], GS[h],
                                   GS[h + 1], sums);
@@ -358,7 +371,7 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
   k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT><<<(int)grid, Geo<kBwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)items, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
-      &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd), status);
+      &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd), status, p->first_polls, (uint32_t)p->pairs);
   return check_launch();
 }
 

@@ -33,7 +33,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
     uint32_t *queue, unsigned long long *evals_out, pk_device_status *status, const float *__restrict__ target,
-    float *__restrict__ dimg, float scale, double *loss_acc) {
+    float *__restrict__ dimg, float scale, double *loss_acc, uint32_t first_polls, uint32_t npairs) {
   using G = Geo<kPx>;
   constexpr uint32_t kQuads = (kT / kTileSide) * (kT / kTileSide);   // CTAs per list tile
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
@@ -62,8 +62,9 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
   auto fetch = [&](uint32_t b, int nb) {
     for (int j = tid; j < nb; j += G::kThreads) {
       const uint32_t pid = __ldg(vals + b + j);
-      s_pid[j] = pid;
-      tma_load_1d(&s_raw[3 * j], rec + (size_t)pid * kRec, 3 * sizeof(float4), &s_bar);
+      const bool named = pid < npairs;   // else record 0 is fetched in its place and not used
+      s_pid[j] = named ? pid : kNoPair;
+      tma_load_1d(&s_raw[3 * j], rec + (size_t)(named ? pid : 0u) * kRec, 3 * sizeof(float4), &s_bar);
     }
   };
   for (;;) {
@@ -113,7 +114,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
     for (uint32_t base = s; base < e; base += kBatch) {
       const int nb = (int)min((uint32_t)kBatch, e - base);
       if (kTma) {
-        if (!mbar_wait_bounded(&s_bar, phase)) {
+        if (!mbar_wait_bounded(&s_bar, phase, first_polls)) {
           timed_out = true;
           mbar_wait_bounded(&s_bar, phase);   // let this batch's copies land before leaving
         }
@@ -121,7 +122,14 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
         pending = false;
 #pragma unroll
         for (int j = tid; j < kBatch; j += G::kThreads)
-          if (j < nb) stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
+          if (j < nb) {
+            if (s_pid[j] == kNoPair) {
+              stage_none(st, j);
+              atomicOr(&status->flags, PK_DEV_BOUNDS);
+            } else {
+              stage_from(s_raw[3 * j], s_raw[3 * j + 1], s_raw[3 * j + 2], s_pid[j], st, j);
+            }
+          }
         fence_proxy_async();   // these reads of s_raw before the next bulk writes into it
         const uint32_t nxt = base + kBatch;
         const int nbn = nxt < e ? (int)min((uint32_t)kBatch, e - nxt) : 0;
@@ -138,7 +146,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
         __syncthreads();
 #pragma unroll
         for (int j = tid; j < kBatch; j += G::kThreads)
-          if (j < nb) stage_splat(rec, __ldg(vals + base + j), st, j);
+          if (j < nb) stage_splat(rec, __ldg(vals + base + j), npairs, st, j, status);
         __syncthreads();
       }
       if (__any_sync(0xffffffffu, live != 0)) {
@@ -161,10 +169,10 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
             const float4 a = s_a[j], b = s_b[j], c = s_c[j];
             const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
             const uint32_t pos1 = base - s + (uint32_t)j + 1u;
+            evals += __popc(live);   // this splat is evaluated at every live pixel of the thread
 #pragma unroll
             for (int q = 0; q < kPx; ++q) {
               if (!((live >> q) & 1u)) continue;
-              ++evals;
               Hit h;
               if (splat_alpha(a, b, c.z, dx, zx, py0 + (float)(q * G::kRowStep), h)) {
                 const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, h.alpha));
@@ -261,7 +269,7 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)items, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
       &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status, target, dimg,
-      (float)(1.0 / (3.0 * (double)std::max<int64_t>(1, p->P))), &ctr->loss_acc);
+      (float)(1.0 / (3.0 * (double)std::max<int64_t>(1, p->P))), &ctr->loss_acc, p->first_polls, (uint32_t)p->pairs);
   return check_launch();
 }
 

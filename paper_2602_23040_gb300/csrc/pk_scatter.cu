@@ -43,13 +43,21 @@ __global__ __launch_bounds__(kScatterThreads, 4) void k_scatter(const float *__r
     // of s_k / s_dk (each thread touches only its own column)
     auto k = [&](int j, int c) -> float & { return s_k[(3 * j + c) * kScatterThreads + threadIdx.x]; };
     auto dk = [&](int j, int c) -> float & { return s_k[(3 * (NB + j) + c) * kScatterThreads + threadIdx.x]; };
+    bool finite = a.finite;
 #pragma unroll
     for (int j = 0; j < NB; ++j)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        k(j, c) = attr(11 + 3 * j + c);
+        const float kv = attr(11 + 3 * j + c);
+        k(j, c) = kv;
         dk(j, c) = 0.f;
+        finite = finite && isfinite(kv);
       }
+    if (!finite) {   // culled in every view by the projection: a zero gradient
+      if (!accumulate)
+        for (int c = 0; c < D; ++c) dst[(int64_t)c * plane] = 0.f;
+      continue;
+    }
     float dmu[3] = {0.f, 0.f, 0.f};
     float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3D entries xx xy xz yy yz zz
     float dop = 0.f;

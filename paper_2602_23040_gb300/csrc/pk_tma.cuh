@@ -41,10 +41,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Generic-proxy writes to shared memory before async-proxy (TMA) writes.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Bounded wait: gives up after ~2^22 polls (each poll may block briefly).
+// Bounded wait: gives up after `polls` polls (each poll may block briefly;
+// the default ~2^22 polls last well under a few seconds).  The first wait
+// on each batch of a kernel takes the plan's limit (pk_options.
+// first_wait_polls), which a test can set to 0 so that the wait gives up at
+// once; every wait that drains copies already in flight keeps the default,
+// so no block leaves with a bulk copy still landing in its shared memory.
 constexpr uint32_t kWaitPolls = 1u << 22;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitPolls; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t polls = kWaitPolls) {
+  for (uint32_t i = 0; i < polls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

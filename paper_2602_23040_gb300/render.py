@@ -31,6 +31,9 @@ class Renderer:
         # reads the FP32 masters through the LPO quantiser (16-bit position,
         # 8-bit other channels) and the gradients pass it straight through.
         self.lohi: Optional[torch.Tensor] = None
+        # Forward passes run so far: the per-pixel state a backward reads
+        # (T_final, n_contrib, records, sorted lists) belongs to the latest.
+        self.generation = 0
         self._alloc()
 
     def _alloc(self):
@@ -52,6 +55,7 @@ class Renderer:
     # forward: a1 .. a4 (target: the L1 loss gradient fused into a4)
     def forward(self, atlas, occ, dyn=None, stream=None, target=None):
         p = self.plan
+        self.generation += 1
         self._has_dyn = dyn is not None
         if self.lohi is not None:
             api.atlas_gather_lpo(p, atlas, api.LPO_MASTERS, self.lohi, occ, dyn, self.soa, self.texel, self.dynflag,
@@ -212,6 +216,7 @@ class _RenderFn(torch.autograd.Function):
         src = master if proxy is None else proxy
         renderer.forward(src.detach().contiguous(), occ, dyn)
         ctx.renderer = renderer
+        ctx.generation = renderer.generation
         ctx.shape = master.shape
         ctx.device = master.device
         # the renderer keeps the per-pixel state for the backward; hand out a copy of the image
@@ -220,6 +225,11 @@ class _RenderFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_image):
         r: Renderer = ctx.renderer
+        if r.generation != ctx.generation:
+            # the buffers now hold a later forward's state: its gradients
+            # would be handed to this call's inputs
+            raise RuntimeError("render(): the Renderer ran another forward before this render's backward; "
+                               "call backward first or give each render its own Renderer")
         grad = torch.zeros(ctx.shape, dtype=torch.float32, device=ctx.device)
         r.backward(grad_image.contiguous().float(), grad, accumulate=False)
         return grad, None, None, None, None
@@ -233,6 +243,8 @@ def render(master: torch.Tensor, renderer: Renderer, occ: torch.Tensor, dyn: Opt
     ``proxy`` (the FP16 texels actually read) is given, the gradient passes
     straight through it to ``master``.  Returns the concatenated planar
     images ``[3 * P]``; the gradient is zero on texels that are not live or
-    are frozen by ``dyn``.
+    are frozen by ``dyn``.  The renderer keeps the per-pixel state of its
+    latest forward only: a backward through an earlier ``render`` on the
+    same renderer raises instead of returning another call's gradients.
     """
     return _RenderFn.apply(master, renderer, proxy, occ, dyn)

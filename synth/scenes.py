@@ -111,10 +111,15 @@ def look_at(eye: Sequence[float], target: Sequence[float] = (0.0, 0.0, 0.0),
     return R, -R @ eye
 
 
+def _f32(x):
+    # cameras are generated in the precision the renderer's camera record carries (FP32)
+    return np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
+
+
 def pinhole(eye, width: int, height: int, fov_x_deg: float = 60.0, frame: int = 0) -> View:
     R, t = look_at(eye)
-    fx = (width / 2.0) / math.tan(math.radians(fov_x_deg) / 2.0)
-    return View(R=R, t=t, fx=fx, fy=fx, cx=width / 2.0, cy=height / 2.0,
+    fx = float(_f32((width / 2.0) / math.tan(math.radians(fov_x_deg) / 2.0)))
+    return View(R=_f32(R), t=_f32(t), fx=fx, fy=fx, cx=float(_f32(width / 2.0)), cy=float(_f32(height / 2.0)),
                 width=width, height=height, frame=frame)
 
 
@@ -248,8 +253,10 @@ def make_scene(levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple
                  views=views, n_live=n_live, tile=tile)
 
 
-def config_scene(k: int, n_views: Optional[int] = None, frame_start: int = 0) -> Scene:
-    """The five workload shapes, full size.  ``n_views`` truncates the view list."""
+def config_scene(k: int, n_views: Optional[int] = None, frame_start: int = 0, texel_dtype=None) -> Scene:
+    """The five workload shapes, full size.  ``n_views`` truncates the view list;
+    ``texel_dtype`` overrides the texel type (e.g. float32 gives the FP32
+    masters of the FP16 workload: the same values before rounding)."""
     seed = BASE_SEED + k
     if k == 1:
         views = [pinhole((0.0, 0.0, -3.5), 256, 256)]
@@ -270,7 +277,8 @@ def config_scene(k: int, n_views: Optional[int] = None, frame_start: int = 0) ->
         views = ring_views((6, 5, 5), (-1.0, 0.0, 1.0), 4.0, pick)
         levels = [(1024, 1024, 512, 0, 0), (512, 512, 0, 0, 0), (256, 256, 0, 512, 0)]
         sc = make_scene(levels, (1536, 1024), "uniform", views[:n_views] if n_views else views,
-                        texel_dtype=np.float16, seed=seed, name=CONFIG_NAMES[4])
+                        texel_dtype=np.float16 if texel_dtype is None else texel_dtype, seed=seed,
+                        name=CONFIG_NAMES[4])
     elif k == 5:
         F = 4
         views = []

@@ -48,25 +48,48 @@ def u32(t) -> np.ndarray:
     return t.cpu().numpy().view(np.uint32)
 
 
-def check_images(got_img, got_T, ora, tol=IMG_TOL, border_tol=0.05, max_border_frac=0.03):
-    """Non-borderline pixels within tol; borderline pixels bounded and rare."""
-    P = len(ora["T"])
-    border = ora["border"].astype(bool)
-    # per-channel mask in the planar-per-view layout
-    b3 = np.zeros(3 * P, bool)
+# Borderline bits of the oracle (oracle.B_*): image decisions only
+B_Q, B_ALPHA, B_STOP, B_DEPTH, B_CULL = 1, 2, 4, 8, 16
+IMAGE_BORDER = B_Q | B_ALPHA | B_STOP | B_DEPTH | B_CULL
+
+
+def per_channel(values, view_pixels):
+    """[P] per-pixel values -> [3P] in the planar-per-view image layout."""
+    out = np.empty(3 * len(values), values.dtype)
     off = 0
-    for n in ora["view_pixels"]:
+    for n in view_pixels:
         for c in range(3):
-            b3[3 * off + c * n:3 * off + (c + 1) * n] = border[off:off + n]
+            out[3 * off + c * n:3 * off + (c + 1) * n] = values[off:off + n]
         off += n
+    return out
+
+
+def check_images(got_img, got_T, ora, tol=IMG_TOL, max_border_frac=0.02, max_threshold_frac=2e-3, label=""):
+    """Every pixel within tol plus its own flip bound (the change the oracle
+    computed for its borderline decisions going the other way; 0 off the
+    borderline), colour and transmittance.  The borderline fraction is
+    printed; the depth-order part of it is bounded by max_border_frac, the
+    threshold part (q, alpha, stop, cull) by max_threshold_frac."""
+    border = (ora["border"] & IMAGE_BORDER) != 0
+    thresh = (ora["border"] & (IMAGE_BORDER & ~B_DEPTH)) != 0
+    bound = ora["bound"]
     err = np.abs(got_img.astype(np.float64) - ora["img"])
     Terr = np.abs(got_T.astype(np.float64) - ora["T"])
-    assert err[~b3].max(initial=0.0) <= tol, f"image max err {err[~b3].max()}"
-    assert Terr[~border].max(initial=0.0) <= tol, f"T max err {Terr[~border].max()}"
-    assert border.mean() <= max_border_frac, f"borderline fraction {border.mean()}"
-    if b3.any():
-        assert err[b3].max() <= border_tol
-    return dict(max_err=float(err[~b3].max(initial=0.0)), border=int(border.sum()))
+    lim = tol + per_channel(bound[:, 0], ora["view_pixels"])
+    over = err - lim
+    b3 = per_channel(border, ora["view_pixels"])
+    assert over.max(initial=-1.0) <= 0.0, \
+        f"{label} image err {err[over.argmax()]:.3g} over its limit {lim[over.argmax()]:.3g} (borderline {b3[over.argmax()]})"
+    overT = Terr - (tol + bound[:, 1])
+    assert overT.max(initial=-1.0) <= 0.0, f"{label} T err {Terr[overT.argmax()]:.3g}"
+    frac, tfrac = float(border.mean()), float(thresh.mean())
+    print(f"{label} borderline pixels: {frac:.2e} (thresholds {tfrac:.2e}, depth order {frac - tfrac:.2e}); "
+          f"max err off the borderline {err[~b3].max(initial=0.0):.2e}, on it {err[b3].max(initial=0.0):.2e} "
+          f"(largest bound {bound[:, 0].max(initial=0.0):.2e})")
+    assert frac <= max_border_frac, f"borderline fraction {frac}"
+    assert tfrac <= max_threshold_frac, f"threshold-borderline fraction {tfrac}"
+    return dict(max_err=float(err[~b3].max(initial=0.0)), max_err_border=float(err[b3].max(initial=0.0)),
+                border=int(border.sum()), border_frac=frac, threshold_frac=tfrac)
 
 
 def rel_err(a, b):
@@ -85,3 +108,46 @@ def check_grads(got, ref, rtol=GRAD_RTOL):
         out[name] = e
         assert e <= rtol, f"{name}: rel err {e}"
     return out
+
+
+def oracle_views(orc, scene, vsel, dimg_by_view=None, tile=16, threads=None, soa_texel=None):
+    """The FP64 oracle on the views vsel of a (large) scene, one thread per
+    view (the oracle's C routines run without the interpreter lock): per
+    view its own projection, lists, image with borderline bits and flip
+    bounds, and, given dL/dimage of the view, its backward and texel
+    gradient.  Returns images etc. concatenated over vsel in order, and
+    the gradient [D][F*N] summed over the views."""
+    import concurrent.futures as cf
+    import os
+    soa, texel, dynflag = soa_texel if soa_texel is not None else orc.gather(scene)
+    N = len(texel)
+    dyn = dynflag if scene.dyn is not None else None
+
+    def one(i):
+        v = vsel[i]
+        va = orc.views_array([scene.views[v]])
+        rec = orc.project(soa, N, scene.sh_degree, va)
+        vals, ranges = orc.bin_sort(rec, va, tile)
+        out = orc.render(rec, va, tile, vals, ranges)
+        g = None
+        if dimg_by_view is not None:
+            g2 = orc.render_bwd(rec, va, tile, vals, ranges, np.asarray(dimg_by_view[i], np.float64))
+            g = orc.scatter_grad(soa, N, scene.sh_degree, va, g2, dyn)
+        return out, g
+
+    n_thr = threads or min(len(vsel), os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(max_workers=n_thr) as ex:
+        res = list(ex.map(one, range(len(vsel))))
+    cat = lambda k: np.concatenate([r[0][k] for r in res])
+    o = dict(img=cat("img"), T=cat("T"), last=cat("last"), border=cat("border"),
+             bound=np.concatenate([r[0]["bound"] for r in res]),
+             view_pixels=[scene.views[v].width * scene.views[v].height for v in vsel], texel=texel, N=N)
+    if dimg_by_view is not None:
+        o["grad_soa"] = sum(r[1] for r in res)
+    return o
+
+
+def view_slices(scene, vsel):
+    """(image slice, pixel slice) of each view of vsel in the concatenated buffers."""
+    poff = np.cumsum([0] + [v.width * v.height for v in scene.views])
+    return [(slice(3 * poff[v], 3 * poff[v + 1]), slice(poff[v], poff[v + 1])) for v in vsel]

@@ -334,13 +334,15 @@ def test_rasterize_fwd_on_identical_records(orc, seed, tile):
     rec64[..., 11] = 0
     va = orc.views_array(o["views"])
     vals, ranges = orc.bin_sort(rec64, va, tile)
-    ref = orc.render(rec64, va, tile, vals, ranges, m_tol=1e-5)
+    # identical FP32 records on both sides: no mean error (m_tol 0), only the
+    # rounding of the quadratic form; the depth order is the same (the sort
+    # is bit-exact), so near-equal depths are not borderline here
+    ref = orc.render(rec64, va, tile, vals, ranges, m_tol=0.0)
     ref["view_pixels"] = [v.width * v.height for v in o["views"]]
-    # identical FP32 depths on both sides: the depth order is the same (the sort is bit-exact), so
-    # near-equal depths are not borderline here
-    ref["border"] = ref["border"] & ~np.uint8(8)
-    H.check_images(o["img"].cpu().numpy(), o["T"].cpu().numpy(), ref, tol=2e-5, max_border_frac=0.01)
-    ok = ref["border"] == 0
+    ref["border"] = ref["border"] & ~np.uint8(H.B_DEPTH)
+    H.check_images(o["img"].cpu().numpy(), o["T"].cpu().numpy(), ref, tol=2e-5, max_border_frac=1e-3,
+                   max_threshold_frac=1e-3, label=f"identical records seed {seed} tile {tile}")
+    ok = (ref["border"] & H.IMAGE_BORDER) == 0
     assert np.array_equal(H.u32(o["nc"])[ok], ref["last"][ok])
     st = _pk().read_status(o["plan"], o["ws"])
     assert st["evals_fwd"] > 0
@@ -405,57 +407,6 @@ def test_config2_full_size(orc):
     o = oracle_run(orc, sc, dimg=w)
     H.check_images(r.image.cpu().numpy(), r.T.cpu().numpy(), o)
     H.check_grads(gpu_grad_soa(sc, grad, o["texel"]), o["grad_soa"])
-
-
-def _check_sampled_pixels(orc, sc, vsel, seed, per_view=60):
-    """Full-size run in the bench's launch configuration; the oracle renders
-    sampled pixels of the views vsel one by one (FP64, from its own gather
-    and projection) and they must match the GPU's image and transmittance."""
-    plan, r, _ = run_gpu(sc)
-    st = r.status()
-    assert st["flags"] == 0 and st["dups"] > 0
-    img = r.image.cpu().numpy()
-    T = r.T.cpu().numpy()
-    del r
-    torch.cuda.empty_cache()
-    soa, texel, _ = orc.gather(sc)
-    rng = np.random.default_rng(seed)
-    va = orc.views_array([sc.views[v] for v in vsel])
-    rec = orc.project(soa, len(texel), sc.sh_degree, va)
-    pix = []
-    for i, v in enumerate(vsel):
-        vw = sc.views[v]
-        for _ in range(per_view):
-            pix.append((i, int(rng.integers(0, vw.width)), int(rng.integers(0, vw.height))))
-    rgb, Tr, border = orc.render_pixels(rec, va, 16, np.array(pix))
-    poff = np.cumsum([0] + [v.width * v.height for v in sc.views])
-    bad = 0
-    for k, (i, x, y) in enumerate(pix):
-        v = vsel[i]
-        vw = sc.views[v]
-        base = 3 * poff[v] + y * vw.width + x
-        got = np.array([img[base + c * vw.width * vw.height] for c in range(3)])
-        if border[k]:
-            continue
-        err = max(np.abs(got - rgb[k]).max(), abs(T[poff[v] + y * vw.width + x] - Tr[k]))
-        bad += err > H.IMG_TOL
-    assert bad == 0
-
-
-def test_config3_full_size_sampled_pixels(orc):
-    """The 52-view rig at full size, in the bench's launch configuration: sampled pixels."""
-    _check_sampled_pixels(orc, synth.config_scene(3), [0, 1, 25, 51], 13)
-
-
-def test_config5_full_size_sampled_pixels(orc):
-    """The largest workload, 4 frames x 52 views with dynamic texels (208
-    views, 690 M list entries, 2.5 M Gaussians), at full size: sampled pixels
-    of views in every frame."""
-    sc = synth.config_scene(5)
-    assert len(sc.views) == 208 and sc.frames == 4
-    vsel = [0, 53, 118, 207]
-    assert sorted({sc.views[v].frame for v in vsel}) == [0, 1, 2, 3]
-    _check_sampled_pixels(orc, sc, vsel, 15, per_view=40)
 
 
 def test_batched_equals_per_view_loop(orc):

@@ -223,8 +223,9 @@ def test_isotropic_gaussian_closed_form(orc):
     va = orc.views_array(sc.views)
     rec = orc.project(soa, 1, 0, va)[0, 0]
     v = sc.views[0]
+    fx = float(np.float32(v.fx))   # the camera the library receives is FP32
     z = 3.0
-    var = (v.fx * s / z) ** 2 + 0.3
+    var = (fx * s / z) ** 2 + 0.3
     assert abs(rec[0] - v.cx) < 1e-12 and abs(rec[1] - v.cy) < 1e-12
     assert np.allclose(rec[2:5], [1 / var, 0, 1 / var], rtol=1e-9, atol=1e-15)
     o = 1 / (1 + math.exp(-float(np.float32(0.7))))
@@ -349,7 +350,7 @@ def test_tiled_render_equals_bruteforce_and_tile_size(orc):
     f16 = orc.forward(sc, tile=16)
     # brute force over every splat of the view, per pixel
     pix = [(v, x, y) for v, vw in enumerate(views) for y in range(vw.height) for x in range(vw.width)]
-    rgb, T, _ = orc.render_pixels(f16["rec"], f16["views"], 16, np.array(pix))
+    rgb, T, _, _ = orc.render_pixels(f16["rec"], f16["views"], 16, np.array(pix))
     P0 = views[0].width * views[0].height
     img = f16["img"]
     got = np.concatenate([img[:3 * P0].reshape(3, -1).T, img[3 * P0:].reshape(3, -1).T])
@@ -623,3 +624,32 @@ def test_images_do_not_depend_on_tile_side(orc):
     assert out[16][0] != out[32][0]
     assert np.array_equal(out[16][1]["img"], out[32][1]["img"])
     assert np.array_equal(out[16][1]["T"], out[32][1]["T"])
+
+
+def test_nonfinite_texels_render_as_absent(orc):
+    """A Gaussian with a non-finite texel value (any channel) is culled in
+    every view: the oracle's images equal, bit for bit, those of the atlas
+    with those texels removed from the occupancy mask, and its gradient
+    there is zero."""
+    import dataclasses
+    sc = synth.make_scene([(40, 40, 0, 0, 0)], (40, 40), 0.6,
+                          [synth.scenes.pinhole((0.4, 0.3, -3.2), 80, 60),
+                           synth.scenes.pinhole((-2.6, -0.5, -1.8), 60, 72)],
+                          sh_degree=2, seed=8, log_scale=(-3.2, 0.5))
+    F, D, Hh, W = sc.atlas.shape
+    occ = synth.scenes.unpack_bits(sc.occ, W)
+    ys, xs = np.nonzero(occ)
+    pick = np.random.default_rng(2).choice(len(ys), 5, replace=False)
+    bad = sc.atlas.copy()
+    for i, (c, v) in zip(pick, [(0, np.nan), (5, np.inf), (9, np.nan), (10, -np.inf), (D - 1, np.nan)]):
+        bad[0, c, ys[i], xs[i]] = v
+    with_bad = dataclasses.replace(sc, atlas=bad)
+    occ2 = occ.copy()
+    occ2[ys[pick], xs[pick]] = False
+    without = dataclasses.replace(sc, occ=synth.pack_bits(occ2), n_live=sc.n_live - len(pick))
+    a, b = orc.forward(with_bad), orc.forward(without)
+    assert np.array_equal(a["img"], b["img"]) and np.array_equal(a["T"], b["T"])
+    assert np.all(a["rec"][:, pick, 7] == 0)
+    dimg = np.random.default_rng(3).standard_normal(len(a["img"]))
+    g = orc.backward(with_bad, a, dimg)["grad_soa"]
+    assert np.all(g[:, pick] == 0) and np.all(np.isfinite(g))
