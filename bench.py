@@ -33,12 +33,6 @@ import synth  # noqa: E402
 METRIC = "fwd+bwd rendered MPix/s on 1 GB300, batched vs per-view, % of HBM roofline"
 UNIT = "MPix/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
-# FP32 operations of one (pixel, splat) evaluation, counted from the method:
-# forward 17 (offset 2, quadratic form 5, exponent 2, alpha 2, transmittance
-# 2, blend 4); backward 45 (the forward's 10 to recompute alpha, transmittance
-# recovery 2, dL/dalpha 9, colour 6, opacity/conic/mean 14, warp sum share 4).
-OPS_FWD = 17
-OPS_BWD = 45
 FP32_LANES_PER_SM = 128
 
 
@@ -183,6 +177,34 @@ def measured_traffic(stage, dups):
     return None, None
 
 
+def measured_fp32_per_eval(stage):
+    """FP32 lane operations and issued thread instructions per (pixel, splat)
+    evaluation of a compositing kernel, from the committed ncu counters
+    (profiles/fp32_per_evaluation.md: FADD + FMUL + FFMA + 2 x (FADD2 + FMUL2
+    + FFMA2) thread instructions, predicated on, over the launch's
+    evaluations), while the kernel's sources still hash to the profiled
+    version; else None."""
+    import hashlib
+    if stage not in KERNEL_SOURCES:
+        return None
+    kernel, files = KERNEL_SOURCES[stage]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2602_23040_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "fp32_per_evaluation.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 5 and cells[0] == kernel and cells[1] == digest:
+                return {"fp32_lane_ops": float(cells[2]), "thread_inst": float(cells[3]),
+                        "issue_active_pct": float(cells[4]), "source": "ncu counters, 52-view rig cut to 4 views"}
+    return None
+
+
 def launches_per_step(plan):
     # gather 2, project 1, bin_and_sort (as the library counts it), fwd with the loss 2 (zeroing +
     # compositing), bwd 2 (zeroing + adjoint), scatter 1
@@ -205,8 +227,10 @@ def window_views(scene, n, size, seed=0):
     return out
 
 
-def oracle_step(orc, scene, views, soa, texel, dynflag, target_seed=0):
-    """One oracle fwd + L1 + bwd over `views`; returns pixels rendered."""
+def oracle_step(orc, scene, views, soa, texel, dynflag, target_seed=0, keep=None):
+    """One oracle fwd + L1 + bwd over `views`; returns pixels rendered.  With
+    `keep` (a list), appends the step's image, transmittance, borderline
+    bits, flip bounds, dL/dimage and texel gradient to it."""
     va = orc.views_array(views)
     N = len(texel)
     rec = orc.project(soa, N, scene.sh_degree, va)
@@ -216,24 +240,82 @@ def oracle_step(orc, scene, views, soa, texel, dynflag, target_seed=0):
     tgt = np.random.default_rng(target_seed).uniform(0, 1, 3 * P)
     dimg = np.sign(r["img"] - tgt) / (3 * P)
     g2 = orc.render_bwd(rec, va, 16, vals, ranges, dimg)
-    orc.scatter_grad(soa, N, scene.sh_degree, va, g2, dynflag if scene.dyn is not None else None)
+    g = orc.scatter_grad(soa, N, scene.sh_degree, va, g2, dynflag if scene.dyn is not None else None)
+    if keep is not None:
+        keep.append(dict(img=r["img"], T=r["T"], border=r["border"], bound=r["bound"], dimg=dimg, grad=g, P=P))
     return P
 
 
 def cpu_baseline(scene, budget_s=20.0, window=256):
+    """The oracle timed on view windows of the workload; also returns the
+    windows and the oracle's outputs on them (for the accuracy check)."""
     import oracle as orc
     soa, texel, dynflag = orc.gather(scene)
     t0 = time.perf_counter()
     pix, n = 0, 0
     views = window_views(scene, min(8, len(scene.views)), window)
+    kept = []
     while n < len(views) and (time.perf_counter() - t0) < budget_s:
-        pix += oracle_step(orc, scene, [views[n]], soa, texel, dynflag, n)
+        pix += oracle_step(orc, scene, [views[n]], soa, texel, dynflag, n, keep=kept)
         n += 1
     dt = time.perf_counter() - t0
     return {"value": pix / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} view windows of {window}x{window} px from {scene.name}, all {scene.n_live} "
                       f"Gaussians each, fwd + L1 + bwd in FP64, single thread",
-            "seconds": dt}
+            "seconds": dt}, views[:n], kept
+
+
+GROUPS = {"position": (0, 3), "log_scale": (3, 6), "rotation": (6, 10), "opacity": (10, 11), "sh_dc": (11, 14),
+          "sh_rest": (14, None)}
+IMAGE_BORDER = 1 | 2 | 4 | 8 | 16   # the oracle's borderline bits of image decisions
+
+
+def accuracy_on_windows(scene, views, kept, atlas, occ, dyn, dev):
+    """The library on the CPU-baseline's view windows, all in one launch,
+    against the oracle's outputs there: image error off the borderline
+    pixels, the largest excess over a borderline pixel's flip bound (<= 0:
+    every pixel within), the borderline fractions, and the relative error of
+    each attribute group of the texel gradient for the oracle's own
+    dL/dimage."""
+    import torch
+    import paper_2602_23040_gb300 as pk
+    if not kept:
+        return None
+    r = pk.Renderer(pk.Plan.for_scene(scene, views=views, tile=32), dev)
+    r.ensure_capacity(atlas, occ, dyn)
+    F, D, Hh, W = scene.atlas.shape
+    dimg = torch.from_numpy(np.concatenate([k["dimg"] for k in kept]).astype(np.float32)).to(dev)
+    grad = torch.zeros(F * D * Hh * W, dtype=torch.float32, device=dev)
+    r.backward(dimg, grad)
+    torch.cuda.synchronize(dev)
+    st = r.status()
+    img = r.image.cpu().numpy().astype(np.float64)
+    T = r.T.cpu().numpy().astype(np.float64)
+    texel = r.texel[:r.plan.N].cpu().numpy().view(np.uint32)
+    g = grad.view(F, D, Hh * W).cpu().numpy().astype(np.float64)
+    g = np.concatenate([g[f][:, texel] for f in range(F)], axis=1)
+    ref = sum(k["grad"] for k in kept)
+    off, worst_off, excess, nb, nt = 0, 0.0, -1.0, 0, 0
+    for k in kept:
+        P = k["P"]
+        b = (k["border"] & IMAGE_BORDER) != 0
+        nb += int(b.sum())
+        nt += int(((k["border"] & (IMAGE_BORDER & ~8)) != 0).sum())
+        for c in range(3):
+            e = np.abs(img[3 * off + c * P:3 * off + (c + 1) * P] - k["img"][c * P:(c + 1) * P])
+            worst_off = max(worst_off, float(e[~b].max(initial=0.0)))
+            excess = max(excess, float((e - k["bound"][:, 0]).max()))
+        excess = max(excess, float((np.abs(T[off:off + P] - k["T"]) - k["bound"][:, 1]).max()))
+        off += P
+    rel = {}
+    for name, (a, bnd) in GROUPS.items():
+        den = np.linalg.norm(ref[a:bnd])
+        if den > 0:
+            rel[name] = float(np.linalg.norm(g[a:bnd] - ref[a:bnd]) / den)
+    return {"image_max_abs_err_off_borderline": worst_off, "image_max_err_over_flip_bound": excess,
+            "borderline_frac": nb / off, "threshold_borderline_frac": nt / off, "pixels": off,
+            "grad_rel_err": rel, "status_flags": int(st["flags"]),
+            "sample": f"the CPU baseline's {len(kept)} view windows, one launch (32 px tiles); oracle FP64"}
 
 
 def _oracle_worker(args):
@@ -436,12 +518,24 @@ def main():
         r.ensure_capacity(atlas, occ, dyn)
         # a profiler run keeps the default options (the ones the tuner picks
         # at this workload) so that its launch sequence stays short and fixed
-        batch = r.plan.batch if args.profile else r.autotune(atlas, occ, dyn, target, stream)
+        batch = r.plan.batch if args.profile else r.autotune(atlas, occ, dyn, target, stream,
+                                                             tiles=(args.tile, 48 - args.tile))
         r.l1_step(atlas, occ, dyn, target, grad)
     plan = r.plan
     st = r.status(stream)
     assert st["flags"] == 0, st
+    # the evaluation counts (for the ALU roofline) from one pass of the
+    # counting variant of the compositing kernels on the same buffers; the
+    # timed step runs the variant without counters
+    cplan = plan.with_options(count_evals=True)
+    with torch.cuda.stream(stream):
+        pk.rasterize_fwd_l1(cplan, r.records, r.sorted_vals, r.ranges, target, r.image, r.T, r.n_contrib, r.dimage,
+                            r.ws)
+        pk.rasterize_bwd(cplan, r.records, r.sorted_vals, r.ranges, r.T, r.n_contrib, r.dimage, r.grad2d, r.ws)
+    st = pk.read_status(cplan, r.ws, stream)
+    assert st["flags"] == 0, st
     dups, evals_fwd, evals_bwd = int(st["dups"]), int(st["evals_fwd"]), int(st["evals_bwd"])
+    del cplan
 
     # CUDA graph of the whole step
     g = torch.cuda.CUDAGraph()
@@ -515,12 +609,23 @@ def main():
               key=lambda n: stage_ms[n])
     t_dom = stage_ms[dom] * 1e-3
     if dom in ("a4_rasterize_fwd_l1", "a5_rasterize_bwd"):
-        ops = (evals_fwd * OPS_FWD) if dom == "a4_rasterize_fwd_l1" else (evals_bwd * OPS_BWD)
-        ach = ops / t_dom / 1e12
+        evals = evals_fwd if dom == "a4_rasterize_fwd_l1" else evals_bwd
+        meas = measured_fp32_per_eval(dom)
+        # FP32 lane operations per evaluation: the kernel's own, counted by
+        # ncu (FADD/FMUL/FFMA, packed forms twice); without a capture of the
+        # current sources, the method's ~13 of the scope table
+        per_eval = meas["fp32_lane_ops"] if meas else 13.0
+        ach = evals * per_eval / t_dom / 1e12
         traffic, tsrc = measured_traffic(dom, dups)
-        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak_tops, "unit": "TOP/s (FP32)",
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak_tops, "unit": "TOP/s (FP32 lane ops)",
                 "frac": ach / alu_peak_tops, "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz",
+                "fp32_ops_per_evaluation": per_eval,
+                "ops_source": meas["source"] if meas else "method count (13 per evaluation), no capture of these sources",
+                "evaluations": evals,
+                "frac_at_13_ops": evals * 13.0 / t_dom / 1e12 / alu_peak_tops,
+                "issue_active_frac": meas["issue_active_pct"] / 100.0 if meas else None,
+                "thread_instructions_per_evaluation": meas["thread_inst"] if meas else None,
                 "hbm_frac": bytes_alg[dom] / t_dom / 1e9 / hbm}
     else:
         ach = bytes_alg[dom] / t_dom / 1e9
@@ -533,8 +638,10 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": scene.name, "gaussians": plan.G, "views": plan.V, "pixels": plan.P,
                    "sh_degree": scene.sh_degree, "texels": "fp16" if texel_bytes == 2 else "fp32",
-                   "tile": args.tile, "batch": {"fwd": plan.batch, "bwd": plan.batch_bwd},
+                   "tile": plan.tile, "batch": {"fwd": plan.batch, "bwd": plan.batch_bwd},
                    "staging": {"fwd": plan.stage_fwd, "bwd": plan.stage_bwd},
+                   "sort_digit_bits": {"depth": plan.sort_bits_depth, "tile": plan.sort_bits_tile},
+                   "tile_trials_ms": getattr(r, "tile_times_ms", None),
                    "pixels_per_thread": {"fwd": 2, "bwd": 4},
                    "tuned_by": "defaults (profiler run)" if args.profile else "pk_autotune", "graph": "whole step in one CUDA graph",
                    "l2": "inputs larger than L2 (atlas %.0f MB, records %.0f MB)" % (
@@ -651,7 +758,7 @@ def main():
         del bufs, g2, h_atlas, h_target
 
     if not args.profile and not args.no_per_view and rank == 0:
-        loop = pk.PerViewLoop.for_scene(scene, dev, tile=args.tile,
+        loop = pk.PerViewLoop.for_scene(scene, dev, tile=plan.tile,
                                         max_dups=int(dups / max(1, plan.V) * 2) + 65536)
         with torch.cuda.stream(stream):
             loop.ensure_capacity(atlas, occ, dyn, target, grad)
@@ -666,16 +773,39 @@ def main():
         torch.cuda.synchronize(dev)
         pv_ms = a0.elapsed_time(a1) / kp
         ok = all(pk.read_status(p, w)["flags"] == 0 for p, w in zip(loop.plans, loop.ws))
+        # the same loop captured in one CUDA graph: its device time without the
+        # host's launch gaps, for a like-for-like ratio with the batched graph
+        gl = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gl, stream=stream):
+            loop.step(atlas, occ, dyn, target, grad)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            gl.replay()
+            b0.record(stream)
+            for _ in range(kp):
+                gl.replay()
+            b1.record(stream)
+        torch.cuda.synchronize(dev)
+        pvg_ms = b0.elapsed_time(b1) / kp
+        eager_batched = sum(stage_ms.values())
         out["per_view_loop"] = {"value": plan.P / (pv_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": pv_ms,
                                 "launch": "eager, one view per call sequence", "status_ok": ok,
-                                "batched_speedup": pv_ms / ms}
-        del loop
+                                "batched_speedup": pv_ms / ms,
+                                "graph_ms_per_step": pvg_ms, "graph_value": plan.P / (pvg_ms * 1e-3) / 1e6,
+                                "batched_speedup_same_mode": {
+                                    "graph": pvg_ms / ms,
+                                    "eager": pv_ms / eager_batched,
+                                    "eager_batched_ms": eager_batched,
+                                    "note": "graph: both captured whole, device time only; eager: the batched "
+                                            "step's per-call sum against the eager per-view loop"}}
+        del loop, gl
 
     if (args.with_rows or not args.profile) and not args.no_rows and rank == 0:
         out["next_rows"] = next_rows(plan, r, scene, atlas, occ, target, stream, dev, hbm)
 
     if not args.profile and not args.no_cpu_baseline and rank == 0:
-        out["cpu_baseline"] = cpu_baseline(scene)
+        out["cpu_baseline"], win_views, kept = cpu_baseline(scene)
+        out["accuracy"] = accuracy_on_windows(scene, win_views, kept, atlas, occ, dyn, dev)
         out["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(args.config, args.views)
 
     if rank == 0:

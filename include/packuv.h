@@ -125,6 +125,13 @@ typedef struct pk_options {
   int32_t stage_fwd;               /* pk_stage_mode of pk_rasterize_fwd; default PK_STAGE_LOADS */
   int32_t stage_bwd;               /* pk_stage_mode of pk_rasterize_bwd; default PK_STAGE_LOADS */
   int32_t batch_bwd;               /* the same for pk_rasterize_bwd (0 = 128) */
+  int32_t sort_bits_tile;          /* digit width of the radix passes of pk_bin_and_sort's tile sort:
+                                      8 or 11 (0 = 8); pk_autotune picks it */
+  int32_t sort_bits_depth;         /* ... and of its depth sort of the pairs: 8 or 11 (0 = 8) */
+  int32_t count_evals;             /* 1: the compositing kernels count their (pixel, splat)
+                                      evaluations into the status block (evals_fwd, evals_bwd), a
+                                      measurement; 0 (default): no counter in their loops, the
+                                      status fields are left at 0 */
   int32_t first_wait_polls;        /* polls of the first bounded wait on each bulk-copied batch
                                       (radix sort, and the compositing kernels in PK_STAGE_BULK):
                                       0 = the default (about 2^22); -1 = give up without polling,
@@ -163,8 +170,8 @@ typedef struct pk_device_status {
   uint64_t dups;                   /* entries emitted by the last bin_and_sort */
   uint64_t dups_needed;            /* entries the last bin_and_sort needed */
   uint64_t valid_pairs;            /* pairs touching at least one tile */
-  uint64_t evals_fwd;              /* (pixel, splat) evaluations of the last forward */
-  uint64_t evals_bwd;              /* ... of the last backward */
+  uint64_t evals_fwd;              /* (pixel, splat) evaluations of the last forward (count_evals) */
+  uint64_t evals_bwd;              /* ... of the last backward (count_evals) */
   double loss;                     /* last pk_l1_loss_grad / pk_photo_loss_grad value */
   double ssim;                     /* mean SSIM of the last pk_photo_loss_grad (0 after L1) */
   uint64_t nonfinite;              /* Gaussians (over all frames) with a non-finite texel value,
@@ -201,19 +208,21 @@ void pk_plan_destroy(pk_plan *plan);
  * caller's current inputs and on `stream`, pk_rasterize_fwd and then
  * pk_rasterize_bwd for every staging batch (64, 128, 256 splats) and keeps
  * the fastest of each, then times each kernel with both staging modes and
- * keeps the faster one per kernel (two timed runs after one warm-up each; a
- * choice other than the default 128 / plain loads must be more than 2 %
- * faster).  The choices are stored in the plan's options; *chosen_batch
- * receives the forward's batch (may be NULL).  The tile side (a plan option:
- * it changes the binning) and the sort's digit width (8 bits; 10- and 11-bit
- * digits measured slower) are not tuned here.  The arguments
- * are those of the two calls; afterwards image, T_final, n_contrib and
- * grad2d hold a forward and backward with the chosen options.
+ * keeps the faster one per kernel, then times pk_bin_and_sort with 8- and
+ * 11-bit radix digits for its depth sort and then for its tile sort and
+ * keeps the faster width of each (two timed runs after one warm-up each; a
+ * choice other than the defaults -- 128, plain loads, 8 bits -- must be
+ * more than 2 % faster).  The choices are stored in the plan's options
+ * (pk_plan_options reads them); *chosen_batch receives the forward's batch
+ * (may be NULL).  The tile side changes the plan's tiles and buffers, so it
+ * is not tuned here: a caller times plans of both sides and keeps one.  The
+ * arguments are those of the calls; afterwards sorted_vals and tile_ranges
+ * hold the records' lists (the same for every width), and image, T_final,
+ * n_contrib and grad2d a forward and backward with the chosen options.
  * Synchronises `stream`; do not call it during graph capture. */
-pk_status pk_autotune(pk_plan *plan, const float *records, const uint32_t *sorted_vals,
-                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
-                      const float *dL_dimage, float *grad2d, void *workspace, pk_stream_t stream,
-                      int32_t *chosen_batch);
+pk_status pk_autotune(pk_plan *plan, const float *records, uint32_t *sorted_vals, uint32_t *tile_ranges,
+                      float *image, float *T_final, uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                      void *workspace, pk_stream_t stream, int32_t *chosen_batch);
 
 /* Upload the plan's view tables into the workspace and clear its status
  * block.  Call once per workspace (and again after reusing the memory

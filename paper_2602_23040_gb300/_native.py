@@ -47,7 +47,8 @@ class View(C.Structure):
 class Options(C.Structure):
     _fields_ = [("tile", C.c_int32), ("znear", C.c_float), ("bg", C.c_float * 3), ("max_dups", C.c_uint64),
                 ("bin_mode", C.c_int32), ("batch", C.c_int32), ("stage_fwd", C.c_int32), ("stage_bwd", C.c_int32),
-                ("batch_bwd", C.c_int32), ("first_wait_polls", C.c_int32)]
+                ("batch_bwd", C.c_int32), ("sort_bits_tile", C.c_int32), ("sort_bits_depth", C.c_int32),
+                ("count_evals", C.c_int32), ("first_wait_polls", C.c_int32)]
 
 
 class Sizes(C.Structure):

@@ -75,12 +75,15 @@ class Plan:
                  sh_degree: int, frames: int, texel_type: str, views, n_live: int, tile: int = 32,
                  znear: float = 0.01, bg=(0.0, 0.0, 0.0), max_dups: int = 0, bin_mode: str = "ellipse",
                  batch: int = 128, stage_fwd: str = "loads", stage_bwd: str = "loads", batch_bwd: int = None,
+                 sort_bits_tile: int = 8, sort_bits_depth: int = 8, count_evals: bool = False,
                  first_wait_polls: int = 0):
         lib = N.load()
         self._args = dict(levels=list(levels), atlas_wh=tuple(atlas_wh), sh_degree=sh_degree, frames=frames,
                           texel_type=texel_type, views=list(views), n_live=n_live, tile=tile, znear=znear,
                           bg=tuple(bg), max_dups=max_dups, bin_mode=bin_mode, batch=batch, stage_fwd=stage_fwd,
-                          stage_bwd=stage_bwd, batch_bwd=batch_bwd, first_wait_polls=first_wait_polls)
+                          stage_bwd=stage_bwd, batch_bwd=batch_bwd, sort_bits_tile=sort_bits_tile,
+                          sort_bits_depth=sort_bits_depth, count_evals=count_evals,
+                          first_wait_polls=first_wait_polls)
         if batch_bwd is None:
             batch_bwd = batch
         d = N.AtlasDesc()
@@ -99,11 +102,14 @@ class Plan:
         o.stage_fwd = STAGE_MODES[stage_fwd]
         o.stage_bwd = STAGE_MODES[stage_bwd]
         o.batch_bwd = int(batch_bwd)
+        o.sort_bits_tile, o.sort_bits_depth = int(sort_bits_tile), int(sort_bits_depth)
+        o.count_evals = 1 if count_evals else 0
         o.first_wait_polls = int(first_wait_polls)
         self.bin_mode = bin_mode
         self.batch = int(batch)
         self.batch_bwd = int(batch_bwd)
         self.stage_fwd, self.stage_bwd = stage_fwd, stage_bwd
+        self.sort_bits_tile, self.sort_bits_depth = int(sort_bits_tile), int(sort_bits_depth)
         self._views = _views_array(views)
         h = C.c_void_p()
         N.check("pk_plan_create", lib.pk_plan_create(C.byref(d), self._views, len(views), int(n_live),
@@ -127,9 +133,17 @@ class Plan:
 
     def with_capacity(self, max_dups: int) -> "Plan":
         """Same plan with another capacity of (pair, tile) entries."""
+        return self.with_options(max_dups=int(max_dups))
+
+    def with_options(self, **kw) -> "Plan":
+        """Same plan with some options replaced (e.g. the tile side)."""
         a = dict(self._args)
-        a["max_dups"] = int(max_dups)
+        a.update(kw)
         return Plan(**a)
+
+    @property
+    def tile(self) -> int:
+        return int(self._args["tile"])
 
     def close(self):
         if getattr(self, "handle", None):
@@ -334,9 +348,10 @@ def render_bwd(plan: Plan, soa, dynflag, texel, records, sorted_vals, tile_range
 
 def autotune(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_contrib, dL_dimage, grad2d, ws,
              stream=None) -> int:
-    """Time the compositing forward and backward for each staging batch on
-    the current inputs and keep the fastest of each in the plan; returns the
-    forward's."""
+    """pk_autotune: time the compositing forward and backward for each
+    staging batch and mode, and the sort for each radix digit width, on the
+    current inputs; the plan keeps the fastest choices.  Returns the
+    forward's batch."""
     chosen = C.c_int32(0)
     rc = N.load().pk_autotune(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
@@ -351,8 +366,10 @@ def autotune(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_co
     names = {v: k for k, v in STAGE_MODES.items()}
     plan.batch, plan.stage_fwd, plan.stage_bwd = int(o.batch), names[o.stage_fwd], names[o.stage_bwd]
     plan.batch_bwd = int(o.batch_bwd)
+    plan.sort_bits_tile, plan.sort_bits_depth = int(o.sort_bits_tile), int(o.sort_bits_depth)
     plan._args.update(batch=plan.batch, stage_fwd=plan.stage_fwd, stage_bwd=plan.stage_bwd,
-                      batch_bwd=plan.batch_bwd)
+                      batch_bwd=plan.batch_bwd, sort_bits_tile=plan.sort_bits_tile,
+                      sort_bits_depth=plan.sort_bits_depth)
     return plan.batch
 
 

@@ -506,7 +506,9 @@ struct Radix {
   static constexpr int kTile = kThreads * kItems;          // a multiple of 4
   static constexpr int kCopies = RB <= 8 ? kWarps : 2;     // private histograms in the upsweep
   static constexpr int kPerThread = kR / kThreads;         // buckets per thread in the digit scan
-  static constexpr int kMinBlocks = IT >= 12 ? 3 : (IT >= 8 ? 4 : 5);   // resident per SM (downsweep)
+  // resident per SM (downsweep): 8-bit digits by registers, 11-bit digits by
+  // shared memory (per-warp counters and the double buffer, ~82-98 KB)
+  static constexpr int kMinBlocks = RB > 8 ? 2 : (IT >= 12 ? 3 : (IT >= 8 ? 4 : 5));
 };
 constexpr int kPairItems = 12, kEntryItems = 8;
 
@@ -982,18 +984,23 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 
 // One stable pass over key bits [shift, shift + bits), bits <= 8, over the
 // depth-sorted pairs (pair_blocks() blocks) or over the entries
-// (sort_blocks() blocks, or the segmented table's).  (Wider digits, tried
-// at 11 bits, cut the passes but each pass ran at two blocks per SM with
-// scattered short runs and came out slower overall.)
-pk_status radix_pass(bool entries, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
+// (sort_blocks() blocks, or the segmented table's), with digits of up to
+// rb = 8 or 11 bits (pk_options.sort_bits_*: wider digits take fewer passes
+// but run fewer blocks per SM and scatter into more runs).
+pk_status radix_pass(bool entries, int rb, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
                      pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls, cudaStream_t st,
                      SegSpec sp = SegSpec{nullptr, nullptr}) {
-  if (entries)
-    return radix_pass_rb<kMaxRadixBits, kEntryItems>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks,
-                                                      status, sp, abort_flag, first_polls, st);
-  return radix_pass_rb<kMaxRadixBits, kPairItems>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks,
-                                                   status, sp, abort_flag, first_polls, st);
+#define PK_PASS(RB, IT)                                                                                        \
+  return radix_pass_rb<RB, IT>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, sp,  \
+                               abort_flag, first_polls, st)
+  if (entries) {
+    if (rb > 8) PK_PASS(11, kEntryItems);
+    PK_PASS(8, kEntryItems);
+  }
+  if (rb > 8) PK_PASS(11, kPairItems);
+  PK_PASS(8, kPairItems);
+#undef PK_PASS
 }
 
 int sm_count() {
@@ -1004,17 +1011,19 @@ int sm_count() {
 }
 
 // Blocks of the pair passes: resident ones, within the histogram.
-int pair_blocks() {
-  return std::max(1, std::min(kSortBlocks, Radix<kMaxRadixBits, kPairItems>::kMinBlocks * sm_count()));
+int pair_blocks(int rb) {
+  const int per_sm = rb > 8 ? Radix<11, kPairItems>::kMinBlocks : Radix<8, kPairItems>::kMinBlocks;
+  return std::max(1, std::min(kSortBlocks, per_sm * sm_count()));
 }
 
 }  // namespace
 
 // Blocks of the entry passes on this device.
-int pk::sort_blocks() {
+int pk::sort_blocks(int rb) {
   // the entry passes' resident blocks, leaving the histogram room for the
   // segmented table's one extra block per view
-  return std::max(1, std::min(kSortBlocks - 128, Radix<kMaxRadixBits, kEntryItems>::kMinBlocks * sm_count()));
+  const int per_sm = rb > 8 ? Radix<11, kEntryItems>::kMinBlocks : Radix<8, kEntryItems>::kMinBlocks;
+  return std::max(1, std::min(kSortBlocks - 128, per_sm * sm_count()));
 }
 
 namespace {
@@ -1024,14 +1033,14 @@ namespace {
 // histogram counter}.  Returns the number of blocks, or 0 when the views do
 // not fit the histogram.
 template <typename Weight>
-int share_blocks(int V, int nblocks, const Weight &weight, int4 *tab) {
+int share_blocks(int V, int nblocks, int rb, const Weight &weight, int4 *tab) {
   int64_t total = 0;
   for (int v = 0; v < V; ++v) total += weight(v);
   int nb = 0;
   for (int v = 0; v < V; ++v) {
     const int parts = std::max<int>(1, (int)((int64_t)nblocks * weight(v) / std::max<int64_t>(1, total)));
     if (nb + parts > kSortBlocks) return 0;
-    for (int j = 0; j < parts; ++j) tab[nb + j] = make_int4(v, j, parts, (1 << kMaxRadixBits) * nb);
+    for (int j = 0; j < parts; ++j) tab[nb + j] = make_int4(v, j, parts, (1 << rb) * nb);
     nb += parts;
   }
   return nb;
@@ -1045,10 +1054,11 @@ int share_blocks(int V, int nblocks, const Weight &weight, int4 *tab) {
 bool pk::seg_tables(const pk_plan *p, int4 *tab, int *ntile, int *npair) {
   *ntile = *npair = 0;
   if (p->V < 2) return false;
-  const int nt = share_blocks(p->V, sort_blocks(),
+  const int rt = p->opts.sort_bits_tile, rd = p->opts.sort_bits_depth;
+  const int nt = share_blocks(p->V, sort_blocks(rt), rt,
                               [&](int v) { return (int64_t)p->h_views[v].tiles_x * p->h_views[v].tiles_y; },
                               tab);
-  const int np = share_blocks(p->V, pair_blocks(), [](int) { return int64_t(1); }, tab + kSortBlocks);
+  const int np = share_blocks(p->V, pair_blocks(rd), rd, [](int) { return int64_t(1); }, tab + kSortBlocks);
   if (nt == 0 || np == 0) return false;
   *ntile = nt;
   *npair = np;
@@ -1057,10 +1067,10 @@ bool pk::seg_tables(const pk_plan *p, int4 *tab, int *ntile, int *npair) {
 
 namespace {
 
-// Digit widths for a key of `bits` bits: as few passes of <= kMaxRadixBits
-// bits as possible, split evenly.
-int radix_plan(int bits, int *widths) {
-  const int npass = (bits + kMaxRadixBits - 1) / kMaxRadixBits;
+// Digit widths for a key of `bits` bits: as few passes of <= maxw bits as
+// possible, split evenly.
+int radix_plan(int bits, int maxw, int *widths) {
+  const int npass = (bits + maxw - 1) / maxw;
   for (int i = 0, left = bits; i < npass; ++i) {
     widths[i] = (left + (npass - i) - 1) / (npass - i);
     left -= widths[i];
@@ -1130,11 +1140,12 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   }
   pk_status e;
   int widths[8];
-  int np = radix_plan(32, widths), shift = 0;
+  const int rd = p->opts.sort_bits_depth, rt = p->opts.sort_bits_tile;
+  int np = radix_plan(32, rd, widths), shift = 0;
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
-    if ((e = radix_pass(false, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist,
-                        seg ? npseg : pair_blocks(), status, &ctr->sort_abort, p->first_polls, st, psp)) != PK_OK)
+    if ((e = radix_pass(false, rd, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist,
+                        seg ? npseg : pair_blocks(rd), status, &ctr->sort_abort, p->first_polls, st, psp)) != PK_OK)
       return e;
     shift += widths[pass];
   }
@@ -1147,7 +1158,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   // emission and the stable tile sort; the last pass lands in sorted_vals
   int key_bits = p->tile_bits;
   SegSpec sp{nullptr, nullptr};
-  int nblocks = sort_blocks();
+  int nblocks = sort_blocks(rt);
   if (seg) {
     key_bits = local_tile_bits(p);
     k_view_segments<true><<<(p->V + kThreads) / kThreads, kThreads, 0, st>>>(pval, offs, ctr, (uint32_t)p->N, p->V,
@@ -1155,7 +1166,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     sp = SegSpec{tab, vseg};
     nblocks = nseg;
   }
-  np = radix_plan(key_bits, widths);
+  np = radix_plan(key_bits, rt, widths);
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
   k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->pairs, p->T,
@@ -1171,7 +1182,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
     shift -= widths[pass];
-    if ((e = radix_pass(true, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
+    if ((e = radix_pass(true, rt, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
                         status, &ctr->sort_abort, p->first_polls, st, sp)) != PK_OK)
       return e;
   }
@@ -1193,10 +1204,10 @@ int pk::bin_kernel_count(const pk_plan *p) {
   int nt = 0, np = 0;
   const bool seg = seg_tables(p, tab, &nt, &np);
   int widths[8];
-  int passes = radix_plan(32, widths);
+  int passes = radix_plan(32, p->opts.sort_bits_depth, widths);
   int kernels = 1 + 4 + 3 + 1 + 1;
   if (seg) kernels += 2;   // the pairs' and the entries' view segments
-  passes += radix_plan(seg ? local_tile_bits(p) : p->tile_bits, widths);
+  passes += radix_plan(seg ? local_tile_bits(p) : p->tile_bits, p->opts.sort_bits_tile, widths);
   return kernels + 3 * passes;
 }
 
@@ -1285,7 +1296,9 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   L.offs = take(sizeof(uint32_t) * pairs);
   L.rmask = take(sizeof(uint4) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
-  L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
+  // digit counters of the widest radix pass of the plan's two sorts
+  L.hist = take(sizeof(uint32_t) * (size_t(1) << std::max(p->opts.sort_bits_tile, p->opts.sort_bits_depth)) *
+                kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);
   L.dval = take(sizeof(uint32_t) * maxd);

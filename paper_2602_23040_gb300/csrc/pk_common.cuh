@@ -31,7 +31,7 @@ constexpr float kInvExpScale = -1.38629436111989061f;   // 1 / kExpScale = -2 ln
 // Fixed grid sizes of the device-count-driven kernels (scan, radix sort).
 constexpr int kScanBlocks = 4096;
 constexpr int kSortBlocks = 768;      // most radix blocks of one pass (histogram capacity)
-constexpr int kMaxRadixBits = 8;      // widest radix digit
+constexpr int kMaxRadixBits = 11;     // widest radix digit (pk_options.sort_bits_*: 8 or 11)
 
 // Per-view constants on the device, 144 bytes.
 struct alignas(16) DevView {
@@ -113,7 +113,7 @@ pk_status zero_async(std::initializer_list<std::pair<void *, size_t>> spans, cud
 // tables of the segmented (per-view) sorts: tab[0, kSortBlocks) for the
 // tile passes, tab[kSortBlocks, 2 kSortBlocks) for the depth passes
 // (pk_binsort.cu); false = the plan sorts unsegmented.
-int sort_blocks();
+int sort_blocks(int rb);
 bool seg_tables(const pk_plan *p, int4 *tab, int *ntile, int *npair);
 // Kernels one pk_bin_and_sort call launches for this plan on this device.
 int bin_kernel_count(const pk_plan *p);

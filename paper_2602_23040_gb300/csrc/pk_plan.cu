@@ -176,9 +176,17 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   o.stage_fwd = PK_STAGE_LOADS;
   o.stage_bwd = PK_STAGE_LOADS;
   o.batch_bwd = 128;
+  o.sort_bits_tile = 8;
+  o.sort_bits_depth = 8;
+  o.count_evals = 0;
   o.first_wait_polls = 0;
   if (opts) o = *opts;
+  if (o.count_evals != 0 && o.count_evals != 1) return PK_ERR_ARG;
   if (o.first_wait_polls < -1) return PK_ERR_ARG;
+  if (o.sort_bits_tile == 0) o.sort_bits_tile = 8;
+  if (o.sort_bits_depth == 0) o.sort_bits_depth = 8;
+  for (const int32_t b : {o.sort_bits_tile, o.sort_bits_depth})
+    if (b != 8 && b != 11) return PK_ERR_ARG;
   if (o.bin_mode != PK_BIN_RECT && o.bin_mode != PK_BIN_ELLIPSE) return PK_ERR_ARG;
   if (o.batch == 0) o.batch = 128;
   if (o.batch_bwd == 0) o.batch_bwd = 128;
@@ -300,6 +308,8 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   L.offs = take(sizeof(uint32_t) * pairs);
   L.rmask = take(sizeof(uint4) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
+  // digit counters of the widest radix pass (room for 11-bit digits, so
+  // that pk_autotune may pick them)
   L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);
@@ -422,8 +432,8 @@ pk_status time_runs(Fn fn, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int 
 
 }  // namespace
 
-extern "C" pk_status pk_autotune(pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                                 const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+extern "C" pk_status pk_autotune(pk_plan *p, const float *records, uint32_t *sorted_vals, uint32_t *tile_ranges,
+                                 float *image, float *T_final, uint32_t *n_contrib,
                                  const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream,
                                  int32_t *chosen_batch) {
   if (!p) return PK_ERR_ARG;
@@ -479,10 +489,35 @@ extern "C" pk_status pk_autotune(pk_plan *p, const float *records, const uint32_
     e = k == 0 ? time_runs(fwd, st, e0, e1, 2, &ms_bulk) : time_runs(bwd, st, e0, e1, 2, &ms_bulk);
     if (e == PK_OK) *mode = ms_bulk < kMargin * ms_loads ? PK_STAGE_BULK : PK_STAGE_LOADS;
   }
+  // the digit widths of the two radix sorts of pk_bin_and_sort (8 or 11
+  // bits): the depth sort's first, then the tile sort's, each timed over the
+  // whole call; the lists do not depend on them.  The segmented sorts'
+  // block tables depend on the widths and are uploaded again.
+  auto upload_tables = [&]() -> pk_status {
+    int nt = 0, np = 0;
+    if (seg_tables(p, p->h_segtab, &nt, &np) &&
+        cudaMemcpyAsync(at<char>(ws, p->ws.sblk), p->h_segtab, sizeof(p->h_segtab), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+      return PK_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? PK_OK : PK_ERR_CUDA;
+  };
+  auto sort = [&]() { return pk_bin_and_sort(p, records, sorted_vals, tile_ranges, ws, stream); };
+  for (int k = 0; k < 2 && e == PK_OK; ++k) {
+    int32_t *bits = k == 0 ? &p->opts.sort_bits_depth : &p->opts.sort_bits_tile;
+    float ms8 = 0.f, ms11 = 0.f;
+    *bits = 8;
+    if ((e = upload_tables()) != PK_OK || (e = time_runs(sort, st, e0, e1, 2, &ms8)) != PK_OK) break;
+    *bits = 11;
+    if ((e = upload_tables()) != PK_OK || (e = time_runs(sort, st, e0, e1, 2, &ms11)) != PK_OK) break;
+    *bits = ms11 < kMargin * ms8 ? 11 : 8;
+    e = upload_tables();
+  }
   if (e != PK_OK) {
     p->opts = keep;
+    upload_tables();
   } else {
-    e = both();
+    e = sort();
+    if (e == PK_OK) e = both();
   }
   if (e == PK_OK && cudaStreamSynchronize(st) != cudaSuccess) e = PK_ERR_CUDA;
   cudaEventDestroy(e0);

@@ -150,8 +150,9 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // registers spill in the splat loop (9.07 ms at the 52-view rig) and 80
 // leave 12 CTAs (9.31 ms) against 8.78 ms.
 // kT: side of the tiles the lists were binned for; each CTA takes a 16 x 16
-// quadrant of one, as in the forward.
-template <int kBatch, bool kTma, int kPx, int kT>
+// quadrant of one, as in the forward.  kCount: count the evaluations (a
+// measurement; the variant without it carries no counter in its loop).
+template <int kBatch, bool kTma, int kPx, int kT, bool kCount>
 __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
@@ -313,14 +314,12 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
           const f32x2 z2 = dup2(0.f);
           AdjSums sums{z2, z2, z2, z2, z2, z2, z2};
           bool act = false;
-          uint32_t on = 0;   // bit h: pixel h blended or skipped this splat in the forward
-#pragma unroll
-          for (int h = 0; h < kPx; ++h) on |= (uint32_t)(pos < nc[h]) << h;
-          evals += __popc(on);
 #pragma unroll
           for (int h = 0; h < kPx; h += 2) {
-            const bool e0 = (on >> h) & 1u, e1 = (on >> (h + 1)) & 1u;
+            // the pixels blended or skipped this splat in the forward
+            const bool e0 = pos < nc[h], e1 = pos < nc[h + 1];
             if (!(e0 || e1)) continue;
+            if (kCount) evals += (uint32_t)e0 + (uint32_t)e1;
             act |= pixel_adjoint2(a, b, c4, dx, zx, pack2(pyq[h], pyq[h + 1]), e0, e1, pack2(g0[h], g0[h + 1]),
                                   pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]), T[h], T[h + 1], GS[h],
                                   GS[h + 1], sums);
@@ -345,14 +344,16 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
     }
     __syncthreads();
   }
-  unsigned long long ev = evals;
+  if (kCount) {
+    unsigned long long ev = evals;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-  if (lane == 0 && ev) atomicAdd(evals_out, ev);
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if (lane == 0 && ev) atomicAdd(evals_out, ev);
+  }
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
-template <int kBatch, bool kBwdTma, int kT>
+template <int kBatch, bool kBwdTma, int kT, bool kCount>
 pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
                      const float *dL_dimage, float *grad2d, void *ws, DevCounters *ctr, pk_device_status *status,
@@ -360,7 +361,7 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT>,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT, kCount>,
                                                 Geo<kBwdPx>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
@@ -368,7 +369,7 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > items) grid = items;
   if (grid < 1) grid = 1;
-  k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT><<<(int)grid, Geo<kBwdPx>::kThreads, 0, st>>>(
+  k_raster_bwd<kBatch, kBwdTma, kBwdPx, kT, kCount><<<(int)grid, Geo<kBwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)items, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], T_final, n_contrib, dL_dimage, grad2d,
       &ctr->tile_queue[1], reinterpret_cast<unsigned long long *>(&status->evals_bwd), status, p->first_polls, (uint32_t)p->pairs);
@@ -391,11 +392,16 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
                              {&status->evals_bwd, sizeof(uint64_t)}},
                             st);
   if (ze != PK_OK) return ze;
-#define PK_BWD(B, M)                                                                                          \
-  return p->T == 32 ? launch_bwd<B, M, 32>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, \
-                                           grad2d, ws, ctr, status, st)                                         \
-                    : launch_bwd<B, M, 16>(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, \
-                                           grad2d, ws, ctr, status, st)
+#define PK_BWD_T(B, M, C)                                                                                   \
+  return p->T == 32 ? launch_bwd<B, M, 32, C>(p, records, sorted_vals, tile_ranges, T_final, n_contrib,       \
+                                              dL_dimage, grad2d, ws, ctr, status, st)                         \
+                    : launch_bwd<B, M, 16, C>(p, records, sorted_vals, tile_ranges, T_final, n_contrib,       \
+                                              dL_dimage, grad2d, ws, ctr, status, st)
+#define PK_BWD(B, M)          \
+  if (p->opts.count_evals) {  \
+    PK_BWD_T(B, M, true);     \
+  }                           \
+  PK_BWD_T(B, M, false)
   const bool tma = p->opts.stage_bwd == PK_STAGE_BULK;
   switch (p->opts.batch_bwd) {
     case 64:
@@ -409,4 +415,5 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
       PK_BWD(256, false);
   }
 #undef PK_BWD
+#undef PK_BWD_T
 }

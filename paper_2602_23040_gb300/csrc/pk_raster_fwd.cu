@@ -27,7 +27,9 @@ namespace {
 // With a target (not null) the epilogue also takes the L1 term of the
 // objective: dL/dimage = sign(image - target) * scale and the sum of
 // |image - target| (FP32 per thread, FP64 across warps) into loss_acc.
-template <int kBatch, bool kTma, int kPx, int kT>
+// kCount: count the (pixel, splat) evaluations into evals_out (a
+// measurement; the variant without it carries no counter in its loop).
+template <int kBatch, bool kTma, int kPx, int kT, bool kCount>
 __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
@@ -169,7 +171,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
             const float4 a = s_a[j], b = s_b[j], c = s_c[j];
             const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
             const uint32_t pos1 = base - s + (uint32_t)j + 1u;
-            evals += __popc(live);   // this splat is evaluated at every live pixel of the thread
+            if (kCount) evals += __popc(live);   // evaluated at every live pixel of the thread
 #pragma unroll
             for (int q = 0; q < kPx; ++q) {
               if (!((live >> q) & 1u)) continue;
@@ -236,10 +238,12 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
     __syncthreads();   // everyone has read s_tile / s_view before the next fetch
   }
   // one atomic per warp for the evaluation counter (and the loss)
-  unsigned long long ev = evals;
+  if (kCount) {
+    unsigned long long ev = evals;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-  if (lane == 0 && ev) atomicAdd(evals_out, ev);
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if (lane == 0 && ev) atomicAdd(evals_out, ev);
+  }
   if (target) {
     double dl = (double)lsum;
 #pragma unroll
@@ -249,7 +253,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
 }
 
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
-template <int kBatch, bool kFwdTma, int kT>
+template <int kBatch, bool kFwdTma, int kT, bool kCount>
 pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
                      DevCounters *ctr, pk_device_status *status, const float *target, float *dimg,
@@ -257,7 +261,7 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT>,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT, kCount>,
                                                 Geo<kFwdPx>::kThreads, 0);
   if (sms < 1) sms = 1;
   if (per_sm < 1) per_sm = 1;
@@ -265,7 +269,7 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > items) grid = items;
   if (grid < 1) grid = 1;
-  k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT><<<(int)grid, Geo<kFwdPx>::kThreads, 0, st>>>(
+  k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT, kCount><<<(int)grid, Geo<kFwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)items, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
       &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status, target, dimg,
@@ -285,11 +289,16 @@ pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *
                              {&ctr->loss_acc, target ? 2 * sizeof(double) + sizeof(float) : 0}},
                             st);
   if (ze != PK_OK) return ze;
-#define PK_FWD(B, M)                                                                                           \
-  return p->T == 32 ? launch_fwd<B, M, 32>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, \
-                                           ctr, status, target, dimg, st)                                        \
-                    : launch_fwd<B, M, 16>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, ws, \
-                                           ctr, status, target, dimg, st)
+#define PK_FWD_T(B, M, C)                                                                                     \
+  return p->T == 32 ? launch_fwd<B, M, 32, C>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, \
+                                              ws, ctr, status, target, dimg, st)                                \
+                    : launch_fwd<B, M, 16, C>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, \
+                                              ws, ctr, status, target, dimg, st)
+#define PK_FWD(B, M)          \
+  if (p->opts.count_evals) {  \
+    PK_FWD_T(B, M, true);     \
+  }                           \
+  PK_FWD_T(B, M, false)
   const bool tma = p->opts.stage_fwd == PK_STAGE_BULK;
   switch (p->opts.batch) {
     case 64:
@@ -303,6 +312,7 @@ pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *
       PK_FWD(256, false);
   }
 #undef PK_FWD
+#undef PK_FWD_T
 }
 
 }  // namespace

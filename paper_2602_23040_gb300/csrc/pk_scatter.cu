@@ -62,10 +62,22 @@ __global__ __launch_bounds__(kScatterThreads, 4) void k_scatter(const float *__r
     float dS[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma3D entries xx xy xz yy yz zz
     float dop = 0.f;
     const int vb = __ldg(fview_off + f), ve = __ldg(fview_off + f + 1);
-    for (int vi = vb; vi < ve; ++vi) {
-      const int v = __ldg(fview_idx + vi);
+    // the next view's 2D gradient record is loaded while this view's is
+    // chained, so two loads per thread are in flight instead of one
+    auto load_g = [&](int vi, int &v, float4 &x0, float4 &x1, float4 &x2) {
+      v = __ldg(fview_idx + vi);
       const float4 *gsrc = reinterpret_cast<const float4 *>(grad2d + ((int64_t)v * N + g) * kG2d);
-      const float4 g0 = __ldg(gsrc), g1 = __ldg(gsrc + 1), g2 = __ldg(gsrc + 2);
+      x0 = __ldg(gsrc);
+      x1 = __ldg(gsrc + 1);
+      x2 = __ldg(gsrc + 2);
+    };
+    int nv = 0;
+    float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
+    if (vb < ve) load_g(vb, nv, n0, n1, n2);
+    for (int vi = vb; vi < ve; ++vi) {
+      const int v = nv;
+      const float4 g0 = n0, g1 = n1, g2 = n2;
+      if (vi + 1 < ve) load_g(vi + 1, nv, n0, n1, n2);
       if (g0.x == 0.f && g0.y == 0.f && g0.z == 0.f && g0.w == 0.f && g1.x == 0.f && g1.y == 0.f &&
           g1.z == 0.f && g1.w == 0.f && g2.x == 0.f)
         continue;

@@ -93,14 +93,57 @@ class Renderer:
         api.photo_loss_grad(self.plan, self.image, target, self.dimage, self.ws, lam, stream)
         self.backward(self.dimage, grad_atlas, False, stream)
 
-    def autotune(self, atlas, occ, dyn, target, stream=None) -> int:
-        """Forward + L1 gradient on the given inputs, then pk_autotune: the
-        fastest compositing batch is kept in the plan.  Host-synchronising:
+    def autotune(self, atlas, occ, dyn, target, stream=None, tiles=None) -> int:
+        """Pick the launch options on the given inputs.  With ``tiles`` (tile
+        sides, e.g. (32, 16)) each side gets a plan of its own -- the binning
+        and the buffers differ -- and the one whose sort + forward (with the
+        L1 term) + backward takes least device time is kept; then
+        pk_autotune picks that plan's compositing batch and staging and its
+        radix digit widths.  Returns the forward's batch.  Host-synchronising:
         call it before graph capture."""
+        if tiles:
+            times = {}
+            for side in tiles:
+                if side != self.plan.tile:
+                    self._replan(self.plan.with_options(tile=int(side)), atlas, occ, dyn, stream)
+                times[side] = self._time_sort_and_composite(target, stream)
+            best = min(times, key=times.get)
+            self.tile_times_ms = times
+            if best != self.plan.tile:
+                self._replan(self.plan.with_options(tile=int(best)), atlas, occ, dyn, stream)
         self.forward(atlas, occ, dyn, stream)
         api.l1_loss_grad(self.plan, self.image, target, self.dimage, self.ws, stream)
         return api.autotune(self.plan, self.records, self.sorted_vals, self.ranges, self.image, self.T,
                             self.n_contrib, self.dimage, self.grad2d, self.ws, stream)
+
+    def _replan(self, plan, atlas, occ, dyn, stream=None):
+        """Adopt another plan (new workspace and buffers) sized for these inputs."""
+        self.plan = plan
+        self.ws = api.make_workspace(plan, self.device)
+        api.workspace_init(plan, self.ws)
+        self._alloc()
+        self.ensure_capacity(atlas, occ, dyn, stream)
+
+    def _time_sort_and_composite(self, target, stream=None, reps=2) -> float:
+        """Device milliseconds of bin_and_sort + fused forward/L1 + backward
+        on the current records (one warm-up, then the mean of ``reps``)."""
+        p = self.plan
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+
+        def once():
+            api.bin_and_sort(p, self.records, self.sorted_vals, self.ranges, self.ws, st)
+            api.rasterize_fwd_l1(p, self.records, self.sorted_vals, self.ranges, target, self.image, self.T,
+                                 self.n_contrib, self.dimage, self.ws, st)
+            api.rasterize_bwd(p, self.records, self.sorted_vals, self.ranges, self.T, self.n_contrib, self.dimage,
+                              self.grad2d, self.ws, st)
+        once()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            once()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
 
     def status(self, stream=None) -> dict:
         return api.read_status(self.plan, self.ws, stream)

@@ -124,10 +124,10 @@ def _synthetic_records(views, N, seed):
     return rec
 
 
-def _records_plan(views, N, bin_mode="ellipse", tile=16):
+def _records_plan(views, N, bin_mode="ellipse", tile=16, **kw):
     pk = _pk()
     side = int(math.ceil(math.sqrt(N)))
-    return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, bin_mode=bin_mode, tile=tile)
+    return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, bin_mode=bin_mode, tile=tile, **kw)
 
 
 def _records_setup(seed, N=700):
@@ -137,13 +137,18 @@ def _records_setup(seed, N=700):
     return views, rec
 
 
-@pytest.mark.parametrize("seed,mode,tile", [(1, "ellipse", 16), (2, "ellipse", 16), (3, "rect", 16), (4, "rect", 16),
-                                            (1, "ellipse", 32), (3, "rect", 32)])
-def test_bin_and_sort_bit_exact(orc, seed, mode, tile):
+@pytest.mark.parametrize("seed,mode,tile,bits", [(1, "ellipse", 16, (8, 8)), (2, "ellipse", 16, (8, 8)),
+                                                 (3, "rect", 16, (8, 8)), (4, "rect", 16, (8, 8)),
+                                                 (1, "ellipse", 32, (8, 8)), (3, "rect", 32, (8, 8)),
+                                                 (2, "ellipse", 16, (11, 11)), (5, "ellipse", 32, (11, 8)),
+                                                 (6, "rect", 16, (8, 11))])
+def test_bin_and_sort_bit_exact(orc, seed, mode, tile, bits):
+    """Every tile's list bit for bit, for either radix digit width of the
+    depth sort and of the tile sort (bits = (depth, tile))."""
     pk = _pk()
     views, rec = _records_setup(seed)
     V, N = rec.shape[:2]
-    plan = _records_plan(views, N, mode, tile)
+    plan = _records_plan(views, N, mode, tile, sort_bits_depth=bits[0], sort_bits_tile=bits[1])
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
@@ -228,14 +233,15 @@ def _ragged_records(tile, seed, spread):
     return views, rec
 
 
-@pytest.mark.parametrize("tile,spread", [(16, False), (16, True), (32, False), (32, True)])
-def test_bin_and_sort_ragged_view_segments(orc, tile, spread):
+@pytest.mark.parametrize("tile,spread,bits", [(16, False, 8), (16, True, 8), (32, False, 8), (32, True, 8),
+                                              (16, True, 11), (32, False, 11)])
+def test_bin_and_sort_ragged_view_segments(orc, tile, spread, bits):
     """Per-view segments of 0-3 items at every start residue (both the depth
-    passes and the tile passes run segmented by view here)."""
+    passes and the tile passes run segmented by view here), 8- or 11-bit digits."""
     pk = _pk()
     views, rec = _ragged_records(tile, 11 + tile + spread, spread)
     V, N = rec.shape[:2]
-    plan = _records_plan(views, N, "ellipse", tile)
+    plan = _records_plan(views, N, "ellipse", tile, sort_bits_depth=bits, sort_bits_tile=bits)
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
@@ -263,7 +269,7 @@ def _records_forward(seed, dimg_seed=None, tile=16):
     views, rec = _records_setup(seed, N=500)
     V, N = rec.shape[:2]
     rec[..., 5] = np.minimum(rec[..., 5], 0.999)
-    plan = _records_plan(views, N, tile=tile)
+    plan = _records_plan(views, N, tile=tile, count_evals=True)
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
@@ -514,6 +520,47 @@ def test_every_batch_size_and_autotune():
     assert torch.equal(r.image, ref[0])
 
 
+def test_autotune_tile_side_and_digit_widths(orc):
+    """The tuner over tile sides (a plan each) and radix digit widths: the
+    tuned plan's images and transmittance are bit-identical to the default
+    plan's, and its lists equal the oracle's tile by tile."""
+    pk = _pk()
+    sc = H.scene_small_sh3(seed=717)
+    atlas, occ, dyn = H.upload(sc)
+    target = torch.from_numpy(synth.random_target(sc)).cuda()
+    ref = pk.Renderer(pk.Plan.for_scene(sc, tile=32))
+    assert ref.ensure_capacity(atlas, occ, dyn)["flags"] == 0
+    r = pk.Renderer(pk.Plan.for_scene(sc, tile=32))
+    r.ensure_capacity(atlas, occ, dyn)
+    r.autotune(atlas, occ, dyn, target, tiles=(32, 16))
+    p = r.plan
+    assert p.tile in (16, 32) and set(r.tile_times_ms) == {16, 32}
+    assert p.sort_bits_tile in (8, 11) and p.sort_bits_depth in (8, 11)
+    r.forward(atlas, occ, dyn)
+    torch.cuda.synchronize()
+    st = r.status()
+    assert st["flags"] == 0
+    assert torch.equal(r.image, ref.image) and torch.equal(r.T, ref.T)
+    V, N = p.V, p.N
+    rec = r.records.cpu().numpy().reshape(V * N, 12)
+    va = orc.views_array(sc.views)
+    ref_vals, ref_ranges = orc.bin_sort32(rec[:, 0], rec[:, 1], rec[:, 7], rec[:, 6], va, N, p.tile, rec[:, 2],
+                                          rec[:, 3], rec[:, 4], mode=orc.BIN_ELLIPSE)
+    assert st["dups"] == len(ref_vals)
+    assert_same_tile_lists(H.u32(r.sorted_vals[:len(ref_vals)]), H.u32(r.ranges).reshape(-1, 2), ref_vals,
+                           ref_ranges)
+    # either digit width, either sort: the same lists
+    for bits in ((11, 11), (11, 8), (8, 11)):
+        q = p.with_options(sort_bits_depth=bits[0], sort_bits_tile=bits[1])
+        ws = pk.make_workspace(q)
+        pk.workspace_init(q, ws)
+        vals = torch.empty(q.max_dups + 64, dtype=torch.int32, device="cuda")
+        ranges = torch.empty(2 * q.n_tiles, dtype=torch.int32, device="cuda")
+        pk.bin_and_sort(q, r.records, vals, ranges, ws)
+        assert pk.read_status(q, ws)["flags"] == 0
+        assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.u32(ranges).reshape(-1, 2), ref_vals, ref_ranges)
+
+
 def test_render_fwd_bwd_convenience_calls():
     """pk_render_fwd / pk_render_bwd chain the six calls: same outputs."""
     pk = _pk()
@@ -564,3 +611,27 @@ def test_binning_from_fp64_projection_differs_only_at_borderline_pairs(orc, mode
     print(f"{mode}: {differ} of {V * N} pairs have another tile count from the FP64 projection")
     assert differ <= max(3, 0.002 * V * N)
     assert abs(int(a.sum()) - int(b.sum())) <= 2 * max(1, differ)
+
+
+def test_counting_variant_changes_nothing_but_the_counts():
+    """The compositing kernels with and without the evaluation counters:
+    bit-identical images, transmittance and contributor counts, 2D
+    gradients equal up to their atomic order; only the counting plan
+    reports evaluations."""
+    pk = _pk()
+    o = _records_forward(5, dimg_seed=9)
+    plan, ws = o["plan"], o["ws"]
+    st = pk.read_status(plan, ws)
+    assert st["evals_fwd"] > 0 and st["evals_bwd"] > 0
+    q = plan.with_options(count_evals=False)
+    ws2 = pk.make_workspace(q)
+    pk.workspace_init(q, ws2)
+    img, T, nc = torch.empty_like(o["img"]), torch.empty_like(o["T"]), torch.empty_like(o["nc"])
+    pk.rasterize_fwd(q, o["drec"], o["vals"], o["ranges"], img, T, nc, ws2)
+    g2 = torch.empty_like(o["g2"])
+    pk.rasterize_bwd(q, o["drec"], o["vals"], o["ranges"], T, nc, torch.from_numpy(o["w"]).cuda(), g2, ws2)
+    st2 = pk.read_status(q, ws2)
+    assert st2["evals_fwd"] == 0 and st2["evals_bwd"] == 0 and st2["flags"] == 0
+    assert torch.equal(img, o["img"]) and torch.equal(T, o["T"]) and torch.equal(nc, o["nc"])
+    a, b = g2.cpu().numpy().astype(np.float64), o["g2"].cpu().numpy().astype(np.float64)
+    assert np.abs(a - b).max() <= 1e-5 * max(1e-12, np.abs(b).max())
