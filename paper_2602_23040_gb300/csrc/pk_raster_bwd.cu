@@ -397,11 +397,13 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
                                               dL_dimage, grad2d, ws, ctr, status, st)                         \
                     : launch_bwd<B, M, 16, C>(p, records, sorted_vals, tile_ranges, T_final, n_contrib,       \
                                               dL_dimage, grad2d, ws, ctr, status, st)
-#define PK_BWD(B, M)          \
-  if (p->opts.count_evals) {  \
-    PK_BWD_T(B, M, true);     \
-  }                           \
-  PK_BWD_T(B, M, false)
+#define PK_BWD(B, M)            \
+  {                             \
+    if (p->opts.count_evals) {  \
+      PK_BWD_T(B, M, true);     \
+    }                           \
+    PK_BWD_T(B, M, false);      \
+  }
   const bool tma = p->opts.stage_bwd == PK_STAGE_BULK;
   switch (p->opts.batch_bwd) {
     case 64:

@@ -294,11 +294,13 @@ pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *
                                               ws, ctr, status, target, dimg, st)                                \
                     : launch_fwd<B, M, 16, C>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, \
                                               ws, ctr, status, target, dimg, st)
-#define PK_FWD(B, M)          \
-  if (p->opts.count_evals) {  \
-    PK_FWD_T(B, M, true);     \
-  }                           \
-  PK_FWD_T(B, M, false)
+#define PK_FWD(B, M)            \
+  {                             \
+    if (p->opts.count_evals) {  \
+      PK_FWD_T(B, M, true);     \
+    }                           \
+    PK_FWD_T(B, M, false);      \
+  }
   const bool tma = p->opts.stage_fwd == PK_STAGE_BULK;
   switch (p->opts.batch) {
     case 64:
