@@ -17,6 +17,11 @@ namespace {
 constexpr int kScanThreads = 1024;
 
 // woff[i] = number of live texels in mask words [0, i); woff[nwords] = total.
+// One block: each pass covers kScanThreads * kRun consecutive words, a run
+// of kRun per thread (popcounts summed in the thread, one block-wide scan of
+// the run totals, then the run's prefixes written back), so a 1024^2 mask
+// takes one pass instead of 32 barrier-separated steps.
+constexpr int kRun = 32;
 __global__ __launch_bounds__(kScanThreads) void k_word_scan(const uint32_t *__restrict__ occ, int64_t nwords,
                                                             uint32_t *__restrict__ woff,
                                                             pk_device_status *status, int64_t N) {
@@ -25,13 +30,31 @@ __global__ __launch_bounds__(kScanThreads) void k_word_scan(const uint32_t *__re
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_carry = 0;
   __syncthreads();
-  for (int64_t base = 0; base < nwords; base += kScanThreads) {
-    int64_t i = base + tid;
-    uint32_t c = i < nwords ? __popc(occ[i]) : 0u;
-    uint32_t x = c;
+  for (int64_t base = 0; base < nwords; base += (int64_t)kScanThreads * kRun) {
+    const int64_t w0 = base + (int64_t)tid * kRun;
+    uint32_t c[kRun];
+    uint32_t tot = 0;
+    if (w0 + kRun <= nwords && (reinterpret_cast<uintptr_t>(occ) & 15u) == 0) {
+      // a whole run: 16-byte loads (the run starts on a 128-byte boundary)
+      const uint4 *q = reinterpret_cast<const uint4 *>(occ + w0);
+#pragma unroll
+      for (int k = 0; k < kRun / 4; ++k) {
+        const uint4 v = __ldg(q + k);
+        c[4 * k] = __popc(v.x);
+        c[4 * k + 1] = __popc(v.y);
+        c[4 * k + 2] = __popc(v.z);
+        c[4 * k + 3] = __popc(v.w);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) c[k] = w0 + k < nwords ? __popc(__ldg(occ + w0 + k)) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < kRun; ++k) tot += c[k];
+    uint32_t x = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) s_warp[warp] = x;
@@ -40,17 +63,21 @@ __global__ __launch_bounds__(kScanThreads) void k_word_scan(const uint32_t *__re
       uint32_t w = s_warp[lane];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
         if (lane >= o) w += y;
       }
       s_warp[lane] = w;
     }
     __syncthreads();
-    uint32_t carry = s_carry;
-    uint32_t excl = carry + (warp ? s_warp[warp - 1] : 0u) + x - c;
-    if (i < nwords) woff[i] = excl;
+    const uint32_t carry = s_carry;
+    uint32_t run = carry + (warp ? s_warp[warp - 1] : 0u) + x - tot;
+#pragma unroll
+    for (int k = 0; k < kRun; ++k) {
+      if (w0 + k < nwords) woff[w0 + k] = run;
+      run += c[k];
+    }
     __syncthreads();
-    if (tid == kScanThreads - 1) s_carry = excl + c;
+    if (tid == 0) s_carry = carry + s_warp[31];
     __syncthreads();
   }
   if (tid == 0) {

@@ -98,7 +98,7 @@ def test_project_matches_oracle(orc):
 # a3 binning and sort: bit-exact on identical FP32 inputs
 # ---------------------------------------------------------------------------
 
-def _synthetic_records(views, N, seed):
+def _synthetic_records(views, N, seed, huge=True):
     rng = np.random.default_rng(seed)
     V = len(views)
     rec = np.zeros((V, N, 12), np.float32)
@@ -120,7 +120,8 @@ def _synthetic_records(views, N, seed):
         rec[v, :, 8:11] = rng.uniform(0, 1, (N, 3))
     rec[:, ::13, 7] = 0                          # culled pairs
     rec[:, 5::17, 6] = rec[:, 5, 6][:, None]     # exact depth ties
-    rec[:, 7::29, 7] = 4000                      # footprints larger than the view
+    if huge:
+        rec[:, 7::29, 7] = 4000                  # footprints larger than the view
     return rec
 
 
@@ -130,10 +131,10 @@ def _records_plan(views, N, bin_mode="ellipse", tile=16, **kw):
     return pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, bin_mode=bin_mode, tile=tile, **kw)
 
 
-def _records_setup(seed, N=700):
+def _records_setup(seed, N=700, huge=True):
     views = [synth.scenes.pinhole((0, 0, -3), 150, 100), synth.scenes.pinhole((0, 0, -3), 67, 131),
              synth.scenes.pinhole((0, 0, -3), 16, 16)]
-    rec = _synthetic_records(views, N, seed)
+    rec = _synthetic_records(views, N, seed, huge)
     return views, rec
 
 
@@ -142,11 +143,14 @@ def _records_setup(seed, N=700):
                                                  (1, "ellipse", 32, (8, 8)), (3, "rect", 32, (8, 8)),
                                                  (2, "ellipse", 16, (11, 11)), (5, "ellipse", 32, (11, 8)),
                                                  (6, "rect", 16, (8, 11))])
-def test_bin_and_sort_bit_exact(orc, seed, mode, tile, bits):
+@pytest.mark.parametrize("huge", [True, False])
+def test_bin_and_sort_bit_exact(orc, seed, mode, tile, bits, huge):
     """Every tile's list bit for bit, for either radix digit width of the
-    depth sort and of the tile sort (bits = (depth, tile))."""
+    depth sort and of the tile sort (bits = (depth, tile)); with footprints
+    larger than the view among the pairs (warps walk their candidates
+    together) or without (most warps walk them lane by lane)."""
     pk = _pk()
-    views, rec = _records_setup(seed)
+    views, rec = _records_setup(seed, huge=huge)
     V, N = rec.shape[:2]
     plan = _records_plan(views, N, mode, tile, sort_bits_depth=bits[0], sort_bits_tile=bits[1])
     ws = pk.make_workspace(plan)
