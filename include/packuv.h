@@ -229,10 +229,13 @@ pk_status pk_autotune(pk_plan *plan, const float *records, uint32_t *sorted_vals
  * for another plan), before any other call and outside graph capture. */
 pk_status pk_workspace_init(const pk_plan *plan, void *workspace, pk_stream_t stream);
 
-/* Copy the device status block to *out (enqueues a copy on `stream` and
- * synchronises that stream).  The copy goes through a small pinned host
- * buffer that the plan allocates on first use and frees in
- * pk_plan_destroy, so one plan's status is read by one thread at a time. */
+/* Copy the device status block to *out: one small kernel on `stream`
+ * writes it into a small pinned, device-mapped host buffer of the plan
+ * (allocated on first use, freed by pk_plan_destroy; no copy engine, so the
+ * read never waits behind the caller's copies on other streams), then the
+ * call synchronises `stream`.  One plan's status is read by one thread at
+ * a time.  Returns PK_ERR_CAPACITY / PK_ERR_TIMEOUT when those flags are
+ * set (the block is copied either way). */
 pk_status pk_read_status(const pk_plan *plan, const void *workspace, pk_stream_t stream,
                          pk_device_status *out);
 

@@ -152,10 +152,6 @@ __device__ __forceinline__ uint32_t pack_rect(int a, int b) { return (uint32_t)a
 // receiving candidates from the count pass, so the emission need not test
 // them again.
 constexpr uint32_t kMaskBits = 64;
-// When no pair of a warp has more candidates than this, each lane walks its
-// own (no owner search per candidate); larger footprints share the work of
-// the warp's lanes candidate by candidate.
-constexpr uint32_t kLaneWalk = 16;
 
 // Per-warp staging of 32 splats' candidate rectangles for the cooperative
 // walk over their candidate tiles (one candidate per lane per step).
@@ -266,29 +262,6 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
       if (p < (uint64_t)pairs) {
         cnt[p] = ncand;
         pinfo[p] = make_uint4(0u, 0u, pack_rect(ws.r0.x, ws.r0.y), pack_rect(ws.r0.z, ncand ? (int)ncand / ws.r0.z : 0));
-      }
-      continue;
-    }
-    // every pair of the warp small: each lane tests its own candidates,
-    // row by row (the same tests and mask bits as the cooperative walk)
-    if (__reduce_max_sync(0xffffffffu, ncand) <= kLaneWalk) {
-      uint32_t mine = 0;
-      uint64_t mask = 0;
-      if (ncand) {
-        const Foot f{ws.g0.x, ws.g0.y, ws.g0.z, ws.g0.w, ws.g1.x, ws.g1.y, ws.g1.z, ws.g1.w};
-        const int wt = ws.r0.z, ht = (int)ncand / wt;
-        uint32_t local = 0;
-        for (int ly = 0; ly < ht; ++ly)
-          for (int lx = 0; lx < wt; ++lx, ++local)
-            if (tile_hit(f, ws.r0.x + lx, ws.r0.y + ly, ws.r0.w, ws.r1.x, T)) {
-              ++mine;
-              mask |= uint64_t(1) << local;
-            }
-      }
-      if (p < (uint64_t)pairs) {
-        cnt[p] = mine;
-        pinfo[p] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), pack_rect(ws.r0.x, ws.r0.y),
-                              pack_rect(ws.r0.z, ncand ? (int)ncand / ws.r0.z : 0));
       }
       continue;
     }
@@ -871,30 +844,6 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
     uint32_t off0 = 0;
     if (lane == 0) off0 = offs[w * 32];
     off0 = __shfl_sync(0xffffffffu, off0, 0);
-    // every pair of the warp with a receive mask (or the rectangle rule) and
-    // few candidates: each lane writes its own entries, in candidate order,
-    // from its pair's offset on (the positions of the cooperative walk)
-    const bool masked = mode == PK_BIN_RECT || (uint32_t)ws.r1.w <= kMaskBits;
-    if (__all_sync(0xffffffffu, masked) && __reduce_max_sync(0xffffffffu, ncand) <= kLaneWalk) {
-      if (ncand) {
-        const uint32_t base = (uint32_t)ws.r1.y, wt = (uint32_t)ws.r0.z, tx = (uint32_t)ws.r1.z;
-        uint32_t at = k < n ? offs[k] : dups;
-        for (uint32_t local = 0; local < ncand; ++local) {
-          if (mode != PK_BIN_RECT && !((msk >> local) & 1u)) continue;
-          uint32_t ly, lx;
-          divmod_small(local, wt, rw, ly, lx);
-          if (at < dups) {
-            keys[at] = base + ly * tx + lx;
-            vals[at] = p;
-          } else {   // more receiving tiles than counted: never write past the entries
-            atomicOr(&status->flags, PK_DEV_BOUNDS);
-            ctr->sort_abort = 1u;
-          }
-          ++at;
-        }
-      }
-      continue;
-    }
     s_ws[warp][lane] = ws;
     __syncwarp();
     const uint32_t incl = warp_incl_scan(ncand);

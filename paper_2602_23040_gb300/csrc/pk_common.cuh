@@ -93,7 +93,7 @@ struct pk_plan {
   int32_t *h_fview_off;    // [F+1]
   int32_t *h_fview_idx;    // [V]
   int4 h_segtab[2 * pk::kSortBlocks];   // block tables of the segmented sorts (copied to the device)
-  void *h_status;          // pinned host copy of the status block and counters (first pk_read_status)
+  void *h_status;          // mapped pinned host copy of the status block and counters (first pk_read_status)
 };
 
 namespace pk {

@@ -45,6 +45,16 @@ __global__ __launch_bounds__(256) void k_zero(ZeroSpans z) {
   }
 }
 
+// Status block and counters -> host memory mapped into the device: one
+// block's stores, no copy engine.  (A device-to-host copy can queue on a
+// copy engine behind the caller's unrelated host-to-device copies of
+// another stream -- the next iteration's inputs -- and wait for them.)
+__global__ void k_status_out(const uint32_t *__restrict__ st, int nst, const uint32_t *__restrict__ ctr, int nctr,
+                             uint32_t *host_st, uint32_t *host_ctr) {
+  for (int i = threadIdx.x; i < nst; i += blockDim.x) host_st[i] = st[i];
+  for (int i = threadIdx.x; i < nctr; i += blockDim.x) host_ctr[i] = ctr[i];
+}
+
 }  // namespace
 
 // One kernel instead of cudaMemsetAsync: inside a CUDA graph a memset node
@@ -386,22 +396,24 @@ extern "C" pk_status pk_workspace_init(const pk_plan *p, void *ws, pk_stream_t s
 extern "C" pk_status pk_read_status(const pk_plan *p, const void *ws, pk_stream_t stream, pk_device_status *out) {
   if (!p || !ws || !out) return PK_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // both blocks land in a small pinned buffer of the plan (allocated on
-  // first use), so the copies are plain asynchronous ones instead of going
-  // through the driver's staging of pageable memory
+  // both blocks land in a small mapped pinned buffer of the plan (allocated
+  // on first use), written by one small kernel on `stream`
   constexpr size_t kCtrOff = (sizeof(pk_device_status) + 15) & ~size_t(15);
   pk_plan *pm = const_cast<pk_plan *>(p);
-  if (!pm->h_status && cudaMallocHost(&pm->h_status, kCtrOff + sizeof(DevCounters)) != cudaSuccess) {
-    pm->h_status = nullptr;
-    return PK_ERR_CUDA;
+  if (!pm->h_status) {
+    if (cudaHostAlloc(&pm->h_status, kCtrOff + sizeof(DevCounters), cudaHostAllocMapped) != cudaSuccess) {
+      pm->h_status = nullptr;
+      return PK_ERR_CUDA;
+    }
   }
+  void *dmap = nullptr;
+  if (cudaHostGetDevicePointer(&dmap, pm->h_status, 0) != cudaSuccess || !dmap) return PK_ERR_CUDA;
   char *hb = static_cast<char *>(pm->h_status);
-  if (cudaMemcpyAsync(hb, at<char>(const_cast<void *>(ws), p->ws.status), sizeof(*out), cudaMemcpyDeviceToHost,
-                      st) != cudaSuccess)
-    return PK_ERR_CUDA;
-  if (cudaMemcpyAsync(hb + kCtrOff, at<char>(const_cast<void *>(ws), p->ws.counters), sizeof(DevCounters),
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return PK_ERR_CUDA;
+  static_assert(sizeof(pk_device_status) % 4 == 0 && sizeof(DevCounters) % 4 == 0, "status words");
+  k_status_out<<<1, 64, 0, st>>>(at<uint32_t>(const_cast<void *>(ws), p->ws.status), (int)(sizeof(*out) / 4),
+                                 at<uint32_t>(const_cast<void *>(ws), p->ws.counters), (int)(sizeof(DevCounters) / 4),
+                                 static_cast<uint32_t *>(dmap), reinterpret_cast<uint32_t *>(static_cast<char *>(dmap) + kCtrOff));
+  if (check_launch() != PK_OK) return PK_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PK_ERR_CUDA;
   DevCounters c;
   memcpy(out, hb, sizeof(*out));
