@@ -752,7 +752,10 @@ def main():
                                        "first_upload": u_ev[0][0].elapsed_time(u_ev[0][1]),
                                        "each": [round(x, 3) for x in step_ms],
                                        "phases_each": {n: [round(x, 3) for x in v] for n, v in host.items()},
-                                       "graph_each": [round(a.elapsed_time(b), 3) for a, b in g_ev]},
+                                       "graph_each": [round(a.elapsed_time(b), 3) for a, b in g_ev],
+                                       "upload_each": [round(a.elapsed_time(b), 3) for a, b in u_ev],
+                                       "upload_start_lag_each": [round(g_ev[k][0].elapsed_time(u_ev[k + 1][0]), 3)
+                                                                 for k in range(ke - 1)]},
                       "steps": ke, "host_cpus": host_cpus}
         if cpus_before is not None:
             os.sched_setaffinity(0, cpus_before)

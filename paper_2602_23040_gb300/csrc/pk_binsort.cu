@@ -128,7 +128,14 @@ __device__ __forceinline__ void shrink_to_footprint(float mx, float my, float a,
                                                     int &ty0, int &tx1, int &ty1) {
   const float det = a * c - b * b;
   if (!(a > 0.f) || !(c > 0.f) || !(det > 0.f) || !isfinite(det)) return;
-  const float ex = 3.f * sqrtf(c / det) * 1.01f + 1.f, ey = 3.f * sqrtf(a / det) * 1.01f + 1.f;
+  // MUFU reciprocal and square root (relative error near 2^-22): the 1 %
+  // and one-pixel widening dwarfs it, so the box still holds every tile
+  // the exact test accepts
+  float idet, sx, sy;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(idet) : "f"(det));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sx) : "f"(c * idet));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(sy) : "f"(a * idet));
+  const float ex = 3.f * sx * 1.01f + 1.f, ey = 3.f * sy * 1.01f + 1.f;
   // tile tx holds pixel centres [tx T + 0.5, tx T + T - 0.5]
   const float rT = 1.f / (float)T;   // T is a power of two: x * rT == x / T exactly
   const float fx0 = floorf((mx - ex - 0.5f) * rT), fx1 = floorf((mx + ex - 0.5f) * rT);
@@ -699,8 +706,41 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
       break;
     }
     parity[cur] ^= 1u;
-    // stable warp-level ranking: items in (warp, item, lane) order
     uint32_t key[C::kItems], rank[C::kItems];
+    // a tile whose keys all share one digit (e.g. the top byte of depths
+    // within one binade pair) keeps its order: its run goes out as it is
+    {
+      const uint32_t d0 = (bk[0] >> shift) & mask;   // valid >= 1 here
+      bool same = true;
+#pragma unroll
+      for (int j = 0; j < C::kItems; ++j) {
+        const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);
+        if (li < valid) same = same && ((bk[li] >> shift) & mask) == d0;
+      }
+      if (__syncthreads_and(same)) {
+        const uint32_t o0 = s_gbase[d0];
+        bool bad = false;
+        for (uint32_t i = tid; i < valid; i += kThreads) {
+          const uint64_t o = (uint64_t)o0 + i;
+          if (o >= n) {   // a histogram out of step with the keys: never write past the items
+            bad = true;
+            continue;
+          }
+          kout[o] = bk[i];
+          vout[o] = bv[i];
+        }
+        if (bad) {
+          atomicOr(&status->flags, PK_DEV_BOUNDS);
+          *abort_flag = 1u;
+        }
+        __syncthreads();
+        if (tid == 0) s_gbase[d0] = o0 + valid;
+        fence_proxy_async();   // this buffer's generic reads before the next TMA into it
+        __syncthreads();
+        continue;
+      }
+    }
+    // stable warp-level ranking: items in (warp, item, lane) order
 #pragma unroll
     for (int j = 0; j < C::kItems; ++j) {
       const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);

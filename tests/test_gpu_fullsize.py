@@ -123,3 +123,24 @@ def test_config4_full_size_fp16_and_masters(orc):
           f"{frac:.2e} (oracle FP16 vs masters: mean {float(quant.mean()):.2e}, p99 "
           f"{float(np.quantile(quant, 0.99)):.2e}, max {float(quant.max()):.2e})")
     assert mean <= 2e-3
+
+
+def test_config5_at_16px_tiles_past_a_billion_entries():
+    """The 208-view sequence binned for 16 px tiles: about 1.6 G (pair, tile)
+    entries, past 2^30, through the same 32-bit entry offsets (the plan
+    caps entries at 0xFFFFF000); its images and transmittance are bit for
+    bit those of the 32 px plan (images do not depend on the tile side)."""
+    import paper_2602_23040_gb300 as pk
+    sc = synth.config_scene(5)
+    atlas, occ, dyn = H.upload(sc)
+    out = {}
+    for tile in (32, 16):
+        r = pk.Renderer(pk.Plan.for_scene(sc, tile=tile))
+        st = r.ensure_capacity(atlas, occ, dyn)
+        assert st["flags"] == 0, st
+        out[tile] = (int(st["dups"]), r.image.clone(), r.T.clone())
+        del r
+        torch.cuda.empty_cache()
+    print(f"entries: 32 px {out[32][0]:,}, 16 px {out[16][0]:,}")
+    assert out[16][0] > (1 << 30) and out[16][0] > 2 * out[32][0]
+    assert torch.equal(out[16][1], out[32][1]) and torch.equal(out[16][2], out[32][2])
