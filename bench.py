@@ -148,8 +148,10 @@ def algorithmic_bytes(plan, texel_bytes, dups, n_dyn):
 # Sources of each rooflined kernel: the DRAM traffic measured by ncu is
 # reported only while these still hash to the profiled version.
 KERNEL_SOURCES = {
-    "a4_rasterize_fwd_l1": ("k_raster_fwd", ["pk_raster_fwd.cu", "pk_raster.cuh", "pk_common.cuh", "pk_tma.cuh"]),
-    "a5_rasterize_bwd": ("k_raster_bwd", ["pk_raster_bwd.cu", "pk_raster.cuh", "pk_common.cuh", "pk_tma.cuh"]),
+    "a4_rasterize_fwd_l1": ("k_raster_fwd", ["pk_raster_fwd.cu", "pk_raster.cuh", "pk_f32x2.cuh", "pk_common.cuh",
+                                             "pk_tma.cuh"]),
+    "a5_rasterize_bwd": ("k_raster_bwd", ["pk_raster_bwd.cu", "pk_raster.cuh", "pk_f32x2.cuh", "pk_common.cuh",
+                                          "pk_tma.cuh"]),
 }
 
 

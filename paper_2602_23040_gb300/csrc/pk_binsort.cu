@@ -630,7 +630,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
     const uint32_t *__restrict__ hist, pk_device_status *status, SegSpec sp, uint32_t *abort_flag,
-    uint32_t first_polls) {
+    uint32_t first_polls, bool try_single) {
   using C = Radix<RB, IT>;
   constexpr int kTile = C::kTile;
   constexpr int kSpan = Down<RB, IT>::kSpan;
@@ -707,9 +707,11 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     }
     parity[cur] ^= 1u;
     uint32_t key[C::kItems], rank[C::kItems];
-    // a tile whose keys all share one digit (e.g. the top byte of depths
-    // within one binade pair) keeps its order: its run goes out as it is
-    {
+    // a tile whose keys all share one digit keeps its order: its run goes
+    // out as it is (tried only where that is likely -- the top byte of the
+    // depths, which all lie within a binade or two -- since the check costs
+    // a pass over the tile)
+    if (try_single) {
       const uint32_t d0 = (bk[0] >> shift) & mask;   // valid >= 1 here
       bool same = true;
 #pragma unroll
@@ -1009,7 +1011,7 @@ template <int RB, int IT>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
                         pk_device_status *status, SegSpec sp, uint32_t *abort_flag, uint32_t first_polls,
-                        cudaStream_t st) {
+                        bool try_single, cudaStream_t st) {
   using C = Radix<RB, IT>;
   if (cudaFuncSetAttribute(k_radix_downsweep<RB, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Down<RB, IT>::kSmem) != cudaSuccess)
@@ -1018,7 +1020,7 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
   k_radix_upsweep<RB, IT><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist, sp);
   k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
   k_radix_downsweep<RB, IT><<<nblocks, kThreads, Down<RB, IT>::kSmem, st>>>(
-      kin, vin, kout, vout, n_dev, n_host, shift, mask, hist, status, sp, abort_flag, first_polls);
+      kin, vin, kout, vout, n_dev, n_host, shift, mask, hist, status, sp, abort_flag, first_polls, try_single);
   return check_launch();
 }
 
@@ -1029,11 +1031,11 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 // but run fewer blocks per SM and scatter into more runs).
 pk_status radix_pass(bool entries, int rb, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
-                     pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls, cudaStream_t st,
-                     SegSpec sp = SegSpec{nullptr, nullptr}) {
+                     pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls, bool try_single,
+                     cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}) {
 #define PK_PASS(RB, IT)                                                                                        \
   return radix_pass_rb<RB, IT>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, sp,  \
-                               abort_flag, first_polls, st)
+                               abort_flag, first_polls, try_single, st)
   if (entries) {
     if (rb > 8) PK_PASS(11, kEntryItems);
     PK_PASS(8, kEntryItems);
@@ -1185,7 +1187,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
     if ((e = radix_pass(false, rd, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist,
-                        seg ? npseg : pair_blocks(rd), status, &ctr->sort_abort, p->first_polls, st, psp)) != PK_OK)
+                        seg ? npseg : pair_blocks(rd), status, &ctr->sort_abort, p->first_polls, pass == np - 1, st,
+                        psp)) != PK_OK)
       return e;
     shift += widths[pass];
   }
@@ -1223,7 +1226,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     const int a = pass & 1, b = a ^ 1;
     shift -= widths[pass];
     if ((e = radix_pass(true, rt, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
-                        status, &ctr->sort_abort, p->first_polls, st, sp)) != PK_OK)
+                        status, &ctr->sort_abort, p->first_polls, false, st, sp)) != PK_OK)
       return e;
   }
   k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], seg ? key_bits : 0,

@@ -6,6 +6,7 @@
 #pragma once
 
 #include "pk_common.cuh"
+#include "pk_f32x2.cuh"
 
 namespace pk {
 
@@ -136,42 +137,6 @@ __device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint3
   }
   const float4 *r = reinterpret_cast<const float4 *>(rec + (size_t)pid * kRec);
   stage_from(__ldg(r), __ldg(r + 1), __ldg(r + 2), pid, s, j);
-}
-
-// Two FP32 values in one 64-bit register for the packed FP32 instructions
-// of this GPU generation (add / sub / mul / fma .rn.f32x2): one issue does
-// both round-to-nearest operations, each with exactly the scalar result.
-// The backward runs two pixels of a thread (same column, rows apart)
-// through them side by side.
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
-  f32x2 v;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
-  return v;
-}
-__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f32x2 dup2(float v) { return pack2(v, v); }
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
-  f32x2 d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
-  f32x2 d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
-  f32x2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
-  f32x2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
 }
 
 // The exponent power = k q = A dx^2 + B dx dy + C dy^2 of a staged splat at

@@ -9,11 +9,15 @@
 // the 32 x 32 tile with the same separable window (the adjoint of the
 // window sums).  Every pass is register-tiled: a thread produces 6 or 8
 // consecutive outputs of one row or column from one sliding read of the
-// inputs, so shared-memory reads are about 1/4 of the multiply-adds.
+// inputs, so shared-memory reads are about 1/4 of the multiply-adds.  The
+// sums travel in pairs -- (X, Y), (XX, YY) and, backwards, (d1, d11) -- so
+// each tap is one packed FP32 multiply-add per pair (two round-to-nearest
+// results, each the scalar one) plus one scalar for the fifth sum.
 // Image and target are read once per tile (plus halo) and the gradient
 // written once; the arithmetic (about 400 FP32 operations per value)
 // bounds the kernel.
 #include "pk_common.cuh"
+#include "pk_f32x2.cuh"
 
 using namespace pk;
 
@@ -40,8 +44,10 @@ constexpr int kGE = 8;   // stage E: tile rows per item (32 = 4 x 8)
 
 struct SsimSmem {
   float x[kI][kIP], y[kI][kIP];       // inputs, 0 outside the image
-  float h[5][kI][kMP];                // horizontal sums; later [3][kM][kTP] backward sums
-  float d[3][kM][kMP];                // partial derivatives of the SSIM map
+  f32x2 h01[kI][kMP], h23[kI][kMP];   // horizontal sums (X, Y), (XX, YY); later the backward
+  float h4[kI][kMP];                  //   sums ((d1, d11) pairs, d12) on [kM][kTP]; XY
+  f32x2 d01[kM][kMP];                 // partial derivatives of the SSIM map: (d1, d11), d12
+  float d2[kM][kMP];
 };
 
 __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restrict__ img,
@@ -62,8 +68,13 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
   const float *X = img + 3 * view.pix_off + c * plane, *Y = tgt + 3 * view.pix_off + c * plane;
   const int tid = threadIdx.x;
   float w[2 * kR + 1];
+  f32x2 wd[2 * kR + 1];   // each weight twice, for the packed pairs
 #pragma unroll
-  for (int j = 0; j <= 2 * kR; ++j) w[j] = c_w[j];
+  for (int j = 0; j <= 2 * kR; ++j) {
+    w[j] = c_w[j];
+    wd[j] = dup2(w[j]);
+  }
+  const f32x2 z2 = dup2(0.f);
 
   // A: inputs over [ty0 - 10, ty0 + 42) x [tx0 - 10, tx0 + 42), every load
   // of a thread issued before the first store
@@ -94,30 +105,35 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
   // and kGB consecutive window-sum columns (threads walk down the rows)
   for (int it = tid; it < kI * (kM / kGB); it += kSsimThreads) {
     const int g = it / kI, r = it - g * kI, q0 = g * kGB;
-    float a[5][kGB];
+    f32x2 a01[kGB], a23[kGB];
+    float a4[kGB];
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-      for (int o = 0; o < kGB; ++o) a[k][o] = 0.f;
+    for (int o = 0; o < kGB; ++o) {
+      a01[o] = z2;
+      a23[o] = z2;
+      a4[o] = 0.f;
+    }
 #pragma unroll
     for (int t = 0; t < kGB + 2 * kR; ++t) {
       const float xv = S.x[r][q0 + t], yv = S.y[r][q0 + t];
-      const float xx2 = xv * xv, yy2 = yv * yv, xy = xv * yv;
+      const f32x2 v = pack2(xv, yv);
+      const f32x2 sq = mul2(v, v);
+      const float xy = xv * yv;
 #pragma unroll
       for (int o = 0; o < kGB; ++o) {
         const int j = t - o;
         if (j < 0 || j > 2 * kR) continue;
-        a[0][o] = fmaf(w[j], xv, a[0][o]);
-        a[1][o] = fmaf(w[j], yv, a[1][o]);
-        a[2][o] = fmaf(w[j], xx2, a[2][o]);
-        a[3][o] = fmaf(w[j], yy2, a[3][o]);
-        a[4][o] = fmaf(w[j], xy, a[4][o]);
+        a01[o] = fma2(wd[j], v, a01[o]);
+        a23[o] = fma2(wd[j], sq, a23[o]);
+        a4[o] = fmaf(w[j], xy, a4[o]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-      for (int o = 0; o < kGB; ++o) S.h[k][r][q0 + o] = a[k][o];
+    for (int o = 0; o < kGB; ++o) {
+      S.h01[r][q0 + o] = a01[o];
+      S.h23[r][q0 + o] = a23[o];
+      S.h4[r][q0 + o] = a4[o];
+    }
   }
   __syncthreads();
   // C: vertical window sums on kGC consecutive rows of one column, then the
@@ -126,22 +142,25 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
   float ssim_sum = 0.f;
   for (int it = tid; it < kM * (kM / kGC); it += kSsimThreads) {
     const int g = it / kM, q = it - g * kM, r0 = g * kGC;
-    float a[5][kGC];
+    f32x2 a01[kGC], a23[kGC];
+    float a4[kGC];
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-      for (int o = 0; o < kGC; ++o) a[k][o] = 0.f;
+    for (int o = 0; o < kGC; ++o) {
+      a01[o] = z2;
+      a23[o] = z2;
+      a4[o] = 0.f;
+    }
 #pragma unroll
     for (int t = 0; t < kGC + 2 * kR; ++t) {
-      float hv[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) hv[k] = S.h[k][r0 + t][q];
+      const f32x2 h01 = S.h01[r0 + t][q], h23 = S.h23[r0 + t][q];
+      const float h4 = S.h4[r0 + t][q];
 #pragma unroll
       for (int o = 0; o < kGC; ++o) {
         const int j = t - o;
         if (j < 0 || j > 2 * kR) continue;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) a[k][o] = fmaf(w[j], hv[k], a[k][o]);
+        a01[o] = fma2(wd[j], h01, a01[o]);
+        a23[o] = fma2(wd[j], h23, a23[o]);
+        a4[o] = fmaf(w[j], h4, a4[o]);
       }
     }
     const int xx = tx0 - kR + q;
@@ -150,7 +169,10 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
       const int r = r0 + o, yy = ty0 - kR + r;
       float d1 = 0.f, d11 = 0.f, d12 = 0.f;
       if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-        const float m1 = a[0][o], m2 = a[1][o], e11 = a[2][o], e22 = a[3][o], e12 = a[4][o];
+        float m1, m2, e11, e22;
+        unpack2(a01[o], m1, m2);
+        unpack2(a23[o], e11, e22);
+        const float e12 = a4[o];
         const float A1 = 2.f * m1 * m2 + kC1, A2 = 2.f * (e12 - m1 * m2) + kC2;
         const float B1 = m1 * m1 + m2 * m2 + kC1, B2 = (e11 - m1 * m1) + (e22 - m2 * m2) + kC2;
         // approximate reciprocals (2 ulp): far inside the FP32 tolerance of the loss
@@ -162,39 +184,41 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
         d12 = 2.f * s * iA2;
         if (r >= kR && r < kR + kT && q >= kR && q < kR + kT) ssim_sum += s;
       }
-      S.d[0][r][q] = d1;
-      S.d[1][r][q] = d11;
-      S.d[2][r][q] = d12;
+      S.d01[r][q] = pack2(d1, d11);
+      S.d2[r][q] = d12;
     }
   }
   __syncthreads();
   // D: backward horizontal sums of the three maps: one row of the 42 region,
-  // kGD consecutive tile columns (into the h buffer, as [3][kM][kTP])
-  float(*hb)[kM][kTP] = reinterpret_cast<float(*)[kM][kTP]>(&S.h[0][0][0]);
+  // kGD consecutive tile columns (into the h buffers, as [kM][kTP])
+  f32x2(*hb01)[kTP] = reinterpret_cast<f32x2(*)[kTP]>(&S.h01[0][0]);
+  float(*hb2)[kTP] = reinterpret_cast<float(*)[kTP]>(&S.h4[0][0]);
   for (int it = tid; it < kM * (kT / kGD); it += kSsimThreads) {
     const int g = it / kM, r = it - g * kM, q0 = g * kGD;
-    float a[3][kGD];
+    f32x2 b01[kGD];
+    float b2[kGD];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int o = 0; o < kGD; ++o) a[k][o] = 0.f;
+    for (int o = 0; o < kGD; ++o) {
+      b01[o] = z2;
+      b2[o] = 0.f;
+    }
 #pragma unroll
     for (int t = 0; t < kGD + 2 * kR; ++t) {
-      float dv[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) dv[k] = S.d[k][r][q0 + t];
+      const f32x2 d01 = S.d01[r][q0 + t];
+      const float d2 = S.d2[r][q0 + t];
 #pragma unroll
       for (int o = 0; o < kGD; ++o) {
         const int j = t - o;
         if (j < 0 || j > 2 * kR) continue;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) a[k][o] = fmaf(w[j], dv[k], a[k][o]);
+        b01[o] = fma2(wd[j], d01, b01[o]);
+        b2[o] = fmaf(w[j], d2, b2[o]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int o = 0; o < kGD; ++o) hb[k][r][q0 + o] = a[k][o];
+    for (int o = 0; o < kGD; ++o) {
+      hb01[r][q0 + o] = b01[o];
+      hb2[r][q0 + o] = b2[o];
+    }
   }
   __syncthreads();
   // E: vertical sums onto kGE rows of one tile column, combined with X, Y
@@ -205,22 +229,23 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
     const int g = it / kT, q = it - g * kT, r0 = g * kGE;
     const int xx = tx0 + q;
     if (xx >= W) continue;
-    float a[3][kGE];
+    f32x2 c01[kGE];
+    float c2[kGE];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int o = 0; o < kGE; ++o) a[k][o] = 0.f;
+    for (int o = 0; o < kGE; ++o) {
+      c01[o] = z2;
+      c2[o] = 0.f;
+    }
 #pragma unroll
     for (int t = 0; t < kGE + 2 * kR; ++t) {
-      float bv[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) bv[k] = hb[k][r0 + t][q];
+      const f32x2 v01 = hb01[r0 + t][q];
+      const float v2 = hb2[r0 + t][q];
 #pragma unroll
       for (int o = 0; o < kGE; ++o) {
         const int j = t - o;
         if (j < 0 || j > 2 * kR) continue;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) a[k][o] = fmaf(w[j], bv[k], a[k][o]);
+        c01[o] = fma2(wd[j], v01, c01[o]);
+        c2[o] = fmaf(w[j], v2, c2[o]);
       }
     }
 #pragma unroll
@@ -228,7 +253,9 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
       const int r = r0 + o, yy = ty0 + r;
       if (yy >= H) break;
       const float xv = S.x[r + 2 * kR][q + 2 * kR], yv = S.y[r + 2 * kR][q + 2 * kR];
-      const float dS = a[0][o] + 2.f * xv * a[1][o] + yv * a[2][o];
+      float s0, s1;
+      unpack2(c01[o], s0, s1);
+      const float dS = s0 + 2.f * xv * s1 + yv * c2[o];
       const float dd = xv - yv;
       l1_sum += fabsf(dd);
       const float sg = dd > 0.f ? 1.f : (dd < 0.f ? -1.f : 0.f);
