@@ -483,6 +483,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--prefetch", type=int, default=6, help="input sets in flight in the end-to-end loop")
     ap.add_argument("--profile", action="store_true", help="short run for a profiler: no extras")
     ap.add_argument("--no-rows", action="store_true", help="skip the rows after the render step")
     ap.add_argument("--with-rows", action="store_true", help="time the rows after the render step even with --profile")
@@ -663,61 +664,67 @@ def main():
     if not args.profile and not args.no_e2e:
         # End to end through the public API with host buffers: every step
         # copies its inputs (atlas and target images) from pinned host
-        # memory and reads its loss back.  The inputs are double-buffered:
-        # the next step's host->device copies run on a second stream while
-        # this step computes (a second graph reads the second buffer pair).
+        # memory and reads its loss back.  The inputs are prefetched D steps
+        # deep (D buffer sets, one captured graph per set): the copies of
+        # the next D - 1 steps run on a second stream while this step
+        # computes, so an occasional slow host-to-device copy (seen at 85 ms
+        # instead of 5.6 ms) lands before its step needs it.
         # the host side runs on the CPUs local to this GPU, so the pinned
         # input buffers are placed (first touch) in the memory nearest to it
         cpus_before, host_cpus = gpu_local_affinity(local)
         h_atlas = torch.from_numpy(scene.atlas).pin_memory()
         h_target = torch.from_numpy(synth.random_target(scene)).pin_memory()
-        bufs = [(atlas, target), (torch.empty_like(atlas), torch.empty_like(target))]
-        g2 = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(stream):
-            r.l1_step(bufs[1][0], occ, dyn, bufs[1][1], grad)      # warm the second buffer pair
-        with torch.cuda.graph(g2, stream=stream):
-            r.l1_step(bufs[1][0], occ, dyn, bufs[1][1], grad)
-        graphs = [g, g2]
+        D = max(2, args.prefetch)
+        bufs = [(atlas, target)] + [(torch.empty_like(atlas), torch.empty_like(target)) for _ in range(D - 1)]
+        graphs = [g]
+        for i in range(1, D):
+            gi = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(stream):
+                r.l1_step(bufs[i][0], occ, dyn, bufs[i][1], grad)      # warm this buffer set
+            with torch.cuda.graph(gi, stream=stream):
+                r.l1_step(bufs[i][0], occ, dyn, bufs[i][1], grad)
+            graphs.append(gi)
         copy_stream = torch.cuda.Stream(dev)
-        ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-        ev_done = [torch.cuda.Event(), torch.cuda.Event()]
-        ke = max(3, min(2 * args.steps, 40))   # the first upload of a run is slow (reported): amortise it
+        ev_in = [torch.cuda.Event() for _ in range(D)]
+        ev_done = [torch.cuda.Event() for _ in range(D)]
+        ke = max(3, min(2 * args.steps, 40))
         # device time of each step's graph and of each upload, for the breakdown
         g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ke)]
         u_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ke)]
 
-        def upload(slot, k):
+        def upload(slot, k, timed=True):
             with torch.cuda.stream(copy_stream):
                 copy_stream.wait_event(ev_done[slot])
-                u_ev[k][0].record(copy_stream)
+                if timed:
+                    u_ev[k][0].record(copy_stream)
                 bufs[slot][0].copy_(h_atlas, non_blocking=True)
                 bufs[slot][1].copy_(h_target, non_blocking=True)
-                u_ev[k][1].record(copy_stream)
+                if timed:
+                    u_ev[k][1].record(copy_stream)
                 ev_in[slot].record(copy_stream)
 
-        # warm-up: two untimed steps of the same pattern (each graph's first
+        # warm-up: one untimed pass over every buffer set (each graph's first
         # replay uploads it to the device; the first copies touch the pinned pages)
-        for k in range(2):
-            upload(k % 2, 0)
+        for k in range(D):
+            upload(k, 0, timed=False)
             with torch.cuda.stream(stream):
-                stream.wait_event(ev_in[k % 2])
-                graphs[k % 2].replay()
-                ev_done[k % 2].record(stream)
+                stream.wait_event(ev_in[k])
+                graphs[k].replay()
+                ev_done[k].record(stream)
             r.status(stream)
         torch.cuda.synchronize(dev)
-        for e_ in ev_done:
-            e_.record(stream)
         # a host loop that feeds the GPU: the interpreter's cyclic garbage
         # collector is held off while it runs (its passes are host pauses
         # unrelated to the library)
         gc.collect()
         gc.disable()
         t0 = time.perf_counter()
-        upload(0, 0)
+        for k in range(min(D - 1, ke)):
+            upload(k % D, k)
         host = {"replay": [], "upload": [], "status": []}
         step_ms = []
         for k in range(ke):
-            slot = k % 2
+            slot = k % D
             h0 = time.perf_counter()
             with torch.cuda.stream(stream):
                 stream.wait_event(ev_in[slot])
@@ -726,8 +733,8 @@ def main():
                 g_ev[k][1].record(stream)
                 ev_done[slot].record(stream)
             h1 = time.perf_counter()
-            if k + 1 < ke:
-                upload(1 - slot, k + 1)
+            if k + D - 1 < ke:
+                upload((k + D - 1) % D, k + D - 1)
             h2 = time.perf_counter()
             s = r.status(stream)          # device -> host read of this step's loss (waits for the step)
             h3 = time.perf_counter()
@@ -741,27 +748,23 @@ def main():
         gap_ms = statistics.median(g_ev[k][1].elapsed_time(g_ev[k + 1][0]) for k in range(ke - 1))
         graph_ms = statistics.median(a.elapsed_time(b) for a, b in g_ev)
         upload_ms = statistics.median(a.elapsed_time(b) for a, b in u_ev)
-        # when the next step's upload starts, from the start of this step's graph
-        upload_lag_ms = statistics.median(g_ev[k][0].elapsed_time(u_ev[k + 1][0]) for k in range(ke - 1))
         out["e2e"] = {"value": plan.P / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
                       "h2d_bytes_per_step": int(h_atlas.numel() * h_atlas.element_size() + h_target.numel() * 4),
                       "d2h_bytes_per_step": int(ctypes_sizeof_status()), "loss": s["loss"],
-                      "pipeline": "inputs double-buffered; next step's copies overlap this step's compute",
+                      "pipeline": f"inputs prefetched {D} steps deep (one buffer set and graph each); the next "
+                                  "steps' copies overlap this step's compute",
                       "graph_ms_per_step": graph_ms, "upload_ms_per_step": upload_ms,
-                      "upload_start_after_graph_start_ms": upload_lag_ms, "device_gap_between_graphs_ms": gap_ms,
+                      "device_gap_between_graphs_ms": gap_ms,
                       "host_ms": {n: statistics.median(v) for n, v in host.items()},
                       "host_step_ms": {"median": statistics.median(step_ms), "max": max(step_ms),
-                                       "first_upload": u_ev[0][0].elapsed_time(u_ev[0][1]),
                                        "each": [round(x, 3) for x in step_ms],
                                        "phases_each": {n: [round(x, 3) for x in v] for n, v in host.items()},
                                        "graph_each": [round(a.elapsed_time(b), 3) for a, b in g_ev],
-                                       "upload_each": [round(a.elapsed_time(b), 3) for a, b in u_ev],
-                                       "upload_start_lag_each": [round(g_ev[k][0].elapsed_time(u_ev[k + 1][0]), 3)
-                                                                 for k in range(ke - 1)]},
+                                       "upload_each": [round(a.elapsed_time(b), 3) for a, b in u_ev]},
                       "steps": ke, "host_cpus": host_cpus}
         if cpus_before is not None:
             os.sched_setaffinity(0, cpus_before)
-        del bufs, g2, h_atlas, h_target
+        del bufs, graphs, h_atlas, h_target
 
     if not args.profile and not args.no_per_view and rank == 0:
         loop = pk.PerViewLoop.for_scene(scene, dev, tile=plan.tile,
