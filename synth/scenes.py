@@ -189,7 +189,8 @@ def make_scene(levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple
                texel_dtype=np.float32, means: str = "clusters", seed: int = BASE_SEED,
                dynamic_frac: float = 0.0, flow_amp: float = 0.05, frame_start: int = 0,
                name: str = "custom", tile: int = 32,
-               log_scale: Tuple[float, float] = (-4.0, 0.5), mean_box: float = 1.0) -> Scene:
+               log_scale: Tuple[float, float] = (-4.0, 0.5), mean_box: float = 1.0,
+               uv_order: bool = True) -> Scene:
     """Generate one scene.
 
     ``occupancy`` is a fraction of texels per level (a float, applied to every
@@ -197,6 +198,8 @@ def make_scene(levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple
     U(0.4, 0.8) per level).  Exactly ``floor(fraction * level texels)``
     texels of each level are occupied.  ``log_scale`` is the (mean, std) of
     the log-scales and ``mean_box`` scales every mean (for small test scenes).
+    ``uv_order``: live texels hold the means in the order of their spherical
+    UV cells (as the method's maps do); False assigns them at random.
     """
     rng = np.random.default_rng(seed)
     aw, ah = atlas_wh
@@ -218,6 +221,19 @@ def make_scene(levels: Sequence[Tuple[int, int, int, int, int]], atlas_wh: Tuple
     n_live = len(ys)
 
     mu0 = _means(rng, n_live, means) * mean_box
+    if uv_order and n_live:
+        # The method's maps hold each Gaussian at the texel of its UV cell
+        # (the spherical cell of eq. uvgs2), so neighbouring texels hold
+        # Gaussians of neighbouring directions.  The live texels are filled
+        # in that order: means sorted by the row-major cell index of their
+        # direction on the base level's w x h grid.
+        w0, h0 = levels[0][0], levels[0][1]
+        rho = np.linalg.norm(mu0, axis=1)
+        theta = np.arctan2(mu0[:, 1], mu0[:, 0])
+        phi = np.arccos(np.clip(mu0[:, 2] / np.maximum(rho, 1e-30), -1.0, 1.0))
+        u = np.minimum(np.floor((np.pi + theta) / (2 * np.pi) * w0), w0 - 1).astype(np.int64)
+        v = np.minimum(np.floor(phi / np.pi * h0), h0 - 1).astype(np.int64)
+        mu0 = mu0[np.lexsort((u, v))]
     ls = rng.normal(log_scale[0], log_scale[1], size=(n_live, 3))
     q = rng.standard_normal((n_live, 4))
     q /= np.linalg.norm(q, axis=1, keepdims=True)

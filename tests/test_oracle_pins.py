@@ -579,7 +579,9 @@ def test_render_bwd_matches_differences_in_record_space(orc):
     g2 = orc.render_bwd(rec, va, 16, vals, ranges, w)
     fields = [0, 1, 2, 3, 4, 5, 8, 9, 10]      # m, conic, opacity, rgb
     n_ok = 0
-    for _ in range(40):
+    for _ in range(120):   # directions whose step flips a decision are skipped
+        if n_ok >= 40:
+            break
         d = np.zeros_like(rec)
         d[..., fields] = rng.standard_normal(rec[..., fields].shape)
         d[rec[..., 7] == 0] = 0
