@@ -161,48 +161,37 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
           hits[k] = __ballot_sync(0xffffffffu, j < nb && block_may_hit(s_box[j], s_q[j], s_a[j].x, s_a[j].y,
                                                                        wx0, wx1, wy0, wy1));
         }
-        // One splat at pixel q of the thread (the pixel is compositing).
-        auto blend = [&](int q, const float4 &a, const float4 &b, const float4 &c, float dx, float zx,
-                         uint32_t pos1) {
-          Hit h;
-          if (splat_alpha(a, b, c.z, dx, zx, py0 + (float)(q * G::kRowStep), h)) {
-            const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, h.alpha));
-            if (Tn < kTMin) {
-              live &= ~(1u << q);
-            } else {
-              const float w = __fmul_rn(h.alpha, T[q]);
-              c0[q] = __fmaf_rn(w, b.z, c0[q]);
-              c1[q] = __fmaf_rn(w, b.w, c1[q]);
-              c2[q] = __fmaf_rn(w, c.x, c2[q]);
-              T[q] = Tn;
-              last[q] = pos1;
-            }
-          }
-        };
-        constexpr uint32_t kAll = (1u << kPx) - 1u;
+        bool any_live = true;
 #pragma unroll
         for (int k = 0; k < kBatch / 32; ++k) {
           uint32_t m = hits[k];
-          while (m) {
+          while (m && any_live) {
             const int j = 32 * k + __ffs(m) - 1;
             m &= m - 1;
             const float4 a = s_a[j], b = s_b[j], c = s_c[j];
             const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
             const uint32_t pos1 = base - s + (uint32_t)j + 1u;
             if (kCount) evals += __popc(live);   // evaluated at every live pixel of the thread
-            if (live == kAll) {   // every pixel of the thread still compositing: no per-pixel test
 #pragma unroll
-              for (int q = 0; q < kPx; ++q) blend(q, a, b, c, dx, zx, pos1);
-            } else {
-#pragma unroll
-              for (int q = 0; q < kPx; ++q)
-                if ((live >> q) & 1u) blend(q, a, b, c, dx, zx, pos1);
+            for (int q = 0; q < kPx; ++q) {
+              if (!((live >> q) & 1u)) continue;
+              Hit h;
+              if (splat_alpha(a, b, c.z, dx, zx, py0 + (float)(q * G::kRowStep), h)) {
+                const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, h.alpha));
+                if (Tn < kTMin) {
+                  live &= ~(1u << q);
+                } else {
+                  const float w = __fmul_rn(h.alpha, T[q]);
+                  c0[q] = __fmaf_rn(w, b.z, c0[q]);
+                  c1[q] = __fmaf_rn(w, b.w, c1[q]);
+                  c2[q] = __fmaf_rn(w, c.x, c2[q]);
+                  T[q] = Tn;
+                  last[q] = pos1;
+                }
+              }
             }
+            any_live = __any_sync(0xffffffffu, live != 0);
           }
-          // whether the warp is done is checked once per word of 32 staged
-          // splats; a warp that finishes inside a word walks the rest of it
-          // with every pixel skipping
-          if (!__any_sync(0xffffffffu, live != 0)) break;
         }
       }
       if (__syncthreads_count(live != 0) == 0) break;

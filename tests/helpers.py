@@ -96,6 +96,19 @@ def check_images(got_img, got_T, ora, tol=IMG_TOL, max_border_frac=0.08, max_thr
                 border=int(border.sum()), border_frac=frac, threshold_frac=tfrac)
 
 
+def zero_on_borderline(w, ora):
+    """dL/dimage w with every channel of the oracle's borderline pixels set
+    to 0.  Where the two sides may take an image decision differently (a
+    depth order or a threshold within FP32 error), the splats that pixel
+    sends gradient to differ as well, so a gradient comparison leaves those
+    pixels out on both sides; the images themselves are still checked
+    there, against each pixel's flip bound."""
+    border = (ora["border"] & IMAGE_BORDER) != 0
+    w = np.array(w, copy=True)
+    w[per_channel(border, ora["view_pixels"])] = 0
+    return w
+
+
 def rel_err(a, b):
     den = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a))

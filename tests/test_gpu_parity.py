@@ -47,9 +47,14 @@ def oracle_run(orc, scene, dimg=None):
     o = orc.forward(scene)
     o["view_pixels"] = [v.width * v.height for v in scene.views]
     if dimg is not None:
-        b = orc.backward(scene, o, dimg.astype(np.float32).astype(np.float64))
-        o.update(b)
-        o["grad_atlas"] = orc.grad_to_atlas(scene, b["grad_soa"], o["texel"])
+        oracle_backward(orc, scene, o, dimg)
+    return o
+
+
+def oracle_backward(orc, scene, o, dimg):
+    b = orc.backward(scene, o, dimg.astype(np.float32).astype(np.float64))
+    o.update(b)
+    o["grad_atlas"] = orc.grad_to_atlas(scene, b["grad_soa"], o["texel"])
     return o
 
 
@@ -383,9 +388,10 @@ def test_end_to_end(orc, which):
           "frames_dyn": lambda: H.scene_small_sh3(frames=2, dyn=0.3),
           "config1": lambda: synth.config_scene(1)}[which]()
     P = sc.pixels
-    w = np.random.default_rng(11).standard_normal(3 * P).astype(np.float32)
+    o = oracle_run(orc, sc)
+    w = H.zero_on_borderline(np.random.default_rng(11).standard_normal(3 * P).astype(np.float32), o)
     plan, r, grad = run_gpu(sc, dimg=w)
-    o = oracle_run(orc, sc, dimg=w)
+    oracle_backward(orc, sc, o, w)
     H.check_images(r.image.cpu().numpy(), r.T.cpu().numpy(), o)
     g = gpu_grad_soa(sc, grad, o["texel"])
     H.check_grads(g, o["grad_soa"])
@@ -412,9 +418,10 @@ def test_rect_and_ellipse_binning_give_the_same_images(orc):
 def test_config2_full_size(orc):
     """1080p single view, 157,286 Gaussians with SH degree 3: images and gradients in full."""
     sc = synth.config_scene(2)
-    w = np.random.default_rng(12).standard_normal(3 * sc.pixels).astype(np.float32)
+    o = oracle_run(orc, sc)
+    w = H.zero_on_borderline(np.random.default_rng(12).standard_normal(3 * sc.pixels).astype(np.float32), o)
     plan, r, grad = run_gpu(sc, dimg=w)
-    o = oracle_run(orc, sc, dimg=w)
+    oracle_backward(orc, sc, o, w)
     H.check_images(r.image.cpu().numpy(), r.T.cpu().numpy(), o)
     H.check_grads(gpu_grad_soa(sc, grad, o["texel"]), o["grad_soa"])
 
