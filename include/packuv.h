@@ -118,7 +118,8 @@ typedef struct pk_options {
                                       depend on it, 32 halves the entries to sort at C3 */
   float znear;                     /* cull z <= znear; default 0.01 */
   float bg[3];                     /* background colour; default 0 */
-  uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs */
+  uint64_t max_dups;               /* capacity of (pair, tile) entries; 0 = 32 * pairs; at most
+                                      2^35 (a larger value is lowered to it) */
   int32_t bin_mode;                /* pk_bin_mode; default PK_BIN_ELLIPSE */
   int32_t batch;                   /* splats staged per batch by pk_rasterize_fwd: 64, 128 or
                                       256 (0 = 128); pk_autotune picks it */
@@ -220,7 +221,7 @@ void pk_plan_destroy(pk_plan *plan);
  * hold the records' lists (the same for every width), and image, T_final,
  * n_contrib and grad2d a forward and backward with the chosen options.
  * Synchronises `stream`; do not call it during graph capture. */
-pk_status pk_autotune(pk_plan *plan, const float *records, uint32_t *sorted_vals, uint32_t *tile_ranges,
+pk_status pk_autotune(pk_plan *plan, const float *records, uint32_t *sorted_vals, uint64_t *tile_ranges,
                       float *image, float *T_final, uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
                       void *workspace, pk_stream_t stream, int32_t *chosen_batch);
 
@@ -290,12 +291,13 @@ pk_status pk_project_and_sh(const pk_plan *plan, const float *soa, float *record
  * list through tile_ranges.
  * records:     [V*N][12] (reads m, conic, z, radius).
  * sorted_vals: out [max_dups] uint32 pair index of each entry.
- * tile_ranges: out [n_tiles][2] uint32 [start, end) into sorted_vals;
+ * tile_ranges: out [n_tiles][2] uint64 [start, end) into sorted_vals (entry
+ *              positions are 64-bit: a plan may hold up to 2^35 entries);
  *              global tile id = tile_off(v) + ty * ceil(W_v/T) + tx.
  * If the entries exceed max_dups the device sets PK_DEV_CAPACITY, records
  * dups_needed and emits nothing (all ranges empty). */
 pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
-                          uint32_t *tile_ranges, void *workspace, pk_stream_t stream);
+                          uint64_t *tile_ranges, void *workspace, pk_stream_t stream);
 
 /* pk_bin_and_sort without a workspace.  The paper has no counterpart: this
  * is a convenience for callers that cannot give the library device memory
@@ -304,8 +306,9 @@ pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *s
  * stall the frame, or a small tool without a device allocator.  Same
  * inputs, outputs and bit-exact result as pk_bin_and_sort; the scratch is a
  * 64 MiB array inside the library (reserved on every GPU that loads it, for
- * the life of the process), so the plan must satisfy 40 * V * N + 12 *
- * max_dups + 152 * V + about 0.8 MB <= 64 MiB, else PK_ERR_TOO_LARGE is
+ * the life of the process), so the plan must satisfy 44 * V * N + 12 *
+ * max_dups + 164 * V + about 1.7 MB <= 64 MiB (with 8-bit radix digits;
+ * about 12.7 MB in place of 1.7 MB with 11-bit ones), else PK_ERR_TOO_LARGE is
  * returned and nothing is enqueued.  n_entries: out, one device uint32 --
  * the entries written; 0xFFFFFFFF if they exceeded max_dups (then nothing
  * was emitted); 0xFFFFFFFE if a bounded device wait gave up or an index
@@ -319,7 +322,7 @@ pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *s
  * plan's view and tile tables from host memory each time and never
  * allocates. */
 pk_status pk_bin_and_sort_noalloc(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
-                                  uint32_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream);
+                                  uint64_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream);
 
 /* a4 -- Supp. "Viewer": C = sum_i T_i alpha_i c_i, T_i = prod_{j<i}
  * (1 - alpha_j), front to back in the order of pk_bin_and_sort, plus
@@ -332,7 +335,7 @@ pk_status pk_bin_and_sort_noalloc(const pk_plan *plan, const float *records, uin
  * Each CTA composites a 16 x 16 block: a 32 px tile's list is walked by the
  * four CTAs of its quadrants. */
 pk_status pk_rasterize_fwd(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
-                           const uint32_t *tile_ranges, float *image, float *T_final,
+                           const uint64_t *tile_ranges, float *image, float *T_final,
                            uint32_t *n_contrib, void *workspace, pk_stream_t stream);
 
 /* a5 -- adjoint of pk_rasterize_fwd (Sec. 4.2 "Objective").  Walks each
@@ -342,7 +345,7 @@ pk_status pk_rasterize_fwd(const pk_plan *plan, const float *records, const uint
  * conic_c, opacity, red, green, blue), conic_b being the off-diagonal
  * entry counted once.  dL_dimage has the layout of image. */
 pk_status pk_rasterize_bwd(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
-                           const uint32_t *tile_ranges, const float *T_final,
+                           const uint64_t *tile_ranges, const float *T_final,
                            const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
                            void *workspace, pk_stream_t stream);
 
@@ -362,12 +365,12 @@ pk_status pk_atlas_scatter_grad(const pk_plan *plan, const float *soa, const flo
  * arguments (and errors) of those calls; stops at the first error. */
 pk_status pk_render_fwd(const pk_plan *plan, const void *atlas, const uint32_t *occ, const uint32_t *dyn,
                         float *soa, uint32_t *texel, uint8_t *dynflag, float *records, uint32_t *sorted_vals,
-                        uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+                        uint64_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
                         void *workspace, pk_stream_t stream);
 
 /* Convenience: the backward, pk_rasterize_bwd -> pk_atlas_scatter_grad. */
 pk_status pk_render_bwd(const pk_plan *plan, const float *soa, const uint8_t *dynflag, const uint32_t *texel,
-                        const float *records, const uint32_t *sorted_vals, const uint32_t *tile_ranges,
+                        const float *records, const uint32_t *sorted_vals, const uint64_t *tile_ranges,
                         const float *T_final, const uint32_t *n_contrib, const float *dL_dimage,
                         float *grad2d, float *grad_atlas, int32_t accumulate, void *workspace,
                         pk_stream_t stream);
@@ -384,7 +387,7 @@ pk_status pk_l1_loss_grad(const pk_plan *plan, const float *image, const float *
  * up to rounding).  Saves writing the image out and reading it back.
  * target: [3 * P] float32, planar per view like the image. */
 pk_status pk_rasterize_fwd_l1(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
-                              const uint32_t *tile_ranges, const float *target, float *image,
+                              const uint64_t *tile_ranges, const float *target, float *image,
                               float *T_final, uint32_t *n_contrib, float *dL_dimage, void *workspace,
                               pk_stream_t stream);
 

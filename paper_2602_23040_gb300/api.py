@@ -16,6 +16,7 @@ import torch
 from . import _native as N
 
 _I32 = torch.int32
+_I64 = torch.int64
 
 
 def _stream(stream) -> C.c_void_p:
@@ -241,7 +242,7 @@ def project_and_sh(plan: Plan, soa, records, ws, stream=None) -> None:
 def bin_and_sort(plan: Plan, records, sorted_vals, tile_ranges, ws, stream=None) -> None:
     rc = N.load().pk_bin_and_sort(plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
                                   _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups),
-                                  _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+                                  _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
                                   _ptr(ws, "workspace"), _stream(stream))
     N.check("pk_bin_and_sort", rc)
 
@@ -250,7 +251,7 @@ def rasterize_fwd(plan: Plan, records, sorted_vals, tile_ranges, image, T_final,
                   stream=None) -> None:
     rc = N.load().pk_rasterize_fwd(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
-        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
         _ptr(image, "image", torch.float32, 3 * plan.P), _ptr(T_final, "T_final", torch.float32, plan.P),
         _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(ws, "workspace"), _stream(stream))
     N.check("pk_rasterize_fwd", rc)
@@ -260,7 +261,7 @@ def rasterize_bwd(plan: Plan, records, sorted_vals, tile_ranges, T_final, n_cont
                   stream=None) -> None:
     rc = N.load().pk_rasterize_bwd(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
-        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
         _ptr(T_final, "T_final", torch.float32, plan.P), _ptr(n_contrib, "n_contrib", _I32, plan.P),
         _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
         _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs), _ptr(ws, "workspace"),
@@ -294,7 +295,7 @@ def rasterize_fwd_l1(plan: Plan, records, sorted_vals, tile_ranges, target, imag
     """rasterize_fwd with the L1 loss gradient fused into its epilogue."""
     rc = N.load().pk_rasterize_fwd_l1(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
-        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
         _ptr(target, "target", torch.float32, 3 * plan.P), _ptr(image, "image", torch.float32, 3 * plan.P),
         _ptr(T_final, "T_final", torch.float32, plan.P), _ptr(n_contrib, "n_contrib", _I32, plan.P),
         _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P), _ptr(ws, "workspace"), _stream(stream))
@@ -323,7 +324,7 @@ def render_fwd(plan: Plan, atlas, occ, dyn, soa, texel, dynflag, records, sorted
         _ptr(dyn, "dyn", _I32, words, allow_none=True), _ptr(soa, "soa", torch.float32, D * plan.G),
         _ptr(texel, "texel", _I32, plan.N), _ptr(dynflag, "dynflag", torch.uint8, plan.N),
         _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
-        _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups), _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
         _ptr(image, "image", torch.float32, 3 * plan.P), _ptr(T_final, "T_final", torch.float32, plan.P),
         _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(ws, "workspace"), _stream(stream))
     N.check("pk_render_fwd", rc)
@@ -338,7 +339,7 @@ def render_bwd(plan: Plan, soa, dynflag, texel, records, sorted_vals, tile_range
         plan.handle, _ptr(soa, "soa", torch.float32, D * plan.G),
         _ptr(dynflag, "dynflag", torch.uint8, plan.N, allow_none=True), _ptr(texel, "texel", _I32, plan.N),
         _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs), _ptr(sorted_vals, "sorted_vals", _I32),
-        _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles), _ptr(T_final, "T_final", torch.float32, plan.P),
+        _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles), _ptr(T_final, "T_final", torch.float32, plan.P),
         _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
         _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs),
         _ptr(grad_atlas, "grad_atlas", torch.float32, F * D * H * W), 1 if accumulate else 0, _ptr(ws, "workspace"),
@@ -355,7 +356,7 @@ def autotune(plan: Plan, records, sorted_vals, tile_ranges, image, T_final, n_co
     chosen = C.c_int32(0)
     rc = N.load().pk_autotune(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
-        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
         _ptr(image, "image", torch.float32, 3 * plan.P), _ptr(T_final, "T_final", torch.float32, plan.P),
         _ptr(n_contrib, "n_contrib", _I32, plan.P), _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
         _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs), _ptr(ws, "workspace"), _stream(stream),
@@ -385,7 +386,7 @@ def bin_and_sort_noalloc(plan: Plan, records, sorted_vals, tile_ranges, n_entrie
     rc = N.load().pk_bin_and_sort_noalloc(
         plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
         _ptr(sorted_vals, "sorted_vals", _I32, plan.max_dups),
-        _ptr(tile_ranges, "tile_ranges", _I32, 2 * plan.n_tiles), _ptr(n_entries, "n_entries", _I32, 1),
+        _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles), _ptr(n_entries, "n_entries", _I32, 1),
         _stream(stream))
     N.check("pk_bin_and_sort_noalloc", rc)
 

@@ -334,12 +334,12 @@ struct SrcSorted {     // tile count of the i-th pair in depth order
   }
 };
 
-__device__ __forceinline__ uint64_t load_n(const uint32_t *n_dev, uint64_t n_host) {
-  return n_dev ? (uint64_t)*n_dev : n_host;
+__device__ __forceinline__ uint64_t load_n(const uint64_t *n_dev, uint64_t n_host) {
+  return n_dev ? *n_dev : n_host;
 }
 
 template <typename Src>
-__global__ __launch_bounds__(kThreads) void k_scan_reduce(Src src, const uint32_t *n_dev, uint64_t n_host,
+__global__ __launch_bounds__(kThreads) void k_scan_reduce(Src src, const uint64_t *n_dev, uint64_t n_host,
                                                           uint64_t *__restrict__ bsum) {
   __shared__ uint64_t s[kWarps + 1];
   const uint64_t n = load_n(n_dev, n_host);
@@ -387,7 +387,7 @@ __global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, 
     const uint64_t total = s[32];
     ctr->scan_total = total;
     if (mode == 0) {
-      ctr->n_valid = (uint32_t)total;
+      ctr->n_valid = total;
       status->valid_pairs = total;
     } else {
       status->dups_needed = total;
@@ -399,7 +399,7 @@ __global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, 
         status->dups = 0;
         atomicOr(&status->flags, PK_DEV_CAPACITY);
       } else {
-        ctr->dups = (uint32_t)total;
+        ctr->dups = total;
         status->dups = total;
       }
     }
@@ -439,26 +439,28 @@ __global__ __launch_bounds__(kThreads) void k_compact_down(const uint32_t *__res
   }
 }
 
-// Down-sweep of the emission-offset scan: offs[i] = entries before pair i.
-__global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const uint32_t *n_dev,
+// Down-sweep of the emission-offset scan: offs[i] = entries before pair i
+// (64-bit: the entries of a launch may pass 2^32).
+__global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const uint64_t *n_dev,
                                                            const uint64_t *__restrict__ bsum,
-                                                           const DevCounters *ctr, uint32_t *__restrict__ offs) {
-  __shared__ uint32_t s[kWarps + 1];
+                                                           const DevCounters *ctr, uint64_t *__restrict__ offs) {
+  __shared__ uint64_t s[kWarps + 1];
   if (ctr->dups == 0) return;   // overflow (or nothing): nothing will be emitted
   const uint64_t n = *n_dev;
   uint64_t b0, b1;
   chunk_of(n, gridDim.x, blockIdx.x, kScanTile, b0, b1);
-  uint32_t run = (uint32_t)bsum[blockIdx.x];
+  uint64_t run = bsum[blockIdx.x];
   for (uint64_t base = b0; base < b1; base += kScanTile) {
     const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems], c = 0;
+    uint32_t v[kScanItems];
+    uint64_t c = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
       v[j] = i0 + j < b1 ? src(i0 + j) : 0u;
       c += v[j];
     }
-    uint32_t tot;
-    uint32_t pre = block_excl_scan<uint32_t>(c, tot, s) + run;
+    uint64_t tot;
+    uint64_t pre = block_excl_scan<uint64_t>(c, tot, s) + run;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
       if (i0 + j < b1) offs[i0 + j] = pre;
@@ -482,7 +484,7 @@ __global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const 
 // it.
 struct SegSpec {
   const int4 *tab;
-  const uint32_t *seg;
+  const uint64_t *seg;
 };
 
 __device__ __forceinline__ void radix_chunk(const SegSpec &sp, uint64_t n, int tile, uint64_t &b0, uint64_t &b1,
@@ -521,8 +523,8 @@ constexpr int kPairItems = 12, kEntryItems = 8;
 
 template <int RB, int IT>
 __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__restrict__ keys,
-                                                            const uint32_t *n_dev, uint64_t n_host, int shift,
-                                                            uint32_t mask, uint32_t *__restrict__ hist, SegSpec sp) {
+                                                            const uint64_t *n_dev, uint64_t n_host, int shift,
+                                                            uint32_t mask, uint64_t *__restrict__ hist, SegSpec sp) {
   using C = Radix<RB, IT>;
   __shared__ uint32_t s_cnt[C::kCopies][C::kR];   // private digit counts
   for (int i = threadIdx.x; i < C::kCopies * C::kR; i += kThreads) (&s_cnt[0][0])[i] = 0;
@@ -566,45 +568,52 @@ __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__re
 }
 
 // Exclusive scan of hist in [digit][block] order (one block of 1024 threads,
-// coalesced: each pass covers 4096 consecutive counters).
-__global__ __launch_bounds__(1024) void k_radix_scan(uint32_t *__restrict__ hist, int count) {
-  __shared__ uint32_t s[33];
-  __shared__ uint32_t s_carry;
+// coalesced: each pass covers 4096 consecutive counters).  The counters are
+// 64-bit: after the scan they are output positions, and the entries of a
+// launch may pass 2^32.
+__global__ __launch_bounds__(1024) void k_radix_scan(uint64_t *__restrict__ hist, int count) {
+  __shared__ uint64_t s[33];
+  __shared__ uint64_t s_carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (int base = 0; base < count; base += 4096) {
     const int i = base + 4 * tid;
-    uint4 q = make_uint4(0, 0, 0, 0);
-    if (i + 3 < count) q = *reinterpret_cast<const uint4 *>(hist + i);
-    else {
-      if (i < count) q.x = hist[i];
-      if (i + 1 < count) q.y = hist[i + 1];
-      if (i + 2 < count) q.z = hist[i + 2];
+    uint64_t q[4];
+    if (i + 3 < count) {
+      const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(hist + i);
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(hist + i + 2);
+      q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) q[j] = i + j < count ? hist[i + j] : 0ull;
     }
-    const uint32_t sum = q.x + q.y + q.z + q.w;
-    const uint32_t incl = warp_incl_scan(sum);
+    const uint64_t sum = q[0] + q[1] + q[2] + q[3];
+    const uint64_t incl = warp_incl_scan(sum);
     if (lane == 31) s[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-      const uint32_t w = s[lane];
-      const uint32_t wi = warp_incl_scan(w);
+      const uint64_t w = s[lane];
+      const uint64_t wi = warp_incl_scan(w);
       s[lane] = wi - w;
       if (lane == 31) s[32] = wi;
     }
     __syncthreads();
-    const uint32_t carry = s_carry;
-    uint32_t e = carry + s[warp] + incl - sum;
-    uint4 o;
-    o.x = e; e += q.x;
-    o.y = e; e += q.y;
-    o.z = e; e += q.z;
-    o.w = e;
-    if (i + 3 < count) *reinterpret_cast<uint4 *>(hist + i) = o;
-    else {
-      if (i < count) hist[i] = o.x;
-      if (i + 1 < count) hist[i + 1] = o.y;
-      if (i + 2 < count) hist[i + 2] = o.z;
+    const uint64_t carry = s_carry;
+    uint64_t e = carry + s[warp] + incl - sum;
+    uint64_t o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      o[j] = e;
+      e += q[j];
+    }
+    if (i + 3 < count) {
+      *reinterpret_cast<ulonglong2 *>(hist + i) = make_ulonglong2(o[0], o[1]);
+      *reinterpret_cast<ulonglong2 *>(hist + i + 2) = make_ulonglong2(o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i + j < count) hist[i + j] = o[j];
     }
     __syncthreads();
     if (tid == 0) s_carry = carry + s[32];
@@ -621,15 +630,15 @@ struct Down {
   static constexpr int kSpan = kTile + 4;                         // a tile plus up to 3 keys of misalignment
   static constexpr size_t kBuf = 2 * sizeof(uint32_t) * kSpan;    // keys + values of one tile
   static constexpr size_t kSmem = 2 * kBuf + sizeof(uint16_t) * kWarps * Radix<RB, IT>::kR +
-                                  2 * sizeof(uint32_t) * Radix<RB, IT>::kR + sizeof(uint32_t) * (kWarps + 1) +
-                                  2 * sizeof(uint64_t) + 16;
+                                  (sizeof(uint32_t) + sizeof(uint64_t)) * Radix<RB, IT>::kR +
+                                  sizeof(uint32_t) * (kWarps + 1) + 2 * sizeof(uint64_t) + 16;
 };
 
 template <int RB, int IT>
 __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, const uint32_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
-    const uint32_t *__restrict__ hist, pk_device_status *status, SegSpec sp, uint32_t *abort_flag,
+    uint32_t *__restrict__ vout, const uint64_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
+    const uint64_t *__restrict__ hist, pk_device_status *status, SegSpec sp, uint32_t *abort_flag,
     uint32_t first_polls, bool try_single) {
   using C = Radix<RB, IT>;
   constexpr int kTile = C::kTile;
@@ -638,8 +647,8 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
   uint32_t *buf[2] = {reinterpret_cast<uint32_t *>(s_raw), reinterpret_cast<uint32_t *>(s_raw + Down<RB, IT>::kBuf)};
   uint16_t *s_wcnt = reinterpret_cast<uint16_t *>(s_raw + 2 * Down<RB, IT>::kBuf);       // [kWarps][kR]
   uint32_t *s_start = reinterpret_cast<uint32_t *>(s_wcnt + kWarps * C::kR);         // [kR]
-  uint32_t *s_gbase = s_start + C::kR;                                              // [kR]
-  uint32_t *s_scan = s_gbase + C::kR;                                               // [kWarps + 1]
+  uint64_t *s_gbase = reinterpret_cast<uint64_t *>(s_start + C::kR);                // [kR] output positions
+  uint32_t *s_scan = reinterpret_cast<uint32_t *>(s_gbase + C::kR);                 // [kWarps + 1]
   uint64_t *s_bar = reinterpret_cast<uint64_t *>(
       (reinterpret_cast<uintptr_t>(s_scan + kWarps + 1) + 7) & ~uintptr_t(7));      // [2]
   __shared__ int s_abort;
@@ -648,6 +657,13 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
   uint64_t b0, b1;
   uint32_t hbase, hstride;
   radix_chunk(sp, n, kTile, b0, b1, hbase, hstride);
+  if (b1 - b0 > 0xffffffffull) {   // a block's digit counts are 32-bit: give the call up
+    if (tid == 0) {
+      atomicOr(&status->flags, PK_DEV_BOUNDS);
+      *abort_flag = 1u;
+    }
+    return;
+  }
   for (int d = tid; d < C::kR; d += kThreads) s_gbase[d] = hist[hbase + (size_t)d * hstride];
   const int ntile = (int)((b1 - b0 + kTile - 1) / kTile);
   // Every tile of this chunk starts mis = b0 mod 4 keys past a 16-byte
@@ -720,7 +736,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
         if (li < valid) same = same && ((bk[li] >> shift) & mask) == d0;
       }
       if (__syncthreads_and(same)) {
-        const uint32_t o0 = s_gbase[d0];
+        const uint64_t o0 = s_gbase[d0];
         bool bad = false;
         for (uint32_t i = tid; i < valid; i += kThreads) {
           const uint64_t o = (uint64_t)o0 + i;
@@ -802,7 +818,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     for (uint32_t i = tid; i < valid; i += kThreads) {
       const uint32_t k = bk[i];
       const uint32_t d = (k >> shift) & mask;
-      const uint32_t o = s_gbase[d] + (i - s_start[d]);
+      const uint64_t o = s_gbase[d] + (i - s_start[d]);
       if (o >= n) {   // a histogram out of step with the keys: never write past the items
         atomicOr(&status->flags, PK_DEV_BOUNDS);
         *abort_flag = 1u;
@@ -829,13 +845,13 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
 // ---------------------------------------------------------------------------
 
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
-                                                   const uint32_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
+                                                   const uint64_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
                                                    DevCounters *ctr, const DevView *__restrict__ views,
                                                    int64_t N, int64_t pairs, int T, int mode, int local_bits,
                                                    uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                                                    pk_device_status *status) {
   __shared__ WarpSplat s_ws[kWarps][32];
-  const uint32_t dups = ctr->dups;
+  const uint64_t dups = ctr->dups;
   if (dups == 0) return;
   const uint64_t n = ctr->n_valid;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -883,7 +899,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       }
     }
     const float rw = __frcp_rn((float)ws.r0.z);
-    uint32_t off0 = 0;
+    uint64_t off0 = 0;
     if (lane == 0) off0 = offs[w * 32];
     off0 = __shfl_sync(0xffffffffu, off0, 0);
     s_ws[warp][lane] = ws;
@@ -916,7 +932,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       }
       const uint32_t bal = __ballot_sync(0xffffffffu, take);
       if (take) {
-        const uint32_t at = off0 + written + __popc(bal & lt);
+        const uint64_t at = off0 + written + __popc(bal & lt);
         if (at < dups) {
           keys[at] = (uint32_t)r1.y + ly * (uint32_t)r1.z + lx;
           vals[at] = o_p;
@@ -932,18 +948,18 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
 }
 
 // Tile ranges from the sorted tile ids; four entries per thread.
-// Per-tile [start, end) of the sorted entries.  Keys are global tile ids,
-// or (local_bits > 0) the view above a per-view local tile id: then the
-// view's tile_off is added to the local id.
+// Per-tile [start, end) of the sorted entries (64-bit positions).  Keys
+// are global tile ids, or (local_bits > 0) the view above a per-view local
+// tile id: then the view's tile_off is added to the local id.
 __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict__ keys, int local_bits,
                                                      const uint32_t *__restrict__ toff, const DevCounters *ctr,
-                                                     uint32_t *__restrict__ ranges, int V, uint32_t n_tiles,
+                                                     uint64_t *__restrict__ ranges, int V, uint32_t n_tiles,
                                                      pk_device_status *status) {
-  const uint32_t n = ctr->sort_abort ? 0u : ctr->dups;   // a pass gave up: every range stays empty
-  const uint32_t nq = (n + 3) / 4;
+  const uint64_t n = ctr->sort_abort ? 0u : ctr->dups;   // a pass gave up: every range stays empty
+  const uint64_t nq = (n + 3) / 4;
   const uint32_t lmask = (1u << local_bits) - 1u;
-  for (uint32_t q = blockIdx.x * kThreads + threadIdx.x; q < nq; q += gridDim.x * kThreads) {
-    const uint32_t i0 = 4 * q;
+  for (uint64_t q = blockIdx.x * (uint64_t)kThreads + threadIdx.x; q < nq; q += (uint64_t)gridDim.x * kThreads) {
+    const uint64_t i0 = 4 * q;
     uint32_t k[6];   // tile ids of entries i0 - 1 .. i0 + 4
     k[0] = i0 ? __ldg(keys + i0 - 1) : 0xffffffffu;
     if (i0 + 3 < n) {
@@ -972,7 +988,7 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const uint32_t i = i0 + j;
+      const uint64_t i = i0 + j;
       if (i >= n) break;
       const uint32_t t = k[1 + j];
       if (i == 0 || k[j] != t) ranges[2 * (size_t)t] = i;
@@ -988,10 +1004,11 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
 // its index (n where none is left); seg[V] = the total.
 template <bool kEntries>
 __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__restrict__ pval,
-                                                            const uint32_t *__restrict__ offs,
+                                                            const uint64_t *__restrict__ offs,
                                                             const DevCounters *ctr, uint32_t N, int V,
-                                                            uint32_t *__restrict__ seg) {
-  const uint32_t n = ctr->n_valid, total = kEntries ? ctr->dups : n;
+                                                            uint64_t *__restrict__ seg) {
+  const uint32_t n = (uint32_t)ctr->n_valid;   // valid pairs < 2^32 (pair indices are 32-bit)
+  const uint64_t total = kEntries ? ctr->dups : n;
   for (int v = blockIdx.x * kThreads + threadIdx.x; v <= V; v += gridDim.x * kThreads) {
     if (n == 0 || total == 0) {
       seg[v] = 0;
@@ -1009,7 +1026,7 @@ __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__re
 
 template <int RB, int IT>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                        const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
+                        const uint64_t *n_dev, uint64_t n_host, int shift, int bits, uint64_t *hist, int nblocks,
                         pk_device_status *status, SegSpec sp, uint32_t *abort_flag, uint32_t first_polls,
                         bool try_single, cudaStream_t st) {
   using C = Radix<RB, IT>;
@@ -1030,7 +1047,7 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 // rb = 8 or 11 bits (pk_options.sort_bits_*: wider digits take fewer passes
 // but run fewer blocks per SM and scatter into more runs).
 pk_status radix_pass(bool entries, int rb, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
-                     const uint32_t *n_dev, uint64_t n_host, int shift, int bits, uint32_t *hist, int nblocks,
+                     const uint64_t *n_dev, uint64_t n_host, int shift, int bits, uint64_t *hist, int nblocks,
                      pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls, bool try_single,
                      cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}) {
 #define PK_PASS(RB, IT)                                                                                        \
@@ -1133,20 +1150,20 @@ int local_tile_bits(const pk_plan *p) {
 // The whole binning + sort on one workspace layout (shared by the two
 // entry points below).
 pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const float *records,
-                            uint32_t *sorted_vals, uint32_t *tile_ranges, uint64_t maxd, cudaStream_t st) {
+                            uint32_t *sorted_vals, uint64_t *tile_ranges, uint64_t maxd, cudaStream_t st) {
   const DevView *views = at<DevView>(ws, L.views);
   DevCounters *ctr = at<DevCounters>(ws, L.counters);
   pk_device_status *status = at<pk_device_status>(ws, L.status);
   uint32_t *cnt = at<uint32_t>(ws, L.pair_cnt);
   uint32_t *zk[2] = {at<uint32_t>(ws, L.zkey0), at<uint32_t>(ws, L.zkey1)};
   uint32_t *pv[2] = {at<uint32_t>(ws, L.pval0), at<uint32_t>(ws, L.pval1)};
-  uint32_t *offs = at<uint32_t>(ws, L.offs);
+  uint64_t *offs = at<uint64_t>(ws, L.offs);
   uint4 *pinfo = at<uint4>(ws, L.rmask);
   uint64_t *bsum = at<uint64_t>(ws, L.blocksums);
-  uint32_t *hist = at<uint32_t>(ws, L.hist);
+  uint64_t *hist = at<uint64_t>(ws, L.hist);
   uint32_t *dk0 = at<uint32_t>(ws, L.dkey0), *dk1 = at<uint32_t>(ws, L.dkey1);
   uint32_t *dv = at<uint32_t>(ws, L.dval);
-  const uint32_t *n_valid = &ctr->n_valid;
+  const uint64_t *n_valid = &ctr->n_valid;
   const uint64_t pairs = (uint64_t)p->pairs;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -1157,9 +1174,9 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   int nseg = 0, npseg = 0;
   const bool seg = seg_tables(p, tab_host, &nseg, &npseg);
   const int4 *tab = at<int4>(ws, L.sblk);
-  uint32_t *vseg = at<uint32_t>(ws, L.vseg), *pseg = vseg + (p->V + 1);
+  uint64_t *vseg = at<uint64_t>(ws, L.vseg), *pseg = vseg + (p->V + 1);
 
-  pk_status ze = zero_async({{tile_ranges, sizeof(uint32_t) * 2 * (size_t)p->n_tiles},
+  pk_status ze = zero_async({{tile_ranges, sizeof(uint64_t) * 2 * (size_t)p->n_tiles},
                              {ctr, pairs == 0 ? sizeof(DevCounters) : 0},
                              {&ctr->sort_abort, pairs == 0 ? 0 : sizeof(uint32_t)}},
                             st);
@@ -1255,7 +1272,7 @@ int pk::bin_kernel_count(const pk_plan *p) {
 }
 
 extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
-                                     uint32_t *tile_ranges, void *ws, pk_stream_t stream) {
+                                     uint64_t *tile_ranges, void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !ws) return PK_ERR_ARG;
   if (!aligned16(records) || !aligned16(sorted_vals) || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PK_ERR_ARG;
   return bin_and_sort_impl(p, p->ws, ws, records, sorted_vals, tile_ranges, p->max_dups,
@@ -1307,13 +1324,13 @@ __global__ void k_report_entries(const DevCounters *ctr, const pk_device_status 
   const uint32_t f = status->flags;
   *n_entries = (f & PK_DEV_CAPACITY) ? 0xffffffffu
                                      : ((f & (PK_DEV_TIMEOUT | PK_DEV_BOUNDS)) || ctr->sort_abort) ? 0xfffffffeu
-                                                                                                    : ctr->dups;
+                                                                                                    : (uint32_t)ctr->dups;
 }
 
 }  // namespace
 
 extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *records, uint32_t *sorted_vals,
-                                             uint32_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream) {
+                                             uint64_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !n_entries) return PK_ERR_ARG;
   if (!aligned16(records) || !aligned16(sorted_vals)) return PK_ERR_ARG;
   // layout of this plan's scratch inside the static array
@@ -1330,17 +1347,17 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   L.views = take(sizeof(DevView) * p->V);
   L.toff = take(sizeof(uint32_t) * (p->V + 1));
   L.sblk = take(sizeof(int4) * 2 * kSortBlocks);
-  L.vseg = take(sizeof(uint32_t) * 2 * (p->V + 1));
+  L.vseg = take(sizeof(uint64_t) * 2 * (p->V + 1));
   L.pair_cnt = take(sizeof(uint32_t) * pairs);
   L.zkey0 = take(sizeof(uint32_t) * pairs);
   L.zkey1 = take(sizeof(uint32_t) * pairs);
   L.pval0 = take(sizeof(uint32_t) * pairs);
   L.pval1 = take(sizeof(uint32_t) * pairs);
-  L.offs = take(sizeof(uint32_t) * pairs);
+  L.offs = take(sizeof(uint64_t) * pairs);
   L.rmask = take(sizeof(uint4) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
   // digit counters of the widest radix pass of the plan's two sorts
-  L.hist = take(sizeof(uint32_t) * (size_t(1) << std::max(p->opts.sort_bits_tile, p->opts.sort_bits_depth)) *
+  L.hist = take(sizeof(uint64_t) * (size_t(1) << std::max(p->opts.sort_bits_tile, p->opts.sort_bits_depth)) *
                 kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);

@@ -32,6 +32,7 @@ constexpr float kInvExpScale = -1.38629436111989061f;   // 1 / kExpScale = -2 ln
 constexpr int kScanBlocks = 4096;
 constexpr int kSortBlocks = 768;      // most radix blocks of one pass (histogram capacity)
 constexpr int kMaxRadixBits = 11;     // widest radix digit (pk_options.sort_bits_*: 8 or 11)
+constexpr uint64_t kMaxEntries = uint64_t(1) << 35;   // most (pair, tile) entries of a plan
 
 // Per-view constants on the device, 144 bytes.
 struct alignas(16) DevView {
@@ -51,8 +52,8 @@ static_assert(sizeof(DevView) % 16 == 0, "DevView layout");
 
 // Internal device scalars kept after the public status block.
 struct DevCounters {
-  uint32_t n_valid;        // pairs with >= 1 tile (after the compaction scan)
-  uint32_t dups;           // entries emitted (0 on overflow)
+  uint64_t n_valid;        // pairs with >= 1 tile (after the compaction scan)
+  uint64_t dups;           // entries emitted (0 on overflow); 64-bit, as are entry positions
   uint32_t tile_queue[4];  // persistent-kernel work counters
   uint64_t scan_total;     // total of the last scan
   double loss_acc;         // sum of |image - target| of the last loss call

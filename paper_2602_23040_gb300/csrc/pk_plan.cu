@@ -225,7 +225,9 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   if (pairs > 0xFFFFFFFFull) return PK_ERR_ARG;   // pair indices are 32-bit
   uint64_t maxd = o.max_dups ? o.max_dups : 32 * pairs;
   if (maxd < 1024) maxd = 1024;
-  if (maxd > 0xFFFFF000ull) maxd = 0xFFFFF000ull;
+  // entry positions are 64-bit; 2^35 entries (412 GB of lists and sort
+  // buffers) is beyond any one GPU's memory
+  if (maxd > kMaxEntries) maxd = kMaxEntries;
   o.max_dups = maxd;
 
   pk_plan *p = new (std::nothrow) pk_plan;
@@ -315,17 +317,17 @@ extern "C" pk_status pk_plan_create(const pk_atlas_desc *desc, const pk_view *vi
   L.zkey1 = take(sizeof(uint32_t) * pairs);
   L.pval0 = take(sizeof(uint32_t) * pairs);
   L.pval1 = take(sizeof(uint32_t) * pairs);
-  L.offs = take(sizeof(uint32_t) * pairs);
+  L.offs = take(sizeof(uint64_t) * pairs);
   L.rmask = take(sizeof(uint4) * pairs);
   L.blocksums = take(sizeof(uint64_t) * (kScanBlocks + 1));
   // digit counters of the widest radix pass (room for 11-bit digits, so
   // that pk_autotune may pick them)
-  L.hist = take(sizeof(uint32_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
+  L.hist = take(sizeof(uint64_t) * (size_t(1) << kMaxRadixBits) * kSortBlocks);
   L.dkey0 = take(sizeof(uint32_t) * maxd);
   L.dkey1 = take(sizeof(uint32_t) * maxd);
   L.dval = take(sizeof(uint32_t) * maxd);
   L.sblk = take(sizeof(int4) * 2 * kSortBlocks);
-  L.vseg = take(sizeof(uint32_t) * 2 * (V + 1));
+  L.vseg = take(sizeof(uint64_t) * 2 * (V + 1));
   L.mask_tmp = take(sizeof(uint32_t) * (size_t)p->mask_words);
   L.mask_coarse = take(sizeof(uint32_t) * (size_t)p->coarse_words);
   L.total = off;
@@ -444,7 +446,7 @@ pk_status time_runs(Fn fn, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int 
 
 }  // namespace
 
-extern "C" pk_status pk_autotune(pk_plan *p, const float *records, uint32_t *sorted_vals, uint32_t *tile_ranges,
+extern "C" pk_status pk_autotune(pk_plan *p, const float *records, uint32_t *sorted_vals, uint64_t *tile_ranges,
                                  float *image, float *T_final, uint32_t *n_contrib,
                                  const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream,
                                  int32_t *chosen_batch) {

@@ -15,21 +15,23 @@ constexpr int kTileSide = 16;   // side of the pixel block of one compositing CT
 // kernels (64, 128 or 256; pk_options.batch, chosen by pk_autotune).
 constexpr int kBatchMax = 256;
 
-// One CTA per 16 x 16 pixel block with kPx pixels per thread (2 or 4).  A
-// warp covers a kBW x 8 block (8 x 8 for 2 pixels, 16 x 8 for 4) and skips
-// as a whole every splat that misses its block; a lane holds one column of
-// it, kPx pixels kRowStep rows apart.  More pixels per lane spread the
-// per-splat work of a warp (shared-memory loads, the block test, the
-// gradient reduction) over more pixels, at the price of a coarser block
-// test.
+// One CTA per 16 x 16 pixel block with kPx pixels per thread (2, 4 or 8).
+// A warp covers a kBW x kBH block (8 x 8 for 2 pixels, 16 x 8 for 4, the
+// whole 16 x 16 for 8) and skips as a whole every splat that misses its
+// block; a lane holds one column of it, kPx pixels kRowStep rows apart.
+// More pixels per lane spread the per-splat work of a warp (shared-memory
+// loads, the block test, the gradient reduction) over more pixels, at the
+// price of a coarser block test and more registers.
 template <int kPx>
 struct Geo {
-  static_assert(kPx == 2 || kPx == 4, "2 or 4 pixels per thread");
-  static constexpr int kThreads = kTileSide * kTileSide / kPx;   // 128 or 64
+  static_assert(kPx == 2 || kPx == 4 || kPx == 8, "2, 4 or 8 pixels per thread");
+  static constexpr int kThreads = kTileSide * kTileSide / kPx;   // 128, 64 or 32
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kBW = kPx == 2 ? 8 : 16;
-  static constexpr int kRowStep = 32 / kBW;                       // 4 or 2
+  static constexpr int kBH = kPx == 8 ? 16 : 8;
+  static constexpr int kRowStep = kBH / kPx;                      // 4, 2 or 2
   static constexpr int kBlocksX = kTileSide / kBW;                // warp blocks per row
+  static_assert(kBW * kBH == 32 * kPx, "a warp's block holds its lanes' pixels");
 };
 
 // Pixels per thread: the forward keeps 2 (its per-splat work is small, and
@@ -43,7 +45,7 @@ __device__ __forceinline__ void pixel_of(int tid, int &ox, int &oy, int &bx, int
   using G = Geo<kPx>;
   const int w = tid >> 5, l = tid & 31;
   bx = (w % G::kBlocksX) * G::kBW;
-  by = (w / G::kBlocksX) * 8;
+  by = (w / G::kBlocksX) * G::kBH;
   ox = bx + (l % G::kBW);
   oy = by + l / G::kBW;
 }

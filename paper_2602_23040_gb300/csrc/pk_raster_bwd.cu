@@ -154,7 +154,7 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // measurement; the variant without it carries no counter in its loop).
 template <int kBatch, bool kTma, int kPx, int kT, bool kCount>
 __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_raster_bwd(
-    const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+    const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint64_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
     const float *__restrict__ dimg, float *__restrict__ grad2d, uint32_t *queue, unsigned long long *evals_out,
@@ -185,7 +185,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
   }
   // bulk copies of the records of list entries [b, b + nb) into s_raw
   // (expect_tx is set by thread 0 before the block barrier that precedes this)
-  auto fetch = [&](uint32_t b, int nb) {
+  auto fetch = [&](uint64_t b, int nb) {
     for (int j = tid; j < nb; j += G::kThreads) {
       const uint32_t pid = __ldg(vals + b + j);
       const bool named = pid < npairs;   // else record 0 is fetched in its place and not used
@@ -217,8 +217,11 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
     const int x = X0 + ox, y0 = Y0 + oy;
     const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
     const float wx0 = (float)(X0 + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
-    const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + 7.f;
-    const uint32_t s = __ldg(ranges + 2 * (size_t)t), len = __ldg(ranges + 2 * (size_t)t + 1) - s;
+    const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + (float)(G::kBH - 1);
+    // list start, and its length (one tile's list names each of its
+    // view's pairs at most once: below 2^32)
+    const uint64_t s = __ldg(ranges + 2 * (size_t)t);
+    const uint32_t len = (uint32_t)(__ldg(ranges + 2 * (size_t)t + 1) - s);
     const size_t plane = (size_t)W * H;
     float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx], pyq[kPx];
     uint32_t nc[kPx];
@@ -355,7 +358,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
 template <int kBatch, bool kBwdTma, int kT, bool kCount>
 pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                     const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                     const uint64_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
                      const float *dL_dimage, float *grad2d, void *ws, DevCounters *ctr, pk_device_status *status,
                      cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -379,7 +382,7 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
 }  // namespace
 
 extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                                      const uint32_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                                      const uint64_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
                                       const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !T_final || !n_contrib || !dL_dimage || !grad2d || !ws)
     return PK_ERR_ARG;

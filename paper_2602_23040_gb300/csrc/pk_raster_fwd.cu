@@ -31,7 +31,7 @@ namespace {
 // measurement; the variant without it carries no counter in its loop).
 template <int kBatch, bool kTma, int kPx, int kT, bool kCount>
 __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_raster_fwd(
-    const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint32_t *__restrict__ ranges,
+    const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint64_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
     uint32_t *queue, unsigned long long *evals_out, pk_device_status *status, const float *__restrict__ target,
@@ -61,7 +61,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
   }
   // bulk copies of the records of list entries [b, b + nb) into s_raw
   // (expect_tx is set by thread 0 before the block barrier that precedes this)
-  auto fetch = [&](uint32_t b, int nb) {
+  auto fetch = [&](uint64_t b, int nb) {
     for (int j = tid; j < nb; j += G::kThreads) {
       const uint32_t pid = __ldg(vals + b + j);
       const bool named = pid < npairs;   // else record 0 is fetched in its place and not used
@@ -94,8 +94,8 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
     const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f;
     // pixel-centre bounds of this warp's block
     const float wx0 = (float)(X0 + bx) + 0.5f, wx1 = wx0 + (float)(G::kBW - 1);
-    const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + 7.f;
-    const uint32_t s = __ldg(ranges + 2 * (size_t)t), e = __ldg(ranges + 2 * (size_t)t + 1);
+    const float wy0 = (float)(Y0 + by) + 0.5f, wy1 = wy0 + (float)(G::kBH - 1);
+    const uint64_t s = __ldg(ranges + 2 * (size_t)t), e = __ldg(ranges + 2 * (size_t)t + 1);
     float T[kPx], c0[kPx], c1[kPx], c2[kPx];
     uint32_t last[kPx];
     uint32_t live = 0;   // bit k: pixel k is inside the view and still compositing
@@ -108,13 +108,13 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
     }
     bool pending = false;   // a fetch is in flight (uniform over the block)
     if (kTma && s < e) {
-      if (tid == 0) mbar_expect_tx(&s_bar, (uint32_t)min((uint32_t)kBatch, e - s) * 3u * sizeof(float4));
+      if (tid == 0) mbar_expect_tx(&s_bar, (uint32_t)min((uint64_t)kBatch, e - s) * 3u * sizeof(float4));
       __syncthreads();
-      fetch(s, (int)min((uint32_t)kBatch, e - s));
+      fetch(s, (int)min((uint64_t)kBatch, e - s));
       pending = true;
     }
-    for (uint32_t base = s; base < e; base += kBatch) {
-      const int nb = (int)min((uint32_t)kBatch, e - base);
+    for (uint64_t base = s; base < e; base += kBatch) {
+      const int nb = (int)min((uint64_t)kBatch, e - base);
       if (kTma) {
         if (!mbar_wait_bounded(&s_bar, phase, first_polls)) {
           timed_out = true;
@@ -133,8 +133,8 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
             }
           }
         fence_proxy_async();   // these reads of s_raw before the next bulk writes into it
-        const uint32_t nxt = base + kBatch;
-        const int nbn = nxt < e ? (int)min((uint32_t)kBatch, e - nxt) : 0;
+        const uint64_t nxt = base + kBatch;
+        const int nbn = nxt < e ? (int)min((uint64_t)kBatch, e - nxt) : 0;
         if (tid == 0 && nbn > 0) mbar_expect_tx(&s_bar, (uint32_t)nbn * 3u * sizeof(float4));
         if (__syncthreads_or(timed_out)) {
           timed_out = true;
@@ -170,7 +170,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
             m &= m - 1;
             const float4 a = s_a[j], b = s_b[j], c = s_c[j];
             const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
-            const uint32_t pos1 = base - s + (uint32_t)j + 1u;
+            const uint32_t pos1 = (uint32_t)(base - s) + (uint32_t)j + 1u;   // within the tile's list
             if (kCount) evals += __popc(live);   // evaluated at every live pixel of the thread
 #pragma unroll
             for (int q = 0; q < kPx; ++q) {
@@ -255,7 +255,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
 // One persistent launch: as many CTAs as fit on the GPU, at most one per tile.
 template <int kBatch, bool kFwdTma, int kT, bool kCount>
 pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                     const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
+                     const uint64_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
                      DevCounters *ctr, pk_device_status *status, const float *target, float *dimg,
                      cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -278,7 +278,7 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
 }
 
 pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                        const uint32_t *tile_ranges, const float *target, float *image, float *T_final,
+                        const uint64_t *tile_ranges, const float *target, float *image, float *T_final,
                         uint32_t *n_contrib, float *dimg, void *ws, cudaStream_t st) {
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
@@ -320,7 +320,7 @@ pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *
 }  // namespace
 
 extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                                      const uint32_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
+                                      const uint64_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
                                       void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !image || !T_final || !n_contrib || !ws) return PK_ERR_ARG;
   if (!aligned16(records)) return PK_ERR_ARG;
@@ -329,7 +329,7 @@ extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, co
 }
 
 extern "C" pk_status pk_rasterize_fwd_l1(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                                         const uint32_t *tile_ranges, const float *target, float *image,
+                                         const uint64_t *tile_ranges, const float *target, float *image,
                                          float *T_final, uint32_t *n_contrib, float *dL_dimage, void *ws,
                                          pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !target || !image || !T_final || !n_contrib ||

@@ -5,7 +5,7 @@
 
 extern "C" pk_status pk_render_fwd(const pk_plan *p, const void *atlas, const uint32_t *occ, const uint32_t *dyn,
                                    float *soa, uint32_t *texel, uint8_t *dynflag, float *records,
-                                   uint32_t *sorted_vals, uint32_t *tile_ranges, float *image, float *T_final,
+                                   uint32_t *sorted_vals, uint64_t *tile_ranges, float *image, float *T_final,
                                    uint32_t *n_contrib, void *ws, pk_stream_t stream) {
   pk_status e = pk_atlas_gather(p, atlas, occ, dyn, soa, texel, dynflag, ws, stream);
   if (e == PK_OK) e = pk_project_and_sh(p, soa, records, ws, stream);
@@ -15,7 +15,7 @@ extern "C" pk_status pk_render_fwd(const pk_plan *p, const void *atlas, const ui
 }
 
 extern "C" pk_status pk_render_bwd(const pk_plan *p, const float *soa, const uint8_t *dynflag, const uint32_t *texel,
-                                   const float *records, const uint32_t *sorted_vals, const uint32_t *tile_ranges,
+                                   const float *records, const uint32_t *sorted_vals, const uint64_t *tile_ranges,
                                    const float *T_final, const uint32_t *n_contrib, const float *dL_dimage,
                                    float *grad2d, float *grad_atlas, int32_t accumulate, void *ws,
                                    pk_stream_t stream) {

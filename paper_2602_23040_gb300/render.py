@@ -44,7 +44,7 @@ class Renderer:
         self.dynflag = torch.empty(max(p.N, 1), dtype=torch.uint8, device=self.device)
         self.records = torch.empty(12 * max(p.pairs, 1), dtype=f32, device=self.device)
         self.sorted_vals = torch.empty(int(p.max_dups) + 64, dtype=i32, device=self.device)
-        self.ranges = torch.empty(2 * p.n_tiles, dtype=i32, device=self.device)
+        self.ranges = torch.empty(2 * p.n_tiles, dtype=torch.int64, device=self.device)
         self.image = torch.empty(3 * p.P, dtype=f32, device=self.device)
         self.T = torch.empty(p.P, dtype=f32, device=self.device)
         self.n_contrib = torch.empty(p.P, dtype=i32, device=self.device)
@@ -199,7 +199,7 @@ class PerViewLoop:
         self.grad2d = torch.empty(12 * max(p0.pairs, 1), dtype=f32, device=self.device)
         md = max(int(p.max_dups) for p in self.plans)
         self.sorted_vals = torch.empty(md + 64, dtype=i32, device=self.device)
-        self.ranges = torch.empty(2 * max(p.n_tiles for p in self.plans), dtype=i32, device=self.device)
+        self.ranges = torch.empty(2 * max(p.n_tiles for p in self.plans), dtype=torch.int64, device=self.device)
         P = sum(p.P for p in self.plans)
         self.image = torch.empty(3 * P, dtype=f32, device=self.device)
         self.T = torch.empty(P, dtype=f32, device=self.device)

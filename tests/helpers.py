@@ -48,6 +48,11 @@ def u32(t) -> np.ndarray:
     return t.cpu().numpy().view(np.uint32)
 
 
+def i64(t) -> np.ndarray:
+    """A device int64 tensor (tile ranges: 64-bit entry positions) on the host."""
+    return t.cpu().numpy().astype(np.int64)
+
+
 # Borderline bits of the oracle (oracle.B_*): image decisions only
 B_Q, B_ALPHA, B_STOP, B_DEPTH, B_CULL = 1, 2, 4, 8, 16
 IMAGE_BORDER = B_Q | B_ALPHA | B_STOP | B_DEPTH | B_CULL

@@ -162,7 +162,7 @@ def test_bin_and_sort_bit_exact(orc, seed, mode, tile, bits, huge):
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
     vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
-    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int64, device="cuda")
     pk.bin_and_sort(plan, drec, vals, ranges, ws)
     st = pk.read_status(plan, ws)
     va = orc.views_array(views)
@@ -170,7 +170,7 @@ def test_bin_and_sort_bit_exact(orc, seed, mode, tile, bits, huge):
     ref_vals, ref_ranges = orc.bin_sort32(r[:, 0], r[:, 1], r[:, 7], r[:, 6], va, N, tile, r[:, 2], r[:, 3],
                                           r[:, 4], mode={"ellipse": orc.BIN_ELLIPSE, "rect": orc.BIN_RECT}[mode])
     assert st["dups"] == len(ref_vals) and st["flags"] == 0
-    assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.u32(ranges).reshape(-1, 2), ref_vals, ref_ranges)
+    assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.i64(ranges).reshape(-1, 2), ref_vals, ref_ranges)
 
 
 def assert_same_tile_lists(vals, ranges, ref_vals, ref_ranges):
@@ -203,7 +203,7 @@ def test_bin_and_sort_capacity_overflow(orc):
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
-    ranges = torch.full((2 * plan.n_tiles,), 7, dtype=torch.int32, device="cuda")
+    ranges = torch.full((2 * plan.n_tiles,), 7, dtype=torch.int64, device="cuda")
     pk.bin_and_sort(plan, torch.from_numpy(rec.reshape(-1)).cuda(), vals, ranges, ws)
     st = pk.read_status(plan, ws)
     assert st["flags"] & 1 and st["rc"] == 3 and st["dups"] == 0 and st["dups_needed"] > 1024
@@ -255,7 +255,7 @@ def test_bin_and_sort_ragged_view_segments(orc, tile, spread, bits):
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
     vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
-    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int64, device="cuda")
     pk.bin_and_sort(plan, drec, vals, ranges, ws)
     st = pk.read_status(plan, ws)
     va = orc.views_array(views)
@@ -266,7 +266,7 @@ def test_bin_and_sort_ragged_view_segments(orc, tile, spread, bits):
     if not spread:
         assert len(ref_vals) == sum(RAGGED_COUNTS)
     assert st["dups"] == len(ref_vals) and st["flags"] == 0
-    assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.u32(ranges).reshape(-1, 2), ref_vals, ref_ranges)
+    assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.i64(ranges).reshape(-1, 2), ref_vals, ref_ranges)
 
 
 # ---------------------------------------------------------------------------
@@ -283,7 +283,7 @@ def _records_forward(seed, dimg_seed=None, tile=16):
     pk.workspace_init(plan, ws)
     drec = torch.from_numpy(rec.reshape(-1)).cuda()
     vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
-    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    ranges = torch.empty(2 * plan.n_tiles, dtype=torch.int64, device="cuda")
     img = torch.empty(3 * plan.P, dtype=torch.float32, device="cuda")
     T = torch.empty(plan.P, dtype=torch.float32, device="cuda")
     nc = torch.empty(plan.P, dtype=torch.int32, device="cuda")
@@ -558,7 +558,7 @@ def test_autotune_tile_side_and_digit_widths(orc):
     ref_vals, ref_ranges = orc.bin_sort32(rec[:, 0], rec[:, 1], rec[:, 7], rec[:, 6], va, N, p.tile, rec[:, 2],
                                           rec[:, 3], rec[:, 4], mode=orc.BIN_ELLIPSE)
     assert st["dups"] == len(ref_vals)
-    assert_same_tile_lists(H.u32(r.sorted_vals[:len(ref_vals)]), H.u32(r.ranges).reshape(-1, 2), ref_vals,
+    assert_same_tile_lists(H.u32(r.sorted_vals[:len(ref_vals)]), H.i64(r.ranges).reshape(-1, 2), ref_vals,
                            ref_ranges)
     # either digit width, either sort: the same lists
     for bits in ((11, 11), (11, 8), (8, 11)):
@@ -566,10 +566,10 @@ def test_autotune_tile_side_and_digit_widths(orc):
         ws = pk.make_workspace(q)
         pk.workspace_init(q, ws)
         vals = torch.empty(q.max_dups + 64, dtype=torch.int32, device="cuda")
-        ranges = torch.empty(2 * q.n_tiles, dtype=torch.int32, device="cuda")
+        ranges = torch.empty(2 * q.n_tiles, dtype=torch.int64, device="cuda")
         pk.bin_and_sort(q, r.records, vals, ranges, ws)
         assert pk.read_status(q, ws)["flags"] == 0
-        assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.u32(ranges).reshape(-1, 2), ref_vals, ref_ranges)
+        assert_same_tile_lists(H.u32(vals[:len(ref_vals)]), H.i64(ranges).reshape(-1, 2), ref_vals, ref_ranges)
 
 
 def test_render_fwd_bwd_convenience_calls():

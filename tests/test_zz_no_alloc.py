@@ -57,12 +57,12 @@ def test_noalloc_matches_regular_call_twice(pk):
     for seed in (1, 2):                       # two calls in a row on the shared array
         rec = torch.from_numpy(_records(views, N, seed).reshape(-1)).cuda()
         vals_ref = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
-        rng_ref = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+        rng_ref = torch.empty(2 * plan.n_tiles, dtype=torch.int64, device="cuda")
         pk.bin_and_sort(plan, rec, vals_ref, rng_ref, ws)
         st = pk.read_status(plan, ws)
         assert st["flags"] == 0 and st["dups"] > 0
         vals = torch.full((plan.max_dups + 64,), -7, dtype=torch.int32, device="cuda")
-        rng = torch.full((2 * plan.n_tiles,), -7, dtype=torch.int32, device="cuda")
+        rng = torch.full((2 * plan.n_tiles,), -7, dtype=torch.int64, device="cuda")
         n = torch.zeros(1, dtype=torch.int32, device="cuda")
         pk.bin_and_sort_noalloc(plan, rec, vals, rng, n)
         torch.cuda.synchronize()
@@ -79,7 +79,7 @@ def test_noalloc_reports_overflow_and_rejects_oversized_plans(pk):
     plan = pk.Plan([(side, side, 0, 0, 0)], (side, side), 0, 1, "f32", views, N, max_dups=1024)
     rec = torch.from_numpy(_records(views, N, 3).reshape(-1)).cuda()
     vals = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
-    rng = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    rng = torch.empty(2 * plan.n_tiles, dtype=torch.int64, device="cuda")
     n = torch.zeros(1, dtype=torch.int32, device="cuda")
     pk.bin_and_sort_noalloc(plan, rec, vals, rng, n)
     torch.cuda.synchronize()
@@ -101,11 +101,11 @@ def _both(pk, plan, rec):
     ws = pk.make_workspace(plan)
     pk.workspace_init(plan, ws)
     vals_ref = torch.empty(plan.max_dups + 64, dtype=torch.int32, device="cuda")
-    rng_ref = torch.empty(2 * plan.n_tiles, dtype=torch.int32, device="cuda")
+    rng_ref = torch.empty(2 * plan.n_tiles, dtype=torch.int64, device="cuda")
     pk.bin_and_sort(plan, rec, vals_ref, rng_ref, ws)
     st = pk.read_status(plan, ws)
     vals = torch.full((plan.max_dups + 64,), -7, dtype=torch.int32, device="cuda")
-    rng = torch.full((2 * plan.n_tiles,), -7, dtype=torch.int32, device="cuda")
+    rng = torch.full((2 * plan.n_tiles,), -7, dtype=torch.int64, device="cuda")
     n = torch.zeros(1, dtype=torch.int32, device="cuda")
     pk.bin_and_sort_noalloc(plan, rec, vals, rng, n)
     torch.cuda.synchronize()
@@ -138,7 +138,7 @@ def test_noalloc_reports_a_wait_that_gave_up(pk):
     rec = torch.from_numpy(_records(views, 3000, 13).reshape(-1)).cuda()
     bad = _plan(pk, views, 3000, max_dups=400_000, first_wait_polls=-1)
     vals = torch.empty(bad.max_dups + 64, dtype=torch.int32, device="cuda")
-    rng = torch.full((2 * bad.n_tiles,), 7, dtype=torch.int32, device="cuda")
+    rng = torch.full((2 * bad.n_tiles,), 7, dtype=torch.int64, device="cuda")
     n = torch.zeros(1, dtype=torch.int32, device="cuda")
     pk.bin_and_sort_noalloc(bad, rec, vals, rng, n)
     torch.cuda.synchronize()
