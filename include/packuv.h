@@ -292,7 +292,8 @@ pk_status pk_project_and_sh(const pk_plan *plan, const float *soa, float *record
  * records:     [V*N][12] (reads m, conic, z, radius).
  * sorted_vals: out [max_dups] uint32 pair index of each entry.
  * tile_ranges: out [n_tiles][2] uint64 [start, end) into sorted_vals (entry
- *              positions are 64-bit: a plan may hold up to 2^35 entries);
+ *              positions are 64-bit: a plan may hold up to 2^35 entries),
+ *              8-byte aligned;
  *              global tile id = tile_off(v) + ty * ceil(W_v/T) + tx.
  * If the entries exceed max_dups the device sets PK_DEV_CAPACITY, records
  * dups_needed and emits nothing (all ranges empty). */

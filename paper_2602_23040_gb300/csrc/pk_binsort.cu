@@ -634,13 +634,31 @@ struct Down {
                                   sizeof(uint32_t) * (kWarps + 1) + 2 * sizeof(uint64_t) + 16;
 };
 
-template <int RB, int IT>
+// The last pass over packed entries (one word: tile id above pair index)
+// writes no words: it writes each entry's pair index into vout and folds
+// the tile ranges in with atomics (start as the largest ~position, end as
+// the largest position + 1, on ranges zeroed beforehand; k_range_fix turns
+// them into [start, end)).  In a segmented sort both ids are local to the
+// block's view.
+struct Unpack {
+  uint64_t *ranges;
+  const uint32_t *toff;   // [V + 1] first global tile of each view
+  uint32_t N;             // pairs per view
+  int pbits;              // pair-index bits below the tile id
+  uint32_t n_tiles;
+  uint64_t npairs;
+};
+
+// kMode 0: values travel with the keys (vin/vout); 1: keys only (packed
+// entries); 2: keys only, the last pass (pair indices and tile ranges out).
+template <int RB, int IT, int kMode>
 __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix_downsweep(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint64_t *n_dev, uint64_t n_host, int shift, uint32_t mask,
     const uint64_t *__restrict__ hist, pk_device_status *status, SegSpec sp, uint32_t *abort_flag,
-    uint32_t first_polls, bool try_single) {
+    uint32_t first_polls, bool try_single, Unpack up) {
   using C = Radix<RB, IT>;
+  constexpr bool kV = kMode == 0, kLast = kMode == 2;
   constexpr int kTile = C::kTile;
   constexpr int kSpan = Down<RB, IT>::kSpan;
   extern __shared__ __align__(16) unsigned char s_raw[];
@@ -666,6 +684,15 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
   }
   for (int d = tid; d < C::kR; d += kThreads) s_gbase[d] = hist[hbase + (size_t)d * hstride];
   const int ntile = (int)((b1 - b0 + kTile - 1) / kTile);
+  // last packed pass: the block's view (segmented) turns local ids global
+  uint32_t tile0 = 0, tile1 = up.n_tiles;
+  uint64_t pid0 = 0;
+  if (kLast && sp.tab) {
+    const int vw = sp.tab[blockIdx.x].x;
+    tile0 = __ldg(up.toff + vw);
+    tile1 = __ldg(up.toff + vw + 1);
+    pid0 = (uint64_t)vw * up.N;
+  }
   // Every tile of this chunk starts mis = b0 mod 4 keys past a 16-byte
   // boundary: the bulk copy starts at that boundary and takes whole
   // 16-byte groups; tile key li lands at buf[mis + li].
@@ -675,10 +702,10 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     const uint32_t valid = (uint32_t)min((uint64_t)kTile, b1 - base);
     const uint32_t bytes = ((mis + valid) & ~3u) * 4u;
     uint32_t *dst = buf[t & 1];
-    mbar_expect_tx(&s_bar[t & 1], 2 * bytes);
+    mbar_expect_tx(&s_bar[t & 1], (kV ? 2u : 1u) * bytes);
     if (bytes) {
       tma_load_1d(dst, kin + (base - mis), bytes, &s_bar[t & 1]);
-      tma_load_1d(dst + kSpan, vin + (base - mis), bytes, &s_bar[t & 1]);
+      if (kV) tma_load_1d(dst + kSpan, vin + (base - mis), bytes, &s_bar[t & 1]);
     }
   };
   if (tid == 0) {
@@ -709,7 +736,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     const uint32_t tail0 = whole ? whole - mis : 0u;
     if (tid < (int)(valid - tail0)) {
       bk[tail0 + tid] = __ldg(kin + base + tail0 + tid);
-      bv[tail0 + tid] = __ldg(vin + base + tail0 + tid);
+      if (kV) bv[tail0 + tid] = __ldg(vin + base + tail0 + tid);
     }
     for (int i = tid; i < kWarps * C::kR / 2; i += kThreads) reinterpret_cast<uint32_t *>(s_wcnt)[i] = 0;
     if (__syncthreads_or(!ok)) {
@@ -727,7 +754,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
     // out as it is (tried only where that is likely -- the top byte of the
     // depths, which all lie within a binade or two -- since the check costs
     // a pass over the tile)
-    if (try_single) {
+    if (!kLast && try_single) {
       const uint32_t d0 = (bk[0] >> shift) & mask;   // valid >= 1 here
       bool same = true;
 #pragma unroll
@@ -745,7 +772,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
             continue;
           }
           kout[o] = bk[i];
-          vout[o] = bv[i];
+          if (kV) vout[o] = bv[i];
         }
         if (bad) {
           atomicOr(&status->flags, PK_DEV_BOUNDS);
@@ -802,7 +829,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
 #pragma unroll
     for (int j = 0; j < C::kItems; ++j) {
       const uint32_t li = (uint32_t)(warp * 32 * C::kItems + j * 32 + lane);
-      val[j] = li < valid ? bv[li] : 0u;
+      val[j] = kV && li < valid ? bv[li] : 0u;
     }
     __syncthreads();
 #pragma unroll
@@ -812,7 +839,7 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
       const uint32_t d = in ? ((key[j] >> shift) & mask) : (uint32_t)(C::kR - 1);
       const uint32_t r = s_start[d] + wc[d] + rank[j];
       bk[r] = key[j];
-      bv[r] = val[j];
+      if (kV) bv[r] = val[j];
     }
     __syncthreads();
     for (uint32_t i = tid; i < valid; i += kThreads) {
@@ -824,8 +851,25 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
         *abort_flag = 1u;
         continue;
       }
-      kout[o] = k;
-      vout[o] = bv[i];
+      if (kLast) {
+        // a tile's entries are one run here (same digit, and the earlier
+        // passes left them together), so its first and last write the range
+        const uint32_t lt = k >> up.pbits;
+        const uint64_t tile = (uint64_t)tile0 + lt, gp = pid0 + (k & ((1u << up.pbits) - 1u));
+        if (tile >= tile1 || gp >= up.npairs) {   // a word that names no tile or pair
+          atomicOr(&status->flags, PK_DEV_BOUNDS);
+          *abort_flag = 1u;
+          continue;
+        }
+        vout[o] = (uint32_t)gp;
+        if (i == 0 || (bk[i - 1] >> up.pbits) != lt)
+          atomicMax(reinterpret_cast<unsigned long long *>(up.ranges + 2 * tile), (unsigned long long)~o);
+        if (i + 1 == valid || (bk[i + 1] >> up.pbits) != lt)
+          atomicMax(reinterpret_cast<unsigned long long *>(up.ranges + 2 * tile + 1), (unsigned long long)(o + 1));
+      } else {
+        kout[o] = k;
+        if (kV) vout[o] = bv[i];
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -848,8 +892,8 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
                                                    const uint64_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
                                                    DevCounters *ctr, const DevView *__restrict__ views,
                                                    int64_t N, int64_t pairs, int T, int mode, int local_bits,
-                                                   uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                                                   pk_device_status *status) {
+                                                   int pbits, uint32_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ vals, pk_device_status *status) {
   __shared__ WarpSplat s_ws[kWarps][32];
   const uint64_t dups = ctr->dups;
   if (dups == 0) return;
@@ -859,7 +903,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
   for (uint64_t w = blockIdx.x * (uint64_t)kWarps + warp; w * 32 < n; w += nwarps) {
     const uint64_t k = w * 32 + lane;
-    uint32_t ncand = 0, p = 0;
+    uint32_t ncand = 0, p = 0, pw = 0;   // pw: the entry's value (packed: the pair index below the key)
     uint64_t msk = 0;
     WarpSplat ws;
     ws.g0 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -892,8 +936,12 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
         }
         ws.r0 = make_int4(x0, y0, wt, v.width);
         // key: the global tile id, or (segmented sort) the view above the
-        // local tile id, whose low local_bits bits alone are sorted
-        const uint32_t kbase = local_bits ? (vi << local_bits) : (uint32_t)v.tile_off;
+        // local tile id, whose low local_bits bits alone are sorted.
+        // Packed (pbits > 0): one word, the tile id (local to the view in a
+        // segmented sort) above the pair index (local to the view there too)
+        const uint32_t kbase = pbits ? (local_bits ? 0u : (uint32_t)v.tile_off)
+                                     : (local_bits ? (vi << local_bits) : (uint32_t)v.tile_off);
+        pw = pbits && local_bits ? p - vi * (uint32_t)N : p;
         ws.r1 = make_int4(v.height, (int)(kbase + (uint32_t)y0 * v.tiles_x + (uint32_t)x0), v.tiles_x, (int)ncand);
         msk = ((uint64_t)info.y << 32) | info.x;
       }
@@ -913,7 +961,7 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       const uint32_t ee = e < E ? e : E - 1;
       const int o = candidate_owner(incl, ee);
       const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
-      const uint32_t o_p = __shfl_sync(0xffffffffu, p, o);
+      const uint32_t o_p = __shfl_sync(0xffffffffu, pw, o);
       const uint64_t o_msk = __shfl_sync(0xffffffffu, msk, o);
       const WarpSplat &os = s_ws[warp][o];
       const int4 r0 = os.r0, r1 = os.r1;
@@ -934,8 +982,13 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       if (take) {
         const uint64_t at = off0 + written + __popc(bal & lt);
         if (at < dups) {
-          keys[at] = (uint32_t)r1.y + ly * (uint32_t)r1.z + lx;
-          vals[at] = o_p;
+          const uint32_t key = (uint32_t)r1.y + ly * (uint32_t)r1.z + lx;
+          if (pbits) {
+            keys[at] = (key << pbits) | o_p;
+          } else {
+            keys[at] = key;
+            vals[at] = o_p;
+          }
         } else {   // more receiving tiles than counted: never write past the entries
           atomicOr(&status->flags, PK_DEV_BOUNDS);
           ctr->sort_abort = 1u;
@@ -997,6 +1050,23 @@ __global__ __launch_bounds__(kThreads) void k_ranges(const uint32_t *__restrict_
   }
 }
 
+// Tile ranges after the last packed pass, which left start as the largest
+// ~position (0: no entry) and end as the largest position + 1.  A call
+// that gave up leaves every range empty.
+__global__ __launch_bounds__(kThreads) void k_range_fix(uint64_t *__restrict__ ranges, uint32_t n_tiles,
+                                                        const DevCounters *ctr) {
+  const bool gave_up = ctr->sort_abort != 0;
+  for (uint32_t t = blockIdx.x * kThreads + threadIdx.x; t < n_tiles; t += gridDim.x * kThreads) {
+    const uint64_t a = ranges[2 * (size_t)t];
+    if (gave_up || a == 0ull) {
+      ranges[2 * (size_t)t] = 0ull;
+      ranges[2 * (size_t)t + 1] = 0ull;
+    } else {
+      ranges[2 * (size_t)t] = ~a;
+    }
+  }
+}
+
 // Where every view's items start, the pairs being grouped by view (pair
 // pid belongs to view pid / N): one thread per view finds the first pair
 // with pid >= v N by binary search.  kEntries: seg[v] = offs of that pair
@@ -1024,20 +1094,20 @@ __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__re
   }
 }
 
-template <int RB, int IT>
+template <int RB, int IT, int kMode>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint64_t *n_dev, uint64_t n_host, int shift, int bits, uint64_t *hist, int nblocks,
                         pk_device_status *status, SegSpec sp, uint32_t *abort_flag, uint32_t first_polls,
-                        bool try_single, cudaStream_t st) {
+                        bool try_single, const Unpack &up, cudaStream_t st) {
   using C = Radix<RB, IT>;
-  if (cudaFuncSetAttribute(k_radix_downsweep<RB, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(k_radix_downsweep<RB, IT, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Down<RB, IT>::kSmem) != cudaSuccess)
     return PK_ERR_CUDA;
   const uint32_t mask = (1u << bits) - 1u;
   k_radix_upsweep<RB, IT><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist, sp);
   k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
-  k_radix_downsweep<RB, IT><<<nblocks, kThreads, Down<RB, IT>::kSmem, st>>>(
-      kin, vin, kout, vout, n_dev, n_host, shift, mask, hist, status, sp, abort_flag, first_polls, try_single);
+  k_radix_downsweep<RB, IT, kMode><<<nblocks, kThreads, Down<RB, IT>::kSmem, st>>>(
+      kin, vin, kout, vout, n_dev, n_host, shift, mask, hist, status, sp, abort_flag, first_polls, try_single, up);
   return check_launch();
 }
 
@@ -1045,20 +1115,29 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 // depth-sorted pairs (pair_blocks() blocks) or over the entries
 // (sort_blocks() blocks, or the segmented table's), with digits of up to
 // rb = 8 or 11 bits (pk_options.sort_bits_*: wider digits take fewer passes
-// but run fewer blocks per SM and scatter into more runs).
+// but run fewer blocks per SM and scatter into more runs).  vin == nullptr:
+// packed entries, keys only; then up.ranges != nullptr marks the last pass.
 pk_status radix_pass(bool entries, int rb, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint64_t *n_dev, uint64_t n_host, int shift, int bits, uint64_t *hist, int nblocks,
                      pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls, bool try_single,
-                     cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}) {
-#define PK_PASS(RB, IT)                                                                                        \
-  return radix_pass_rb<RB, IT>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, sp,  \
-                               abort_flag, first_polls, try_single, st)
+                     cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}, Unpack up = Unpack{}) {
+#define PK_PASS(RB, IT, M)                                                                                        \
+  return radix_pass_rb<RB, IT, M>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, sp,  \
+                                  abort_flag, first_polls, try_single, up, st)
   if (entries) {
-    if (rb > 8) PK_PASS(11, kEntryItems);
-    PK_PASS(8, kEntryItems);
+    if (!vin && up.ranges) {
+      if (rb > 8) PK_PASS(11, kEntryItems, 2);
+      PK_PASS(8, kEntryItems, 2);
+    }
+    if (!vin) {
+      if (rb > 8) PK_PASS(11, kEntryItems, 1);
+      PK_PASS(8, kEntryItems, 1);
+    }
+    if (rb > 8) PK_PASS(11, kEntryItems, 0);
+    PK_PASS(8, kEntryItems, 0);
   }
-  if (rb > 8) PK_PASS(11, kPairItems);
-  PK_PASS(8, kPairItems);
+  if (rb > 8) PK_PASS(11, kPairItems, 0);
+  PK_PASS(8, kPairItems, 0);
 #undef PK_PASS
 }
 
@@ -1226,29 +1305,48 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     sp = SegSpec{tab, vseg};
     nblocks = nseg;
   }
+  // Packed entries when the tile id and the pair index fit one word
+  // together (both local to the view in a segmented sort; at the 52-view
+  // rig 11 + 20 bits): the tile passes then move 4 bytes per entry
+  // instead of 8, and the last one writes the pair indices and folds the
+  // tile ranges in (no pass over the sorted keys).
+  const uint64_t pid_end = seg ? (uint64_t)p->N : pairs;
+  int pbits = 1;
+  while ((uint64_t(1) << pbits) < pid_end) ++pbits;
+  const bool packed = key_bits + pbits <= 32;
   np = radix_plan(key_bits, rt, widths);
   uint32_t *vbuf[2] = {(np & 1) ? dv : sorted_vals, (np & 1) ? sorted_vals : dv};
   uint32_t *kbuf[2] = {dk0, dk1};
   k_emit<<<std::max(1, sms) * 32, kThreads, 0, st>>>(records, pval, offs, pinfo, ctr, views, p->N, p->pairs, p->T,
-                                                      p->opts.bin_mode, seg ? key_bits : 0, kbuf[0], vbuf[0],
-                                                      status);
+                                                      p->opts.bin_mode, seg ? key_bits : 0, packed ? pbits : 0,
+                                                      kbuf[0], vbuf[0], status);
   // Digits from the top down: each tile's entries still end up contiguous
   // and in emission order, and the first pass, whose input holds each
   // splat's tiles side by side, ranks on tile-row bands that the 32 entries
   // of a warp rarely differ in (ranking slows with the distinct digits of
   // a warp).  The tiles follow one another by (low digit, high digit)
   // instead of by id.
-  shift = key_bits;
+  shift = (packed ? pbits : 0) + key_bits;
+  const Unpack up{tile_ranges, at<uint32_t>(ws, L.toff), (uint32_t)p->N, pbits, (uint32_t)p->n_tiles, pairs};
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
+    const bool last = pass + 1 == np;
     shift -= widths[pass];
-    if ((e = radix_pass(true, rt, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
-                        status, &ctr->sort_abort, p->first_polls, false, st, sp)) != PK_OK)
-      return e;
+    if (packed)
+      e = radix_pass(true, rt, kbuf[a], nullptr, last ? nullptr : kbuf[b], last ? sorted_vals : nullptr, &ctr->dups,
+                     0, shift, widths[pass], hist, nblocks, status, &ctr->sort_abort, p->first_polls, false, st, sp,
+                     last ? up : Unpack{});
+    else
+      e = radix_pass(true, rt, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
+                     status, &ctr->sort_abort, p->first_polls, false, st, sp);
+    if (e != PK_OK) return e;
   }
-  k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], seg ? key_bits : 0,
-                                                        at<uint32_t>(ws, L.toff), ctr, tile_ranges, p->V,
-                                                        (uint32_t)p->n_tiles, status);
+  if (packed)
+    k_range_fix<<<std::max(1, sms) * 4, kThreads, 0, st>>>(tile_ranges, (uint32_t)p->n_tiles, ctr);
+  else
+    k_ranges<<<std::max(1, sms) * 16, kThreads, 0, st>>>(kbuf[np & 1], seg ? key_bits : 0,
+                                                          at<uint32_t>(ws, L.toff), ctr, tile_ranges, p->V,
+                                                          (uint32_t)p->n_tiles, status);
   return check_launch();
 }
 
@@ -1274,7 +1372,9 @@ int pk::bin_kernel_count(const pk_plan *p) {
 extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
                                      uint64_t *tile_ranges, void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !ws) return PK_ERR_ARG;
-  if (!aligned16(records) || !aligned16(sorted_vals) || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PK_ERR_ARG;
+  if (!aligned16(records) || !aligned16(sorted_vals) || (reinterpret_cast<uintptr_t>(ws) & 255u) ||
+      (reinterpret_cast<uintptr_t>(tile_ranges) & 7u))
+    return PK_ERR_ARG;
   return bin_and_sort_impl(p, p->ws, ws, records, sorted_vals, tile_ranges, p->max_dups,
                            reinterpret_cast<cudaStream_t>(stream));
 }
@@ -1332,7 +1432,8 @@ __global__ void k_report_entries(const DevCounters *ctr, const pk_device_status 
 extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *records, uint32_t *sorted_vals,
                                              uint64_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !n_entries) return PK_ERR_ARG;
-  if (!aligned16(records) || !aligned16(sorted_vals)) return PK_ERR_ARG;
+  if (!aligned16(records) || !aligned16(sorted_vals) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u))
+    return PK_ERR_ARG;
   // layout of this plan's scratch inside the static array
   const uint64_t pairs = (uint64_t)p->pairs, maxd = p->max_dups;
   WsLayout L{};

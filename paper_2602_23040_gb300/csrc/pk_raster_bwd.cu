@@ -386,7 +386,8 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
                                       const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !T_final || !n_contrib || !dL_dimage || !grad2d || !ws)
     return PK_ERR_ARG;
-  if (!aligned16(records) || !aligned16(grad2d)) return PK_ERR_ARG;
+  if (!aligned16(records) || !aligned16(grad2d) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u))
+    return PK_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);

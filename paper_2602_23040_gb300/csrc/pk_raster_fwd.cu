@@ -323,7 +323,7 @@ extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, co
                                       const uint64_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib,
                                       void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !image || !T_final || !n_contrib || !ws) return PK_ERR_ARG;
-  if (!aligned16(records)) return PK_ERR_ARG;
+  if (!aligned16(records) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return PK_ERR_ARG;
   return rasterize_fwd(p, records, sorted_vals, tile_ranges, nullptr, image, T_final, n_contrib, nullptr, ws,
                        reinterpret_cast<cudaStream_t>(stream));
 }
@@ -335,7 +335,7 @@ extern "C" pk_status pk_rasterize_fwd_l1(const pk_plan *p, const float *records,
   if (!p || !records || !sorted_vals || !tile_ranges || !target || !image || !T_final || !n_contrib ||
       !dL_dimage || !ws)
     return PK_ERR_ARG;
-  if (!aligned16(records)) return PK_ERR_ARG;
+  if (!aligned16(records) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return PK_ERR_ARG;
   return rasterize_fwd(p, records, sorted_vals, tile_ranges, target, image, T_final, n_contrib, dL_dimage, ws,
                        reinterpret_cast<cudaStream_t>(stream));
 }
