@@ -888,13 +888,27 @@ __global__ __launch_bounds__(kThreads, (Radix<RB, IT>::kMinBlocks)) void k_radix
 // that the stores of a warp are contiguous.
 // ---------------------------------------------------------------------------
 
+// What a lane of the emission walk reads of the pair that owns its
+// candidate: everything it needs comes from shared memory in two 16-byte
+// loads (three more for a footprint of more than 64 candidates), instead of
+// one shuffle per value.
+struct EmitPair {
+  int4 c;      // key of the first candidate tile, tiles per view row (bit 31: > 64 candidates), width w, 1/w bits
+  uint4 e;     // first candidate's index in the warp's walk, value, receiving mask (low, high)
+};
+struct EmitFoot {
+  float4 g0, g1;   // the footprint (mx, my, a, b), (c, 1/a, 1/c, 2b)
+  int4 r;          // first candidate tile (x, y), view width and height
+};
+
 __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec, const uint32_t *__restrict__ pval,
                                                    const uint64_t *__restrict__ offs, const uint4 *__restrict__ pinfo,
                                                    DevCounters *ctr, const DevView *__restrict__ views,
                                                    int64_t N, int64_t pairs, int T, int mode, int local_bits,
                                                    int pbits, uint32_t *__restrict__ keys,
                                                    uint32_t *__restrict__ vals, pk_device_status *status) {
-  __shared__ WarpSplat s_ws[kWarps][32];
+  __shared__ EmitPair s_ep[kWarps][32];
+  __shared__ EmitFoot s_ef[kWarps][32];
   const uint64_t dups = ctr->dups;
   if (dups == 0) return;
   const uint64_t n = ctr->n_valid;
@@ -903,18 +917,15 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
   for (uint64_t w = blockIdx.x * (uint64_t)kWarps + warp; w * 32 < n; w += nwarps) {
     const uint64_t k = w * 32 + lane;
-    uint32_t ncand = 0, p = 0, pw = 0;   // pw: the entry's value (packed: the pair index below the key)
-    uint64_t msk = 0;
-    WarpSplat ws;
-    ws.g0 = make_float4(0.f, 0.f, 0.f, 0.f);
-    ws.g1 = ws.g0;
-    ws.r0 = make_int4(0, 0, 1, 1);
-    ws.r1 = make_int4(1, 0, 1, 0);
+    uint32_t ncand = 0;
+    EmitPair ep;
+    ep.c = make_int4(0, 0, 1, __float_as_int(1.f));
+    ep.e = make_uint4(0u, 0u, 0u, 0u);
     if (k < n) {
       // the count pass left the candidate rectangle and, for up to 64
       // candidates, the mask of the receiving ones: the record is read
       // again only for a larger footprint
-      p = pval[k];
+      uint32_t p = pval[k];
       if ((uint64_t)p >= (uint64_t)pairs) {   // never index past the pairs
         atomicOr(&status->flags, PK_DEV_BOUNDS);
         ctr->sort_abort = 1u;
@@ -927,67 +938,70 @@ __global__ __launch_bounds__(kThreads) void k_emit(const float *__restrict__ rec
       if (ncand) {
         const uint32_t vi = p / (uint32_t)N;
         const DevView &v = views[vi];
-        if (mode != PK_BIN_RECT && ncand > kMaskBits) {
+        const bool large = mode != PK_BIN_RECT && ncand > kMaskBits;
+        if (large) {
           const float4 a = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec));
           const float4 b = __ldg(reinterpret_cast<const float4 *>(rec + (uint64_t)p * kRec) + 1);
           const Foot f = make_foot(a.x, a.y, a.z, a.w, b.x);
-          ws.g0 = make_float4(f.mx, f.my, f.a, f.b);
-          ws.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
+          EmitFoot ef;
+          ef.g0 = make_float4(f.mx, f.my, f.a, f.b);
+          ef.g1 = make_float4(f.c, f.ra, f.rc, f.b2);
+          ef.r = make_int4(x0, y0, v.width, v.height);
+          s_ef[warp][lane] = ef;
         }
-        ws.r0 = make_int4(x0, y0, wt, v.width);
         // key: the global tile id, or (segmented sort) the view above the
         // local tile id, whose low local_bits bits alone are sorted.
         // Packed (pbits > 0): one word, the tile id (local to the view in a
         // segmented sort) above the pair index (local to the view there too)
         const uint32_t kbase = pbits ? (local_bits ? 0u : (uint32_t)v.tile_off)
                                      : (local_bits ? (vi << local_bits) : (uint32_t)v.tile_off);
-        pw = pbits && local_bits ? p - vi * (uint32_t)N : p;
-        ws.r1 = make_int4(v.height, (int)(kbase + (uint32_t)y0 * v.tiles_x + (uint32_t)x0), v.tiles_x, (int)ncand);
-        msk = ((uint64_t)info.y << 32) | info.x;
+        const uint32_t pw = pbits && local_bits ? p - vi * (uint32_t)N : p;
+        ep.c = make_int4((int)(kbase + (uint32_t)y0 * v.tiles_x + (uint32_t)x0),
+                         v.tiles_x | (large ? (int)0x80000000u : 0), wt, __float_as_int(__frcp_rn((float)wt)));
+        ep.e = make_uint4(0u, pw, info.x, info.y);
       }
     }
-    const float rw = __frcp_rn((float)ws.r0.z);
     uint64_t off0 = 0;
     if (lane == 0) off0 = offs[w * 32];
     off0 = __shfl_sync(0xffffffffu, off0, 0);
-    s_ws[warp][lane] = ws;
-    __syncwarp();
     const uint32_t incl = warp_incl_scan(ncand);
-    const uint32_t excl = incl - ncand;
+    ep.e.x = incl - ncand;
+    s_ep[warp][lane] = ep;
+    __syncwarp();
     const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
     uint32_t written = 0;
     for (uint32_t e0 = 0; e0 < E; e0 += 32) {
       const uint32_t e = e0 + lane;
       const uint32_t ee = e < E ? e : E - 1;
       const int o = candidate_owner(incl, ee);
-      const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
-      const uint32_t o_p = __shfl_sync(0xffffffffu, pw, o);
-      const uint64_t o_msk = __shfl_sync(0xffffffffu, msk, o);
-      const WarpSplat &os = s_ws[warp][o];
-      const int4 r0 = os.r0, r1 = os.r1;
-      const uint32_t local = ee - o_excl;
+      const int4 c = s_ep[warp][o].c;
+      const uint4 oe = s_ep[warp][o].e;
+      const uint32_t local = ee - oe.x;
       uint32_t ly, lx;
-      divmod_small(local, (uint32_t)r0.z, __shfl_sync(0xffffffffu, rw, o), ly, lx);
+      divmod_small(local, (uint32_t)c.z, __int_as_float(c.w), ly, lx);
       bool take = e < E;
+      const bool large = c.y < 0;
       if (take && mode != PK_BIN_RECT) {
-        if (r1.w <= kMaskBits) {
-          take = (o_msk >> local) & 1u;
+        if (!large) {
+          take = ((local < 32 ? oe.z >> local : oe.w >> (local - 32)) & 1u) != 0u;
         } else {
-          const float4 g0 = os.g0, g1 = os.g1;
+          const EmitFoot &ef = s_ef[warp][o];
+          const float4 g0 = ef.g0, g1 = ef.g1;
+          const int4 r = ef.r;
           const Foot f{g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-          take = tile_hit(f, r0.x + (int)lx, r0.y + (int)ly, r0.w, r1.x, T);
+          take = tile_hit(f, r.x + (int)lx, r.y + (int)ly, r.z, r.w, T);
         }
       }
       const uint32_t bal = __ballot_sync(0xffffffffu, take);
       if (take) {
         const uint64_t at = off0 + written + __popc(bal & lt);
         if (at < dups) {
-          const uint32_t key = (uint32_t)r1.y + ly * (uint32_t)r1.z + lx;
+          const uint32_t key = (uint32_t)c.x + ly * (uint32_t)(c.y & 0x7fffffff) + lx;
           if (pbits) {
-            keys[at] = (key << pbits) | o_p;
+            keys[at] = (key << pbits) | oe.y;
           } else {
             keys[at] = key;
-            vals[at] = o_p;
+            vals[at] = oe.y;
           }
         } else {   // more receiving tiles than counted: never write past the entries
           atomicOr(&status->flags, PK_DEV_BOUNDS);
