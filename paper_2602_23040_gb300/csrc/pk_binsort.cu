@@ -236,9 +236,10 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
                                                          const DevView *__restrict__ views, int T, int mode,
                                                          uint32_t *__restrict__ cnt, uint4 *__restrict__ pinfo,
                                                          uint32_t *__restrict__ zbits) {
+  constexpr uint32_t kBalChunks = 64;   // a walk of up to 2,048 candidates keeps its ballots
   __shared__ WarpSplat s_ws[kWarps][32];
+  __shared__ uint32_t s_bal[kWarps][kBalChunks];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t lt = lanemask_lt();
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
   for (uint64_t w = blockIdx.x * (uint64_t)kWarps + warp; w * 32 < (uint64_t)pairs; w += nwarps) {
     const uint64_t p = w * 32 + lane;
@@ -272,33 +273,22 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
       }
       continue;
     }
-    s_ws[warp][lane] = ws;
-    __syncwarp();
-    const float rw = __frcp_rn((float)ws.r0.z);   // for the candidate -> (row, column) split
     const uint32_t incl = warp_incl_scan(ncand);
     const uint32_t excl = incl - ncand;
+    // the owner's walk offset and 1 / width ride in the record, so a lane
+    // reads its candidate's owner from shared memory alone
+    ws.r1.y = (int)excl;
+    ws.r1.z = __float_as_int(__frcp_rn((float)ws.r0.z));   // for the candidate -> (row, column) split
+    s_ws[warp][lane] = ws;
+    __syncwarp();
     const uint32_t E = __shfl_sync(0xffffffffu, incl, 31);
+    // Each lane's own candidates [excl, incl) are read off the walk's
+    // ballots: after the walk from the kept ballots (a lane visits only
+    // the 1-3 steps its pair spans), or, for a longer walk, step by step.
+    const bool keep = E <= 32 * kBalChunks;
     uint32_t mine = 0;
     uint64_t mask = 0;
-    for (uint32_t e0 = 0; e0 < E; e0 += 32) {
-      const uint32_t e = e0 + lane;
-      const uint32_t ee = e < E ? e : E - 1;
-      const int o = candidate_owner(incl, ee);
-      const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, o);
-      const WarpSplat &os = s_ws[warp][o];
-      const int4 r0 = os.r0;
-      const uint32_t local = ee - o_excl;
-      uint32_t lyq, lxr;
-      divmod_small(local, (uint32_t)r0.z, __shfl_sync(0xffffffffu, rw, o), lyq, lxr);
-      const int ty = r0.y + (int)lyq, tx = r0.x + (int)lxr;
-      bool hit = false;
-      if (e < E) {
-        const float4 g0 = os.g0, g1 = os.g1;
-        const Foot f{g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
-        hit = tile_hit(f, tx, ty, r0.w, os.r1.x, T);
-      }
-      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-      // this lane's own pair: its candidates in [excl, incl) meet this step's [e0, e0 + 32)
+    auto take_bits = [&](uint32_t e0, uint32_t bal) {
       const uint32_t lo = max(excl, e0), hi = min(incl, e0 + 32);
       if (lo < hi) {
         const uint32_t span = hi - lo;
@@ -306,8 +296,35 @@ __global__ __launch_bounds__(kThreads) void k_pair_count(const float *__restrict
         mine += __popc(bits);
         if (ncand <= kMaskBits) mask |= (uint64_t)bits << (lo - excl);
       }
+    };
+    for (uint32_t e0 = 0; e0 < E; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const uint32_t ee = e < E ? e : E - 1;
+      const int o = candidate_owner(incl, ee);
+      const WarpSplat &os = s_ws[warp][o];
+      const int4 r0 = os.r0, r1 = os.r1;
+      const uint32_t local = ee - (uint32_t)r1.y;
+      uint32_t lyq, lxr;
+      divmod_small(local, (uint32_t)r0.z, __int_as_float(r1.z), lyq, lxr);
+      const int ty = r0.y + (int)lyq, tx = r0.x + (int)lxr;
+      bool hit = false;
+      if (e < E) {
+        const float4 g0 = os.g0, g1 = os.g1;
+        const Foot f{g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+        hit = tile_hit(f, tx, ty, r0.w, r1.x, T);
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      if (keep) {
+        if (lane == 0) s_bal[warp][e0 >> 5] = bal;
+      } else {
+        take_bits(e0, bal);
+      }
     }
-    (void)lt;
+    if (keep) {
+      __syncwarp();   // lane 0's ballots visible to every lane
+      if (ncand)
+        for (uint32_t c = excl >> 5; 32 * c < incl; ++c) take_bits(32 * c, s_bal[warp][c]);
+    }
     if (p < (uint64_t)pairs) {
       cnt[p] = mine;
       pinfo[p] = make_uint4((uint32_t)mask, (uint32_t)(mask >> 32), pack_rect(ws.r0.x, ws.r0.y),
@@ -325,15 +342,6 @@ struct SrcValid {      // 1 if pair i touches a tile
   const uint32_t *cnt;
   __device__ uint32_t operator()(uint64_t i) const { return cnt[i] > 0u ? 1u : 0u; }
 };
-struct SrcSorted {     // tile count of the i-th pair in depth order
-  const uint32_t *cnt, *pval;
-  uint64_t pairs;      // a pair index past the pairs (a depth pass that gave up) counts 0
-  __device__ uint32_t operator()(uint64_t i) const {
-    const uint32_t p = pval[i];
-    return p < pairs ? cnt[p] : 0u;
-  }
-};
-
 __device__ __forceinline__ uint64_t load_n(const uint64_t *n_dev, uint64_t n_host) {
   return n_dev ? *n_dev : n_host;
 }
@@ -406,43 +414,98 @@ __global__ __launch_bounds__(1024) void k_scan_top(uint64_t *__restrict__ bsum, 
   }
 }
 
+// Eight consecutive items of a u32 array from item i0 (a multiple of 8): two
+// 16-byte loads where all eight lie below b1, else one by one (0 past b1).
+__device__ __forceinline__ void load8(const uint32_t *__restrict__ a, uint64_t i0, uint64_t b1, uint32_t (&v)[8]) {
+  if (i0 + 7 < b1) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(a + i0));
+    const uint4 y = __ldg(reinterpret_cast<const uint4 *>(a + i0) + 1);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = i0 + j < b1 ? __ldg(a + i0 + j) : 0u;
+  }
+}
+static_assert(kScanItems == 8, "load8 takes a thread's scan items");
+
 // Down-sweep of the compaction: writes (bits(z), pair) of every valid pair
-// in pair order.
+// in pair order.  A tile's outputs go through shared memory so that the
+// writes are contiguous.
 __global__ __launch_bounds__(kThreads) void k_compact_down(const uint32_t *__restrict__ cnt,
                                                            const uint32_t *__restrict__ zbits, uint64_t n,
                                                            const uint64_t *__restrict__ bsum,
                                                            uint32_t *__restrict__ zkey, uint32_t *__restrict__ pval) {
   __shared__ uint32_t s[kWarps + 1];
+  __shared__ uint32_t s_z[kScanTile], s_p[kScanTile];
   uint64_t b0, b1;
   chunk_of(n, gridDim.x, blockIdx.x, kScanTile, b0, b1);
-  uint32_t run = (uint32_t)bsum[blockIdx.x];
+  uint32_t run = (uint32_t)bsum[blockIdx.x];   // valid pairs < 2^32
   for (uint64_t base = b0; base < b1; base += kScanTile) {
     const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanItems;
-    uint32_t f[kScanItems], c = 0;
+    uint32_t cv[8], zv[8], c = 0;
+    load8(cnt, i0, b1, cv);
+    load8(zbits, i0, b1, zv);
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      f[j] = (i0 + j < b1 && cnt[i0 + j] > 0u) ? 1u : 0u;
-      c += f[j];
-    }
+    for (int j = 0; j < 8; ++j) c += cv[j] > 0u ? 1u : 0u;
     uint32_t tot;
-    uint32_t pre = block_excl_scan<uint32_t>(c, tot, s) + run;
+    uint32_t pre = block_excl_scan<uint32_t>(c, tot, s);
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      if (f[j]) {
-        const uint64_t p = i0 + j;
-        zkey[pre] = __ldg(zbits + p);
-        pval[pre] = (uint32_t)p;
+    for (int j = 0; j < 8; ++j)
+      if (cv[j] > 0u) {
+        s_z[pre] = zv[j];
+        s_p[pre] = (uint32_t)(i0 + j);
         ++pre;
       }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < tot; k += kThreads) {
+      zkey[run + k] = s_z[k];
+      pval[run + k] = s_p[k];
     }
+    __syncthreads();   // before the next tile's outputs reuse s_z, s_p
     run += tot;
   }
 }
 
+// Tile counts of the pairs in depth order, gathered once: csorted[i] =
+// cnt[pval[i]] (0 for a pair index past the pairs, which a depth pass that
+// gave up can leave), and each block's sum for the offset scan.
+__global__ __launch_bounds__(kThreads) void k_reduce_sorted(const uint32_t *__restrict__ cnt,
+                                                            const uint32_t *__restrict__ pval, uint64_t pairs,
+                                                            const uint64_t *n_dev, uint32_t *__restrict__ csorted,
+                                                            uint64_t *__restrict__ bsum) {
+  __shared__ uint64_t s[kWarps + 1];
+  const uint64_t n = *n_dev;
+  uint64_t b0, b1;
+  chunk_of(n, gridDim.x, blockIdx.x, kScanTile, b0, b1);
+  uint64_t acc = 0;
+  for (uint64_t base = b0; base < b1; base += kScanTile) {
+    const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t pv[8], v[8];
+    load8(pval, i0, b1, pv);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      v[j] = i0 + j < b1 && pv[j] < pairs ? __ldg(cnt + pv[j]) : 0u;
+      acc += v[j];
+    }
+    if (i0 + 7 < b1) {
+      reinterpret_cast<uint4 *>(csorted + i0)[0] = make_uint4(v[0], v[1], v[2], v[3]);
+      reinterpret_cast<uint4 *>(csorted + i0)[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (i0 + j < b1) csorted[i0 + j] = v[j];
+    }
+  }
+  uint64_t tot;
+  block_excl_scan<uint64_t>(acc, tot, s);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
 // Down-sweep of the emission-offset scan: offs[i] = entries before pair i
-// (64-bit: the entries of a launch may pass 2^32).
-__global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const uint64_t *n_dev,
-                                                           const uint64_t *__restrict__ bsum,
+// (64-bit: the entries of a launch may pass 2^32), from the gathered counts.
+__global__ __launch_bounds__(kThreads) void k_offsets_down(const uint32_t *__restrict__ csorted,
+                                                           const uint64_t *n_dev, const uint64_t *__restrict__ bsum,
                                                            const DevCounters *ctr, uint64_t *__restrict__ offs) {
   __shared__ uint64_t s[kWarps + 1];
   if (ctr->dups == 0) return;   // overflow (or nothing): nothing will be emitted
@@ -452,19 +515,26 @@ __global__ __launch_bounds__(kThreads) void k_offsets_down(SrcSorted src, const 
   uint64_t run = bsum[blockIdx.x];
   for (uint64_t base = b0; base < b1; base += kScanTile) {
     const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanItems;
-    uint32_t v[kScanItems];
+    uint32_t v[8];
+    load8(csorted, i0, b1, v);
     uint64_t c = 0;
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      v[j] = i0 + j < b1 ? src(i0 + j) : 0u;
-      c += v[j];
-    }
+    for (int j = 0; j < 8; ++j) c += v[j];
     uint64_t tot;
     uint64_t pre = block_excl_scan<uint64_t>(c, tot, s) + run;
+    uint64_t o[8];
 #pragma unroll
-    for (int j = 0; j < kScanItems; ++j) {
-      if (i0 + j < b1) offs[i0 + j] = pre;
+    for (int j = 0; j < 8; ++j) {
+      o[j] = pre;
       pre += v[j];
+    }
+    if (i0 + 7 < b1) {
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) reinterpret_cast<ulonglong2 *>(offs + i0)[j / 2] = make_ulonglong2(o[j], o[j + 1]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (i0 + j < b1) offs[i0 + j] = o[j];
     }
     run += tot;
   }
@@ -1304,10 +1374,10 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   }
   const uint32_t *pval = pv[np & 1];
   // emission offsets in (view,) depth order, capacity check
-  SrcSorted ss{cnt, pval, pairs};
-  k_scan_reduce<SrcSorted><<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, 0, bsum);
+  uint32_t *csorted = zk[1];   // the depth keys are spent: their buffer takes the gathered counts
+  k_reduce_sorted<<<kScanBlocks, kThreads, 0, st>>>(cnt, pval, pairs, n_valid, csorted, bsum);
   k_scan_top<<<1, 1024, 0, st>>>(bsum, kScanBlocks, 1, maxd, ctr, status);
-  k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(ss, n_valid, bsum, ctr, offs);
+  k_offsets_down<<<kScanBlocks, kThreads, 0, st>>>(csorted, n_valid, bsum, ctr, offs);
   // emission and the stable tile sort; the last pass lands in sorted_vals
   int key_bits = p->tile_bits;
   SegSpec sp{nullptr, nullptr};
