@@ -319,9 +319,9 @@ pk_status pk_bin_and_sort(const pk_plan *plan, const float *records, uint32_t *s
  * call shares the one array and leaves its contents behind (each call
  * clears its status and counters and uploads its own plan's tables before
  * use): calls whose work can overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.  The call copies the
- * plan's view and tile tables from host memory each time and never
- * allocates. */
+ * threads) race and must be serialised by the caller.  The call hands the
+ * plan's view and tile tables to the device as kernel arguments (a few
+ * small launches, no host-to-device copy) and never allocates. */
 pk_status pk_bin_and_sort_noalloc(const pk_plan *plan, const float *records, uint32_t *sorted_vals,
                                   uint64_t *tile_ranges, uint32_t *n_entries, pk_stream_t stream);
 

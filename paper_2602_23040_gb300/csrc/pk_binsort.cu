@@ -1474,6 +1474,7 @@ extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uin
 // sized once for every process that loads the library.
 // ---------------------------------------------------------------------------
 
+#include <cstring>
 #include <mutex>
 
 namespace {
@@ -1509,6 +1510,33 @@ __global__ void k_report_entries(const DevCounters *ctr, const pk_device_status 
   *n_entries = (f & PK_DEV_CAPACITY) ? 0xffffffffu
                                      : ((f & (PK_DEV_TIMEOUT | PK_DEV_BOUNDS)) || ctr->sort_abort) ? 0xfffffffeu
                                                                                                     : (uint32_t)ctr->dups;
+}
+
+// The plan's host tables reach the static array as kernel arguments, which
+// the launch itself copies: no host buffer has to stay pinned or alive
+// after the call, and no copy engine is involved.  Chunks of 960 words keep
+// each launch's arguments inside the 4 KB parameter space.
+constexpr uint32_t kChunkWords = 960;
+struct WordChunk {
+  uint32_t n;
+  uint32_t w[kChunkWords];
+};
+__global__ void k_put_words(const WordChunk c, uint32_t *__restrict__ dst) {
+  for (uint32_t i = threadIdx.x; i < c.n; i += blockDim.x) dst[i] = c.w[i];
+}
+pk_status put_words(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  const uint32_t *s = static_cast<const uint32_t *>(src);
+  uint32_t *d = static_cast<uint32_t *>(dst);
+  const size_t words = bytes / 4;
+  WordChunk c;
+  for (size_t off = 0; off < words; off += kChunkWords) {
+    c.n = (uint32_t)std::min<size_t>(kChunkWords, words - off);
+    std::memcpy(c.w, s + off, sizeof(uint32_t) * c.n);
+    k_put_words<<<1, 256, 0, st>>>(c, d + off);
+    const pk_status e = check_launch();
+    if (e != PK_OK) return e;
+  }
+  return PK_OK;
 }
 
 }  // namespace
@@ -1556,17 +1584,12 @@ extern "C" pk_status pk_bin_and_sort_noalloc(const pk_plan *p, const float *reco
   // the array keeps the previous call's contents: reset the status and
   // counters, refresh this plan's view table
   if ((e = zero_async({{at<char>(ws, L.status), L.views - L.status}}, st)) != PK_OK) return e;
-  if (cudaMemcpyAsync(at<char>(ws, L.views), p->h_views, sizeof(DevView) * p->V, cudaMemcpyHostToDevice, st) !=
-      cudaSuccess)
-    return PK_ERR_CUDA;
-  if (cudaMemcpyAsync(at<char>(ws, L.toff), p->h_toff, sizeof(uint32_t) * (p->V + 1), cudaMemcpyHostToDevice, st) !=
-      cudaSuccess)
-    return PK_ERR_CUDA;
-  int4 *tab = const_cast<pk_plan *>(p)->h_segtab;   // plan-owned: outlives the copy
+  if ((e = put_words(at<char>(ws, L.views), p->h_views, sizeof(DevView) * p->V, st)) != PK_OK) return e;
+  if ((e = put_words(at<char>(ws, L.toff), p->h_toff, sizeof(uint32_t) * (p->V + 1), st)) != PK_OK) return e;
+  int4 tab[2 * kSortBlocks] = {};
   int nt = 0, np = 0;
-  if (seg_tables(p, tab, &nt, &np) &&
-      cudaMemcpyAsync(at<char>(ws, L.sblk), tab, sizeof(p->h_segtab), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return PK_ERR_CUDA;
+  if (seg_tables(p, tab, &nt, &np) && (e = put_words(at<char>(ws, L.sblk), tab, sizeof(tab), st)) != PK_OK)
+    return e;
   if ((e = bin_and_sort_impl(p, L, ws, records, sorted_vals, tile_ranges, maxd, st)) != PK_OK) return e;
   const DevCounters *ctr = at<DevCounters>(ws, L.counters);
   const pk_device_status *status = at<pk_device_status>(ws, L.status);

@@ -142,17 +142,16 @@ __device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint3
 }
 
 // The exponent power = k q = A dx^2 + B dx dy + C dy^2 of a staged splat at
-// two pixel centres of one column (common dx and zx = A dx, rows py, dy =
-// py - m_y), two lanes at a time: u = B dy + zx, power = u dx + (C dy) dy,
-// each step rounded to nearest in this order, exactly the steps of
-// splat_alpha below (the forward's scalar form), so the two kernels take
-// identical skip and clamp decisions.  A pixel skips the splat unless
-// power >= pcut; then alpha = min(0.99, o 2^power).
-__device__ __forceinline__ f32x2 splat_power2(const float4 &a, const float4 &b, float dx, float zx, f32x2 py,
+// two pixel centres of one column, two lanes at a time, from the per-splat
+// terms zxdx = (A dx) dx and bdx = B dx of the column: power = (C dy + bdx)
+// dy + zxdx, dy = py - m_y, each step rounded to nearest in this order,
+// exactly the steps of splat_alpha below (the forward's scalar form), so the
+// two kernels take identical skip and clamp decisions.  A pixel skips the
+// splat unless power >= pcut; then alpha = min(0.99, o 2^power).
+__device__ __forceinline__ f32x2 splat_power2(const float4 &a, const float4 &b, float bdx, float zxdx, f32x2 py,
                                               f32x2 &dy) {
   dy = sub2(py, dup2(a.y));
-  const f32x2 u = fma2(dup2(a.w), dy, dup2(zx));
-  return fma2(u, dup2(dx), mul2(mul2(dup2(b.x), dy), dy));
+  return fma2(fma2(dup2(b.x), dy, dup2(bdx)), dy, dup2(zxdx));
 }
 
 struct Hit {
@@ -163,14 +162,13 @@ struct Hit {
 // alpha of a staged splat at pixel centre (px, py); false if skipped.
 // alpha = min(0.99, o 2^power).  Written with explicit round-to-nearest
 // operations so the forward and the backward decide identically.
-// dx = px - m_x and zx = A dx are shared by the two pixels of a thread
-// (same column), so the caller computes them once per splat.
-__device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, float pcut, float dx, float zx,
-                                            float py, Hit &h) {
+// dx = px - m_x, zxdx = (A dx) dx and bdx = B dx are shared by the pixels of
+// a thread (same column), so the caller computes them once per splat.
+__device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, float pcut, float dx, float bdx,
+                                            float zxdx, float py, Hit &h) {
   h.dx = dx;
   h.dy = __fsub_rn(py, a.y);
-  const float u = __fmaf_rn(a.w, h.dy, zx);
-  const float power = __fmaf_rn(u, h.dx, __fmul_rn(__fmul_rn(b.x, h.dy), h.dy));
+  const float power = __fmaf_rn(__fmaf_rn(b.x, h.dy, bdx), h.dy, zxdx);
   if (!(power >= pcut)) return false;
   h.G = ex2_approx(power);
   const float araw = __fmul_rn(b.y, h.G);

@@ -78,12 +78,12 @@ struct AdjSums {
 // once per splat.  A lane that skips the splat takes alpha 0, which leaves
 // its T and GS unchanged and adds 0 to every sum.  Returns false if both
 // pixels skip.
-__device__ __forceinline__ bool pixel_adjoint2(const float4 &a, const float4 &b, const float4 &c4, float dx, float zx,
+__device__ __forceinline__ bool pixel_adjoint2(const float4 &a, const float4 &b, const float4 &c4, float bdx, float zxdx,
                                                f32x2 py, bool e0, bool e1, f32x2 g0, f32x2 g1, f32x2 g2, float &T0,
                                                float &T1, float &GS0, float &GS1, AdjSums &s) {
   f32x2 dy;
   float p0, p1;
-  unpack2(splat_power2(a, b, dx, zx, py, dy), p0, p1);
+  unpack2(splat_power2(a, b, bdx, zxdx, py, dy), p0, p1);
   const bool ok0 = e0 && p0 >= c4.z, ok1 = e1 && p1 >= c4.z;
   if (!(ok0 || ok1)) return false;
   const float G0 = ex2_approx(p0), G1 = ex2_approx(p1);
@@ -313,7 +313,8 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
           const int j = 32 * k + bit;
           const uint32_t pos = beg + (uint32_t)j;   // 0-based list position
           const float4 a = s_a[j], b = s_b[j], c4 = s_c[j];
-          const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
+          const float dx = __fsub_rn(px, a.x);
+          const float zxdx = __fmul_rn(__fmul_rn(a.z, dx), dx), bdx = __fmul_rn(a.w, dx);
           const f32x2 z2 = dup2(0.f);
           AdjSums sums{z2, z2, z2, z2, z2, z2, z2};
           bool act = false;
@@ -323,7 +324,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
             const bool e0 = pos < nc[h], e1 = pos < nc[h + 1];
             if (!(e0 || e1)) continue;
             if (kCount) evals += (uint32_t)e0 + (uint32_t)e1;
-            act |= pixel_adjoint2(a, b, c4, dx, zx, pack2(pyq[h], pyq[h + 1]), e0, e1, pack2(g0[h], g0[h + 1]),
+            act |= pixel_adjoint2(a, b, c4, bdx, zxdx, pack2(pyq[h], pyq[h + 1]), e0, e1, pack2(g0[h], g0[h + 1]),
                                   pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]), T[h], T[h + 1], GS[h],
                                   GS[h + 1], sums);
           }

@@ -169,14 +169,15 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
             const int j = 32 * k + __ffs(m) - 1;
             m &= m - 1;
             const float4 a = s_a[j], b = s_b[j], c = s_c[j];
-            const float dx = __fsub_rn(px, a.x), zx = __fmul_rn(a.z, dx);
+            const float dx = __fsub_rn(px, a.x);
+            const float zxdx = __fmul_rn(__fmul_rn(a.z, dx), dx), bdx = __fmul_rn(a.w, dx);
             const uint32_t pos1 = (uint32_t)(base - s) + (uint32_t)j + 1u;   // within the tile's list
             if (kCount) evals += __popc(live);   // evaluated at every live pixel of the thread
 #pragma unroll
             for (int q = 0; q < kPx; ++q) {
               if (!((live >> q) & 1u)) continue;
               Hit h;
-              if (splat_alpha(a, b, c.z, dx, zx, py0 + (float)(q * G::kRowStep), h)) {
+              if (splat_alpha(a, b, c.z, dx, bdx, zxdx, py0 + (float)(q * G::kRowStep), h)) {
                 const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, h.alpha));
                 if (Tn < kTMin) {
                   live &= ~(1u << q);
