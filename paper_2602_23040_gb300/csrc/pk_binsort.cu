@@ -637,57 +637,96 @@ __global__ __launch_bounds__(kThreads) void k_radix_upsweep(const uint32_t *__re
   }
 }
 
-// Exclusive scan of hist in [digit][block] order (one block of 1024 threads,
-// coalesced: each pass covers 4096 consecutive counters).  The counters are
+// Exclusive scan of hist in [digit][block] order.  The counters are
 // 64-bit: after the scan they are output positions, and the entries of a
-// launch may pass 2^32.
-__global__ __launch_bounds__(1024) void k_radix_scan(uint64_t *__restrict__ hist, int count) {
+// launch may pass 2^32.  Each block of 1024 threads takes a chunk of 4096
+// consecutive counters: k_radix_chunk_sums writes each chunk's total,
+// k_radix_scan_chunks adds the totals of the chunks before its own (at most
+// a few hundred) and scans its chunk in place -- two short launches instead
+// of one block walking every chunk in turn (63 us a pass at the 52-view
+// rig).  The chunk totals use the binning's block-sum buffer, idle while
+// the radix passes run.
+constexpr int kHistChunk = 4096;
+__global__ __launch_bounds__(1024) void k_radix_chunk_sums(const uint64_t *__restrict__ hist, int count,
+                                                           uint64_t *__restrict__ csum) {
+  __shared__ uint64_t s[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i = blockIdx.x * kHistChunk + 4 * tid;
+  uint64_t t = 0;
+  if (i + 3 < count) {
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(hist + i);
+    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(hist + i + 2);
+    t = a.x + a.y + b.x + b.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t += i + j < count ? hist[i + j] : 0ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) s[warp] = t;
+  __syncthreads();
+  if (warp == 0) {
+    t = s[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) csum[blockIdx.x] = t;
+  }
+}
+
+__global__ __launch_bounds__(1024) void k_radix_scan_chunks(uint64_t *__restrict__ hist, int count,
+                                                            const uint64_t *__restrict__ csum) {
   __shared__ uint64_t s[33];
   __shared__ uint64_t s_carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_carry = 0;
+  const int b = blockIdx.x;
+  // counters of the chunks before this one
+  uint64_t c = 0;
+  for (int k = tid; k < b; k += 1024) c += csum[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) s[warp] = c;
   __syncthreads();
-  for (int base = 0; base < count; base += 4096) {
-    const int i = base + 4 * tid;
-    uint64_t q[4];
-    if (i + 3 < count) {
-      const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(hist + i);
-      const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(hist + i + 2);
-      q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y;
-    } else {
+  if (warp == 0) {
+    c = s[lane];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) q[j] = i + j < count ? hist[i + j] : 0ull;
-    }
-    const uint64_t sum = q[0] + q[1] + q[2] + q[3];
-    const uint64_t incl = warp_incl_scan(sum);
-    if (lane == 31) s[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const uint64_t w = s[lane];
-      const uint64_t wi = warp_incl_scan(w);
-      s[lane] = wi - w;
-      if (lane == 31) s[32] = wi;
-    }
-    __syncthreads();
-    const uint64_t carry = s_carry;
-    uint64_t e = carry + s[warp] + incl - sum;
-    uint64_t o[4];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) s_carry = c;
+  }
+  __syncthreads();
+  const int i = b * kHistChunk + 4 * tid;
+  uint64_t q[4];
+  if (i + 3 < count) {
+    const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(hist + i);
+    const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(hist + i + 2);
+    q[0] = x.x; q[1] = x.y; q[2] = y.x; q[3] = y.y;
+  } else {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      o[j] = e;
-      e += q[j];
-    }
-    if (i + 3 < count) {
-      *reinterpret_cast<ulonglong2 *>(hist + i) = make_ulonglong2(o[0], o[1]);
-      *reinterpret_cast<ulonglong2 *>(hist + i + 2) = make_ulonglong2(o[2], o[3]);
-    } else {
+    for (int j = 0; j < 4; ++j) q[j] = i + j < count ? hist[i + j] : 0ull;
+  }
+  const uint64_t sum = q[0] + q[1] + q[2] + q[3];
+  const uint64_t incl = warp_incl_scan(sum);
+  if (lane == 31) s[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint64_t w = s[lane];
+    const uint64_t wi = warp_incl_scan(w);
+    s[lane] = wi - w;
+  }
+  __syncthreads();
+  uint64_t e = s_carry + s[warp] + incl - sum;
+  uint64_t o[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (i + j < count) hist[i + j] = o[j];
-    }
-    __syncthreads();
-    if (tid == 0) s_carry = carry + s[32];
-    __syncthreads();
+  for (int j = 0; j < 4; ++j) {
+    o[j] = e;
+    e += q[j];
+  }
+  if (i + 3 < count) {
+    *reinterpret_cast<ulonglong2 *>(hist + i) = make_ulonglong2(o[0], o[1]);
+    *reinterpret_cast<ulonglong2 *>(hist + i + 2) = make_ulonglong2(o[2], o[3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (i + j < count) hist[i + j] = o[j];
   }
 }
 
@@ -1181,15 +1220,17 @@ __global__ __launch_bounds__(kThreads) void k_view_segments(const uint32_t *__re
 template <int RB, int IT, int kMode>
 pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                         const uint64_t *n_dev, uint64_t n_host, int shift, int bits, uint64_t *hist, int nblocks,
-                        pk_device_status *status, SegSpec sp, uint32_t *abort_flag, uint32_t first_polls,
-                        bool try_single, const Unpack &up, cudaStream_t st) {
+                        uint64_t *csum, pk_device_status *status, SegSpec sp, uint32_t *abort_flag,
+                        uint32_t first_polls, bool try_single, const Unpack &up, cudaStream_t st) {
   using C = Radix<RB, IT>;
   if (cudaFuncSetAttribute(k_radix_downsweep<RB, IT, kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)Down<RB, IT>::kSmem) != cudaSuccess)
     return PK_ERR_CUDA;
   const uint32_t mask = (1u << bits) - 1u;
   k_radix_upsweep<RB, IT><<<nblocks, kThreads, 0, st>>>(kin, n_dev, n_host, shift, mask, hist, sp);
-  k_radix_scan<<<1, 1024, 0, st>>>(hist, C::kR * nblocks);
+  const int count = C::kR * nblocks, nchunks = (count + kHistChunk - 1) / kHistChunk;
+  k_radix_chunk_sums<<<nchunks, 1024, 0, st>>>(hist, count, csum);
+  k_radix_scan_chunks<<<nchunks, 1024, 0, st>>>(hist, count, csum);
   k_radix_downsweep<RB, IT, kMode><<<nblocks, kThreads, Down<RB, IT>::kSmem, st>>>(
       kin, vin, kout, vout, n_dev, n_host, shift, mask, hist, status, sp, abort_flag, first_polls, try_single, up);
   return check_launch();
@@ -1203,11 +1244,12 @@ pk_status radix_pass_rb(const uint32_t *kin, const uint32_t *vin, uint32_t *kout
 // packed entries, keys only; then up.ranges != nullptr marks the last pass.
 pk_status radix_pass(bool entries, int rb, const uint32_t *kin, const uint32_t *vin, uint32_t *kout, uint32_t *vout,
                      const uint64_t *n_dev, uint64_t n_host, int shift, int bits, uint64_t *hist, int nblocks,
-                     pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls, bool try_single,
-                     cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr}, Unpack up = Unpack{}) {
+                     uint64_t *csum, pk_device_status *status, uint32_t *abort_flag, uint32_t first_polls,
+                     bool try_single, cudaStream_t st, SegSpec sp = SegSpec{nullptr, nullptr},
+                     Unpack up = Unpack{}) {
 #define PK_PASS(RB, IT, M)                                                                                        \
-  return radix_pass_rb<RB, IT, M>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, status, sp,  \
-                                  abort_flag, first_polls, try_single, up, st)
+  return radix_pass_rb<RB, IT, M>(kin, vin, kout, vout, n_dev, n_host, shift, bits, hist, nblocks, csum, status, \
+                                  sp, abort_flag, first_polls, try_single, up, st)
   if (entries) {
     if (!vin && up.ranges) {
       if (rb > 8) PK_PASS(11, kEntryItems, 2);
@@ -1367,8 +1409,8 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
   for (int pass = 0; pass < np; ++pass) {
     const int a = pass & 1, b = a ^ 1;
     if ((e = radix_pass(false, rd, zk[a], pv[a], zk[b], pv[b], n_valid, 0, shift, widths[pass], hist,
-                        seg ? npseg : pair_blocks(rd), status, &ctr->sort_abort, p->first_polls, pass == np - 1, st,
-                        psp)) != PK_OK)
+                        seg ? npseg : pair_blocks(rd), bsum, status, &ctr->sort_abort, p->first_polls,
+                        pass == np - 1, st, psp)) != PK_OK)
       return e;
     shift += widths[pass];
   }
@@ -1418,11 +1460,11 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
     shift -= widths[pass];
     if (packed)
       e = radix_pass(true, rt, kbuf[a], nullptr, last ? nullptr : kbuf[b], last ? sorted_vals : nullptr, &ctr->dups,
-                     0, shift, widths[pass], hist, nblocks, status, &ctr->sort_abort, p->first_polls, false, st, sp,
-                     last ? up : Unpack{});
+                     0, shift, widths[pass], hist, nblocks, bsum, status, &ctr->sort_abort, p->first_polls, false,
+                     st, sp, last ? up : Unpack{});
     else
       e = radix_pass(true, rt, kbuf[a], vbuf[a], kbuf[b], vbuf[b], &ctr->dups, 0, shift, widths[pass], hist, nblocks,
-                     status, &ctr->sort_abort, p->first_polls, false, st, sp);
+                     bsum, status, &ctr->sort_abort, p->first_polls, false, st, sp);
     if (e != PK_OK) return e;
   }
   if (packed)
@@ -1438,7 +1480,7 @@ pk_status bin_and_sort_impl(const pk_plan *p, const WsLayout &L, void *ws, const
 
 // Mirrors the launches of bin_and_sort_impl: zeroing, count, scan (2),
 // compaction, [pair segments], the depth passes, offsets (3), [entry
-// segments], emission, the tile passes, ranges; 3 kernels per radix pass.
+// segments], emission, the tile passes, ranges; 4 kernels per radix pass.
 int pk::bin_kernel_count(const pk_plan *p) {
   if (!p) return 0;
   if (p->pairs == 0) return 1;
@@ -1450,7 +1492,7 @@ int pk::bin_kernel_count(const pk_plan *p) {
   int kernels = 1 + 4 + 3 + 1 + 1;
   if (seg) kernels += 2;   // the pairs' and the entries' view segments
   passes += radix_plan(seg ? local_tile_bits(p) : p->tile_bits, p->opts.sort_bits_tile, widths);
-  return kernels + 3 * passes;
+  return kernels + 4 * passes;
 }
 
 extern "C" pk_status pk_bin_and_sort(const pk_plan *p, const float *records, uint32_t *sorted_vals,
