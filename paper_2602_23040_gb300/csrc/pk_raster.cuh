@@ -62,7 +62,7 @@ __device__ __forceinline__ int view_of_tile(const uint32_t *__restrict__ toff, i
 
 struct Staged {
   float4 *a;     // m_x, m_y, A = k conic_a, B = 2 k conic_b      (k = -log2(e) / 2)
-  float4 *b;     // C = k conic_c, opacity, red, green
+  float4 *b;     // C = k conic_c, -opacity, red, green
   float4 *c;     // blue, pair index (bits), pcut, 0
   float4 *box;   // conservative pixel-centre box of the contributing ellipse
   float4 *q;     // conic_a, conic_b, conic_c, qlim = min(9, 2 ln(255 o)) for the block test
@@ -99,7 +99,7 @@ __device__ __forceinline__ void stage_from(const float4 r0, const float4 r1, con
                                            const Staged &s, int j) {
   const float ca = r0.z, cb = r0.w, cc = r1.x, o = r1.y;
   s.a[j] = make_float4(r0.x, r0.y, __fmul_rn(kExpScale, ca), __fmul_rn(2.f * kExpScale, cb));
-  s.b[j] = make_float4(__fmul_rn(kExpScale, cc), o, r2.x, r2.y);
+  s.b[j] = make_float4(__fmul_rn(kExpScale, cc), -o, r2.x, r2.y);
   const float pcut = fmaxf(9.f * kExpScale, -__log2f(255.f * o));
   s.c[j] = make_float4(r2.z, __uint_as_float(pid), pcut, 0.f);
   const float qlim = fminf(kQMax, 2.f * __logf(255.f * o));
@@ -171,7 +171,7 @@ __device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, fl
   const float power = __fmaf_rn(__fmaf_rn(b.x, h.dy, bdx), h.dy, zxdx);
   if (!(power >= pcut)) return false;
   h.G = ex2_approx(power);
-  const float araw = __fmul_rn(b.y, h.G);
+  const float araw = __fmul_rn(-b.y, h.G);
   h.clamped = araw > kAlphaMax;
   h.alpha = h.clamped ? kAlphaMax : araw;
   return true;

@@ -75,52 +75,62 @@ struct AdjSums {
 // opacity gradients go to the sums a5..a8.  The conic and mean gradients
 // are linear in dq = dL/dq, so a pixel only adds dq, dq dy and dq dy^2 to
 // q1, qy, qyy (dx is common to a thread's pixels) and the caller forms them
-// once per splat.  A lane that skips the splat takes alpha 0, which leaves
-// its T and GS unchanged and adds 0 to every sum.  Returns false if both
-// pixels skip.
+// once per splat.  A pixel that skips the splat (or is past its last
+// blended entry: e false) takes alpha 0, which leaves its T and GS
+// unchanged and adds 0 to every sum, so the pair runs without a branch.
+// GS is kept negated (NGS = -dL/dC . S) and alpha as nal = -alpha (the
+// staged opacity is negated), which turns dL/dalpha into one fused
+// multiply-add.  kFirst: this pair starts the sums instead of adding to
+// them.  Returns false if both pixels skip.
+template <bool kFirst>
 __device__ __forceinline__ bool pixel_adjoint2(const float4 &a, const float4 &b, const float4 &c4, float bdx, float zxdx,
                                                f32x2 py, bool e0, bool e1, f32x2 g0, f32x2 g1, f32x2 g2, float &T0,
-                                               float &T1, float &GS0, float &GS1, AdjSums &s) {
+                                               float &T1, float &NGS0, float &NGS1, AdjSums &s) {
   f32x2 dy;
   float p0, p1;
   unpack2(splat_power2(a, b, bdx, zxdx, py, dy), p0, p1);
   const bool ok0 = e0 && p0 >= c4.z, ok1 = e1 && p1 >= c4.z;
-  if (!(ok0 || ok1)) return false;
+  // a pixel that skips has power < pcut <= 0 (the conic is positive
+  // definite), so G stays finite and its zero alpha zeroes every product
   const float G0 = ex2_approx(p0), G1 = ex2_approx(p1);
+  // 1 + nal, nal Ti and the sums below are exactly the negations of the
+  // alpha forms
   float r0, r1;
   unpack2(mul2(dup2(b.y), pack2(G0, G1)), r0, r1);
-  const bool cl0 = r0 > kAlphaMax, cl1 = r1 > kAlphaMax;
-  const float al0 = ok0 ? (cl0 ? kAlphaMax : r0) : 0.f;
-  const float al1 = ok1 ? (cl1 ? kAlphaMax : r1) : 0.f;
-  const f32x2 al = pack2(al0, al1);
+  const bool cl0 = r0 < -kAlphaMax, cl1 = r1 < -kAlphaMax;
+  const float nal0 = ok0 ? (cl0 ? -kAlphaMax : r0) : 0.f;
+  const float nal1 = ok1 ? (cl1 ? -kAlphaMax : r1) : 0.f;
+  const f32x2 nal = pack2(nal0, nal1);
   float om0, om1;
-  unpack2(sub2(dup2(1.f), al), om0, om1);
+  unpack2(add2(dup2(1.f), nal), om0, om1);
   const f32x2 inv = pack2(rcp_approx(om0), rcp_approx(om1));
   const f32x2 Tv = pack2(T0, T1);
   float ti0, ti1;
   const f32x2 Ti = mul2(Tv, inv);
   unpack2(Ti, ti0, ti1);
-  const f32x2 wT = mul2(al, Ti);
-  // dL/dalpha = (T g.rgb - g.S) / (1 - alpha)
+  const f32x2 nwT = mul2(nal, Ti);
+  // dL/dalpha = (T g.rgb - g.S) / (1 - alpha), with NGS = -g.S
   const f32x2 gr = fma2(g2, dup2(c4.x), fma2(g1, dup2(b.w), mul2(g0, dup2(b.z))));
-  const f32x2 GSv = pack2(GS0, GS1);
+  const f32x2 NGSv = pack2(NGS0, NGS1);
   float da0, da1;
-  unpack2(mul2(sub2(mul2(Tv, gr), GSv), inv), da0, da1);
-  unpack2(fma2(wT, gr, GSv), GS0, GS1);
-  if (ok0) T0 = ti0;
-  if (ok1) T1 = ti1;
-  s.a6 = fma2(wT, g0, s.a6);
-  s.a7 = fma2(wT, g1, s.a7);
-  s.a8 = fma2(wT, g2, s.a8);
+  unpack2(mul2(fma2(Tv, gr, NGSv), inv), da0, da1);
+  unpack2(fma2(nwT, gr, NGSv), NGS0, NGS1);
+  // a skipping pixel has alpha 0: 1 / (1 - 0) = 1 exactly, T stays
+  T0 = ti0;
+  T1 = ti1;
+  // the first pair of a thread starts the sums, the others add to them
+  s.a6 = kFirst ? mul2(nwT, g0) : fma2(nwT, g0, s.a6);
+  s.a7 = kFirst ? mul2(nwT, g1) : fma2(nwT, g1, s.a7);
+  s.a8 = kFirst ? mul2(nwT, g2) : fma2(nwT, g2, s.a8);
   // alpha = o 2^power, power = k q: dL/dq = -alpha dL/dalpha / 2 (unclamped pixels only)
   const f32x2 dav = pack2(ok0 && !cl0 ? da0 : 0.f, ok1 && !cl1 ? da1 : 0.f);
-  s.a5 = fma2(dav, pack2(G0, G1), s.a5);
-  const f32x2 dq = mul2(mul2(dup2(-0.5f), al), dav);
+  s.a5 = kFirst ? mul2(dav, pack2(G0, G1)) : fma2(dav, pack2(G0, G1), s.a5);
+  const f32x2 dq = mul2(mul2(dup2(0.5f), nal), dav);
   const f32x2 t = mul2(dq, dy);
-  s.q1 = add2(s.q1, dq);
-  s.qy = add2(s.qy, t);
-  s.qyy = fma2(t, dy, s.qyy);
-  return true;
+  s.q1 = kFirst ? dq : add2(s.q1, dq);
+  s.qy = kFirst ? t : add2(s.qy, t);
+  s.qyy = kFirst ? mul2(t, dy) : fma2(t, dy, s.qyy);
+  return ok0 || ok1;
 }
 
 __device__ __forceinline__ float lane_sum(f32x2 v) {
@@ -145,10 +155,9 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // kTma: the records of the next (earlier) batch are fetched into shared
 // memory by bulk copies (one 48-byte copy per splat, completed on an
 // mbarrier) while the current batch is processed.  kPx: pixels per thread.
-// At 4 pixels per thread the kernel is held to 72 registers (8 bytes
-// spilled) for 14 resident CTAs per SM: with the packed pixel pairs, 64
-// registers spill in the splat loop (9.07 ms at the 52-view rig) and 80
-// leave 12 CTAs (9.31 ms) against 8.78 ms.
+// At 4 pixels per thread the kernel is held to 72 registers (no spills) for
+// 14 resident CTAs per SM: with the packed pixel pairs, 64 registers spill
+// in the splat loop and 80 leave 12 CTAs, both slower.
 // kT: side of the tiles the lists were binned for; each CTA takes a 16 x 16
 // quadrant of one, as in the forward.  kCount: count the evaluations (a
 // measurement; the variant without it carries no counter in its loop).
@@ -223,7 +232,7 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
     const uint64_t s = __ldg(ranges + 2 * (size_t)t);
     const uint32_t len = (uint32_t)(__ldg(ranges + 2 * (size_t)t + 1) - s);
     const size_t plane = (size_t)W * H;
-    float T[kPx], GS[kPx], g0[kPx], g1[kPx], g2[kPx], pyq[kPx];
+    float T[kPx], NGS[kPx], g0[kPx], g1[kPx], g2[kPx], pyq[kPx];
     uint32_t nc[kPx];
     uint32_t ncmax = 0;
 #pragma unroll
@@ -244,8 +253,8 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
         g1[q] = gi[plane];
         g2[q] = gi[2 * plane];
       }
-      // dL/dC . (colour composited behind the current splat, background included)
-      GS[q] = T[q] * fmaf(g2[q], bg2, fmaf(g1[q], bg1, g0[q] * bg0));
+      // -dL/dC . (colour composited behind the current splat, background included)
+      NGS[q] = -(T[q] * fmaf(g2[q], bg2, fmaf(g1[q], bg1, g0[q] * bg0)));
       ncmax = max(ncmax, nc[q]);
     }
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, ncmax);
@@ -259,6 +268,19 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
       if (tid == 0) mbar_expect_tx(&s_bar, (tmax - b0) * 3u * (uint32_t)sizeof(float4));
       __syncthreads();
       fetch(s + b0, (int)(tmax - b0));
+    }
+    // plain loads: each thread's list entries of the next (earlier) batch
+    // are read a batch ahead, so staging waits for one load (the record)
+    // instead of two
+    constexpr int kPer = (kBatch + G::kThreads - 1) / G::kThreads;
+    uint32_t npid[kPer];
+    if (!kTma) {
+      const uint32_t b0 = tmax > (uint32_t)kBatch ? tmax - kBatch : 0u;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int j = tid + u * G::kThreads;
+        npid[u] = j < kBatch && b0 + (uint32_t)j < tmax ? __ldg(vals + s + b0 + j) : 0u;
+      }
     }
     for (uint32_t end = tmax; end > 0;) {
       const uint32_t beg = end > (uint32_t)kBatch ? end - kBatch : 0u;
@@ -291,8 +313,16 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
       } else {
         __syncthreads();
 #pragma unroll
-        for (int j = tid; j < kBatch; j += G::kThreads)
-          if (j < nb) stage_splat(rec, __ldg(vals + s + beg + j), npairs, st, j, status);
+        for (int u = 0; u < kPer; ++u) {
+          const int j = tid + u * G::kThreads;
+          if (j < nb) stage_splat(rec, npid[u], npairs, st, j, status);
+        }
+        const uint32_t nbeg = beg > (uint32_t)kBatch ? beg - kBatch : 0u;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int j = tid + u * G::kThreads;
+          npid[u] = j < kBatch && nbeg + (uint32_t)j < beg ? __ldg(vals + s + nbeg + j) : 0u;
+        }
         __syncthreads();
       }
       // splats that can reach this warp's block and that some pixel of the
@@ -315,25 +345,29 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
           const float4 a = s_a[j], b = s_b[j], c4 = s_c[j];
           const float dx = __fsub_rn(px, a.x);
           const float zxdx = __fmul_rn(__fmul_rn(a.z, dx), dx), bdx = __fmul_rn(a.w, dx);
-          const f32x2 z2 = dup2(0.f);
-          AdjSums sums{z2, z2, z2, z2, z2, z2, z2};
+          AdjSums sums;   // started by the first pair
           bool act = false;
 #pragma unroll
           for (int h = 0; h < kPx; h += 2) {
             // the pixels blended or skipped this splat in the forward
             const bool e0 = pos < nc[h], e1 = pos < nc[h + 1];
-            if (!(e0 || e1)) continue;
             if (kCount) evals += (uint32_t)e0 + (uint32_t)e1;
-            act |= pixel_adjoint2(a, b, c4, bdx, zxdx, pack2(pyq[h], pyq[h + 1]), e0, e1, pack2(g0[h], g0[h + 1]),
-                                  pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]), T[h], T[h + 1], GS[h],
-                                  GS[h + 1], sums);
+            if (h == 0) {
+              act = pixel_adjoint2<true>(a, b, c4, bdx, zxdx, pack2(pyq[h], pyq[h + 1]), e0, e1,
+                                         pack2(g0[h], g0[h + 1]), pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]),
+                                         T[h], T[h + 1], NGS[h], NGS[h + 1], sums);
+            } else {
+              act |= pixel_adjoint2<false>(a, b, c4, bdx, zxdx, pack2(pyq[h], pyq[h + 1]), e0, e1,
+                                           pack2(g0[h], g0[h + 1]), pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]),
+                                           T[h], T[h + 1], NGS[h], NGS[h + 1], sums);
+            }
           }
           if (__any_sync(0xffffffffu, act)) {
             float acc[9];
             acc[5] = lane_sum(sums.a5);
-            acc[6] = lane_sum(sums.a6);
-            acc[7] = lane_sum(sums.a7);
-            acc[8] = lane_sum(sums.a8);
+            acc[6] = -lane_sum(sums.a6);   // the colour sums hold -alpha T dL/dC
+            acc[7] = -lane_sum(sums.a7);
+            acc[8] = -lane_sum(sums.a8);
             conic_mean_grads(a, b, dx, lane_sum(sums.q1), lane_sum(sums.qy), lane_sum(sums.qyy), acc);
             const float sum = warp_reduce_scatter9(acc, lane);
             if (my_idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + my_idx, sum);

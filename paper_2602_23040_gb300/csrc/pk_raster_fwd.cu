@@ -113,6 +113,17 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
       fetch(s, (int)min((uint64_t)kBatch, e - s));
       pending = true;
     }
+    // plain loads: each thread's list entries of the next batch are read a
+    // batch ahead, so staging waits for one load (the record) instead of two
+    constexpr int kPer = (kBatch + G::kThreads - 1) / G::kThreads;
+    uint32_t npid[kPer];
+    if (!kTma) {
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int j = tid + u * G::kThreads;
+        npid[u] = j < kBatch && s + j < e ? __ldg(vals + s + j) : 0u;
+      }
+    }
     for (uint64_t base = s; base < e; base += kBatch) {
       const int nb = (int)min((uint64_t)kBatch, e - base);
       if (kTma) {
@@ -147,8 +158,16 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
       } else {
         __syncthreads();
 #pragma unroll
-        for (int j = tid; j < kBatch; j += G::kThreads)
-          if (j < nb) stage_splat(rec, __ldg(vals + base + j), npairs, st, j, status);
+        for (int u = 0; u < kPer; ++u) {
+          const int j = tid + u * G::kThreads;
+          if (j < nb) stage_splat(rec, npid[u], npairs, st, j, status);
+        }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const int j = tid + u * G::kThreads;
+          const uint64_t nx = base + kBatch + (uint64_t)j;
+          npid[u] = j < kBatch && nx < e ? __ldg(vals + nx) : 0u;
+        }
         __syncthreads();
       }
       if (__any_sync(0xffffffffu, live != 0)) {
