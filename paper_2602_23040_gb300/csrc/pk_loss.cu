@@ -53,7 +53,8 @@ extern "C" pk_status pk_l1_loss_grad(const pk_plan *p, const float *image, const
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   // loss_acc, ssim_acc and ssim_lambda (0: the loss is L1 alone)
-  if (cudaMemsetAsync(&ctr->loss_acc, 0, 2 * sizeof(double) + sizeof(float), st) != cudaSuccess) return PK_ERR_CUDA;
+  pk_status ze = zero_async({{&ctr->loss_acc, 2 * sizeof(double) + sizeof(float)}}, st);
+  if (ze != PK_OK) return ze;
   const int64_t n = 3 * p->P;
   if (n == 0) return PK_OK;
   int64_t blocks = (n / 4 + 255) / 256;

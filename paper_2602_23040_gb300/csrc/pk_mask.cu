@@ -280,9 +280,10 @@ extern "C" pk_status pk_dynamic_mask(const pk_plan *p, const float *records, con
   if (!aligned16(records)) return PK_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int aw = p->desc.atlas_w, ah = p->desc.atlas_h;
-  if (!accumulate &&
-      cudaMemsetAsync(dyn, 0, sizeof(uint32_t) * (size_t)ah * (size_t)((aw + 31) / 32), st) != cudaSuccess)
-    return PK_ERR_CUDA;
+  if (!accumulate) {
+    const pk_status ze = zero_async({{dyn, sizeof(uint32_t) * (size_t)ah * (size_t)((aw + 31) / 32)}}, st);
+    if (ze != PK_OK) return ze;
+  }
   if (p->N == 0) return PK_OK;
   const DevView *views = at<DevView>(ws, p->ws.views);
   uint32_t *coarse = at<uint32_t>(ws, p->ws.mask_coarse);

@@ -310,7 +310,8 @@ extern "C" pk_status pk_photo_loss_grad(const pk_plan *p, const float *image, co
     g_weights_set[dev] = true;
   }
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
-  if (cudaMemsetAsync(&ctr->loss_acc, 0, 2 * sizeof(double) + sizeof(float), st) != cudaSuccess) return PK_ERR_CUDA;
+  pk_status ze = zero_async({{&ctr->loss_acc, 2 * sizeof(double) + sizeof(float)}}, st);
+  if (ze != PK_OK) return ze;
   int maxw = 1, maxh = 1;
   for (int v = 0; v < p->V; ++v) {
     maxw = max(maxw, p->h_views[v].width);

@@ -198,7 +198,8 @@ extern "C" pk_status pk_uv_max_k(const float *soa, int64_t n, int64_t stride, in
   const UvScratch L = uv_layout(n, cells);
   uint32_t *slot = at<uint32_t>(scratch, L.slot), *offs = at<uint32_t>(scratch, L.offs);
   uint32_t *bsum = at<uint32_t>(scratch, L.bsum), *bucket = at<uint32_t>(scratch, L.bucket);
-  if (cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)cells, st) != cudaSuccess) return PK_ERR_CUDA;
+  pk_status ze = zero_async({{count, sizeof(uint32_t) * (size_t)cells}}, st);
+  if (ze != PK_OK) return ze;
   if (n == 0) return PK_OK;
   const unsigned gn = (unsigned)((n + kUvThreads - 1) / kUvThreads);
   const int64_t blocks = (cells + kUvScanItems - 1) / kUvScanItems;
