@@ -3,10 +3,10 @@
 // T_i = T_{i+1} / (1 - alpha_i) from the stored final transmittance, so no
 // per-step state of the forward is kept.  Each thread holds four pixels
 // (two packed pairs); per splat the 9 gradients of a warp's 128 pixels are
-// summed by a reduce-scatter over the lanes (12 shuffles instead of 45 for
-// nine full butterfly sums), after which nine
-// lanes each hold one complete sum and add it to the splat's gradient
-// record with one coalesced atomic instruction.
+// summed over the lanes (eight by a reduce-scatter, the ninth by a
+// butterfly: 14 shuffles instead of 45 for nine full butterfly sums),
+// after which nine lanes each hold one complete sum and add it to the
+// splat's gradient record with one coalesced atomic instruction.
 #include "pk_raster.cuh"
 #include "pk_tma.cuh"
 
@@ -14,50 +14,46 @@ using namespace pk;
 
 namespace {
 
-// Index of the value a lane holds after warp_reduce_scatter9 (-1: padding).
-// Level sets [0..4 | 5..8], then slots [0,1,2 | 3,4], [0,1 | 2], [0 | 1].
-__device__ __forceinline__ int reduce_scatter9_index(int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  const int s2 = b2 ? (b1 ? -1 : 2) : (b1 ? 1 : 0);                  // slot in x
-  const int s3 = s2 < 0 ? -1 : (b3 ? (s2 < 2 ? 3 + s2 : -1) : s2);    // slot in w
-  const int s4 = s3 < 0 ? -1 : (b4 ? (s3 < 4 ? 5 + s3 : -1) : s3);    // value index
-  return (lane & 1) ? -1 : s4;
+// Sum over the 32 lanes of nine values per lane, eight of them by a
+// reduce-scatter and the ninth by a plain butterfly: xor-16 splits v[0..7]
+// 4 | 4, xor-8 each half 2 | 2, xor-4 1 | 1 (one select pair, shuffle and
+// add per value and level), then xor-2 and xor-1 add the last value
+// outright.  Lane l then holds the complete sum of v[4 (l & 16) / 16 + 2
+// (l & 8) / 8 + (l & 4) / 4] in *s8 and every lane the sum of v[8] in *s9
+// -- 9 + 5 shuffles and 14 selects, against 12 shuffles and 24 selects for
+// a reduce-scatter of all nine.
+__device__ __forceinline__ int reduce_scatter8_index(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-// Reduce-scatter of v[0..8] over the 32 lanes.  Level xor-16 splits the
-// nine values 5 | 4, xor-8 splits each half 3 | 2, xor-4 2 | 1, xor-2 1 | 1
-// and xor-1 adds the last pair.  Returns the complete sum of value
-// reduce_scatter9_index(lane) held by this lane.
-__device__ __forceinline__ float warp_reduce_scatter9(const float (&v)[9], int lane) {
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  float w[5];
+__device__ __forceinline__ void warp_reduce_9(const float (&v)[9], int lane, float &s8, float &s9) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float w[4];
 #pragma unroll
-  for (int j = 0; j < 5; ++j) {
-    const float lo = v[j], hi = (5 + j < 9) ? v[5 + j] : 0.f;
+  for (int j = 0; j < 4; ++j) {
+    const float lo = v[j], hi = v[4 + j];
     const float r = __shfl_xor_sync(0xffffffffu, b4 ? lo : hi, 16);
     w[j] = (b4 ? hi : lo) + r;
   }
-  float x[3];
+  float x[2];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const float lo = w[j], hi = (3 + j < 5) ? w[3 + j] : 0.f;
+  for (int j = 0; j < 2; ++j) {
+    const float lo = w[j], hi = w[2 + j];
     const float r = __shfl_xor_sync(0xffffffffu, b3 ? lo : hi, 8);
     x[j] = (b3 ? hi : lo) + r;
   }
-  float y[2];
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const float lo = x[j], hi = (2 + j < 3) ? x[2 + j] : 0.f;
-    const float r = __shfl_xor_sync(0xffffffffu, b2 ? lo : hi, 4);
-    y[j] = (b2 ? hi : lo) + r;
-  }
   float z;
   {
-    const float r = __shfl_xor_sync(0xffffffffu, b1 ? y[0] : y[1], 2);
-    z = (b1 ? y[1] : y[0]) + r;
+    const float r = __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
+    z = (b2 ? x[1] : x[0]) + r;
   }
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
   z += __shfl_xor_sync(0xffffffffu, z, 1);
-  return z;
+  s8 = z;
+  float t = v[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  s9 = t;
 }
 
 // Per-splat sums of a thread's pixels, kept as two packed lanes (the two
@@ -181,7 +177,9 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
   const Staged st{s_a, s_b, s_c, s_box, s_q};
   int ox, oy, bx, by;
   pixel_of<kPx>(tid, ox, oy, bx, by);
-  const int my_idx = reduce_scatter9_index(lane);
+  // the lane that adds each of the nine sums: lanes 0, 4, ..., 28 the
+  // scattered eight, lane 1 the ninth (-1: none)
+  const int my_idx = (lane & 3) == 0 ? reduce_scatter8_index(lane) : (lane == 1 ? 8 : -1);
   uint32_t evals = 0;   // per thread: far below 2^32
   uint32_t phase = 0;
   bool timed_out = false;
@@ -369,8 +367,9 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
             acc[7] = -lane_sum(sums.a7);
             acc[8] = -lane_sum(sums.a8);
             conic_mean_grads(a, b, dx, lane_sum(sums.q1), lane_sum(sums.qy), lane_sum(sums.qyy), acc);
-            const float sum = warp_reduce_scatter9(acc, lane);
-            if (my_idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + my_idx, sum);
+            float s8, s9;
+            warp_reduce_9(acc, lane, s8, s9);
+            if (my_idx >= 0) atomicAdd(grad2d + (size_t)__float_as_uint(c4.y) * kG2d + my_idx, lane == 1 ? s9 : s8);
           }
         }
       }
