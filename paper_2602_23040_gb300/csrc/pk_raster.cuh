@@ -145,7 +145,7 @@ __device__ __forceinline__ void stage_splat(const float *__restrict__ rec, uint3
 // two pixel centres of one column, two lanes at a time, from the per-splat
 // terms zxdx = (A dx) dx and bdx = B dx of the column: power = (C dy + bdx)
 // dy + zxdx, dy = py - m_y, each step rounded to nearest in this order,
-// exactly the steps of splat_alpha below (the forward's scalar form), so the
+// exactly the steps of splat_power below (the forward's scalar form), so the
 // two kernels take identical skip and clamp decisions.  A pixel skips the
 // splat unless power >= pcut; then alpha = min(0.99, o 2^power).
 __device__ __forceinline__ f32x2 splat_power2(const float4 &a, const float4 &b, float bdx, float zxdx, f32x2 py,
@@ -154,27 +154,12 @@ __device__ __forceinline__ f32x2 splat_power2(const float4 &a, const float4 &b, 
   return fma2(fma2(dup2(b.x), dy, dup2(bdx)), dy, dup2(zxdx));
 }
 
-struct Hit {
-  float alpha, G, dx, dy;
-  bool clamped;
-};
-
-// alpha of a staged splat at pixel centre (px, py); false if skipped.
-// alpha = min(0.99, o 2^power).  Written with explicit round-to-nearest
-// operations so the forward and the backward decide identically.
-// dx = px - m_x, zxdx = (A dx) dx and bdx = B dx are shared by the pixels of
-// a thread (same column), so the caller computes them once per splat.
-__device__ __forceinline__ bool splat_alpha(const float4 &a, const float4 &b, float pcut, float dx, float bdx,
-                                            float zxdx, float py, Hit &h) {
-  h.dx = dx;
-  h.dy = __fsub_rn(py, a.y);
-  const float power = __fmaf_rn(__fmaf_rn(b.x, h.dy, bdx), h.dy, zxdx);
-  if (!(power >= pcut)) return false;
-  h.G = ex2_approx(power);
-  const float araw = __fmul_rn(-b.y, h.G);
-  h.clamped = araw > kAlphaMax;
-  h.alpha = h.clamped ? kAlphaMax : araw;
-  return true;
+// The same exponent at one pixel centre (the forward's scalar form): the
+// steps and rounding of splat_power2, so the two kernels take identical
+// skip and clamp decisions.
+__device__ __forceinline__ float splat_power(const float4 &a, const float4 &b, float bdx, float zxdx, float py) {
+  const float dy = __fsub_rn(py, a.y);
+  return __fmaf_rn(__fmaf_rn(b.x, dy, bdx), dy, zxdx);
 }
 
 __device__ __forceinline__ bool box_misses(const float4 &box, float x0, float x1, float y0, float y1) {

@@ -86,8 +86,8 @@ __device__ __forceinline__ bool pixel_adjoint2(const float4 &a, const float4 &b,
   float p0, p1;
   unpack2(splat_power2(a, b, bdx, zxdx, py, dy), p0, p1);
   const bool ok0 = e0 && p0 >= c4.z, ok1 = e1 && p1 >= c4.z;
-  // a pixel that skips has power < pcut <= 0 (the conic is positive
-  // definite), so G stays finite and its zero alpha zeroes every product
+  // power <= 0 for the positive-definite conics of pk_project_and_sh: G in
+  // [0, 1] at every pixel, and a skipping pixel's zero alpha zeroes its terms
   const float G0 = ex2_approx(p0), G1 = ex2_approx(p1);
   // 1 + nal, nal Ti and the sums below are exactly the negations of the
   // alpha forms

@@ -194,14 +194,17 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
             if (kCount) evals += __popc(live);   // evaluated at every live pixel of the thread
 #pragma unroll
             for (int q = 0; q < kPx; ++q) {
-              if (!((live >> q) & 1u)) continue;
-              Hit h;
-              if (splat_alpha(a, b, c.z, dx, bdx, zxdx, py0 + (float)(q * G::kRowStep), h)) {
-                const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, h.alpha));
+              // one test per pixel: still compositing, and power >= pcut (both
+              // q <= 9 and alpha >= 1/255); alpha = min(0.99, o 2^power)
+              const float power = splat_power(a, b, bdx, zxdx, py0 + (float)(q * G::kRowStep));
+              if (((live >> q) & 1u) && power >= c.z) {
+                const float araw = __fmul_rn(-b.y, ex2_approx(power));   // staged opacity is negated
+                const float alpha = araw > kAlphaMax ? kAlphaMax : araw;
+                const float Tn = __fmul_rn(T[q], __fsub_rn(1.f, alpha));
                 if (Tn < kTMin) {
                   live &= ~(1u << q);
                 } else {
-                  const float w = __fmul_rn(h.alpha, T[q]);
+                  const float w = __fmul_rn(alpha, T[q]);
                   c0[q] = __fmaf_rn(w, b.z, c0[q]);
                   c1[q] = __fmaf_rn(w, b.w, c1[q]);
                   c2[q] = __fmaf_rn(w, c.x, c2[q]);
