@@ -63,29 +63,28 @@ struct AdjSums {
 };
 
 // Two pixels' shares of the adjoint of a blended splat, pixels h and h + 1
-// of a thread side by side in the packed FP32 lanes (e0 / e1: the pixel
-// blended or skipped this splat in the forward).  Per pixel, T
+// of a thread side by side in the packed FP32 lanes, from their exponents
+// pw and row offsets dy (splat_power2); ok0 / ok1: the pixel blended or
+// skipped this splat in the forward and passes its footprint test.  Per pixel, T
 // (transmittance after the splat) becomes T before it; GS = dL/dC . S, S
 // being the colour composited behind (background included), takes the
 // splat's own term (only that dot product enters dL/dalpha); the colour and
 // opacity gradients go to the sums a5..a8.  The conic and mean gradients
 // are linear in dq = dL/dq, so a pixel only adds dq, dq dy and dq dy^2 to
 // q1, qy, qyy (dx is common to a thread's pixels) and the caller forms them
-// once per splat.  A pixel that skips the splat (or is past its last
-// blended entry: e false) takes alpha 0, which leaves its T and GS
-// unchanged and adds 0 to every sum, so the pair runs without a branch.
-// GS is kept negated (NGS = -dL/dC . S) and alpha as nal = -alpha (the
-// staged opacity is negated), which turns dL/dalpha into one fused
-// multiply-add.  kFirst: this pair starts the sums instead of adding to
-// them.  Returns false if both pixels skip.
+// once per splat.  A pixel that skips the splat (ok false: outside the
+// footprint, or past its last blended entry) takes alpha 0, which leaves
+// its T and GS unchanged and adds 0 to every sum, so the pair runs without
+// a branch.  GS is kept negated (NGS = -dL/dC . S) and alpha as nal =
+// -alpha (the staged opacity is negated), which turns dL/dalpha into one
+// fused multiply-add.  kFirst: this pair starts the sums instead of adding
+// to them.
 template <bool kFirst>
-__device__ __forceinline__ bool pixel_adjoint2(const float4 &a, const float4 &b, const float4 &c4, float bdx, float zxdx,
-                                               f32x2 py, bool e0, bool e1, f32x2 g0, f32x2 g1, f32x2 g2, float &T0,
+__device__ __forceinline__ void pixel_adjoint2(const float4 &a, const float4 &b, const float4 &c4, f32x2 pw, f32x2 dy,
+                                               bool ok0, bool ok1, f32x2 g0, f32x2 g1, f32x2 g2, float &T0,
                                                float &T1, float &NGS0, float &NGS1, AdjSums &s) {
-  f32x2 dy;
   float p0, p1;
-  unpack2(splat_power2(a, b, bdx, zxdx, py, dy), p0, p1);
-  const bool ok0 = e0 && p0 >= c4.z, ok1 = e1 && p1 >= c4.z;
+  unpack2(pw, p0, p1);
   // power <= 0 for the positive-definite conics of pk_project_and_sh: G in
   // [0, 1] at every pixel, and a skipping pixel's zero alpha zeroes its terms
   const float G0 = ex2_approx(p0), G1 = ex2_approx(p1);
@@ -126,7 +125,6 @@ __device__ __forceinline__ bool pixel_adjoint2(const float4 &a, const float4 &b,
   s.q1 = kFirst ? dq : add2(s.q1, dq);
   s.qy = kFirst ? t : add2(s.qy, t);
   s.qyy = kFirst ? mul2(t, dy) : fma2(t, dy, s.qyy);
-  return ok0 || ok1;
 }
 
 __device__ __forceinline__ float lane_sum(f32x2 v) {
@@ -343,24 +341,37 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_ras
           const float4 a = s_a[j], b = s_b[j], c4 = s_c[j];
           const float dx = __fsub_rn(px, a.x);
           const float zxdx = __fmul_rn(__fmul_rn(a.z, dx), dx), bdx = __fmul_rn(a.w, dx);
-          AdjSums sums;   // started by the first pair
-          bool act = false;
+          // the exponent at the thread's pixels, and which of them blended
+          // or skipped this splat in the forward and pass its footprint
+          // test; a splat that no pixel of the warp takes is left at once
+          f32x2 pw[kPx / 2], dyv[kPx / 2];
+          bool ok[kPx];
+          bool any = false;
 #pragma unroll
           for (int h = 0; h < kPx; h += 2) {
-            // the pixels blended or skipped this splat in the forward
             const bool e0 = pos < nc[h], e1 = pos < nc[h + 1];
             if (kCount) evals += (uint32_t)e0 + (uint32_t)e1;
-            if (h == 0) {
-              act = pixel_adjoint2<true>(a, b, c4, bdx, zxdx, pack2(pyq[h], pyq[h + 1]), e0, e1,
-                                         pack2(g0[h], g0[h + 1]), pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]),
-                                         T[h], T[h + 1], NGS[h], NGS[h + 1], sums);
-            } else {
-              act |= pixel_adjoint2<false>(a, b, c4, bdx, zxdx, pack2(pyq[h], pyq[h + 1]), e0, e1,
-                                           pack2(g0[h], g0[h + 1]), pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]),
-                                           T[h], T[h + 1], NGS[h], NGS[h + 1], sums);
-            }
+            pw[h / 2] = splat_power2(a, b, bdx, zxdx, pack2(pyq[h], pyq[h + 1]), dyv[h / 2]);
+            float p0, p1;
+            unpack2(pw[h / 2], p0, p1);
+            ok[h] = e0 && p0 >= c4.z;
+            ok[h + 1] = e1 && p1 >= c4.z;
+            any = any || ok[h] || ok[h + 1];
           }
-          if (__any_sync(0xffffffffu, act)) {
+          if (!__any_sync(0xffffffffu, any)) continue;
+          AdjSums sums;   // started by the first pair
+#pragma unroll
+          for (int h = 0; h < kPx; h += 2) {
+            if (h == 0)
+              pixel_adjoint2<true>(a, b, c4, pw[h / 2], dyv[h / 2], ok[h], ok[h + 1], pack2(g0[h], g0[h + 1]),
+                                   pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]), T[h], T[h + 1], NGS[h],
+                                   NGS[h + 1], sums);
+            else
+              pixel_adjoint2<false>(a, b, c4, pw[h / 2], dyv[h / 2], ok[h], ok[h + 1], pack2(g0[h], g0[h + 1]),
+                                    pack2(g1[h], g1[h + 1]), pack2(g2[h], g2[h + 1]), T[h], T[h + 1], NGS[h],
+                                    NGS[h + 1], sums);
+          }
+          {
             float acc[9];
             acc[5] = lane_sum(sums.a5);
             acc[6] = -lane_sum(sums.a6);   // the colour sums hold -alpha T dL/dC
