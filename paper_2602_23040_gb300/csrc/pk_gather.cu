@@ -71,10 +71,25 @@ __global__ __launch_bounds__(kScanThreads) void k_word_scan(const uint32_t *__re
     __syncthreads();
     const uint32_t carry = s_carry;
     uint32_t run = carry + (warp ? s_warp[warp - 1] : 0u) + x - tot;
+    if (w0 + kRun <= nwords && (reinterpret_cast<uintptr_t>(woff) & 15u) == 0) {
+      // a whole run: 16-byte stores, a quarter of the store instructions
+      uint4 *o4 = reinterpret_cast<uint4 *>(woff + w0);
 #pragma unroll
-    for (int k = 0; k < kRun; ++k) {
-      if (w0 + k < nwords) woff[w0 + k] = run;
-      run += c[k];
+      for (int k = 0; k < kRun / 4; ++k) {
+        uint4 v;
+        v.x = run;
+        v.y = v.x + c[4 * k];
+        v.z = v.y + c[4 * k + 1];
+        v.w = v.z + c[4 * k + 2];
+        run = v.w + c[4 * k + 3];
+        o4[k] = v;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRun; ++k) {
+        if (w0 + k < nwords) woff[w0 + k] = run;
+        run += c[k];
+      }
     }
     __syncthreads();
     if (tid == 0) s_carry = carry + s_warp[31];
