@@ -39,7 +39,8 @@ class Renderer:
     def _alloc(self):
         p = self.plan
         f32, i32 = torch.float32, torch.int32
-        self.soa = torch.empty(p.D * p.G, dtype=f32, device=self.device)
+        # (at least one element each: the library takes no null pointer, even for an empty array)
+        self.soa = torch.empty(max(p.D * p.G, 4), dtype=f32, device=self.device)
         self.texel = torch.empty(max(p.N, 1), dtype=i32, device=self.device)
         self.dynflag = torch.empty(max(p.N, 1), dtype=torch.uint8, device=self.device)
         self.records = torch.empty(12 * max(p.pairs, 1), dtype=f32, device=self.device)
@@ -192,7 +193,7 @@ class PerViewLoop:
         self.ws = [api.make_workspace(p, self.device) for p in self.plans]
         for p, w in zip(self.plans, self.ws):
             api.workspace_init(p, w)
-        self.soa = torch.empty(p0.D * p0.G, dtype=f32, device=self.device)
+        self.soa = torch.empty(max(p0.D * p0.G, 4), dtype=f32, device=self.device)
         self.texel = torch.empty(max(p0.N, 1), dtype=i32, device=self.device)
         self.dynflag = torch.empty(max(p0.N, 1), dtype=torch.uint8, device=self.device)
         self.records = torch.empty(12 * max(p0.pairs, 1), dtype=f32, device=self.device)

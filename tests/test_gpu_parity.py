@@ -500,6 +500,37 @@ def test_nothing_visible_gives_background():
     assert np.all(r.T.cpu().numpy() == 1.0) and r.status()["dups"] == 0
 
 
+def test_empty_atlas_renders_background_and_leaves_gradients():
+    """No live texel at all (N = 0): every call of the step still runs.  The
+    image is the background, T = 1, no pixel has a contributor, no list
+    entry is made, and the scatter writes nothing (it writes live texels
+    only, so the gradient buffer keeps what it held)."""
+    pk = _pk()
+    views = [synth.scenes.pinhole((0.4, 0.3, -3.2), 64, 48), synth.scenes.pinhole((-2.6, -0.5, -1.8), 40, 56)]
+    sc = synth.make_scene([(32, 32, 0, 0, 0)], (32, 32), 0.0, views, sh_degree=3, seed=3)
+    assert sc.n_live == 0
+    F, D, Hh, W = sc.atlas.shape
+    plan = pk.Plan(sc.levels, (W, Hh), sc.sh_degree, F, "f32", sc.views, 0, bg=(0.25, 0.5, 1.0))
+    r = pk.Renderer(plan)
+    atlas, occ, dyn = H.upload(sc)
+    r.forward(atlas, occ, dyn)
+    grad = torch.full((F * D * Hh * W,), 7.0, dtype=torch.float32, device="cuda")
+    r.backward(torch.ones(3 * sc.pixels, dtype=torch.float32, device="cuda"), grad)
+    torch.cuda.synchronize()
+    img = r.image.cpu().numpy()   # [view][3][H][W] concatenated
+    off = 0
+    for v in sc.views:
+        n = v.width * v.height
+        for c, b in enumerate((0.25, 0.5, 1.0)):
+            assert np.all(img[3 * off + c * n:3 * off + (c + 1) * n] == b)
+        off += n
+    assert np.all(r.T.cpu().numpy() == 1.0)
+    assert np.all(r.n_contrib.cpu().numpy() == 0)
+    st = r.status()
+    assert st["flags"] == 0 and st["dups"] == 0, st
+    assert np.all(grad.cpu().numpy() == 7.0)
+
+
 def test_every_batch_size_and_autotune():
     """The compositing batch (64, 128, 256 splats) and the staging mode (loads
     or bulk copies) change nothing but speed: images, transmittance and
