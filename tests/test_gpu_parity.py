@@ -405,6 +405,26 @@ def test_end_to_end(orc, which):
     assert np.all(grad.view(F, D, Hh * W).cpu().numpy()[:, :, ~live] == 0)
 
 
+def test_end_to_end_degenerate_view_sizes(orc):
+    """Views of 1 x 1, 1 x 37, 37 x 1, 17 x 15, 33 x 31 and 48 x 16 pixels
+    (focal length 100 px each): rows and columns of tiles cut short on every
+    side, compositing CTAs and warp blocks mostly past the view's edge.
+    Images and gradients against the oracle, as for any scene."""
+    sizes = [(1, 1), (1, 37), (37, 1), (17, 15), (33, 31), (48, 16)]
+    eyes = [(0.4, 0.3, -3.2), (-2.6, -0.5, -1.8), (2.0, 1.2, 2.5), (0.3, -2.9, 1.1), (-1.7, 2.2, -2.0), (3.1, 0.2, 0.4)]
+    views = [synth.scenes.pinhole(e, w, h, fov_x_deg=2.0 * math.degrees(math.atan(w / 200.0)))
+             for e, (w, h) in zip(eyes, sizes)]
+    sc = synth.make_scene([(128, 128, 0, 0, 0)], (128, 128), 0.6, views, sh_degree=3, seed=606,
+                          log_scale=(-3.6, 0.5))
+    P = sc.pixels
+    o = oracle_run(orc, sc)
+    w = H.zero_on_borderline(np.random.default_rng(21).standard_normal(3 * P).astype(np.float32), o)
+    plan, r, grad = run_gpu(sc, dimg=w)
+    oracle_backward(orc, sc, o, w)
+    H.check_images(r.image.cpu().numpy(), r.T.cpu().numpy(), o, label="degenerate views")
+    H.check_grads(gpu_grad_soa(sc, grad, o["texel"]), o["grad_soa"])
+
+
 def test_rect_and_ellipse_binning_give_the_same_images(orc):
     sc = H.scene_small_sh3(seed=404)
     w = np.random.default_rng(15).standard_normal(3 * sc.pixels).astype(np.float32)
