@@ -580,10 +580,11 @@ def main():
         lambda: pk.atlas_gather(plan, atlas, occ, dyn, r.soa, r.texel, r.dynflag, r.ws),
         lambda: pk.project_and_sh(plan, r.soa, r.records, r.ws),
         lambda: pk.bin_and_sort(plan, r.records, r.sorted_vals, r.ranges, r.ws),
-        lambda: pk.rasterize_fwd_l1(plan, r.records, r.sorted_vals, r.ranges, target, r.image, r.T, r.n_contrib,
-                                    r.dimage, r.ws),
-        lambda: pk.rasterize_bwd(plan, r.records, r.sorted_vals, r.ranges, r.T, r.n_contrib, r.dimage, r.grad2d,
-                                 r.ws),
+        # the step's pair: the forward also clears the 2D gradient records
+        lambda: pk.rasterize_fwd_l1_clear(plan, r.records, r.sorted_vals, r.ranges, target, r.image, r.T,
+                                          r.n_contrib, r.dimage, r.grad2d, r.ws),
+        lambda: pk.rasterize_bwd_accumulate(plan, r.records, r.sorted_vals, r.ranges, r.T, r.n_contrib, r.dimage,
+                                            r.grad2d, r.ws),
         lambda: pk.atlas_scatter_grad(plan, r.soa, r.grad2d, r.dynflag if dyn is not None else None, r.texel,
                                       grad, False, r.ws),
     ]

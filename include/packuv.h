@@ -350,6 +350,15 @@ pk_status pk_rasterize_bwd(const pk_plan *plan, const float *records, const uint
                            const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
                            void *workspace, pk_stream_t stream);
 
+/* pk_rasterize_bwd without the clearing of grad2d: the gradients are added
+ * to what grad2d holds ([V*N][12] float32, 16-byte aligned) -- zeros left by
+ * pk_rasterize_fwd_l1_clear, or an earlier backward's sums to add to.  The
+ * same arguments, layouts and errors as pk_rasterize_bwd. */
+pk_status pk_rasterize_bwd_accumulate(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
+                                      const uint64_t *tile_ranges, const float *T_final,
+                                      const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                                      void *workspace, pk_stream_t stream);
+
 /* a6 -- chain rule from grad2d through the projection and SH colour back to
  * the texel attributes, summed over the views of each Gaussian's frame,
  * then multiplied by D_i (Sec. 4.2 "Gradient Freezing"); the FP16 proxy is
@@ -391,6 +400,18 @@ pk_status pk_rasterize_fwd_l1(const pk_plan *plan, const float *records, const u
                               const uint64_t *tile_ranges, const float *target, float *image,
                               float *T_final, uint32_t *n_contrib, float *dL_dimage, void *workspace,
                               pk_stream_t stream);
+
+/* pk_rasterize_fwd_l1 that also sets grad2d ([V*N][12] float32, 16-byte
+ * aligned) to zero, for a following pk_rasterize_bwd_accumulate: the
+ * compositing kernel clears a share of it per work item, stores that ride
+ * along with its arithmetic-bound work instead of a clearing pass in front
+ * of the backward (the pair is one step's forward and backward of Sec. 4.2
+ * "Objective" with the L1 term).  Outputs and errors otherwise as
+ * pk_rasterize_fwd_l1. */
+pk_status pk_rasterize_fwd_l1_clear(const pk_plan *plan, const float *records, const uint32_t *sorted_vals,
+                                    const uint64_t *tile_ranges, const float *target, float *image,
+                                    float *T_final, uint32_t *n_contrib, float *dL_dimage, float *grad2d,
+                                    void *workspace, pk_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Motion masks and the dynamic mask D_i                                     */

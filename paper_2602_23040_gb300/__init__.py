@@ -25,8 +25,10 @@ from .api import (  # noqa: F401
     photo_loss_grad,
     project_and_sh,
     rasterize_bwd,
+    rasterize_bwd_accumulate,
     rasterize_fwd,
     rasterize_fwd_l1,
+    rasterize_fwd_l1_clear,
     read_status,
     render_bwd,
     render_fwd,
@@ -37,7 +39,8 @@ from .render import PerViewLoop, Renderer, render  # noqa: F401
 
 __all__ = [
     "Plan", "Renderer", "PerViewLoop", "render", "atlas_layout", "atlas_gather", "project_and_sh",
-    "bin_and_sort", "bin_and_sort_noalloc", "rasterize_fwd", "rasterize_fwd_l1", "rasterize_bwd",
+    "bin_and_sort", "bin_and_sort_noalloc", "rasterize_fwd", "rasterize_fwd_l1", "rasterize_fwd_l1_clear",
+    "rasterize_bwd", "rasterize_bwd_accumulate",
     "atlas_scatter_grad", "l1_loss_grad", "photo_loss_grad", "motion_mask", "dynamic_mask", "lpo_minmax", "lpo_encode", "atlas_gather_lpo", "uv_max_k", "autotune",
     "render_fwd", "render_bwd",
     "make_workspace", "workspace_init", "read_status",

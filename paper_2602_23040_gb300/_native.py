@@ -84,9 +84,11 @@ SIGNATURES = {
     "pk_bin_and_sort": (ST, [P, P, P, P, P, P]),
     "pk_rasterize_fwd": (ST, [P, P, P, P, P, P, P, P, P]),
     "pk_rasterize_bwd": (ST, [P, P, P, P, P, P, P, P, P, P]),
+    "pk_rasterize_bwd_accumulate": (ST, [P, P, P, P, P, P, P, P, P, P]),
     "pk_atlas_scatter_grad": (ST, [P, P, P, P, P, P, C.c_int32, P, P]),
     "pk_l1_loss_grad": (ST, [P, P, P, P, P, P]),
     "pk_rasterize_fwd_l1": (ST, [P, P, P, P, P, P, P, P, P, P, P]),
+    "pk_rasterize_fwd_l1_clear": (ST, [P, P, P, P, P, P, P, P, P, P, P, P]),
     "pk_bin_and_sort_noalloc": (ST, [P, P, P, P, P, P]),
     "pk_motion_mask": (ST, [P, P, C.c_float, C.c_int32, P, P, P]),
     "pk_dynamic_mask": (ST, [P, P, P, P, C.c_float, P, C.c_int32, P, P]),

@@ -269,6 +269,19 @@ def rasterize_bwd(plan: Plan, records, sorted_vals, tile_ranges, T_final, n_cont
     N.check("pk_rasterize_bwd", rc)
 
 
+def rasterize_bwd_accumulate(plan: Plan, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d,
+                             ws, stream=None) -> None:
+    """rasterize_bwd adding to grad2d instead of clearing it first."""
+    rc = N.load().pk_rasterize_bwd_accumulate(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
+        _ptr(T_final, "T_final", torch.float32, plan.P), _ptr(n_contrib, "n_contrib", _I32, plan.P),
+        _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
+        _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs), _ptr(ws, "workspace"),
+        _stream(stream))
+    N.check("pk_rasterize_bwd_accumulate", rc)
+
+
 def atlas_scatter_grad(plan: Plan, soa, grad2d, dynflag, texel, grad_atlas, accumulate: bool, ws,
                        stream=None) -> None:
     F, D = plan.desc.frames, plan.D
@@ -300,6 +313,20 @@ def rasterize_fwd_l1(plan: Plan, records, sorted_vals, tile_ranges, target, imag
         _ptr(T_final, "T_final", torch.float32, plan.P), _ptr(n_contrib, "n_contrib", _I32, plan.P),
         _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P), _ptr(ws, "workspace"), _stream(stream))
     N.check("pk_rasterize_fwd_l1", rc)
+
+
+def rasterize_fwd_l1_clear(plan: Plan, records, sorted_vals, tile_ranges, target, image, T_final, n_contrib,
+                           dL_dimage, grad2d, ws, stream=None) -> None:
+    """rasterize_fwd_l1 that also sets grad2d to zero (for rasterize_bwd_accumulate)."""
+    rc = N.load().pk_rasterize_fwd_l1_clear(
+        plan.handle, _ptr(records, "records", torch.float32, N.RECORD_FLOATS * plan.pairs),
+        _ptr(sorted_vals, "sorted_vals", _I32), _ptr(tile_ranges, "tile_ranges", _I64, 2 * plan.n_tiles),
+        _ptr(target, "target", torch.float32, 3 * plan.P), _ptr(image, "image", torch.float32, 3 * plan.P),
+        _ptr(T_final, "T_final", torch.float32, plan.P), _ptr(n_contrib, "n_contrib", _I32, plan.P),
+        _ptr(dL_dimage, "dL_dimage", torch.float32, 3 * plan.P),
+        _ptr(grad2d, "grad2d", torch.float32, N.GRAD2D_FLOATS * plan.pairs), _ptr(ws, "workspace"),
+        _stream(stream))
+    N.check("pk_rasterize_fwd_l1_clear", rc)
 
 
 def photo_loss_grad(plan: Plan, image, target, dL_dimage, ws, lam: float = 0.2, stream=None) -> None:

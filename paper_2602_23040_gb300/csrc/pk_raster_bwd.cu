@@ -426,17 +426,20 @@ pk_status launch_bwd(const pk_plan *p, const float *records, const uint32_t *sor
 
 }  // namespace
 
-extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
-                                      const uint64_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
-                                      const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream) {
+namespace {
+
+// zero_grad2d: clear the gradient records first (pk_rasterize_bwd), or add
+// to what they hold (pk_rasterize_bwd_accumulate).
+pk_status rasterize_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                        const uint64_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                        const float *dL_dimage, float *grad2d, void *ws, bool zero_grad2d, cudaStream_t st) {
   if (!p || !records || !sorted_vals || !tile_ranges || !T_final || !n_contrib || !dL_dimage || !grad2d || !ws)
     return PK_ERR_ARG;
   if (!aligned16(records) || !aligned16(grad2d) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u))
     return PK_ERR_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
-  pk_status ze = zero_async({{grad2d, sizeof(float) * kG2d * (size_t)p->pairs},
+  pk_status ze = zero_async({{grad2d, zero_grad2d ? sizeof(float) * kG2d * (size_t)p->pairs : 0},
                              {&ctr->tile_queue[1], sizeof(uint32_t)},
                              {&status->evals_bwd, sizeof(uint64_t)}},
                             st);
@@ -467,4 +470,21 @@ extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, co
   }
 #undef PK_BWD
 #undef PK_BWD_T
+}
+
+}  // namespace
+
+extern "C" pk_status pk_rasterize_bwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                                      const uint64_t *tile_ranges, const float *T_final, const uint32_t *n_contrib,
+                                      const float *dL_dimage, float *grad2d, void *ws, pk_stream_t stream) {
+  return rasterize_bwd(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, true,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" pk_status pk_rasterize_bwd_accumulate(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                                                 const uint64_t *tile_ranges, const float *T_final,
+                                                 const uint32_t *n_contrib, const float *dL_dimage, float *grad2d,
+                                                 void *ws, pk_stream_t stream) {
+  return rasterize_bwd(p, records, sorted_vals, tile_ranges, T_final, n_contrib, dL_dimage, grad2d, ws, false,
+                       reinterpret_cast<cudaStream_t>(stream));
 }

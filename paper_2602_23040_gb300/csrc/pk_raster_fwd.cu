@@ -29,13 +29,17 @@ namespace {
 // |image - target| (FP32 per thread, FP64 across warps) into loss_acc.
 // kCount: count the (pixel, splat) evaluations into evals_out (a
 // measurement; the variant without it carries no counter in its loop).
+// clr (may be null): clr_n4 float4 set to zero along the way, clr_per of
+// them per work item -- the backward's gradient records, cleared by stores
+// that ride along with the compositing instead of a pass of their own.
 template <int kBatch, bool kTma, int kPx, int kT, bool kCount>
 __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_raster_fwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint64_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, float *__restrict__ image, float *__restrict__ Tout, uint32_t *__restrict__ ncontrib,
     uint32_t *queue, unsigned long long *evals_out, pk_device_status *status, const float *__restrict__ target,
-    float *__restrict__ dimg, float scale, double *loss_acc, uint32_t first_polls, uint32_t npairs) {
+    float *__restrict__ dimg, float scale, double *loss_acc, uint32_t first_polls, uint32_t npairs,
+    float4 *__restrict__ clr, uint64_t clr_n4, uint64_t clr_per) {
   using G = Geo<kPx>;
   constexpr uint32_t kQuads = (kT / kTileSide) * (kT / kTileSide);   // CTAs per list tile
   __shared__ float4 s_a[kBatch], s_b[kBatch], s_c[kBatch], s_box[kBatch], s_q[kBatch];
@@ -79,6 +83,10 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
     __syncthreads();
     const uint32_t w = s_tile;
     if (w >= n_items) break;
+    if (clr) {   // this work item's share of the buffer to clear (every item takes one, so all of it is)
+      const uint64_t c0 = (uint64_t)w * clr_per, c1 = min(clr_n4, c0 + clr_per);
+      for (uint64_t i = c0 + tid; i < c1; i += G::kThreads) clr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const uint32_t t = w / kQuads, q = w - t * kQuads;
     const DevView &view = views[s_view];
     const int W = view.width, H = view.height;
@@ -279,8 +287,8 @@ __global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 2 ? 10 : 1)) void k_ras
 template <int kBatch, bool kFwdTma, int kT, bool kCount>
 pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                      const uint64_t *tile_ranges, float *image, float *T_final, uint32_t *n_contrib, void *ws,
-                     DevCounters *ctr, pk_device_status *status, const float *target, float *dimg,
-                     cudaStream_t st) {
+                     DevCounters *ctr, pk_device_status *status, const float *target, float *dimg, float *clear,
+                     uint64_t clear_floats, cudaStream_t st) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -292,17 +300,21 @@ pk_status launch_fwd(const pk_plan *p, const float *records, const uint32_t *sor
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > items) grid = items;
   if (grid < 1) grid = 1;
+  const uint64_t clr_n4 = clear ? clear_floats / 4 : 0;
+  const uint64_t clr_per = items > 0 ? (clr_n4 + (uint64_t)items - 1) / (uint64_t)items : 0;
   k_raster_fwd<kBatch, kFwdTma, kFwdPx, kT, kCount><<<(int)grid, Geo<kFwdPx>::kThreads, 0, st>>>(
       records, sorted_vals, tile_ranges, at<DevView>(ws, p->ws.views), at<uint32_t>(ws, p->ws.toff), p->V,
       (uint32_t)items, p->opts.bg[0], p->opts.bg[1], p->opts.bg[2], image, T_final, n_contrib,
       &ctr->tile_queue[0], reinterpret_cast<unsigned long long *>(&status->evals_fwd), status, target, dimg,
-      (float)(1.0 / (3.0 * (double)std::max<int64_t>(1, p->P))), &ctr->loss_acc, p->first_polls, (uint32_t)p->pairs);
+      (float)(1.0 / (3.0 * (double)std::max<int64_t>(1, p->P))), &ctr->loss_acc, p->first_polls, (uint32_t)p->pairs,
+      reinterpret_cast<float4 *>(clr_n4 ? clear : nullptr), clr_n4, clr_per);
   return check_launch();
 }
 
 pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
                         const uint64_t *tile_ranges, const float *target, float *image, float *T_final,
-                        uint32_t *n_contrib, float *dimg, void *ws, cudaStream_t st) {
+                        uint32_t *n_contrib, float *dimg, float *clear, uint64_t clear_floats, void *ws,
+                        cudaStream_t st) {
   DevCounters *ctr = at<DevCounters>(ws, p->ws.counters);
   pk_device_status *status = at<pk_device_status>(ws, p->ws.status);
   // the tile queue, the evaluation counter and, with a target, loss_acc,
@@ -314,9 +326,9 @@ pk_status rasterize_fwd(const pk_plan *p, const float *records, const uint32_t *
   if (ze != PK_OK) return ze;
 #define PK_FWD_T(B, M, C)                                                                                     \
   return p->T == 32 ? launch_fwd<B, M, 32, C>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, \
-                                              ws, ctr, status, target, dimg, st)                                \
+                                              ws, ctr, status, target, dimg, clear, clear_floats, st)           \
                     : launch_fwd<B, M, 16, C>(p, records, sorted_vals, tile_ranges, image, T_final, n_contrib, \
-                                              ws, ctr, status, target, dimg, st)
+                                              ws, ctr, status, target, dimg, clear, clear_floats, st)
 #define PK_FWD(B, M)            \
   {                             \
     if (p->opts.count_evals) {  \
@@ -347,8 +359,8 @@ extern "C" pk_status pk_rasterize_fwd(const pk_plan *p, const float *records, co
                                       void *ws, pk_stream_t stream) {
   if (!p || !records || !sorted_vals || !tile_ranges || !image || !T_final || !n_contrib || !ws) return PK_ERR_ARG;
   if (!aligned16(records) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return PK_ERR_ARG;
-  return rasterize_fwd(p, records, sorted_vals, tile_ranges, nullptr, image, T_final, n_contrib, nullptr, ws,
-                       reinterpret_cast<cudaStream_t>(stream));
+  return rasterize_fwd(p, records, sorted_vals, tile_ranges, nullptr, image, T_final, n_contrib, nullptr, nullptr, 0,
+                       ws, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" pk_status pk_rasterize_fwd_l1(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
@@ -359,6 +371,19 @@ extern "C" pk_status pk_rasterize_fwd_l1(const pk_plan *p, const float *records,
       !dL_dimage || !ws)
     return PK_ERR_ARG;
   if (!aligned16(records) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u)) return PK_ERR_ARG;
-  return rasterize_fwd(p, records, sorted_vals, tile_ranges, target, image, T_final, n_contrib, dL_dimage, ws,
-                       reinterpret_cast<cudaStream_t>(stream));
+  return rasterize_fwd(p, records, sorted_vals, tile_ranges, target, image, T_final, n_contrib, dL_dimage, nullptr,
+                       0, ws, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" pk_status pk_rasterize_fwd_l1_clear(const pk_plan *p, const float *records, const uint32_t *sorted_vals,
+                                               const uint64_t *tile_ranges, const float *target, float *image,
+                                               float *T_final, uint32_t *n_contrib, float *dL_dimage,
+                                               float *grad2d, void *ws, pk_stream_t stream) {
+  if (!p || !records || !sorted_vals || !tile_ranges || !target || !image || !T_final || !n_contrib ||
+      !dL_dimage || !grad2d || !ws)
+    return PK_ERR_ARG;
+  if (!aligned16(records) || !aligned16(grad2d) || (reinterpret_cast<uintptr_t>(tile_ranges) & 7u))
+    return PK_ERR_ARG;
+  return rasterize_fwd(p, records, sorted_vals, tile_ranges, target, image, T_final, n_contrib, dL_dimage, grad2d,
+                       (uint64_t)kG2d * (uint64_t)p->pairs, ws, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -54,7 +54,8 @@ class Renderer:
         self._has_dyn = False
 
     # forward: a1 .. a4 (target: the L1 loss gradient fused into a4)
-    def forward(self, atlas, occ, dyn=None, stream=None, target=None):
+    def _front(self, atlas, occ, dyn, stream):
+        # a1 .. a3: gather, projection, binning + sort
         p = self.plan
         self.generation += 1
         self._has_dyn = dyn is not None
@@ -65,6 +66,10 @@ class Renderer:
             api.atlas_gather(p, atlas, occ, dyn, self.soa, self.texel, self.dynflag, self.ws, stream)
         api.project_and_sh(p, self.soa, self.records, self.ws, stream)
         api.bin_and_sort(p, self.records, self.sorted_vals, self.ranges, self.ws, stream)
+
+    def forward(self, atlas, occ, dyn=None, stream=None, target=None):
+        p = self.plan
+        self._front(atlas, occ, dyn, stream)
         if target is None:
             api.rasterize_fwd(p, self.records, self.sorted_vals, self.ranges, self.image, self.T, self.n_contrib,
                               self.ws, stream)
@@ -83,9 +88,17 @@ class Renderer:
         return grad_atlas
 
     def l1_step(self, atlas, occ, dyn, target, grad_atlas, stream=None):
-        """One fitting step: forward with the L1 loss gradient, backward."""
-        self.forward(atlas, occ, dyn, stream, target=target)
-        self.backward(self.dimage, grad_atlas, False, stream)
+        """One fitting step: forward with the L1 loss gradient, backward.  The
+        forward also clears the 2D gradient records, so the backward adds to
+        them without a clearing pass of its own."""
+        p = self.plan
+        self._front(atlas, occ, dyn, stream)
+        api.rasterize_fwd_l1_clear(p, self.records, self.sorted_vals, self.ranges, target, self.image, self.T,
+                                   self.n_contrib, self.dimage, self.grad2d, self.ws, stream)
+        api.rasterize_bwd_accumulate(p, self.records, self.sorted_vals, self.ranges, self.T, self.n_contrib,
+                                     self.dimage, self.grad2d, self.ws, stream)
+        api.atlas_scatter_grad(p, self.soa, self.grad2d, self.dynflag if self._has_dyn else None, self.texel,
+                               grad_atlas, False, self.ws, stream)
 
     def photo_step(self, atlas, occ, dyn, target, grad_atlas, lam: float = 0.2, stream=None):
         """One fitting step with the paper's photometric objective

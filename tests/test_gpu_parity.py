@@ -342,6 +342,70 @@ def test_rasterize_fwd_l1_matches_separate_calls(orc, seed):
     assert abs(st["loss"] - want) <= 1e-6 * abs(want)
 
 
+@pytest.mark.parametrize("seed,tile", [(5, 16), (5, 32)])
+def test_clearing_forward_and_accumulating_backward(seed, tile):
+    """pk_rasterize_fwd_l1_clear: the outputs of pk_rasterize_fwd_l1 bit for
+    bit, and every float of grad2d (filled with garbage first) zero after
+    it; pk_rasterize_bwd_accumulate then gives pk_rasterize_bwd's gradients
+    (up to the order of their atomic sums), and a second call doubles them."""
+    pk = _pk()
+    o = _records_forward(seed, dimg_seed=seed + 9, tile=tile)
+    plan, ws = o["plan"], o["ws"]
+    target = torch.from_numpy(np.random.default_rng(seed + 41).random(3 * plan.P).astype(np.float32)).cuda()
+    img0, T0, nc0, g0 = (torch.empty_like(o["img"]), torch.empty_like(o["T"]), torch.empty_like(o["nc"]),
+                         torch.empty_like(o["img"]))
+    pk.rasterize_fwd_l1(plan, o["drec"], o["vals"], o["ranges"], target, img0, T0, nc0, g0, ws)
+    img, T = torch.full_like(o["img"], -1.0), torch.full_like(o["T"], -1.0)
+    nc, g = torch.full_like(o["nc"], -1), torch.full_like(o["img"], 7.0)
+    g2 = torch.full((12 * plan.pairs,), float("nan"), dtype=torch.float32, device="cuda")
+    pk.rasterize_fwd_l1_clear(plan, o["drec"], o["vals"], o["ranges"], target, img, T, nc, g, g2, ws)
+    torch.cuda.synchronize()
+    assert pk.read_status(plan, ws)["flags"] == 0
+    for a, b in ((img, img0), (T, T0), (g, g0)):
+        assert torch.equal(a.view(torch.int32), b.view(torch.int32))
+    assert torch.equal(nc, nc0)
+    assert torch.equal(g2.view(torch.int32), torch.zeros_like(g2).view(torch.int32))
+    w = torch.from_numpy(o["w"]).cuda()
+    pk.rasterize_bwd_accumulate(plan, o["drec"], o["vals"], o["ranges"], o["T"], o["nc"], w, g2, ws)
+    torch.cuda.synchronize()
+    ref = o["g2"].cpu().numpy().astype(np.float64)
+    got = g2.cpu().numpy().astype(np.float64)
+    scale = max(1e-12, np.abs(ref).max())
+    assert np.abs(got - ref).max() <= 1e-5 * scale
+    pk.rasterize_bwd_accumulate(plan, o["drec"], o["vals"], o["ranges"], o["T"], o["nc"], w, g2, ws)
+    torch.cuda.synchronize()
+    assert np.abs(g2.cpu().numpy().astype(np.float64) - 2.0 * ref).max() <= 2e-5 * scale
+
+
+def test_l1_step_equals_forward_then_backward():
+    """Renderer.l1_step (the clearing forward, the accumulating backward)
+    against forward with the L1 target then backward: the same image and
+    dL/dimage bit for bit, the same texel gradient up to the order of the
+    atomic sums, whatever the 2D gradient buffer held before."""
+    pk = _pk()
+    sc = H.scene_small_sh3(seed=515)
+    atlas, occ, dyn = H.upload(sc)
+    F, D, Hh, W = sc.atlas.shape
+    target = torch.from_numpy(synth.random_target(sc)).cuda()
+    r = pk.Renderer(pk.Plan.for_scene(sc))
+    r.ensure_capacity(atlas, occ, dyn)
+    ga = torch.zeros(F * D * Hh * W, dtype=torch.float32, device="cuda")
+    r.forward(atlas, occ, dyn, target=target)
+    r.backward(r.dimage, ga)
+    torch.cuda.synchronize()
+    img0, dimg0 = r.image.clone(), r.dimage.clone()
+    r.grad2d.fill_(float("nan"))
+    gb = torch.zeros_like(ga)
+    r.l1_step(atlas, occ, dyn, target, gb)
+    torch.cuda.synchronize()
+    assert r.status()["flags"] == 0
+    assert torch.equal(r.image.view(torch.int32), img0.view(torch.int32))
+    assert torch.equal(r.dimage.view(torch.int32), dimg0.view(torch.int32))
+    a, b = ga.cpu().numpy().astype(np.float64), gb.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(b))
+    assert np.abs(a - b).max() <= 1e-5 * max(1e-12, np.abs(a).max())
+
+
 @pytest.mark.parametrize("seed,tile", [(5, 16), (6, 16), (5, 32)])
 def test_rasterize_fwd_on_identical_records(orc, seed, tile):
     o = _records_forward(seed, tile=tile)
