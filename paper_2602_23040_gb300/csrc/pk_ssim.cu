@@ -7,7 +7,7 @@
 // region (halo 5) by a horizontal then a vertical 11-tap pass, turns them
 // into the SSIM value and its partial derivatives, and sums those back onto
 // the 32 x 32 tile with the same separable window (the adjoint of the
-// window sums).  Every pass is register-tiled: a thread produces 6 or 8
+// window sums).  Every pass is register-tiled: a thread produces 4 to 8
 // consecutive outputs of one row or column from one sliding read of the
 // inputs, so shared-memory reads are about 1/4 of the multiply-adds.  The
 // sums travel in pairs -- (X, Y), (XX, YY) and, backwards, (d1, d11) -- so
@@ -15,7 +15,11 @@
 // results, each the scalar one) plus one scalar for the fifth sum.
 // Image and target are read once per tile (plus halo) and the gradient
 // written once; the arithmetic (about 400 FP32 operations per value)
-// bounds the kernel.
+// bounds the kernel.  The five barrier-separated stages each leave some
+// threads idle, so the SM is kept busy by CTAs at different stages: the
+// derivative maps reuse the shared memory of the input window (the last
+// stage reads its centre values again from global memory, where they are
+// still cached), which brings a CTA to 67 KB and three CTAs onto an SM.
 #include "pk_common.cuh"
 #include "pk_f32x2.cuh"
 
@@ -38,19 +42,27 @@ __constant__ float c_w[2 * kR + 1];
 // hit distinct banks.
 constexpr int kIP = kI + 1, kMP = kM + 1, kTP = kT + 1;
 constexpr int kGB = 6;   // stage B: window-sum columns per item (42 = 7 x 6)
-constexpr int kGC = 6;   // stage C: window-sum rows per item (42 = 7 x 6)
+constexpr int kGC = 7;   // stage C: window-sum rows per item (42 = 6 x 7)
 constexpr int kGD = 8;   // stage D: tile columns per item (32 = 4 x 8)
-constexpr int kGE = 8;   // stage E: tile rows per item (32 = 4 x 8)
+constexpr int kGE = 4;   // stage E: tile rows per item (32 = 8 x 4)
 
 struct SsimSmem {
-  float x[kI][kIP], y[kI][kIP];       // inputs, 0 outside the image
+  union {
+    struct {
+      float x[kI][kIP], y[kI][kIP];   // inputs, 0 outside the image (read by the horizontal sums only)
+    };
+    struct {
+      f32x2 d01[kM][kMP];             // then: partial derivatives of the SSIM map, (d1, d11) and d12
+      float d2[kM][kMP];
+    };
+  };
   f32x2 h01[kI][kMP], h23[kI][kMP];   // horizontal sums (X, Y), (XX, YY); later the backward
   float h4[kI][kMP];                  //   sums ((d1, d11) pairs, d12) on [kM][kTP]; XY
-  f32x2 d01[kM][kMP];                 // partial derivatives of the SSIM map: (d1, d11), d12
-  float d2[kM][kMP];
 };
+static_assert(sizeof(float) * 2 * kM * kMP + sizeof(float) * kM * kMP <= sizeof(float) * 2 * kI * kIP,
+              "the derivative maps fit in the input tiles they replace");
 
-__global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restrict__ img,
+__global__ __launch_bounds__(kSsimThreads, 3) void k_photo(const float *__restrict__ img,
                                                            const float *__restrict__ tgt,
                                                            const DevView *__restrict__ views, float lambda,
                                                            float inv_n, float *__restrict__ grad, double *l1_acc,
@@ -222,7 +234,8 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
   }
   __syncthreads();
   // E: vertical sums onto kGE rows of one tile column, combined with X, Y
-  // and the L1 term
+  // (read again from global memory: their shared copy now holds the
+  // derivative maps) and the L1 term
   float l1_sum = 0.f;
   const float gl1 = (1.f - lambda) * inv_n, gs = lambda * inv_n;
   for (int it = tid; it < kT * (kT / kGE); it += kSsimThreads) {
@@ -252,7 +265,7 @@ __global__ __launch_bounds__(kSsimThreads, 2) void k_photo(const float *__restri
     for (int o = 0; o < kGE; ++o) {
       const int r = r0 + o, yy = ty0 + r;
       if (yy >= H) break;
-      const float xv = S.x[r + 2 * kR][q + 2 * kR], yv = S.y[r + 2 * kR][q + 2 * kR];
+      const float xv = __ldg(X + (int64_t)yy * W + xx), yv = __ldg(Y + (int64_t)yy * W + xx);
       float s0, s1;
       unpack2(c01[o], s0, s1);
       const float dS = s0 + 2.f * xv * s1 + yv * c2[o];
