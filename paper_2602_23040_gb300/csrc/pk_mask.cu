@@ -8,13 +8,14 @@
 // square dilation, a horizontal pass on 64-bit word pairs with logarithmic
 // bit smearing and a vertical pass of (2r + 1) coalesced word loads.
 //
-// The dynamic mask takes one thread per Gaussian that visits its views in
-// order and stops at the first hit, so the OR over cameras happens on the
-// device and a dynamic Gaussian usually costs one view.  Per view the
-// pair's projected record gives mean, conic and radius; a block mask (one
-// bit per 32 x 32 pixels) skips motion-free parts of the square around the
-// mean, the word mask motion-free 32-pixel runs, and only pixels whose
-// mask bit is set are tested against the ellipse.
+// The dynamic mask takes one lane per Gaussian; a warp visits the views in
+// order and a Gaussian stops at its first hit, so the OR over cameras
+// happens on the device and a dynamic Gaussian usually costs one view.
+// Per view the pair's projected record gives mean, conic and radius; a
+// block mask (one bit per 32 x 32 pixels) rules out most pairs on the
+// lane that owns them, and the rest are scanned by the whole warp, one
+// row per lane: the word mask skips motion-free 32-pixel runs, and only
+// pixels whose mask bit is set are tested against the ellipse.
 #include "pk_common.cuh"
 
 using namespace pk;
@@ -135,82 +136,40 @@ __global__ __launch_bounds__(kMaskThreads) void k_mask_coarse(const uint32_t *__
   if (lane == 0) coarse[view.coarse_off + w] = word;
 }
 
-// Alg. 1 step 5 and the OR over views for Gaussian g, views in order, until
-// the first hit.  Square and d^2 in FP32 without fused multiply-adds, in the
-// order stated in packuv.h; the block mask skips 32-pixel words of blocks
-// without motion, the word mask pixels without motion, and a conservative
-// filter the rows and columns outside the ellipse's extent.
-__global__ __launch_bounds__(kMaskThreads) void k_dynamic_mask(const float *__restrict__ rec,
-                                                                const uint32_t *__restrict__ texel,
-                                                                const uint32_t *__restrict__ mask,
-                                                                const uint32_t *__restrict__ coarse,
-                                                                const DevView *__restrict__ views, int V,
-                                                                int64_t N, int atlas_w, int atlas_h, float r_max,
-                                                                uint32_t *dyn) {
-  const int64_t g = (int64_t)blockIdx.x * kMaskThreads + threadIdx.x;
-  if (g >= N) return;
-  const uint32_t t = __ldg(texel + g);
-  // texel ids past the atlas (unwritten after a live-count mismatch) are skipped
-  if (t >= (uint32_t)atlas_w * (uint32_t)atlas_h) return;
-  for (int v = 0; v < V; ++v) {
-    const float4 r0 = __ldg(reinterpret_cast<const float4 *>(rec + ((size_t)v * N + g) * kRec));
-    const float2 r1 = __ldg(reinterpret_cast<const float2 *>(rec + ((size_t)v * N + g) * kRec + 4));
-    float rad = __ldg(rec + ((size_t)v * N + g) * kRec + 7);
-    if (!(rad > 0.0f)) continue;
-    if (r_max > 0.0f && rad > r_max) rad = r_max;
-    const float mx = r0.x, my = r0.y, a = r0.z, b = r0.w, c = r1.x;
-    if (!isfinite(mx) || !isfinite(my)) continue;
-    const DevView &view = views[v];
-    const int W = view.width, H = view.height, wpr = (W + 31) >> 5, cpr = (wpr + 31) >> 5;
-    const float ax = __fsub_rn(mx, 0.5f), ay = __fsub_rn(my, 0.5f);
-    const float lox = fmaxf(ceilf(__fsub_rn(ax, rad)), 0.0f), hix = fminf(floorf(__fadd_rn(ax, rad)), (float)(W - 1));
-    const float loy = fmaxf(ceilf(__fsub_rn(ay, rad)), 0.0f), hiy = fminf(floorf(__fadd_rn(ay, rad)), (float)(H - 1));
-    if (!(lox <= hix) || !(loy <= hiy)) continue;
-    int x0 = (int)lox, x1 = (int)hix, y0 = (int)loy, y1 = (int)hiy;
-    // Candidate filter (never decides a pixel, only skips ones that cannot
-    // pass): rows within the ellipse's y extent 3 sqrt(a / det) and, per row,
-    // the x interval of {q <= 9}, both widened far beyond FP32 error.
-    const float det = a * c - b * b;
-    const bool filt = a > 0.0f && c > 0.0f && det > 0.0f && isfinite(det);
-    if (filt) {
-      const float ey = 3.0f * sqrtf(a / det) * 1.001f + 1.0f, ex = 3.0f * sqrtf(c / det) * 1.001f + 1.0f;
-      y0 = max(y0, (int)fmaxf(ceilf(ay - ey), 0.0f));
-      y1 = min(y1, (int)fminf(floorf(ay + ey), (float)(H - 1)));
-      x0 = max(x0, (int)fmaxf(ceilf(ax - ex), 0.0f));
-      x1 = min(x1, (int)fminf(floorf(ax + ex), (float)(W - 1)));
-      if (y0 > y1 || x0 > x1) continue;
-    }
-    const uint32_t *vmask = mask + view.mask_off;
-    const uint32_t *vcoarse = coarse + view.coarse_off;
-    const float b2 = __fmul_rn(2.0f, b);
-    const float ra = filt ? 1.0f / a : 0.0f, pad = filt ? 9e-4f * a : 0.0f;
-    const int w0 = x0 >> 5, w1 = x1 >> 5;
-    for (int cy = y0 >> 5; cy <= (y1 >> 5); ++cy) {
-      const uint32_t *crow = vcoarse + (int64_t)cy * cpr;
-      // skip the 32 rows of this block row at once if no block in [w0, w1] moves
-      bool moving = false;
-      for (int cw = w0 >> 5; cw <= (w1 >> 5) && !moving; ++cw) {
-        uint32_t cm = __ldg(crow + cw);
-        if (cw == (w0 >> 5)) cm &= ~0u << (w0 & 31);
-        if (cw == (w1 >> 5)) cm &= ~0u >> (31 - (w1 & 31));
-        moving = cm != 0u;
+// Does the ellipse q <= 9 of a pair cover a moving pixel of its rectangle
+// [x0, x1] x [y0, y1]?  Called by a whole warp with the same pair: lane l
+// takes rows y0 + l, y0 + l + 32, ...; per row a conservative filter keeps
+// the x interval of {q <= 9} (widened far beyond FP32 error: it never
+// decides a pixel, it only skips ones that cannot pass), the block mask
+// skips 32-pixel words of blocks without motion, the word mask pixels
+// without motion, and each moving pixel left takes the decision: d^2 in
+// FP32 without fused multiply-adds, in the order stated in packuv.h.
+__device__ bool warp_pair_hits(float mx, float my, float a, float b, float c, int x0, int x1, int y0, int y1, int W,
+                               int wpr, int cpr, const uint32_t *__restrict__ vmask,
+                               const uint32_t *__restrict__ vcoarse, int lane) {
+  const float ax = __fsub_rn(mx, 0.5f);
+  const float det = a * c - b * b;
+  const bool filt = a > 0.0f && c > 0.0f && det > 0.0f && isfinite(det);
+  const float b2 = __fmul_rn(2.0f, b);
+  const float ra = filt ? 1.0f / a : 0.0f, pad = filt ? 9e-4f * a : 0.0f;
+  for (int yb = y0; yb <= y1; yb += 32) {
+    const int y = yb + lane;
+    bool h = false;
+    if (y <= y1) {
+      const uint32_t *crow = vcoarse + (int64_t)(y >> 5) * cpr;
+      const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), my);
+      int xa = x0, xb = x1;
+      if (filt) {
+        const float disc = 9.0f * a - dy * dy * det;
+        const float half = sqrtf(fmaxf(disc, 0.0f) + pad) * ra + 1.0f;
+        const float xc = ax - b * dy * ra;
+        xa = max(xa, (int)fmaxf(ceilf(xc - half), 0.0f));
+        xb = min(xb, (int)fminf(floorf(xc + half), (float)(W - 1)));
       }
-      if (!moving) continue;
-      const int ya = max(y0, 32 * cy), yb = min(y1, 32 * cy + 31);
-      for (int y = ya; y <= yb; ++y) {
-        const float dy = __fsub_rn(__fadd_rn((float)y, 0.5f), my);
-        int xa = x0, xb = x1;
-        if (filt) {
-          const float disc = 9.0f * a - dy * dy * det;
-          const float half = sqrtf(fmaxf(disc, 0.0f) + pad) * ra + 1.0f;
-          const float xc = ax - b * dy * ra;
-          xa = max(xa, (int)fmaxf(ceilf(xc - half), 0.0f));
-          xb = min(xb, (int)fminf(floorf(xc + half), (float)(W - 1)));
-          if (xa > xb) continue;
-        }
+      if (xa <= xb) {
         const float cyy = __fmul_rn(__fmul_rn(c, dy), dy), bdy = __fmul_rn(b2, dy);
         const int wa = xa >> 5, wb = xb >> 5;
-        for (int wx = wa; wx <= wb; ++wx) {
+        for (int wx = wa; wx <= wb && !h; ++wx) {
           if (!((__ldg(crow + (wx >> 5)) >> (wx & 31)) & 1u)) continue;
           uint32_t m = __ldg(vmask + (int64_t)y * wpr + wx);
           if (wx == wa) m &= ~0u << (xa & 31);
@@ -221,12 +180,110 @@ __global__ __launch_bounds__(kMaskThreads) void k_dynamic_mask(const float *__re
             const float dx = __fsub_rn(__fadd_rn((float)x, 0.5f), mx);
             const float q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(a, dx), dx), cyy), __fmul_rn(bdy, dx));
             if (q <= kQMax) {
-              const uint32_t ty = t / (uint32_t)atlas_w, tx = t - ty * (uint32_t)atlas_w;
-              atomicOr(dyn + (size_t)ty * (((uint32_t)atlas_w + 31u) >> 5) + (tx >> 5), 1u << (tx & 31u));
-              return;
+              h = true;
+              break;
             }
           }
         }
+      }
+    }
+    if (__any_sync(0xffffffffu, h)) return true;
+  }
+  return false;
+}
+
+// Alg. 1 step 5 and the OR over views.  A warp holds 32 Gaussians and
+// walks the views together.  Per view each lane does the cheap part for
+// its own pair: the square of radius r around the mean, the conservative
+// extent filter (rows within 3 sqrt(a / det) of the mean, columns within
+// 3 sqrt(c / det), widened) and the block mask over that rectangle.  The
+// pairs whose rectangle reaches a moving block are then scanned one after
+// the other by the whole warp (warp_pair_hits), so that a long scan near
+// the motion does not run on one lane while the others wait.  A Gaussian
+// is marked at its first hit and takes no further views.
+__global__ __launch_bounds__(kMaskThreads) void k_dynamic_mask(const float *__restrict__ rec,
+                                                                const uint32_t *__restrict__ texel,
+                                                                const uint32_t *__restrict__ mask,
+                                                                const uint32_t *__restrict__ coarse,
+                                                                const DevView *__restrict__ views, int V,
+                                                                int64_t N, int atlas_w, int atlas_h, float r_max,
+                                                                uint32_t *dyn) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kMaskThreads + threadIdx.x;
+  uint32_t t = 0;
+  bool live = g < N;
+  if (live) {
+    t = __ldg(texel + g);
+    // texel ids past the atlas (unwritten after a live-count mismatch) are skipped
+    live = t < (uint32_t)atlas_w * (uint32_t)atlas_h;
+  }
+  for (int v = 0; v < V; ++v) {
+    if (!__any_sync(0xffffffffu, live)) break;
+    const DevView &view = views[v];
+    const int W = view.width, H = view.height, wpr = (W + 31) >> 5, cpr = (wpr + 31) >> 5;
+    const uint32_t *vmask = mask + view.mask_off;
+    const uint32_t *vcoarse = coarse + view.coarse_off;
+    float mx = 0.0f, my = 0.0f, a = 0.0f, b = 0.0f, c = 0.0f;
+    int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
+    bool need = false;
+    if (live) {
+      const size_t pr = ((size_t)v * N + g) * kRec;
+      const float4 r0 = __ldg(reinterpret_cast<const float4 *>(rec + pr));
+      const float2 r1 = __ldg(reinterpret_cast<const float2 *>(rec + pr + 4));
+      float rad = __ldg(rec + pr + 7);
+      mx = r0.x;
+      my = r0.y;
+      a = r0.z;
+      b = r0.w;
+      c = r1.x;
+      if (r_max > 0.0f && rad > r_max) rad = r_max;
+      if (rad > 0.0f && isfinite(mx) && isfinite(my)) {
+        const float ax = __fsub_rn(mx, 0.5f), ay = __fsub_rn(my, 0.5f);
+        const float lox = fmaxf(ceilf(__fsub_rn(ax, rad)), 0.0f),
+                    hix = fminf(floorf(__fadd_rn(ax, rad)), (float)(W - 1));
+        const float loy = fmaxf(ceilf(__fsub_rn(ay, rad)), 0.0f),
+                    hiy = fminf(floorf(__fadd_rn(ay, rad)), (float)(H - 1));
+        if (lox <= hix && loy <= hiy) {
+          x0 = (int)lox;
+          x1 = (int)hix;
+          y0 = (int)loy;
+          y1 = (int)hiy;
+          const float det = a * c - b * b;
+          if (a > 0.0f && c > 0.0f && det > 0.0f && isfinite(det)) {
+            const float ey = 3.0f * sqrtf(a / det) * 1.001f + 1.0f, ex = 3.0f * sqrtf(c / det) * 1.001f + 1.0f;
+            y0 = max(y0, (int)fmaxf(ceilf(ay - ey), 0.0f));
+            y1 = min(y1, (int)fminf(floorf(ay + ey), (float)(H - 1)));
+            x0 = max(x0, (int)fmaxf(ceilf(ax - ex), 0.0f));
+            x1 = min(x1, (int)fminf(floorf(ax + ex), (float)(W - 1)));
+          }
+          // does a block of the rectangle move?
+          const int w0 = x0 >> 5, w1 = x1 >> 5;
+          for (int cy = y0 >> 5; y0 <= y1 && x0 <= x1 && cy <= (y1 >> 5) && !need; ++cy) {
+            const uint32_t *crow = vcoarse + (int64_t)cy * cpr;
+            for (int cw = w0 >> 5; cw <= (w1 >> 5) && !need; ++cw) {
+              uint32_t cm = __ldg(crow + cw);
+              if (cw == (w0 >> 5)) cm &= ~0u << (w0 & 31);
+              if (cw == (w1 >> 5)) cm &= ~0u >> (31 - (w1 & 31));
+              need = cm != 0u;
+            }
+          }
+        }
+      }
+    }
+    uint32_t todo = __ballot_sync(0xffffffffu, need);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1u;
+      const float smx = __shfl_sync(0xffffffffu, mx, src), smy = __shfl_sync(0xffffffffu, my, src);
+      const float sa = __shfl_sync(0xffffffffu, a, src), sb = __shfl_sync(0xffffffffu, b, src);
+      const float sc = __shfl_sync(0xffffffffu, c, src);
+      const int sx0 = __shfl_sync(0xffffffffu, x0, src), sx1 = __shfl_sync(0xffffffffu, x1, src);
+      const int sy0 = __shfl_sync(0xffffffffu, y0, src), sy1 = __shfl_sync(0xffffffffu, y1, src);
+      if (warp_pair_hits(smx, smy, sa, sb, sc, sx0, sx1, sy0, sy1, W, wpr, cpr, vmask, vcoarse, lane) &&
+          lane == src) {
+        const uint32_t ty = t / (uint32_t)atlas_w, tx = t - ty * (uint32_t)atlas_w;
+        atomicOr(dyn + (size_t)ty * (((uint32_t)atlas_w + 31u) >> 5) + (tx >> 5), 1u << (tx & 31u));
+        live = false;
       }
     }
   }
