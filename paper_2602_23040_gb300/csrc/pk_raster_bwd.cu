@@ -149,14 +149,13 @@ __device__ __forceinline__ void conic_mean_grads(const float4 &a, const float4 &
 // kTma: the records of the next (earlier) batch are fetched into shared
 // memory by bulk copies (one 48-byte copy per splat, completed on an
 // mbarrier) while the current batch is processed.  kPx: pixels per thread.
-// At 4 pixels per thread the kernel is held to 72 registers (no spills) for
-// 14 resident CTAs per SM: with the packed pixel pairs, 64 registers spill
-// in the splat loop and 80 leave 12 CTAs, both slower.
+// At 4 pixels per thread the kernel is held to 64 registers (no spills) for
+// 16 resident CTAs per SM (72 registers and 14 CTAs: 1 % slower).
 // kT: side of the tiles the lists were binned for; each CTA takes a 16 x 16
 // quadrant of one, as in the forward.  kCount: count the evaluations (a
 // measurement; the variant without it carries no counter in its loop).
 template <int kBatch, bool kTma, int kPx, int kT, bool kCount>
-__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 14 : 1)) void k_raster_bwd(
+__global__ __launch_bounds__(Geo<kPx>::kThreads, (kPx == 4 ? 16 : 1)) void k_raster_bwd(
     const float *__restrict__ rec, const uint32_t *__restrict__ vals, const uint64_t *__restrict__ ranges,
     const DevView *__restrict__ views, const uint32_t *__restrict__ toff, int V, uint32_t n_items, float bg0,
     float bg1, float bg2, const float *__restrict__ Tfin, const uint32_t *__restrict__ ncontrib,
